@@ -1,0 +1,375 @@
+"""Benchmark: beam segments/s of the hybrid beam/ray tracer on one GB300.
+
+Workload (default): the district configuration -- a synthetic 2 km x 2 km
+city of 5,000 extruded buildings (198,903 triangles), 1,000 point sources at
+0.5 m on lane centres, 20,480 beams per source (icosahedron level 5),
+reflection orders 0..6, 250,000 microphones on a 4 m grid at 1.5 m.
+
+One step = the whole hot path on one batch: scene ingest and BVH build,
+microphone binning, beam generation, axis-ray traversal, reflection,
+microphone test and energy scatter, level readout.
+
+  value   device-resident inputs (torch CUDA tensors) -> segments/s
+  e2e     the same calls with pinned host buffers, host->device copies and the
+          device->host read of the levels inside the timed region
+
+`--impl reference` times the FP64 CPU oracle instead, on a bounded sample of
+the same workload (a seeded subset of the sources per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "beam segments/s"
+UNIT = "segments/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="district", choices=["district", "tiny"])
+    ap.add_argument("--sources", type=int, default=None, help="override the source count")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def make_workload(name, rank=0, n_sources=None):
+    from paper_1912_03998_gb300 import synth
+    if name == "tiny":
+        w = synth.tiny_city(seed=1 + rank)
+    else:
+        w = synth.district(seed=2, n_sources=1000)
+        if rank:  # independent traffic snapshot per rank, same city
+            rng = np.random.Generator(np.random.PCG64(1000 + rank))
+            w.src[:, :2] = w.src[rng.permutation(len(w.src)), :2]
+    if n_sources is not None:
+        w = w.subset_sources(np.arange(min(n_sources, len(w.src))))
+    return w
+
+
+def describe(w, tiles):
+    return {"workload": f"{w.name}: {w.scene.info.get('n_buildings', 64)} buildings, "
+                        f"{w.scene.n_tris} triangles, {len(w.src)} sources, L={w.level} "
+                        f"({20 * 4 ** w.level} beams/source), K={w.max_order}, "
+                        f"{len(w.mics)} microphones",
+            "triangles": w.scene.n_tris, "sources": len(w.src), "icosa_level": w.level,
+            "max_order": w.max_order, "microphones": len(w.mics), "bands": 8,
+            "tiles": f"{tiles[0]}x{tiles[1]}"}
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out, _ = self.p.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("trace.cu", "bt_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1912_03998_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the traversal kernel from the committed ncu
+    summary, only if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "k_trace_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    return d.get("dram_bytes_per_launch_scaled")
+
+
+def flush_l2(buf):
+    buf.zero_()
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world):
+    import torch
+    from paper_1912_03998_gb300 import btrace
+    dev = torch.device("cuda", rank % max(1, torch.cuda.device_count()))
+    torch.cuda.set_device(dev)
+    w = make_workload(args.workload, rank, args.sources)
+    tiles = (1, 1)
+    stream = torch.cuda.current_stream(dev)
+    ctx = btrace.bt_create(dev.index, stream.cuda_stream)
+    D = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    d_in = dict(verts=D(w.scene.verts), tris=D(w.scene.tris), mat=D(w.scene.mat),
+                refl=D(w.scene.refl), src=D(w.src), power=D(w.power), mics=D(w.mics))
+    n_m, nb = len(w.mics), w.scene.refl.shape[1]
+    d_level = torch.empty((n_m, nb), dtype=torch.float64, device=dev)
+    params = btrace.bt_params_default()
+    params.max_order = w.max_order
+    params.tiles_x, params.tiles_y = tiles
+    l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(inp, level_out):
+        sid = btrace.bt_load_scene(ctx, inp["verts"], inp["tris"], inp["mat"], inp["refl"])
+        btrace.bt_set_sources(ctx, sid, inp["src"], inp["power"], w.level)
+        btrace.bt_set_microphones(ctx, sid, inp["mics"])
+        btrace.bt_trace(ctx, sid, params)
+        st = btrace.bt_read_levels(ctx, sid, level_out, None, None)
+        btrace.bt_unload_scene(ctx, sid)
+        return st
+
+    def timed(inp, level_out, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        stats = []
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        n0 = btrace.bt_kernel_launches()
+        for i in range(steps):
+            flush_l2(l2_flush)
+            ev[i][0].record(stream)
+            stats.append(step(inp, level_out))
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        launches = btrace.bt_kernel_launches() - n0
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, stats, launches
+
+    for _ in range(args.warmup):
+        step(d_in, d_level)
+    with Clocks(dev.index) as clk:
+        ms, stats, launches = timed(d_in, d_level, args.steps)
+    segs = sum(s["segments"] for s in stats)
+    contrib = sum(s["contributions"] for s in stats)
+    total_ms = sum(ms)
+    # roofline of the dominant kernel: algorithmic node + triangle bytes per
+    # launch (counted in one extra, untimed trace) over its mean launch time
+    tk = sum(s["trace_kernel_ms"] for s in stats)
+    sk = sum(s["scatter_kernel_ms"] for s in stats)
+    tl = sum(s["trace_launches"] for s in stats)
+    params.count_work = 1
+    cst = step(d_in, d_level)
+    params.count_work = 0
+    alg_bytes = 64.0 * cst["nodes_visited"] + 48.0 * cst["tris_tested"]
+    bytes_per_launch = alg_bytes / max(1, cst["trace_launches"])
+    achieved = bytes_per_launch / (tk / max(1, tl) * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = ncu_traffic()
+    res = dict(segs=segs, contrib=contrib, total_ms=total_ms, ms=ms, launches=launches,
+               stats=stats[-1], tk=tk, sk=sk, tl=tl, alg_bytes=alg_bytes,
+               bytes_per_launch=bytes_per_launch, achieved=achieved, peak=peak,
+               peak_kind=peak_kind, traffic=traffic, clocks=clk.summary(), work=cst, w=w,
+               tiles=tiles)
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        h_in = {k: pin(v.cpu().numpy()) for k, v in d_in.items()}
+        h_level = torch.empty((n_m, nb), dtype=torch.float64).pin_memory()
+        step(h_in, h_level)
+        e_ms, e_stats, _ = timed(h_in, h_level, args.steps)
+        h2d = sum(int(v.numel() * v.element_size()) for v in h_in.values())
+        d2h = int(h_level.numel() * h_level.element_size())
+        res["e2e"] = {"value": sum(s["segments"] for s in e_stats) / (sum(e_ms) * 1e-3),
+                      "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                      "ms_per_step": sum(e_ms) / len(e_ms)}
+    btrace.bt_destroy(ctx)
+    return res
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_sample(w, seconds, threads, rng_seed=5):
+    """Time the oracle on a seeded subset of sources sized to ~`seconds`."""
+    from oracle import oracle as O
+    sc = O.Scene(w.scene)
+    rng = np.random.Generator(np.random.PCG64(rng_seed))
+    order = rng.permutation(len(w.src))
+    n = min(len(w.src), threads)
+    t0 = time.perf_counter()
+    O.trace(sc, w.src[order[:n]], w.power[order[:n]], w.level, w.mics, w.max_order,
+            n_threads=threads)
+    pilot = time.perf_counter() - t0
+    n2 = int(min(len(w.src), max(n, n * seconds / max(pilot, 1e-3))))
+    n2 = max(threads, (n2 // threads) * threads) if n2 >= threads else n2
+    sel = order[:n2]
+    t0 = time.perf_counter()
+    r = O.trace(sc, w.src[sel], w.power[sel], w.level, w.mics, w.max_order, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return dict(value=r["stats"]["segments"] / dt, seconds=dt, n_sources=n2, stats=r["stats"])
+
+
+def run_reference(args, rank, world):
+    w = make_workload(args.workload, 0, args.sources)
+    threads = os.cpu_count() or 1
+    per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    from oracle import oracle as O
+    sc = O.Scene(w.scene)
+    probe = oracle_sample(w, per_step, threads)
+    n = probe["n_sources"]
+    rng = np.random.Generator(np.random.PCG64(77))
+    segs = 0.0
+    total = 0.0
+    for i in range(args.warmup + args.steps):
+        sel = rng.choice(len(w.src), n, replace=False)
+        t0 = time.perf_counter()
+        r = O.trace(sc, w.src[sel], w.power[sel], w.level, w.mics, w.max_order, n_threads=threads)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            segs += r["stats"]["segments"]
+            total += dt
+    value = segs / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {**describe(w, (1, 1)),
+                       "sample": f"{n} of {len(w.src)} sources per step (seeded), all microphones"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{n} of {len(w.src)} sources per step, {threads} threads"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ main
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, rank, world)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", int(os.environ.get("LOCAL_RANK", rank))))
+    res = run_ours(args, int(os.environ.get("LOCAL_RANK", rank)), world)
+    # whole-job value: segments of all ranks over the slowest rank's time
+    segs, total_ms = float(res["segs"]), float(res["total_ms"])
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([segs, total_ms], dtype=torch.float64, device="cuda")
+        s = t.clone()
+        dist.all_reduce(s[:1], op=dist.ReduceOp.SUM)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.MAX)
+        segs, total_ms = float(s[0]), float(t[1])
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    w = res["w"]
+    value = segs / (total_ms * 1e-3)
+    cfg = describe(w, res["tiles"])
+    cfg.update({"l2": "flushed before every step (256 MB write, outside the events)",
+                "precision": "FP32 traversal and microphone tests, FP64 energy accumulation",
+                "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"})
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": cfg, "clocks": res["clocks"],
+            "gpu_launches": res["launches"],
+            "contributions_per_s": res["contrib"] * world / (total_ms * 1e-3),
+            "roofline": {"kernel": "k_trace", "bound": "hbm", "achieved": res["achieved"],
+                         "peak": res["peak"], "unit": "GB/s",
+                         "frac": res["achieved"] / res["peak"], "traffic": res["traffic"],
+                         "peak_kind": res["peak_kind"],
+                         "algorithmic_bytes_per_launch": res["bytes_per_launch"],
+                         "launches_per_step": res["tl"] / args.steps,
+                         "kernel_ms_per_step": res["tk"] / args.steps,
+                         "scatter_kernel_ms_per_step": res["sk"] / args.steps,
+                         "nodes_per_segment": res["work"]["nodes_visited"] / max(1, res["work"]["segments"]),
+                         "tris_per_segment": res["work"]["tris_tested"] / max(1, res["work"]["segments"])},
+            "stats": {k: res["stats"][k] for k in ("segments", "hits", "escapes", "emitted",
+                                                   "candidates", "contributions")}}
+    if "e2e" in res:
+        line["e2e"] = res["e2e"]
+    if not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        cb = oracle_sample(w, args.cpu_seconds, threads)
+        line["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": threads,
+                                "kind": "oracle",
+                                "sample": f"{cb['n_sources']} of {len(w.src)} sources (seeded), "
+                                          f"all {len(w.mics)} microphones, {cb['seconds']:.1f} s"}
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

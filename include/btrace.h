@@ -1,0 +1,172 @@
+/*
+ * btrace.h -- C ABI of libbtrace, a GB300 (sm_103a) implementation of the
+ * hybrid beam/ray-tracing method of "Beam-tracing domain decomposition method
+ * for urban acoustic pollution" (Gbikpi-Benissan & Magoules, arXiv:1912.03998).
+ *
+ * The problem (Section 2 and Section 4): acoustic beams leave point sources,
+ * their energy split by the power per direction; each beam's intersection
+ * with a city model is resolved by its guiding (axis) ray only, and a beam is
+ * never split; every reflection creates an image (virtual) source and a
+ * mirrored beam, up to a maximum order; microphones lying inside a beam
+ * receive its energy; the result is a sound level per microphone and band.
+ *
+ * Conventions shared by every call:
+ *   - Return value: BT_OK (0) or a negative BT_E_* code.  No call aborts the
+ *     process.  After an error, bt_last_error() describes it.
+ *   - Pointers: every array argument may be host memory (pageable or pinned)
+ *     or device memory of the context's GPU; the library tells them apart by
+ *     unified addressing and copies them before the call returns.  The caller
+ *     keeps ownership of all its arrays.
+ *   - Units: metres (z up, ground at z = 0), watts, dB.  float32 inputs are
+ *     promoted exactly where the library computes in higher precision.
+ *   - Streams: all device work of a context runs on the context's stream (the
+ *     one given to bt_create, or one the context creates).  Calls are
+ *     synchronous with respect to that stream: they return once their work has
+ *     finished.  A context is not thread-safe; use one per host thread.
+ *   - Device memory: scenes, acceleration structures, microphone bins and
+ *     energy accumulators stay resident on the device until bt_destroy, or
+ *     until a later call on the same scene replaces them.
+ */
+#ifndef BTRACE_H
+#define BTRACE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BT_OK 0
+#define BT_E_INVALID (-1)    /* bad argument or input value (NaN, index out of range, ...) */
+#define BT_E_NOMEM (-2)      /* a device or host allocation failed */
+#define BT_E_CUDA (-3)       /* a CUDA runtime call failed */
+#define BT_E_STATE (-4)      /* call out of order (e.g. trace before sources are set) */
+#define BT_E_QUEUE_FULL (-5) /* a device work queue overflowed */
+#define BT_E_TIMEOUT (-6)    /* a bounded device wait gave up (watchdog) */
+
+#define BT_MAX_BANDS 8       /* octave bands 63 Hz .. 8 kHz */
+#define BT_MAX_SCENES 64     /* resident scenes per context */
+#define BT_MAX_TILES 32      /* per axis */
+
+/* Precision of the trace (Section 2 does not fix one).
+ * BT_PREC_MIXED: float32 traversal, hit tests and microphone tests; float64
+ * energy accumulation.  It is the only mode implemented so far; the others are
+ * rejected with BT_E_INVALID. */
+#define BT_PREC_FP32 0
+#define BT_PREC_MIXED 1
+#define BT_PREC_FP64 2
+
+typedef struct bt_ctx bt_ctx;
+
+/* Parameters of one trace.  Start from bt_params_default(). */
+typedef struct {
+  int32_t max_order;                        /* K: reflections traced, orders 0..K (0..32) */
+  float air_atten_db_per_m[BT_MAX_BANDS];   /* air damping per band, dB/m (Section 2); default 0 */
+  float energy_threshold_w;                 /* delete a reflected beam whose largest per-band
+                                               power W_b*prod(r_b) falls below this; 0 = off */
+  float t_eps_m;                            /* self-hit guard, metres; default 1e-3 */
+  int32_t tiles_x, tiles_y;                 /* sub-domain grid over the scene's xy box
+                                               (Section 3); 1 x 1 = no split; max 32 x 32 */
+  int32_t precision;                        /* BT_PREC_* */
+  int32_t watchdog_ms;                      /* bound on any device-side wait; default 2000 */
+  int32_t chunk_beams;                      /* beam lineages per launch batch; 0 = automatic */
+  int32_t count_work;                       /* 1: also count BVH nodes visited and triangles
+                                               tested (slower; for roofline accounting) */
+} bt_trace_params;
+
+/* Counters of the last trace of a scene. */
+typedef struct {
+  int64_t beams;          /* primary beams launched: n_sources * 20 * 4^L */
+  int64_t segments;       /* beam segments traced (one per axis-ray query) */
+  int64_t hits;           /* segments whose axis ray hit a triangle */
+  int64_t escapes;        /* segments whose axis ray left the scene */
+  int64_t emitted;        /* segments whose footprint overlapped the microphone grid */
+  int64_t candidates;     /* microphones tested against a segment */
+  int64_t contributions;  /* (microphone, segment) pairs inside the beam */
+  int64_t handoffs;       /* rays passed from one sub-domain to the next */
+  int64_t steals;         /* work items taken from another sub-domain's queue */
+  int64_t rounds;         /* sub-domain exchange rounds */
+  int64_t nodes_visited;  /* BVH nodes fetched (only with count_work) */
+  int64_t tris_tested;    /* triangles tested (only with count_work) */
+  int64_t trace_launches; /* launches of the traversal kernel */
+  int64_t scatter_launches; /* launches of the microphone scatter kernel */
+  double trace_ms;        /* device time of the whole trace (CUDA events) */
+  double trace_kernel_ms; /* summed device time of the traversal kernel launches */
+  double scatter_kernel_ms; /* summed device time of the scatter kernel launches */
+} bt_stats;
+
+/* Fill *p with the defaults: K = 4, no air damping, no threshold, t_eps = 1 mm,
+ * 1 x 1 tiles, BT_PREC_MIXED, watchdog 2000 ms, automatic chunking. */
+int bt_params_default(bt_trace_params *p);
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to run on, or NULL for a stream owned by the context.  On success *out owns
+ * all device memory of the context. */
+int bt_create(bt_ctx **out, int device, void *cuda_stream);
+
+/* Free every resource of the context (waits for its stream first).  NULL is a
+ * no-op. */
+int bt_destroy(bt_ctx *ctx);
+
+/* Load a city model (Section 4: buildings and ground as triangles) and build
+ * its acceleration structure on the device (Section 2: the guiding ray is
+ * resolved by efficient ray shooting).
+ *   verts        [n_verts][3] float32, metres
+ *   tris         [n_tris][3] int32 vertex indices, 0 <= index < n_verts
+ *   tri_material [n_tris] uint8, < n_materials
+ *   refl         [n_materials][n_bands] float32 energy reflection coefficients in [0, 1]
+ *   n_bands      1..BT_MAX_BANDS
+ * *scene_id_out receives the new scene's id (0..BT_MAX_SCENES-1).  Errors:
+ * BT_E_INVALID for NaN/inf coordinates, indices or materials out of range,
+ * coefficients outside [0, 1]; BT_E_NOMEM; BT_E_CUDA. */
+int bt_load_scene(bt_ctx *ctx, const float *verts, int64_t n_verts, const int32_t *tris,
+                  int64_t n_tris, const uint8_t *tri_material, const float *refl,
+                  int32_t n_materials, int32_t n_bands, int32_t *scene_id_out);
+
+/* Drop a scene and its device memory. */
+int bt_unload_scene(bt_ctx *ctx, int32_t scene_id);
+
+/* Point sources of a scene (Section 4: car traffic sources).
+ *   pos     [n_s][3] float32
+ *   power_w [n_s][n_bands] float32 acoustic power per band, >= 0
+ *   icosa_level L in 0..8: each source emits 20 * 4^L beams, one per face of
+ *   a geodesic icosahedron, each carrying power_w * (solid angle / 4 pi)
+ *   (Section 2: the source energy is split between beams by direction). */
+int bt_set_sources(bt_ctx *ctx, int32_t scene_id, const float *pos, const float *power_w,
+                   int64_t n_s, int32_t icosa_level);
+
+/* Microphones of a scene (Section 4: a regular grid of receivers).
+ *   pos [n_m][3] float32.  They are binned on the device into an xy cell grid
+ *   (Section 3: microphones are partitioned with the geometry). */
+int bt_set_microphones(bt_ctx *ctx, int32_t scene_id, const float *pos, int64_t n_m);
+
+/* Trace every beam of every source of the scene (Section 2, hybrid method)
+ * and accumulate per-microphone, per-band intensity.  Replaces the result of
+ * any earlier trace of the scene.  Errors: BT_E_STATE when sources or
+ * microphones are missing; BT_E_INVALID for bad parameters;
+ * BT_E_QUEUE_FULL / BT_E_TIMEOUT from the sub-domain scheduler. */
+int bt_trace(bt_ctx *ctx, int32_t scene_id, const bt_trace_params *p);
+
+/* Read the result of the last trace of the scene.
+ *   level_db  [n_m][n_bands] float64: 10 log10(I / 1e-12 W/m^2), -inf where no
+ *             beam reached the microphone (Section 4: sound level distribution)
+ *   intensity [n_m][n_bands] float64 W/m^2, may be NULL
+ *   path_count [n_m] int32 beam segments that contained the microphone, may be NULL
+ *   stats     may be NULL
+ * level_db may also be NULL when only the other outputs are wanted. */
+int bt_read_levels(bt_ctx *ctx, int32_t scene_id, double *level_db, double *intensity,
+                   int32_t *path_count, bt_stats *stats);
+
+/* Message of the last error of the context ("" if none).  Valid until the
+ * next call on the context. */
+const char *bt_last_error(const bt_ctx *ctx);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all contexts).  Lets a caller count the kernels inside a timed region. */
+int64_t bt_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BTRACE_H */

@@ -1,0 +1,245 @@
+"""Python binding of libbtrace (include/btrace.h): argument marshalling only.
+
+The functions carry the C names and arguments.  Arrays may be numpy arrays
+(host memory) or torch tensors (host or CUDA memory of the context's device);
+the library copies them.  Every step of the trace runs in the CUDA kernels of
+libbtrace.so; there is no fallback, and importing the binding fails loudly
+when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build_lib
+
+BT_OK = 0
+BT_E_INVALID, BT_E_NOMEM, BT_E_CUDA, BT_E_STATE, BT_E_QUEUE_FULL, BT_E_TIMEOUT = -1, -2, -3, -4, -5, -6
+BT_MAX_BANDS = 8
+BT_PREC_FP32, BT_PREC_MIXED, BT_PREC_FP64 = 0, 1, 2
+
+_ERR_NAMES = {BT_E_INVALID: "BT_E_INVALID", BT_E_NOMEM: "BT_E_NOMEM", BT_E_CUDA: "BT_E_CUDA",
+              BT_E_STATE: "BT_E_STATE", BT_E_QUEUE_FULL: "BT_E_QUEUE_FULL",
+              BT_E_TIMEOUT: "BT_E_TIMEOUT"}
+
+
+class bt_trace_params(C.Structure):
+    _fields_ = [("max_order", C.c_int32), ("air_atten_db_per_m", C.c_float * BT_MAX_BANDS),
+                ("energy_threshold_w", C.c_float), ("t_eps_m", C.c_float),
+                ("tiles_x", C.c_int32), ("tiles_y", C.c_int32), ("precision", C.c_int32),
+                ("watchdog_ms", C.c_int32), ("chunk_beams", C.c_int32), ("count_work", C.c_int32)]
+
+
+class bt_stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("beams", "segments", "hits", "escapes", "emitted",
+                                         "candidates", "contributions", "handoffs", "steals",
+                                         "rounds", "nodes_visited", "tris_tested", "trace_launches",
+                                         "scatter_launches")] + \
+        [(n, C.c_double) for n in ("trace_ms", "trace_kernel_ms", "scatter_kernel_ms")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class BtError(RuntimeError):
+    def __init__(self, code, message):
+        super().__init__(f"{_ERR_NAMES.get(code, code)}: {message}")
+        self.code = code
+        self.message = message
+
+
+_lock = threading.Lock()
+_lib = None
+EXPECTED_SYMBOLS = ("bt_params_default", "bt_create", "bt_destroy", "bt_load_scene",
+                    "bt_unload_scene", "bt_set_sources", "bt_set_microphones", "bt_trace",
+                    "bt_read_levels", "bt_last_error", "bt_kernel_launches")
+
+
+def lib_path() -> str:
+    return build_lib.LIB
+
+
+def lib():
+    """Load libbtrace.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(build_lib.LIB):
+                raise RuntimeError(f"{build_lib.LIB} is missing: build it with "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(build_lib.LIB)
+            p, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+            L.bt_params_default.argtypes = [C.POINTER(bt_trace_params)]
+            L.bt_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, p]
+            L.bt_destroy.argtypes = [p]
+            L.bt_load_scene.argtypes = [p, p, i64, p, i64, p, p, i32, i32, C.POINTER(i32)]
+            L.bt_unload_scene.argtypes = [p, i32]
+            L.bt_set_sources.argtypes = [p, i32, p, p, i64, i32]
+            L.bt_set_microphones.argtypes = [p, i32, p, i64]
+            L.bt_trace.argtypes = [p, i32, C.POINTER(bt_trace_params)]
+            L.bt_read_levels.argtypes = [p, i32, p, p, p, C.POINTER(bt_stats)]
+            L.bt_last_error.argtypes = [p]
+            L.bt_last_error.restype = C.c_char_p
+            L.bt_kernel_launches.argtypes = []
+            L.bt_kernel_launches.restype = C.c_int64
+            for name in EXPECTED_SYMBOLS:
+                if name not in ("bt_last_error", "bt_kernel_launches"):
+                    getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _arr(x, dtype):
+    """(pointer, n_elements, keepalive) of a numpy array or torch tensor."""
+    if x is None:
+        return None, 0, None
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):  # torch tensor
+        import torch
+        tdt = {np.float32: torch.float32, np.int32: torch.int32, np.uint8: torch.uint8,
+               np.float64: torch.float64}[np.dtype(dtype).type]
+        t = x.to(tdt).contiguous()
+        return C.c_void_p(t.data_ptr()), t.numel(), t
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data_as(C.c_void_p), a.size, a
+
+
+def _check(rc, ctx):
+    if rc != BT_OK:
+        msg = lib().bt_last_error(ctx)
+        raise BtError(rc, msg.decode() if msg else "")
+
+
+def bt_params_default() -> bt_trace_params:
+    p = bt_trace_params()
+    lib().bt_params_default(C.byref(p))
+    return p
+
+
+def bt_create(device: int = 0, stream=None):
+    """Context on `device`; `stream` is a cudaStream_t handle (int) or None."""
+    h = C.c_void_p()
+    rc = lib().bt_create(C.byref(h), int(device), C.c_void_p(stream) if stream else None)
+    if rc != BT_OK:
+        raise BtError(rc, "bt_create failed")
+    return h
+
+
+def bt_destroy(ctx):
+    lib().bt_destroy(ctx)
+
+
+def bt_kernel_launches() -> int:
+    return int(lib().bt_kernel_launches())
+
+
+def bt_last_error(ctx) -> str:
+    m = lib().bt_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def bt_load_scene(ctx, verts, tris, tri_material, refl) -> int:
+    pv, nv, kv = _arr(verts, np.float32)
+    pt, nt, kt = _arr(tris, np.int32)
+    pm, nm, km = _arr(tri_material, np.uint8)
+    pr, nr, kr = _arr(refl, np.float32)
+    shape = getattr(refl, "shape", None) or np.asarray(refl).shape
+    n_mat, n_bands = int(shape[0]), int(shape[1])
+    sid = C.c_int32(-1)
+    rc = lib().bt_load_scene(ctx, pv, nv // 3, pt, nt // 3, pm, pr, n_mat, n_bands, C.byref(sid))
+    _check(rc, ctx)
+    return sid.value
+
+
+def bt_unload_scene(ctx, scene_id: int):
+    _check(lib().bt_unload_scene(ctx, int(scene_id)), ctx)
+
+
+def bt_set_sources(ctx, scene_id: int, pos, power_w, icosa_level: int):
+    pp, npos, kp = _arr(pos, np.float32)
+    pw, _, kw = _arr(power_w, np.float32)
+    _check(lib().bt_set_sources(ctx, int(scene_id), pp, pw, npos // 3, int(icosa_level)), ctx)
+
+
+def bt_set_microphones(ctx, scene_id: int, pos):
+    pp, n, kp = _arr(pos, np.float32)
+    _check(lib().bt_set_microphones(ctx, int(scene_id), pp, n // 3), ctx)
+
+
+def bt_trace(ctx, scene_id: int, params: bt_trace_params):
+    _check(lib().bt_trace(ctx, int(scene_id), C.byref(params)), ctx)
+
+
+def bt_read_levels(ctx, scene_id: int, level_db=None, intensity=None, path_count=None):
+    """Write into the given output arrays (numpy or torch, host or device;
+    NULL where None) and return the trace's stats as a dict."""
+    def out_ptr(x):
+        if x is None:
+            return None
+        if hasattr(x, "data_ptr"):
+            assert x.is_contiguous()
+            return C.c_void_p(x.data_ptr())
+        assert x.flags["C_CONTIGUOUS"] and x.flags["WRITEABLE"]
+        return x.ctypes.data_as(C.c_void_p)
+    st = bt_stats()
+    rc = lib().bt_read_levels(ctx, int(scene_id), out_ptr(level_db), out_ptr(intensity),
+                              out_ptr(path_count), C.byref(st))
+    _check(rc, ctx)
+    return st.as_dict()
+
+
+class Tracer:
+    """Convenience wrapper: one context, scenes loaded from synth.Workload-like
+    objects, results returned as numpy arrays."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.ctx = bt_create(device, stream)
+
+    def close(self):
+        if self.ctx:
+            bt_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, w) -> int:
+        sid = bt_load_scene(self.ctx, w.scene.verts, w.scene.tris, w.scene.mat, w.scene.refl)
+        bt_set_sources(self.ctx, sid, w.src, w.power, w.level)
+        bt_set_microphones(self.ctx, sid, w.mics)
+        return sid
+
+    def params(self, max_order, **kw) -> bt_trace_params:
+        p = bt_params_default()
+        p.max_order = int(max_order)
+        for k, v in kw.items():
+            if k == "air_atten_db_per_m":
+                for b, a in enumerate(v):
+                    p.air_atten_db_per_m[b] = float(a)
+            else:
+                setattr(p, k, v)
+        return p
+
+    def run(self, w, sid=None, **kw):
+        """Trace workload w; returns dict(level, I, cnt, stats) as numpy."""
+        if sid is None:
+            sid = self.load(w)
+        bt_trace(self.ctx, sid, self.params(w.max_order, **kw))
+        nb = int(w.scene.refl.shape[1])
+        n = len(w.mics)
+        L = np.empty((n, nb), np.float64)
+        I = np.empty((n, nb), np.float64)
+        cnt = np.empty(n, np.int32)
+        st = bt_read_levels(self.ctx, sid, L, I, cnt)
+        return dict(level=L, I=I, cnt=cnt, stats=st, scene_id=sid)

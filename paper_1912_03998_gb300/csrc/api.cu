@@ -1,0 +1,612 @@
+// api.cu -- the C ABI of libbtrace (declared in include/btrace.h).
+//
+// Host code only arranges memory and launches; every step of the trace runs
+// in the kernels of build.cu and trace.cu.  All device work of a context is
+// ordered on the context's stream.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+#include <vector>
+
+#include "bt_internal.cuh"
+
+#define BT_API extern "C" __attribute__((visibility("default")))
+
+namespace bt {
+static std::atomic<long long> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace bt
+
+namespace {
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+
+struct SceneState {
+  bool used = false;
+  int64_t n_tris = 0;
+  int n_mat = 0, n_bands = 0;
+  int root = -1;
+  float box[6] = {0, 0, 0, 0, 0, 0};
+  DevBuf nodes, tris, planes, refl;
+  // sources
+  bool has_src = false;
+  int64_t n_src = 0;
+  int level = 0;
+  DevBuf src, power;
+  // microphones
+  bool has_mics = false;
+  int64_t n_mics = 0;
+  int side = 1;
+  DevBuf mics, cell_start, grid, energy, count;
+  // result
+  bool traced = false;
+  bt_stats stats;
+  DevBuf out_level, out_int, out_cnt;
+};
+
+}  // namespace
+
+struct bt_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int n_sm = 1;
+  SceneState sc[BT_MAX_SCENES];
+  char err[512] = {0};
+  DevBuf scratch, stage_a, stage_b, stage_c, segs;
+  bt::Counters *d_ctr = nullptr;
+  bt::Counters *h_ctr = nullptr;  // pinned
+  unsigned long long *d_seg_count = nullptr;
+  float *d_box = nullptr;  // scene box of the scene being loaded (6 floats)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<cudaEvent_t> kev;  // pairs of events around kernel launches of one trace
+  std::vector<DevBuf> pool;      // released device buffers, reused before any new cudaMalloc
+};
+
+namespace {
+
+int fail(bt_ctx *c, int code, const char *fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+struct DeviceGuard {
+  int prev = -1, want;
+  explicit DeviceGuard(int d) : want(d) {
+    cudaGetDevice(&prev);
+    if (prev != want) cudaSetDevice(want);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0 && prev != want) cudaSetDevice(prev);
+  }
+};
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? BT_E_NOMEM : BT_E_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+  } while (0)
+
+// Grow-only device buffer.  A buffer that is too small goes back to the
+// context's pool; the smallest pooled buffer that fits is taken before any new
+// allocation.  Every user of a buffer runs on the context's one stream, so a
+// reused buffer is only touched after the work that used it before.
+int ensure(bt_ctx *c, DevBuf &b, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (b.cap >= bytes) return BT_OK;
+  if (b.p) {
+    c->pool.push_back(b);
+    b = DevBuf();
+  }
+  int best = -1;
+  for (int i = 0; i < (int)c->pool.size(); i++)
+    if (c->pool[i].cap >= bytes && (best < 0 || c->pool[i].cap < c->pool[best].cap)) best = i;
+  if (best >= 0) {
+    b = c->pool[best];
+    c->pool.erase(c->pool.begin() + best);
+    return BT_OK;
+  }
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    // give the pool back to the device and retry once
+    CK(cudaStreamSynchronize(c->stream));
+    for (DevBuf &q : c->pool) cudaFree(q.p);
+    c->pool.clear();
+    e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b = DevBuf();
+      return fail(c, BT_E_NOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+  }
+  b.cap = bytes;
+  return BT_OK;
+}
+
+void release(DevBuf &b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+// Scene buffers go back to the context's pool (freed by bt_destroy).
+void release_scene(bt_ctx *c, SceneState &s) {
+  DevBuf *all[] = {&s.nodes, &s.tris, &s.planes, &s.refl, &s.src, &s.power, &s.mics, &s.cell_start,
+                   &s.grid, &s.energy, &s.count, &s.out_level, &s.out_int, &s.out_cnt};
+  for (DevBuf *b : all)
+    if (b->p) c->pool.push_back(*b);
+  s = SceneState();
+}
+
+#define TRY(x)                 \
+  do {                         \
+    int r_ = (x);              \
+    if (r_ != BT_OK) return r_; \
+  } while (0)
+
+int check_ctx(bt_ctx *c) { return c ? BT_OK : BT_E_INVALID; }
+
+int scene_ref(bt_ctx *c, int32_t id, SceneState **out) {
+  if (id < 0 || id >= BT_MAX_SCENES || !c->sc[id].used)
+    return fail(c, BT_E_INVALID, "unknown scene id %d", id);
+  *out = &c->sc[id];
+  return BT_OK;
+}
+
+// Reset the sticky kernel error word and the counters.
+int reset_counters(bt_ctx *c) {
+  CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(bt::Counters), c->stream));
+  return BT_OK;
+}
+
+int read_counters(bt_ctx *c) {
+  CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(bt::Counters), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return BT_OK;
+}
+
+// ---------------------------------------------------------------- packing
+__global__ void k_pack_sources(const float *pos, const float *power, int64_t n, int n_bands, float4 *src,
+                               float *pw, int *error) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+  if (!isfinite(x) || !isfinite(y) || !isfinite(z)) atomicExch(error, BT_E_INVALID);
+  src[i] = make_float4(x, y, z, 0.0f);
+  for (int b = 0; b < n_bands; b++) {
+    float w = power[i * n_bands + b];
+    if (!isfinite(w) || w < 0.0f) atomicExch(error, BT_E_INVALID);
+    pw[i * n_bands + b] = w;
+  }
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+BT_API int bt_params_default(bt_trace_params *p) {
+  if (!p) return BT_E_INVALID;
+  memset(p, 0, sizeof(*p));
+  p->max_order = 4;
+  p->t_eps_m = 1e-3f;
+  p->tiles_x = 1;
+  p->tiles_y = 1;
+  p->precision = BT_PREC_MIXED;
+  p->watchdog_ms = 2000;
+  return BT_OK;
+}
+
+BT_API int bt_create(bt_ctx **out, int device, void *cuda_stream) {
+  if (!out) return BT_E_INVALID;
+  *out = nullptr;
+  int n_dev = 0;
+  if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) {
+    cudaGetLastError();
+    return BT_E_CUDA;
+  }
+  bt_ctx *c = new (std::nothrow) bt_ctx();
+  if (!c) return BT_E_NOMEM;
+  c->device = device;
+  DeviceGuard g(device);
+  int rc = BT_OK;
+  do {
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+      rc = BT_E_CUDA;
+      break;
+    }
+    if (cuda_stream) {
+      c->stream = (cudaStream_t)cuda_stream;
+    } else {
+      if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { rc = BT_E_CUDA; break; }
+      c->own_stream = true;
+    }
+    if (cudaMalloc(&c->d_ctr, sizeof(bt::Counters)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
+    if (cudaMalloc(&c->d_seg_count, sizeof(unsigned long long)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
+    if (cudaMalloc(&c->d_box, 8 * sizeof(float)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
+    if (cudaMallocHost(&c->h_ctr, sizeof(bt::Counters)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
+    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) { rc = BT_E_CUDA; break; }
+  } while (0);
+  if (rc != BT_OK) {
+    cudaGetLastError();
+    bt_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return BT_OK;
+}
+
+BT_API int bt_destroy(bt_ctx *c) {
+  if (!c) return BT_OK;
+  DeviceGuard g(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto &s : c->sc) release_scene(c, s);
+  for (DevBuf &q : c->pool) release(q);
+  c->pool.clear();
+  release(c->scratch);
+  release(c->stage_a);
+  release(c->stage_b);
+  release(c->stage_c);
+  release(c->segs);
+  if (c->d_ctr) cudaFree(c->d_ctr);
+  if (c->d_seg_count) cudaFree(c->d_seg_count);
+  if (c->d_box) cudaFree(c->d_box);
+  if (c->h_ctr) cudaFreeHost(c->h_ctr);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  for (cudaEvent_t e : c->kev) cudaEventDestroy(e);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  cudaGetLastError();
+  delete c;
+  return BT_OK;
+}
+
+BT_API const char *bt_last_error(const bt_ctx *c) { return c ? c->err : "null context"; }
+
+BT_API int64_t bt_kernel_launches(void) { return (int64_t)bt::g_launches.load(); }
+
+BT_API int bt_load_scene(bt_ctx *c, const float *verts, int64_t n_verts, const int32_t *tris,
+                         int64_t n_tris, const uint8_t *tri_material, const float *refl,
+                         int32_t n_materials, int32_t n_bands, int32_t *scene_id_out) {
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  if (!scene_id_out) return fail(c, BT_E_INVALID, "scene_id_out is NULL");
+  if (n_verts < 0 || n_tris < 0 || n_tris > (1 << 30) || n_verts > ((int64_t)1 << 31))
+    return fail(c, BT_E_INVALID, "bad sizes n_verts=%lld n_tris=%lld", (long long)n_verts, (long long)n_tris);
+  if (n_bands < 1 || n_bands > BT_MAX_BANDS) return fail(c, BT_E_INVALID, "n_bands %d not in 1..%d", n_bands, BT_MAX_BANDS);
+  if (n_materials < 1 || n_materials > 256) return fail(c, BT_E_INVALID, "n_materials %d not in 1..256", n_materials);
+  if (n_tris > 0 && (!verts || !tris || !tri_material)) return fail(c, BT_E_INVALID, "NULL geometry array");
+  if (!refl) return fail(c, BT_E_INVALID, "NULL reflection table");
+  DeviceGuard g(c->device);
+  int id = -1;
+  for (int i = 0; i < BT_MAX_SCENES; i++)
+    if (!c->sc[i].used) { id = i; break; }
+  if (id < 0) return fail(c, BT_E_NOMEM, "all %d scene slots are in use", BT_MAX_SCENES);
+  // reflection table: small, checked on the host
+  float hrefl[256 * BT_MAX_BANDS];
+  CK(cudaMemcpy(hrefl, refl, sizeof(float) * n_materials * n_bands, cudaMemcpyDefault));
+  for (int i = 0; i < n_materials * n_bands; i++)
+    if (!(hrefl[i] >= 0.0f && hrefl[i] <= 1.0f))
+      return fail(c, BT_E_INVALID, "reflection coefficient %d = %g not in [0,1]", i, (double)hrefl[i]);
+  SceneState &s = c->sc[id];
+  s = SceneState();
+  s.n_tris = n_tris;
+  s.n_mat = n_materials;
+  s.n_bands = n_bands;
+  int rc = BT_OK;
+  do {
+    if ((rc = ensure(c, c->stage_a, sizeof(float) * 3 * (size_t)n_verts))) break;
+    if ((rc = ensure(c, c->stage_b, sizeof(int32_t) * 3 * (size_t)n_tris))) break;
+    if ((rc = ensure(c, c->stage_c, (size_t)n_tris))) break;
+    if ((rc = ensure(c, c->scratch, bt::build_scene_scratch_bytes(n_tris)))) break;
+    if ((rc = ensure(c, s.nodes, sizeof(bt::Node) * (size_t)(n_tris > 1 ? n_tris - 1 : 1)))) break;
+    if ((rc = ensure(c, s.tris, sizeof(bt::Tri) * (size_t)n_tris))) break;
+    if ((rc = ensure(c, s.planes, sizeof(bt::Plane) * (size_t)n_tris))) break;
+    if ((rc = ensure(c, s.refl, sizeof(float) * n_materials * n_bands))) break;
+  } while (0);
+  if (rc != BT_OK) { release_scene(c, s); return rc; }
+  s.used = true;
+  cudaStream_t st = c->stream;
+  float *box = c->d_box;
+#define CKS(call)                      \
+  do {                                 \
+    cudaError_t e_ = (call);           \
+    if (e_ != cudaSuccess) {           \
+      cudaGetLastError();              \
+      release_scene(c, s);                \
+      return fail(c, BT_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    }                                  \
+  } while (0)
+  if (n_verts > 0) CKS(cudaMemcpyAsync(c->stage_a.p, verts, sizeof(float) * 3 * n_verts, cudaMemcpyDefault, st));
+  if (n_tris > 0) {
+    CKS(cudaMemcpyAsync(c->stage_b.p, tris, sizeof(int32_t) * 3 * n_tris, cudaMemcpyDefault, st));
+    CKS(cudaMemcpyAsync(c->stage_c.p, tri_material, (size_t)n_tris, cudaMemcpyDefault, st));
+  }
+  CKS(cudaMemcpyAsync(s.refl.p, hrefl, sizeof(float) * n_materials * n_bands, cudaMemcpyHostToDevice, st));
+  CKS(cudaMemsetAsync(c->d_ctr, 0, sizeof(bt::Counters), st));
+  CKS(bt::validate_scene(st, (const float *)c->stage_a.p, n_verts, (const int32_t *)c->stage_b.p, n_tris,
+                         (const uint8_t *)c->stage_c.p, n_materials, box, &c->d_ctr->error));
+  CKS(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(bt::Counters), cudaMemcpyDeviceToHost, st));
+  CKS(cudaMemcpyAsync(s.box, box, sizeof(float) * 6, cudaMemcpyDeviceToHost, st));
+  CKS(cudaStreamSynchronize(st));
+  if (c->h_ctr->error) {
+    release_scene(c, s);
+    return fail(c, BT_E_INVALID, "scene rejected: vertex index, material or coordinate out of range");
+  }
+  CKS(bt::build_scene(st, (const float *)c->stage_a.p, (const int32_t *)c->stage_b.p, n_tris,
+                      (const uint8_t *)c->stage_c.p, (bt::Node *)s.nodes.p, (bt::Tri *)s.tris.p,
+                      (bt::Plane *)s.planes.p, c->scratch.p, c->scratch.cap, box, &c->d_ctr->error));
+  CKS(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(bt::Counters), cudaMemcpyDeviceToHost, st));
+  CKS(cudaStreamSynchronize(st));
+#undef CKS
+  if (c->h_ctr->error) {
+    int e = c->h_ctr->error;
+    release_scene(c, s);
+    return fail(c, BT_E_CUDA, "acceleration structure build failed (device error %d)", e);
+  }
+  s.root = n_tris == 0 ? -1 : (n_tris == 1 ? ~0 : 0);
+  *scene_id_out = id;
+  return BT_OK;
+}
+
+BT_API int bt_unload_scene(bt_ctx *c, int32_t scene_id) {
+  TRY(check_ctx(c));
+  SceneState *s;
+  TRY(scene_ref(c, scene_id, &s));
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  release_scene(c, *s);
+  return BT_OK;
+}
+
+BT_API int bt_set_sources(bt_ctx *c, int32_t scene_id, const float *pos, const float *power_w,
+                          int64_t n_s, int32_t icosa_level) {
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  SceneState *s;
+  TRY(scene_ref(c, scene_id, &s));
+  if (n_s < 0 || n_s > (1 << 24)) return fail(c, BT_E_INVALID, "bad source count %lld", (long long)n_s);
+  if (icosa_level < 0 || icosa_level > 8) return fail(c, BT_E_INVALID, "icosa_level %d not in 0..8", icosa_level);
+  if (n_s > 0 && (!pos || !power_w)) return fail(c, BT_E_INVALID, "NULL source array");
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  TRY(ensure(c, c->stage_a, sizeof(float) * 3 * (size_t)n_s));
+  TRY(ensure(c, c->stage_b, sizeof(float) * s->n_bands * (size_t)n_s));
+  TRY(ensure(c, s->src, sizeof(float4) * (size_t)n_s));
+  TRY(ensure(c, s->power, sizeof(float) * s->n_bands * (size_t)n_s));
+  TRY(reset_counters(c));
+  if (n_s > 0) {
+    CK(cudaMemcpyAsync(c->stage_a.p, pos, sizeof(float) * 3 * n_s, cudaMemcpyDefault, st));
+    CK(cudaMemcpyAsync(c->stage_b.p, power_w, sizeof(float) * s->n_bands * n_s, cudaMemcpyDefault, st));
+    k_pack_sources<<<(int)((n_s + 255) / 256), 256, 0, st>>>((const float *)c->stage_a.p,
+                                                            (const float *)c->stage_b.p, n_s, s->n_bands,
+                                                            (float4 *)s->src.p, (float *)s->power.p,
+                                                            &c->d_ctr->error);
+    bt::note_launches(1);
+    CK(cudaGetLastError());
+  }
+  TRY(read_counters(c));
+  if (c->h_ctr->error) {
+    s->has_src = false;
+    return fail(c, BT_E_INVALID, "source position not finite or power negative/not finite");
+  }
+  s->n_src = n_s;
+  s->level = icosa_level;
+  s->has_src = true;
+  s->traced = false;
+  return BT_OK;
+}
+
+BT_API int bt_set_microphones(bt_ctx *c, int32_t scene_id, const float *pos, int64_t n_m) {
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  SceneState *s;
+  TRY(scene_ref(c, scene_id, &s));
+  if (n_m < 0 || n_m > (1 << 28)) return fail(c, BT_E_INVALID, "bad microphone count %lld", (long long)n_m);
+  if (n_m > 0 && !pos) return fail(c, BT_E_INVALID, "NULL microphone array");
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  int side = (int)ceil(sqrt((double)n_m / 4.0));
+  if (side < 1) side = 1;
+  size_t n_cells = (size_t)side * side;
+  TRY(ensure(c, c->stage_a, sizeof(float) * 3 * (size_t)n_m));
+  TRY(ensure(c, c->scratch, bt::build_mics_scratch_bytes(n_m, side)));
+  TRY(ensure(c, s->mics, sizeof(float4) * (size_t)n_m));
+  TRY(ensure(c, s->cell_start, sizeof(int) * (n_cells + 1)));
+  TRY(ensure(c, s->grid, sizeof(bt::MicGrid)));
+  TRY(ensure(c, s->energy, sizeof(double) * bt::kMaxBands * (size_t)n_m));
+  TRY(ensure(c, s->count, sizeof(int) * (size_t)n_m));
+  TRY(reset_counters(c));
+  if (n_m > 0) CK(cudaMemcpyAsync(c->stage_a.p, pos, sizeof(float) * 3 * n_m, cudaMemcpyDefault, st));
+  CK(bt::build_mics(st, (const float *)c->stage_a.p, n_m, side, (bt::MicGrid *)s->grid.p,
+                    (float4 *)s->mics.p, (int *)s->cell_start.p, c->scratch.p, c->scratch.cap,
+                    &c->d_ctr->error));
+  TRY(read_counters(c));
+  if (c->h_ctr->error) {
+    s->has_mics = false;
+    return fail(c, BT_E_INVALID, "microphone position not finite");
+  }
+  s->n_mics = n_m;
+  s->side = side;
+  s->has_mics = true;
+  s->traced = false;
+  return BT_OK;
+}
+
+BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  SceneState *s;
+  TRY(scene_ref(c, scene_id, &s));
+  if (!p) return fail(c, BT_E_INVALID, "NULL params");
+  if (!s->has_src || !s->has_mics) return fail(c, BT_E_STATE, "sources and microphones must be set before bt_trace");
+  if (p->max_order < 0 || p->max_order > 32) return fail(c, BT_E_INVALID, "max_order %d not in 0..32", p->max_order);
+  if (!(p->t_eps_m > 0.0f) || !isfinite(p->t_eps_m)) return fail(c, BT_E_INVALID, "t_eps_m must be > 0");
+  if (!(p->energy_threshold_w >= 0.0f)) return fail(c, BT_E_INVALID, "energy_threshold_w must be >= 0");
+  if (p->precision != BT_PREC_MIXED) return fail(c, BT_E_INVALID, "precision %d not implemented (use BT_PREC_MIXED)", p->precision);
+  if (p->tiles_x != 1 || p->tiles_y != 1)
+    return fail(c, BT_E_INVALID, "tiles %dx%d: only 1x1 is implemented in this build", p->tiles_x, p->tiles_y);
+  if (p->chunk_beams < 0) return fail(c, BT_E_INVALID, "chunk_beams must be >= 0");
+  int has_alpha = 0;
+  float alpha_log2[BT_MAX_BANDS];
+  for (int b = 0; b < BT_MAX_BANDS; b++) {
+    float a = p->air_atten_db_per_m[b];
+    if (!(a >= 0.0f) || !isfinite(a)) return fail(c, BT_E_INVALID, "air attenuation must be finite and >= 0");
+    alpha_log2[b] = -a * 3.32192809488736f / 10.0f;  // 10^(-a d/10) = 2^(-a d log2(10)/10)
+    if (b < s->n_bands && a != 0.0f) has_alpha = 1;
+  }
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  const int64_t n_beams = (int64_t)20 << (2 * s->level);
+  const int64_t total = s->n_src * n_beams;
+  int64_t chunk = p->chunk_beams > 0 ? p->chunk_beams : ((int64_t)1 << 23) / (p->max_order + 1);
+  if (chunk > total) chunk = total;
+  if (chunk < 1) chunk = 1;
+  const unsigned long long cap = (unsigned long long)chunk * (p->max_order + 1);
+  TRY(ensure(c, c->segs, sizeof(bt::Seg) * cap));
+  TRY(reset_counters(c));
+  CK(cudaMemsetAsync(s->energy.p, 0, sizeof(double) * bt::kMaxBands * (size_t)s->n_mics, st));
+  CK(cudaMemsetAsync(s->count.p, 0, sizeof(int) * (size_t)s->n_mics, st));
+  bt::TraceArgs ta;
+  memset(&ta, 0, sizeof(ta));
+  ta.sc.n_tris = s->n_tris;
+  ta.sc.root = s->root;
+  ta.sc.nodes = (const bt::Node *)s->nodes.p;
+  ta.sc.tris = (const bt::Tri *)s->tris.p;
+  ta.sc.planes = (const bt::Plane *)s->planes.p;
+  ta.sc.refl = (const float *)s->refl.p;
+  ta.sc.n_mat = s->n_mat;
+  ta.sc.n_bands = s->n_bands;
+  for (int k = 0; k < 3; k++) { ta.sc.lo[k] = s->box[k]; ta.sc.hi[k] = s->box[3 + k]; }
+  ta.src = (const float4 *)s->src.p;
+  ta.power = (const float *)s->power.p;
+  ta.n_src = s->n_src;
+  ta.level = s->level;
+  ta.n_beams = n_beams;
+  ta.max_order = p->max_order;
+  ta.t_eps = p->t_eps_m;
+  ta.energy_threshold = p->energy_threshold_w;
+  for (int b = 0; b < BT_MAX_BANDS; b++) ta.alpha_log2[b] = alpha_log2[b];
+  ta.has_alpha = has_alpha;
+  ta.grid = (const bt::MicGrid *)s->grid.p;
+  ta.segs = (bt::Seg *)c->segs.p;
+  ta.seg_count = c->d_seg_count;
+  ta.seg_capacity = cap;
+  ta.ctr = c->d_ctr;
+  ta.count_work = p->count_work ? 1 : 0;
+  bt::ScatterArgs sa;
+  memset(&sa, 0, sizeof(sa));
+  sa.segs = ta.segs;
+  sa.seg_count = c->d_seg_count;
+  sa.seg_capacity = cap;
+  sa.grid = ta.grid;
+  sa.mics = (const float4 *)s->mics.p;
+  sa.cell_start = (const int *)s->cell_start.p;
+  sa.energy = (double *)s->energy.p;
+  sa.count = (int *)s->count.p;
+  sa.n_bands = s->n_bands;
+  for (int b = 0; b < BT_MAX_BANDS; b++) sa.alpha_log2[b] = alpha_log2[b];
+  sa.has_alpha = has_alpha;
+  sa.ctr = c->d_ctr;
+  // events bracket every launch: [4*i, 4*i+1] traversal, [4*i+2, 4*i+3] scatter
+  const int64_t n_chunks = total > 0 ? (total + chunk - 1) / chunk : 0;
+  while ((int64_t)c->kev.size() < 4 * n_chunks) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    c->kev.push_back(e);
+  }
+  CK(cudaEventRecord(c->ev0, st));
+  for (int64_t ci = 0; ci < n_chunks; ci++) {
+    int64_t b0 = ci * chunk;
+    ta.lineage_begin = b0;
+    ta.lineage_end = b0 + chunk < total ? b0 + chunk : total;
+    CK(cudaMemsetAsync(c->d_seg_count, 0, sizeof(unsigned long long), st));
+    CK(cudaEventRecord(c->kev[4 * ci], st));
+    CK(bt::launch_trace(st, ta, c->n_sm));
+    CK(cudaEventRecord(c->kev[4 * ci + 1], st));
+    if (s->n_mics > 0) {
+      CK(cudaEventRecord(c->kev[4 * ci + 2], st));
+      CK(bt::launch_scatter(st, sa, c->n_sm));
+      CK(cudaEventRecord(c->kev[4 * ci + 3], st));
+    }
+  }
+  CK(cudaEventRecord(c->ev1, st));
+  TRY(read_counters(c));
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  double trace_kms = 0.0, scatter_kms = 0.0;
+  for (int64_t ci = 0; ci < n_chunks; ci++) {
+    float a = 0.0f;
+    CK(cudaEventElapsedTime(&a, c->kev[4 * ci], c->kev[4 * ci + 1]));
+    trace_kms += a;
+    if (s->n_mics > 0) {
+      CK(cudaEventElapsedTime(&a, c->kev[4 * ci + 2], c->kev[4 * ci + 3]));
+      scatter_kms += a;
+    }
+  }
+  const bt::Counters &h = *c->h_ctr;
+  bt_stats &o = s->stats;
+  memset(&o, 0, sizeof(o));
+  o.beams = total;
+  o.segments = (int64_t)h.segments;
+  o.hits = (int64_t)h.hits;
+  o.escapes = (int64_t)h.escapes;
+  o.emitted = (int64_t)h.emitted;
+  o.candidates = (int64_t)h.candidates;
+  o.contributions = (int64_t)h.contributions;
+  o.handoffs = (int64_t)h.handoffs;
+  o.steals = (int64_t)h.steals;
+  o.rounds = (int64_t)h.rounds;
+  o.nodes_visited = (int64_t)h.nodes_visited;
+  o.tris_tested = (int64_t)h.tris_tested;
+  o.trace_launches = n_chunks;
+  o.scatter_launches = s->n_mics > 0 ? n_chunks : 0;
+  o.trace_ms = ms;
+  o.trace_kernel_ms = trace_kms;
+  o.scatter_kernel_ms = scatter_kms;
+  if (h.error) {
+    s->traced = false;
+    return fail(c, h.error, h.error == BT_E_QUEUE_FULL ? "device queue or traversal stack overflow"
+                                                        : "device error %d", h.error);
+  }
+  s->traced = true;
+  return BT_OK;
+}
+
+BT_API int bt_read_levels(bt_ctx *c, int32_t scene_id, double *level_db, double *intensity,
+                          int32_t *path_count, bt_stats *stats) {
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  SceneState *s;
+  TRY(scene_ref(c, scene_id, &s));
+  if (!s->traced) return fail(c, BT_E_STATE, "scene %d has no trace result", scene_id);
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  const size_t nv = (size_t)s->n_mics * s->n_bands;
+  TRY(ensure(c, s->out_level, sizeof(double) * nv));
+  TRY(ensure(c, s->out_int, sizeof(double) * nv));
+  TRY(ensure(c, s->out_cnt, sizeof(int) * (size_t)s->n_mics));
+  CK(bt::launch_levels(st, (const double *)s->energy.p, (const int *)s->count.p, (const float4 *)s->mics.p,
+                       s->n_mics, s->n_bands, (double *)s->out_level.p, (double *)s->out_int.p,
+                       (int *)s->out_cnt.p));
+  if (level_db && nv) CK(cudaMemcpyAsync(level_db, s->out_level.p, sizeof(double) * nv, cudaMemcpyDefault, st));
+  if (intensity && nv) CK(cudaMemcpyAsync(intensity, s->out_int.p, sizeof(double) * nv, cudaMemcpyDefault, st));
+  if (path_count && s->n_mics)
+    CK(cudaMemcpyAsync(path_count, s->out_cnt.p, sizeof(int) * (size_t)s->n_mics, cudaMemcpyDefault, st));
+  CK(cudaStreamSynchronize(st));
+  if (stats) *stats = s->stats;
+  return BT_OK;
+}

@@ -1,0 +1,314 @@
+// bt_internal.cuh -- device data layouts and device helpers shared by the
+// kernels of libbtrace.  Not part of the public ABI (include/btrace.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "btrace.h"
+
+namespace bt {
+
+constexpr int kMaxBands = BT_MAX_BANDS;
+constexpr int kStackDepth = 64;        // BVH2 traversal stack (LBVH depth <= 64 for 30-bit keys + index)
+constexpr float kInf = __builtin_huge_valf();
+
+// ------------------------------------------------------------------ layouts
+// BVH2 node, 64 bytes: both children's boxes, so one node fetch decides both.
+// Child index c >= 0: internal node; c < 0: leaf holding triangle slot ~c.
+struct __align__(16) Node {
+  float4 lxy;  // left  lo.x, hi.x, lo.y, hi.y
+  float4 rxy;  // right lo.x, hi.x, lo.y, hi.y
+  float4 lrz;  // left lo.z, hi.z, right lo.z, hi.z
+  int4 child;  // left, right, parent, unused
+};
+
+// Triangle in leaf order, 48 bytes for the hit test: v0.w = material (int
+// bits), v1.w = original triangle id (int bits), v2.w unused.
+struct __align__(16) Tri {
+  float4 v0, v1, v2;
+};
+
+// Plane of a triangle: unit normal (x, y, z) and w = n . v0.
+using Plane = float4;
+
+struct DevScene {
+  int64_t n_tris;
+  int root;              // root child code (internal index >= 0, or ~leaf), -1 when empty
+  const Node *nodes;     // n_tris - 1 internal nodes
+  const Tri *tris;       // n_tris, leaf order
+  const Plane *planes;   // n_tris, leaf order
+  const float *refl;     // [n_mat][n_bands]
+  int n_mat, n_bands;
+  float lo[3], hi[3];    // scene box
+};
+
+// Microphone bin grid over the microphones' xy box; the box [zlo, zhi] is the
+// microphones' height slab.
+struct MicGrid {
+  float x0, y0, cw, ch, inv_cw, inv_ch, zlo, zhi;
+  int nx, ny;
+  int n_mics;
+  int pad;
+};
+
+// One beam segment handed from the trace kernel to the scatter kernel, 128 B.
+// Inside test: n_j . (m - apex) >= 0 (j = 0,1,2), start.xyz . m - start.w > 0,
+// end.xyz . m - end.w >= 0.  A missing plane is (0, 0, 0, -inf).
+struct __align__(16) Seg {
+  float4 apex;  // xyz, w: row range first (int bits)
+  float4 n0;    // w: row range last (int bits)
+  float4 n1;    // w: source index (int bits)
+  float4 n2;    // w: order (int bits)
+  float4 start;
+  float4 end;
+  float4 p03;   // per-band power W_b * prod(r_b), bands 0..3
+  float4 p47;   // bands 4..7
+};
+
+// Device counters of one trace, accumulated with atomics.
+struct Counters {
+  unsigned long long segments, hits, escapes, emitted, candidates, contributions;
+  unsigned long long handoffs, steals, rounds, overflow;
+  unsigned long long nodes_visited, tris_tested;
+  int error;  // sticky error code set by kernels (0 = none)
+  int pad;
+};
+
+struct TraceArgs {
+  DevScene sc;
+  const float4 *src;      // [n_s] xyz
+  const float *power;     // [n_s][n_bands]
+  int64_t n_src;
+  int level;              // icosahedron level L
+  int64_t n_beams;        // 20 * 4^L
+  int max_order;
+  float t_eps;
+  float energy_threshold;
+  float alpha_log2[kMaxBands];  // air damping as a base-2 exponent per metre: -alpha_b * log2(10) / 10
+  int has_alpha;
+  const MicGrid *grid;
+  int64_t lineage_begin, lineage_end;  // chunk of (source, beam) lineages
+  Seg *segs;
+  unsigned long long *seg_count;
+  unsigned long long seg_capacity;
+  Counters *ctr;
+  int count_work;
+};
+
+struct ScatterArgs {
+  const Seg *segs;
+  const unsigned long long *seg_count;
+  unsigned long long seg_capacity;
+  const MicGrid *grid;
+  const float4 *mics;       // sorted by cell: xyz, w = original index (int bits)
+  const int *cell_start;    // [nx * ny + 1]
+  double *energy;           // [n_mics][kMaxBands], sorted order
+  int *count;               // [n_mics], sorted order
+  int n_bands;
+  float alpha_log2[kMaxBands];
+  int has_alpha;
+  Counters *ctr;
+};
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return make_float3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// Cross product without contraction into FMA: b x a is then exactly -(a x b),
+// so two beams sharing an edge test it with exactly opposite signs.
+__device__ __forceinline__ float3 cross_exact(float3 a, float3 b) {
+  return make_float3(__fsub_rn(__fmul_rn(a.y, b.z), __fmul_rn(a.z, b.y)),
+                     __fsub_rn(__fmul_rn(a.z, b.x), __fmul_rn(a.x, b.z)),
+                     __fsub_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
+}
+
+__device__ __forceinline__ float3 normalize3(float3 a) { return a * rsqrtf(dot3(a, a)); }
+
+__device__ __forceinline__ float pick(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+// Ray prepared for the watertight test (Woop, Benthin & Wald, JCGT 2013):
+// axes permuted so the dominant direction component is z, plus a shear.
+struct Ray {
+  float3 o, d, inv;
+  int kx, ky, kz;
+  float sx, sy, sz;
+  float t_eps;
+  float dns;  // d . n_start for a reflected ray, 0 for a primary ray
+};
+
+__device__ __forceinline__ Ray make_ray(float3 o, float3 d, float t_eps, float dns) {
+  Ray r;
+  r.o = o;
+  r.d = d;
+  // zero components become tiny so the slab test never forms 0 * inf
+  float dx = fabsf(d.x) > 1e-20f ? d.x : copysignf(1e-20f, d.x);
+  float dy = fabsf(d.y) > 1e-20f ? d.y : copysignf(1e-20f, d.y);
+  float dz = fabsf(d.z) > 1e-20f ? d.z : copysignf(1e-20f, d.z);
+  r.inv = make_float3(1.0f / dx, 1.0f / dy, 1.0f / dz);
+  float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+  int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+  int kx = kz == 2 ? 0 : kz + 1;
+  int ky = kx == 2 ? 0 : kx + 1;
+  if (pick(d, kz) < 0.0f) { int t = kx; kx = ky; ky = t; }
+  r.kx = kx; r.ky = ky; r.kz = kz;
+  float dkz = pick(d, kz);
+  r.sx = pick(d, kx) / dkz;
+  r.sy = pick(d, ky) / dkz;
+  r.sz = 1.0f / dkz;
+  r.t_eps = t_eps;
+  r.dns = dns;
+  return r;
+}
+
+// Watertight, two-sided ray/triangle test.  Edge functions are formed
+// without FMA contraction so a shared edge gets exactly opposite values in
+// its two triangles, and recomputed in double when one is exactly zero, as
+// the published method prescribes.  Returns the hit distance or +inf.
+__device__ __forceinline__ float hit_watertight(const Ray &r, float4 v0, float4 v1, float4 v2) {
+  float3 A = f3(v0) - r.o, B = f3(v1) - r.o, C = f3(v2) - r.o;
+  float Akz = pick(A, r.kz), Bkz = pick(B, r.kz), Ckz = pick(C, r.kz);
+  float ax = pick(A, r.kx) - r.sx * Akz, ay = pick(A, r.ky) - r.sy * Akz;
+  float bx = pick(B, r.kx) - r.sx * Bkz, by = pick(B, r.ky) - r.sy * Bkz;
+  float cx = pick(C, r.kx) - r.sx * Ckz, cy = pick(C, r.ky) - r.sy * Ckz;
+  float U = __fsub_rn(__fmul_rn(cx, by), __fmul_rn(cy, bx));
+  float V = __fsub_rn(__fmul_rn(ax, cy), __fmul_rn(ay, cx));
+  float W = __fsub_rn(__fmul_rn(bx, ay), __fmul_rn(by, ax));
+  if (U == 0.0f || V == 0.0f || W == 0.0f) {
+    U = (float)((double)cx * (double)by - (double)cy * (double)bx);
+    V = (float)((double)ax * (double)cy - (double)ay * (double)cx);
+    W = (float)((double)bx * (double)ay - (double)by * (double)ax);
+  }
+  if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return kInf;
+  float det = U + V + W;
+  if (det == 0.0f) return kInf;
+  float T = U * (r.sz * Akz) + V * (r.sz * Bkz) + W * (r.sz * Ckz);
+  float t = __fdiv_rn(T, det);
+  return t;
+}
+
+// Hit acceptance (same rule as the oracle): beyond t_eps, and for a reflected
+// ray more than t_eps away from the plane it left.
+__device__ __forceinline__ bool accept_hit(const Ray &r, float t) {
+  return t > r.t_eps && (r.dns == 0.0f || t * r.dns > r.t_eps);
+}
+
+// Robust slab test (Ize 2013: the far distance is grown by 1 + 2*gamma(3)).
+__device__ __forceinline__ bool slab(const Ray &r, float lox, float hix, float loy, float hiy,
+                                     float loz, float hiz, float tmax, float &tnear) {
+  float tx0 = (lox - r.o.x) * r.inv.x, tx1 = (hix - r.o.x) * r.inv.x;
+  float ty0 = (loy - r.o.y) * r.inv.y, ty1 = (hiy - r.o.y) * r.inv.y;
+  float tz0 = (loz - r.o.z) * r.inv.z, tz1 = (hiz - r.o.z) * r.inv.z;
+  float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+  float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1)) * 1.0000004f;
+  tnear = tn;
+  return tn <= fminf(tf, tmax);
+}
+
+// ------------------------------------------------------- footprint polygon
+// Conservative xy footprint of a segment on the microphone slab: each 3D
+// half-space a.m >= b becomes, over z in [zlo, zhi], the weaker half-plane
+// ax x + ay y >= b - max(az zlo, az zhi), grown by a 1 cm slack; the grid
+// rectangle is clipped by those half-planes (Sutherland-Hodgman).
+constexpr int kPolyMax = 12;
+struct Poly {
+  float x[kPolyMax], y[kPolyMax];
+  int n;
+};
+
+__device__ __forceinline__ void poly_clip(Poly &p, float ax, float ay, float b) {
+  Poly q;
+  q.n = 0;
+  for (int i = 0; i < p.n; i++) {
+    int j = i + 1 == p.n ? 0 : i + 1;
+    float fi = ax * p.x[i] + ay * p.y[i] - b;
+    float fj = ax * p.x[j] + ay * p.y[j] - b;
+    if (fi >= 0.0f && q.n < kPolyMax) { q.x[q.n] = p.x[i]; q.y[q.n] = p.y[i]; q.n++; }
+    if ((fi >= 0.0f) != (fj >= 0.0f) && q.n < kPolyMax) {
+      float s = fi / (fi - fj);
+      q.x[q.n] = p.x[i] + s * (p.x[j] - p.x[i]);
+      q.y[q.n] = p.y[i] + s * (p.y[j] - p.y[i]);
+      q.n++;
+    }
+  }
+  p = q;
+}
+
+// Clip by the relaxation of a.m >= b; returns false when the footprint is empty.
+__device__ __forceinline__ bool poly_halfspace(Poly &p, float3 a, float b, const MicGrid &g) {
+  if (!(b > -kInf)) return true;  // missing plane
+  float bz = fmaxf(a.z * g.zlo, a.z * g.zhi);
+  float axy = fabsf(a.x) + fabsf(a.y);
+  float bb = b - bz - 0.01f * axy - 1e-6f * fabsf(b);
+  if (axy == 0.0f) return bb <= 0.0f;
+  poly_clip(p, a.x, a.y, bb);
+  return p.n >= 3;
+}
+
+// Footprint of segment s over the grid; returns false if empty.
+__device__ __forceinline__ bool seg_footprint(const Seg &s, const MicGrid &g, Poly &p) {
+  float m = 0.01f;
+  float X0 = g.x0 - m, X1 = g.x0 + g.cw * g.nx + m, Y0 = g.y0 - m, Y1 = g.y0 + g.ch * g.ny + m;
+  p.n = 4;
+  p.x[0] = X0; p.y[0] = Y0;
+  p.x[1] = X1; p.y[1] = Y0;
+  p.x[2] = X1; p.y[2] = Y1;
+  p.x[3] = X0; p.y[3] = Y1;
+  float3 A = f3(s.apex);
+  float3 n0 = f3(s.n0), n1 = f3(s.n1), n2 = f3(s.n2);
+  if (!poly_halfspace(p, n0, dot3(n0, A), g)) return false;
+  if (!poly_halfspace(p, n1, dot3(n1, A), g)) return false;
+  if (!poly_halfspace(p, n2, dot3(n2, A), g)) return false;
+  if (!poly_halfspace(p, f3(s.start), s.start.w, g)) return false;
+  if (!poly_halfspace(p, f3(s.end), s.end.w, g)) return false;
+  return true;
+}
+
+// x extent of the polygon within the strip y in [ya, yb]
+__device__ __forceinline__ void poly_strip_x(const Poly &p, float ya, float yb, float &xmin, float &xmax) {
+  xmin = kInf;
+  xmax = -kInf;
+  for (int i = 0; i < p.n; i++) {
+    int j = i + 1 == p.n ? 0 : i + 1;
+    float xi = p.x[i], yi = p.y[i], xj = p.x[j], yj = p.y[j];
+    if (yi >= ya && yi <= yb) { xmin = fminf(xmin, xi); xmax = fmaxf(xmax, xi); }
+    if ((yi < ya) != (yj < ya) && yi != yj) {
+      float x = xi + (ya - yi) / (yj - yi) * (xj - xi);
+      xmin = fminf(xmin, x); xmax = fmaxf(xmax, x);
+    }
+    if ((yi < yb) != (yj < yb) && yi != yj) {
+      float x = xi + (yb - yi) / (yj - yi) * (xj - xi);
+      xmin = fminf(xmin, x); xmax = fmaxf(xmax, x);
+    }
+  }
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+}  // namespace bt
+
+// ------------------------------------------------------------ host launchers
+namespace bt {
+// process-wide count of kernel launches (host side), read by bt_kernel_launches()
+void note_launches(int n);
+// scene build in two steps: validation (sets *d_error, fills the scene box)
+// and, only if validation passed, the BVH build.
+cudaError_t validate_scene(cudaStream_t st, const float *d_verts, int64_t n_verts,
+                           const int32_t *d_tris, int64_t n_tris, const uint8_t *d_mat, int n_mat,
+                           float *d_box /*lo xyz, hi xyz*/, int *d_error);
+cudaError_t build_scene(cudaStream_t st, const float *d_verts, const int32_t *d_tris, int64_t n_tris,
+                        const uint8_t *d_mat, Node *d_nodes, Tri *d_tris_out, Plane *d_planes,
+                        void *d_scratch, size_t scratch_bytes, const float *d_box, int *d_error);
+size_t build_scene_scratch_bytes(int64_t n_tris);
+cudaError_t build_mics(cudaStream_t st, const float *d_pos, int64_t n_m, int side, MicGrid *d_grid,
+                       float4 *d_sorted, int *d_cell_start, void *d_scratch, size_t scratch_bytes,
+                       int *d_error);
+size_t build_mics_scratch_bytes(int64_t n_m, int side);
+cudaError_t launch_trace(cudaStream_t st, const TraceArgs &a, int n_sm);
+cudaError_t launch_scatter(cudaStream_t st, const ScatterArgs &a, int n_sm);
+cudaError_t launch_levels(cudaStream_t st, const double *energy, const int *count, const float4 *mics,
+                          int64_t n_m, int n_bands, double *level_db, double *intensity, int *path_count);
+}  // namespace bt

@@ -1,0 +1,252 @@
+"""GPU parity: libbtrace (called through its C ABI) against the FP64 oracle.
+
+Bar: per microphone and band, level within 0.1 dB for >= 99.9% of
+microphones and within 1 dB for all; microphones no beam reached are -inf on
+both sides; path counts exact on the small brute-force scenes.
+"""
+import numpy as np
+import pytest
+
+from paper_1912_03998_gb300 import synth
+from tests.parity import assert_parity, level_db, summary
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tracer():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_03998_gb300 import btrace
+    t = btrace.Tracer(0)
+    yield t
+    t.close()
+
+
+def oracle_levels(oracle_mod, w, **kw):
+    r = oracle_mod.trace_workload(w, **kw)
+    return r, level_db(r["I"])
+
+
+def gpu_run(tracer, w, **kw):
+    r = tracer.run(w, **kw)
+    tracer_sid = r["scene_id"]
+    from paper_1912_03998_gb300 import btrace
+    btrace.bt_unload_scene(tracer.ctx, tracer_sid)
+    return r
+
+
+# ---------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("level", [0, 2, 4])
+def test_free_field(tracer, oracle_mod, level):
+    w = synth.free_field(seed=3, level=level, n_mics=777)
+    g = gpu_run(tracer, w)
+    rr = np.linalg.norm(w.mics.astype(np.float64) - w.src[0].astype(np.float64), axis=1)
+    expect = w.power[0].astype(np.float64)[None, :] / (4 * np.pi * rr[:, None] ** 2)
+    assert (g["cnt"] == 1).all()
+    assert np.abs(g["I"] / expect - 1).max() < 1e-5
+    assert g["stats"]["segments"] == 20 * 4 ** level and g["stats"]["hits"] == 0
+
+
+def test_ground_plane(tracer, oracle_mod):
+    w = synth.ground_only(seed=1, level=5)
+    g = gpu_run(tracer, w)
+    r, L = oracle_levels(oracle_mod, w)
+    assert_parity(g["level"], L, "ground plane")
+    assert (g["cnt"] == r["cnt"]).mean() >= 0.99
+
+
+def test_single_wall(tracer, oracle_mod):
+    w = synth.single_wall(seed=2, level=4)
+    g = gpu_run(tracer, w)
+    r, L = oracle_levels(oracle_mod, w)
+    assert_parity(g["level"], L, "single wall")
+    assert (g["cnt"] == 2).all()
+
+
+# ------------------------------------------------------------- tiny scenes
+@pytest.mark.parametrize("n_boxes,max_order", [(1, 4), (2, 4), (4, 3)])
+def test_boxes_path_counts_exact(tracer, oracle_mod, n_boxes, max_order):
+    w = synth.boxes(n_boxes, seed=5, level=5, max_order=max_order, n_grid=24)
+    g = gpu_run(tracer, w)
+    r, L = oracle_levels(oracle_mod, w)
+    assert (g["cnt"] == r["cnt"]).all(), np.nonzero(g["cnt"] != r["cnt"])
+    assert_parity(g["level"], L, f"boxes{n_boxes}")
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_tiny_city(tracer, oracle_mod, seed):
+    w = synth.tiny_city(seed=seed)  # 8x8 boxes, L = 4, K = 4, 32x32 microphones
+    g = gpu_run(tracer, w)
+    r, L = oracle_levels(oracle_mod, w)
+    s = assert_parity(g["level"], L, f"tiny city seed {seed}")
+    assert (g["cnt"] == r["cnt"]).mean() >= 0.999, s
+    assert g["stats"]["segments"] == r["stats"]["segments"]
+
+
+def test_tiny_city_many_sources_air_damping(tracer, oracle_mod):
+    w = synth.tiny_city(seed=7, level=4, max_order=5, n_sources=9, n_grid=48)
+    w.power[:] = np.random.Generator(np.random.PCG64(3)).uniform(0.01, 1.0, w.power.shape)
+    alpha = np.linspace(0.0, 0.04, synth.N_BANDS)
+    g = gpu_run(tracer, w, air_atten_db_per_m=alpha)
+    r, L = oracle_levels(oracle_mod, w, alpha=alpha, n_threads=4)
+    assert_parity(g["level"], L, "tiny city, 9 sources, air damping")
+
+
+def test_energy_threshold(tracer, oracle_mod):
+    w = synth.tiny_city(seed=3, level=3, max_order=6)
+    g = gpu_run(tracer, w, energy_threshold_w=0.75)
+    r, L = oracle_levels(oracle_mod, w, energy_threshold=0.75)
+    assert_parity(g["level"], L, "threshold")
+    assert g["stats"]["segments"] == r["stats"]["segments"]
+
+
+# ------------------------------------------------------------- edge cases
+def test_ragged_and_degenerate_sizes(tracer, oracle_mod):
+    # ragged microphone counts, microphones outside the city and at many heights,
+    # K = 0, level 0, a single triangle scene
+    base = synth.tiny_city(seed=4, level=3, max_order=3)
+    rng = np.random.Generator(np.random.PCG64(9))
+    mics = np.column_stack([rng.uniform(-300, 900, 4999), rng.uniform(-300, 900, 4999),
+                            rng.uniform(0.0, 90.0, 4999)]).astype(np.float32)
+    for w in (base.with_mics(mics), base.with_mics(mics[:1]), base.with_mics(mics[:33])):
+        g = gpu_run(tracer, w)
+        _, L = oracle_levels(oracle_mod, w)
+        assert_parity(g["level"], L, f"{len(w.mics)} mics")
+    for level, K in ((0, 0), (0, 2), (2, 0)):
+        w = synth.tiny_city(seed=4, level=level, max_order=K)
+        g = gpu_run(tracer, w)
+        r, L = oracle_levels(oracle_mod, w)
+        assert_parity(g["level"], L, f"L={level} K={K}")
+        assert g["stats"]["segments"] == r["stats"]["segments"]
+    one = synth.Scene(np.array([[-50, -50, 0], [50, -50, 0], [0, 80, 0]], np.float32),
+                      np.array([[0, 1, 2]], np.int32), np.zeros(1, np.uint8), synth.refl_table())
+    w = synth.Workload("one", one, np.array([[1, 2, 3]], np.float32), np.ones((1, 8), np.float32),
+                       synth.mic_grid(-40, -40, 40, 40, 9, 9, 1.0), 4, 2)
+    g = gpu_run(tracer, w)
+    r, L = oracle_levels(oracle_mod, w)
+    assert_parity(g["level"], L, "single triangle")
+    assert (g["cnt"] == r["cnt"]).all()
+
+
+def test_empty_inputs(tracer):
+    from paper_1912_03998_gb300 import btrace
+    w = synth.free_field(seed=1, level=1)
+    # no sources: zero intensity everywhere
+    w0 = synth.Workload("nosrc", w.scene, np.zeros((0, 3), np.float32), np.zeros((0, 8), np.float32),
+                        w.mics, 1, 2)
+    g = gpu_run(tracer, w0)
+    assert (g["I"] == 0).all() and np.isneginf(g["level"]).all() and (g["cnt"] == 0).all()
+    # no microphones
+    w1 = w.with_mics(np.zeros((0, 3), np.float32))
+    g = gpu_run(tracer, w1)
+    assert g["level"].shape == (0, 8) and g["stats"]["segments"] == 20 * 4
+
+
+def test_invalid_inputs_rejected(tracer):
+    from paper_1912_03998_gb300 import btrace
+    ctx = tracer.ctx
+    w = synth.tiny_city(seed=1, level=1, max_order=1)
+    bad_v = w.scene.verts.copy()
+    bad_v[5, 2] = np.nan
+    with pytest.raises(btrace.BtError) as e:
+        btrace.bt_load_scene(ctx, bad_v, w.scene.tris, w.scene.mat, w.scene.refl)
+    assert e.value.code == btrace.BT_E_INVALID
+    bad_t = w.scene.tris.copy()
+    bad_t[3, 1] = len(w.scene.verts)
+    with pytest.raises(btrace.BtError) as e:
+        btrace.bt_load_scene(ctx, w.scene.verts, bad_t, w.scene.mat, w.scene.refl)
+    assert e.value.code == btrace.BT_E_INVALID
+    bad_m = w.scene.mat.copy()
+    bad_m[0] = 7
+    with pytest.raises(btrace.BtError):
+        btrace.bt_load_scene(ctx, w.scene.verts, w.scene.tris, bad_m, w.scene.refl)
+    with pytest.raises(btrace.BtError):
+        btrace.bt_load_scene(ctx, w.scene.verts, w.scene.tris, w.scene.mat, w.scene.refl * 2)
+    sid = btrace.bt_load_scene(ctx, w.scene.verts, w.scene.tris, w.scene.mat, w.scene.refl)
+    p = btrace.bt_params_default()
+    with pytest.raises(btrace.BtError) as e:
+        btrace.bt_trace(ctx, sid, p)  # no sources yet
+    assert e.value.code == btrace.BT_E_STATE
+    with pytest.raises(btrace.BtError):
+        btrace.bt_set_sources(ctx, sid, w.src, -w.power, 1)
+    with pytest.raises(btrace.BtError):
+        btrace.bt_set_sources(ctx, sid, w.src, w.power, 9)
+    btrace.bt_set_sources(ctx, sid, w.src, w.power, 1)
+    m = w.mics.copy()
+    m[3, 0] = np.inf
+    with pytest.raises(btrace.BtError):
+        btrace.bt_set_microphones(ctx, sid, m)
+    btrace.bt_set_microphones(ctx, sid, w.mics)
+    p.max_order = 33
+    with pytest.raises(btrace.BtError):
+        btrace.bt_trace(ctx, sid, p)
+    p.max_order = 1
+    btrace.bt_trace(ctx, sid, p)  # the context still works after the errors
+    btrace.bt_unload_scene(ctx, sid)
+
+
+def test_device_pointer_inputs_match_host(tracer):
+    torch = pytest.importorskip("torch")
+    from paper_1912_03998_gb300 import btrace
+    ctx = tracer.ctx
+    w = synth.tiny_city(seed=6, level=3, max_order=3)
+    host = gpu_run(tracer, w)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sid = btrace.bt_load_scene(ctx, dev(w.scene.verts), dev(w.scene.tris), dev(w.scene.mat),
+                               dev(w.scene.refl))
+    btrace.bt_set_sources(ctx, sid, dev(w.src), dev(w.power), w.level)
+    btrace.bt_set_microphones(ctx, sid, dev(w.mics))
+    p = btrace.bt_params_default()
+    p.max_order = w.max_order
+    btrace.bt_trace(ctx, sid, p)
+    L = torch.empty((len(w.mics), 8), dtype=torch.float64, device="cuda")
+    cnt = torch.empty(len(w.mics), dtype=torch.int32, device="cuda")
+    btrace.bt_read_levels(ctx, sid, L, None, cnt)
+    torch.cuda.synchronize()
+    assert (cnt.cpu().numpy() == host["cnt"]).all()
+    Lh = L.cpu().numpy()
+    assert np.allclose(Lh[np.isfinite(Lh)], host["level"][np.isfinite(host["level"])], rtol=0, atol=1e-9)
+    btrace.bt_unload_scene(ctx, sid)
+
+
+def test_repeat_trace_is_reproducible(tracer):
+    w = synth.tiny_city(seed=2, level=4, max_order=4, n_sources=3)
+    a = tracer.run(w)
+    from paper_1912_03998_gb300 import btrace
+    b = tracer.run(w, sid=a["scene_id"])
+    assert (a["cnt"] == b["cnt"]).all()
+    assert np.allclose(a["I"], b["I"], rtol=1e-12, atol=0)
+    btrace.bt_unload_scene(tracer.ctx, a["scene_id"])
+
+
+def test_source_linearity(tracer):
+    # beams of different sources never interact: tracing A u B equals A + B
+    w = synth.tiny_city(seed=8, level=3, max_order=4, n_sources=6)
+    ab = gpu_run(tracer, w)
+    a = gpu_run(tracer, w.subset_sources(np.arange(0, 3)))
+    b = gpu_run(tracer, w.subset_sources(np.arange(3, 6)))
+    assert (ab["cnt"] == a["cnt"] + b["cnt"]).all()
+    assert np.allclose(ab["I"], a["I"] + b["I"], rtol=1e-9, atol=0)
+
+
+# ------------------------------------------------------------- district scale
+@pytest.fixture(scope="module")
+def district():
+    return synth.district(seed=2)
+
+
+def test_district_source_subset(tracer, oracle_mod, district):
+    # full-size district (about 200k triangles, 250k microphones, L = 5,
+    # K = 6) on a seeded subset of 16 of its 1,000 sources
+    import os
+    idx = np.random.Generator(np.random.PCG64(21)).choice(len(district.src), 16, replace=False)
+    w = district.subset_sources(np.sort(idx))
+    g = gpu_run(tracer, w)
+    r, L = oracle_levels(oracle_mod, w, n_threads=max(1, os.cpu_count() or 1))
+    s = assert_parity(g["level"], L, "district, 16 sources")
+    reached = r["cnt"] > 0
+    assert reached.sum() > 10000
+    assert abs(g["stats"]["segments"] / r["stats"]["segments"] - 1) < 1e-3, (g["stats"], r["stats"])
+    print("district 16 sources:", s)
