@@ -49,9 +49,13 @@ extern "C" {
 #define BT_MAX_TILES 32      /* per axis */
 
 /* Precision of the trace (Section 2 does not fix one).
- * BT_PREC_MIXED: float32 traversal, hit tests and microphone tests; float64
- * energy accumulation.  It is the only mode implemented so far; the others are
- * rejected with BT_E_INVALID. */
+ * BT_PREC_FP32: the whole beam lineage (directions, image-source apex, ray
+ *   origin, cone planes) in float32; float64 energy accumulation.
+ * BT_PREC_MIXED (default): the image-source chain in float64; float32
+ *   traversal whose ambiguous triangle tests (ray within 1e-4 relative of an
+ *   edge) and near-equal hit distances are settled in float64; float32
+ *   microphone tests relative to the float64 apex; float64 accumulation.
+ * BT_PREC_FP64 is not implemented yet and is rejected with BT_E_INVALID. */
 #define BT_PREC_FP32 0
 #define BT_PREC_MIXED 1
 #define BT_PREC_FP64 2
@@ -156,6 +160,21 @@ int bt_trace(bt_ctx *ctx, int32_t scene_id, const bt_trace_params *p);
  * level_db may also be NULL when only the other outputs are wanted. */
 int bt_read_levels(bt_ctx *ctx, int32_t scene_id, double *level_db, double *intensity,
                    int32_t *path_count, bt_stats *stats);
+
+/* Closest hit of arbitrary rays in the scene's acceleration structure: the
+ * axis-ray query of bt_trace on its own (Section 2: only the guiding ray of a
+ * beam is tested).
+ *   origins, dirs  [n][3] float32 (dirs are normalised by the library)
+ *   start_normals  [n][3] float32 or NULL: for a ray leaving a reflector, the
+ *                  reflector's normal; hits closer than t_eps_m to that plane
+ *                  are then ignored, as in bt_trace
+ *   t_out          [n] float32 hit distance, +inf on a miss
+ *   tri_out        [n] int32 index of the hit triangle in the scene's input
+ *                  order, -1 on a miss; equal distances go to the lowest index
+ * Hits with distance <= t_eps_m are ignored. */
+int bt_cast_rays(bt_ctx *ctx, int32_t scene_id, const float *origins, const float *dirs,
+                 const float *start_normals, int64_t n, float t_eps_m, float *t_out,
+                 int32_t *tri_out);
 
 /* Message of the last error of the context ("" if none).  Valid until the
  * next call on the context. */

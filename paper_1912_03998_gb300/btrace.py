@@ -55,7 +55,7 @@ _lock = threading.Lock()
 _lib = None
 EXPECTED_SYMBOLS = ("bt_params_default", "bt_create", "bt_destroy", "bt_load_scene",
                     "bt_unload_scene", "bt_set_sources", "bt_set_microphones", "bt_trace",
-                    "bt_read_levels", "bt_last_error", "bt_kernel_launches")
+                    "bt_read_levels", "bt_last_error", "bt_kernel_launches", "bt_cast_rays")
 
 
 def lib_path() -> str:
@@ -83,6 +83,7 @@ def lib():
             L.bt_read_levels.argtypes = [p, i32, p, p, p, C.POINTER(bt_stats)]
             L.bt_last_error.argtypes = [p]
             L.bt_last_error.restype = C.c_char_p
+            L.bt_cast_rays.argtypes = [p, i32, p, p, p, i64, C.c_float, p, p]
             L.bt_kernel_launches.argtypes = []
             L.bt_kernel_launches.restype = C.c_int64
             for name in EXPECTED_SYMBOLS:
@@ -188,6 +189,19 @@ def bt_read_levels(ctx, scene_id: int, level_db=None, intensity=None, path_count
                               out_ptr(path_count), C.byref(st))
     _check(rc, ctx)
     return st.as_dict()
+
+
+def bt_cast_rays(ctx, scene_id: int, origins, dirs, start_normals=None, t_eps_m: float = 1e-3):
+    """Closest hit per ray: (t [n] float32, triangle index [n] int32)."""
+    po, n, ko = _arr(origins, np.float32)
+    pd, _, kd = _arr(dirs, np.float32)
+    pn, _, kn = _arr(start_normals, np.float32)
+    t = np.empty(n // 3, np.float32)
+    ids = np.empty(n // 3, np.int32)
+    rc = lib().bt_cast_rays(ctx, int(scene_id), po, pd, pn, n // 3, C.c_float(t_eps_m),
+                            t.ctypes.data_as(C.c_void_p), ids.ctypes.data_as(C.c_void_p))
+    _check(rc, ctx)
+    return t, ids
 
 
 class Tracer:

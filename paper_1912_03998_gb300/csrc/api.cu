@@ -161,6 +161,21 @@ void release_scene(bt_ctx *c, SceneState &s) {
 
 int check_ctx(bt_ctx *c) { return c ? BT_OK : BT_E_INVALID; }
 
+bt::DevScene dev_scene(const SceneState &s) {
+  bt::DevScene d;
+  memset(&d, 0, sizeof(d));
+  d.n_tris = s.n_tris;
+  d.root = s.root;
+  d.nodes = (const bt::Node *)s.nodes.p;
+  d.tris = (const bt::Tri *)s.tris.p;
+  d.planes = (const bt::Plane *)s.planes.p;
+  d.refl = (const float *)s.refl.p;
+  d.n_mat = s.n_mat;
+  d.n_bands = s.n_bands;
+  for (int k = 0; k < 3; k++) { d.lo[k] = s.box[k]; d.hi[k] = s.box[3 + k]; }
+  return d;
+}
+
 int scene_ref(bt_ctx *c, int32_t id, SceneState **out) {
   if (id < 0 || id >= BT_MAX_SCENES || !c->sc[id].used)
     return fail(c, BT_E_INVALID, "unknown scene id %d", id);
@@ -357,7 +372,7 @@ BT_API int bt_load_scene(bt_ctx *c, const float *verts, int64_t n_verts, const i
     release_scene(c, s);
     return fail(c, BT_E_CUDA, "acceleration structure build failed (device error %d)", e);
   }
-  s.root = n_tris == 0 ? -1 : (n_tris == 1 ? ~0 : 0);
+  s.root = n_tris == 1 ? ~0 : 0;
   *scene_id_out = id;
   return BT_OK;
 }
@@ -456,7 +471,8 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   if (p->max_order < 0 || p->max_order > 32) return fail(c, BT_E_INVALID, "max_order %d not in 0..32", p->max_order);
   if (!(p->t_eps_m > 0.0f) || !isfinite(p->t_eps_m)) return fail(c, BT_E_INVALID, "t_eps_m must be > 0");
   if (!(p->energy_threshold_w >= 0.0f)) return fail(c, BT_E_INVALID, "energy_threshold_w must be >= 0");
-  if (p->precision != BT_PREC_MIXED) return fail(c, BT_E_INVALID, "precision %d not implemented (use BT_PREC_MIXED)", p->precision);
+  if (p->precision != BT_PREC_MIXED && p->precision != BT_PREC_FP32)
+    return fail(c, BT_E_INVALID, "precision %d not implemented (BT_PREC_FP32 or BT_PREC_MIXED)", p->precision);
   if (p->tiles_x != 1 || p->tiles_y != 1)
     return fail(c, BT_E_INVALID, "tiles %dx%d: only 1x1 is implemented in this build", p->tiles_x, p->tiles_y);
   if (p->chunk_beams < 0) return fail(c, BT_E_INVALID, "chunk_beams must be >= 0");
@@ -482,15 +498,7 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   CK(cudaMemsetAsync(s->count.p, 0, sizeof(int) * (size_t)s->n_mics, st));
   bt::TraceArgs ta;
   memset(&ta, 0, sizeof(ta));
-  ta.sc.n_tris = s->n_tris;
-  ta.sc.root = s->root;
-  ta.sc.nodes = (const bt::Node *)s->nodes.p;
-  ta.sc.tris = (const bt::Tri *)s->tris.p;
-  ta.sc.planes = (const bt::Plane *)s->planes.p;
-  ta.sc.refl = (const float *)s->refl.p;
-  ta.sc.n_mat = s->n_mat;
-  ta.sc.n_bands = s->n_bands;
-  for (int k = 0; k < 3; k++) { ta.sc.lo[k] = s->box[k]; ta.sc.hi[k] = s->box[3 + k]; }
+  ta.sc = dev_scene(*s);
   ta.src = (const float4 *)s->src.p;
   ta.power = (const float *)s->power.p;
   ta.n_src = s->n_src;
@@ -507,6 +515,7 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   ta.seg_capacity = cap;
   ta.ctr = c->d_ctr;
   ta.count_work = p->count_work ? 1 : 0;
+  ta.mixed = p->precision == BT_PREC_MIXED ? 1 : 0;
   bt::ScatterArgs sa;
   memset(&sa, 0, sizeof(sa));
   sa.segs = ta.segs;
@@ -608,5 +617,36 @@ BT_API int bt_read_levels(bt_ctx *c, int32_t scene_id, double *level_db, double 
     CK(cudaMemcpyAsync(path_count, s->out_cnt.p, sizeof(int) * (size_t)s->n_mics, cudaMemcpyDefault, st));
   CK(cudaStreamSynchronize(st));
   if (stats) *stats = s->stats;
+  return BT_OK;
+}
+
+BT_API int bt_cast_rays(bt_ctx *c, int32_t scene_id, const float *origins, const float *dirs,
+                        const float *start_normals, int64_t n, float t_eps_m, float *t_out,
+                        int32_t *tri_out) {
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  SceneState *s;
+  TRY(scene_ref(c, scene_id, &s));
+  if (n < 0 || n > (1 << 28)) return fail(c, BT_E_INVALID, "bad ray count %lld", (long long)n);
+  if (n > 0 && (!origins || !dirs || !t_out || !tri_out)) return fail(c, BT_E_INVALID, "NULL ray array");
+  if (!(t_eps_m >= 0.0f)) return fail(c, BT_E_INVALID, "t_eps_m must be >= 0");
+  if (n == 0) return BT_OK;
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  size_t v = sizeof(float) * 3 * (size_t)n;
+  TRY(ensure(c, c->stage_a, 3 * v));
+  TRY(ensure(c, c->stage_b, sizeof(float) * (size_t)n + sizeof(int) * (size_t)n + 256));
+  float *d_o = (float *)c->stage_a.p, *d_d = d_o + 3 * n, *d_ns = start_normals ? d_d + 3 * n : nullptr;
+  float *d_t = (float *)c->stage_b.p;
+  int *d_id = (int *)(d_t + n);
+  TRY(reset_counters(c));
+  CK(cudaMemcpyAsync(d_o, origins, v, cudaMemcpyDefault, st));
+  CK(cudaMemcpyAsync(d_d, dirs, v, cudaMemcpyDefault, st));
+  if (start_normals) CK(cudaMemcpyAsync(d_ns, start_normals, v, cudaMemcpyDefault, st));
+  CK(bt::launch_cast(st, dev_scene(*s), d_o, d_d, d_ns, n, t_eps_m, d_t, d_id, &c->d_ctr->error));
+  CK(cudaMemcpyAsync(t_out, d_t, sizeof(float) * n, cudaMemcpyDefault, st));
+  CK(cudaMemcpyAsync(tri_out, d_id, sizeof(int) * n, cudaMemcpyDefault, st));
+  TRY(read_counters(c));
+  if (c->h_ctr->error) return fail(c, c->h_ctr->error, "device error %d in ray query", c->h_ctr->error);
   return BT_OK;
 }

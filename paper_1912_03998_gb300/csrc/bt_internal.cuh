@@ -34,7 +34,7 @@ using Plane = float4;
 
 struct DevScene {
   int64_t n_tris;
-  int root;              // root child code (internal index >= 0, or ~leaf), -1 when empty
+  int root;              // root child code: internal index >= 0, or ~leaf for one triangle (unused when n_tris == 0)
   const Node *nodes;     // n_tris - 1 internal nodes
   const Tri *tris;       // n_tris, leaf order
   const Plane *planes;   // n_tris, leaf order
@@ -52,19 +52,23 @@ struct MicGrid {
   int pad;
 };
 
-// One beam segment handed from the trace kernel to the scatter kernel, 128 B.
-// Inside test: n_j . (m - apex) >= 0 (j = 0,1,2), start.xyz . m - start.w > 0,
-// end.xyz . m - end.w >= 0.  A missing plane is (0, 0, 0, -inf).
+// One beam segment handed from the trace kernel to the scatter kernel, 144 B.
+// With v = m - apex (formed in float64, then rounded), microphone m is inside
+// when n_j . v >= 0 (j = 0,1,2), start.xyz . v - start.w > 0 and
+// end.xyz . v - end.w >= 0; plane offsets are relative to the apex.  A
+// missing plane is (0, 0, 0, -inf).
 struct __align__(16) Seg {
-  float4 apex;  // xyz, w: row range first (int bits)
-  float4 n0;    // w: row range last (int bits)
-  float4 n1;    // w: source index (int bits)
-  float4 n2;    // w: order (int bits)
+  double ax, ay, az;  // apex (source or image source), float64
+  int cy0, cy1;       // footprint rows on the microphone grid
+  float4 n0;          // cone-face normal 0; w: source index (int bits)
+  float4 n1;          // w: reflection order (int bits)
+  float4 n2;
   float4 start;
   float4 end;
-  float4 p03;   // per-band power W_b * prod(r_b), bands 0..3
-  float4 p47;   // bands 4..7
+  float4 p03;         // per-band power W_b * prod(r_b), bands 0..3
+  float4 p47;         // bands 4..7
 };
+static_assert(sizeof(Seg) == 144, "segment record layout");
 
 // Device counters of one trace, accumulated with atomics.
 struct Counters {
@@ -94,6 +98,7 @@ struct TraceArgs {
   unsigned long long seg_capacity;
   Counters *ctr;
   int count_work;
+  int mixed;  // 1: float64 image-source chain (BT_PREC_MIXED), 0: float32 (BT_PREC_FP32)
 };
 
 struct ScatterArgs {
@@ -168,15 +173,24 @@ __device__ __forceinline__ Ray make_ray(float3 o, float3 d, float t_eps, float d
 // without FMA contraction so a shared edge gets exactly opposite values in
 // its two triangles, and recomputed in double when one is exactly zero, as
 // the published method prescribes.  Returns the hit distance or +inf.
-__device__ __forceinline__ float hit_watertight(const Ray &r, float4 v0, float4 v1, float4 v2) {
+// `amb` is set when the ray passes within a relative 1e-4 of an edge (or
+// nearly parallel to the plane): there a float32 ray that was rounded from a
+// float64 one may decide differently, and callers holding the float64 ray
+// re-test it in float64.
+__device__ __forceinline__ float hit_watertight(const Ray &r, float4 v0, float4 v1, float4 v2, bool &amb) {
   float3 A = f3(v0) - r.o, B = f3(v1) - r.o, C = f3(v2) - r.o;
   float Akz = pick(A, r.kz), Bkz = pick(B, r.kz), Ckz = pick(C, r.kz);
   float ax = pick(A, r.kx) - r.sx * Akz, ay = pick(A, r.ky) - r.sy * Akz;
   float bx = pick(B, r.kx) - r.sx * Bkz, by = pick(B, r.ky) - r.sy * Bkz;
   float cx = pick(C, r.kx) - r.sx * Ckz, cy = pick(C, r.ky) - r.sy * Ckz;
-  float U = __fsub_rn(__fmul_rn(cx, by), __fmul_rn(cy, bx));
-  float V = __fsub_rn(__fmul_rn(ax, cy), __fmul_rn(ay, cx));
-  float W = __fsub_rn(__fmul_rn(bx, ay), __fmul_rn(by, ax));
+  float u1 = __fmul_rn(cx, by), u2 = __fmul_rn(cy, bx);
+  float v1_ = __fmul_rn(ax, cy), v2_ = __fmul_rn(ay, cx);
+  float w1 = __fmul_rn(bx, ay), w2 = __fmul_rn(by, ax);
+  float U = __fsub_rn(u1, u2), V = __fsub_rn(v1_, v2_), W = __fsub_rn(w1, w2);
+  const float tau = 1e-4f;
+  float su = fabsf(u1) + fabsf(u2), sv = fabsf(v1_) + fabsf(v2_), sw = fabsf(w1) + fabsf(w2);
+  amb = fabsf(U) <= tau * su || fabsf(V) <= tau * sv || fabsf(W) <= tau * sw ||
+        fabsf(U + V + W) <= tau * (su + sv + sw);
   if (U == 0.0f || V == 0.0f || W == 0.0f) {
     U = (float)((double)cx * (double)by - (double)cy * (double)bx);
     V = (float)((double)ax * (double)cy - (double)ay * (double)cx);
@@ -188,6 +202,43 @@ __device__ __forceinline__ float hit_watertight(const Ray &r, float4 v0, float4 
   float T = U * (r.sz * Akz) + V * (r.sz * Bkz) + W * (r.sz * Ckz);
   float t = __fdiv_rn(T, det);
   return t;
+}
+
+// float64 vectors
+__device__ __forceinline__ double3 d3(float4 v) { return make_double3(v.x, v.y, v.z); }
+__device__ __forceinline__ double3 operator+(double3 a, double3 b) { return make_double3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ double3 operator-(double3 a, double3 b) { return make_double3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ double3 operator*(double3 a, double s) { return make_double3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ double dot3(double3 a, double3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ double3 cross3(double3 a, double3 b) {
+  return make_double3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+// b x a is exactly -(a x b): no contraction into FMA
+__device__ __forceinline__ double3 cross_exact(double3 a, double3 b) {
+  return make_double3(__dsub_rn(__dmul_rn(a.y, b.z), __dmul_rn(a.z, b.y)),
+                      __dsub_rn(__dmul_rn(a.z, b.x), __dmul_rn(a.x, b.z)),
+                      __dsub_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ double3 normalize3(double3 a) { return a * (1.0 / sqrt(dot3(a, a))); }
+__device__ __forceinline__ float3 to_f3(double3 a) { return make_float3((float)a.x, (float)a.y, (float)a.z); }
+
+// Moller & Trumbore (1997) in float64, two-sided, edges inclusive: the
+// float64 re-test of an ambiguous float32 decision, and the float64 hit
+// distance of the chosen triangle.
+__device__ __forceinline__ bool hit_mt64(double3 o, double3 d, float4 fa, float4 fb, float4 fc, double &t) {
+  double3 a = d3(fa), e1 = d3(fb) - a, e2 = d3(fc) - a;
+  double3 p = cross3(d, e2);
+  double det = dot3(e1, p);
+  if (det == 0.0) return false;
+  double inv = 1.0 / det;
+  double3 s = o - a;
+  double u = dot3(s, p) * inv;
+  if (u < 0.0 || u > 1.0) return false;
+  double3 q = cross3(s, e1);
+  double v = dot3(d, q) * inv;
+  if (v < 0.0 || u + v > 1.0) return false;
+  t = dot3(e2, q) * inv;
+  return true;
 }
 
 // Hit acceptance (same rule as the oracle): beyond t_eps, and for a reflected
@@ -248,7 +299,8 @@ __device__ __forceinline__ bool poly_halfspace(Poly &p, float3 a, float b, const
   return p.n >= 3;
 }
 
-// Footprint of segment s over the grid; returns false if empty.
+// Footprint of segment s over the grid; returns false if empty.  Planes are
+// relative to the apex: n . (m - A) >= w  <=>  n . m >= w + n . A.
 __device__ __forceinline__ bool seg_footprint(const Seg &s, const MicGrid &g, Poly &p) {
   float m = 0.01f;
   float X0 = g.x0 - m, X1 = g.x0 + g.cw * g.nx + m, Y0 = g.y0 - m, Y1 = g.y0 + g.ch * g.ny + m;
@@ -257,13 +309,14 @@ __device__ __forceinline__ bool seg_footprint(const Seg &s, const MicGrid &g, Po
   p.x[1] = X1; p.y[1] = Y0;
   p.x[2] = X1; p.y[2] = Y1;
   p.x[3] = X0; p.y[3] = Y1;
-  float3 A = f3(s.apex);
+  float3 A = make_float3((float)s.ax, (float)s.ay, (float)s.az);
   float3 n0 = f3(s.n0), n1 = f3(s.n1), n2 = f3(s.n2);
+  float3 ns = f3(s.start), ne = f3(s.end);
   if (!poly_halfspace(p, n0, dot3(n0, A), g)) return false;
   if (!poly_halfspace(p, n1, dot3(n1, A), g)) return false;
   if (!poly_halfspace(p, n2, dot3(n2, A), g)) return false;
-  if (!poly_halfspace(p, f3(s.start), s.start.w, g)) return false;
-  if (!poly_halfspace(p, f3(s.end), s.end.w, g)) return false;
+  if (!poly_halfspace(p, ns, s.start.w + dot3(ns, A), g)) return false;
+  if (!poly_halfspace(p, ne, s.end.w + dot3(ne, A), g)) return false;
   return true;
 }
 
@@ -308,6 +361,8 @@ cudaError_t build_mics(cudaStream_t st, const float *d_pos, int64_t n_m, int sid
                        int *d_error);
 size_t build_mics_scratch_bytes(int64_t n_m, int side);
 cudaError_t launch_trace(cudaStream_t st, const TraceArgs &a, int n_sm);
+cudaError_t launch_cast(cudaStream_t st, const DevScene &sc, const float *o, const float *d, const float *ns,
+                        int64_t n, float t_eps, float *t_out, int *tri_out, int *err);
 cudaError_t launch_scatter(cudaStream_t st, const ScatterArgs &a, int n_sm);
 cudaError_t launch_levels(cudaStream_t st, const double *energy, const int *count, const float4 *mics,
                           int64_t n_m, int n_bands, double *level_db, double *intensity, int *path_count);

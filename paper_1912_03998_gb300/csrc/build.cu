@@ -81,15 +81,24 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
   return r;
 }
 
+// Key: 30-bit Morton code of the centroid, plus bit 30 for a triangle whose
+// xy extent exceeds 1/16 of the scene's (a ground sheet, a long roof).  The
+// flag makes the root split those few triangles into their own subtree, so
+// their scene-sized boxes do not enlarge the boxes above ordinary triangles.
 __global__ void k_morton(const float *verts, const int32_t *tris, int64_t n_tris, const float *box,
                          uint32_t *keys, uint32_t *vals) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n_tris) return;
-  float c[3];
+  float c[3], lo[3], hi[3];
   for (int k = 0; k < 3; k++) {
-    c[k] = (verts[3 * (int64_t)tris[3 * t] + k] + verts[3 * (int64_t)tris[3 * t + 1] + k] +
-            verts[3 * (int64_t)tris[3 * t + 2] + k]) * (1.0f / 3.0f);
+    float a = verts[3 * (int64_t)tris[3 * t] + k], b = verts[3 * (int64_t)tris[3 * t + 1] + k],
+          d = verts[3 * (int64_t)tris[3 * t + 2] + k];
+    c[k] = (a + b + d) * (1.0f / 3.0f);
+    lo[k] = fminf(fminf(a, b), d);
+    hi[k] = fmaxf(fmaxf(a, b), d);
   }
+  float scene_xy = fmaxf(box[3] - box[0], box[4] - box[1]);
+  bool large = fmaxf(hi[0] - lo[0], hi[1] - lo[1]) > scene_xy * (1.0f / 16.0f);
   uint32_t q[3];
   for (int k = 0; k < 3; k++) {
     float ext = box[3 + k] - box[k];
@@ -97,7 +106,7 @@ __global__ void k_morton(const float *verts, const int32_t *tris, int64_t n_tris
     u = fminf(fmaxf(u, 0.0f), 1.0f);
     q[k] = (uint32_t)fminf(u * 1024.0f, 1023.0f);
   }
-  keys[t] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+  keys[t] = (large ? (1u << 30) : 0u) | (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
   vals[t] = (uint32_t)t;
 }
 
@@ -321,9 +330,18 @@ __global__ void k_lbvh_boxes(const Tri *tris, int n, Node *nodes, const int *lea
     float llo[3], lhi[3], rlo[3], rhi[3];
     child_box(l, tris, aux, llo, lhi);
     child_box(r, tris, aux, rlo, rhi);
-    nodes[p].lxy = make_float4(llo[0], lhi[0], llo[1], lhi[1]);
-    nodes[p].rxy = make_float4(rlo[0], rhi[0], rlo[1], rhi[1]);
-    nodes[p].lrz = make_float4(llo[2], lhi[2], rlo[2], rhi[2]);
+    // child boxes grown by 1e-6 relative + 0.1 mm: a float32 ray rounded from
+    // a float64 one must not miss a box the float64 ray enters
+    float glo[3], ghi[3], hlo[3], hhi[3];
+    for (int k = 0; k < 3; k++) {
+      glo[k] = llo[k] - (fabsf(llo[k]) * 1e-6f + 1e-4f);
+      ghi[k] = lhi[k] + (fabsf(lhi[k]) * 1e-6f + 1e-4f);
+      hlo[k] = rlo[k] - (fabsf(rlo[k]) * 1e-6f + 1e-4f);
+      hhi[k] = rhi[k] + (fabsf(rhi[k]) * 1e-6f + 1e-4f);
+    }
+    nodes[p].lxy = make_float4(glo[0], ghi[0], glo[1], ghi[1]);
+    nodes[p].rxy = make_float4(hlo[0], hhi[0], hlo[1], hhi[1]);
+    nodes[p].lrz = make_float4(glo[2], ghi[2], hlo[2], hhi[2]);
     for (int k = 0; k < 3; k++) {
       aux[6 * p + k] = fminf(llo[k], rlo[k]);
       aux[6 * p + 3 + k] = fmaxf(lhi[k], rhi[k]);
@@ -377,7 +395,7 @@ cudaError_t build_scene(cudaStream_t st, const float *d_verts, const int32_t *d_
   int blocks = (n + threads - 1) / threads;
   k_morton<<<blocks, threads, 0, st>>>(d_verts, d_tris, n_tris, d_box, keys, vals);
   note_launches(1);
-  cudaError_t e = radix_sort(st, keys, vals, kalt, valt, hist, n, 30);
+  cudaError_t e = radix_sort(st, keys, vals, kalt, valt, hist, n, 31);
   if (e != cudaSuccess) return e;
   k_pack_tris<<<blocks, threads, 0, st>>>(d_verts, d_tris, d_mat, vals, n_tris, d_tris_out, d_planes);
   note_launches(1);

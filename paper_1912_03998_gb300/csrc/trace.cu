@@ -12,7 +12,16 @@
 //             segment's footprint 32 rows at a time, flattens the microphone
 //             runs of those rows with a warp scan, tests every candidate
 //             microphone and adds the beam's intensity with float64 atomics.
+//
+// Precision.  BT_PREC_FP32 carries the whole lineage in float32.
+// BT_PREC_MIXED carries beam directions, apex, ray origin and cone normals in
+// float64 (the image-source chain) and traverses in float32; a triangle whose
+// float32 test is ambiguous (the ray within a relative 1e-4 of an edge) is
+// re-tested in float64, near-equal hit distances are compared in float64, and
+// the chosen hit point is formed in float64.
 #include <stdio.h>
+
+#include <type_traits>
 
 #include "bt_internal.cuh"
 
@@ -20,14 +29,12 @@ namespace bt {
 
 // Regular icosahedron: unit vertices (the cyclic permutations of
 // (0, +-1, +-phi), normalised) and its 20 faces, counter-clockwise seen
-// from outside.
-__constant__ float c_ico_v[12][3] = {
-    {0.000000000f, -0.525731112f, 0.850650808f},  {0.000000000f, 0.525731112f, 0.850650808f},
-    {0.850650808f, 0.000000000f, 0.525731112f},   {-0.850650808f, 0.000000000f, 0.525731112f},
-    {-0.525731112f, -0.850650808f, 0.000000000f}, {0.525731112f, -0.850650808f, 0.000000000f},
-    {0.525731112f, 0.850650808f, 0.000000000f},   {-0.525731112f, 0.850650808f, 0.000000000f},
-    {0.850650808f, 0.000000000f, -0.525731112f},  {-0.850650808f, 0.000000000f, -0.525731112f},
-    {0.000000000f, -0.525731112f, -0.850650808f}, {0.000000000f, 0.525731112f, -0.850650808f},
+// from outside.  Vertex coordinates are 0, +-A or +-B with
+// A = 1/sqrt(1+phi^2), B = phi/sqrt(1+phi^2); the table holds 0, +-1 (A),
+// +-2 (B).
+__constant__ signed char c_ico_s[12][3] = {
+    {0, -1, 2}, {0, 1, 2},   {2, 0, 1},   {-2, 0, 1},  {-1, -2, 0}, {1, -2, 0},
+    {1, 2, 0},  {-1, 2, 0},  {2, 0, -1},  {-2, 0, -1}, {0, -1, -2}, {0, 1, -2},
 };
 __constant__ int c_ico_f[20][3] = {
     {0, 2, 1},  {0, 1, 3},  {0, 5, 2},  {0, 3, 4},  {1, 2, 6},   {1, 7, 3},  {0, 4, 5},
@@ -35,19 +42,45 @@ __constant__ int c_ico_f[20][3] = {
     {4, 9, 10}, {5, 10, 8}, {6, 8, 11}, {7, 11, 9}, {8, 10, 11}, {9, 11, 10},
 };
 
+template <typename T>
+struct Vec3;
+template <>
+struct Vec3<float> { using type = float3; };
+template <>
+struct Vec3<double> { using type = double3; };
+
+template <typename T>
+__device__ __forceinline__ typename Vec3<T>::type ico_vertex(int v) {
+  const T phi = (T)0.5 * ((T)1 + sqrt((T)5));
+  const T inv = (T)1 / sqrt((T)1 + phi * phi);
+  const T A = inv, B = phi * inv;
+  T c[3];
+  for (int k = 0; k < 3; k++) {
+    int s = c_ico_s[v][k];
+    c[k] = s == 0 ? (T)0 : (s == 1 ? A : (s == -1 ? -A : (s == 2 ? B : -B)));
+  }
+  typename Vec3<T>::type r;
+  r.x = c[0];
+  r.y = c[1];
+  r.z = c[2];
+  return r;
+}
+
 // Edge directions of face `i` of the level-L geodesic icosahedron.  The base
 // face is i >> 2L; each further pair of bits picks one of the four children
 // (a,ab,ca), (ab,b,bc), (ca,bc,c), (ab,bc,ca), ab = midpoint pushed to the
 // sphere.  A vertex shared by two faces is computed from the same operands in
 // both, so both faces get the bit-identical direction.
-__device__ __forceinline__ void beam_dirs(int level, int64_t i, float3 &a, float3 &b, float3 &c) {
+template <typename T>
+__device__ __forceinline__ void beam_dirs(int level, int64_t i, typename Vec3<T>::type &a,
+                                          typename Vec3<T>::type &b, typename Vec3<T>::type &c) {
   int f = (int)(i >> (2 * level));
-  a = make_float3(c_ico_v[c_ico_f[f][0]][0], c_ico_v[c_ico_f[f][0]][1], c_ico_v[c_ico_f[f][0]][2]);
-  b = make_float3(c_ico_v[c_ico_f[f][1]][0], c_ico_v[c_ico_f[f][1]][1], c_ico_v[c_ico_f[f][1]][2]);
-  c = make_float3(c_ico_v[c_ico_f[f][2]][0], c_ico_v[c_ico_f[f][2]][1], c_ico_v[c_ico_f[f][2]][2]);
+  a = ico_vertex<T>(c_ico_f[f][0]);
+  b = ico_vertex<T>(c_ico_f[f][1]);
+  c = ico_vertex<T>(c_ico_f[f][2]);
   for (int l = level - 1; l >= 0; --l) {
     int ch = (int)((i >> (2 * l)) & 3);
-    float3 ab = normalize3(a + b), bc = normalize3(b + c), ca = normalize3(c + a);
+    auto ab = normalize3(a + b), bc = normalize3(b + c), ca = normalize3(c + a);
     if (ch == 0) { b = ab; c = ca; }
     else if (ch == 1) { a = ab; c = bc; }
     else if (ch == 2) { a = ca; b = bc; }
@@ -55,27 +88,85 @@ __device__ __forceinline__ void beam_dirs(int level, int64_t i, float3 &a, float
   }
 }
 
+// Best hit so far.  In MIXED mode t64 holds the float64 distance when known.
+struct Best {
+  float t;
+  int slot, id;
+  double t64;
+  bool has64;
+};
+
 // Closest accepted hit of the ray in the BVH; ties in distance go to the
-// lowest original triangle id.  Returns the leaf slot or -1.
-template <bool kCount>
-__device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, float &best_t, int *err,
-                                           unsigned long long &n_nodes, unsigned long long &n_tris) {
-  best_t = kInf;
-  int best_slot = -1, best_id = 0x7fffffff;
-  if (sc.root == -1) return -1;
+// lowest original triangle id.  With kMixed, `od`/`dd` is the float64 ray the
+// float32 ray `r` was rounded from.  Returns the leaf slot or -1.
+template <bool kMixed, bool kCount>
+__device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, double3 od, double3 dd, double dns64,
+                                           Best &best, int *err, unsigned long long &n_nodes,
+                                           unsigned long long &n_tris) {
+  best.t = kInf;
+  best.slot = -1;
+  best.id = 0x7fffffff;
+  best.t64 = 0.0;
+  best.has64 = false;
+  if (sc.n_tris == 0) return -1;
+  // candidate evaluation, shared by the single-leaf root and the loop
+  auto consider = [&](int slot) {
+    if (kCount) n_tris++;
+    const Tri *tp = sc.tris + slot;
+    float4 v0 = __ldg(&tp->v0), v1 = __ldg(&tp->v1), v2 = __ldg(&tp->v2);
+    bool amb;
+    float t = hit_watertight(r, v0, v1, v2, amb);
+    double t64 = 0.0;
+    bool has64 = false;
+    if (kMixed && amb) {
+      double tt;
+      if (!hit_mt64(od, dd, v0, v1, v2, tt)) return;
+      if (!(tt > (double)r.t_eps && (dns64 == 0.0 || tt * dns64 > (double)r.t_eps))) return;
+      t64 = tt;
+      has64 = true;
+      t = (float)tt;
+    } else {
+      if (!(t < kInf && accept_hit(r, t))) return;
+    }
+    int id = __float_as_int(v1.w);
+    if (!kMixed) {
+      if (t < best.t || (t == best.t && id < best.id)) { best.t = t; best.slot = slot; best.id = id; }
+      return;
+    }
+    // MIXED: a clearly nearer or farther float32 distance decides; a near
+    // tie is settled in float64
+    float win = 1e-5f * fabsf(best.t) + 1e-4f;
+    if (best.slot < 0 || t < best.t - win) {
+      best.t = t; best.slot = slot; best.id = id; best.t64 = t64; best.has64 = has64;
+      return;
+    }
+    if (t > best.t + win) return;
+    if (!has64) {
+      double tt;
+      if (!hit_mt64(od, dd, v0, v1, v2, tt)) return;
+      t64 = tt;
+    }
+    if (!best.has64) {
+      const Tri *bp = sc.tris + best.slot;
+      double tb;
+      if (hit_mt64(od, dd, __ldg(&bp->v0), __ldg(&bp->v1), __ldg(&bp->v2), tb)) best.t64 = tb;
+      else best.t64 = (double)best.t;
+      best.has64 = true;
+    }
+    if (t64 < best.t64 || (t64 == best.t64 && id < best.id)) {
+      best.t = (float)t64; best.slot = slot; best.id = id; best.t64 = t64; best.has64 = true;
+    }
+  };
+  int node = sc.root;
+  if (node < 0) {  // a single triangle
+    consider(~node);
+    return best.slot;
+  }
   int stack[kStackDepth];
   int sp = 0;
-  int node = sc.root;
   // a well-formed BVH is visited at most once per node; the bound only
   // guarantees termination should the structure ever be malformed
   int64_t visits = 0;
-  if (node < 0) {  // a single triangle
-    int slot = ~node;
-    if (kCount) n_tris++;
-    float t = hit_watertight(r, __ldg(&sc.tris[slot].v0), __ldg(&sc.tris[slot].v1), __ldg(&sc.tris[slot].v2));
-    if (t < kInf && accept_hit(r, t)) { best_t = t; best_slot = slot; }
-    return best_slot;
-  }
   while (true) {
     if (++visits > sc.n_tris + 64) {
       atomicExch(err, BT_E_TIMEOUT);
@@ -85,26 +176,13 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, flo
     if (kCount) n_nodes++;
     float4 lxy = __ldg(&nd->lxy), rxy = __ldg(&nd->rxy), lrz = __ldg(&nd->lrz);
     int2 ch = __ldg((const int2 *)&nd->child);
+    // in MIXED mode near ties must still be visited
+    float tmax = kMixed ? best.t + (1e-5f * fabsf(best.t) + 1e-4f) : best.t;
     float tl, tr;
-    bool hl = slab(r, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, best_t, tl);
-    bool hr = slab(r, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, best_t, tr);
-#pragma unroll
-    for (int side = 0; side < 2; side++) {
-      int c = side ? ch.y : ch.x;
-      bool h = side ? hr : hl;
-      if (h && c < 0) {
-        int slot = ~c;
-        if (kCount) n_tris++;
-        const Tri *tp = sc.tris + slot;
-        float4 v0 = __ldg(&tp->v0), v1 = __ldg(&tp->v1), v2 = __ldg(&tp->v2);
-        float t = hit_watertight(r, v0, v1, v2);
-        if (t < kInf && accept_hit(r, t)) {
-          int id = __float_as_int(v1.w);
-          if (t < best_t || (t == best_t && id < best_id)) { best_t = t; best_slot = slot; best_id = id; }
-        }
-        if (side) hr = false; else hl = false;
-      }
-    }
+    bool hl = slab(r, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, tmax, tl);
+    bool hr = slab(r, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, tmax, tr);
+    if (hl && ch.x < 0) { consider(~ch.x); hl = false; }
+    if (hr && ch.y < 0) { consider(~ch.y); hr = false; }
     if (hl && hr) {
       bool lf = tl <= tr;
       if (sp < kStackDepth) stack[sp++] = lf ? ch.y : ch.x;
@@ -119,7 +197,7 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, flo
       node = stack[--sp];
     }
   }
-  return best_slot;
+  return best.slot;
 }
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
@@ -136,71 +214,111 @@ __device__ __forceinline__ bool seg_rows(const Seg &s, const MicGrid &g, int &cy
   return true;
 }
 
-template <bool kCount>
+__device__ __forceinline__ float4 plane4(double3 n, double w) {
+  return make_float4((float)n.x, (float)n.y, (float)n.z, (float)w);
+}
+__device__ __forceinline__ float4 plane4(float3 n, float w) { return make_float4(n.x, n.y, n.z, w); }
+__device__ __forceinline__ double3 as_d3(float3 v) { return make_double3(v.x, v.y, v.z); }
+__device__ __forceinline__ double3 as_d3(double3 v) { return v; }
+
+// Warp-aggregated append of a segment record.
+__device__ __forceinline__ void emit_segment(const TraceArgs &a, const Seg &s, bool emit,
+                                             unsigned long long &n_emit) {
+  unsigned mask = __activemask();
+  unsigned bal = __ballot_sync(mask, emit);
+  if (!bal) return;
+  int leader = __ffs(bal) - 1;
+  unsigned long long base = 0;
+  if ((int)lane_id() == leader) base = atomicAdd(a.seg_count, (unsigned long long)__popc(bal));
+  base = __shfl_sync(mask, base, leader);
+  if (emit) {
+    unsigned long long idx = base + __popc(bal & ((1u << lane_id()) - 1u));
+    if (idx < a.seg_capacity) a.segs[idx] = s;
+    else atomicExch(&a.ctr->error, BT_E_QUEUE_FULL);
+    n_emit++;
+  }
+}
+
+template <bool kMixed, bool kCount>
 __global__ void __launch_bounds__(128) k_trace(TraceArgs a) {
+  using T = typename std::conditional<kMixed, double, float>::type;
+  using V = typename Vec3<T>::type;
   const MicGrid g = *a.grid;
   const int nb = a.sc.n_bands;
   unsigned long long n_seg = 0, n_hit = 0, n_esc = 0, n_emit = 0, n_nodes = 0, n_tris = 0;
   for (int64_t lin = a.lineage_begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
        lin < a.lineage_end; lin += (int64_t)gridDim.x * blockDim.x) {
     int64_t si = lin / a.n_beams, bi = lin - si * a.n_beams;
-    float3 d0, d1, d2;
-    beam_dirs(a.level, bi, d0, d1, d2);
-    float3 n0 = cross_exact(d0, d1), n1 = cross_exact(d1, d2), n2 = cross_exact(d2, d0);
-    float3 A = f3(__ldg(&a.src[si]));
-    float3 O = A;
-    float3 D = normalize3(d0 + d1 + d2);
+    V d0, d1, d2;
+    beam_dirs<T>(a.level, bi, d0, d1, d2);
+    V n0 = cross_exact(d0, d1), n1 = cross_exact(d1, d2), n2 = cross_exact(d2, d0);
+    float4 s4 = __ldg(&a.src[si]);
+    V A;
+    A.x = s4.x; A.y = s4.y; A.z = s4.z;
+    V O = A;
+    V D = normalize3((d0 + d1) + d2);
     float P[kMaxBands];
 #pragma unroll
     for (int b = 0; b < kMaxBands; b++) P[b] = b < nb ? __ldg(&a.power[si * nb + b]) : 0.0f;
     float4 start = make_float4(0.0f, 0.0f, 0.0f, -kInf);
-    float dns = 0.0f;
+    T dns = 0;
     for (int k = 0; k <= a.max_order; k++) {
-      Ray r = make_ray(O, D, a.t_eps, dns);
-      float th;
-      int slot = closest_hit<kCount>(a.sc, r, th, &a.ctr->error, n_nodes, n_tris);
+      float3 of = make_float3((float)O.x, (float)O.y, (float)O.z);
+      float3 df = make_float3((float)D.x, (float)D.y, (float)D.z);
+      Ray r = make_ray(of, df, a.t_eps, (float)dns);
+      Best best;
+      int slot = closest_hit<kMixed, kCount>(a.sc, r, as_d3(O), as_d3(D), (double)dns, best, &a.ctr->error,
+                                             n_nodes, n_tris);
       n_seg++;
       float4 end = make_float4(0.0f, 0.0f, 0.0f, -kInf);
-      float4 pl = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      V pn;
+      pn.x = 0; pn.y = 0; pn.z = 0;
+      float4 v0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      T th = 0;
       if (slot >= 0) {
         n_hit++;
-        pl = __ldg(&a.sc.planes[slot]);
-        bool facing = pl.x * D.x + pl.y * D.y + pl.z * D.z < 0.0f;
-        end = facing ? pl : make_float4(-pl.x, -pl.y, -pl.z, -pl.w);
+        const Tri *tp = a.sc.tris + slot;
+        v0 = __ldg(&tp->v0);
+        if (kMixed) {
+          // float64 plane of the hit triangle and float64 hit distance
+          float4 v1 = __ldg(&tp->v1), v2 = __ldg(&tp->v2);
+          double3 un = normalize3(cross3(d3(v1) - d3(v0), d3(v2) - d3(v0)));
+          pn.x = (T)un.x; pn.y = (T)un.y; pn.z = (T)un.z;
+          double tt = best.t64;
+          if (!best.has64 && !hit_mt64(as_d3(O), as_d3(D), v0, v1, v2, tt)) tt = (double)best.t;
+          th = (T)tt;
+        } else {
+          float4 pl = __ldg(&a.sc.planes[slot]);
+          pn.x = (T)pl.x; pn.y = (T)pl.y; pn.z = (T)pl.z;
+          th = (T)best.t;
+        }
+        // end plane on the incident side, offset relative to the apex
+        V en = dot3(pn, D) < (T)0 ? pn : pn * (T)-1;
+        V pv0;
+        pv0.x = v0.x; pv0.y = v0.y; pv0.z = v0.z;
+        end = plane4(en, dot3(en, pv0 - A));
       } else {
         n_esc++;
       }
       Seg s;
-      s.apex = make_float4(A.x, A.y, A.z, 0.0f);
-      s.n0 = make_float4(n0.x, n0.y, n0.z, 0.0f);
-      s.n1 = make_float4(n1.x, n1.y, n1.z, __int_as_float((int)si));
-      s.n2 = make_float4(n2.x, n2.y, n2.z, __int_as_float(k));
+      s.ax = (double)A.x;
+      s.ay = (double)A.y;
+      s.az = (double)A.z;
+      s.n0 = make_float4((float)n0.x, (float)n0.y, (float)n0.z, __int_as_float((int)si));
+      s.n1 = make_float4((float)n1.x, (float)n1.y, (float)n1.z, __int_as_float(k));
+      s.n2 = make_float4((float)n2.x, (float)n2.y, (float)n2.z, 0.0f);
       s.start = start;
       s.end = end;
       s.p03 = make_float4(P[0], P[1], P[2], P[3]);
       s.p47 = make_float4(P[4], P[5], P[6], P[7]);
       int cy0 = 0, cy1 = -1;
       bool emit = g.n_mics > 0 && seg_rows(s, g, cy0, cy1);
-      s.apex.w = __int_as_float(cy0);
-      s.n0.w = __int_as_float(cy1);
-      unsigned mask = __activemask();
-      unsigned bal = __ballot_sync(mask, emit);
-      if (bal) {
-        int leader = __ffs(bal) - 1;
-        unsigned long long base = 0;
-        if ((int)lane_id() == leader) base = atomicAdd(a.seg_count, (unsigned long long)__popc(bal));
-        base = __shfl_sync(mask, base, leader);
-        if (emit) {
-          unsigned long long idx = base + __popc(bal & ((1u << lane_id()) - 1u));
-          if (idx < a.seg_capacity) a.segs[idx] = s;
-          else atomicExch(&a.ctr->error, BT_E_QUEUE_FULL);
-          n_emit++;
-        }
-      }
+      s.cy0 = cy0;
+      s.cy1 = cy1;
+      emit_segment(a, s, emit, n_emit);
       if (slot < 0 || k == a.max_order) break;
       // Image source: mirror the apex, the cone and the axis in the hit
       // plane; the reflected beam starts on that plane and loses energy.
-      float4 v0 = __ldg(&a.sc.tris[slot].v0);
       int mat = __float_as_int(v0.w);
       float wmax = 0.0f;
 #pragma unroll
@@ -209,18 +327,18 @@ __global__ void __launch_bounds__(128) k_trace(TraceArgs a) {
         wmax = fmaxf(wmax, P[b]);
       }
       if (a.energy_threshold > 0.0f && wmax < a.energy_threshold) break;
-      float3 pn = make_float3(pl.x, pl.y, pl.z);
-      float3 H = O + D * th;
-      float da = dot3(A - f3(v0), pn);
-      A = A - pn * (2.0f * da);
-      n0 = n0 - pn * (2.0f * dot3(n0, pn));
-      n1 = n1 - pn * (2.0f * dot3(n1, pn));
-      n2 = n2 - pn * (2.0f * dot3(n2, pn));
-      D = D - pn * (2.0f * dot3(D, pn));
+      V pv0;
+      pv0.x = v0.x; pv0.y = v0.y; pv0.z = v0.z;
+      V H = O + D * th;
+      A = A - pn * ((T)2 * dot3(A - pv0, pn));
+      n0 = n0 - pn * ((T)2 * dot3(n0, pn));
+      n1 = n1 - pn * ((T)2 * dot3(n1, pn));
+      n2 = n2 - pn * ((T)2 * dot3(n2, pn));
+      D = D - pn * ((T)2 * dot3(D, pn));
       O = H;
-      bool toward = dot3(pn, D) > 0.0f;
-      start = toward ? pl : make_float4(-pl.x, -pl.y, -pl.z, -pl.w);
-      dns = fabsf(dot3(pn, D));
+      V sn = dot3(pn, D) > (T)0 ? pn : pn * (T)-1;
+      start = plane4(sn, dot3(sn, pv0 - A));
+      dns = dot3(sn, D);
     }
   }
   // warp-aggregated counters
@@ -246,6 +364,33 @@ __global__ void __launch_bounds__(128) k_trace(TraceArgs a) {
   }
 }
 
+// Closest hit of arbitrary float32 rays (the axis-ray query of the trace
+// kernel on its own), decided as in MIXED mode with the float32 ray promoted
+// to float64 for ambiguous triangles.  ns: optional start-plane normals.
+__global__ void k_cast(DevScene sc, const float *o, const float *d, const float *ns, int64_t n, float t_eps,
+                       float *t_out, int *tri_out, int *err) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double3 O = make_double3(o[3 * i], o[3 * i + 1], o[3 * i + 2]);
+  double3 D = normalize3(make_double3(d[3 * i], d[3 * i + 1], d[3 * i + 2]));
+  double dns = 0.0;
+  if (ns) dns = fabs(dot3(D, make_double3(ns[3 * i], ns[3 * i + 1], ns[3 * i + 2])));
+  Ray r = make_ray(to_f3(O), to_f3(D), t_eps, (float)dns);
+  Best best;
+  unsigned long long a = 0, b = 0;
+  int slot = closest_hit<true, false>(sc, r, O, D, dns, best, err, a, b);
+  t_out[i] = slot >= 0 ? (best.has64 ? (float)best.t64 : best.t) : kInf;
+  tri_out[i] = slot >= 0 ? best.id : -1;
+}
+
+cudaError_t launch_cast(cudaStream_t st, const DevScene &sc, const float *o, const float *d, const float *ns,
+                        int64_t n, float t_eps, float *t_out, int *tri_out, int *err) {
+  if (n <= 0) return cudaSuccess;
+  k_cast<<<(int)((n + 127) / 128), 128, 0, st>>>(sc, o, d, ns, n, t_eps, t_out, tri_out, err);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_trace(cudaStream_t st, const TraceArgs &a, int n_sm) {
   int64_t n = a.lineage_end - a.lineage_begin;
   if (n <= 0) return cudaSuccess;
@@ -253,8 +398,13 @@ cudaError_t launch_trace(cudaStream_t st, const TraceArgs &a, int n_sm) {
   int64_t blocks = (n + threads - 1) / threads;
   int64_t cap = (int64_t)n_sm * 64;
   if (blocks > cap) blocks = cap;
-  if (a.count_work) k_trace<true><<<(int)blocks, threads, 0, st>>>(a);
-  else k_trace<false><<<(int)blocks, threads, 0, st>>>(a);
+  if (a.mixed) {
+    if (a.count_work) k_trace<true, true><<<(int)blocks, threads, 0, st>>>(a);
+    else k_trace<true, false><<<(int)blocks, threads, 0, st>>>(a);
+  } else {
+    if (a.count_work) k_trace<false, true><<<(int)blocks, threads, 0, st>>>(a);
+    else k_trace<false, false><<<(int)blocks, threads, 0, st>>>(a);
+  }
   note_launches(1);
   return cudaGetLastError();
 }
@@ -269,14 +419,12 @@ __global__ void __launch_bounds__(256) k_scatter(ScatterArgs a) {
   const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long si = warp0; si < (long long)n_seg; si += n_warps) {
-    const Seg *sp = a.segs + si;
-    Seg s;
-    s.apex = __ldg(&sp->apex); s.n0 = __ldg(&sp->n0); s.n1 = __ldg(&sp->n1); s.n2 = __ldg(&sp->n2);
-    s.start = __ldg(&sp->start); s.end = __ldg(&sp->end); s.p03 = __ldg(&sp->p03); s.p47 = __ldg(&sp->p47);
+    const Seg s = a.segs[si];
     Poly p;
     if (!seg_footprint(s, g, p)) continue;
-    const int cy0 = __float_as_int(s.apex.w), cy1 = __float_as_int(s.n0.w);
-    const float3 A = f3(s.apex), n0 = f3(s.n0), n1 = f3(s.n1), n2 = f3(s.n2);
+    const int cy0 = s.cy0, cy1 = s.cy1;
+    const double ax = s.ax, ay = s.ay, az = s.az;
+    const float3 n0 = f3(s.n0), n1 = f3(s.n1), n2 = f3(s.n2);
     const float3 ns = f3(s.start), ne = f3(s.end);
     const float ws = s.start.w, we = s.end.w;
     const float P[kMaxBands] = {s.p03.x, s.p03.y, s.p03.z, s.p03.w, s.p47.x, s.p47.y, s.p47.z, s.p47.w};
@@ -314,11 +462,12 @@ __global__ void __launch_bounds__(256) k_scatter(ScatterArgs a) {
         if (i < total) {
           int mi = ofirst + (i - oexcl);
           float4 m = __ldg(&a.mics[mi]);
-          float3 mv = f3(m);
-          float3 v = mv - A;
+          // m - apex in float64, then float32 tests relative to the apex
+          float3 v = make_float3((float)((double)m.x - ax), (float)((double)m.y - ay),
+                                 (float)((double)m.z - az));
           n_cand++;
           bool in = dot3(n0, v) >= 0.0f && dot3(n1, v) >= 0.0f && dot3(n2, v) >= 0.0f &&
-                    dot3(ns, mv) - ws > 0.0f && dot3(ne, mv) - we >= 0.0f;
+                    dot3(ns, v) - ws > 0.0f && dot3(ne, v) - we >= 0.0f;
           float d2 = dot3(v, v);
           if (in && d2 > 1e-18f) {
             float gf = 1.0f / (4.0f * 3.14159265358979f * d2);

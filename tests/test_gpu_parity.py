@@ -250,3 +250,39 @@ def test_district_source_subset(tracer, oracle_mod, district):
     assert reached.sum() > 10000
     assert abs(g["stats"]["segments"] / r["stats"]["segments"] - 1) < 1e-3, (g["stats"], r["stats"])
     print("district 16 sources:", s)
+
+
+# ------------------------------------------------------------- hit queries
+@pytest.mark.parametrize("scene_name", ["tiny", "district"])
+def test_cast_rays_match_oracle(tracer, oracle_mod, scene_name, district):
+    # a4 on its own: the closest hit of seeded random rays, GPU vs oracle on
+    # the same float32 rays; the triangle index must agree exactly
+    from paper_1912_03998_gb300 import btrace
+    w = synth.tiny_city(seed=4) if scene_name == "tiny" else district
+    lo, hi = w.scene.verts.min(0), w.scene.verts.max(0)
+    rng = np.random.Generator(np.random.PCG64(12))
+    n = 200_000
+    o = np.column_stack([rng.uniform(lo[0] + 500, hi[0] - 500, n), rng.uniform(lo[1] + 500, hi[1] - 500, n),
+                         rng.uniform(0.1, 60.0, n)]).astype(np.float32)
+    d = rng.normal(size=(n, 3)).astype(np.float32)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    sid = btrace.bt_load_scene(tracer.ctx, w.scene.verts, w.scene.tris, w.scene.mat, w.scene.refl)
+    tg, ig = btrace.bt_cast_rays(tracer.ctx, sid, o, d)
+    btrace.bt_unload_scene(tracer.ctx, sid)
+    dd = d.astype(np.float64)
+    dd /= np.linalg.norm(dd, axis=1, keepdims=True)
+    to, io = oracle_mod.cast_rays(oracle_mod.Scene(w.scene), o.astype(np.float64), dd,
+                                  mode=oracle_mod.HIT_BVH)
+    assert (io >= 0).mean() > 0.3
+    mism = np.nonzero(ig != io)[0]
+    assert len(mism) <= n * 1e-5, [(int(i), int(ig[i]), float(tg[i]), int(io[i]), float(to[i])) for i in mism[:10]]
+    hit = (io >= 0) & (ig == io)
+    assert np.allclose(tg[hit], to[hit], rtol=1e-5, atol=1e-4)
+
+
+def test_fp32_precision_mode(tracer, oracle_mod):
+    from paper_1912_03998_gb300 import btrace
+    w = synth.tiny_city(seed=2)
+    g = gpu_run(tracer, w, precision=btrace.BT_PREC_FP32)
+    _, L = oracle_levels(oracle_mod, w)
+    assert_parity(g["level"], L, "tiny city, FP32 chain")
