@@ -411,7 +411,12 @@ static void consider(const oscene *s, const ray_q *r, int tri, double *best_t, i
     tile_of(s, h.x, h.y, &ix, &iy);
     if (ix != tile_xy[0] || iy != tile_xy[1]) return;
   }
-  if (t < *best_t || (t == *best_t && tri < *best_id)) {
+  /* Two surfaces hit at the same distance (a box floor lying on the ground,
+   * the shared edge of two faces) form a tie in exact arithmetic; distances
+   * within 1e-9 relative count as equal so that the lowest index, not the
+   * rounding, decides. */
+  double tol = 1e-9 * (1.0 + fabs(t));
+  if (*best_id < 0 || t < *best_t - tol || (fabs(t - *best_t) <= tol && tri < *best_id)) {
     *best_t = t;
     *best_id = tri;
   }
@@ -450,7 +455,7 @@ static void hit_bvh(const oscene *s, const bvh *h, const ray_q *r, double *bt, i
   while (sp > 0) {
     const bnode *nd = &h->nodes[stack[--sp]];
     double te = box_enter(nd->lo, nd->hi, r->o, r->d);
-    if (te == INFINITY || te > *bt + 1e-6 * (1.0 + fabs(*bt))) continue;
+    if (te == INFINITY || te > *bt + 1e-6 * (1.0 + fabs(*bt))) continue; /* margin covers the tie window */
     if (nd->left < 0) {
       for (int i = nd->first; i < nd->first + nd->count; i++)
         consider(s, r, h->idx[i], bt, bid, tile_xy);

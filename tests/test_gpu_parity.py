@@ -277,7 +277,8 @@ def test_cast_rays_match_oracle(tracer, oracle_mod, scene_name, district):
     mism = np.nonzero(ig != io)[0]
     assert len(mism) <= n * 1e-5, [(int(i), int(ig[i]), float(tg[i]), int(io[i]), float(to[i])) for i in mism[:10]]
     hit = (io >= 0) & (ig == io)
-    assert np.allclose(tg[hit], to[hit], rtol=1e-5, atol=1e-4)
+    # float32 origins at 2 km carry 1.2e-4 m of rounding
+    assert np.allclose(tg[hit], to[hit], rtol=1e-5, atol=1e-3)
 
 
 def test_fp32_precision_mode(tracer, oracle_mod):
