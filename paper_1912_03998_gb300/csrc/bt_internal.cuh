@@ -38,6 +38,7 @@ struct DevScene {
   const Node *nodes;     // n_tris - 1 internal nodes
   const Tri *tris;       // n_tris, leaf order
   const Plane *planes;   // n_tris, leaf order
+  const double4 *planes64;  // n_tris, leaf order: float64 unit normal and n . v0
   const float *refl;     // [n_mat][n_bands]
   int n_mat, n_bands;
   float lo[3], hi[3];    // scene box
@@ -60,9 +61,9 @@ struct MicGrid {
 struct __align__(16) Seg {
   double ax, ay, az;  // apex (source or image source), float64
   int cy0, cy1;       // footprint rows on the microphone grid
-  float4 n0;          // cone-face normal 0; w: source index (int bits)
-  float4 n1;          // w: reflection order (int bits)
-  float4 n2;
+  float4 n0;          // cone-face normal 0; w: leaf slot of the start plane's triangle (int bits, -1 none)
+  float4 n1;          // w: leaf slot of the end plane's triangle (int bits, -1 none)
+  float4 n2;          // w: reflection order (int bits)
   float4 start;
   float4 end;
   float4 p03;         // per-band power W_b * prod(r_b), bands 0..3
@@ -99,9 +100,12 @@ struct TraceArgs {
   Counters *ctr;
   int count_work;
   int mixed;  // 1: float64 image-source chain (BT_PREC_MIXED), 0: float32 (BT_PREC_FP32)
+  const double *beam_table;  // MIXED: per beam 3 cone normals + axis, float64 [n_beams][12]
 };
 
 struct ScatterArgs {
+  const Tri *tris;          // leaf order (start/end plane vertices)
+  const double4 *planes64;  // leaf order
   const Seg *segs;
   const unsigned long long *seg_count;
   unsigned long long seg_capacity;
@@ -220,6 +224,11 @@ __device__ __forceinline__ double3 cross_exact(double3 a, double3 b) {
                       __dsub_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x)));
 }
 __device__ __forceinline__ double3 normalize3(double3 a) { return a * (1.0 / sqrt(dot3(a, a))); }
+__device__ __forceinline__ double4 ldg_d4(const double4 *p) {
+  const double2 *q = reinterpret_cast<const double2 *>(p);
+  double2 a = __ldg(q), b = __ldg(q + 1);
+  return make_double4(a.x, a.y, b.x, b.y);
+}
 __device__ __forceinline__ float3 to_f3(double3 a) { return make_float3((float)a.x, (float)a.y, (float)a.z); }
 
 // Moller & Trumbore (1997) in float64, two-sided, edges inclusive: the
@@ -354,7 +363,9 @@ cudaError_t validate_scene(cudaStream_t st, const float *d_verts, int64_t n_vert
                            float *d_box /*lo xyz, hi xyz*/, int *d_error);
 cudaError_t build_scene(cudaStream_t st, const float *d_verts, const int32_t *d_tris, int64_t n_tris,
                         const uint8_t *d_mat, Node *d_nodes, Tri *d_tris_out, Plane *d_planes,
-                        void *d_scratch, size_t scratch_bytes, const float *d_box, int *d_error);
+                        double4 *d_planes64, void *d_scratch, size_t scratch_bytes, const float *d_box,
+                        int *d_error);
+cudaError_t launch_beam_table(cudaStream_t st, int level, double *table);
 size_t build_scene_scratch_bytes(int64_t n_tris);
 cudaError_t build_mics(cudaStream_t st, const float *d_pos, int64_t n_m, int side, MicGrid *d_grid,
                        float4 *d_sorted, int *d_cell_start, void *d_scratch, size_t scratch_bytes,

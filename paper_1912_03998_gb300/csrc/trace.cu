@@ -88,6 +88,37 @@ __device__ __forceinline__ void beam_dirs(int level, int64_t i, typename Vec3<T>
   }
 }
 
+// Float64 beam table of one icosahedron level: per beam the three cone-face
+// normals d_j x d_{j+1} (formed without FMA, so neighbours share exactly
+// opposite normals) and the unit axis, 12 doubles.
+__global__ void k_beam_table(int level, int64_t n_beams, double *table) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_beams) return;
+  double3 d0, d1, d2;
+  beam_dirs<double>(level, i, d0, d1, d2);
+  double3 v[4] = {cross_exact(d0, d1), cross_exact(d1, d2), cross_exact(d2, d0), normalize3((d0 + d1) + d2)};
+  double *o = table + 12 * i;
+  for (int k = 0; k < 4; k++) {
+    o[3 * k] = v[k].x;
+    o[3 * k + 1] = v[k].y;
+    o[3 * k + 2] = v[k].z;
+  }
+}
+
+cudaError_t launch_beam_table(cudaStream_t st, int level, double *table) {
+  int64_t n = (int64_t)20 << (2 * level);
+  k_beam_table<<<(int)((n + 127) / 128), 128, 0, st>>>(level, n, table);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// Float64 distance along the ray to the plane of leaf slot `slot`.
+__device__ __forceinline__ double plane_t64(const DevScene &sc, int slot, double3 od, double3 dd) {
+  double4 pl = ldg_d4(&sc.planes64[slot]);
+  double3 n = make_double3(pl.x, pl.y, pl.z);
+  return (pl.w - dot3(n, od)) / dot3(n, dd);
+}
+
 // Best hit so far.  In MIXED mode t64 holds the float64 distance when known.
 struct Best {
   float t;
@@ -134,26 +165,21 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, dou
       return;
     }
     // MIXED: a clearly nearer or farther float32 distance decides; a near
-    // tie is settled in float64
+    // tie is settled in float64, where distances within 1e-9 relative tie
+    // and go to the lowest triangle index
     float win = 1e-5f * fabsf(best.t) + 1e-4f;
     if (best.slot < 0 || t < best.t - win) {
       best.t = t; best.slot = slot; best.id = id; best.t64 = t64; best.has64 = has64;
       return;
     }
     if (t > best.t + win) return;
-    if (!has64) {
-      double tt;
-      if (!hit_mt64(od, dd, v0, v1, v2, tt)) return;
-      t64 = tt;
-    }
+    if (!has64) t64 = plane_t64(sc, slot, od, dd);
     if (!best.has64) {
-      const Tri *bp = sc.tris + best.slot;
-      double tb;
-      if (hit_mt64(od, dd, __ldg(&bp->v0), __ldg(&bp->v1), __ldg(&bp->v2), tb)) best.t64 = tb;
-      else best.t64 = (double)best.t;
+      best.t64 = plane_t64(sc, best.slot, od, dd);
       best.has64 = true;
     }
-    if (t64 < best.t64 || (t64 == best.t64 && id < best.id)) {
+    double tol = 1e-9 * (1.0 + fabs(t64));
+    if (t64 < best.t64 - tol || (fabs(t64 - best.t64) <= tol && id < best.id)) {
       best.t = (float)t64; best.slot = slot; best.id = id; best.t64 = t64; best.has64 = true;
     }
   };
@@ -249,14 +275,26 @@ __global__ void __launch_bounds__(128) k_trace(TraceArgs a) {
   for (int64_t lin = a.lineage_begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
        lin < a.lineage_end; lin += (int64_t)gridDim.x * blockDim.x) {
     int64_t si = lin / a.n_beams, bi = lin - si * a.n_beams;
-    V d0, d1, d2;
-    beam_dirs<T>(a.level, bi, d0, d1, d2);
-    V n0 = cross_exact(d0, d1), n1 = cross_exact(d1, d2), n2 = cross_exact(d2, d0);
+    V n0, n1, n2, D;
+    if (kMixed) {
+      const double *bt = a.beam_table + 12 * bi;
+      n0.x = __ldg(bt + 0); n0.y = __ldg(bt + 1); n0.z = __ldg(bt + 2);
+      n1.x = __ldg(bt + 3); n1.y = __ldg(bt + 4); n1.z = __ldg(bt + 5);
+      n2.x = __ldg(bt + 6); n2.y = __ldg(bt + 7); n2.z = __ldg(bt + 8);
+      D.x = __ldg(bt + 9); D.y = __ldg(bt + 10); D.z = __ldg(bt + 11);
+    } else {
+      V d0, d1, d2;
+      beam_dirs<T>(a.level, bi, d0, d1, d2);
+      n0 = cross_exact(d0, d1);
+      n1 = cross_exact(d1, d2);
+      n2 = cross_exact(d2, d0);
+      D = normalize3((d0 + d1) + d2);
+    }
     float4 s4 = __ldg(&a.src[si]);
     V A;
     A.x = s4.x; A.y = s4.y; A.z = s4.z;
     V O = A;
-    V D = normalize3((d0 + d1) + d2);
+    int start_slot = -1;
     float P[kMaxBands];
 #pragma unroll
     for (int b = 0; b < kMaxBands; b++) P[b] = b < nb ? __ldg(&a.power[si * nb + b]) : 0.0f;
@@ -281,12 +319,9 @@ __global__ void __launch_bounds__(128) k_trace(TraceArgs a) {
         v0 = __ldg(&tp->v0);
         if (kMixed) {
           // float64 plane of the hit triangle and float64 hit distance
-          float4 v1 = __ldg(&tp->v1), v2 = __ldg(&tp->v2);
-          double3 un = normalize3(cross3(d3(v1) - d3(v0), d3(v2) - d3(v0)));
-          pn.x = (T)un.x; pn.y = (T)un.y; pn.z = (T)un.z;
-          double tt = best.t64;
-          if (!best.has64 && !hit_mt64(as_d3(O), as_d3(D), v0, v1, v2, tt)) tt = (double)best.t;
-          th = (T)tt;
+          double4 p64 = ldg_d4(&a.sc.planes64[slot]);
+          pn.x = (T)p64.x; pn.y = (T)p64.y; pn.z = (T)p64.z;
+          th = (T)(best.has64 ? best.t64 : plane_t64(a.sc, slot, as_d3(O), as_d3(D)));
         } else {
           float4 pl = __ldg(&a.sc.planes[slot]);
           pn.x = (T)pl.x; pn.y = (T)pl.y; pn.z = (T)pl.z;
@@ -304,9 +339,9 @@ __global__ void __launch_bounds__(128) k_trace(TraceArgs a) {
       s.ax = (double)A.x;
       s.ay = (double)A.y;
       s.az = (double)A.z;
-      s.n0 = make_float4((float)n0.x, (float)n0.y, (float)n0.z, __int_as_float((int)si));
-      s.n1 = make_float4((float)n1.x, (float)n1.y, (float)n1.z, __int_as_float(k));
-      s.n2 = make_float4((float)n2.x, (float)n2.y, (float)n2.z, 0.0f);
+      s.n0 = make_float4((float)n0.x, (float)n0.y, (float)n0.z, __int_as_float(start_slot));
+      s.n1 = make_float4((float)n1.x, (float)n1.y, (float)n1.z, __int_as_float(slot));
+      s.n2 = make_float4((float)n2.x, (float)n2.y, (float)n2.z, __int_as_float(k));
       s.start = start;
       s.end = end;
       s.p03 = make_float4(P[0], P[1], P[2], P[3]);
@@ -339,6 +374,7 @@ __global__ void __launch_bounds__(128) k_trace(TraceArgs a) {
       V sn = dot3(pn, D) > (T)0 ? pn : pn * (T)-1;
       start = plane4(sn, dot3(sn, pv0 - A));
       dns = dot3(sn, D);
+      start_slot = slot;
     }
   }
   // warp-aggregated counters
@@ -410,6 +446,16 @@ cudaError_t launch_trace(cudaStream_t st, const TraceArgs &a, int n_sm) {
 }
 
 // ------------------------------------------------------------------ scatter
+// Signed distance of m from the plane of leaf slot `slot`, in float64,
+// oriented like the float32 normal `nf` of the segment record.
+__device__ __forceinline__ double plane_side64(const ScatterArgs &a, int slot, float3 nf, float4 m) {
+  double4 pl = ldg_d4(&a.planes64[slot]);
+  float4 v0 = __ldg(&a.tris[slot].v0);
+  double3 n = make_double3(pl.x, pl.y, pl.z);
+  if (n.x * nf.x + n.y * nf.y + n.z * nf.z < 0.0) n = n * -1.0;
+  return dot3(n, make_double3((double)m.x - v0.x, (double)m.y - v0.y, (double)m.z - v0.z));
+}
+
 __global__ void __launch_bounds__(256) k_scatter(ScatterArgs a) {
   const MicGrid g = *a.grid;
   const unsigned lane = lane_id();
@@ -427,6 +473,7 @@ __global__ void __launch_bounds__(256) k_scatter(ScatterArgs a) {
     const float3 n0 = f3(s.n0), n1 = f3(s.n1), n2 = f3(s.n2);
     const float3 ns = f3(s.start), ne = f3(s.end);
     const float ws = s.start.w, we = s.end.w;
+    const int s_slot = __float_as_int(s.n0.w), e_slot = __float_as_int(s.n1.w);
     const float P[kMaxBands] = {s.p03.x, s.p03.y, s.p03.z, s.p03.w, s.p47.x, s.p47.y, s.p47.z, s.p47.w};
     for (int rb = cy0; rb <= cy1; rb += 32) {
       int row = rb + (int)lane;
@@ -466,8 +513,17 @@ __global__ void __launch_bounds__(256) k_scatter(ScatterArgs a) {
           float3 v = make_float3((float)((double)m.x - ax), (float)((double)m.y - ay),
                                  (float)((double)m.z - az));
           n_cand++;
-          bool in = dot3(n0, v) >= 0.0f && dot3(n1, v) >= 0.0f && dot3(n2, v) >= 0.0f &&
-                    dot3(ns, v) - ws > 0.0f && dot3(ne, v) - we >= 0.0f;
+          bool in = dot3(n0, v) >= 0.0f && dot3(n1, v) >= 0.0f && dot3(n2, v) >= 0.0f;
+          if (in) {
+            // start/end planes: float32 relative to the apex; within the
+            // rounding band of a plane the test is redone in float64 against
+            // the triangle's own plane, the form the definition uses
+            float band = 1e-4f + 1e-6f * (fabsf(v.x) + fabsf(v.y) + fabsf(v.z));
+            float fs = dot3(ns, v) - ws, fe = dot3(ne, v) - we;
+            if (fabsf(fs) <= band && s_slot >= 0) fs = (float)plane_side64(a, s_slot, ns, m);
+            if (fabsf(fe) <= band && e_slot >= 0) fe = (float)plane_side64(a, e_slot, ne, m);
+            in = fs > 0.0f && fe >= 0.0f;
+          }
           float d2 = dot3(v, v);
           if (in && d2 > 1e-18f) {
             float gf = 1.0f / (4.0f * 3.14159265358979f * d2);
