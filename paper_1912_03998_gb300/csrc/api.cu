@@ -66,6 +66,7 @@ struct bt_ctx {
   bt::Counters *d_ctr = nullptr;
   bt::Counters *h_ctr = nullptr;  // pinned
   unsigned long long *d_seg_count = nullptr;
+  unsigned long long *d_lineage_next = nullptr;
   float *d_box = nullptr;  // scene box of the scene being loaded (6 floats)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> kev;  // pairs of events around kernel launches of one trace
@@ -171,7 +172,7 @@ bt::DevScene dev_scene(const SceneState &s) {
   d.nodes = (const bt::Node *)s.nodes.p;
   d.tris = (const bt::Tri *)s.tris.p;
   d.planes = (const bt::Plane *)s.planes.p;
-  d.planes64 = (const double4 *)s.planes64.p;
+  d.planes64 = (const bt::Plane64 *)s.planes64.p;
   d.refl = (const float *)s.refl.p;
   d.n_mat = s.n_mat;
   d.n_bands = s.n_bands;
@@ -255,6 +256,7 @@ BT_API int bt_create(bt_ctx **out, int device, void *cuda_stream) {
     if (cudaMalloc(&c->d_ctr, sizeof(bt::Counters)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
     if (cudaMalloc(&c->d_seg_count, sizeof(unsigned long long)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
     if (cudaMalloc(&c->d_box, 8 * sizeof(float)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
+    if (cudaMalloc(&c->d_lineage_next, sizeof(unsigned long long)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
     if (cudaMallocHost(&c->h_ctr, sizeof(bt::Counters)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
     if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) { rc = BT_E_CUDA; break; }
   } while (0);
@@ -283,6 +285,7 @@ BT_API int bt_destroy(bt_ctx *c) {
   if (c->d_ctr) cudaFree(c->d_ctr);
   if (c->d_seg_count) cudaFree(c->d_seg_count);
   if (c->d_box) cudaFree(c->d_box);
+  if (c->d_lineage_next) cudaFree(c->d_lineage_next);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -334,7 +337,7 @@ BT_API int bt_load_scene(bt_ctx *c, const float *verts, int64_t n_verts, const i
     if ((rc = ensure(c, s.nodes, sizeof(bt::Node) * (size_t)(n_tris > 1 ? n_tris - 1 : 1)))) break;
     if ((rc = ensure(c, s.tris, sizeof(bt::Tri) * (size_t)n_tris))) break;
     if ((rc = ensure(c, s.planes, sizeof(bt::Plane) * (size_t)n_tris))) break;
-    if ((rc = ensure(c, s.planes64, sizeof(double4) * (size_t)n_tris))) break;
+    if ((rc = ensure(c, s.planes64, sizeof(bt::Plane64) * (size_t)n_tris))) break;
     if ((rc = ensure(c, s.refl, sizeof(float) * n_materials * n_bands))) break;
   } while (0);
   if (rc != BT_OK) { release_scene(c, s); return rc; }
@@ -368,7 +371,7 @@ BT_API int bt_load_scene(bt_ctx *c, const float *verts, int64_t n_verts, const i
   }
   CKS(bt::build_scene(st, (const float *)c->stage_a.p, (const int32_t *)c->stage_b.p, n_tris,
                       (const uint8_t *)c->stage_c.p, (bt::Node *)s.nodes.p, (bt::Tri *)s.tris.p,
-                      (bt::Plane *)s.planes.p, (double4 *)s.planes64.p, c->scratch.p, c->scratch.cap, box,
+                      (bt::Plane *)s.planes.p, (bt::Plane64 *)s.planes64.p, c->scratch.p, c->scratch.cap, box,
                       &c->d_ctr->error));
   CKS(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(bt::Counters), cudaMemcpyDeviceToHost, st));
   CKS(cudaStreamSynchronize(st));
@@ -519,6 +522,7 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   ta.segs = (bt::Seg *)c->segs.p;
   ta.seg_count = c->d_seg_count;
   ta.seg_capacity = cap;
+  ta.lineage_next = c->d_lineage_next;
   ta.ctr = c->d_ctr;
   ta.count_work = p->count_work ? 1 : 0;
   ta.mixed = p->precision == BT_PREC_MIXED ? 1 : 0;
@@ -559,6 +563,7 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
     ta.lineage_begin = b0;
     ta.lineage_end = b0 + chunk < total ? b0 + chunk : total;
     CK(cudaMemsetAsync(c->d_seg_count, 0, sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(c->d_lineage_next, 0, sizeof(unsigned long long), st));
     CK(cudaEventRecord(c->kev[4 * ci], st));
     CK(bt::launch_trace(st, ta, c->n_sm));
     CK(cudaEventRecord(c->kev[4 * ci + 1], st));

@@ -31,6 +31,10 @@ struct __align__(16) Tri {
 
 // Plane of a triangle: unit normal (x, y, z) and w = n . v0.
 using Plane = float4;
+// The same in float64, 32 bytes.
+struct __align__(32) Plane64 {
+  double x, y, z, w;
+};
 
 struct DevScene {
   int64_t n_tris;
@@ -38,7 +42,7 @@ struct DevScene {
   const Node *nodes;     // n_tris - 1 internal nodes
   const Tri *tris;       // n_tris, leaf order
   const Plane *planes;   // n_tris, leaf order
-  const double4 *planes64;  // n_tris, leaf order: float64 unit normal and n . v0
+  const Plane64 *planes64;  // n_tris, leaf order: float64 unit normal and n . v0
   const float *refl;     // [n_mat][n_bands]
   int n_mat, n_bands;
   float lo[3], hi[3];    // scene box
@@ -94,6 +98,7 @@ struct TraceArgs {
   int has_alpha;
   const MicGrid *grid;
   int64_t lineage_begin, lineage_end;  // chunk of (source, beam) lineages
+  unsigned long long *lineage_next;    // lineages of the chunk taken so far (zeroed per chunk)
   Seg *segs;
   unsigned long long *seg_count;
   unsigned long long seg_capacity;
@@ -105,7 +110,7 @@ struct TraceArgs {
 
 struct ScatterArgs {
   const Tri *tris;          // leaf order (start/end plane vertices)
-  const double4 *planes64;  // leaf order
+  const Plane64 *planes64;  // leaf order
   const Seg *segs;
   const unsigned long long *seg_count;
   unsigned long long seg_capacity;
@@ -191,10 +196,15 @@ __device__ __forceinline__ float hit_watertight(const Ray &r, float4 v0, float4 
   float v1_ = __fmul_rn(ax, cy), v2_ = __fmul_rn(ay, cx);
   float w1 = __fmul_rn(bx, ay), w2 = __fmul_rn(by, ax);
   float U = __fsub_rn(u1, u2), V = __fsub_rn(v1_, v2_), W = __fsub_rn(w1, w2);
+  // ambiguous: every edge function that is clearly away from zero agrees in
+  // sign (so the decision is not a clear miss) and at least one lies within
+  // the rounding band of its terms
   const float tau = 1e-4f;
   float su = fabsf(u1) + fabsf(u2), sv = fabsf(v1_) + fabsf(v2_), sw = fabsf(w1) + fabsf(w2);
-  amb = fabsf(U) <= tau * su || fabsf(V) <= tau * sv || fabsf(W) <= tau * sw ||
-        fabsf(U + V + W) <= tau * (su + sv + sw);
+  bool zu = fabsf(U) <= tau * su, zv = fabsf(V) <= tau * sv, zw = fabsf(W) <= tau * sw;
+  bool pos = (!zu && U > 0.0f) || (!zv && V > 0.0f) || (!zw && W > 0.0f);
+  bool neg = (!zu && U < 0.0f) || (!zv && V < 0.0f) || (!zw && W < 0.0f);
+  amb = (zu || zv || zw) && !(pos && neg);
   if (U == 0.0f || V == 0.0f || W == 0.0f) {
     U = (float)((double)cx * (double)by - (double)cy * (double)bx);
     V = (float)((double)ax * (double)cy - (double)ay * (double)cx);
@@ -224,10 +234,12 @@ __device__ __forceinline__ double3 cross_exact(double3 a, double3 b) {
                       __dsub_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x)));
 }
 __device__ __forceinline__ double3 normalize3(double3 a) { return a * (1.0 / sqrt(dot3(a, a))); }
-__device__ __forceinline__ double4 ldg_d4(const double4 *p) {
+__device__ __forceinline__ Plane64 ldg_d4(const Plane64 *p) {
   const double2 *q = reinterpret_cast<const double2 *>(p);
   double2 a = __ldg(q), b = __ldg(q + 1);
-  return make_double4(a.x, a.y, b.x, b.y);
+  Plane64 r;
+  r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
+  return r;
 }
 __device__ __forceinline__ float3 to_f3(double3 a) { return make_float3((float)a.x, (float)a.y, (float)a.z); }
 
@@ -363,7 +375,7 @@ cudaError_t validate_scene(cudaStream_t st, const float *d_verts, int64_t n_vert
                            float *d_box /*lo xyz, hi xyz*/, int *d_error);
 cudaError_t build_scene(cudaStream_t st, const float *d_verts, const int32_t *d_tris, int64_t n_tris,
                         const uint8_t *d_mat, Node *d_nodes, Tri *d_tris_out, Plane *d_planes,
-                        double4 *d_planes64, void *d_scratch, size_t scratch_bytes, const float *d_box,
+                        Plane64 *d_planes64, void *d_scratch, size_t scratch_bytes, const float *d_box,
                         int *d_error);
 cudaError_t launch_beam_table(cudaStream_t st, int level, double *table);
 size_t build_scene_scratch_bytes(int64_t n_tris);

@@ -273,7 +273,7 @@ __global__ void k_lbvh_topology(const uint32_t *keys, int n, Node *nodes, int *l
 
 // Triangles in leaf order with their planes; the normal is formed in double.
 __global__ void k_pack_tris(const float *verts, const int32_t *tris, const uint8_t *mat,
-                            const uint32_t *order, int64_t n, Tri *out, Plane *planes, double4 *planes64) {
+                            const uint32_t *order, int64_t n, Tri *out, Plane *planes, Plane64 *planes64) {
   int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
   int64_t t = order[s];
@@ -292,7 +292,10 @@ __global__ void k_pack_tris(const float *verts, const int32_t *tris, const uint8
   if (l > 0.0) { nx /= l; ny /= l; nz /= l; } else { nx = ny = nz = 0.0; }
   double w = nx * v[0].x + ny * v[0].y + nz * v[0].z;
   planes[s] = make_float4((float)nx, (float)ny, (float)nz, (float)w);
-  planes64[s] = make_double4(nx, ny, nz, w);
+  planes64[s].x = nx;
+  planes64[s].y = ny;
+  planes64[s].z = nz;
+  planes64[s].w = w;
 }
 
 __device__ __forceinline__ void tri_box(const Tri &t, float lo[3], float hi[3]) {
@@ -378,7 +381,7 @@ cudaError_t validate_scene(cudaStream_t st, const float *d_verts, int64_t n_vert
 // index and material is then in range and every coordinate finite.
 cudaError_t build_scene(cudaStream_t st, const float *d_verts, const int32_t *d_tris, int64_t n_tris,
                         const uint8_t *d_mat, Node *d_nodes, Tri *d_tris_out, Plane *d_planes,
-                        double4 *d_planes64, void *d_scratch, size_t scratch_bytes, const float *d_box,
+                        Plane64 *d_planes64, void *d_scratch, size_t scratch_bytes, const float *d_box,
                         int *d_error) {
   if (n_tris == 0) return cudaSuccess;
   if (scratch_bytes < build_scene_scratch_bytes(n_tris)) return cudaErrorInvalidValue;

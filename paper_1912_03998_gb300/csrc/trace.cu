@@ -114,7 +114,7 @@ cudaError_t launch_beam_table(cudaStream_t st, int level, double *table) {
 
 // Float64 distance along the ray to the plane of leaf slot `slot`.
 __device__ __forceinline__ double plane_t64(const DevScene &sc, int slot, double3 od, double3 dd) {
-  double4 pl = ldg_d4(&sc.planes64[slot]);
+  Plane64 pl = ldg_d4(&sc.planes64[slot]);
   double3 n = make_double3(pl.x, pl.y, pl.z);
   return (pl.w - dot3(n, od)) / dot3(n, dd);
 }
@@ -128,11 +128,13 @@ struct Best {
 };
 
 // Closest accepted hit of the ray in the BVH; ties in distance go to the
-// lowest original triangle id.  With kMixed, `od`/`dd` is the float64 ray the
-// float32 ray `r` was rounded from.  Returns the leaf slot or -1.
+// lowest original triangle id.  With kMixed, the float64 ray the float32 ray
+// `r` was rounded from is at od[0..5 * stride] (origin xyz, direction xyz,
+// in shared memory), read only on the rare float64 paths.  Returns the leaf
+// slot or -1.
 template <bool kMixed, bool kCount>
-__device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, double3 od, double3 dd, double dns64,
-                                           Best &best, int *err, unsigned long long &n_nodes,
+__device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, const double *od, int stride,
+                                           double dns64, Best &best, int *err, unsigned long long &n_nodes,
                                            unsigned long long &n_tris) {
   best.t = kInf;
   best.slot = -1;
@@ -140,7 +142,11 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, dou
   best.t64 = 0.0;
   best.has64 = false;
   if (sc.n_tris == 0) return -1;
-  // candidate evaluation, shared by the single-leaf root and the loop
+  auto ray64 = [&](double3 &o, double3 &d) {
+    o = make_double3(od[0], od[stride], od[2 * stride]);
+    d = make_double3(od[3 * stride], od[4 * stride], od[5 * stride]);
+  };
+  // candidate evaluation (one call site, so the code is emitted once)
   auto consider = [&](int slot) {
     if (kCount) n_tris++;
     const Tri *tp = sc.tris + slot;
@@ -150,8 +156,10 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, dou
     double t64 = 0.0;
     bool has64 = false;
     if (kMixed && amb) {
+      double3 o, d;
+      ray64(o, d);
       double tt;
-      if (!hit_mt64(od, dd, v0, v1, v2, tt)) return;
+      if (!hit_mt64(o, d, v0, v1, v2, tt)) return;
       if (!(tt > (double)r.t_eps && (dns64 == 0.0 || tt * dns64 > (double)r.t_eps))) return;
       t64 = tt;
       has64 = true;
@@ -173,9 +181,11 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, dou
       return;
     }
     if (t > best.t + win) return;
-    if (!has64) t64 = plane_t64(sc, slot, od, dd);
+    double3 o, d;
+    ray64(o, d);
+    if (!has64) t64 = plane_t64(sc, slot, o, d);
     if (!best.has64) {
-      best.t64 = plane_t64(sc, best.slot, od, dd);
+      best.t64 = plane_t64(sc, best.slot, o, d);
       best.has64 = true;
     }
     double tol = 1e-9 * (1.0 + fabs(t64));
@@ -183,45 +193,53 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, dou
       best.t = (float)t64; best.slot = slot; best.id = id; best.t64 = t64; best.has64 = true;
     }
   };
-  int node = sc.root;
-  if (node < 0) {  // a single triangle
-    consider(~node);
-    return best.slot;
-  }
   int stack[kStackDepth];
   int sp = 0;
+  int node = sc.root;
   // a well-formed BVH is visited at most once per node; the bound only
   // guarantees termination should the structure ever be malformed
   int64_t visits = 0;
   while (true) {
-    if (++visits > sc.n_tris + 64) {
-      atomicExch(err, BT_E_TIMEOUT);
-      break;
-    }
-    const Node *nd = sc.nodes + node;
-    if (kCount) n_nodes++;
-    float4 lxy = __ldg(&nd->lxy), rxy = __ldg(&nd->rxy), lrz = __ldg(&nd->lrz);
-    int2 ch = __ldg((const int2 *)&nd->child);
-    // in MIXED mode near ties must still be visited
-    float tmax = kMixed ? best.t + (1e-5f * fabsf(best.t) + 1e-4f) : best.t;
-    float tl, tr;
-    bool hl = slab(r, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, tmax, tl);
-    bool hr = slab(r, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, tmax, tr);
-    if (hl && ch.x < 0) { consider(~ch.x); hl = false; }
-    if (hr && ch.y < 0) { consider(~ch.y); hr = false; }
-    if (hl && hr) {
-      bool lf = tl <= tr;
-      if (sp < kStackDepth) stack[sp++] = lf ? ch.y : ch.x;
-      else atomicExch(err, BT_E_QUEUE_FULL);
-      node = lf ? ch.x : ch.y;
-    } else if (hl) {
-      node = ch.x;
-    } else if (hr) {
-      node = ch.y;
+    int c0 = -1, c1 = -1, nc = 0;
+    bool more = true;
+    if (node < 0) {  // a single-triangle scene: the root is a leaf
+      c0 = ~node;
+      nc = 1;
+      more = false;
     } else {
-      if (sp == 0) break;
-      node = stack[--sp];
+      if (++visits > sc.n_tris + 64) {
+        atomicExch(err, BT_E_TIMEOUT);
+        break;
+      }
+      const Node *nd = sc.nodes + node;
+      if (kCount) n_nodes++;
+      float4 lxy = __ldg(&nd->lxy), rxy = __ldg(&nd->rxy), lrz = __ldg(&nd->lrz);
+      int2 ch = __ldg((const int2 *)&nd->child);
+      // in MIXED mode near ties must still be visited
+      float tmax = kMixed ? best.t + (1e-5f * fabsf(best.t) + 1e-4f) : best.t;
+      float tl, tr;
+      bool hl = slab(r, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, tmax, tl);
+      bool hr = slab(r, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, tmax, tr);
+      if (hl && ch.x < 0) { c0 = ~ch.x; nc = 1; hl = false; }
+      if (hr && ch.y < 0) { if (nc) c1 = ~ch.y; else c0 = ~ch.y; nc++; hr = false; }
+      if (hl && hr) {
+        bool lf = tl <= tr;
+        if (sp < kStackDepth) stack[sp++] = lf ? ch.y : ch.x;
+        else atomicExch(err, BT_E_QUEUE_FULL);
+        node = lf ? ch.x : ch.y;
+      } else if (hl) {
+        node = ch.x;
+      } else if (hr) {
+        node = ch.y;
+      } else if (sp > 0) {
+        node = stack[--sp];
+      } else {
+        more = false;
+      }
     }
+#pragma unroll 1
+    for (int c = 0; c < nc; c++) consider(c == 0 ? c0 : c1);
+    if (!more) break;
   }
   return best.slot;
 }
@@ -244,8 +262,6 @@ __device__ __forceinline__ float4 plane4(double3 n, double w) {
   return make_float4((float)n.x, (float)n.y, (float)n.z, (float)w);
 }
 __device__ __forceinline__ float4 plane4(float3 n, float w) { return make_float4(n.x, n.y, n.z, w); }
-__device__ __forceinline__ double3 as_d3(float3 v) { return make_double3(v.x, v.y, v.z); }
-__device__ __forceinline__ double3 as_d3(double3 v) { return v; }
 
 // Warp-aggregated append of a segment record.
 __device__ __forceinline__ void emit_segment(const TraceArgs &a, const Seg &s, bool emit,
@@ -265,116 +281,200 @@ __device__ __forceinline__ void emit_segment(const TraceArgs &a, const Seg &s, b
   }
 }
 
+// Lineage state of one thread, kept in shared memory (one column per
+// thread) so that it does not hold registers across the traversal.
+constexpr int kTraceThreads = 128;
+template <typename T>
+struct LineageSmem {
+  T a[3][kTraceThreads];   // apex (source or image source)
+  T n[9][kTraceThreads];   // cone-face normals
+  double od[6][kTraceThreads];  // ray origin and direction (float64 in both modes)
+  float p[kMaxBands][kTraceThreads];  // band power W_b prod(r_b)
+  float st[4][kTraceThreads];         // start plane (relative to the apex)
+};
+
+template <typename T>
+__device__ __forceinline__ typename Vec3<T>::type lds3(const T (*arr)[kTraceThreads], int row, int t) {
+  typename Vec3<T>::type v;
+  v.x = arr[row][t];
+  v.y = arr[row + 1][t];
+  v.z = arr[row + 2][t];
+  return v;
+}
+template <typename T, typename V>
+__device__ __forceinline__ void sts3(T (*arr)[kTraceThreads], int row, int t, V v) {
+  arr[row][t] = (T)v.x;
+  arr[row + 1][t] = (T)v.y;
+  arr[row + 2][t] = (T)v.z;
+}
+
+// Persistent warps: every lane works on one lineage at a time and takes the
+// next one from a global counter as soon as its lineage ends, so a warp stays
+// full until the batch runs out (warp-vote refill of finished lanes).
 template <bool kMixed, bool kCount>
-__global__ void __launch_bounds__(128) k_trace(TraceArgs a) {
+__global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
   using T = typename std::conditional<kMixed, double, float>::type;
   using V = typename Vec3<T>::type;
+  __shared__ LineageSmem<T> sm;
+  const int t = threadIdx.x;
+  const unsigned lane = lane_id();
   const MicGrid g = *a.grid;
   const int nb = a.sc.n_bands;
   unsigned long long n_seg = 0, n_hit = 0, n_esc = 0, n_emit = 0, n_nodes = 0, n_tris = 0;
-  for (int64_t lin = a.lineage_begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-       lin < a.lineage_end; lin += (int64_t)gridDim.x * blockDim.x) {
-    int64_t si = lin / a.n_beams, bi = lin - si * a.n_beams;
-    V n0, n1, n2, D;
-    if (kMixed) {
-      const double *bt = a.beam_table + 12 * bi;
-      n0.x = __ldg(bt + 0); n0.y = __ldg(bt + 1); n0.z = __ldg(bt + 2);
-      n1.x = __ldg(bt + 3); n1.y = __ldg(bt + 4); n1.z = __ldg(bt + 5);
-      n2.x = __ldg(bt + 6); n2.y = __ldg(bt + 7); n2.z = __ldg(bt + 8);
-      D.x = __ldg(bt + 9); D.y = __ldg(bt + 10); D.z = __ldg(bt + 11);
-    } else {
-      V d0, d1, d2;
-      beam_dirs<T>(a.level, bi, d0, d1, d2);
-      n0 = cross_exact(d0, d1);
-      n1 = cross_exact(d1, d2);
-      n2 = cross_exact(d2, d0);
-      D = normalize3((d0 + d1) + d2);
-    }
-    float4 s4 = __ldg(&a.src[si]);
-    V A;
-    A.x = s4.x; A.y = s4.y; A.z = s4.z;
-    V O = A;
-    int start_slot = -1;
-    float P[kMaxBands];
+  int64_t lin = -1;
+  int k = 0, start_slot = -1;
+  T dns = 0;
+  bool done = false;
+  while (true) {
+    // refill lanes whose lineage ended
+    bool need = !done && lin < 0;
+    unsigned nm = __ballot_sync(0xffffffffu, need);
+    if (nm) {
+      int leader = __ffs(nm) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(a.lineage_next, (unsigned long long)__popc(nm));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (need) {
+        int64_t mine = a.lineage_begin + (int64_t)(base + __popc(nm & ((1u << lane) - 1u)));
+        if (mine < a.lineage_end) {
+          lin = mine;
+          int64_t si = lin / a.n_beams, bi = lin - si * a.n_beams;
+          V n0, n1, n2, D;
+          if (kMixed) {
+            const double *bt = a.beam_table + 12 * bi;
+            n0.x = __ldg(bt + 0); n0.y = __ldg(bt + 1); n0.z = __ldg(bt + 2);
+            n1.x = __ldg(bt + 3); n1.y = __ldg(bt + 4); n1.z = __ldg(bt + 5);
+            n2.x = __ldg(bt + 6); n2.y = __ldg(bt + 7); n2.z = __ldg(bt + 8);
+            D.x = __ldg(bt + 9); D.y = __ldg(bt + 10); D.z = __ldg(bt + 11);
+          } else {
+            V d0, d1, d2;
+            beam_dirs<T>(a.level, bi, d0, d1, d2);
+            n0 = cross_exact(d0, d1);
+            n1 = cross_exact(d1, d2);
+            n2 = cross_exact(d2, d0);
+            D = normalize3((d0 + d1) + d2);
+          }
+          float4 s4 = __ldg(&a.src[si]);
+          V A;
+          A.x = s4.x; A.y = s4.y; A.z = s4.z;
+          sts3(sm.a, 0, t, A);
+          sts3(sm.n, 0, t, n0);
+          sts3(sm.n, 3, t, n1);
+          sts3(sm.n, 6, t, n2);
+          sts3(sm.od, 0, t, A);
+          sts3(sm.od, 3, t, D);
 #pragma unroll
-    for (int b = 0; b < kMaxBands; b++) P[b] = b < nb ? __ldg(&a.power[si * nb + b]) : 0.0f;
-    float4 start = make_float4(0.0f, 0.0f, 0.0f, -kInf);
-    T dns = 0;
-    for (int k = 0; k <= a.max_order; k++) {
-      float3 of = make_float3((float)O.x, (float)O.y, (float)O.z);
-      float3 df = make_float3((float)D.x, (float)D.y, (float)D.z);
-      Ray r = make_ray(of, df, a.t_eps, (float)dns);
-      Best best;
-      int slot = closest_hit<kMixed, kCount>(a.sc, r, as_d3(O), as_d3(D), (double)dns, best, &a.ctr->error,
-                                             n_nodes, n_tris);
-      n_seg++;
-      float4 end = make_float4(0.0f, 0.0f, 0.0f, -kInf);
-      V pn;
-      pn.x = 0; pn.y = 0; pn.z = 0;
-      float4 v0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      T th = 0;
-      if (slot >= 0) {
-        n_hit++;
-        const Tri *tp = a.sc.tris + slot;
-        v0 = __ldg(&tp->v0);
-        if (kMixed) {
-          // float64 plane of the hit triangle and float64 hit distance
-          double4 p64 = ldg_d4(&a.sc.planes64[slot]);
-          pn.x = (T)p64.x; pn.y = (T)p64.y; pn.z = (T)p64.z;
-          th = (T)(best.has64 ? best.t64 : plane_t64(a.sc, slot, as_d3(O), as_d3(D)));
+          for (int b = 0; b < kMaxBands; b++) sm.p[b][t] = b < nb ? __ldg(&a.power[si * nb + b]) : 0.0f;
+          sm.st[0][t] = 0.0f; sm.st[1][t] = 0.0f; sm.st[2][t] = 0.0f; sm.st[3][t] = -kInf;
+          k = 0;
+          start_slot = -1;
+          dns = 0;
         } else {
-          float4 pl = __ldg(&a.sc.planes[slot]);
-          pn.x = (T)pl.x; pn.y = (T)pl.y; pn.z = (T)pl.z;
-          th = (T)best.t;
+          done = true;
         }
-        // end plane on the incident side, offset relative to the apex
-        V en = dot3(pn, D) < (T)0 ? pn : pn * (T)-1;
-        V pv0;
-        pv0.x = v0.x; pv0.y = v0.y; pv0.z = v0.z;
-        end = plane4(en, dot3(en, pv0 - A));
-      } else {
-        n_esc++;
       }
+    }
+    if (__all_sync(0xffffffffu, done)) break;
+    if (done) continue;
+    // ---- one segment of this lane's lineage
+    Ray r;
+    {
+      double3 O = lds3(sm.od, 0, t), D = lds3(sm.od, 3, t);
+      r = make_ray(to_f3(O), to_f3(D), a.t_eps, (float)dns);
+    }
+    Best best;
+    int slot = closest_hit<kMixed, kCount>(a.sc, r, &sm.od[0][t], kTraceThreads, (double)dns, best,
+                                           &a.ctr->error, n_nodes, n_tris);
+    n_seg++;
+    V O, D;
+    {
+      double3 o = lds3(sm.od, 0, t), d = lds3(sm.od, 3, t);
+      O.x = (T)o.x; O.y = (T)o.y; O.z = (T)o.z;
+      D.x = (T)d.x; D.y = (T)d.y; D.z = (T)d.z;
+    }
+    V A = lds3(sm.a, 0, t);
+    float4 end = make_float4(0.0f, 0.0f, 0.0f, -kInf);
+    V pn;
+    pn.x = 0; pn.y = 0; pn.z = 0;
+    float4 v0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    T th = 0;
+    if (slot >= 0) {
+      n_hit++;
+      v0 = __ldg(&a.sc.tris[slot].v0);
+      if (kMixed) {
+        // float64 plane of the hit triangle and float64 hit distance
+        Plane64 p64 = ldg_d4(&a.sc.planes64[slot]);
+        pn.x = (T)p64.x; pn.y = (T)p64.y; pn.z = (T)p64.z;
+        th = (T)(best.has64 ? best.t64
+                            : plane_t64(a.sc, slot, make_double3(O.x, O.y, O.z), make_double3(D.x, D.y, D.z)));
+      } else {
+        float4 pl = __ldg(&a.sc.planes[slot]);
+        pn.x = (T)pl.x; pn.y = (T)pl.y; pn.z = (T)pl.z;
+        th = (T)best.t;
+      }
+      // end plane on the incident side, offset relative to the apex
+      V en = dot3(pn, D) < (T)0 ? pn : pn * (T)-1;
+      V pv0;
+      pv0.x = v0.x; pv0.y = v0.y; pv0.z = v0.z;
+      end = plane4(en, dot3(en, pv0 - A));
+    } else {
+      n_esc++;
+    }
+    {
       Seg s;
       s.ax = (double)A.x;
       s.ay = (double)A.y;
       s.az = (double)A.z;
-      s.n0 = make_float4((float)n0.x, (float)n0.y, (float)n0.z, __int_as_float(start_slot));
-      s.n1 = make_float4((float)n1.x, (float)n1.y, (float)n1.z, __int_as_float(slot));
-      s.n2 = make_float4((float)n2.x, (float)n2.y, (float)n2.z, __int_as_float(k));
-      s.start = start;
+      s.n0 = make_float4((float)sm.n[0][t], (float)sm.n[1][t], (float)sm.n[2][t], __int_as_float(start_slot));
+      s.n1 = make_float4((float)sm.n[3][t], (float)sm.n[4][t], (float)sm.n[5][t], __int_as_float(slot));
+      s.n2 = make_float4((float)sm.n[6][t], (float)sm.n[7][t], (float)sm.n[8][t], __int_as_float(k));
+      s.start = make_float4(sm.st[0][t], sm.st[1][t], sm.st[2][t], sm.st[3][t]);
       s.end = end;
-      s.p03 = make_float4(P[0], P[1], P[2], P[3]);
-      s.p47 = make_float4(P[4], P[5], P[6], P[7]);
+      s.p03 = make_float4(sm.p[0][t], sm.p[1][t], sm.p[2][t], sm.p[3][t]);
+      s.p47 = make_float4(sm.p[4][t], sm.p[5][t], sm.p[6][t], sm.p[7][t]);
       int cy0 = 0, cy1 = -1;
       bool emit = g.n_mics > 0 && seg_rows(s, g, cy0, cy1);
       s.cy0 = cy0;
       s.cy1 = cy1;
       emit_segment(a, s, emit, n_emit);
-      if (slot < 0 || k == a.max_order) break;
+    }
+    bool ends = slot < 0 || k == a.max_order;
+    if (!ends) {
       // Image source: mirror the apex, the cone and the axis in the hit
       // plane; the reflected beam starts on that plane and loses energy.
       int mat = __float_as_int(v0.w);
       float wmax = 0.0f;
 #pragma unroll
       for (int b = 0; b < kMaxBands; b++) {
-        if (b < nb) P[b] *= __ldg(&a.sc.refl[mat * nb + b]);
-        wmax = fmaxf(wmax, P[b]);
+        float p = sm.p[b][t];
+        if (b < nb) p *= __ldg(&a.sc.refl[mat * nb + b]);
+        sm.p[b][t] = p;
+        wmax = fmaxf(wmax, p);
       }
-      if (a.energy_threshold > 0.0f && wmax < a.energy_threshold) break;
+      if (a.energy_threshold > 0.0f && wmax < a.energy_threshold) ends = true;
+    }
+    if (!ends) {
       V pv0;
       pv0.x = v0.x; pv0.y = v0.y; pv0.z = v0.z;
       V H = O + D * th;
       A = A - pn * ((T)2 * dot3(A - pv0, pn));
-      n0 = n0 - pn * ((T)2 * dot3(n0, pn));
-      n1 = n1 - pn * ((T)2 * dot3(n1, pn));
-      n2 = n2 - pn * ((T)2 * dot3(n2, pn));
+#pragma unroll
+      for (int j = 0; j < 3; j++) {
+        V nj = lds3(sm.n, 3 * j, t);
+        sts3(sm.n, 3 * j, t, nj - pn * ((T)2 * dot3(nj, pn)));
+      }
       D = D - pn * ((T)2 * dot3(D, pn));
-      O = H;
+      sts3(sm.a, 0, t, A);
+      sts3(sm.od, 0, t, H);
+      sts3(sm.od, 3, t, D);
       V sn = dot3(pn, D) > (T)0 ? pn : pn * (T)-1;
-      start = plane4(sn, dot3(sn, pv0 - A));
+      float4 st4 = plane4(sn, dot3(sn, pv0 - A));
+      sm.st[0][t] = st4.x; sm.st[1][t] = st4.y; sm.st[2][t] = st4.z; sm.st[3][t] = st4.w;
       dns = dot3(sn, D);
       start_slot = slot;
+      k++;
+    } else {
+      lin = -1;
     }
   }
   // warp-aggregated counters
@@ -388,7 +488,7 @@ __global__ void __launch_bounds__(128) k_trace(TraceArgs a) {
       n_tris += __shfl_xor_sync(0xffffffffu, n_tris, o);
     }
   }
-  if (lane_id() == 0) {
+  if (lane == 0) {
     if (kCount) {
       atomicAdd(&a.ctr->nodes_visited, n_nodes);
       atomicAdd(&a.ctr->tris_tested, n_tris);
@@ -403,18 +503,22 @@ __global__ void __launch_bounds__(128) k_trace(TraceArgs a) {
 // Closest hit of arbitrary float32 rays (the axis-ray query of the trace
 // kernel on its own), decided as in MIXED mode with the float32 ray promoted
 // to float64 for ambiguous triangles.  ns: optional start-plane normals.
-__global__ void k_cast(DevScene sc, const float *o, const float *d, const float *ns, int64_t n, float t_eps,
-                       float *t_out, int *tri_out, int *err) {
+__global__ void __launch_bounds__(128) k_cast(DevScene sc, const float *o, const float *d, const float *ns,
+                                              int64_t n, float t_eps, float *t_out, int *tri_out, int *err) {
+  __shared__ double od[6][128];
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int t = threadIdx.x;
   double3 O = make_double3(o[3 * i], o[3 * i + 1], o[3 * i + 2]);
   double3 D = normalize3(make_double3(d[3 * i], d[3 * i + 1], d[3 * i + 2]));
   double dns = 0.0;
   if (ns) dns = fabs(dot3(D, make_double3(ns[3 * i], ns[3 * i + 1], ns[3 * i + 2])));
+  od[0][t] = O.x; od[1][t] = O.y; od[2][t] = O.z;
+  od[3][t] = D.x; od[4][t] = D.y; od[5][t] = D.z;
   Ray r = make_ray(to_f3(O), to_f3(D), t_eps, (float)dns);
   Best best;
   unsigned long long a = 0, b = 0;
-  int slot = closest_hit<true, false>(sc, r, O, D, dns, best, err, a, b);
+  int slot = closest_hit<true, false>(sc, r, &od[0][t], 128, dns, best, err, a, b);
   t_out[i] = slot >= 0 ? (best.has64 ? (float)best.t64 : best.t) : kInf;
   tri_out[i] = slot >= 0 ? best.id : -1;
 }
@@ -427,29 +531,37 @@ cudaError_t launch_cast(cudaStream_t st, const DevScene &sc, const float *o, con
   return cudaGetLastError();
 }
 
+// One persistent grid: enough blocks to fill every SM at the kernel's
+// occupancy, each block looping until the batch's lineages are taken.
+template <bool kMixed, bool kCount>
+static cudaError_t launch_trace_t(cudaStream_t st, const TraceArgs &a, int n_sm) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<kMixed, kCount>, kTraceThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t n = a.lineage_end - a.lineage_begin;
+  int64_t blocks = (int64_t)n_sm * per_sm;
+  int64_t need = (n + kTraceThreads - 1) / kTraceThreads;
+  if (blocks > need) blocks = need;
+  k_trace<kMixed, kCount><<<(int)blocks, kTraceThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_trace(cudaStream_t st, const TraceArgs &a, int n_sm) {
   int64_t n = a.lineage_end - a.lineage_begin;
   if (n <= 0) return cudaSuccess;
-  int threads = 128;
-  int64_t blocks = (n + threads - 1) / threads;
-  int64_t cap = (int64_t)n_sm * 64;
-  if (blocks > cap) blocks = cap;
-  if (a.mixed) {
-    if (a.count_work) k_trace<true, true><<<(int)blocks, threads, 0, st>>>(a);
-    else k_trace<true, false><<<(int)blocks, threads, 0, st>>>(a);
-  } else {
-    if (a.count_work) k_trace<false, true><<<(int)blocks, threads, 0, st>>>(a);
-    else k_trace<false, false><<<(int)blocks, threads, 0, st>>>(a);
-  }
+  cudaError_t e;
+  if (a.mixed) e = a.count_work ? launch_trace_t<true, true>(st, a, n_sm) : launch_trace_t<true, false>(st, a, n_sm);
+  else e = a.count_work ? launch_trace_t<false, true>(st, a, n_sm) : launch_trace_t<false, false>(st, a, n_sm);
   note_launches(1);
-  return cudaGetLastError();
+  return e;
 }
 
 // ------------------------------------------------------------------ scatter
 // Signed distance of m from the plane of leaf slot `slot`, in float64,
 // oriented like the float32 normal `nf` of the segment record.
 __device__ __forceinline__ double plane_side64(const ScatterArgs &a, int slot, float3 nf, float4 m) {
-  double4 pl = ldg_d4(&a.planes64[slot]);
+  Plane64 pl = ldg_d4(&a.planes64[slot]);
   float4 v0 = __ldg(&a.tris[slot].v0);
   double3 n = make_double3(pl.x, pl.y, pl.z);
   if (n.x * nf.x + n.y * nf.y + n.z * nf.z < 0.0) n = n * -1.0;
