@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"],
+                    help="mixed: float64 image-source chain (the parity-checked default)")
     return ap.parse_args()
 
 
@@ -173,6 +175,7 @@ def run_ours(args, rank, world):
     params = btrace.bt_params_default()
     params.max_order = w.max_order
     params.tiles_x, params.tiles_y = tiles
+    params.precision = btrace.BT_PREC_MIXED if args.precision == "mixed" else btrace.BT_PREC_FP32
     l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(inp, level_out):
@@ -336,7 +339,10 @@ def main():
     value = segs / (total_ms * 1e-3)
     cfg = describe(w, res["tiles"])
     cfg.update({"l2": "flushed before every step (256 MB write, outside the events)",
-                "precision": "FP32 traversal and microphone tests, FP64 energy accumulation",
+                "precision": ("MIXED: FP64 image-source chain, FP32 traversal with FP64 re-test of "
+                              "ambiguous hits, FP32 microphone tests with FP64 re-test near planes, "
+                              "FP64 energy accumulation") if args.precision == "mixed" else
+                             "FP32 chain, traversal and microphone tests, FP64 energy accumulation",
                 "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,

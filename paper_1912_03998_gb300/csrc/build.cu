@@ -99,9 +99,11 @@ __global__ void k_morton(const float *verts, const int32_t *tris, int64_t n_tris
   }
   float scene_xy = fmaxf(box[3] - box[0], box[4] - box[1]);
   bool large = fmaxf(hi[0] - lo[0], hi[1] - lo[1]) > scene_xy * (1.0f / 16.0f);
+  // one scale for all axes (the largest extent): a flat city then splits on
+  // x and y far more often than on z
+  float ext = fmaxf(fmaxf(box[3] - box[0], box[4] - box[1]), box[5] - box[2]);
   uint32_t q[3];
   for (int k = 0; k < 3; k++) {
-    float ext = box[3 + k] - box[k];
     float u = ext > 0.0f ? (c[k] - box[k]) / ext : 0.5f;
     u = fminf(fmaxf(u, 0.0f), 1.0f);
     q[k] = (uint32_t)fminf(u * 1024.0f, 1023.0f);

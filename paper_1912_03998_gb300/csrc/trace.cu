@@ -246,15 +246,17 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, con
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
-// Row range of the segment's footprint, or false if it misses the grid.
-__device__ __forceinline__ bool seg_rows(const Seg &s, const MicGrid &g, int &cy0, int &cy1) {
-  Poly p;
-  if (!seg_footprint(s, g, p)) return false;
-  float ymin = kInf, ymax = -kInf;
-  for (int i = 0; i < p.n; i++) { ymin = fminf(ymin, p.y[i]); ymax = fmaxf(ymax, p.y[i]); }
-  if (!(ymin <= ymax)) return false;
-  cy0 = clampi((int)floorf((ymin - g.y0) * g.inv_ch), 0, g.ny - 1);
-  cy1 = clampi((int)floorf((ymax - g.y0) * g.inv_ch), 0, g.ny - 1);
+// Cheap rejection of a segment that cannot reach the microphones' height
+// slab: the cone lies on one side of its apex height when all three edge
+// directions (d_j ~ n_{j-1} x n_j for a counter-clockwise cone) point the same
+// way in z.  Everything else goes to the scatter, which clips the footprint.
+__device__ __forceinline__ bool may_reach_slab(const Seg &s, const MicGrid &g) {
+  float dz0 = s.n2.x * s.n0.y - s.n2.y * s.n0.x;
+  float dz1 = s.n0.x * s.n1.y - s.n0.y * s.n1.x;
+  float dz2 = s.n1.x * s.n2.y - s.n1.y * s.n2.x;
+  float az = (float)s.az, m = 1e-3f;
+  if (dz0 < 0.0f && dz1 < 0.0f && dz2 < 0.0f && az < g.zlo - m) return false;
+  if (dz0 > 0.0f && dz1 > 0.0f && dz2 > 0.0f && az > g.zhi + m) return false;
   return true;
 }
 
@@ -288,7 +290,7 @@ template <typename T>
 struct LineageSmem {
   T a[3][kTraceThreads];   // apex (source or image source)
   T n[9][kTraceThreads];   // cone-face normals
-  double od[6][kTraceThreads];  // ray origin and direction (float64 in both modes)
+  T od[6][kTraceThreads];  // ray origin and direction
   float p[kMaxBands][kTraceThreads];  // band power W_b prod(r_b)
   float st[4][kTraceThreads];         // start plane (relative to the apex)
 };
@@ -379,19 +381,15 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
     // ---- one segment of this lane's lineage
     Ray r;
     {
-      double3 O = lds3(sm.od, 0, t), D = lds3(sm.od, 3, t);
-      r = make_ray(to_f3(O), to_f3(D), a.t_eps, (float)dns);
+      V O = lds3(sm.od, 0, t), D = lds3(sm.od, 3, t);
+      r = make_ray(make_float3((float)O.x, (float)O.y, (float)O.z), make_float3((float)D.x, (float)D.y, (float)D.z),
+                   a.t_eps, (float)dns);
     }
     Best best;
-    int slot = closest_hit<kMixed, kCount>(a.sc, r, &sm.od[0][t], kTraceThreads, (double)dns, best,
-                                           &a.ctr->error, n_nodes, n_tris);
+    int slot = closest_hit<kMixed, kCount>(a.sc, r, kMixed ? (const double *)&sm.od[0][t] : nullptr, kTraceThreads,
+                                           (double)dns, best, &a.ctr->error, n_nodes, n_tris);
     n_seg++;
-    V O, D;
-    {
-      double3 o = lds3(sm.od, 0, t), d = lds3(sm.od, 3, t);
-      O.x = (T)o.x; O.y = (T)o.y; O.z = (T)o.z;
-      D.x = (T)d.x; D.y = (T)d.y; D.z = (T)d.z;
-    }
+    V O = lds3(sm.od, 0, t), D = lds3(sm.od, 3, t);
     V A = lds3(sm.a, 0, t);
     float4 end = make_float4(0.0f, 0.0f, 0.0f, -kInf);
     V pn;
@@ -432,11 +430,9 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
       s.end = end;
       s.p03 = make_float4(sm.p[0][t], sm.p[1][t], sm.p[2][t], sm.p[3][t]);
       s.p47 = make_float4(sm.p[4][t], sm.p[5][t], sm.p[6][t], sm.p[7][t]);
-      int cy0 = 0, cy1 = -1;
-      bool emit = g.n_mics > 0 && seg_rows(s, g, cy0, cy1);
-      s.cy0 = cy0;
-      s.cy1 = cy1;
-      emit_segment(a, s, emit, n_emit);
+      s.cy0 = 0;
+      s.cy1 = -1;
+      emit_segment(a, s, g.n_mics > 0 && may_reach_slab(s, g), n_emit);
     }
     bool ends = slot < 0 || k == a.max_order;
     if (!ends) {
@@ -568,33 +564,125 @@ __device__ __forceinline__ double plane_side64(const ScatterArgs &a, int slot, f
   return dot3(n, make_double3((double)m.x - v0.x, (double)m.y - v0.y, (double)m.z - v0.z));
 }
 
-__global__ void __launch_bounds__(256) k_scatter(ScatterArgs a) {
+// Per-warp shared state of the scatter: 32 segments, one per lane, stored as
+// [field][lane] so that lanes reading different segments hit different banks.
+constexpr int kScatterWarps = 4;
+enum : int {
+  F_AX = 0, F_RX = 3, F_N0 = 6, F_N1 = 9, F_N2 = 12, F_NS = 15, F_NE = 19, F_P = 23, F_SLOTS = 31,
+  F_CY0 = 33, F_CY1 = 34, F_PN = 35, F_PX = 36, F_PY = F_PX + kPolyMax, F_COUNT = F_PY + kPolyMax
+};
+struct ScatterSmem {
+  float f[kScatterWarps][F_COUNT][32];
+};
+
+__device__ __forceinline__ int warp_incl_scan(int v, unsigned lane) {
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, v, o);
+    if ((int)lane >= o) v += y;
+  }
+  return v;
+}
+
+// Largest lane whose exclusive prefix is <= i (the owner of item i).
+__device__ __forceinline__ int warp_owner(int excl, int i) {
+  int owner = 0;
+  for (int step = 16; step >= 1; step >>= 1) {
+    int ex = __shfl_sync(0xffffffffu, excl, owner + step);
+    if (ex <= i) owner += step;
+  }
+  return owner;
+}
+
+// One warp takes 32 segments at a time.  Each lane loads one segment and
+// builds its footprint; the warp then walks the (segment, cell row) pairs of
+// all 32 footprints 32 at a time, turns each into its run of microphones, and
+// walks the runs 32 candidates at a time, so every lane has work whatever
+// the footprint sizes.
+__global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
+  __shared__ ScatterSmem sm;
   const MicGrid g = *a.grid;
   const unsigned lane = lane_id();
-  const unsigned long long n_seg = min(*a.seg_count, a.seg_capacity);
+  const int w = threadIdx.x >> 5;
+  float(*F)[32] = sm.f[w];
+  const long long n_seg = (long long)min(*a.seg_count, a.seg_capacity);
   const int nb = a.n_bands;
   unsigned long long n_cand = 0, n_contrib = 0;
   const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long si = warp0; si < (long long)n_seg; si += n_warps) {
-    const Seg s = a.segs[si];
-    Poly p;
-    if (!seg_footprint(s, g, p)) continue;
-    const int cy0 = s.cy0, cy1 = s.cy1;
-    const double ax = s.ax, ay = s.ay, az = s.az;
-    const float3 n0 = f3(s.n0), n1 = f3(s.n1), n2 = f3(s.n2);
-    const float3 ns = f3(s.start), ne = f3(s.end);
-    const float ws = s.start.w, we = s.end.w;
-    const int s_slot = __float_as_int(s.n0.w), e_slot = __float_as_int(s.n1.w);
-    const float P[kMaxBands] = {s.p03.x, s.p03.y, s.p03.z, s.p03.w, s.p47.x, s.p47.y, s.p47.z, s.p47.w};
-    for (int rb = cy0; rb <= cy1; rb += 32) {
-      int row = rb + (int)lane;
+  for (long long base = warp0 * 32; base < n_seg; base += n_warps * 32) {
+    // ---- 1. one segment per lane: parameters and footprint
+    long long si = base + lane;
+    int nrows = 0;
+    if (si < n_seg) {
+      const Seg s = a.segs[si];
+      Poly p;
+      int cy0 = 0, cy1 = -1;
+      if (seg_footprint(s, g, p)) {
+        float ymin = kInf, ymax = -kInf;
+        for (int i = 0; i < p.n; i++) { ymin = fminf(ymin, p.y[i]); ymax = fmaxf(ymax, p.y[i]); }
+        if (ymin <= ymax) {
+          cy0 = clampi((int)floorf((ymin - g.y0) * g.inv_ch), 0, g.ny - 1);
+          cy1 = clampi((int)floorf((ymax - g.y0) * g.inv_ch), 0, g.ny - 1);
+        }
+      }
+      nrows = cy1 >= cy0 ? cy1 - cy0 + 1 : 0;
+      // apex as a float plus a float residual: m - apex is then formed in
+      // float32 to within about one rounding of the float64 difference
+      float ax = (float)s.ax, ay = (float)s.ay, az = (float)s.az;
+      F[F_AX][lane] = ax; F[F_AX + 1][lane] = ay; F[F_AX + 2][lane] = az;
+      F[F_RX][lane] = (float)(s.ax - (double)ax);
+      F[F_RX + 1][lane] = (float)(s.ay - (double)ay);
+      F[F_RX + 2][lane] = (float)(s.az - (double)az);
+      F[F_N0][lane] = s.n0.x; F[F_N0 + 1][lane] = s.n0.y; F[F_N0 + 2][lane] = s.n0.z;
+      F[F_N1][lane] = s.n1.x; F[F_N1 + 1][lane] = s.n1.y; F[F_N1 + 2][lane] = s.n1.z;
+      F[F_N2][lane] = s.n2.x; F[F_N2 + 1][lane] = s.n2.y; F[F_N2 + 2][lane] = s.n2.z;
+      F[F_NS][lane] = s.start.x; F[F_NS + 1][lane] = s.start.y; F[F_NS + 2][lane] = s.start.z;
+      F[F_NS + 3][lane] = s.start.w;
+      F[F_NE][lane] = s.end.x; F[F_NE + 1][lane] = s.end.y; F[F_NE + 2][lane] = s.end.z;
+      F[F_NE + 3][lane] = s.end.w;
+      F[F_P][lane] = s.p03.x; F[F_P + 1][lane] = s.p03.y; F[F_P + 2][lane] = s.p03.z;
+      F[F_P + 3][lane] = s.p03.w; F[F_P + 4][lane] = s.p47.x; F[F_P + 5][lane] = s.p47.y;
+      F[F_P + 6][lane] = s.p47.z; F[F_P + 7][lane] = s.p47.w;
+      F[F_SLOTS][lane] = s.n0.w;  // start-plane triangle slot (int bits)
+      F[F_SLOTS + 1][lane] = s.n1.w;  // end-plane triangle slot (int bits)
+      F[F_CY0][lane] = __int_as_float(cy0);
+      F[F_PN][lane] = __int_as_float(p.n);
+      for (int i = 0; i < kPolyMax; i++) {
+        F[F_PX + i][lane] = i < p.n ? p.x[i] : 0.0f;
+        F[F_PY + i][lane] = i < p.n ? p.y[i] : 0.0f;
+      }
+    }
+    __syncwarp();
+    // ---- 2. (segment, row) pairs of the 32 footprints, 32 at a time
+    const int rincl = warp_incl_scan(nrows, lane);
+    const int total_rows = __shfl_sync(0xffffffffu, rincl, 31);
+    const int rexcl = rincl - nrows;
+    for (int rb = 0; rb < total_rows; rb += 32) {
+      int r = rb + (int)lane;
+      int so = warp_owner(rexcl, r);  // segment lane owning pair r
+      int so_excl = __shfl_sync(0xffffffffu, rexcl, so);
       int first = 0, cnt = 0;
-      if (row <= cy1) {
+      if (r < total_rows) {
+        int row = __float_as_int(F[F_CY0][so]) + (r - so_excl);
         float ya = g.y0 + row * g.ch, yb = ya + g.ch;
         float my = 1e-3f * g.ch;
-        float xmin, xmax;
-        poly_strip_x(p, ya - my, yb + my, xmin, xmax);
+        // x extent of the owner's footprint within the row's strip
+        int pn = __float_as_int(F[F_PN][so]);
+        float xmin = kInf, xmax = -kInf;
+        float y0s = ya - my, y1s = yb + my;
+        for (int i = 0; i < pn; i++) {
+          int j = i + 1 == pn ? 0 : i + 1;
+          float xi = F[F_PX + i][so], yi = F[F_PY + i][so], xj = F[F_PX + j][so], yj = F[F_PY + j][so];
+          if (yi >= y0s && yi <= y1s) { xmin = fminf(xmin, xi); xmax = fmaxf(xmax, xi); }
+          if ((yi < y0s) != (yj < y0s) && yi != yj) {
+            float x = xi + (y0s - yi) / (yj - yi) * (xj - xi);
+            xmin = fminf(xmin, x); xmax = fmaxf(xmax, x);
+          }
+          if ((yi < y1s) != (yj < y1s) && yi != yj) {
+            float x = xi + (y1s - yi) / (yj - yi) * (xj - xi);
+            xmin = fminf(xmin, x); xmax = fmaxf(xmax, x);
+          }
+        }
         if (xmin <= xmax) {
           int cx0 = clampi((int)floorf((xmin - g.x0) * g.inv_cw), 0, g.nx - 1);
           int cx1 = clampi((int)floorf((xmax - g.x0) * g.inv_cw), 0, g.nx - 1);
@@ -602,36 +690,35 @@ __global__ void __launch_bounds__(256) k_scatter(ScatterArgs a) {
           cnt = __ldg(&a.cell_start[row * g.nx + cx1 + 1]) - first;
         }
       }
-      int incl = cnt;
-      for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if ((int)lane >= o) incl += y;
-      }
-      const int total = __shfl_sync(0xffffffffu, incl, 31);
-      const int excl = incl - cnt;
-      for (int base = 0; base < total; base += 32) {
-        int i = base + (int)lane;
-        int owner = 0;
-        for (int step = 16; step >= 1; step >>= 1) {
-          int ex = __shfl_sync(0xffffffffu, excl, owner + step);
-          if (ex <= i) owner += step;
-        }
-        int ofirst = __shfl_sync(0xffffffffu, first, owner);
-        int oexcl = __shfl_sync(0xffffffffu, excl, owner);
-        if (i < total) {
-          int mi = ofirst + (i - oexcl);
+      // ---- 3. candidates of those runs, 32 at a time
+      const int cincl = warp_incl_scan(cnt, lane);
+      const int total_c = __shfl_sync(0xffffffffu, cincl, 31);
+      const int cexcl = cincl - cnt;
+      for (int cb = 0; cb < total_c; cb += 32) {
+        int c = cb + (int)lane;
+        int ro = warp_owner(cexcl, c);
+        int ofirst = __shfl_sync(0xffffffffu, first, ro);
+        int oexcl = __shfl_sync(0xffffffffu, cexcl, ro);
+        int s = __shfl_sync(0xffffffffu, so, ro);
+        if (c < total_c) {
+          int mi = ofirst + (c - oexcl);
           float4 m = __ldg(&a.mics[mi]);
-          // m - apex in float64, then float32 tests relative to the apex
-          float3 v = make_float3((float)((double)m.x - ax), (float)((double)m.y - ay),
-                                 (float)((double)m.z - az));
+          float3 v = make_float3((m.x - F[F_AX][s]) - F[F_RX][s], (m.y - F[F_AX + 1][s]) - F[F_RX + 1][s],
+                                 (m.z - F[F_AX + 2][s]) - F[F_RX + 2][s]);
           n_cand++;
+          float3 n0 = make_float3(F[F_N0][s], F[F_N0 + 1][s], F[F_N0 + 2][s]);
+          float3 n1 = make_float3(F[F_N1][s], F[F_N1 + 1][s], F[F_N1 + 2][s]);
+          float3 n2 = make_float3(F[F_N2][s], F[F_N2 + 1][s], F[F_N2 + 2][s]);
           bool in = dot3(n0, v) >= 0.0f && dot3(n1, v) >= 0.0f && dot3(n2, v) >= 0.0f;
           if (in) {
             // start/end planes: float32 relative to the apex; within the
             // rounding band of a plane the test is redone in float64 against
             // the triangle's own plane, the form the definition uses
+            float3 ns = make_float3(F[F_NS][s], F[F_NS + 1][s], F[F_NS + 2][s]);
+            float3 ne = make_float3(F[F_NE][s], F[F_NE + 1][s], F[F_NE + 2][s]);
             float band = 1e-4f + 1e-6f * (fabsf(v.x) + fabsf(v.y) + fabsf(v.z));
-            float fs = dot3(ns, v) - ws, fe = dot3(ne, v) - we;
+            float fs = dot3(ns, v) - F[F_NS + 3][s], fe = dot3(ne, v) - F[F_NE + 3][s];
+            int s_slot = __float_as_int(F[F_SLOTS][s]), e_slot = __float_as_int(F[F_SLOTS + 1][s]);
             if (fabsf(fs) <= band && s_slot >= 0) fs = (float)plane_side64(a, s_slot, ns, m);
             if (fabsf(fe) <= band && e_slot >= 0) fe = (float)plane_side64(a, e_slot, ne, m);
             in = fs > 0.0f && fe >= 0.0f;
@@ -644,9 +731,9 @@ __global__ void __launch_bounds__(256) k_scatter(ScatterArgs a) {
 #pragma unroll
             for (int b = 0; b < kMaxBands; b++) {
               if (b < nb) {
-                float c = P[b] * gf;
-                if (a.has_alpha) c *= exp2f(a.alpha_log2[b] * dist);
-                atomicAdd(e + b, (double)c);
+                float cval = F[F_P + b][s] * gf;
+                if (a.has_alpha) cval *= exp2f(a.alpha_log2[b] * dist);
+                atomicAdd(e + b, (double)cval);
               }
             }
             atomicAdd(&a.count[mi], 1);
@@ -655,6 +742,7 @@ __global__ void __launch_bounds__(256) k_scatter(ScatterArgs a) {
         }
       }
     }
+    __syncwarp();
   }
   for (int o = 16; o > 0; o >>= 1) {
     n_cand += __shfl_xor_sync(0xffffffffu, n_cand, o);
@@ -667,7 +755,11 @@ __global__ void __launch_bounds__(256) k_scatter(ScatterArgs a) {
 }
 
 cudaError_t launch_scatter(cudaStream_t st, const ScatterArgs &a, int n_sm) {
-  k_scatter<<<n_sm * 8, 256, 0, st>>>(a);
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter, 32 * kScatterWarps, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  k_scatter<<<n_sm * per_sm, 32 * kScatterWarps, 0, st>>>(a);
   note_launches(1);
   return cudaGetLastError();
 }
