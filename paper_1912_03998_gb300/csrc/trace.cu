@@ -14,11 +14,14 @@
 //             microphone and adds the beam's intensity with float64 atomics.
 //
 // Precision.  BT_PREC_FP32 carries the whole lineage in float32.
-// BT_PREC_MIXED carries beam directions, apex, ray origin and cone normals in
-// float64 (the image-source chain) and traverses in float32; a triangle whose
-// float32 test is ambiguous (the ray within a relative 1e-4 of an edge) is
-// re-tested in float64, near-equal hit distances are compared in float64, and
-// the chosen hit point is formed in float64.
+// BT_PREC_MIXED carries the axis ray (origin and direction) in float64 from
+// the float64 beam table through every reflection, and traverses in float32;
+// a triangle whose float32 test is ambiguous (the ray within a relative 1e-4
+// of an edge) is re-tested in float64, near-equal hit distances are compared
+// in float64, and the hit point is formed in float64 on the triangle's
+// float64 plane.  Apex and cone normals stay float32: the microphone tests
+// are float32, and the start/end plane decisions near a wall are re-tested in
+// float64 by the scatter.
 #include <stdio.h>
 
 #include <type_traits>
@@ -116,7 +119,11 @@ cudaError_t launch_beam_table(cudaStream_t st, int level, double *table) {
 __device__ __forceinline__ double plane_t64(const DevScene &sc, int slot, double3 od, double3 dd) {
   Plane64 pl = ldg_d4(&sc.planes64[slot]);
   double3 n = make_double3(pl.x, pl.y, pl.z);
-  return (pl.w - dot3(n, od)) / dot3(n, dd);
+  double x = dot3(n, dd);
+  double r = (double)(1.0f / (float)x);
+  r = r * (2.0 - x * r);
+  r = r * (2.0 - x * r);
+  return (pl.w - dot3(n, od)) * r;
 }
 
 // Best hit so far.  In MIXED mode t64 holds the float64 distance when known.
@@ -248,12 +255,17 @@ __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 // Cheap rejection of a segment that cannot reach the microphones' height
 // slab: the cone lies on one side of its apex height when all three edge
-// directions (d_j ~ n_{j-1} x n_j for a counter-clockwise cone) point the same
-// way in z.  Everything else goes to the scatter, which clips the footprint.
+// directions point the same way in z.  Edge j is along n_{j-1} x n_j times
+// the sign of det(n0, n1, n2), which a mirror image flips.  Everything else
+// goes to the scatter, which clips the footprint exactly.
 __device__ __forceinline__ bool may_reach_slab(const Seg &s, const MicGrid &g) {
-  float dz0 = s.n2.x * s.n0.y - s.n2.y * s.n0.x;
-  float dz1 = s.n0.x * s.n1.y - s.n0.y * s.n1.x;
-  float dz2 = s.n1.x * s.n2.y - s.n1.y * s.n2.x;
+  float3 n0 = f3(s.n0), n1 = f3(s.n1), n2 = f3(s.n2);
+  float det = n0.x * (n1.y * n2.z - n1.z * n2.y) + n0.y * (n1.z * n2.x - n1.x * n2.z) +
+              n0.z * (n1.x * n2.y - n1.y * n2.x);
+  float sg = det >= 0.0f ? 1.0f : -1.0f;
+  float dz0 = sg * (n2.x * n0.y - n2.y * n0.x);
+  float dz1 = sg * (n0.x * n1.y - n0.y * n1.x);
+  float dz2 = sg * (n1.x * n2.y - n1.y * n2.x);
   float az = (float)s.az, m = 1e-3f;
   if (dz0 < 0.0f && dz1 < 0.0f && dz2 < 0.0f && az < g.zlo - m) return false;
   if (dz0 > 0.0f && dz1 > 0.0f && dz2 > 0.0f && az > g.zhi + m) return false;
@@ -284,15 +296,17 @@ __device__ __forceinline__ void emit_segment(const TraceArgs &a, const Seg &s, b
 }
 
 // Lineage state of one thread, kept in shared memory (one column per
-// thread) so that it does not hold registers across the traversal.
+// thread) so that it does not hold registers across the traversal.  The ray
+// (origin, direction) is float64 in MIXED mode; apex, cone normals, band
+// power and start plane are float32 in both modes.
 constexpr int kTraceThreads = 128;
-template <typename T>
+template <typename TR>
 struct LineageSmem {
-  T a[3][kTraceThreads];   // apex (source or image source)
-  T n[9][kTraceThreads];   // cone-face normals
-  T od[6][kTraceThreads];  // ray origin and direction
-  float p[kMaxBands][kTraceThreads];  // band power W_b prod(r_b)
-  float st[4][kTraceThreads];         // start plane (relative to the apex)
+  float a[3][kTraceThreads];           // apex (source or image source)
+  float n[9][kTraceThreads];           // cone-face normals
+  TR od[6][kTraceThreads];             // ray origin and direction
+  float p[kMaxBands][kTraceThreads];   // band power W_b prod(r_b)
+  float st[4][kTraceThreads];          // start plane (relative to the apex)
 };
 
 template <typename T>
@@ -310,14 +324,23 @@ __device__ __forceinline__ void sts3(T (*arr)[kTraceThreads], int row, int t, V 
   arr[row + 2][t] = (T)v.z;
 }
 
+// Reciprocal in float64 from a float32 seed and two Newton steps (relative
+// error ~1e-15): cheaper than a float64 division on the slow FP64 pipe.
+__device__ __forceinline__ double rcp64(double x) {
+  double r = (double)(1.0f / (float)x);
+  r = r * (2.0 - x * r);
+  r = r * (2.0 - x * r);
+  return r;
+}
+
 // Persistent warps: every lane works on one lineage at a time and takes the
 // next one from a global counter as soon as its lineage ends, so a warp stays
 // full until the batch runs out (warp-vote refill of finished lanes).
 template <bool kMixed, bool kCount>
 __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
-  using T = typename std::conditional<kMixed, double, float>::type;
-  using V = typename Vec3<T>::type;
-  __shared__ LineageSmem<T> sm;
+  using TR = typename std::conditional<kMixed, double, float>::type;
+  using VR = typename Vec3<TR>::type;
+  __shared__ LineageSmem<TR> sm;
   const int t = threadIdx.x;
   const unsigned lane = lane_id();
   const MicGrid g = *a.grid;
@@ -325,7 +348,8 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
   unsigned long long n_seg = 0, n_hit = 0, n_esc = 0, n_emit = 0, n_nodes = 0, n_tris = 0;
   int64_t lin = -1;
   int k = 0, start_slot = -1;
-  T dns = 0;
+  float dns = 0.0f;
+  double dns64 = 0.0;
   bool done = false;
   while (true) {
     // refill lanes whose lineage ended
@@ -341,24 +365,27 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
         if (mine < a.lineage_end) {
           lin = mine;
           int64_t si = lin / a.n_beams, bi = lin - si * a.n_beams;
-          V n0, n1, n2, D;
+          float3 n0, n1, n2;
+          VR D;
           if (kMixed) {
+            // float64 table: normals rounded to float32 (rounding keeps
+            // neighbours' shared normals exactly opposite), float64 axis
             const double *bt = a.beam_table + 12 * bi;
-            n0.x = __ldg(bt + 0); n0.y = __ldg(bt + 1); n0.z = __ldg(bt + 2);
-            n1.x = __ldg(bt + 3); n1.y = __ldg(bt + 4); n1.z = __ldg(bt + 5);
-            n2.x = __ldg(bt + 6); n2.y = __ldg(bt + 7); n2.z = __ldg(bt + 8);
+            n0 = make_float3((float)__ldg(bt + 0), (float)__ldg(bt + 1), (float)__ldg(bt + 2));
+            n1 = make_float3((float)__ldg(bt + 3), (float)__ldg(bt + 4), (float)__ldg(bt + 5));
+            n2 = make_float3((float)__ldg(bt + 6), (float)__ldg(bt + 7), (float)__ldg(bt + 8));
             D.x = __ldg(bt + 9); D.y = __ldg(bt + 10); D.z = __ldg(bt + 11);
           } else {
-            V d0, d1, d2;
-            beam_dirs<T>(a.level, bi, d0, d1, d2);
+            float3 d0, d1, d2;
+            beam_dirs<float>(a.level, bi, d0, d1, d2);
             n0 = cross_exact(d0, d1);
             n1 = cross_exact(d1, d2);
             n2 = cross_exact(d2, d0);
-            D = normalize3((d0 + d1) + d2);
+            float3 df = normalize3((d0 + d1) + d2);
+            D.x = df.x; D.y = df.y; D.z = df.z;
           }
           float4 s4 = __ldg(&a.src[si]);
-          V A;
-          A.x = s4.x; A.y = s4.y; A.z = s4.z;
+          float3 A = make_float3(s4.x, s4.y, s4.z);
           sts3(sm.a, 0, t, A);
           sts3(sm.n, 0, t, n0);
           sts3(sm.n, 3, t, n1);
@@ -370,7 +397,8 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
           sm.st[0][t] = 0.0f; sm.st[1][t] = 0.0f; sm.st[2][t] = 0.0f; sm.st[3][t] = -kInf;
           k = 0;
           start_slot = -1;
-          dns = 0;
+          dns = 0.0f;
+          dns64 = 0.0;
         } else {
           done = true;
         }
@@ -381,40 +409,26 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
     // ---- one segment of this lane's lineage
     Ray r;
     {
-      V O = lds3(sm.od, 0, t), D = lds3(sm.od, 3, t);
+      VR O = lds3(sm.od, 0, t), D = lds3(sm.od, 3, t);
       r = make_ray(make_float3((float)O.x, (float)O.y, (float)O.z), make_float3((float)D.x, (float)D.y, (float)D.z),
-                   a.t_eps, (float)dns);
+                   a.t_eps, dns);
     }
     Best best;
     int slot = closest_hit<kMixed, kCount>(a.sc, r, kMixed ? (const double *)&sm.od[0][t] : nullptr, kTraceThreads,
-                                           (double)dns, best, &a.ctr->error, n_nodes, n_tris);
+                                           dns64, best, &a.ctr->error, n_nodes, n_tris);
     n_seg++;
-    V O = lds3(sm.od, 0, t), D = lds3(sm.od, 3, t);
-    V A = lds3(sm.a, 0, t);
+    float3 A = lds3(sm.a, 0, t);
     float4 end = make_float4(0.0f, 0.0f, 0.0f, -kInf);
-    V pn;
-    pn.x = 0; pn.y = 0; pn.z = 0;
     float4 v0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    T th = 0;
+    float4 plf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (slot >= 0) {
       n_hit++;
       v0 = __ldg(&a.sc.tris[slot].v0);
-      if (kMixed) {
-        // float64 plane of the hit triangle and float64 hit distance
-        Plane64 p64 = ldg_d4(&a.sc.planes64[slot]);
-        pn.x = (T)p64.x; pn.y = (T)p64.y; pn.z = (T)p64.z;
-        th = (T)(best.has64 ? best.t64
-                            : plane_t64(a.sc, slot, make_double3(O.x, O.y, O.z), make_double3(D.x, D.y, D.z)));
-      } else {
-        float4 pl = __ldg(&a.sc.planes[slot]);
-        pn.x = (T)pl.x; pn.y = (T)pl.y; pn.z = (T)pl.z;
-        th = (T)best.t;
-      }
+      plf = __ldg(&a.sc.planes[slot]);
       // end plane on the incident side, offset relative to the apex
-      V en = dot3(pn, D) < (T)0 ? pn : pn * (T)-1;
-      V pv0;
-      pv0.x = v0.x; pv0.y = v0.y; pv0.z = v0.z;
-      end = plane4(en, dot3(en, pv0 - A));
+      float3 pn = f3(plf);
+      float3 en = dot3(pn, r.d) < 0.0f ? pn : pn * -1.0f;
+      end = make_float4(en.x, en.y, en.z, dot3(en, f3(v0) - A));
     } else {
       n_esc++;
     }
@@ -423,9 +437,9 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
       s.ax = (double)A.x;
       s.ay = (double)A.y;
       s.az = (double)A.z;
-      s.n0 = make_float4((float)sm.n[0][t], (float)sm.n[1][t], (float)sm.n[2][t], __int_as_float(start_slot));
-      s.n1 = make_float4((float)sm.n[3][t], (float)sm.n[4][t], (float)sm.n[5][t], __int_as_float(slot));
-      s.n2 = make_float4((float)sm.n[6][t], (float)sm.n[7][t], (float)sm.n[8][t], __int_as_float(k));
+      s.n0 = make_float4(sm.n[0][t], sm.n[1][t], sm.n[2][t], __int_as_float(start_slot));
+      s.n1 = make_float4(sm.n[3][t], sm.n[4][t], sm.n[5][t], __int_as_float(slot));
+      s.n2 = make_float4(sm.n[6][t], sm.n[7][t], sm.n[8][t], __int_as_float(k));
       s.start = make_float4(sm.st[0][t], sm.st[1][t], sm.st[2][t], sm.st[3][t]);
       s.end = end;
       s.p03 = make_float4(sm.p[0][t], sm.p[1][t], sm.p[2][t], sm.p[3][t]);
@@ -436,8 +450,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
     }
     bool ends = slot < 0 || k == a.max_order;
     if (!ends) {
-      // Image source: mirror the apex, the cone and the axis in the hit
-      // plane; the reflected beam starts on that plane and loses energy.
+      // energy lost at the reflection
       int mat = __float_as_int(v0.w);
       float wmax = 0.0f;
 #pragma unroll
@@ -450,23 +463,45 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
       if (a.energy_threshold > 0.0f && wmax < a.energy_threshold) ends = true;
     }
     if (!ends) {
-      V pv0;
-      pv0.x = v0.x; pv0.y = v0.y; pv0.z = v0.z;
-      V H = O + D * th;
-      A = A - pn * ((T)2 * dot3(A - pv0, pn));
+      // Image source: mirror the apex, the cone and the axis in the hit
+      // plane; the reflected beam starts at the hit point on that plane.
+      float3 pn = f3(plf), pv0 = f3(v0);
+      A = A - pn * (2.0f * dot3(A - pv0, pn));
 #pragma unroll
       for (int j = 0; j < 3; j++) {
-        V nj = lds3(sm.n, 3 * j, t);
-        sts3(sm.n, 3 * j, t, nj - pn * ((T)2 * dot3(nj, pn)));
+        float3 nj = lds3(sm.n, 3 * j, t);
+        sts3(sm.n, 3 * j, t, nj - pn * (2.0f * dot3(nj, pn)));
       }
-      D = D - pn * ((T)2 * dot3(D, pn));
       sts3(sm.a, 0, t, A);
+      VR O = lds3(sm.od, 0, t), D = lds3(sm.od, 3, t);
+      VR H, Dn;
+      if (kMixed) {
+        // float64 ray: hit distance to the triangle's float64 plane, mirror
+        Plane64 p64 = ldg_d4(&a.sc.planes64[slot]);
+        double3 n = make_double3(p64.x, p64.y, p64.z);
+        double3 Od = make_double3(O.x, O.y, O.z), Dd = make_double3(D.x, D.y, D.z);
+        double th = best.has64 ? best.t64 : (p64.w - dot3(n, Od)) * rcp64(dot3(n, Dd));
+        double3 h = Od + Dd * th;
+        double3 dn = Dd - n * (2.0 * dot3(Dd, n));
+        H.x = h.x; H.y = h.y; H.z = h.z;
+        Dn.x = dn.x; Dn.y = dn.y; Dn.z = dn.z;
+        dns64 = fabs(dot3(n, dn));
+        dns = (float)dns64;
+      } else {
+        float3 Of = make_float3((float)O.x, (float)O.y, (float)O.z), Df = make_float3((float)D.x, (float)D.y, (float)D.z);
+        float3 h = Of + Df * best.t;
+        float3 dn = Df - pn * (2.0f * dot3(Df, pn));
+        H.x = h.x; H.y = h.y; H.z = h.z;
+        Dn.x = dn.x; Dn.y = dn.y; Dn.z = dn.z;
+        dns = fabsf(dot3(pn, dn));
+        dns64 = 0.0;
+      }
       sts3(sm.od, 0, t, H);
-      sts3(sm.od, 3, t, D);
-      V sn = dot3(pn, D) > (T)0 ? pn : pn * (T)-1;
-      float4 st4 = plane4(sn, dot3(sn, pv0 - A));
-      sm.st[0][t] = st4.x; sm.st[1][t] = st4.y; sm.st[2][t] = st4.z; sm.st[3][t] = st4.w;
-      dns = dot3(sn, D);
+      sts3(sm.od, 3, t, Dn);
+      float3 dnf = make_float3((float)Dn.x, (float)Dn.y, (float)Dn.z);
+      float3 sn = dot3(pn, dnf) > 0.0f ? pn : pn * -1.0f;
+      float sw = dot3(sn, pv0 - A);
+      sm.st[0][t] = sn.x; sm.st[1][t] = sn.y; sm.st[2][t] = sn.z; sm.st[3][t] = sw;
       start_slot = slot;
       k++;
     } else {
