@@ -34,7 +34,7 @@ struct SceneState {
   int n_mat = 0, n_bands = 0;
   int root = -1;
   float box[6] = {0, 0, 0, 0, 0, 0};
-  DevBuf nodes, tris, planes, planes64, refl;
+  DevBuf nodes, tris, planes, planes64, planes_df, refl;
   // sources
   bool has_src = false;
   int64_t n_src = 0;
@@ -61,7 +61,7 @@ struct bt_ctx {
   SceneState sc[BT_MAX_SCENES];
   char err[512] = {0};
   DevBuf scratch, stage_a, stage_b, stage_c, segs;
-  DevBuf beam_table;       // float64 cone normals + axis per beam of one icosahedron level
+  DevBuf beam_table;       // cone normals + axis per beam of one icosahedron level, float pairs
   int beam_table_level = -1;
   bt::Counters *d_ctr = nullptr;
   bt::Counters *h_ctr = nullptr;  // pinned
@@ -149,7 +149,7 @@ void release(DevBuf &b) {
 
 // Scene buffers go back to the context's pool (freed by bt_destroy).
 void release_scene(bt_ctx *c, SceneState &s) {
-  DevBuf *all[] = {&s.nodes, &s.tris, &s.planes, &s.planes64, &s.refl, &s.src, &s.power, &s.mics, &s.cell_start,
+  DevBuf *all[] = {&s.nodes, &s.tris, &s.planes, &s.planes64, &s.planes_df, &s.refl, &s.src, &s.power, &s.mics, &s.cell_start,
                    &s.grid, &s.energy, &s.count, &s.out_level, &s.out_int, &s.out_cnt};
   for (DevBuf *b : all)
     if (b->p) c->pool.push_back(*b);
@@ -173,6 +173,7 @@ bt::DevScene dev_scene(const SceneState &s) {
   d.tris = (const bt::Tri *)s.tris.p;
   d.planes = (const bt::Plane *)s.planes.p;
   d.planes64 = (const bt::Plane64 *)s.planes64.p;
+  d.planes_df = (const bt::PlaneDF *)s.planes_df.p;
   d.refl = (const float *)s.refl.p;
   d.n_mat = s.n_mat;
   d.n_bands = s.n_bands;
@@ -338,6 +339,7 @@ BT_API int bt_load_scene(bt_ctx *c, const float *verts, int64_t n_verts, const i
     if ((rc = ensure(c, s.tris, sizeof(bt::Tri) * (size_t)n_tris))) break;
     if ((rc = ensure(c, s.planes, sizeof(bt::Plane) * (size_t)n_tris))) break;
     if ((rc = ensure(c, s.planes64, sizeof(bt::Plane64) * (size_t)n_tris))) break;
+    if ((rc = ensure(c, s.planes_df, sizeof(bt::PlaneDF) * (size_t)n_tris))) break;
     if ((rc = ensure(c, s.refl, sizeof(float) * n_materials * n_bands))) break;
   } while (0);
   if (rc != BT_OK) { release_scene(c, s); return rc; }
@@ -371,8 +373,8 @@ BT_API int bt_load_scene(bt_ctx *c, const float *verts, int64_t n_verts, const i
   }
   CKS(bt::build_scene(st, (const float *)c->stage_a.p, (const int32_t *)c->stage_b.p, n_tris,
                       (const uint8_t *)c->stage_c.p, (bt::Node *)s.nodes.p, (bt::Tri *)s.tris.p,
-                      (bt::Plane *)s.planes.p, (bt::Plane64 *)s.planes64.p, c->scratch.p, c->scratch.cap, box,
-                      &c->d_ctr->error));
+                      (bt::Plane *)s.planes.p, (bt::Plane64 *)s.planes64.p, (bt::PlaneDF *)s.planes_df.p,
+                      c->scratch.p, c->scratch.cap, box, &c->d_ctr->error));
   CKS(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(bt::Counters), cudaMemcpyDeviceToHost, st));
   CKS(cudaStreamSynchronize(st));
 #undef CKS
@@ -528,16 +530,16 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   ta.mixed = p->precision == BT_PREC_MIXED ? 1 : 0;
   if (ta.mixed && total > 0) {
     if (c->beam_table_level != s->level) {
-      TRY(ensure(c, c->beam_table, sizeof(double) * 12 * (size_t)n_beams));
-      CK(bt::launch_beam_table(st, s->level, (double *)c->beam_table.p));
+      TRY(ensure(c, c->beam_table, sizeof(float) * 24 * (size_t)n_beams));
+      CK(bt::launch_beam_table(st, s->level, (float *)c->beam_table.p));
       c->beam_table_level = s->level;
     }
-    ta.beam_table = (const double *)c->beam_table.p;
+    ta.beam_table = (const float *)c->beam_table.p;
   }
   bt::ScatterArgs sa;
   memset(&sa, 0, sizeof(sa));
   sa.tris = ta.sc.tris;
-  sa.planes64 = ta.sc.planes64;
+  sa.planes_df = ta.sc.planes_df;
   sa.segs = ta.segs;
   sa.seg_count = c->d_seg_count;
   sa.seg_capacity = cap;

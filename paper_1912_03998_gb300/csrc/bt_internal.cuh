@@ -35,6 +35,11 @@ using Plane = float4;
 struct __align__(32) Plane64 {
   double x, y, z, w;
 };
+// The same as float pairs (hi + lo, see double-float below): hi = (n.hi, w.hi),
+// lo = (n.lo, w.lo).
+struct __align__(16) PlaneDF {
+  float4 hi, lo;
+};
 
 struct DevScene {
   int64_t n_tris;
@@ -43,6 +48,7 @@ struct DevScene {
   const Tri *tris;       // n_tris, leaf order
   const Plane *planes;   // n_tris, leaf order
   const Plane64 *planes64;  // n_tris, leaf order: float64 unit normal and n . v0
+  const PlaneDF *planes_df; // n_tris, leaf order: the float64 plane split into float pairs
   const float *refl;     // [n_mat][n_bands]
   int n_mat, n_bands;
   float lo[3], hi[3];    // scene box
@@ -57,23 +63,26 @@ struct MicGrid {
   int pad;
 };
 
-// One beam segment handed from the trace kernel to the scatter kernel, 144 B.
-// With v = m - apex (formed in float64, then rounded), microphone m is inside
-// when n_j . v >= 0 (j = 0,1,2), start.xyz . v - start.w > 0 and
+// One beam segment handed from the trace kernel to the scatter kernel, 192 B.
+// The apex and the cone normals are float pairs (hi + lo; lo is zero in
+// BT_PREC_FP32).  With v = m - apex, microphone m is inside when
+// n_j . v >= 0 (j = 0,1,2), start.xyz . v - start.w > 0 and
 // end.xyz . v - end.w >= 0; plane offsets are relative to the apex.  A
 // missing plane is (0, 0, 0, -inf).
 struct __align__(16) Seg {
-  double ax, ay, az;  // apex (source or image source), float64
-  int cy0, cy1;       // footprint rows on the microphone grid
-  float4 n0;          // cone-face normal 0; w: leaf slot of the start plane's triangle (int bits, -1 none)
-  float4 n1;          // w: leaf slot of the end plane's triangle (int bits, -1 none)
-  float4 n2;          // w: reflection order (int bits)
+  float ahi[3], alo[3];  // apex (source or image source)
+  int cy0, cy1;          // footprint rows on the microphone grid (set by the scatter)
+  float4 n0;             // cone-face normal 0 (hi); w: leaf slot of the start plane's triangle (-1 none)
+  float4 n1;             // w: leaf slot of the end plane's triangle (-1 none)
+  float4 n2;             // w: reflection order (int bits)
   float4 start;
   float4 end;
-  float4 p03;         // per-band power W_b * prod(r_b), bands 0..3
-  float4 p47;         // bands 4..7
+  float4 p03;            // per-band power W_b * prod(r_b), bands 0..3
+  float4 p47;            // bands 4..7
+  float nlo[9];          // lo parts of the three cone normals
+  float pad[3];
 };
-static_assert(sizeof(Seg) == 144, "segment record layout");
+static_assert(sizeof(Seg) == 192, "segment record layout");
 
 // Device counters of one trace, accumulated with atomics.
 struct Counters {
@@ -105,12 +114,12 @@ struct TraceArgs {
   Counters *ctr;
   int count_work;
   int mixed;  // 1: float64 image-source chain (BT_PREC_MIXED), 0: float32 (BT_PREC_FP32)
-  const double *beam_table;  // MIXED: per beam 3 cone normals + axis, float64 [n_beams][12]
+  const float *beam_table;   // MIXED: per beam 3 cone normals + axis as float pairs: [n_beams][12] hi, then lo
 };
 
 struct ScatterArgs {
   const Tri *tris;          // leaf order (start/end plane vertices)
-  const Plane64 *planes64;  // leaf order
+  const PlaneDF *planes_df; // leaf order
   const Seg *segs;
   const unsigned long long *seg_count;
   unsigned long long seg_capacity;
@@ -280,6 +289,80 @@ __device__ __forceinline__ bool slab(const Ray &r, float lox, float hix, float l
   return tn <= fminf(tf, tmax);
 }
 
+// ------------------------------------------------------------ double-float
+// Unevaluated sums hi + lo of two float32 (about 48 significant bits), built
+// from the error-free transformations TwoSum (Knuth), Fast2Sum (Dekker) and
+// FMA-based TwoProd, in the arrangement of the published double-double
+// algorithms (Hida, Li & Bailey).  GB300 runs float32 some 64 times faster
+// than float64, so the image-source chain uses these pairs instead of double.
+// Every step is written with explicit round-to-nearest intrinsics so the
+// compiler cannot contract or reassociate it.
+struct df {
+  float hi, lo;
+};
+struct df3 {
+  df x, y, z;
+};
+
+__device__ __forceinline__ df mkdf(float a) { return df{a, 0.0f}; }
+__device__ __forceinline__ df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return df{s, e};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // needs |a| >= |b| (or a == 0)
+  float s = __fadd_rn(a, b);
+  return df{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return df{p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi), t = two_sum(a.lo, b.lo);
+  s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df df_mul(df a, df b) {
+  df p = two_prod(a.hi, b.hi);
+  return fast_two_sum(p.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo)));
+}
+__device__ __forceinline__ df df_mulf(df a, float b) {
+  df p = two_prod(a.hi, b);
+  return fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+__device__ __forceinline__ df df_div(df a, df b) {
+  float q1 = __fdiv_rn(a.hi, b.hi);
+  df r = df_sub(a, df_mulf(b, q1));
+  float q2 = __fdiv_rn(r.hi, b.hi);
+  r = df_sub(r, df_mulf(b, q2));
+  float q3 = __fdiv_rn(r.hi, b.hi);
+  df q = fast_two_sum(q1, q2);
+  return df_add(q, mkdf(q3));
+}
+__device__ __forceinline__ df3 mkdf3(float3 v) { return df3{mkdf(v.x), mkdf(v.y), mkdf(v.z)}; }
+__device__ __forceinline__ df3 df3_add(df3 a, df3 b) { return df3{df_add(a.x, b.x), df_add(a.y, b.y), df_add(a.z, b.z)}; }
+__device__ __forceinline__ df3 df3_sub(df3 a, df3 b) { return df3{df_sub(a.x, b.x), df_sub(a.y, b.y), df_sub(a.z, b.z)}; }
+__device__ __forceinline__ df3 df3_scale(df3 a, df s) { return df3{df_mul(a.x, s), df_mul(a.y, s), df_mul(a.z, s)}; }
+__device__ __forceinline__ df df3_dot(df3 a, df3 b) {
+  return df_add(df_add(df_mul(a.x, b.x), df_mul(a.y, b.y)), df_mul(a.z, b.z));
+}
+// mirror of a direction (or plane normal) v in the plane with unit normal n
+__device__ __forceinline__ df3 df3_mirror(df3 v, df3 n) {
+  df k = df3_dot(v, n);
+  k = df{2.0f * k.hi, 2.0f * k.lo};
+  return df3_sub(v, df3_scale(n, k));
+}
+__device__ __forceinline__ float3 df3_hi(df3 a) { return make_float3(a.x.hi, a.y.hi, a.z.hi); }
+__device__ __forceinline__ double df_to_d(df a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ df d_to_df(double x) {
+  float hi = (float)x;
+  return df{hi, (float)(x - (double)hi)};
+}
+
 // ------------------------------------------------------- footprint polygon
 // Conservative xy footprint of a segment on the microphone slab: each 3D
 // half-space a.m >= b becomes, over z in [zlo, zhi], the weaker half-plane
@@ -330,7 +413,7 @@ __device__ __forceinline__ bool seg_footprint(const Seg &s, const MicGrid &g, Po
   p.x[1] = X1; p.y[1] = Y0;
   p.x[2] = X1; p.y[2] = Y1;
   p.x[3] = X0; p.y[3] = Y1;
-  float3 A = make_float3((float)s.ax, (float)s.ay, (float)s.az);
+  float3 A = make_float3(s.ahi[0], s.ahi[1], s.ahi[2]);
   float3 n0 = f3(s.n0), n1 = f3(s.n1), n2 = f3(s.n2);
   float3 ns = f3(s.start), ne = f3(s.end);
   if (!poly_halfspace(p, n0, dot3(n0, A), g)) return false;
@@ -375,9 +458,9 @@ cudaError_t validate_scene(cudaStream_t st, const float *d_verts, int64_t n_vert
                            float *d_box /*lo xyz, hi xyz*/, int *d_error);
 cudaError_t build_scene(cudaStream_t st, const float *d_verts, const int32_t *d_tris, int64_t n_tris,
                         const uint8_t *d_mat, Node *d_nodes, Tri *d_tris_out, Plane *d_planes,
-                        Plane64 *d_planes64, void *d_scratch, size_t scratch_bytes, const float *d_box,
-                        int *d_error);
-cudaError_t launch_beam_table(cudaStream_t st, int level, double *table);
+                        Plane64 *d_planes64, PlaneDF *d_planes_df, void *d_scratch, size_t scratch_bytes,
+                        const float *d_box, int *d_error);
+cudaError_t launch_beam_table(cudaStream_t st, int level, float *table);
 size_t build_scene_scratch_bytes(int64_t n_tris);
 cudaError_t build_mics(cudaStream_t st, const float *d_pos, int64_t n_m, int side, MicGrid *d_grid,
                        float4 *d_sorted, int *d_cell_start, void *d_scratch, size_t scratch_bytes,

@@ -275,7 +275,8 @@ __global__ void k_lbvh_topology(const uint32_t *keys, int n, Node *nodes, int *l
 
 // Triangles in leaf order with their planes; the normal is formed in double.
 __global__ void k_pack_tris(const float *verts, const int32_t *tris, const uint8_t *mat,
-                            const uint32_t *order, int64_t n, Tri *out, Plane *planes, Plane64 *planes64) {
+                            const uint32_t *order, int64_t n, Tri *out, Plane *planes, Plane64 *planes64,
+                            PlaneDF *planes_df) {
   int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
   int64_t t = order[s];
@@ -298,6 +299,9 @@ __global__ void k_pack_tris(const float *verts, const int32_t *tris, const uint8
   planes64[s].y = ny;
   planes64[s].z = nz;
   planes64[s].w = w;
+  float hx = (float)nx, hy = (float)ny, hz = (float)nz, hw = (float)w;
+  planes_df[s].hi = make_float4(hx, hy, hz, hw);
+  planes_df[s].lo = make_float4((float)(nx - hx), (float)(ny - hy), (float)(nz - hz), (float)(w - hw));
 }
 
 __device__ __forceinline__ void tri_box(const Tri &t, float lo[3], float hi[3]) {
@@ -383,8 +387,8 @@ cudaError_t validate_scene(cudaStream_t st, const float *d_verts, int64_t n_vert
 // index and material is then in range and every coordinate finite.
 cudaError_t build_scene(cudaStream_t st, const float *d_verts, const int32_t *d_tris, int64_t n_tris,
                         const uint8_t *d_mat, Node *d_nodes, Tri *d_tris_out, Plane *d_planes,
-                        Plane64 *d_planes64, void *d_scratch, size_t scratch_bytes, const float *d_box,
-                        int *d_error) {
+                        Plane64 *d_planes64, PlaneDF *d_planes_df, void *d_scratch, size_t scratch_bytes,
+                        const float *d_box, int *d_error) {
   if (n_tris == 0) return cudaSuccess;
   if (scratch_bytes < build_scene_scratch_bytes(n_tris)) return cudaErrorInvalidValue;
   int n = (int)n_tris;
@@ -405,7 +409,7 @@ cudaError_t build_scene(cudaStream_t st, const float *d_verts, const int32_t *d_
   cudaError_t e = radix_sort(st, keys, vals, kalt, valt, hist, n, 31);
   if (e != cudaSuccess) return e;
   k_pack_tris<<<blocks, threads, 0, st>>>(d_verts, d_tris, d_mat, vals, n_tris, d_tris_out, d_planes,
-                                         d_planes64);
+                                         d_planes64, d_planes_df);
   note_launches(1);
   if (n >= 2) {
     k_lbvh_topology<<<(n - 1 + threads - 1) / threads, threads, 0, st>>>(keys, n, d_nodes, leaf_parent);

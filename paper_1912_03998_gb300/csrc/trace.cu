@@ -3,25 +3,26 @@
 // microphone-in-beam test and per-band energy scatter, and level readout.
 //
 // Two kernels per batch of beam lineages:
-//   k_trace   one thread per lineage (source, icosahedron face): for orders
-//             0..K it casts the beam's axis ray through the BVH, writes the
-//             segment (apex, cone planes, start/end planes, band power) if its
-//             footprint overlaps the microphone grid, and reflects the beam
-//             about the hit triangle's plane (image source).
-//   k_scatter one warp per segment: the warp walks the cell rows under the
-//             segment's footprint 32 rows at a time, flattens the microphone
-//             runs of those rows with a warp scan, tests every candidate
-//             microphone and adds the beam's intensity with float64 atomics.
+//   k_trace   persistent warps, one lineage (source, icosahedron face) per
+//             lane: for orders 0..K it casts the beam's axis ray through the
+//             BVH, writes the segment (apex, cone planes, start/end planes,
+//             band power) unless it cannot reach the microphones' height, and
+//             reflects the beam about the hit triangle's plane (image source);
+//             a lane whose lineage ends takes the next one at once.
+//   k_scatter each lane of a warp builds the footprint of one segment; the
+//             warp then flattens the (segment, cell row) pairs and the
+//             microphone runs of those rows, tests every candidate microphone
+//             and adds the beam's intensity with float64 atomics.
 //
-// Precision.  BT_PREC_FP32 carries the whole lineage in float32.
-// BT_PREC_MIXED carries the axis ray (origin and direction) in float64 from
-// the float64 beam table through every reflection, and traverses in float32;
-// a triangle whose float32 test is ambiguous (the ray within a relative 1e-4
-// of an edge) is re-tested in float64, near-equal hit distances are compared
-// in float64, and the hit point is formed in float64 on the triangle's
-// float64 plane.  Apex and cone normals stay float32: the microphone tests
-// are float32, and the start/end plane decisions near a wall are re-tested in
-// float64 by the scatter.
+// Precision.  BT_PREC_FP32 carries the lineage in float32.  BT_PREC_MIXED
+// carries the image-source chain -- apex, cone normals, ray origin and
+// direction -- as float pairs (about 48 bits, on the float32 pipe) from a
+// float64 beam table through every reflection, on the triangles' float64
+// planes.  Traversal is float32; a triangle whose float32 test is ambiguous
+// (the ray within a relative 1e-4 of an edge) is re-tested in float64, near-
+// equal hit distances are compared in float64.  Microphone tests are float32
+// and re-tested with float pairs when a microphone lies within the rounding
+// band of a cone or start/end plane.
 #include <stdio.h>
 
 #include <type_traits>
@@ -91,39 +92,39 @@ __device__ __forceinline__ void beam_dirs(int level, int64_t i, typename Vec3<T>
   }
 }
 
-// Float64 beam table of one icosahedron level: per beam the three cone-face
-// normals d_j x d_{j+1} (formed without FMA, so neighbours share exactly
-// opposite normals) and the unit axis, 12 doubles.
-__global__ void k_beam_table(int level, int64_t n_beams, double *table) {
+// Beam table of one icosahedron level, formed in float64 and stored as float
+// pairs: per beam the three cone-face normals d_j x d_{j+1} (no FMA, so
+// neighbours share exactly opposite normals; the split keeps that) and the
+// unit axis -- 12 hi floats, then 12 lo floats.
+__global__ void k_beam_table(int level, int64_t n_beams, float *table) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n_beams) return;
   double3 d0, d1, d2;
   beam_dirs<double>(level, i, d0, d1, d2);
   double3 v[4] = {cross_exact(d0, d1), cross_exact(d1, d2), cross_exact(d2, d0), normalize3((d0 + d1) + d2)};
-  double *o = table + 12 * i;
+  float *o = table + 24 * i;
   for (int k = 0; k < 4; k++) {
-    o[3 * k] = v[k].x;
-    o[3 * k + 1] = v[k].y;
-    o[3 * k + 2] = v[k].z;
+    double c[3] = {v[k].x, v[k].y, v[k].z};
+    for (int q = 0; q < 3; q++) {
+      df h = d_to_df(c[q]);
+      o[3 * k + q] = h.hi;
+      o[12 + 3 * k + q] = h.lo;
+    }
   }
 }
 
-cudaError_t launch_beam_table(cudaStream_t st, int level, double *table) {
+cudaError_t launch_beam_table(cudaStream_t st, int level, float *table) {
   int64_t n = (int64_t)20 << (2 * level);
   k_beam_table<<<(int)((n + 127) / 128), 128, 0, st>>>(level, n, table);
   note_launches(1);
   return cudaGetLastError();
 }
 
-// Float64 distance along the ray to the plane of leaf slot `slot`.
+// float64 distance along the ray to the plane of leaf slot `slot`.
 __device__ __forceinline__ double plane_t64(const DevScene &sc, int slot, double3 od, double3 dd) {
   Plane64 pl = ldg_d4(&sc.planes64[slot]);
   double3 n = make_double3(pl.x, pl.y, pl.z);
-  double x = dot3(n, dd);
-  double r = (double)(1.0f / (float)x);
-  r = r * (2.0 - x * r);
-  r = r * (2.0 - x * r);
-  return (pl.w - dot3(n, od)) * r;
+  return (pl.w - dot3(n, od)) / dot3(n, dd);
 }
 
 // Best hit so far.  In MIXED mode t64 holds the float64 distance when known.
@@ -134,25 +135,31 @@ struct Best {
   bool has64;
 };
 
+// Ray as float pairs in shared memory: rows 0..5 of `hi` and `lo` hold origin
+// xyz and direction xyz, `stride` floats apart.
+struct RaySrc {
+  const float *hi, *lo;
+  int stride;
+  __device__ __forceinline__ void get(double3 &o, double3 &d) const {
+    o = make_double3((double)hi[0] + lo[0], (double)hi[stride] + lo[stride], (double)hi[2 * stride] + lo[2 * stride]);
+    d = make_double3((double)hi[3 * stride] + lo[3 * stride], (double)hi[4 * stride] + lo[4 * stride],
+                     (double)hi[5 * stride] + lo[5 * stride]);
+  }
+};
+
 // Closest accepted hit of the ray in the BVH; ties in distance go to the
-// lowest original triangle id.  With kMixed, the float64 ray the float32 ray
-// `r` was rounded from is at od[0..5 * stride] (origin xyz, direction xyz,
-// in shared memory), read only on the rare float64 paths.  Returns the leaf
-// slot or -1.
+// lowest original triangle id.  With kMixed, `rs` gives the float-pair ray
+// that the float32 ray `r` rounds, read only on the rare float64 paths.
+// Returns the leaf slot or -1.
 template <bool kMixed, bool kCount>
-__device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, const double *od, int stride,
-                                           double dns64, Best &best, int *err, unsigned long long &n_nodes,
-                                           unsigned long long &n_tris) {
+__device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, RaySrc rs, double dns64, Best &best,
+                                           int *err, unsigned long long &n_nodes, unsigned long long &n_tris) {
   best.t = kInf;
   best.slot = -1;
   best.id = 0x7fffffff;
   best.t64 = 0.0;
   best.has64 = false;
   if (sc.n_tris == 0) return -1;
-  auto ray64 = [&](double3 &o, double3 &d) {
-    o = make_double3(od[0], od[stride], od[2 * stride]);
-    d = make_double3(od[3 * stride], od[4 * stride], od[5 * stride]);
-  };
   // candidate evaluation (one call site, so the code is emitted once)
   auto consider = [&](int slot) {
     if (kCount) n_tris++;
@@ -164,7 +171,7 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, con
     bool has64 = false;
     if (kMixed && amb) {
       double3 o, d;
-      ray64(o, d);
+      rs.get(o, d);
       double tt;
       if (!hit_mt64(o, d, v0, v1, v2, tt)) return;
       if (!(tt > (double)r.t_eps && (dns64 == 0.0 || tt * dns64 > (double)r.t_eps))) return;
@@ -189,7 +196,7 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, con
     }
     if (t > best.t + win) return;
     double3 o, d;
-    ray64(o, d);
+    rs.get(o, d);
     if (!has64) t64 = plane_t64(sc, slot, o, d);
     if (!best.has64) {
       best.t64 = plane_t64(sc, best.slot, o, d);
@@ -258,24 +265,18 @@ __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 // directions point the same way in z.  Edge j is along n_{j-1} x n_j times
 // the sign of det(n0, n1, n2), which a mirror image flips.  Everything else
 // goes to the scatter, which clips the footprint exactly.
-__device__ __forceinline__ bool may_reach_slab(const Seg &s, const MicGrid &g) {
-  float3 n0 = f3(s.n0), n1 = f3(s.n1), n2 = f3(s.n2);
+__device__ __forceinline__ bool may_reach_slab(float3 n0, float3 n1, float3 n2, float az, const MicGrid &g) {
   float det = n0.x * (n1.y * n2.z - n1.z * n2.y) + n0.y * (n1.z * n2.x - n1.x * n2.z) +
               n0.z * (n1.x * n2.y - n1.y * n2.x);
   float sg = det >= 0.0f ? 1.0f : -1.0f;
   float dz0 = sg * (n2.x * n0.y - n2.y * n0.x);
   float dz1 = sg * (n0.x * n1.y - n0.y * n1.x);
   float dz2 = sg * (n1.x * n2.y - n1.y * n2.x);
-  float az = (float)s.az, m = 1e-3f;
+  float m = 1e-3f;
   if (dz0 < 0.0f && dz1 < 0.0f && dz2 < 0.0f && az < g.zlo - m) return false;
   if (dz0 > 0.0f && dz1 > 0.0f && dz2 > 0.0f && az > g.zhi + m) return false;
   return true;
 }
-
-__device__ __forceinline__ float4 plane4(double3 n, double w) {
-  return make_float4((float)n.x, (float)n.y, (float)n.z, (float)w);
-}
-__device__ __forceinline__ float4 plane4(float3 n, float w) { return make_float4(n.x, n.y, n.z, w); }
 
 // Warp-aggregated append of a segment record.
 __device__ __forceinline__ void emit_segment(const TraceArgs &a, const Seg &s, bool emit,
@@ -295,42 +296,48 @@ __device__ __forceinline__ void emit_segment(const TraceArgs &a, const Seg &s, b
   }
 }
 
-// Lineage state of one thread, kept in shared memory (one column per
-// thread) so that it does not hold registers across the traversal.  The ray
-// (origin, direction) is float64 in MIXED mode; apex, cone normals, band
-// power and start plane are float32 in both modes.
+// Lineage state of one thread, in shared memory (one column per thread) so
+// that it holds no registers across the traversal.  Rows: apex 0..2, cone
+// normals 3..11, ray origin 12..14, ray direction 15..17; `lo` holds the low
+// parts of the float pairs (MIXED only).
 constexpr int kTraceThreads = 128;
-template <typename TR>
+constexpr int kRowA = 0, kRowN = 3, kRowO = 12, kRowD = 15, kRows = 18;
+template <bool kMixed>
 struct LineageSmem {
-  float a[3][kTraceThreads];           // apex (source or image source)
-  float n[9][kTraceThreads];           // cone-face normals
-  TR od[6][kTraceThreads];             // ray origin and direction
-  float p[kMaxBands][kTraceThreads];   // band power W_b prod(r_b)
-  float st[4][kTraceThreads];          // start plane (relative to the apex)
+  float hi[kRows][kTraceThreads];
+  float lo[kMixed ? kRows : 1][kTraceThreads];
+  float p[kMaxBands][kTraceThreads];  // band power W_b prod(r_b)
+  float st[4][kTraceThreads];         // start plane (relative to the apex)
 };
 
-template <typename T>
-__device__ __forceinline__ typename Vec3<T>::type lds3(const T (*arr)[kTraceThreads], int row, int t) {
-  typename Vec3<T>::type v;
-  v.x = arr[row][t];
-  v.y = arr[row + 1][t];
-  v.z = arr[row + 2][t];
+template <bool kMixed>
+__device__ __forceinline__ df3 ld_df3(const LineageSmem<kMixed> &sm, int row, int t) {
+  df3 v;
+  v.x = df{sm.hi[row][t], kMixed ? sm.lo[row][t] : 0.0f};
+  v.y = df{sm.hi[row + 1][t], kMixed ? sm.lo[row + 1][t] : 0.0f};
+  v.z = df{sm.hi[row + 2][t], kMixed ? sm.lo[row + 2][t] : 0.0f};
   return v;
 }
-template <typename T, typename V>
-__device__ __forceinline__ void sts3(T (*arr)[kTraceThreads], int row, int t, V v) {
-  arr[row][t] = (T)v.x;
-  arr[row + 1][t] = (T)v.y;
-  arr[row + 2][t] = (T)v.z;
+template <bool kMixed>
+__device__ __forceinline__ void st_df3(LineageSmem<kMixed> &sm, int row, int t, df3 v) {
+  sm.hi[row][t] = v.x.hi;
+  sm.hi[row + 1][t] = v.y.hi;
+  sm.hi[row + 2][t] = v.z.hi;
+  if (kMixed) {
+    sm.lo[row][t] = v.x.lo;
+    sm.lo[row + 1][t] = v.y.lo;
+    sm.lo[row + 2][t] = v.z.lo;
+  }
 }
-
-// Reciprocal in float64 from a float32 seed and two Newton steps (relative
-// error ~1e-15): cheaper than a float64 division on the slow FP64 pipe.
-__device__ __forceinline__ double rcp64(double x) {
-  double r = (double)(1.0f / (float)x);
-  r = r * (2.0 - x * r);
-  r = r * (2.0 - x * r);
-  return r;
+template <bool kMixed>
+__device__ __forceinline__ float3 ld_hi3(const LineageSmem<kMixed> &sm, int row, int t) {
+  return make_float3(sm.hi[row][t], sm.hi[row + 1][t], sm.hi[row + 2][t]);
+}
+template <bool kMixed>
+__device__ __forceinline__ void st_f3(LineageSmem<kMixed> &sm, int row, int t, float3 v) {
+  sm.hi[row][t] = v.x;
+  sm.hi[row + 1][t] = v.y;
+  sm.hi[row + 2][t] = v.z;
 }
 
 // Persistent warps: every lane works on one lineage at a time and takes the
@@ -338,9 +345,7 @@ __device__ __forceinline__ double rcp64(double x) {
 // full until the batch runs out (warp-vote refill of finished lanes).
 template <bool kMixed, bool kCount>
 __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
-  using TR = typename std::conditional<kMixed, double, float>::type;
-  using VR = typename Vec3<TR>::type;
-  __shared__ LineageSmem<TR> sm;
+  __shared__ LineageSmem<kMixed> sm;
   const int t = threadIdx.x;
   const unsigned lane = lane_id();
   const MicGrid g = *a.grid;
@@ -351,6 +356,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
   float dns = 0.0f;
   double dns64 = 0.0;
   bool done = false;
+  const RaySrc rs{&sm.hi[kRowO][t], kMixed ? &sm.lo[kRowO][t] : &sm.hi[kRowO][t], kTraceThreads};
   while (true) {
     // refill lanes whose lineage ended
     bool need = !done && lin < 0;
@@ -365,33 +371,28 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
         if (mine < a.lineage_end) {
           lin = mine;
           int64_t si = lin / a.n_beams, bi = lin - si * a.n_beams;
-          float3 n0, n1, n2;
-          VR D;
+          float4 s4 = __ldg(&a.src[si]);
+          float3 A = make_float3(s4.x, s4.y, s4.z);
           if (kMixed) {
-            // float64 table: normals rounded to float32 (rounding keeps
-            // neighbours' shared normals exactly opposite), float64 axis
-            const double *bt = a.beam_table + 12 * bi;
-            n0 = make_float3((float)__ldg(bt + 0), (float)__ldg(bt + 1), (float)__ldg(bt + 2));
-            n1 = make_float3((float)__ldg(bt + 3), (float)__ldg(bt + 4), (float)__ldg(bt + 5));
-            n2 = make_float3((float)__ldg(bt + 6), (float)__ldg(bt + 7), (float)__ldg(bt + 8));
-            D.x = __ldg(bt + 9); D.y = __ldg(bt + 10); D.z = __ldg(bt + 11);
+            const float *bt = a.beam_table + 24 * bi;
+            for (int q = 0; q < 12; q++) {
+              sm.hi[kRowN + q][t] = __ldg(bt + q);
+              sm.lo[kRowN + q][t] = __ldg(bt + 12 + q);
+            }
+            for (int q = 0; q < 3; q++) {
+              sm.lo[kRowA + q][t] = 0.0f;
+              sm.lo[kRowO + q][t] = 0.0f;
+            }
           } else {
             float3 d0, d1, d2;
             beam_dirs<float>(a.level, bi, d0, d1, d2);
-            n0 = cross_exact(d0, d1);
-            n1 = cross_exact(d1, d2);
-            n2 = cross_exact(d2, d0);
-            float3 df = normalize3((d0 + d1) + d2);
-            D.x = df.x; D.y = df.y; D.z = df.z;
+            st_f3(sm, kRowN, t, cross_exact(d0, d1));
+            st_f3(sm, kRowN + 3, t, cross_exact(d1, d2));
+            st_f3(sm, kRowN + 6, t, cross_exact(d2, d0));
+            st_f3(sm, kRowD, t, normalize3((d0 + d1) + d2));
           }
-          float4 s4 = __ldg(&a.src[si]);
-          float3 A = make_float3(s4.x, s4.y, s4.z);
-          sts3(sm.a, 0, t, A);
-          sts3(sm.n, 0, t, n0);
-          sts3(sm.n, 3, t, n1);
-          sts3(sm.n, 6, t, n2);
-          sts3(sm.od, 0, t, A);
-          sts3(sm.od, 3, t, D);
+          st_f3(sm, kRowA, t, A);
+          st_f3(sm, kRowO, t, A);
 #pragma unroll
           for (int b = 0; b < kMaxBands; b++) sm.p[b][t] = b < nb ? __ldg(&a.power[si * nb + b]) : 0.0f;
           sm.st[0][t] = 0.0f; sm.st[1][t] = 0.0f; sm.st[2][t] = 0.0f; sm.st[3][t] = -kInf;
@@ -407,17 +408,10 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
     if (__all_sync(0xffffffffu, done)) break;
     if (done) continue;
     // ---- one segment of this lane's lineage
-    Ray r;
-    {
-      VR O = lds3(sm.od, 0, t), D = lds3(sm.od, 3, t);
-      r = make_ray(make_float3((float)O.x, (float)O.y, (float)O.z), make_float3((float)D.x, (float)D.y, (float)D.z),
-                   a.t_eps, dns);
-    }
+    const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), a.t_eps, dns);
     Best best;
-    int slot = closest_hit<kMixed, kCount>(a.sc, r, kMixed ? (const double *)&sm.od[0][t] : nullptr, kTraceThreads,
-                                           dns64, best, &a.ctr->error, n_nodes, n_tris);
+    int slot = closest_hit<kMixed, kCount>(a.sc, r, rs, dns64, best, &a.ctr->error, n_nodes, n_tris);
     n_seg++;
-    float3 A = lds3(sm.a, 0, t);
     float4 end = make_float4(0.0f, 0.0f, 0.0f, -kInf);
     float4 v0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float4 plf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -428,25 +422,32 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
       // end plane on the incident side, offset relative to the apex
       float3 pn = f3(plf);
       float3 en = dot3(pn, r.d) < 0.0f ? pn : pn * -1.0f;
-      end = make_float4(en.x, en.y, en.z, dot3(en, f3(v0) - A));
+      float ew;
+      if (kMixed) ew = df3_dot(mkdf3(en), df3_sub(mkdf3(f3(v0)), ld_df3(sm, kRowA, t))).hi;
+      else ew = dot3(en, f3(v0) - ld_hi3(sm, kRowA, t));
+      end = make_float4(en.x, en.y, en.z, ew);
     } else {
       n_esc++;
     }
     {
       Seg s;
-      s.ax = (double)A.x;
-      s.ay = (double)A.y;
-      s.az = (double)A.z;
-      s.n0 = make_float4(sm.n[0][t], sm.n[1][t], sm.n[2][t], __int_as_float(start_slot));
-      s.n1 = make_float4(sm.n[3][t], sm.n[4][t], sm.n[5][t], __int_as_float(slot));
-      s.n2 = make_float4(sm.n[6][t], sm.n[7][t], sm.n[8][t], __int_as_float(k));
+      for (int q = 0; q < 3; q++) {
+        s.ahi[q] = sm.hi[kRowA + q][t];
+        s.alo[q] = kMixed ? sm.lo[kRowA + q][t] : 0.0f;
+      }
+      float3 n0 = ld_hi3(sm, kRowN, t), n1 = ld_hi3(sm, kRowN + 3, t), n2 = ld_hi3(sm, kRowN + 6, t);
+      s.n0 = make_float4(n0.x, n0.y, n0.z, __int_as_float(start_slot));
+      s.n1 = make_float4(n1.x, n1.y, n1.z, __int_as_float(slot));
+      s.n2 = make_float4(n2.x, n2.y, n2.z, __int_as_float(k));
+      for (int q = 0; q < 9; q++) s.nlo[q] = kMixed ? sm.lo[kRowN + q][t] : 0.0f;
+      s.pad[0] = s.pad[1] = s.pad[2] = 0.0f;
       s.start = make_float4(sm.st[0][t], sm.st[1][t], sm.st[2][t], sm.st[3][t]);
       s.end = end;
       s.p03 = make_float4(sm.p[0][t], sm.p[1][t], sm.p[2][t], sm.p[3][t]);
       s.p47 = make_float4(sm.p[4][t], sm.p[5][t], sm.p[6][t], sm.p[7][t]);
       s.cy0 = 0;
       s.cy1 = -1;
-      emit_segment(a, s, g.n_mics > 0 && may_reach_slab(s, g), n_emit);
+      emit_segment(a, s, g.n_mics > 0 && may_reach_slab(n0, n1, n2, s.ahi[2], g), n_emit);
     }
     bool ends = slot < 0 || k == a.max_order;
     if (!ends) {
@@ -466,42 +467,48 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
       // Image source: mirror the apex, the cone and the axis in the hit
       // plane; the reflected beam starts at the hit point on that plane.
       float3 pn = f3(plf), pv0 = f3(v0);
-      A = A - pn * (2.0f * dot3(A - pv0, pn));
-#pragma unroll
-      for (int j = 0; j < 3; j++) {
-        float3 nj = lds3(sm.n, 3 * j, t);
-        sts3(sm.n, 3 * j, t, nj - pn * (2.0f * dot3(nj, pn)));
-      }
-      sts3(sm.a, 0, t, A);
-      VR O = lds3(sm.od, 0, t), D = lds3(sm.od, 3, t);
-      VR H, Dn;
+      float3 Dn;
       if (kMixed) {
-        // float64 ray: hit distance to the triangle's float64 plane, mirror
-        Plane64 p64 = ldg_d4(&a.sc.planes64[slot]);
-        double3 n = make_double3(p64.x, p64.y, p64.z);
-        double3 Od = make_double3(O.x, O.y, O.z), Dd = make_double3(D.x, D.y, D.z);
-        double th = best.has64 ? best.t64 : (p64.w - dot3(n, Od)) * rcp64(dot3(n, Dd));
-        double3 h = Od + Dd * th;
-        double3 dn = Dd - n * (2.0 * dot3(Dd, n));
-        H.x = h.x; H.y = h.y; H.z = h.z;
-        Dn.x = dn.x; Dn.y = dn.y; Dn.z = dn.z;
-        dns64 = fabs(dot3(n, dn));
+        PlaneDF pd = a.sc.planes_df[slot];
+        df3 n = df3{df{pd.hi.x, pd.lo.x}, df{pd.hi.y, pd.lo.y}, df{pd.hi.z, pd.lo.z}};
+        df w = df{pd.hi.w, pd.lo.w};
+        df3 A = ld_df3(sm, kRowA, t), O = ld_df3(sm, kRowO, t), D = ld_df3(sm, kRowD, t);
+        df th = best.has64 ? d_to_df(best.t64) : df_div(df_sub(w, df3_dot(n, O)), df3_dot(n, D));
+        df3 H = df3_add(O, df3_scale(D, th));
+        df da = df3_dot(df3_sub(A, mkdf3(pv0)), n);
+        A = df3_sub(A, df3_scale(n, df{2.0f * da.hi, 2.0f * da.lo}));
+        st_df3(sm, kRowA, t, A);
+#pragma unroll
+        for (int j = 0; j < 3; j++) st_df3(sm, kRowN + 3 * j, t, df3_mirror(ld_df3(sm, kRowN + 3 * j, t), n));
+        D = df3_mirror(D, n);
+        st_df3(sm, kRowO, t, H);
+        st_df3(sm, kRowD, t, D);
+        df dn = df3_dot(n, D);
+        dns64 = fabs((double)dn.hi + (double)dn.lo);
         dns = (float)dns64;
+        Dn = df3_hi(D);
+        float3 sn = dot3(pn, Dn) > 0.0f ? pn : pn * -1.0f;
+        float sw = df3_dot(mkdf3(sn), df3_sub(mkdf3(pv0), A)).hi;
+        sm.st[0][t] = sn.x; sm.st[1][t] = sn.y; sm.st[2][t] = sn.z; sm.st[3][t] = sw;
       } else {
-        float3 Of = make_float3((float)O.x, (float)O.y, (float)O.z), Df = make_float3((float)D.x, (float)D.y, (float)D.z);
-        float3 h = Of + Df * best.t;
-        float3 dn = Df - pn * (2.0f * dot3(Df, pn));
-        H.x = h.x; H.y = h.y; H.z = h.z;
-        Dn.x = dn.x; Dn.y = dn.y; Dn.z = dn.z;
-        dns = fabsf(dot3(pn, dn));
+        float3 A = ld_hi3(sm, kRowA, t), O = ld_hi3(sm, kRowO, t), D = ld_hi3(sm, kRowD, t);
+        A = A - pn * (2.0f * dot3(A - pv0, pn));
+        st_f3(sm, kRowA, t, A);
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+          float3 nj = ld_hi3(sm, kRowN + 3 * j, t);
+          st_f3(sm, kRowN + 3 * j, t, nj - pn * (2.0f * dot3(nj, pn)));
+        }
+        float3 H = O + D * best.t;
+        Dn = D - pn * (2.0f * dot3(D, pn));
+        st_f3(sm, kRowO, t, H);
+        st_f3(sm, kRowD, t, Dn);
+        dns = fabsf(dot3(pn, Dn));
         dns64 = 0.0;
+        float3 sn = dot3(pn, Dn) > 0.0f ? pn : pn * -1.0f;
+        float sw = dot3(sn, pv0 - A);
+        sm.st[0][t] = sn.x; sm.st[1][t] = sn.y; sm.st[2][t] = sn.z; sm.st[3][t] = sw;
       }
-      sts3(sm.od, 0, t, H);
-      sts3(sm.od, 3, t, Dn);
-      float3 dnf = make_float3((float)Dn.x, (float)Dn.y, (float)Dn.z);
-      float3 sn = dot3(pn, dnf) > 0.0f ? pn : pn * -1.0f;
-      float sw = dot3(sn, pv0 - A);
-      sm.st[0][t] = sn.x; sm.st[1][t] = sn.y; sm.st[2][t] = sn.z; sm.st[3][t] = sw;
       start_slot = slot;
       k++;
     } else {
@@ -532,24 +539,28 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
 }
 
 // Closest hit of arbitrary float32 rays (the axis-ray query of the trace
-// kernel on its own), decided as in MIXED mode with the float32 ray promoted
-// to float64 for ambiguous triangles.  ns: optional start-plane normals.
+// kernel on its own), decided as in MIXED mode with the float32 origin and
+// the float64-normalised direction as float pairs.  ns: optional start-plane
+// normals.
 __global__ void __launch_bounds__(128) k_cast(DevScene sc, const float *o, const float *d, const float *ns,
                                               int64_t n, float t_eps, float *t_out, int *tri_out, int *err) {
-  __shared__ double od[6][128];
+  __shared__ float rh[6][128], rl[6][128];
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int t = threadIdx.x;
-  double3 O = make_double3(o[3 * i], o[3 * i + 1], o[3 * i + 2]);
-  double3 D = normalize3(make_double3(d[3 * i], d[3 * i + 1], d[3 * i + 2]));
+  float3 O = make_float3(o[3 * i], o[3 * i + 1], o[3 * i + 2]);
+  double3 Dd = normalize3(make_double3(d[3 * i], d[3 * i + 1], d[3 * i + 2]));
+  df3 D = df3{d_to_df(Dd.x), d_to_df(Dd.y), d_to_df(Dd.z)};
   double dns = 0.0;
-  if (ns) dns = fabs(dot3(D, make_double3(ns[3 * i], ns[3 * i + 1], ns[3 * i + 2])));
-  od[0][t] = O.x; od[1][t] = O.y; od[2][t] = O.z;
-  od[3][t] = D.x; od[4][t] = D.y; od[5][t] = D.z;
-  Ray r = make_ray(to_f3(O), to_f3(D), t_eps, (float)dns);
+  if (ns) dns = fabs(dot3(Dd, make_double3(ns[3 * i], ns[3 * i + 1], ns[3 * i + 2])));
+  rh[0][t] = O.x; rh[1][t] = O.y; rh[2][t] = O.z;
+  rl[0][t] = 0.0f; rl[1][t] = 0.0f; rl[2][t] = 0.0f;
+  rh[3][t] = D.x.hi; rh[4][t] = D.y.hi; rh[5][t] = D.z.hi;
+  rl[3][t] = D.x.lo; rl[4][t] = D.y.lo; rl[5][t] = D.z.lo;
+  Ray r = make_ray(O, df3_hi(D), t_eps, (float)dns);
   Best best;
   unsigned long long a = 0, b = 0;
-  int slot = closest_hit<true, false>(sc, r, &od[0][t], 128, dns, best, err, a, b);
+  int slot = closest_hit<true, false>(sc, r, RaySrc{&rh[0][t], &rl[0][t], 128}, dns, best, err, a, b);
   t_out[i] = slot >= 0 ? (best.has64 ? (float)best.t64 : best.t) : kInf;
   tri_out[i] = slot >= 0 ? best.id : -1;
 }
@@ -589,22 +600,12 @@ cudaError_t launch_trace(cudaStream_t st, const TraceArgs &a, int n_sm) {
 }
 
 // ------------------------------------------------------------------ scatter
-// Signed distance of m from the plane of leaf slot `slot`, in float64,
-// oriented like the float32 normal `nf` of the segment record.
-__device__ __forceinline__ double plane_side64(const ScatterArgs &a, int slot, float3 nf, float4 m) {
-  Plane64 pl = ldg_d4(&a.planes64[slot]);
-  float4 v0 = __ldg(&a.tris[slot].v0);
-  double3 n = make_double3(pl.x, pl.y, pl.z);
-  if (n.x * nf.x + n.y * nf.y + n.z * nf.z < 0.0) n = n * -1.0;
-  return dot3(n, make_double3((double)m.x - v0.x, (double)m.y - v0.y, (double)m.z - v0.z));
-}
-
 // Per-warp shared state of the scatter: 32 segments, one per lane, stored as
 // [field][lane] so that lanes reading different segments hit different banks.
 constexpr int kScatterWarps = 4;
 enum : int {
-  F_AX = 0, F_RX = 3, F_N0 = 6, F_N1 = 9, F_N2 = 12, F_NS = 15, F_NE = 19, F_P = 23, F_SLOTS = 31,
-  F_CY0 = 33, F_CY1 = 34, F_PN = 35, F_PX = 36, F_PY = F_PX + kPolyMax, F_COUNT = F_PY + kPolyMax
+  F_AX = 0, F_RX = 3, F_N0 = 6, F_NLO = 15, F_NS = 24, F_NE = 28, F_P = 32, F_SLOTS = 40,
+  F_CY0 = 42, F_PN = 43, F_PX = 44, F_PY = F_PX + kPolyMax, F_COUNT = F_PY + kPolyMax
 };
 struct ScatterSmem {
   float f[kScatterWarps][F_COUNT][32];
@@ -628,6 +629,24 @@ __device__ __forceinline__ int warp_owner(int excl, int i) {
   return owner;
 }
 
+// m - apex as float pairs (apex hi in F[F_AX..], lo parts in F[F_RX..])
+__device__ __forceinline__ df3 rel_df(const float (*F)[32], int s, float4 m) {
+  return df3_sub(mkdf3(make_float3(m.x, m.y, m.z)),
+                 df3{df{F[F_AX][s], F[F_RX][s]}, df{F[F_AX + 1][s], F[F_RX + 1][s]}, df{F[F_AX + 2][s], F[F_RX + 2][s]}});
+}
+
+// Signed distance of m from the plane of leaf slot `slot` as a float pair,
+// oriented like the float32 normal `nf` of the segment record.
+__device__ __forceinline__ float plane_side_df(const ScatterArgs &a, int slot, float3 nf, float4 m) {
+  PlaneDF pd = a.planes_df[slot];
+  float4 v0 = __ldg(&a.tris[slot].v0);
+  df3 n = df3{df{pd.hi.x, pd.lo.x}, df{pd.hi.y, pd.lo.y}, df{pd.hi.z, pd.lo.z}};
+  df3 rel = df3_sub(mkdf3(make_float3(m.x, m.y, m.z)), mkdf3(f3(v0)));
+  df e = df3_dot(n, rel);
+  float sg = pd.hi.x * nf.x + pd.hi.y * nf.y + pd.hi.z * nf.z < 0.0f ? -1.0f : 1.0f;
+  return sg * (e.hi + e.lo);
+}
+
 // One warp takes 32 segments at a time.  Each lane loads one segment and
 // builds its footprint; the warp then walks the (segment, cell row) pairs of
 // all 32 footprints 32 at a time, turns each into its run of microphones, and
@@ -649,10 +668,14 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
     long long si = base + lane;
     int nrows = 0;
     if (si < n_seg) {
-      const Seg s = a.segs[si];
+      Seg sl;
+      const float4 *src4 = reinterpret_cast<const float4 *>(a.segs + si);
+      float4 *dst4 = reinterpret_cast<float4 *>(&sl);
+#pragma unroll
+      for (int q = 0; q < (int)(sizeof(Seg) / 16); q++) dst4[q] = __ldg(src4 + q);
       Poly p;
       int cy0 = 0, cy1 = -1;
-      if (seg_footprint(s, g, p)) {
+      if (seg_footprint(sl, g, p)) {
         float ymin = kInf, ymax = -kInf;
         for (int i = 0; i < p.n; i++) { ymin = fminf(ymin, p.y[i]); ymax = fmaxf(ymax, p.y[i]); }
         if (ymin <= ymax) {
@@ -661,25 +684,23 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
         }
       }
       nrows = cy1 >= cy0 ? cy1 - cy0 + 1 : 0;
-      // apex as a float plus a float residual: m - apex is then formed in
-      // float32 to within about one rounding of the float64 difference
-      float ax = (float)s.ax, ay = (float)s.ay, az = (float)s.az;
-      F[F_AX][lane] = ax; F[F_AX + 1][lane] = ay; F[F_AX + 2][lane] = az;
-      F[F_RX][lane] = (float)(s.ax - (double)ax);
-      F[F_RX + 1][lane] = (float)(s.ay - (double)ay);
-      F[F_RX + 2][lane] = (float)(s.az - (double)az);
-      F[F_N0][lane] = s.n0.x; F[F_N0 + 1][lane] = s.n0.y; F[F_N0 + 2][lane] = s.n0.z;
-      F[F_N1][lane] = s.n1.x; F[F_N1 + 1][lane] = s.n1.y; F[F_N1 + 2][lane] = s.n1.z;
-      F[F_N2][lane] = s.n2.x; F[F_N2 + 1][lane] = s.n2.y; F[F_N2 + 2][lane] = s.n2.z;
-      F[F_NS][lane] = s.start.x; F[F_NS + 1][lane] = s.start.y; F[F_NS + 2][lane] = s.start.z;
-      F[F_NS + 3][lane] = s.start.w;
-      F[F_NE][lane] = s.end.x; F[F_NE + 1][lane] = s.end.y; F[F_NE + 2][lane] = s.end.z;
-      F[F_NE + 3][lane] = s.end.w;
-      F[F_P][lane] = s.p03.x; F[F_P + 1][lane] = s.p03.y; F[F_P + 2][lane] = s.p03.z;
-      F[F_P + 3][lane] = s.p03.w; F[F_P + 4][lane] = s.p47.x; F[F_P + 5][lane] = s.p47.y;
-      F[F_P + 6][lane] = s.p47.z; F[F_P + 7][lane] = s.p47.w;
-      F[F_SLOTS][lane] = s.n0.w;  // start-plane triangle slot (int bits)
-      F[F_SLOTS + 1][lane] = s.n1.w;  // end-plane triangle slot (int bits)
+      for (int q = 0; q < 3; q++) {
+        F[F_AX + q][lane] = sl.ahi[q];
+        F[F_RX + q][lane] = sl.alo[q];
+      }
+      F[F_N0][lane] = sl.n0.x; F[F_N0 + 1][lane] = sl.n0.y; F[F_N0 + 2][lane] = sl.n0.z;
+      F[F_N0 + 3][lane] = sl.n1.x; F[F_N0 + 4][lane] = sl.n1.y; F[F_N0 + 5][lane] = sl.n1.z;
+      F[F_N0 + 6][lane] = sl.n2.x; F[F_N0 + 7][lane] = sl.n2.y; F[F_N0 + 8][lane] = sl.n2.z;
+      for (int q = 0; q < 9; q++) F[F_NLO + q][lane] = sl.nlo[q];
+      F[F_NS][lane] = sl.start.x; F[F_NS + 1][lane] = sl.start.y; F[F_NS + 2][lane] = sl.start.z;
+      F[F_NS + 3][lane] = sl.start.w;
+      F[F_NE][lane] = sl.end.x; F[F_NE + 1][lane] = sl.end.y; F[F_NE + 2][lane] = sl.end.z;
+      F[F_NE + 3][lane] = sl.end.w;
+      F[F_P][lane] = sl.p03.x; F[F_P + 1][lane] = sl.p03.y; F[F_P + 2][lane] = sl.p03.z;
+      F[F_P + 3][lane] = sl.p03.w; F[F_P + 4][lane] = sl.p47.x; F[F_P + 5][lane] = sl.p47.y;
+      F[F_P + 6][lane] = sl.p47.z; F[F_P + 7][lane] = sl.p47.w;
+      F[F_SLOTS][lane] = sl.n0.w;      // start-plane triangle slot (int bits)
+      F[F_SLOTS + 1][lane] = sl.n1.w;  // end-plane triangle slot (int bits)
       F[F_CY0][lane] = __int_as_float(cy0);
       F[F_PN][lane] = __int_as_float(p.n);
       for (int i = 0; i < kPolyMax; i++) {
@@ -738,24 +759,37 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
         if (c < total_c) {
           int mi = ofirst + (c - oexcl);
           float4 m = __ldg(&a.mics[mi]);
+          // m - apex with the apex as hi + lo: one extra rounding at most
           float3 v = make_float3((m.x - F[F_AX][s]) - F[F_RX][s], (m.y - F[F_AX + 1][s]) - F[F_RX + 1][s],
                                  (m.z - F[F_AX + 2][s]) - F[F_RX + 2][s]);
           n_cand++;
-          float3 n0 = make_float3(F[F_N0][s], F[F_N0 + 1][s], F[F_N0 + 2][s]);
-          float3 n1 = make_float3(F[F_N1][s], F[F_N1 + 1][s], F[F_N1 + 2][s]);
-          float3 n2 = make_float3(F[F_N2][s], F[F_N2 + 1][s], F[F_N2 + 2][s]);
-          bool in = dot3(n0, v) >= 0.0f && dot3(n1, v) >= 0.0f && dot3(n2, v) >= 0.0f;
+          // cone planes: float32; within the rounding band of a plane the
+          // test is redone with float pairs
+          const float band_v = 2e-6f * (fabsf(v.x) + fabsf(v.y) + fabsf(v.z));
+          bool in = true;
+#pragma unroll
+          for (int j = 0; j < 3; j++) {
+            float3 nj = make_float3(F[F_N0 + 3 * j][s], F[F_N0 + 3 * j + 1][s], F[F_N0 + 3 * j + 2][s]);
+            float e = dot3(nj, v);
+            if (fabsf(e) <= band_v * (fabsf(nj.x) + fabsf(nj.y) + fabsf(nj.z))) {
+              df3 nd = df3{df{nj.x, F[F_NLO + 3 * j][s]}, df{nj.y, F[F_NLO + 3 * j + 1][s]},
+                           df{nj.z, F[F_NLO + 3 * j + 2][s]}};
+              df ed = df3_dot(nd, rel_df(F, s, m));
+              e = ed.hi + ed.lo;
+            }
+            in = in && e >= 0.0f;
+          }
           if (in) {
             // start/end planes: float32 relative to the apex; within the
-            // rounding band of a plane the test is redone in float64 against
-            // the triangle's own plane, the form the definition uses
+            // rounding band the test is redone with float pairs against the
+            // triangle's own plane, the form the definition uses
             float3 ns = make_float3(F[F_NS][s], F[F_NS + 1][s], F[F_NS + 2][s]);
             float3 ne = make_float3(F[F_NE][s], F[F_NE + 1][s], F[F_NE + 2][s]);
             float band = 1e-4f + 1e-6f * (fabsf(v.x) + fabsf(v.y) + fabsf(v.z));
             float fs = dot3(ns, v) - F[F_NS + 3][s], fe = dot3(ne, v) - F[F_NE + 3][s];
             int s_slot = __float_as_int(F[F_SLOTS][s]), e_slot = __float_as_int(F[F_SLOTS + 1][s]);
-            if (fabsf(fs) <= band && s_slot >= 0) fs = (float)plane_side64(a, s_slot, ns, m);
-            if (fabsf(fe) <= band && e_slot >= 0) fe = (float)plane_side64(a, e_slot, ne, m);
+            if (fabsf(fs) <= band && s_slot >= 0) fs = plane_side_df(a, s_slot, ns, m);
+            if (fabsf(fe) <= band && e_slot >= 0) fe = plane_side_df(a, e_slot, ne, m);
             in = fs > 0.0f && fe >= 0.0f;
           }
           float d2 = dot3(v, v);
