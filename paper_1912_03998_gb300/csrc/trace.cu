@@ -374,12 +374,16 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
           float4 s4 = __ldg(&a.src[si]);
           float3 A = make_float3(s4.x, s4.y, s4.z);
           if (kMixed) {
+            // table: 9 normal components then the 3 axis components, hi
+            // parts first, lo parts 12 floats later
             const float *bt = a.beam_table + 24 * bi;
-            for (int q = 0; q < 12; q++) {
+            for (int q = 0; q < 9; q++) {
               sm.hi[kRowN + q][t] = __ldg(bt + q);
               sm.lo[kRowN + q][t] = __ldg(bt + 12 + q);
             }
             for (int q = 0; q < 3; q++) {
+              sm.hi[kRowD + q][t] = __ldg(bt + 9 + q);
+              sm.lo[kRowD + q][t] = __ldg(bt + 21 + q);
               sm.lo[kRowA + q][t] = 0.0f;
               sm.lo[kRowO + q][t] = 0.0f;
             }
