@@ -176,6 +176,32 @@ int bt_cast_rays(bt_ctx *ctx, int32_t scene_id, const float *origins, const floa
                  const float *start_normals, int64_t n, float t_eps_m, float *t_out,
                  int32_t *tri_out);
 
+/* Trace without allocating (the paper has no counterpart).  For callers that
+ * must not call cudaMalloc or cudaFree during a trace: a service running
+ * under a device-memory budget fixed up front, where another framework's pool
+ * owns the rest of the GPU and a new allocation could fail part-way; or a
+ * per-frame update loop, where cudaMalloc and cudaFree synchronise the device
+ * and stall every other stream.  The scene, its sources and microphones must
+ * already be set (those calls allocate); this call then allocates nothing.
+ * It computes what bt_trace followed by bt_read_levels gives, and like
+ * bt_trace it replaces the scene's last result (bt_read_levels and the stats
+ * then refer to it).
+ *   level_db   [n_m][n_bands] float64, DEVICE memory of the context's GPU
+ *   path_count [n_m] int32, device memory, or NULL
+ * Its scratch is one static device array of BT_NOALLOC_SCRATCH_MB MiB inside
+ * the library, held on every GPU that loads the library until the process
+ * exits.  The icosahedron level must be <= BT_NOALLOC_MAX_LEVEL (the beam table
+ * lives in that scratch); larger requests fail with BT_E_INVALID and say so.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call, from any context, shares the one
+ * array and clears what must start at zero; calls whose device work overlaps
+ * (different streams or host threads) race on it. */
+#define BT_NOALLOC_SCRATCH_MB 32
+#define BT_NOALLOC_MAX_LEVEL 6
+int bt_trace_noalloc(bt_ctx *ctx, int32_t scene_id, const bt_trace_params *p, double *level_db,
+                     int32_t *path_count);
+
 /* Message of the last error of the context ("" if none).  Valid until the
  * next call on the context. */
 const char *bt_last_error(const bt_ctx *ctx);

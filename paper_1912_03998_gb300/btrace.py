@@ -55,7 +55,8 @@ _lock = threading.Lock()
 _lib = None
 EXPECTED_SYMBOLS = ("bt_params_default", "bt_create", "bt_destroy", "bt_load_scene",
                     "bt_unload_scene", "bt_set_sources", "bt_set_microphones", "bt_trace",
-                    "bt_read_levels", "bt_last_error", "bt_kernel_launches", "bt_cast_rays")
+                    "bt_read_levels", "bt_last_error", "bt_kernel_launches", "bt_cast_rays",
+                    "bt_trace_noalloc")
 
 
 def lib_path() -> str:
@@ -84,6 +85,7 @@ def lib():
             L.bt_last_error.argtypes = [p]
             L.bt_last_error.restype = C.c_char_p
             L.bt_cast_rays.argtypes = [p, i32, p, p, p, i64, C.c_float, p, p]
+            L.bt_trace_noalloc.argtypes = [p, i32, C.POINTER(bt_trace_params), p, p]
             L.bt_kernel_launches.argtypes = []
             L.bt_kernel_launches.restype = C.c_int64
             for name in EXPECTED_SYMBOLS:
@@ -171,6 +173,17 @@ def bt_set_microphones(ctx, scene_id: int, pos):
 
 def bt_trace(ctx, scene_id: int, params: bt_trace_params):
     _check(lib().bt_trace(ctx, int(scene_id), C.byref(params)), ctx)
+
+
+def bt_trace_noalloc(ctx, scene_id: int, params: bt_trace_params, level_db, path_count=None):
+    """Trace into caller-owned device arrays without allocating (torch CUDA
+    tensors: level_db float64 [n_m, n_bands], path_count int32 [n_m] or None)."""
+    for x in (level_db, path_count):
+        if x is not None:
+            assert x.is_cuda and x.is_contiguous()
+    rc = lib().bt_trace_noalloc(ctx, int(scene_id), C.byref(params), C.c_void_p(level_db.data_ptr()),
+                                C.c_void_p(path_count.data_ptr()) if path_count is not None else None)
+    _check(rc, ctx)
 
 
 def bt_read_levels(ctx, scene_id: int, level_db=None, intensity=None, path_count=None):

@@ -673,3 +673,184 @@ BT_API int bt_cast_rays(bt_ctx *c, int32_t scene_id, const float *origins, const
   if (c->h_ctr->error) return fail(c, c->h_ctr->error, "device error %d in ray query", c->h_ctr->error);
   return BT_OK;
 }
+
+// ============================================================ no allocation
+// A trace that calls no cudaMalloc/cudaFree: its scratch (counters, beam
+// table, segment records) lives in one file-scope device array of fixed size,
+// and its results go straight into device arrays the caller owns.
+namespace {
+
+constexpr size_t kNoAllocBytes = (size_t)BT_NOALLOC_SCRATCH_MB << 20;
+// Reserved on every GPU that loads this library, until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch per device ordinal, looked up on the
+// first no-allocation call made with that device current.
+void *g_noalloc_ptr[256] = {nullptr};
+
+__global__ void k_levels_noalloc(const double *energy, const int *count, const float4 *mics, int64_t n_m,
+                                 int n_bands, double *level_db, int *path_count) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n_m) return;
+  int64_t orig = __float_as_int(mics[p].w);
+  for (int b = 0; b < n_bands; b++) {
+    double I = energy[p * bt::kMaxBands + b];
+    level_db[orig * n_bands + b] = I > 0.0 ? 10.0 * log10(I) + 120.0 : -__builtin_huge_val();
+  }
+  if (path_count) path_count[orig] = count[p];
+}
+
+bool is_device_ptr(const void *p, int device) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == device;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+BT_API int bt_trace_noalloc(bt_ctx *c, int32_t scene_id, const bt_trace_params *p, double *level_db,
+                            int32_t *path_count) {
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  SceneState *s;
+  TRY(scene_ref(c, scene_id, &s));
+  if (!p) return fail(c, BT_E_INVALID, "NULL params");
+  if (!s->has_src || !s->has_mics) return fail(c, BT_E_STATE, "sources and microphones must be set first");
+  if (p->max_order < 0 || p->max_order > 32) return fail(c, BT_E_INVALID, "max_order %d not in 0..32", p->max_order);
+  if (!(p->t_eps_m > 0.0f) || !isfinite(p->t_eps_m)) return fail(c, BT_E_INVALID, "t_eps_m must be > 0");
+  if (!(p->energy_threshold_w >= 0.0f)) return fail(c, BT_E_INVALID, "energy_threshold_w must be >= 0");
+  if (p->precision != BT_PREC_MIXED && p->precision != BT_PREC_FP32)
+    return fail(c, BT_E_INVALID, "precision %d not implemented (BT_PREC_FP32 or BT_PREC_MIXED)", p->precision);
+  if (p->tiles_x != 1 || p->tiles_y != 1)
+    return fail(c, BT_E_INVALID, "tiles %dx%d: only 1x1 is implemented in this build", p->tiles_x, p->tiles_y);
+  if (s->level > BT_NOALLOC_MAX_LEVEL)
+    return fail(c, BT_E_INVALID, "bt_trace_noalloc: icosahedron level %d exceeds the limit of %d of its %d MiB scratch",
+                s->level, BT_NOALLOC_MAX_LEVEL, BT_NOALLOC_SCRATCH_MB);
+  const size_t nv = (size_t)s->n_mics * s->n_bands;
+  if (nv > 0 && (!level_db || !is_device_ptr(level_db, c->device)))
+    return fail(c, BT_E_INVALID, "bt_trace_noalloc: level_db must be device memory of device %d", c->device);
+  if (path_count && !is_device_ptr(path_count, c->device))
+    return fail(c, BT_E_INVALID, "bt_trace_noalloc: path_count must be device memory of device %d or NULL", c->device);
+  int has_alpha = 0;
+  float alpha_log2[BT_MAX_BANDS];
+  for (int b = 0; b < BT_MAX_BANDS; b++) {
+    float a = p->air_atten_db_per_m[b];
+    if (!(a >= 0.0f) || !isfinite(a)) return fail(c, BT_E_INVALID, "air attenuation must be finite and >= 0");
+    alpha_log2[b] = -a * 3.32192809488736f / 10.0f;
+    if (b < s->n_bands && a != 0.0f) has_alpha = 1;
+  }
+  DeviceGuard g(c->device);
+  if (c->device < 0 || c->device >= 256) return fail(c, BT_E_INVALID, "device ordinal %d out of range", c->device);
+  if (!g_noalloc_ptr[c->device]) {
+    // set-up, once per device, with that device current
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return fail(c, BT_E_CUDA, "bt_trace_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    }
+    g_noalloc_ptr[c->device] = ptr;
+  }
+  // carve the scratch: counters, two cursors, beam table, segment records
+  char *base = (char *)g_noalloc_ptr[c->device];
+  const int64_t n_beams = (int64_t)20 << (2 * s->level);
+  const int mixed = p->precision == BT_PREC_MIXED ? 1 : 0;
+  size_t off = 0;
+  bt::Counters *ctr = (bt::Counters *)(base + off);
+  off = align_up(off + sizeof(bt::Counters), 256);
+  unsigned long long *seg_count = (unsigned long long *)(base + off);
+  unsigned long long *lineage_next = seg_count + 1;
+  off = align_up(off + 2 * sizeof(unsigned long long), 256);
+  float *beam_table = (float *)(base + off);
+  if (mixed) off = align_up(off + sizeof(float) * 24 * (size_t)n_beams, 256);
+  bt::Seg *segs = (bt::Seg *)(base + off);
+  const unsigned long long seg_room = (kNoAllocBytes - off) / sizeof(bt::Seg);
+  const int64_t total = s->n_src * n_beams;
+  int64_t chunk = (int64_t)(seg_room / (unsigned long long)(p->max_order + 1));
+  if (chunk < 1) return fail(c, BT_E_INVALID, "bt_trace_noalloc: max_order %d too large for its scratch", p->max_order);
+  if (chunk > total) chunk = total > 0 ? total : 1;
+  const unsigned long long cap = (unsigned long long)chunk * (p->max_order + 1);
+  cudaStream_t st = c->stream;
+  CK(cudaMemsetAsync(ctr, 0, sizeof(bt::Counters), st));
+  CK(cudaMemsetAsync(s->energy.p, 0, sizeof(double) * bt::kMaxBands * (size_t)s->n_mics, st));
+  CK(cudaMemsetAsync(s->count.p, 0, sizeof(int) * (size_t)s->n_mics, st));
+  if (mixed && total > 0) CK(bt::launch_beam_table(st, s->level, beam_table));
+  bt::TraceArgs ta;
+  memset(&ta, 0, sizeof(ta));
+  ta.sc = dev_scene(*s);
+  ta.src = (const float4 *)s->src.p;
+  ta.power = (const float *)s->power.p;
+  ta.n_src = s->n_src;
+  ta.level = s->level;
+  ta.n_beams = n_beams;
+  ta.max_order = p->max_order;
+  ta.t_eps = p->t_eps_m;
+  ta.energy_threshold = p->energy_threshold_w;
+  for (int b = 0; b < BT_MAX_BANDS; b++) ta.alpha_log2[b] = alpha_log2[b];
+  ta.has_alpha = has_alpha;
+  ta.grid = (const bt::MicGrid *)s->grid.p;
+  ta.segs = segs;
+  ta.seg_count = seg_count;
+  ta.seg_capacity = cap;
+  ta.lineage_next = lineage_next;
+  ta.ctr = ctr;
+  ta.count_work = 0;
+  ta.mixed = mixed;
+  ta.beam_table = mixed ? beam_table : nullptr;
+  bt::ScatterArgs sa;
+  memset(&sa, 0, sizeof(sa));
+  sa.tris = ta.sc.tris;
+  sa.planes_df = ta.sc.planes_df;
+  sa.segs = segs;
+  sa.seg_count = seg_count;
+  sa.seg_capacity = cap;
+  sa.grid = ta.grid;
+  sa.mics = (const float4 *)s->mics.p;
+  sa.cell_start = (const int *)s->cell_start.p;
+  sa.energy = (double *)s->energy.p;
+  sa.count = (int *)s->count.p;
+  sa.n_bands = s->n_bands;
+  for (int b = 0; b < BT_MAX_BANDS; b++) sa.alpha_log2[b] = alpha_log2[b];
+  sa.has_alpha = has_alpha;
+  sa.ctr = ctr;
+  const int64_t n_chunks = total > 0 ? (total + chunk - 1) / chunk : 0;
+  for (int64_t ci = 0; ci < n_chunks; ci++) {
+    ta.lineage_begin = ci * chunk;
+    ta.lineage_end = ta.lineage_begin + chunk < total ? ta.lineage_begin + chunk : total;
+    CK(cudaMemsetAsync(seg_count, 0, 2 * sizeof(unsigned long long), st));
+    CK(bt::launch_trace(st, ta, c->n_sm));
+    if (s->n_mics > 0) CK(bt::launch_scatter(st, sa, c->n_sm));
+  }
+  if (s->n_mics > 0) {
+    k_levels_noalloc<<<(int)((s->n_mics + 255) / 256), 256, 0, st>>>(
+        (const double *)s->energy.p, (const int *)s->count.p, (const float4 *)s->mics.p, s->n_mics, s->n_bands,
+        level_db, path_count);
+    bt::note_launches(1);
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(c->h_ctr, ctr, sizeof(bt::Counters), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const bt::Counters &h = *c->h_ctr;
+  bt_stats &o = s->stats;
+  memset(&o, 0, sizeof(o));
+  o.beams = total;
+  o.segments = (int64_t)h.segments;
+  o.hits = (int64_t)h.hits;
+  o.escapes = (int64_t)h.escapes;
+  o.emitted = (int64_t)h.emitted;
+  o.candidates = (int64_t)h.candidates;
+  o.contributions = (int64_t)h.contributions;
+  o.trace_launches = n_chunks;
+  o.scatter_launches = s->n_mics > 0 ? n_chunks : 0;
+  if (h.error) {
+    s->traced = false;
+    return fail(c, h.error, "device error %d in the no-allocation trace", h.error);
+  }
+  s->traced = true;
+  return BT_OK;
+}
