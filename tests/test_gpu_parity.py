@@ -287,3 +287,20 @@ def test_fp32_precision_mode(tracer, oracle_mod):
     g = gpu_run(tracer, w, precision=btrace.BT_PREC_FP32)
     _, L = oracle_levels(oracle_mod, w)
     assert_parity(g["level"], L, "tiny city, FP32 chain")
+
+
+def test_district_full_size_sampled_microphones(tracer, oracle_mod, district):
+    # the bench configuration itself: all 1,000 sources and all 250,000
+    # microphones on the GPU; the oracle computes a seeded sample of 2,000
+    # microphones from all sources (a microphone's result does not depend on
+    # the other microphones)
+    import os
+    g = gpu_run(tracer, district)
+    pick = np.sort(np.random.Generator(np.random.PCG64(33)).choice(len(district.mics), 2000, replace=False))
+    r, L = oracle_levels(oracle_mod, district.with_mics(district.mics[pick]),
+                         n_threads=max(1, os.cpu_count() or 1))
+    s = assert_parity(g["level"][pick], L, "district, 1000 sources, sampled microphones")
+    assert (g["cnt"][pick] == r["cnt"]).mean() >= 0.999
+    assert (r["cnt"] > 0).mean() > 0.5
+    assert abs(g["stats"]["segments"] / r["stats"]["segments"] - 1) < 1e-4
+    print("district full size, 2000 sampled microphones:", s)
