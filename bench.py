@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--tiles", default="1x1", help="sub-domain grid, e.g. 4x4")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"],
                     help="mixed: float64 image-source chain (the parity-checked default)")
     return ap.parse_args()
@@ -164,7 +165,7 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", rank % max(1, torch.cuda.device_count()))
     torch.cuda.set_device(dev)
     w = make_workload(args.workload, rank, args.sources)
-    tiles = (1, 1)
+    tiles = tuple(int(v) for v in args.tiles.lower().split("x"))
     stream = torch.cuda.current_stream(dev)
     ctx = btrace.bt_create(dev.index, stream.cuda_stream)
     D = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)

@@ -10,6 +10,7 @@
 
 #include <atomic>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "bt_internal.cuh"
@@ -45,6 +46,11 @@ struct SceneState {
   int64_t n_mics = 0;
   int side = 1;
   DevBuf mics, cell_start, grid, energy, count;
+  // tiled hierarchy (sub-domains), built on the first trace that asks for it
+  int tiled_tx = 0, tiled_ty = 0;
+  int64_t n_pairs = 0;
+  bt::TileGrid tg;
+  DevBuf t_nodes, t_tris, t_planes, t_planes64, t_planes_df, t_roots;
   // result
   bool traced = false;
   bt_stats stats;
@@ -71,6 +77,8 @@ struct bt_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> kev;  // pairs of events around kernel launches of one trace
   std::vector<DevBuf> pool;      // released device buffers, reused before any new cudaMalloc
+  DevBuf t_state, t_qa, t_qb, t_cnt;  // sub-domain trace: lineage state, queues, counts and heads
+  int *h_tile_counts = nullptr;       // pinned [BT_MAX_TILES * BT_MAX_TILES]
 };
 
 namespace {
@@ -149,7 +157,8 @@ void release(DevBuf &b) {
 
 // Scene buffers go back to the context's pool (freed by bt_destroy).
 void release_scene(bt_ctx *c, SceneState &s) {
-  DevBuf *all[] = {&s.nodes, &s.tris, &s.planes, &s.planes64, &s.planes_df, &s.refl, &s.src, &s.power, &s.mics, &s.cell_start,
+  DevBuf *all[] = {&s.t_nodes, &s.t_tris, &s.t_planes, &s.t_planes64, &s.t_planes_df, &s.t_roots,
+                   &s.nodes, &s.tris, &s.planes, &s.planes64, &s.planes_df, &s.refl, &s.src, &s.power, &s.mics, &s.cell_start,
                    &s.grid, &s.energy, &s.count, &s.out_level, &s.out_int, &s.out_cnt};
   for (DevBuf *b : all)
     if (b->p) c->pool.push_back(*b);
@@ -215,6 +224,66 @@ __global__ void k_pack_sources(const float *pos, const float *power, int64_t n, 
   }
 }
 
+
+// Tiled hierarchy of a scene for a tx x ty sub-domain grid (cached until the
+// grid changes or the scene is dropped).
+int ensure_tiled(bt_ctx *c, SceneState &s, int tx, int ty) {
+  if (s.tiled_tx == tx && s.tiled_ty == ty) return BT_OK;
+  cudaStream_t st = c->stream;
+  bt::TileGrid tg;
+  tg.gx0 = s.box[0] - 1.0f;
+  tg.gy0 = s.box[1] - 1.0f;
+  tg.gx1 = s.box[3] + 1.0f;
+  tg.gy1 = s.box[4] + 1.0f;
+  tg.wx = (tg.gx1 - tg.gx0) / tx;
+  tg.wy = (tg.gy1 - tg.gy0) / ty;
+  tg.tx = tx;
+  tg.ty = ty;
+  const int T = tx * ty;
+  s.tiled_tx = s.tiled_ty = 0;
+  TRY(ensure(c, s.t_roots, sizeof(int) * T));
+  int64_t P = 0;
+  if (s.n_tris > 0) {
+    CK(cudaMemcpyAsync(c->d_box, s.box, sizeof(float) * 6, cudaMemcpyHostToDevice, st));
+    TRY(ensure(c, c->scratch, sizeof(uint32_t) * (size_t)(s.n_tris + 1) + 256));
+    CK(bt::tiled_count(st, (const bt::Tri *)s.tris.p, s.n_tris, tg, (uint32_t *)c->scratch.p));
+    uint32_t pairs = 0;
+    CK(cudaMemcpyAsync(&pairs, (uint32_t *)c->scratch.p + s.n_tris, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    P = pairs;
+    // the offsets stay at the start of the scratch; grow it without losing them
+    size_t need = bt::build_tiled_scratch_bytes(s.n_tris, P);
+    if (c->scratch.cap < need) {
+      DevBuf fresh;
+      TRY(ensure(c, fresh, need));
+      CK(cudaMemcpyAsync(fresh.p, c->scratch.p, sizeof(uint32_t) * (size_t)(s.n_tris + 1), cudaMemcpyDeviceToDevice, st));
+      c->pool.push_back(c->scratch);
+      c->scratch = fresh;
+    }
+    TRY(ensure(c, s.t_nodes, sizeof(bt::Node) * (size_t)(P > 1 ? P - 1 : 1)));
+    TRY(ensure(c, s.t_tris, sizeof(bt::Tri) * (size_t)P));
+    TRY(ensure(c, s.t_planes, sizeof(bt::Plane) * (size_t)P));
+    TRY(ensure(c, s.t_planes64, sizeof(bt::Plane64) * (size_t)P));
+    TRY(ensure(c, s.t_planes_df, sizeof(bt::PlaneDF) * (size_t)P));
+    CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(bt::Counters), st));
+    CK(bt::tiled_build(st, (const bt::Tri *)s.tris.p, (const bt::Plane *)s.planes.p, (const bt::Plane64 *)s.planes64.p,
+                       (const bt::PlaneDF *)s.planes_df.p, s.n_tris, tg, c->d_box, (const uint32_t *)c->scratch.p, P,
+                       c->scratch.p, c->scratch.cap, (bt::Node *)s.t_nodes.p, (bt::Tri *)s.t_tris.p,
+                       (bt::Plane *)s.t_planes.p, (bt::Plane64 *)s.t_planes64.p, (bt::PlaneDF *)s.t_planes_df.p,
+                       (int *)s.t_roots.p, &c->d_ctr->error));
+  } else {
+    std::vector<int> empty(T, (int)0x80000000);
+    CK(cudaMemcpyAsync(s.t_roots.p, empty.data(), sizeof(int) * T, cudaMemcpyHostToDevice, st));
+  }
+  TRY(read_counters(c));
+  if (c->h_ctr->error) return fail(c, BT_E_CUDA, "tiled hierarchy build failed (device error %d)", c->h_ctr->error);
+  s.n_pairs = P;
+  s.tg = tg;
+  s.tiled_tx = tx;
+  s.tiled_ty = ty;
+  return BT_OK;
+}
+
 }  // namespace
 
 // ====================================================================== ABI
@@ -259,6 +328,10 @@ BT_API int bt_create(bt_ctx **out, int device, void *cuda_stream) {
     if (cudaMalloc(&c->d_box, 8 * sizeof(float)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
     if (cudaMalloc(&c->d_lineage_next, sizeof(unsigned long long)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
     if (cudaMallocHost(&c->h_ctr, sizeof(bt::Counters)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
+    if (cudaMallocHost(&c->h_tile_counts, sizeof(int) * BT_MAX_TILES * BT_MAX_TILES) != cudaSuccess) {
+      rc = BT_E_NOMEM;
+      break;
+    }
     if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) { rc = BT_E_CUDA; break; }
   } while (0);
   if (rc != BT_OK) {
@@ -288,6 +361,11 @@ BT_API int bt_destroy(bt_ctx *c) {
   if (c->d_box) cudaFree(c->d_box);
   if (c->d_lineage_next) cudaFree(c->d_lineage_next);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
+  if (c->h_tile_counts) cudaFreeHost(c->h_tile_counts);
+  release(c->t_state);
+  release(c->t_qa);
+  release(c->t_qb);
+  release(c->t_cnt);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   for (cudaEvent_t e : c->kev) cudaEventDestroy(e);
@@ -484,8 +562,8 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   if (!(p->energy_threshold_w >= 0.0f)) return fail(c, BT_E_INVALID, "energy_threshold_w must be >= 0");
   if (p->precision != BT_PREC_MIXED && p->precision != BT_PREC_FP32)
     return fail(c, BT_E_INVALID, "precision %d not implemented (BT_PREC_FP32 or BT_PREC_MIXED)", p->precision);
-  if (p->tiles_x != 1 || p->tiles_y != 1)
-    return fail(c, BT_E_INVALID, "tiles %dx%d: only 1x1 is implemented in this build", p->tiles_x, p->tiles_y);
+  if (p->tiles_x < 1 || p->tiles_y < 1 || p->tiles_x > BT_MAX_TILES || p->tiles_y > BT_MAX_TILES)
+    return fail(c, BT_E_INVALID, "tiles %dx%d not in 1..%d per axis", p->tiles_x, p->tiles_y, BT_MAX_TILES);
   if (p->chunk_beams < 0) return fail(c, BT_E_INVALID, "chunk_beams must be >= 0");
   int has_alpha = 0;
   float alpha_log2[BT_MAX_BANDS];
@@ -499,17 +577,41 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   cudaStream_t st = c->stream;
   const int64_t n_beams = (int64_t)20 << (2 * s->level);
   const int64_t total = s->n_src * n_beams;
+  const bool tiled = p->tiles_x * p->tiles_y > 1;
+  const int T = p->tiles_x * p->tiles_y;
   int64_t chunk = p->chunk_beams > 0 ? p->chunk_beams : ((int64_t)1 << 23) / (p->max_order + 1);
+  if (tiled && p->chunk_beams <= 0) {
+    // queues take 8 T bytes per lineage: keep all per-lineage buffers near 2 GiB
+    int64_t per = (int64_t)sizeof(bt::Seg) * (p->max_order + 1) + 4 * bt::kStateRows + 8 * (int64_t)T;
+    int64_t lim = ((int64_t)2 << 30) / per;
+    if (chunk > lim) chunk = lim;
+  }
   if (chunk > total) chunk = total;
   if (chunk < 1) chunk = 1;
   const unsigned long long cap = (unsigned long long)chunk * (p->max_order + 1);
   TRY(ensure(c, c->segs, sizeof(bt::Seg) * cap));
+  if (tiled) {
+    TRY(ensure_tiled(c, *s, p->tiles_x, p->tiles_y));
+    TRY(ensure(c, c->t_state, sizeof(uint32_t) * bt::kStateRows * (size_t)chunk));
+    TRY(ensure(c, c->t_qa, sizeof(int) * (size_t)T * (size_t)chunk));
+    TRY(ensure(c, c->t_qb, sizeof(int) * (size_t)T * (size_t)chunk));
+    TRY(ensure(c, c->t_cnt, sizeof(int) * 3 * (size_t)T));
+  }
   TRY(reset_counters(c));
   CK(cudaMemsetAsync(s->energy.p, 0, sizeof(double) * bt::kMaxBands * (size_t)s->n_mics, st));
   CK(cudaMemsetAsync(s->count.p, 0, sizeof(int) * (size_t)s->n_mics, st));
   bt::TraceArgs ta;
   memset(&ta, 0, sizeof(ta));
   ta.sc = dev_scene(*s);
+  if (tiled) {
+    ta.sc.n_tris = s->n_pairs;
+    ta.sc.nodes = (const bt::Node *)s->t_nodes.p;
+    ta.sc.tris = (const bt::Tri *)s->t_tris.p;
+    ta.sc.planes = (const bt::Plane *)s->t_planes.p;
+    ta.sc.planes64 = (const bt::Plane64 *)s->t_planes64.p;
+    ta.sc.planes_df = (const bt::PlaneDF *)s->t_planes_df.p;
+    ta.sc.root = 0;
+  }
   ta.src = (const float4 *)s->src.p;
   ta.power = (const float *)s->power.p;
   ta.n_src = s->n_src;
@@ -552,13 +654,41 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   for (int b = 0; b < BT_MAX_BANDS; b++) sa.alpha_log2[b] = alpha_log2[b];
   sa.has_alpha = has_alpha;
   sa.ctr = c->d_ctr;
-  // events bracket every launch: [4*i, 4*i+1] traversal, [4*i+2, 4*i+3] scatter
-  const int64_t n_chunks = total > 0 ? (total + chunk - 1) / chunk : 0;
-  while ((int64_t)c->kev.size() < 4 * n_chunks) {
-    cudaEvent_t e;
-    CK(cudaEventCreate(&e));
-    c->kev.push_back(e);
+  bt::TiledArgs tga;
+  memset(&tga, 0, sizeof(tga));
+  if (tiled) {
+    tga.tg = s->tg;
+    tga.n_tiles = T;
+    tga.roots = (const int *)s->t_roots.p;
+    tga.state = (uint32_t *)c->t_state.p;
+    tga.cap = (int)chunk;
   }
+  // Events bracket every launch; kind 0 traversal, 1 scatter.
+  struct Mark {
+    int ev, kind;
+  };
+  std::vector<Mark> marks;
+  int n_ev = 0;
+  auto mark = [&](int kind) -> int {
+    while ((int)c->kev.size() < n_ev + 1) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return BT_E_CUDA;
+      c->kev.push_back(e);
+    }
+    if (cudaEventRecord(c->kev[n_ev], st) != cudaSuccess) return BT_E_CUDA;
+    marks.push_back(Mark{n_ev, kind});
+    n_ev++;
+    return BT_OK;
+  };
+  auto scatter_round = [&]() -> int {
+    if (s->n_mics <= 0) return BT_OK;
+    TRY(mark(1));
+    CK(bt::launch_scatter(st, sa, c->n_sm));
+    return mark(1);
+  };
+  const int64_t n_chunks = total > 0 ? (total + chunk - 1) / chunk : 0;
+  int64_t n_trace_launches = 0, n_scatter_launches = 0, n_rounds = 0;
+  const int max_rounds = (p->max_order + 1) * (p->tiles_x + p->tiles_y + 2) + 8;
   CK(cudaEventRecord(c->ev0, st));
   for (int64_t ci = 0; ci < n_chunks; ci++) {
     int64_t b0 = ci * chunk;
@@ -566,13 +696,44 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
     ta.lineage_end = b0 + chunk < total ? b0 + chunk : total;
     CK(cudaMemsetAsync(c->d_seg_count, 0, sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(c->d_lineage_next, 0, sizeof(unsigned long long), st));
-    CK(cudaEventRecord(c->kev[4 * ci], st));
-    CK(bt::launch_trace(st, ta, c->n_sm));
-    CK(cudaEventRecord(c->kev[4 * ci + 1], st));
-    if (s->n_mics > 0) {
-      CK(cudaEventRecord(c->kev[4 * ci + 2], st));
-      CK(bt::launch_scatter(st, sa, c->n_sm));
-      CK(cudaEventRecord(c->kev[4 * ci + 3], st));
+    if (!tiled) {
+      TRY(mark(0));
+      CK(bt::launch_trace(st, ta, c->n_sm));
+      TRY(mark(0));
+      n_trace_launches++;
+      TRY(scatter_round());
+      n_scatter_launches += s->n_mics > 0;
+      continue;
+    }
+    // sub-domain rounds: round 0 on fresh lineages, then hand-offs
+    int *cnt = (int *)c->t_cnt.p;  // [0,T) in-counts, [T,2T) out-counts, [2T,3T) heads
+    int *qin = (int *)c->t_qa.p, *qout = (int *)c->t_qb.p;
+    int *cin = cnt, *cout = cnt + T;
+    for (int round = 0;; round++) {
+      if (round >= max_rounds) return fail(c, BT_E_TIMEOUT, "sub-domain exchange did not finish in %d rounds", max_rounds);
+      CK(cudaMemsetAsync(cout, 0, sizeof(int) * T, st));
+      CK(cudaMemsetAsync(cnt + 2 * T, 0, sizeof(int) * T, st));
+      if (round > 0) CK(cudaMemsetAsync(c->d_seg_count, 0, sizeof(unsigned long long), st));
+      tga.round = round;
+      tga.q_in = qin;
+      tga.q_in_count = cin;
+      tga.q_in_head = cnt + 2 * T;
+      tga.q_out = qout;
+      tga.q_out_count = cout;
+      TRY(mark(0));
+      CK(bt::launch_trace_tiled(st, ta, tga, c->n_sm));
+      TRY(mark(0));
+      n_trace_launches++;
+      n_rounds++;
+      TRY(scatter_round());
+      n_scatter_launches += s->n_mics > 0;
+      CK(cudaMemcpyAsync(c->h_tile_counts, cout, sizeof(int) * T, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      int64_t pending = 0;
+      for (int q = 0; q < T; q++) pending += c->h_tile_counts[q];
+      if (pending == 0) break;
+      std::swap(qin, qout);
+      std::swap(cin, cout);
     }
   }
   CK(cudaEventRecord(c->ev1, st));
@@ -580,14 +741,11 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   float ms = 0.0f;
   CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
   double trace_kms = 0.0, scatter_kms = 0.0;
-  for (int64_t ci = 0; ci < n_chunks; ci++) {
+  for (size_t q = 0; q + 1 < marks.size(); q += 2) {
     float a = 0.0f;
-    CK(cudaEventElapsedTime(&a, c->kev[4 * ci], c->kev[4 * ci + 1]));
-    trace_kms += a;
-    if (s->n_mics > 0) {
-      CK(cudaEventElapsedTime(&a, c->kev[4 * ci + 2], c->kev[4 * ci + 3]));
-      scatter_kms += a;
-    }
+    CK(cudaEventElapsedTime(&a, c->kev[marks[q].ev], c->kev[marks[q + 1].ev]));
+    if (marks[q].kind == 0) trace_kms += a;
+    else scatter_kms += a;
   }
   const bt::Counters &h = *c->h_ctr;
   bt_stats &o = s->stats;
@@ -601,11 +759,11 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   o.contributions = (int64_t)h.contributions;
   o.handoffs = (int64_t)h.handoffs;
   o.steals = (int64_t)h.steals;
-  o.rounds = (int64_t)h.rounds;
+  o.rounds = n_rounds;
   o.nodes_visited = (int64_t)h.nodes_visited;
   o.tris_tested = (int64_t)h.tris_tested;
-  o.trace_launches = n_chunks;
-  o.scatter_launches = s->n_mics > 0 ? n_chunks : 0;
+  o.trace_launches = n_trace_launches;
+  o.scatter_launches = n_scatter_launches;
   o.trace_ms = ms;
   o.trace_kernel_ms = trace_kms;
   o.scatter_kernel_ms = scatter_kms;

@@ -41,6 +41,31 @@ struct __align__(16) PlaneDF {
   float4 hi, lo;
 };
 
+// Sub-domain grid over the scene's xy box grown by 1 m: tx x ty tiles of
+// wx x wy, tile (ix, iy) = [gx0 + ix wx, gx0 + (ix+1) wx) x [...), half-open,
+// points outside clamped to the border tiles.
+struct TileGrid {
+  float gx0, gy0, wx, wy;
+  float gx1, gy1;
+  int tx, ty;
+};
+
+// Everything the tiled trace round needs besides TraceArgs.  Queues hold
+// lineage slots (0..cap-1 within the batch), one array of `cap` per tile.
+struct TiledArgs {
+  TileGrid tg;
+  int n_tiles;
+  const int *roots;         // [n_tiles] subtree root per tile (INT_MIN: empty tile)
+  uint32_t *state;          // lineage state, kStateRows rows of `cap` words
+  int cap;
+  const int *q_in;          // [n_tiles][cap] hand-offs to process this round
+  const int *q_in_count;    // [n_tiles]
+  int *q_in_head;           // [n_tiles] pop cursors
+  int *q_out;               // [n_tiles][cap] hand-offs for the next round
+  int *q_out_count;         // [n_tiles]
+  int round;                // 0: fresh lineages; > 0: hand-offs
+};
+
 struct DevScene {
   int64_t n_tris;
   int root;              // root child code: internal index >= 0, or ~leaf for one triangle (unused when n_tris == 0)
@@ -461,12 +486,20 @@ cudaError_t build_scene(cudaStream_t st, const float *d_verts, const int32_t *d_
                         Plane64 *d_planes64, PlaneDF *d_planes_df, void *d_scratch, size_t scratch_bytes,
                         const float *d_box, int *d_error);
 cudaError_t launch_beam_table(cudaStream_t st, int level, float *table);
+size_t build_tiled_scratch_bytes(int64_t n_src, int64_t n_pairs);
+cudaError_t tiled_count(cudaStream_t st, const Tri *src, int64_t n_src, const TileGrid &tg, uint32_t *offs);
+cudaError_t tiled_build(cudaStream_t st, const Tri *src, const Plane *sp, const Plane64 *sp64, const PlaneDF *spdf,
+                        int64_t n_src, const TileGrid &tg, const float *d_box, const uint32_t *offs, int64_t n_pairs,
+                        void *scratch, size_t scratch_bytes, Node *nodes, Tri *tris, Plane *planes,
+                        Plane64 *planes64, PlaneDF *planes_df, int *roots, int *d_error);
 size_t build_scene_scratch_bytes(int64_t n_tris);
 cudaError_t build_mics(cudaStream_t st, const float *d_pos, int64_t n_m, int side, MicGrid *d_grid,
                        float4 *d_sorted, int *d_cell_start, void *d_scratch, size_t scratch_bytes,
                        int *d_error);
 size_t build_mics_scratch_bytes(int64_t n_m, int side);
 cudaError_t launch_trace(cudaStream_t st, const TraceArgs &a, int n_sm);
+cudaError_t launch_trace_tiled(cudaStream_t st, const TraceArgs &a, const TiledArgs &t, int n_sm);
+constexpr int kStateRows = 56;
 cudaError_t launch_cast(cudaStream_t st, const DevScene &sc, const float *o, const float *d, const float *ns,
                         int64_t n, float t_eps, float *t_out, int *tri_out, int *err);
 cudaError_t launch_scatter(cudaStream_t st, const ScatterArgs &a, int n_sm);

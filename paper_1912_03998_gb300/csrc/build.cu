@@ -85,30 +85,35 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
 // xy extent exceeds 1/16 of the scene's (a ground sheet, a long roof).  The
 // flag makes the root split those few triangles into their own subtree, so
 // their scene-sized boxes do not enlarge the boxes above ordinary triangles.
-__global__ void k_morton(const float *verts, const int32_t *tris, int64_t n_tris, const float *box,
-                         uint32_t *keys, uint32_t *vals) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= n_tris) return;
-  float c[3], lo[3], hi[3];
-  for (int k = 0; k < 3; k++) {
-    float a = verts[3 * (int64_t)tris[3 * t] + k], b = verts[3 * (int64_t)tris[3 * t + 1] + k],
-          d = verts[3 * (int64_t)tris[3 * t + 2] + k];
-    c[k] = (a + b + d) * (1.0f / 3.0f);
-    lo[k] = fminf(fminf(a, b), d);
-    hi[k] = fmaxf(fmaxf(a, b), d);
-  }
+// One scale for all axes (the largest extent): a flat city then splits on x
+// and y far more often than on z.
+__device__ __forceinline__ uint32_t tri_key(float3 a, float3 b, float3 d, const float *box) {
+  float c[3] = {(a.x + b.x + d.x) * (1.0f / 3.0f), (a.y + b.y + d.y) * (1.0f / 3.0f),
+                (a.z + b.z + d.z) * (1.0f / 3.0f)};
+  float dx = fmaxf(fmaxf(a.x, b.x), d.x) - fminf(fminf(a.x, b.x), d.x);
+  float dy = fmaxf(fmaxf(a.y, b.y), d.y) - fminf(fminf(a.y, b.y), d.y);
   float scene_xy = fmaxf(box[3] - box[0], box[4] - box[1]);
-  bool large = fmaxf(hi[0] - lo[0], hi[1] - lo[1]) > scene_xy * (1.0f / 16.0f);
-  // one scale for all axes (the largest extent): a flat city then splits on
-  // x and y far more often than on z
-  float ext = fmaxf(fmaxf(box[3] - box[0], box[4] - box[1]), box[5] - box[2]);
+  bool large = fmaxf(dx, dy) > scene_xy * (1.0f / 16.0f);
+  float ext = fmaxf(scene_xy, box[5] - box[2]);
   uint32_t q[3];
   for (int k = 0; k < 3; k++) {
     float u = ext > 0.0f ? (c[k] - box[k]) / ext : 0.5f;
     u = fminf(fmaxf(u, 0.0f), 1.0f);
     q[k] = (uint32_t)fminf(u * 1024.0f, 1023.0f);
   }
-  keys[t] = (large ? (1u << 30) : 0u) | (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+  return (large ? (1u << 30) : 0u) | (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+}
+
+__global__ void k_morton(const float *verts, const int32_t *tris, int64_t n_tris, const float *box,
+                         uint32_t *keys, uint32_t *vals) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n_tris) return;
+  float3 v[3];
+  for (int k = 0; k < 3; k++) {
+    const float *p = verts + 3 * (int64_t)tris[3 * t + k];
+    v[k] = make_float3(p[0], p[1], p[2]);
+  }
+  keys[t] = tri_key(v[0], v[1], v[2], box);
   vals[t] = (uint32_t)t;
 }
 
@@ -243,9 +248,17 @@ __device__ __forceinline__ int lcp(const uint32_t *keys, int n, int i, int j) {
   if (a == b) return 32 + __clz((unsigned)(i ^ j));
   return __clz(a ^ b);
 }
+__device__ __forceinline__ int lcp(const unsigned long long *keys, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  unsigned long long a = keys[i], b = keys[j];
+  if (a == b) return 64 + __clz((unsigned)(i ^ j));
+  return __clzll(a ^ b);
+}
 
 // One thread per internal node: direction, range end and split (Karras 2012).
-__global__ void k_lbvh_topology(const uint32_t *keys, int n, Node *nodes, int *leaf_parent) {
+// child.w keeps the far end j of the node's key range [min(i,j), max(i,j)].
+template <typename K>
+__global__ void k_lbvh_topology(const K *keys, int n, Node *nodes, int *leaf_parent) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
   int d = (lcp(keys, n, i, i + 1) - lcp(keys, n, i, i - 1)) >= 0 ? 1 : -1;
@@ -268,6 +281,7 @@ __global__ void k_lbvh_topology(const uint32_t *keys, int n, Node *nodes, int *l
   int right = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
   nodes[i].child.x = left;
   nodes[i].child.y = right;
+  nodes[i].child.w = j;
   if (left < 0) leaf_parent[gamma] = i; else nodes[left].child.z = i;
   if (right < 0) leaf_parent[gamma + 1] = i; else nodes[right].child.z = i;
   if (i == 0) nodes[0].child.z = -1;
@@ -412,11 +426,175 @@ cudaError_t build_scene(cudaStream_t st, const float *d_verts, const int32_t *d_
                                          d_planes64, d_planes_df);
   note_launches(1);
   if (n >= 2) {
-    k_lbvh_topology<<<(n - 1 + threads - 1) / threads, threads, 0, st>>>(keys, n, d_nodes, leaf_parent);
+    k_lbvh_topology<uint32_t><<<(n - 1 + threads - 1) / threads, threads, 0, st>>>(keys, n, d_nodes, leaf_parent);
     cudaMemsetAsync(flags, 0, sizeof(unsigned) * m, st);
     k_lbvh_boxes<<<blocks, threads, 0, st>>>(d_tris_out, n, d_nodes, leaf_parent, aux, flags, d_error);
     note_launches(2);
   }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ sub-domains
+// Tiled hierarchy (Section 3: geometry split into sub-domains).  Every
+// (tile, triangle) pair whose xy boxes touch becomes a leaf; the leaves are
+// sorted by (tile, large flag, Morton code), so the leaves of one tile are
+// contiguous and form one subtree of the LBVH, whose root k_tile_roots finds.
+// Input: the scene's packed triangles (leaf order of the 1x1 hierarchy).
+__device__ __forceinline__ void tile_span(float lo, float hi, float g0, float w, int n, int &a, int &b) {
+  const float mg = 1e-3f;
+  a = clampi((int)floorf((lo - mg - g0) / w), 0, n - 1);
+  b = clampi((int)floorf((hi + mg - g0) / w), 0, n - 1);
+}
+
+__global__ void k_tile_count(const Tri *src, int n, TileGrid tg, uint32_t *counts) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  if (i == n) { counts[n] = 0; return; }
+  Tri t = src[i];
+  int x0, x1, y0, y1;
+  tile_span(fminf(fminf(t.v0.x, t.v1.x), t.v2.x), fmaxf(fmaxf(t.v0.x, t.v1.x), t.v2.x), tg.gx0, tg.wx, tg.tx, x0, x1);
+  tile_span(fminf(fminf(t.v0.y, t.v1.y), t.v2.y), fmaxf(fmaxf(t.v0.y, t.v1.y), t.v2.y), tg.gy0, tg.wy, tg.ty, y0, y1);
+  counts[i] = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+}
+
+__global__ void k_tile_emit(const Tri *src, int n, TileGrid tg, const float *box, const uint32_t *offs,
+                            uint32_t *pk, uint32_t *pt, uint32_t *psrc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Tri t = src[i];
+  int x0, x1, y0, y1;
+  tile_span(fminf(fminf(t.v0.x, t.v1.x), t.v2.x), fmaxf(fmaxf(t.v0.x, t.v1.x), t.v2.x), tg.gx0, tg.wx, tg.tx, x0, x1);
+  tile_span(fminf(fminf(t.v0.y, t.v1.y), t.v2.y), fmaxf(fmaxf(t.v0.y, t.v1.y), t.v2.y), tg.gy0, tg.wy, tg.ty, y0, y1);
+  uint32_t key = tri_key(f3(t.v0), f3(t.v1), f3(t.v2), box);
+  uint32_t p = offs[i];
+  for (int y = y0; y <= y1; y++)
+    for (int x = x0; x <= x1; x++, p++) {
+      pk[p] = key;
+      pt[p] = (uint32_t)(y * tg.tx + x);
+      psrc[p] = (uint32_t)i;
+    }
+}
+
+__global__ void k_iota(uint32_t *v, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = (uint32_t)i;
+}
+
+__global__ void k_gather_u32(const uint32_t *in, const uint32_t *idx, uint32_t *out, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[idx[i]];
+}
+
+__global__ void k_tile_keys(const uint32_t *pk, const uint32_t *pt, const uint32_t *psrc, const uint32_t *perm,
+                            int n, unsigned long long *key64, uint32_t *order_src) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t p = perm[i];
+  key64[i] = ((unsigned long long)pt[p] << 31) | pk[p];
+  order_src[i] = psrc[p];
+}
+
+__global__ void k_pack_from_src(const Tri *src, const Plane *sp, const Plane64 *sp64, const PlaneDF *spdf,
+                                const uint32_t *order_src, int n, Tri *out, Plane *planes, Plane64 *planes64,
+                                PlaneDF *planes_df) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t s = order_src[i];
+  out[i] = src[s];
+  planes[i] = sp[s];
+  planes64[i] = sp64[s];
+  planes_df[i] = spdf[s];
+}
+
+__global__ void k_fill_i32(int *v, int n, int value) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = value;
+}
+
+// Root of each tile's subtree: the internal node whose key range is exactly
+// the tile's run of leaves, or ~leaf for a tile with one leaf.
+__global__ void k_tile_roots(const unsigned long long *key64, const Node *nodes, int n, int *roots) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  auto tile = [&](int k) { return (int)(key64[k] >> 31); };
+  int lo, hi;
+  if (i < n - 1) {
+    int j = nodes[i].child.w;
+    lo = i < j ? i : j;
+    hi = i < j ? j : i;
+    int tl = tile(lo);
+    if (tile(hi) == tl && (lo == 0 || tile(lo - 1) != tl) && (hi == n - 1 || tile(hi + 1) != tl)) roots[tl] = i;
+  }
+  // single-leaf tiles
+  int ti = tile(i);
+  if ((i == 0 || tile(i - 1) != ti) && (i == n - 1 || tile(i + 1) != ti)) roots[ti] = ~i;
+}
+
+size_t build_tiled_scratch_bytes(int64_t n_src, int64_t n_pairs) {
+  size_t a = (size_t)(n_src + 1), p = (size_t)(n_pairs > 0 ? n_pairs : 1);
+  return align256(4 * a) + 7 * align256(4 * p) + align256(4 * rs_hist_entries((int)p)) + align256(8 * p) +
+         align256(4 * p) + align256(24 * p) + align256(4 * p);
+}
+
+// Phase 1: pairs per source triangle and their exclusive offsets; offs[n_src]
+// is the number of pairs.  `offs` is n_src + 1 entries of scratch.
+cudaError_t tiled_count(cudaStream_t st, const Tri *src, int64_t n_src, const TileGrid &tg, uint32_t *offs) {
+  int n = (int)n_src;
+  k_tile_count<<<(n + 1 + 255) / 256, 256, 0, st>>>(src, n, tg, offs);
+  k_scan_excl<<<1, 1024, 0, st>>>(offs, n + 1);
+  note_launches(2);
+  return cudaGetLastError();
+}
+
+// Phase 2, once the host knows n_pairs: sort the pairs, build the LBVH over
+// them, pack the leaves and find the tile roots.
+cudaError_t tiled_build(cudaStream_t st, const Tri *src, const Plane *sp, const Plane64 *sp64, const PlaneDF *spdf,
+                        int64_t n_src, const TileGrid &tg, const float *d_box, const uint32_t *offs, int64_t n_pairs,
+                        void *scratch, size_t scratch_bytes, Node *nodes, Tri *tris, Plane *planes,
+                        Plane64 *planes64, PlaneDF *planes_df, int *roots, int *d_error) {
+  if (scratch_bytes < build_tiled_scratch_bytes(n_src, n_pairs)) return cudaErrorInvalidValue;
+  int n = (int)n_src, P = (int)n_pairs, T = tg.tx * tg.ty;
+  char *s = (char *)scratch + align256(4 * (size_t)(n_src + 1));
+  size_t p4 = align256(4 * (size_t)P);
+  uint32_t *pk = (uint32_t *)s; s += p4;
+  uint32_t *pt = (uint32_t *)s; s += p4;
+  uint32_t *psrc = (uint32_t *)s; s += p4;
+  uint32_t *ka = (uint32_t *)s; s += p4;
+  uint32_t *va = (uint32_t *)s; s += p4;
+  uint32_t *kb = (uint32_t *)s; s += p4;
+  uint32_t *vb = (uint32_t *)s; s += p4;
+  uint32_t *hist = (uint32_t *)s; s += align256(4 * rs_hist_entries(P));
+  unsigned long long *key64 = (unsigned long long *)s; s += align256(8 * (size_t)P);
+  int *leaf_parent = (int *)s; s += p4;
+  float *aux = (float *)s; s += align256(24 * (size_t)P);
+  unsigned *flags = (unsigned *)s;
+  const int th = 256, bp = (P + th - 1) / th;
+  k_fill_i32<<<(T + th - 1) / th, th, 0, st>>>(roots, T, (int)0x80000000);
+  k_tile_emit<<<(n + th - 1) / th, th, 0, st>>>(src, n, tg, d_box, offs, pk, pt, psrc);
+  // sort by (large flag, Morton) and then, stably, by tile
+  cudaMemcpyAsync(ka, pk, sizeof(uint32_t) * P, cudaMemcpyDeviceToDevice, st);
+  k_iota<<<bp, th, 0, st>>>(va, P);
+  note_launches(3);
+  cudaError_t e = radix_sort(st, ka, va, kb, vb, hist, P, 31);
+  if (e != cudaSuccess) return e;
+  k_gather_u32<<<bp, th, 0, st>>>(pt, va, ka, P);
+  note_launches(1);
+  int tbits = 1;
+  while ((1 << tbits) < T) tbits++;
+  e = radix_sort(st, ka, va, kb, vb, hist, P, tbits);
+  if (e != cudaSuccess) return e;
+  k_tile_keys<<<bp, th, 0, st>>>(pk, pt, psrc, va, P, key64, kb);
+  k_pack_from_src<<<bp, th, 0, st>>>(src, sp, sp64, spdf, kb, P, tris, planes, planes64, planes_df);
+  note_launches(2);
+  if (P >= 2) {
+    k_lbvh_topology<unsigned long long><<<(P - 1 + th - 1) / th, th, 0, st>>>(key64, P, nodes, leaf_parent);
+    cudaMemsetAsync(flags, 0, sizeof(unsigned) * P, st);
+    k_lbvh_boxes<<<bp, th, 0, st>>>(tris, P, nodes, leaf_parent, aux, flags, d_error);
+    note_launches(2);
+  }
+  k_tile_roots<<<bp, th, 0, st>>>(key64, nodes, P, roots);
+  note_launches(1);
+  (void)n;
   return cudaGetLastError();
 }
 

@@ -151,15 +151,23 @@ struct RaySrc {
 // lowest original triangle id.  With kMixed, `rs` gives the float-pair ray
 // that the float32 ray `r` rounds, read only on the rare float64 paths.
 // Returns the leaf slot or -1.
+// Tile of an xy point, as the definition forms it: floor((x - gx0) /
+// (gx1 - gx0) * tx), clamped to the grid.
+__device__ __forceinline__ int tile_ix(double x, double g0, double g1, int n) {
+  return clampi((int)floor((x - g0) / (g1 - g0) * n), 0, n - 1);
+}
+
 template <bool kMixed, bool kCount>
 __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, RaySrc rs, double dns64, Best &best,
-                                           int *err, unsigned long long &n_nodes, unsigned long long &n_tris) {
+                                           int *err, unsigned long long &n_nodes, unsigned long long &n_tris,
+                                           int root, const TileGrid *tf = nullptr, int tile = 0) {
   best.t = kInf;
   best.slot = -1;
   best.id = 0x7fffffff;
   best.t64 = 0.0;
   best.has64 = false;
-  if (sc.n_tris == 0) return -1;
+  if (sc.n_tris == 0 || root == (int)0x80000000) return -1;
+  const int tile_x = tf ? tile % tf->tx : 0, tile_y = tf ? tile / tf->tx : 0;
   // candidate evaluation (one call site, so the code is emitted once)
   auto consider = [&](int slot) {
     if (kCount) n_tris++;
@@ -180,6 +188,22 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, Ray
       t = (float)tt;
     } else {
       if (!(t < kInf && accept_hit(r, t))) return;
+    }
+    if (tf) {
+      // sub-domain: the hit point must lie in this tile (half-open); near a
+      // tile border the point is formed in float64 in MIXED mode
+      float hx = r.o.x + t * r.d.x, hy = r.o.y + t * r.d.y;
+      float ux = (hx - tf->gx0) / tf->wx, uy = (hy - tf->gy0) / tf->wy;
+      int ix = clampi((int)floorf(ux), 0, tf->tx - 1), iy = clampi((int)floorf(uy), 0, tf->ty - 1);
+      bool near = fabsf(ux - rintf(ux)) < 1e-3f || fabsf(uy - rintf(uy)) < 1e-3f;
+      if (kMixed && near) {
+        double3 o, d;
+        rs.get(o, d);
+        double tt = has64 ? t64 : plane_t64(sc, slot, o, d);
+        ix = tile_ix(o.x + tt * d.x, tf->gx0, tf->gx1, tf->tx);
+        iy = tile_ix(o.y + tt * d.y, tf->gy0, tf->gy1, tf->ty);
+      }
+      if (ix != tile_x || iy != tile_y) return;
     }
     int id = __float_as_int(v1.w);
     if (!kMixed) {
@@ -209,7 +233,7 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, Ray
   };
   int stack[kStackDepth];
   int sp = 0;
-  int node = sc.root;
+  int node = root;
   // a well-formed BVH is visited at most once per node; the bound only
   // guarantees termination should the structure ever be malformed
   int64_t visits = 0;
@@ -340,6 +364,208 @@ __device__ __forceinline__ void st_f3(LineageSmem<kMixed> &sm, int row, int t, f
   sm.hi[row + 2][t] = v.z;
 }
 
+// Start lineage `lin` (source si, beam bi) in this thread's column.
+template <bool kMixed>
+__device__ __forceinline__ void init_lineage(const TraceArgs &a, LineageSmem<kMixed> &sm, int t, int64_t lin) {
+  const int nb = a.sc.n_bands;
+  int64_t si = lin / a.n_beams, bi = lin - si * a.n_beams;
+  float4 s4 = __ldg(&a.src[si]);
+  float3 A = make_float3(s4.x, s4.y, s4.z);
+  if (kMixed) {
+    // table: 9 normal components then the 3 axis components, hi parts
+    // first, lo parts 12 floats later
+    const float *bt = a.beam_table + 24 * bi;
+    for (int q = 0; q < 9; q++) {
+      sm.hi[kRowN + q][t] = __ldg(bt + q);
+      sm.lo[kRowN + q][t] = __ldg(bt + 12 + q);
+    }
+    for (int q = 0; q < 3; q++) {
+      sm.hi[kRowD + q][t] = __ldg(bt + 9 + q);
+      sm.lo[kRowD + q][t] = __ldg(bt + 21 + q);
+      sm.lo[kRowA + q][t] = 0.0f;
+      sm.lo[kRowO + q][t] = 0.0f;
+    }
+  } else {
+    float3 d0, d1, d2;
+    beam_dirs<float>(a.level, bi, d0, d1, d2);
+    st_f3(sm, kRowN, t, cross_exact(d0, d1));
+    st_f3(sm, kRowN + 3, t, cross_exact(d1, d2));
+    st_f3(sm, kRowN + 6, t, cross_exact(d2, d0));
+    st_f3(sm, kRowD, t, normalize3((d0 + d1) + d2));
+  }
+  st_f3(sm, kRowA, t, A);
+  st_f3(sm, kRowO, t, A);
+#pragma unroll
+  for (int b = 0; b < kMaxBands; b++) sm.p[b][t] = b < nb ? __ldg(&a.power[si * nb + b]) : 0.0f;
+  sm.st[0][t] = 0.0f;
+  sm.st[1][t] = 0.0f;
+  sm.st[2][t] = 0.0f;
+  sm.st[3][t] = -kInf;
+}
+
+// Per-lane scalars of a lineage besides its shared-memory column.
+struct LaneState {
+  int64_t lin;
+  int k, start_slot;
+  float dns;
+  double dns64;
+};
+
+struct TraceCounts {
+  unsigned long long seg, hit, esc, emit, nodes, tris, hand, steal;
+};
+
+// A segment is resolved: its axis ray hit triangle `slot` (or escaped, slot
+// < 0).  Write the segment record and, if the beam goes on, reflect it: the
+// image source (Section 2), mirrored cone and axis, energy lost at the
+// reflection.  Returns true if the lineage continues.
+template <bool kMixed>
+__device__ __forceinline__ bool finish_segment(const TraceArgs &a, LineageSmem<kMixed> &sm, int t, const Ray &r,
+                                               const Best &best, int slot, LaneState &ls, const MicGrid &g,
+                                               TraceCounts &cn) {
+  const int nb = a.sc.n_bands;
+  cn.seg++;
+  float4 end = make_float4(0.0f, 0.0f, 0.0f, -kInf);
+  float4 v0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  float4 plf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  if (slot >= 0) {
+    cn.hit++;
+    v0 = __ldg(&a.sc.tris[slot].v0);
+    plf = __ldg(&a.sc.planes[slot]);
+    // end plane on the incident side, offset relative to the apex
+    float3 pn = f3(plf);
+    float3 en = dot3(pn, r.d) < 0.0f ? pn : pn * -1.0f;
+    float ew;
+    if (kMixed) ew = df3_dot(mkdf3(en), df3_sub(mkdf3(f3(v0)), ld_df3(sm, kRowA, t))).hi;
+    else ew = dot3(en, f3(v0) - ld_hi3(sm, kRowA, t));
+    end = make_float4(en.x, en.y, en.z, ew);
+  } else {
+    cn.esc++;
+  }
+  {
+    Seg s;
+    for (int q = 0; q < 3; q++) {
+      s.ahi[q] = sm.hi[kRowA + q][t];
+      s.alo[q] = kMixed ? sm.lo[kRowA + q][t] : 0.0f;
+    }
+    float3 n0 = ld_hi3(sm, kRowN, t), n1 = ld_hi3(sm, kRowN + 3, t), n2 = ld_hi3(sm, kRowN + 6, t);
+    s.n0 = make_float4(n0.x, n0.y, n0.z, __int_as_float(ls.start_slot));
+    s.n1 = make_float4(n1.x, n1.y, n1.z, __int_as_float(slot));
+    s.n2 = make_float4(n2.x, n2.y, n2.z, __int_as_float(ls.k));
+    for (int q = 0; q < 9; q++) s.nlo[q] = kMixed ? sm.lo[kRowN + q][t] : 0.0f;
+    s.pad[0] = s.pad[1] = s.pad[2] = 0.0f;
+    s.start = make_float4(sm.st[0][t], sm.st[1][t], sm.st[2][t], sm.st[3][t]);
+    s.end = end;
+    s.p03 = make_float4(sm.p[0][t], sm.p[1][t], sm.p[2][t], sm.p[3][t]);
+    s.p47 = make_float4(sm.p[4][t], sm.p[5][t], sm.p[6][t], sm.p[7][t]);
+    s.cy0 = 0;
+    s.cy1 = -1;
+    emit_segment(a, s, g.n_mics > 0 && may_reach_slab(n0, n1, n2, s.ahi[2], g), cn.emit);
+  }
+  if (slot < 0 || ls.k == a.max_order) return false;
+  // energy lost at the reflection
+  int mat = __float_as_int(v0.w);
+  float wmax = 0.0f;
+#pragma unroll
+  for (int b = 0; b < kMaxBands; b++) {
+    float p = sm.p[b][t];
+    if (b < nb) p *= __ldg(&a.sc.refl[mat * nb + b]);
+    sm.p[b][t] = p;
+    wmax = fmaxf(wmax, p);
+  }
+  if (a.energy_threshold > 0.0f && wmax < a.energy_threshold) return false;
+  // Image source: mirror the apex, the cone and the axis in the hit plane;
+  // the reflected beam starts at the hit point on that plane.
+  float3 pn = f3(plf), pv0 = f3(v0);
+  float3 Dn;
+  if (kMixed) {
+    PlaneDF pd = a.sc.planes_df[slot];
+    df3 n = df3{df{pd.hi.x, pd.lo.x}, df{pd.hi.y, pd.lo.y}, df{pd.hi.z, pd.lo.z}};
+    df w = df{pd.hi.w, pd.lo.w};
+    df3 A = ld_df3(sm, kRowA, t), O = ld_df3(sm, kRowO, t), D = ld_df3(sm, kRowD, t);
+    df th = best.has64 ? d_to_df(best.t64) : df_div(df_sub(w, df3_dot(n, O)), df3_dot(n, D));
+    df3 H = df3_add(O, df3_scale(D, th));
+    df da = df3_dot(df3_sub(A, mkdf3(pv0)), n);
+    A = df3_sub(A, df3_scale(n, df{2.0f * da.hi, 2.0f * da.lo}));
+    st_df3(sm, kRowA, t, A);
+#pragma unroll
+    for (int j = 0; j < 3; j++) st_df3(sm, kRowN + 3 * j, t, df3_mirror(ld_df3(sm, kRowN + 3 * j, t), n));
+    D = df3_mirror(D, n);
+    st_df3(sm, kRowO, t, H);
+    st_df3(sm, kRowD, t, D);
+    df dn = df3_dot(n, D);
+    ls.dns64 = fabs((double)dn.hi + (double)dn.lo);
+    ls.dns = (float)ls.dns64;
+    Dn = df3_hi(D);
+    float3 sn = dot3(pn, Dn) > 0.0f ? pn : pn * -1.0f;
+    float sw = df3_dot(mkdf3(sn), df3_sub(mkdf3(pv0), A)).hi;
+    sm.st[0][t] = sn.x; sm.st[1][t] = sn.y; sm.st[2][t] = sn.z; sm.st[3][t] = sw;
+  } else {
+    float3 A = ld_hi3(sm, kRowA, t), O = ld_hi3(sm, kRowO, t), D = ld_hi3(sm, kRowD, t);
+    A = A - pn * (2.0f * dot3(A - pv0, pn));
+    st_f3(sm, kRowA, t, A);
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      float3 nj = ld_hi3(sm, kRowN + 3 * j, t);
+      st_f3(sm, kRowN + 3 * j, t, nj - pn * (2.0f * dot3(nj, pn)));
+    }
+    float3 H = O + D * best.t;
+    Dn = D - pn * (2.0f * dot3(D, pn));
+    st_f3(sm, kRowO, t, H);
+    st_f3(sm, kRowD, t, Dn);
+    ls.dns = fabsf(dot3(pn, Dn));
+    ls.dns64 = 0.0;
+    float3 sn = dot3(pn, Dn) > 0.0f ? pn : pn * -1.0f;
+    float sw = dot3(sn, pv0 - A);
+    sm.st[0][t] = sn.x; sm.st[1][t] = sn.y; sm.st[2][t] = sn.z; sm.st[3][t] = sw;
+  }
+  ls.start_slot = slot;
+  ls.k++;
+  return true;
+}
+
+__device__ __forceinline__ void flush_counts(const TraceArgs &a, TraceCounts &cn, bool count_work) {
+  for (int o = 16; o > 0; o >>= 1) {
+    cn.seg += __shfl_xor_sync(0xffffffffu, cn.seg, o);
+    cn.hit += __shfl_xor_sync(0xffffffffu, cn.hit, o);
+    cn.esc += __shfl_xor_sync(0xffffffffu, cn.esc, o);
+    cn.emit += __shfl_xor_sync(0xffffffffu, cn.emit, o);
+    cn.hand += __shfl_xor_sync(0xffffffffu, cn.hand, o);
+    cn.steal += __shfl_xor_sync(0xffffffffu, cn.steal, o);
+    if (count_work) {
+      cn.nodes += __shfl_xor_sync(0xffffffffu, cn.nodes, o);
+      cn.tris += __shfl_xor_sync(0xffffffffu, cn.tris, o);
+    }
+  }
+  if (lane_id() == 0) {
+    if (count_work) {
+      atomicAdd(&a.ctr->nodes_visited, cn.nodes);
+      atomicAdd(&a.ctr->tris_tested, cn.tris);
+    }
+    atomicAdd(&a.ctr->segments, cn.seg);
+    atomicAdd(&a.ctr->hits, cn.hit);
+    atomicAdd(&a.ctr->escapes, cn.esc);
+    atomicAdd(&a.ctr->emitted, cn.emit);
+    if (cn.hand) atomicAdd(&a.ctr->handoffs, cn.hand);
+    if (cn.steal) atomicAdd(&a.ctr->steals, cn.steal);
+  }
+}
+
+// Take the next lineage of the batch for every lane in `need` (warp-vote
+// refill).  Returns the lineage index or -1 when the batch is used up.
+__device__ __forceinline__ int64_t take_lineage(const TraceArgs &a, bool need) {
+  unsigned nm = __ballot_sync(0xffffffffu, need);
+  if (!nm) return -1;
+  const unsigned lane = lane_id();
+  int leader = __ffs(nm) - 1;
+  unsigned long long base = 0;
+  if ((int)lane == leader) base = atomicAdd(a.lineage_next, (unsigned long long)__popc(nm));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (!need) return -1;
+  int64_t mine = a.lineage_begin + (int64_t)(base + __popc(nm & ((1u << lane) - 1u)));
+  return mine < a.lineage_end ? mine : -1;
+}
+
 // Persistent warps: every lane works on one lineage at a time and takes the
 // next one from a global counter as soon as its lineage ends, so a warp stays
 // full until the batch runs out (warp-vote refill of finished lanes).
@@ -347,199 +573,208 @@ template <bool kMixed, bool kCount>
 __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
   __shared__ LineageSmem<kMixed> sm;
   const int t = threadIdx.x;
-  const unsigned lane = lane_id();
   const MicGrid g = *a.grid;
-  const int nb = a.sc.n_bands;
-  unsigned long long n_seg = 0, n_hit = 0, n_esc = 0, n_emit = 0, n_nodes = 0, n_tris = 0;
-  int64_t lin = -1;
-  int k = 0, start_slot = -1;
-  float dns = 0.0f;
-  double dns64 = 0.0;
+  TraceCounts cn = {0, 0, 0, 0, 0, 0, 0, 0};
+  LaneState ls = {-1, 0, -1, 0.0f, 0.0};
   bool done = false;
   const RaySrc rs{&sm.hi[kRowO][t], kMixed ? &sm.lo[kRowO][t] : &sm.hi[kRowO][t], kTraceThreads};
   while (true) {
-    // refill lanes whose lineage ended
-    bool need = !done && lin < 0;
-    unsigned nm = __ballot_sync(0xffffffffu, need);
-    if (nm) {
-      int leader = __ffs(nm) - 1;
-      unsigned long long base = 0;
-      if ((int)lane == leader) base = atomicAdd(a.lineage_next, (unsigned long long)__popc(nm));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (need) {
-        int64_t mine = a.lineage_begin + (int64_t)(base + __popc(nm & ((1u << lane) - 1u)));
-        if (mine < a.lineage_end) {
-          lin = mine;
-          int64_t si = lin / a.n_beams, bi = lin - si * a.n_beams;
-          float4 s4 = __ldg(&a.src[si]);
-          float3 A = make_float3(s4.x, s4.y, s4.z);
-          if (kMixed) {
-            // table: 9 normal components then the 3 axis components, hi
-            // parts first, lo parts 12 floats later
-            const float *bt = a.beam_table + 24 * bi;
-            for (int q = 0; q < 9; q++) {
-              sm.hi[kRowN + q][t] = __ldg(bt + q);
-              sm.lo[kRowN + q][t] = __ldg(bt + 12 + q);
-            }
-            for (int q = 0; q < 3; q++) {
-              sm.hi[kRowD + q][t] = __ldg(bt + 9 + q);
-              sm.lo[kRowD + q][t] = __ldg(bt + 21 + q);
-              sm.lo[kRowA + q][t] = 0.0f;
-              sm.lo[kRowO + q][t] = 0.0f;
-            }
-          } else {
-            float3 d0, d1, d2;
-            beam_dirs<float>(a.level, bi, d0, d1, d2);
-            st_f3(sm, kRowN, t, cross_exact(d0, d1));
-            st_f3(sm, kRowN + 3, t, cross_exact(d1, d2));
-            st_f3(sm, kRowN + 6, t, cross_exact(d2, d0));
-            st_f3(sm, kRowD, t, normalize3((d0 + d1) + d2));
-          }
-          st_f3(sm, kRowA, t, A);
-          st_f3(sm, kRowO, t, A);
-#pragma unroll
-          for (int b = 0; b < kMaxBands; b++) sm.p[b][t] = b < nb ? __ldg(&a.power[si * nb + b]) : 0.0f;
-          sm.st[0][t] = 0.0f; sm.st[1][t] = 0.0f; sm.st[2][t] = 0.0f; sm.st[3][t] = -kInf;
-          k = 0;
-          start_slot = -1;
-          dns = 0.0f;
-          dns64 = 0.0;
-        } else {
-          done = true;
-        }
+    bool need = !done && ls.lin < 0;
+    int64_t mine = take_lineage(a, need);
+    if (need) {
+      if (mine >= 0) {
+        ls = LaneState{mine, 0, -1, 0.0f, 0.0};
+        init_lineage(a, sm, t, mine);
+      } else {
+        done = true;
       }
     }
     if (__all_sync(0xffffffffu, done)) break;
     if (done) continue;
     // ---- one segment of this lane's lineage
-    const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), a.t_eps, dns);
+    const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), a.t_eps, ls.dns);
     Best best;
-    int slot = closest_hit<kMixed, kCount>(a.sc, r, rs, dns64, best, &a.ctr->error, n_nodes, n_tris);
-    n_seg++;
-    float4 end = make_float4(0.0f, 0.0f, 0.0f, -kInf);
-    float4 v0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    float4 plf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (slot >= 0) {
-      n_hit++;
-      v0 = __ldg(&a.sc.tris[slot].v0);
-      plf = __ldg(&a.sc.planes[slot]);
-      // end plane on the incident side, offset relative to the apex
-      float3 pn = f3(plf);
-      float3 en = dot3(pn, r.d) < 0.0f ? pn : pn * -1.0f;
-      float ew;
-      if (kMixed) ew = df3_dot(mkdf3(en), df3_sub(mkdf3(f3(v0)), ld_df3(sm, kRowA, t))).hi;
-      else ew = dot3(en, f3(v0) - ld_hi3(sm, kRowA, t));
-      end = make_float4(en.x, en.y, en.z, ew);
-    } else {
-      n_esc++;
-    }
-    {
-      Seg s;
-      for (int q = 0; q < 3; q++) {
-        s.ahi[q] = sm.hi[kRowA + q][t];
-        s.alo[q] = kMixed ? sm.lo[kRowA + q][t] : 0.0f;
-      }
-      float3 n0 = ld_hi3(sm, kRowN, t), n1 = ld_hi3(sm, kRowN + 3, t), n2 = ld_hi3(sm, kRowN + 6, t);
-      s.n0 = make_float4(n0.x, n0.y, n0.z, __int_as_float(start_slot));
-      s.n1 = make_float4(n1.x, n1.y, n1.z, __int_as_float(slot));
-      s.n2 = make_float4(n2.x, n2.y, n2.z, __int_as_float(k));
-      for (int q = 0; q < 9; q++) s.nlo[q] = kMixed ? sm.lo[kRowN + q][t] : 0.0f;
-      s.pad[0] = s.pad[1] = s.pad[2] = 0.0f;
-      s.start = make_float4(sm.st[0][t], sm.st[1][t], sm.st[2][t], sm.st[3][t]);
-      s.end = end;
-      s.p03 = make_float4(sm.p[0][t], sm.p[1][t], sm.p[2][t], sm.p[3][t]);
-      s.p47 = make_float4(sm.p[4][t], sm.p[5][t], sm.p[6][t], sm.p[7][t]);
-      s.cy0 = 0;
-      s.cy1 = -1;
-      emit_segment(a, s, g.n_mics > 0 && may_reach_slab(n0, n1, n2, s.ahi[2], g), n_emit);
-    }
-    bool ends = slot < 0 || k == a.max_order;
-    if (!ends) {
-      // energy lost at the reflection
-      int mat = __float_as_int(v0.w);
-      float wmax = 0.0f;
-#pragma unroll
-      for (int b = 0; b < kMaxBands; b++) {
-        float p = sm.p[b][t];
-        if (b < nb) p *= __ldg(&a.sc.refl[mat * nb + b]);
-        sm.p[b][t] = p;
-        wmax = fmaxf(wmax, p);
-      }
-      if (a.energy_threshold > 0.0f && wmax < a.energy_threshold) ends = true;
-    }
-    if (!ends) {
-      // Image source: mirror the apex, the cone and the axis in the hit
-      // plane; the reflected beam starts at the hit point on that plane.
-      float3 pn = f3(plf), pv0 = f3(v0);
-      float3 Dn;
-      if (kMixed) {
-        PlaneDF pd = a.sc.planes_df[slot];
-        df3 n = df3{df{pd.hi.x, pd.lo.x}, df{pd.hi.y, pd.lo.y}, df{pd.hi.z, pd.lo.z}};
-        df w = df{pd.hi.w, pd.lo.w};
-        df3 A = ld_df3(sm, kRowA, t), O = ld_df3(sm, kRowO, t), D = ld_df3(sm, kRowD, t);
-        df th = best.has64 ? d_to_df(best.t64) : df_div(df_sub(w, df3_dot(n, O)), df3_dot(n, D));
-        df3 H = df3_add(O, df3_scale(D, th));
-        df da = df3_dot(df3_sub(A, mkdf3(pv0)), n);
-        A = df3_sub(A, df3_scale(n, df{2.0f * da.hi, 2.0f * da.lo}));
-        st_df3(sm, kRowA, t, A);
-#pragma unroll
-        for (int j = 0; j < 3; j++) st_df3(sm, kRowN + 3 * j, t, df3_mirror(ld_df3(sm, kRowN + 3 * j, t), n));
-        D = df3_mirror(D, n);
-        st_df3(sm, kRowO, t, H);
-        st_df3(sm, kRowD, t, D);
-        df dn = df3_dot(n, D);
-        dns64 = fabs((double)dn.hi + (double)dn.lo);
-        dns = (float)dns64;
-        Dn = df3_hi(D);
-        float3 sn = dot3(pn, Dn) > 0.0f ? pn : pn * -1.0f;
-        float sw = df3_dot(mkdf3(sn), df3_sub(mkdf3(pv0), A)).hi;
-        sm.st[0][t] = sn.x; sm.st[1][t] = sn.y; sm.st[2][t] = sn.z; sm.st[3][t] = sw;
-      } else {
-        float3 A = ld_hi3(sm, kRowA, t), O = ld_hi3(sm, kRowO, t), D = ld_hi3(sm, kRowD, t);
-        A = A - pn * (2.0f * dot3(A - pv0, pn));
-        st_f3(sm, kRowA, t, A);
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-          float3 nj = ld_hi3(sm, kRowN + 3 * j, t);
-          st_f3(sm, kRowN + 3 * j, t, nj - pn * (2.0f * dot3(nj, pn)));
+    int slot = closest_hit<kMixed, kCount>(a.sc, r, rs, ls.dns64, best, &a.ctr->error, cn.nodes, cn.tris,
+                                           a.sc.root);
+    if (!finish_segment(a, sm, t, r, best, slot, ls, g, cn)) ls.lin = -1;
+  }
+  flush_counts(a, cn, kCount);
+}
+
+// --------------------------------------------------------------- sub-domains
+// Lineage state saved to global memory at a hand-off (rows of `cap` words).
+template <bool kMixed>
+__device__ __forceinline__ void save_state(const TiledArgs &ta, const LineageSmem<kMixed> &sm, int t, int slot,
+                                           const LaneState &ls) {
+  uint32_t *S = ta.state + slot;
+  const size_t c = (size_t)ta.cap;
+  for (int q = 0; q < kRows; q++) S[q * c] = __float_as_uint(sm.hi[q][t]);
+  if (kMixed)
+    for (int q = 0; q < kRows; q++) S[(kRows + q) * c] = __float_as_uint(sm.lo[q][t]);
+  for (int b = 0; b < kMaxBands; b++) S[(36 + b) * c] = __float_as_uint(sm.p[b][t]);
+  for (int q = 0; q < 4; q++) S[(44 + q) * c] = __float_as_uint(sm.st[q][t]);
+  S[48 * c] = (uint32_t)(ls.lin & 0xffffffffu);
+  S[49 * c] = (uint32_t)(ls.lin >> 32);
+  S[50 * c] = (uint32_t)ls.k;
+  S[51 * c] = (uint32_t)ls.start_slot;
+  S[52 * c] = __float_as_uint(ls.dns);
+  unsigned long long d = __double_as_longlong(ls.dns64);
+  S[53 * c] = (uint32_t)(d & 0xffffffffu);
+  S[54 * c] = (uint32_t)(d >> 32);
+}
+
+template <bool kMixed>
+__device__ __forceinline__ void load_state(const TiledArgs &ta, LineageSmem<kMixed> &sm, int t, int slot,
+                                           LaneState &ls) {
+  const uint32_t *S = ta.state + slot;
+  const size_t c = (size_t)ta.cap;
+  for (int q = 0; q < kRows; q++) sm.hi[q][t] = __uint_as_float(S[q * c]);
+  if (kMixed)
+    for (int q = 0; q < kRows; q++) sm.lo[q][t] = __uint_as_float(S[(kRows + q) * c]);
+  for (int b = 0; b < kMaxBands; b++) sm.p[b][t] = __uint_as_float(S[(36 + b) * c]);
+  for (int q = 0; q < 4; q++) sm.st[q][t] = __uint_as_float(S[(44 + q) * c]);
+  ls.lin = (int64_t)S[48 * c] | ((int64_t)S[49 * c] << 32);
+  ls.k = (int)S[50 * c];
+  ls.start_slot = (int)S[51 * c];
+  ls.dns = __uint_as_float(S[52 * c]);
+  ls.dns64 = __longlong_as_double((long long)((unsigned long long)S[53 * c] | ((unsigned long long)S[54 * c] << 32)));
+}
+
+// One round of the sub-domain trace (Section 3: the geometry is split into
+// tiles; a beam leaving a tile is sent to the tile it enters; exchanged beams
+// are processed next; idle workers take work from busy tiles).  Round 0 takes
+// the batch's fresh lineages; later rounds take the hand-offs of the round
+// before, each warp from its home tile's queue first and then, once that is
+// drained, from the other tiles' queues in turn.  A lineage keeps going while
+// it stays in its tile -- reflections start in the tile of their hit point --
+// and is pushed to the next tile's queue when its ray leaves the tile without
+// a hit there.  Queues are only read during a round and only appended to for
+// the next, so no lane ever waits for another.
+template <bool kMixed, bool kCount>
+__global__ void __launch_bounds__(kTraceThreads) k_trace_tiled(TraceArgs a, TiledArgs ta) {
+  __shared__ LineageSmem<kMixed> sm;
+  const int t = threadIdx.x;
+  const unsigned lane = lane_id();
+  const MicGrid g = *a.grid;
+  const TileGrid tg = ta.tg;
+  TraceCounts cn = {0, 0, 0, 0, 0, 0, 0, 0};
+  LaneState ls = {-1, 0, -1, 0.0f, 0.0};
+  int slot = -1, tile = -1;
+  bool done = false;
+  const int home = (int)(blockIdx.x % (unsigned)ta.n_tiles);
+  int cursor = home, tried = 0;  // warp-uniform
+  const RaySrc rs{&sm.hi[kRowO][t], kMixed ? &sm.lo[kRowO][t] : &sm.hi[kRowO][t], kTraceThreads};
+  while (true) {
+    bool need = !done && slot < 0;
+    if (ta.round == 0) {
+      int64_t mine = take_lineage(a, need);
+      if (need) {
+        if (mine >= 0) {
+          ls = LaneState{mine, 0, -1, 0.0f, 0.0};
+          init_lineage(a, sm, t, mine);
+          slot = (int)(mine - a.lineage_begin);
+          float3 o = ld_hi3(sm, kRowO, t);
+          tile = clampi((int)floorf((o.y - tg.gy0) / tg.wy), 0, tg.ty - 1) * tg.tx +
+                 clampi((int)floorf((o.x - tg.gx0) / tg.wx), 0, tg.tx - 1);
+        } else {
+          done = true;
         }
-        float3 H = O + D * best.t;
-        Dn = D - pn * (2.0f * dot3(D, pn));
-        st_f3(sm, kRowO, t, H);
-        st_f3(sm, kRowD, t, Dn);
-        dns = fabsf(dot3(pn, Dn));
-        dns64 = 0.0;
-        float3 sn = dot3(pn, Dn) > 0.0f ? pn : pn * -1.0f;
-        float sw = dot3(sn, pv0 - A);
-        sm.st[0][t] = sn.x; sm.st[1][t] = sn.y; sm.st[2][t] = sn.z; sm.st[3][t] = sw;
       }
-      start_slot = slot;
-      k++;
     } else {
-      lin = -1;
+      unsigned nm = __ballot_sync(0xffffffffu, need);
+      if (nm) {
+        const int leader = __ffs(nm) - 1, cnt = __popc(nm);
+        int got = 0, base = 0;
+        while (tried < ta.n_tiles && got == 0) {
+          if ((int)lane == leader) {
+            int old = atomicAdd(&ta.q_in_head[cursor], cnt);
+            int avail = __ldg(&ta.q_in_count[cursor]) - old;
+            got = avail < 0 ? 0 : (avail < cnt ? avail : cnt);
+            base = old;
+          }
+          got = __shfl_sync(0xffffffffu, got, leader);
+          base = __shfl_sync(0xffffffffu, base, leader);
+          if (got == 0) {
+            cursor = cursor + 1 == ta.n_tiles ? 0 : cursor + 1;
+            tried++;
+          }
+        }
+        if (need) {
+          int rank = __popc(nm & ((1u << lane) - 1u));
+          if (rank < got) {
+            slot = __ldg(&ta.q_in[(size_t)cursor * ta.cap + base + rank]);
+            tile = cursor;
+            load_state(ta, sm, t, slot, ls);
+            if (cursor != home) cn.steal++;
+          } else if (tried >= ta.n_tiles) {
+            done = true;
+          }
+        }
+      }
     }
-  }
-  // warp-aggregated counters
-  for (int o = 16; o > 0; o >>= 1) {
-    n_seg += __shfl_xor_sync(0xffffffffu, n_seg, o);
-    n_hit += __shfl_xor_sync(0xffffffffu, n_hit, o);
-    n_esc += __shfl_xor_sync(0xffffffffu, n_esc, o);
-    n_emit += __shfl_xor_sync(0xffffffffu, n_emit, o);
-    if (kCount) {
-      n_nodes += __shfl_xor_sync(0xffffffffu, n_nodes, o);
-      n_tris += __shfl_xor_sync(0xffffffffu, n_tris, o);
+    if (__all_sync(0xffffffffu, done)) break;
+    if (done || slot < 0) continue;
+    // ---- search the current tile for this lane's ray
+    const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), a.t_eps, ls.dns);
+    Best best;
+    int hit = closest_hit<kMixed, kCount>(a.sc, r, rs, ls.dns64, best, &a.ctr->error, cn.nodes, cn.tris,
+                                          __ldg(&ta.roots[tile]), &tg, tile);
+    if (hit >= 0) {
+      // the hit lies in this tile; a reflected beam starts here as well
+      if (!finish_segment(a, sm, t, r, best, hit, ls, g, cn)) slot = -1;
+      continue;
     }
-  }
-  if (lane == 0) {
-    if (kCount) {
-      atomicAdd(&a.ctr->nodes_visited, n_nodes);
-      atomicAdd(&a.ctr->tris_tested, n_tris);
+    // no hit in this tile: step to the tile the ray enters next
+    int ix = tile % tg.tx, iy = tile / tg.tx;
+    float tex = kInf, tey = kInf;
+    if (r.d.x > 0.0f) tex = (tg.gx0 + (ix + 1) * tg.wx - r.o.x) / r.d.x;
+    else if (r.d.x < 0.0f) tex = (tg.gx0 + ix * tg.wx - r.o.x) / r.d.x;
+    if (r.d.y > 0.0f) tey = (tg.gy0 + (iy + 1) * tg.wy - r.o.y) / r.d.y;
+    else if (r.d.y < 0.0f) tey = (tg.gy0 + iy * tg.wy - r.o.y) / r.d.y;
+    bool leaves = tex == kInf && tey == kInf;
+    if (!leaves) {
+      if (tex <= tey) ix += r.d.x > 0.0f ? 1 : -1;
+      if (tey <= tex) iy += r.d.y > 0.0f ? 1 : -1;
+      leaves = ix < 0 || ix >= tg.tx || iy < 0 || iy >= tg.ty;
     }
-    atomicAdd(&a.ctr->segments, n_seg);
-    atomicAdd(&a.ctr->hits, n_hit);
-    atomicAdd(&a.ctr->escapes, n_esc);
-    atomicAdd(&a.ctr->emitted, n_emit);
+    if (leaves) {
+      // the ray leaves the grid, and with it every triangle: it escapes
+      finish_segment(a, sm, t, r, best, -1, ls, g, cn);
+      slot = -1;
+      continue;
+    }
+    // hand-off to the neighbouring tile, processed in the next round
+    int next = iy * tg.tx + ix;
+    save_state(ta, sm, t, slot, ls);
+    int pos = atomicAdd(&ta.q_out_count[next], 1);
+    if (pos < ta.cap) ta.q_out[(size_t)next * ta.cap + pos] = slot;
+    else atomicExch(&a.ctr->error, BT_E_QUEUE_FULL);
+    cn.hand++;
+    slot = -1;
   }
+  flush_counts(a, cn, kCount);
+}
+
+template <bool kMixed, bool kCount>
+static cudaError_t launch_tiled_t(cudaStream_t st, const TraceArgs &a, const TiledArgs &ta, int n_sm) {
+  int per_sm = 0;
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tiled<kMixed, kCount>, kTraceThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t blocks = (int64_t)n_sm * per_sm;
+  // at least one block per tile so that every tile has a home warp
+  if (blocks < ta.n_tiles) blocks = ta.n_tiles;
+  k_trace_tiled<kMixed, kCount><<<(int)blocks, kTraceThreads, 0, st>>>(a, ta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_tiled(cudaStream_t st, const TraceArgs &a, const TiledArgs &ta, int n_sm) {
+  cudaError_t e;
+  if (a.mixed) e = a.count_work ? launch_tiled_t<true, true>(st, a, ta, n_sm) : launch_tiled_t<true, false>(st, a, ta, n_sm);
+  else e = a.count_work ? launch_tiled_t<false, true>(st, a, ta, n_sm) : launch_tiled_t<false, false>(st, a, ta, n_sm);
+  note_launches(1);
+  return e;
 }
 
 // Closest hit of arbitrary float32 rays (the axis-ray query of the trace
@@ -564,7 +799,7 @@ __global__ void __launch_bounds__(128) k_cast(DevScene sc, const float *o, const
   Ray r = make_ray(O, df3_hi(D), t_eps, (float)dns);
   Best best;
   unsigned long long a = 0, b = 0;
-  int slot = closest_hit<true, false>(sc, r, RaySrc{&rh[0][t], &rl[0][t], 128}, dns, best, err, a, b);
+  int slot = closest_hit<true, false>(sc, r, RaySrc{&rh[0][t], &rl[0][t], 128}, dns, best, err, a, b, sc.root);
   t_out[i] = slot >= 0 ? (best.has64 ? (float)best.t64 : best.t) : kInf;
   tri_out[i] = slot >= 0 ? best.id : -1;
 }

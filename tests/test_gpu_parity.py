@@ -304,3 +304,30 @@ def test_district_full_size_sampled_microphones(tracer, oracle_mod, district):
     assert (r["cnt"] > 0).mean() > 0.5
     assert abs(g["stats"]["segments"] / r["stats"]["segments"] - 1) < 1e-4
     print("district full size, 2000 sampled microphones:", s)
+
+
+# ------------------------------------------------------------- sub-domains
+@pytest.mark.parametrize("tiles", [(2, 2), (4, 4), (3, 5)])
+def test_tiles_match_oracle_and_unsplit(tracer, oracle_mod, tiles):
+    # Section 3: splitting the geometry into sub-domains with beam hand-off
+    # must not change any result
+    w = synth.tiny_city(seed=3, level=4, max_order=4, n_sources=2)
+    base = gpu_run(tracer, w)
+    g = gpu_run(tracer, w, tiles_x=tiles[0], tiles_y=tiles[1])
+    r, L = oracle_levels(oracle_mod, w)
+    assert_parity(g["level"], L, f"tiles {tiles}")
+    assert (g["cnt"] == base["cnt"]).all()
+    assert np.allclose(g["I"], base["I"], rtol=1e-9, atol=0)
+    assert g["stats"]["segments"] == base["stats"]["segments"] == r["stats"]["segments"]
+    assert g["stats"]["handoffs"] > 0 and g["stats"]["rounds"] > 1
+
+
+def test_tiles_district_source_subset(tracer, oracle_mod, district):
+    import os
+    idx = np.random.Generator(np.random.PCG64(21)).choice(len(district.src), 16, replace=False)
+    w = district.subset_sources(np.sort(idx))
+    g = gpu_run(tracer, w, tiles_x=4, tiles_y=4)
+    r, L = oracle_levels(oracle_mod, w, n_threads=max(1, os.cpu_count() or 1))
+    assert_parity(g["level"], L, "district, 16 sources, 4x4 tiles")
+    assert abs(g["stats"]["segments"] / r["stats"]["segments"] - 1) < 1e-4
+    assert g["stats"]["handoffs"] > 0 and g["stats"]["steals"] >= 0
