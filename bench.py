@@ -362,7 +362,8 @@ def main():
                          "nodes_per_segment": res["work"]["nodes_visited"] / max(1, res["work"]["segments"]),
                          "tris_per_segment": res["work"]["tris_tested"] / max(1, res["work"]["segments"])},
             "stats": {k: res["stats"][k] for k in ("segments", "hits", "escapes", "emitted",
-                                                   "candidates", "contributions")}}
+                                                   "candidates", "contributions", "handoffs",
+                                                   "steals", "rounds")}}
     if "e2e" in res:
         line["e2e"] = res["e2e"]
     if not args.no_cpu_baseline:

@@ -581,10 +581,11 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   const int T = p->tiles_x * p->tiles_y;
   int64_t chunk = p->chunk_beams > 0 ? p->chunk_beams : ((int64_t)1 << 23) / (p->max_order + 1);
   if (tiled && p->chunk_beams <= 0) {
-    // queues take 8 T bytes per lineage: keep all per-lineage buffers near 2 GiB
+    // Fewer, larger batches mean fewer exchange rounds in total; the
+    // per-lineage buffers (segments, state, 2 T queue slots) are kept near
+    // 8 GiB, a small part of the device.
     int64_t per = (int64_t)sizeof(bt::Seg) * (p->max_order + 1) + 4 * bt::kStateRows + 8 * (int64_t)T;
-    int64_t lim = ((int64_t)2 << 30) / per;
-    if (chunk > lim) chunk = lim;
+    chunk = ((int64_t)8 << 30) / per;
   }
   if (chunk > total) chunk = total;
   if (chunk < 1) chunk = 1;
