@@ -76,6 +76,11 @@ typedef struct {
   int32_t chunk_beams;                      /* beam lineages per launch batch; 0 = automatic */
   int32_t count_work;                       /* 1: also count BVH nodes visited and triangles
                                                tested (slower; for roofline accounting) */
+  int32_t queue_depth;                      /* hand-off queue slots per sub-domain, a power of
+                                               two in 32..2^22, or 0 = automatic (at least
+                                               twice the lanes of one launch); also the most
+                                               lineages in flight at once, so that no queue
+                                               can overflow */
 } bt_trace_params;
 
 /* Counters of the last trace of a scene. */
@@ -87,9 +92,9 @@ typedef struct {
   int64_t emitted;        /* segments whose footprint overlapped the microphone grid */
   int64_t candidates;     /* microphones tested against a segment */
   int64_t contributions;  /* (microphone, segment) pairs inside the beam */
-  int64_t handoffs;       /* rays passed from one sub-domain to the next */
-  int64_t steals;         /* work items taken from another sub-domain's queue */
-  int64_t rounds;         /* sub-domain exchange rounds */
+  int64_t handoffs;       /* rays passed from one sub-domain to the next through its queue */
+  int64_t steals;         /* hand-offs served by a warp whose home is another sub-domain */
+  int64_t rounds;         /* persistent sub-domain launches (one per batch of lineages) */
   int64_t nodes_visited;  /* BVH nodes fetched (only with count_work) */
   int64_t tris_tested;    /* triangles tested (only with count_work) */
   int64_t trace_launches; /* launches of the traversal kernel */

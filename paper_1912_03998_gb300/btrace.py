@@ -30,7 +30,8 @@ class bt_trace_params(C.Structure):
     _fields_ = [("max_order", C.c_int32), ("air_atten_db_per_m", C.c_float * BT_MAX_BANDS),
                 ("energy_threshold_w", C.c_float), ("t_eps_m", C.c_float),
                 ("tiles_x", C.c_int32), ("tiles_y", C.c_int32), ("precision", C.c_int32),
-                ("watchdog_ms", C.c_int32), ("chunk_beams", C.c_int32), ("count_work", C.c_int32)]
+                ("watchdog_ms", C.c_int32), ("chunk_beams", C.c_int32), ("count_work", C.c_int32),
+                ("queue_depth", C.c_int32)]
 
 
 class bt_stats(C.Structure):

@@ -77,8 +77,7 @@ struct bt_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> kev;  // pairs of events around kernel launches of one trace
   std::vector<DevBuf> pool;      // released device buffers, reused before any new cudaMalloc
-  DevBuf t_state, t_qa, t_qb, t_cnt;  // sub-domain trace: lineage state, queues, counts and heads
-  int *h_tile_counts = nullptr;       // pinned [BT_MAX_TILES * BT_MAX_TILES]
+  DevBuf t_ring, t_seq, t_qctl;  // sub-domain trace: queue slots, slot sequence words, queue counters
 };
 
 namespace {
@@ -328,10 +327,6 @@ BT_API int bt_create(bt_ctx **out, int device, void *cuda_stream) {
     if (cudaMalloc(&c->d_box, 8 * sizeof(float)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
     if (cudaMalloc(&c->d_lineage_next, sizeof(unsigned long long)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
     if (cudaMallocHost(&c->h_ctr, sizeof(bt::Counters)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
-    if (cudaMallocHost(&c->h_tile_counts, sizeof(int) * BT_MAX_TILES * BT_MAX_TILES) != cudaSuccess) {
-      rc = BT_E_NOMEM;
-      break;
-    }
     if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) { rc = BT_E_CUDA; break; }
   } while (0);
   if (rc != BT_OK) {
@@ -361,11 +356,9 @@ BT_API int bt_destroy(bt_ctx *c) {
   if (c->d_box) cudaFree(c->d_box);
   if (c->d_lineage_next) cudaFree(c->d_lineage_next);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
-  if (c->h_tile_counts) cudaFreeHost(c->h_tile_counts);
-  release(c->t_state);
-  release(c->t_qa);
-  release(c->t_qb);
-  release(c->t_cnt);
+  release(c->t_ring);
+  release(c->t_seq);
+  release(c->t_qctl);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   for (cudaEvent_t e : c->kev) cudaEventDestroy(e);
@@ -565,6 +558,9 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   if (p->tiles_x < 1 || p->tiles_y < 1 || p->tiles_x > BT_MAX_TILES || p->tiles_y > BT_MAX_TILES)
     return fail(c, BT_E_INVALID, "tiles %dx%d not in 1..%d per axis", p->tiles_x, p->tiles_y, BT_MAX_TILES);
   if (p->chunk_beams < 0) return fail(c, BT_E_INVALID, "chunk_beams must be >= 0");
+  if (p->queue_depth != 0 && (p->queue_depth < 32 || p->queue_depth > (1 << 22) ||
+                              (p->queue_depth & (p->queue_depth - 1)) != 0))
+    return fail(c, BT_E_INVALID, "queue_depth must be 0 or a power of two in 32..2^22");
   int has_alpha = 0;
   float alpha_log2[BT_MAX_BANDS];
   for (int b = 0; b < BT_MAX_BANDS; b++) {
@@ -581,22 +577,31 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   const int T = p->tiles_x * p->tiles_y;
   int64_t chunk = p->chunk_beams > 0 ? p->chunk_beams : ((int64_t)1 << 23) / (p->max_order + 1);
   if (tiled && p->chunk_beams <= 0) {
-    // Fewer, larger batches mean fewer exchange rounds in total; the
-    // per-lineage buffers (segments, state, 2 T queue slots) are kept near
-    // 8 GiB, a small part of the device.
-    int64_t per = (int64_t)sizeof(bt::Seg) * (p->max_order + 1) + 4 * bt::kStateRows + 8 * (int64_t)T;
-    chunk = ((int64_t)8 << 30) / per;
+    // One persistent launch per batch: fewer, larger batches mean fewer
+    // launch tails.  The segment records of a batch are kept near 8 GiB, a
+    // small part of the device.
+    chunk = ((int64_t)8 << 30) / ((int64_t)sizeof(bt::Seg) * (p->max_order + 1));
   }
   if (chunk > total) chunk = total;
   if (chunk < 1) chunk = 1;
   const unsigned long long cap = (unsigned long long)chunk * (p->max_order + 1);
   TRY(ensure(c, c->segs, sizeof(bt::Seg) * cap));
+  // Hand-off queues: at most qcap lineages are in flight (traced or queued),
+  // so no tile's ring of qcap slots can overflow.  Automatic: at least twice
+  // the lanes of one launch, so that the cap rarely holds a lane back.
+  unsigned qcap = 1024;
   if (tiled) {
     TRY(ensure_tiled(c, *s, p->tiles_x, p->tiles_y));
-    TRY(ensure(c, c->t_state, sizeof(uint32_t) * bt::kStateRows * (size_t)chunk));
-    TRY(ensure(c, c->t_qa, sizeof(int) * (size_t)T * (size_t)chunk));
-    TRY(ensure(c, c->t_qb, sizeof(int) * (size_t)T * (size_t)chunk));
-    TRY(ensure(c, c->t_cnt, sizeof(int) * 3 * (size_t)T));
+    if (p->queue_depth > 0) {
+      qcap = (unsigned)p->queue_depth;
+    } else {
+      const int64_t lanes = bt::tiled_resident_lanes(c->n_sm);
+      while ((int64_t)qcap < 2 * lanes && qcap < (1u << 22)) qcap <<= 1;
+      while (qcap > 1024 && (int64_t)T * qcap * (bt::kStateRows * 4 + 4) > ((int64_t)4 << 30)) qcap >>= 1;
+    }
+    TRY(ensure(c, c->t_ring, sizeof(uint32_t) * bt::kStateRows * (size_t)T * qcap));
+    TRY(ensure(c, c->t_seq, sizeof(unsigned) * (size_t)T * qcap));
+    TRY(ensure(c, c->t_qctl, sizeof(int) * (3 * (size_t)T + 2)));
   }
   TRY(reset_counters(c));
   CK(cudaMemsetAsync(s->energy.p, 0, sizeof(double) * bt::kMaxBands * (size_t)s->n_mics, st));
@@ -661,8 +666,11 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
     tga.tg = s->tg;
     tga.n_tiles = T;
     tga.roots = (const int *)s->t_roots.p;
-    tga.state = (uint32_t *)c->t_state.p;
-    tga.cap = (int)chunk;
+    tga.qcap = qcap;
+    tga.ring = (uint32_t *)c->t_ring.p;
+    tga.seq = (unsigned *)c->t_seq.p;
+    tga.ctl = (int *)c->t_qctl.p;
+    tga.watchdog_ns = (unsigned long long)(p->watchdog_ms > 0 ? p->watchdog_ms : 2000) * 1000000ull;
   }
   // Events bracket every launch; kind 0 traversal, 1 scatter.
   struct Mark {
@@ -689,7 +697,6 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   };
   const int64_t n_chunks = total > 0 ? (total + chunk - 1) / chunk : 0;
   int64_t n_trace_launches = 0, n_scatter_launches = 0, n_rounds = 0;
-  const int max_rounds = (p->max_order + 1) * (p->tiles_x + p->tiles_y + 2) + 8;
   CK(cudaEventRecord(c->ev0, st));
   for (int64_t ci = 0; ci < n_chunks; ci++) {
     int64_t b0 = ci * chunk;
@@ -697,45 +704,21 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
     ta.lineage_end = b0 + chunk < total ? b0 + chunk : total;
     CK(cudaMemsetAsync(c->d_seg_count, 0, sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(c->d_lineage_next, 0, sizeof(unsigned long long), st));
-    if (!tiled) {
-      TRY(mark(0));
-      CK(bt::launch_trace(st, ta, c->n_sm));
-      TRY(mark(0));
-      n_trace_launches++;
-      TRY(scatter_round());
-      n_scatter_launches += s->n_mics > 0;
-      continue;
+    if (tiled) {
+      CK(cudaMemsetAsync(c->t_seq.p, 0, sizeof(unsigned) * (size_t)T * qcap, st));
+      CK(cudaMemsetAsync(c->t_qctl.p, 0, sizeof(int) * (3 * (size_t)T + 2), st));
     }
-    // sub-domain rounds: round 0 on fresh lineages, then hand-offs
-    int *cnt = (int *)c->t_cnt.p;  // [0,T) in-counts, [T,2T) out-counts, [2T,3T) heads
-    int *qin = (int *)c->t_qa.p, *qout = (int *)c->t_qb.p;
-    int *cin = cnt, *cout = cnt + T;
-    for (int round = 0;; round++) {
-      if (round >= max_rounds) return fail(c, BT_E_TIMEOUT, "sub-domain exchange did not finish in %d rounds", max_rounds);
-      CK(cudaMemsetAsync(cout, 0, sizeof(int) * T, st));
-      CK(cudaMemsetAsync(cnt + 2 * T, 0, sizeof(int) * T, st));
-      if (round > 0) CK(cudaMemsetAsync(c->d_seg_count, 0, sizeof(unsigned long long), st));
-      tga.round = round;
-      tga.q_in = qin;
-      tga.q_in_count = cin;
-      tga.q_in_head = cnt + 2 * T;
-      tga.q_out = qout;
-      tga.q_out_count = cout;
-      TRY(mark(0));
+    TRY(mark(0));
+    if (tiled) {
       CK(bt::launch_trace_tiled(st, ta, tga, c->n_sm));
-      TRY(mark(0));
-      n_trace_launches++;
       n_rounds++;
-      TRY(scatter_round());
-      n_scatter_launches += s->n_mics > 0;
-      CK(cudaMemcpyAsync(c->h_tile_counts, cout, sizeof(int) * T, cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      int64_t pending = 0;
-      for (int q = 0; q < T; q++) pending += c->h_tile_counts[q];
-      if (pending == 0) break;
-      std::swap(qin, qout);
-      std::swap(cin, cout);
+    } else {
+      CK(bt::launch_trace(st, ta, c->n_sm));
     }
+    TRY(mark(0));
+    n_trace_launches++;
+    TRY(scatter_round());
+    n_scatter_launches += s->n_mics > 0;
   }
   CK(cudaEventRecord(c->ev1, st));
   TRY(read_counters(c));

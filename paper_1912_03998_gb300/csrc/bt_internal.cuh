@@ -50,20 +50,28 @@ struct TileGrid {
   int tx, ty;
 };
 
-// Everything the tiled trace round needs besides TraceArgs.  Queues hold
-// lineage slots (0..cap-1 within the batch), one array of `cap` per tile.
+// Everything the sub-domain trace needs besides TraceArgs.  Each tile has a
+// ring queue of handed-off lineages: `qcap` slots (a power of two), each
+// holding a lineage's whole state as kStateRows words (row r of slot q of
+// tile k at ring[(k * kStateRows + r) * qcap + q]).  Positions count up from
+// zero per launch: a producer reserves positions by advancing tail[k] and,
+// once they are written, adds them to avail[k]; a consumer first takes items
+// from avail[k] (a counting semaphore) and then positions from head[k].
+// seq[k * qcap + slot], relative to the position's generation
+// g = pos & ~(qcap - 1), says whether the slot is free for it (g), filled
+// (g + 1), or released to the next generation (g + qcap).  At most qcap
+// lineages are in flight (traced or queued) at any time, so a ring never
+// holds more than qcap items and a producer never waits for a consumer.
 struct TiledArgs {
   TileGrid tg;
   int n_tiles;
   const int *roots;         // [n_tiles] subtree root per tile (INT_MIN: empty tile)
-  uint32_t *state;          // lineage state, kStateRows rows of `cap` words
-  int cap;
-  const int *q_in;          // [n_tiles][cap] hand-offs to process this round
-  const int *q_in_count;    // [n_tiles]
-  int *q_in_head;           // [n_tiles] pop cursors
-  int *q_out;               // [n_tiles][cap] hand-offs for the next round
-  int *q_out_count;         // [n_tiles]
-  int round;                // 0: fresh lineages; > 0: hand-offs
+  unsigned qcap;            // ring slots per tile, a power of two; also the cap on lineages in flight
+  uint32_t *ring;           // [n_tiles][kStateRows][qcap]
+  unsigned *seq;            // [n_tiles][qcap], zero at launch
+  int *ctl;                 // zero at launch: head[n_tiles], tail[n_tiles], avail[n_tiles],
+                            // credits in use, lineages finished
+  unsigned long long watchdog_ns;  // bound on any wait of a warp that has no work
 };
 
 struct DevScene {
@@ -112,7 +120,7 @@ static_assert(sizeof(Seg) == 192, "segment record layout");
 // Device counters of one trace, accumulated with atomics.
 struct Counters {
   unsigned long long segments, hits, escapes, emitted, candidates, contributions;
-  unsigned long long handoffs, steals, rounds, overflow;
+  unsigned long long handoffs, steals, rounds, pad2;
   unsigned long long nodes_visited, tris_tested;
   int error;  // sticky error code set by kernels (0 = none)
   int pad;
@@ -499,6 +507,7 @@ cudaError_t build_mics(cudaStream_t st, const float *d_pos, int64_t n_m, int sid
 size_t build_mics_scratch_bytes(int64_t n_m, int side);
 cudaError_t launch_trace(cudaStream_t st, const TraceArgs &a, int n_sm);
 cudaError_t launch_trace_tiled(cudaStream_t st, const TraceArgs &a, const TiledArgs &t, int n_sm);
+int tiled_resident_lanes(int n_sm);  // lanes of one full persistent sub-domain launch
 constexpr int kStateRows = 56;
 cudaError_t launch_cast(cudaStream_t st, const DevScene &sc, const float *o, const float *d, const float *ns,
                         int64_t n, float t_eps, float *t_out, int *tri_out, int *err);

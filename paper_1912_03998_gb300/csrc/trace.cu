@@ -159,7 +159,7 @@ __device__ __forceinline__ int tile_ix(double x, double g0, double g1, int n) {
 
 template <bool kMixed, bool kCount>
 __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, RaySrc rs, double dns64, Best &best,
-                                           int *err, unsigned long long &n_nodes, unsigned long long &n_tris,
+                                           int *err, unsigned &n_nodes, unsigned &n_tris,
                                            int root, const TileGrid *tf = nullptr, int tile = 0) {
   best.t = kInf;
   best.slot = -1;
@@ -304,7 +304,7 @@ __device__ __forceinline__ bool may_reach_slab(float3 n0, float3 n1, float3 n2, 
 
 // Warp-aggregated append of a segment record.
 __device__ __forceinline__ void emit_segment(const TraceArgs &a, const Seg &s, bool emit,
-                                             unsigned long long &n_emit) {
+                                             unsigned &n_emit) {
   unsigned mask = __activemask();
   unsigned bal = __ballot_sync(mask, emit);
   if (!bal) return;
@@ -326,12 +326,15 @@ __device__ __forceinline__ void emit_segment(const TraceArgs &a, const Seg &s, b
 // parts of the float pairs (MIXED only).
 constexpr int kTraceThreads = 128;
 constexpr int kRowA = 0, kRowN = 3, kRowO = 12, kRowD = 15, kRows = 18;
+// per-lane event counters (rows of LineageSmem::cnt)
+enum { kCSeg, kCHit, kCEsc, kCEmit, kCHand, kCSteal, kCNodes, kCTris, kNumCounts };
 template <bool kMixed>
 struct LineageSmem {
   float hi[kRows][kTraceThreads];
   float lo[kMixed ? kRows : 1][kTraceThreads];
   float p[kMaxBands][kTraceThreads];  // band power W_b prod(r_b)
   float st[4][kTraceThreads];         // start plane (relative to the apex)
+  unsigned cnt[kNumCounts][kTraceThreads];  // per-lane event counts of the launch
 };
 
 template <bool kMixed>
@@ -411,9 +414,19 @@ struct LaneState {
   double dns64;
 };
 
+// Per-lane event counts of one launch, kept in the lane's shared-memory
+// column rather than in registers.  A lane handles at most a few thousand
+// segments per launch, so even the node count stays far below 2^32; the warp
+// sums are formed in 64-bit.
 struct TraceCounts {
-  unsigned long long seg, hit, esc, emit, nodes, tris, hand, steal;
+  unsigned *p;  // &cnt[0][lane's column]
+  __device__ unsigned &operator[](int i) const { return p[i * kTraceThreads]; }
 };
+template <bool kMixed>
+__device__ __forceinline__ TraceCounts init_counts(LineageSmem<kMixed> &sm, int t) {
+  for (int q = 0; q < kNumCounts; q++) sm.cnt[q][t] = 0u;
+  return TraceCounts{&sm.cnt[0][t]};
+}
 
 // A segment is resolved: its axis ray hit triangle `slot` (or escaped, slot
 // < 0).  Write the segment record and, if the beam goes on, reflect it: the
@@ -422,14 +435,14 @@ struct TraceCounts {
 template <bool kMixed>
 __device__ __forceinline__ bool finish_segment(const TraceArgs &a, LineageSmem<kMixed> &sm, int t, const Ray &r,
                                                const Best &best, int slot, LaneState &ls, const MicGrid &g,
-                                               TraceCounts &cn) {
+                                               const TraceCounts &cn) {
   const int nb = a.sc.n_bands;
-  cn.seg++;
+  cn[kCSeg]++;
   float4 end = make_float4(0.0f, 0.0f, 0.0f, -kInf);
   float4 v0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   float4 plf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   if (slot >= 0) {
-    cn.hit++;
+    cn[kCHit]++;
     v0 = __ldg(&a.sc.tris[slot].v0);
     plf = __ldg(&a.sc.planes[slot]);
     // end plane on the incident side, offset relative to the apex
@@ -440,7 +453,7 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, LineageSmem<k
     else ew = dot3(en, f3(v0) - ld_hi3(sm, kRowA, t));
     end = make_float4(en.x, en.y, en.z, ew);
   } else {
-    cn.esc++;
+    cn[kCEsc]++;
   }
   {
     Seg s;
@@ -460,7 +473,7 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, LineageSmem<k
     s.p47 = make_float4(sm.p[4][t], sm.p[5][t], sm.p[6][t], sm.p[7][t]);
     s.cy0 = 0;
     s.cy1 = -1;
-    emit_segment(a, s, g.n_mics > 0 && may_reach_slab(n0, n1, n2, s.ahi[2], g), cn.emit);
+    emit_segment(a, s, g.n_mics > 0 && may_reach_slab(n0, n1, n2, s.ahi[2], g), cn[kCEmit]);
   }
   if (slot < 0 || ls.k == a.max_order) return false;
   // energy lost at the reflection
@@ -524,30 +537,23 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, LineageSmem<k
   return true;
 }
 
-__device__ __forceinline__ void flush_counts(const TraceArgs &a, TraceCounts &cn, bool count_work) {
-  for (int o = 16; o > 0; o >>= 1) {
-    cn.seg += __shfl_xor_sync(0xffffffffu, cn.seg, o);
-    cn.hit += __shfl_xor_sync(0xffffffffu, cn.hit, o);
-    cn.esc += __shfl_xor_sync(0xffffffffu, cn.esc, o);
-    cn.emit += __shfl_xor_sync(0xffffffffu, cn.emit, o);
-    cn.hand += __shfl_xor_sync(0xffffffffu, cn.hand, o);
-    cn.steal += __shfl_xor_sync(0xffffffffu, cn.steal, o);
-    if (count_work) {
-      cn.nodes += __shfl_xor_sync(0xffffffffu, cn.nodes, o);
-      cn.tris += __shfl_xor_sync(0xffffffffu, cn.tris, o);
-    }
-  }
+__device__ __forceinline__ void flush_counts(const TraceArgs &a, const TraceCounts &cn, bool count_work) {
+  // warp sums in 64-bit
+  unsigned long long v[kNumCounts];
+  for (int q = 0; q < kNumCounts; q++) v[q] = cn[q];
+  for (int o = 16; o > 0; o >>= 1)
+    for (int q = 0; q < kNumCounts; q++) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
   if (lane_id() == 0) {
     if (count_work) {
-      atomicAdd(&a.ctr->nodes_visited, cn.nodes);
-      atomicAdd(&a.ctr->tris_tested, cn.tris);
+      atomicAdd(&a.ctr->nodes_visited, v[kCNodes]);
+      atomicAdd(&a.ctr->tris_tested, v[kCTris]);
     }
-    atomicAdd(&a.ctr->segments, cn.seg);
-    atomicAdd(&a.ctr->hits, cn.hit);
-    atomicAdd(&a.ctr->escapes, cn.esc);
-    atomicAdd(&a.ctr->emitted, cn.emit);
-    if (cn.hand) atomicAdd(&a.ctr->handoffs, cn.hand);
-    if (cn.steal) atomicAdd(&a.ctr->steals, cn.steal);
+    atomicAdd(&a.ctr->segments, v[kCSeg]);
+    atomicAdd(&a.ctr->hits, v[kCHit]);
+    atomicAdd(&a.ctr->escapes, v[kCEsc]);
+    atomicAdd(&a.ctr->emitted, v[kCEmit]);
+    if (v[kCHand]) atomicAdd(&a.ctr->handoffs, v[kCHand]);
+    if (v[kCSteal]) atomicAdd(&a.ctr->steals, v[kCSteal]);
   }
 }
 
@@ -574,7 +580,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
   __shared__ LineageSmem<kMixed> sm;
   const int t = threadIdx.x;
   const MicGrid g = *a.grid;
-  TraceCounts cn = {0, 0, 0, 0, 0, 0, 0, 0};
+  const TraceCounts cn = init_counts(sm, t);
   LaneState ls = {-1, 0, -1, 0.0f, 0.0};
   bool done = false;
   const RaySrc rs{&sm.hi[kRowO][t], kMixed ? &sm.lo[kRowO][t] : &sm.hi[kRowO][t], kTraceThreads};
@@ -594,7 +600,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
     // ---- one segment of this lane's lineage
     const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), a.t_eps, ls.dns);
     Best best;
-    int slot = closest_hit<kMixed, kCount>(a.sc, r, rs, ls.dns64, best, &a.ctr->error, cn.nodes, cn.tris,
+    int slot = closest_hit<kMixed, kCount>(a.sc, r, rs, ls.dns64, best, &a.ctr->error, cn[kCNodes], cn[kCTris],
                                            a.sc.root);
     if (!finish_segment(a, sm, t, r, best, slot, ls, g, cn)) ls.lin = -1;
   }
@@ -602,155 +608,337 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
 }
 
 // --------------------------------------------------------------- sub-domains
-// Lineage state saved to global memory at a hand-off (rows of `cap` words).
+// Device-scope ordered accesses for the hand-off queues.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long v;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+  return v;
+}
+
+// Record a watchdog expiry unless an error is already recorded.
+__device__ __forceinline__ void watchdog_fired(const TraceArgs &a) { atomicCAS(&a.ctr->error, 0, BT_E_TIMEOUT); }
+
+// Bounded wait until a queue slot's sequence word reaches `want`.  False if
+// the watchdog ran out first (an error is then recorded).
+__device__ __forceinline__ bool wait_slot(const TraceArgs &a, const TiledArgs &ta, const unsigned *seq, unsigned want) {
+  if (ld_acquire_u32(seq) == want) return true;
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    __nanosleep(32);
+    if (ld_acquire_u32(seq) == want) return true;
+    if (global_ns() - t0 > ta.watchdog_ns) {
+      watchdog_fired(a);
+      return false;
+    }
+  }
+}
+
+// A lineage's state in a queue slot: S points at row 0, rows c words apart.
+// Queue slots are written once and read once by another SM, so both sides
+// go through L2 only.
 template <bool kMixed>
-__device__ __forceinline__ void save_state(const TiledArgs &ta, const LineageSmem<kMixed> &sm, int t, int slot,
+__device__ __forceinline__ void save_state(uint32_t *S, size_t c, const LineageSmem<kMixed> &sm, int t,
                                            const LaneState &ls) {
-  uint32_t *S = ta.state + slot;
-  const size_t c = (size_t)ta.cap;
-  for (int q = 0; q < kRows; q++) S[q * c] = __float_as_uint(sm.hi[q][t]);
+  for (int q = 0; q < kRows; q++) __stcg(S + q * c, __float_as_uint(sm.hi[q][t]));
   if (kMixed)
-    for (int q = 0; q < kRows; q++) S[(kRows + q) * c] = __float_as_uint(sm.lo[q][t]);
-  for (int b = 0; b < kMaxBands; b++) S[(36 + b) * c] = __float_as_uint(sm.p[b][t]);
-  for (int q = 0; q < 4; q++) S[(44 + q) * c] = __float_as_uint(sm.st[q][t]);
-  S[48 * c] = (uint32_t)(ls.lin & 0xffffffffu);
-  S[49 * c] = (uint32_t)(ls.lin >> 32);
-  S[50 * c] = (uint32_t)ls.k;
-  S[51 * c] = (uint32_t)ls.start_slot;
-  S[52 * c] = __float_as_uint(ls.dns);
+    for (int q = 0; q < kRows; q++) __stcg(S + (kRows + q) * c, __float_as_uint(sm.lo[q][t]));
+  for (int b = 0; b < kMaxBands; b++) __stcg(S + (36 + b) * c, __float_as_uint(sm.p[b][t]));
+  for (int q = 0; q < 4; q++) __stcg(S + (44 + q) * c, __float_as_uint(sm.st[q][t]));
+  __stcg(S + 48 * c, (uint32_t)(ls.lin & 0xffffffffu));
+  __stcg(S + 49 * c, (uint32_t)(ls.lin >> 32));
+  __stcg(S + 50 * c, (uint32_t)ls.k);
+  __stcg(S + 51 * c, (uint32_t)ls.start_slot);
+  __stcg(S + 52 * c, __float_as_uint(ls.dns));
   unsigned long long d = __double_as_longlong(ls.dns64);
-  S[53 * c] = (uint32_t)(d & 0xffffffffu);
-  S[54 * c] = (uint32_t)(d >> 32);
+  __stcg(S + 53 * c, (uint32_t)(d & 0xffffffffu));
+  __stcg(S + 54 * c, (uint32_t)(d >> 32));
 }
 
 template <bool kMixed>
-__device__ __forceinline__ void load_state(const TiledArgs &ta, LineageSmem<kMixed> &sm, int t, int slot,
+__device__ __forceinline__ void load_state(const uint32_t *S, size_t c, LineageSmem<kMixed> &sm, int t,
                                            LaneState &ls) {
-  const uint32_t *S = ta.state + slot;
-  const size_t c = (size_t)ta.cap;
-  for (int q = 0; q < kRows; q++) sm.hi[q][t] = __uint_as_float(S[q * c]);
+  for (int q = 0; q < kRows; q++) sm.hi[q][t] = __uint_as_float(__ldcg(S + q * c));
   if (kMixed)
-    for (int q = 0; q < kRows; q++) sm.lo[q][t] = __uint_as_float(S[(kRows + q) * c]);
-  for (int b = 0; b < kMaxBands; b++) sm.p[b][t] = __uint_as_float(S[(36 + b) * c]);
-  for (int q = 0; q < 4; q++) sm.st[q][t] = __uint_as_float(S[(44 + q) * c]);
-  ls.lin = (int64_t)S[48 * c] | ((int64_t)S[49 * c] << 32);
-  ls.k = (int)S[50 * c];
-  ls.start_slot = (int)S[51 * c];
-  ls.dns = __uint_as_float(S[52 * c]);
-  ls.dns64 = __longlong_as_double((long long)((unsigned long long)S[53 * c] | ((unsigned long long)S[54 * c] << 32)));
+    for (int q = 0; q < kRows; q++) sm.lo[q][t] = __uint_as_float(__ldcg(S + (kRows + q) * c));
+  for (int b = 0; b < kMaxBands; b++) sm.p[b][t] = __uint_as_float(__ldcg(S + (36 + b) * c));
+  for (int q = 0; q < 4; q++) sm.st[q][t] = __uint_as_float(__ldcg(S + (44 + q) * c));
+  ls.lin = (int64_t)__ldcg(S + 48 * c) | ((int64_t)__ldcg(S + 49 * c) << 32);
+  ls.k = (int)__ldcg(S + 50 * c);
+  ls.start_slot = (int)__ldcg(S + 51 * c);
+  ls.dns = __uint_as_float(__ldcg(S + 52 * c));
+  ls.dns64 = __longlong_as_double(
+      (long long)((unsigned long long)__ldcg(S + 53 * c) | ((unsigned long long)__ldcg(S + 54 * c) << 32)));
 }
 
-// One round of the sub-domain trace (Section 3: the geometry is split into
-// tiles; a beam leaving a tile is sent to the tile it enters; exchanged beams
-// are processed next; idle workers take work from busy tiles).  Round 0 takes
-// the batch's fresh lineages; later rounds take the hand-offs of the round
-// before, each warp from its home tile's queue first and then, once that is
-// drained, from the other tiles' queues in turn.  A lineage keeps going while
-// it stays in its tile -- reflections start in the tile of their hit point --
-// and is pushed to the next tile's queue when its ray leaves the tile without
-// a hit there.  Queues are only read during a round and only appended to for
-// the next, so no lane ever waits for another.
+// False if the ray cannot reach any triangle under a subtree root: an empty
+// tile, or both child boxes of the root missed (the test the traversal itself
+// would make first).  A single-triangle root is always reachable.
+__device__ __forceinline__ bool root_reachable(const DevScene &sc, int root, const Ray &r) {
+  if (root == (int)0x80000000) return false;
+  if (root < 0) return true;
+  const Node *nd = sc.nodes + root;
+  float4 lxy = __ldg(&nd->lxy), rxy = __ldg(&nd->rxy), lrz = __ldg(&nd->lrz);
+  float tl, tr;
+  return slab(r, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, kInf, tl) ||
+         slab(r, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, kInf, tr);
+}
+
+// Take up to `want` queued hand-offs, from the home tile if it has any, else
+// from the first tile after it that has (work stealing).  Warp-collective;
+// the result is warp-uniform: the tile (-1 if none was taken), the first
+// position and the count.  avail[k] counts written items not yet taken; a
+// take subtracts and gives back what it could not have, so it never takes
+// more than were there.
+__device__ __forceinline__ int take_handoffs(const TiledArgs &ta, int home, int want, unsigned &base, int &got) {
+  const unsigned lane = lane_id();
+  const int T = ta.n_tiles;
+  int *head = ta.ctl, *avail = ta.ctl + 2 * T;
+  got = 0;
+  base = 0;
+  int tile = -1;
+  for (int off = 0; off < T && tile < 0; off += 32) {
+    int q = off + (int)lane;
+    int k = home + q;
+    if (k >= T) k -= T;
+    bool ne = q < T && *(volatile int *)&avail[k] > 0;
+    unsigned b = __ballot_sync(0xffffffffu, ne);
+    if (b) {
+      tile = home + off + __ffs(b) - 1;
+      if (tile >= T) tile -= T;
+    }
+  }
+  if (tile < 0) return -1;
+  if (lane == 0) {
+    int old = atomicSub(&avail[tile], want);
+    int g = old < 0 ? 0 : (old < want ? old : want);
+    if (g < want) atomicAdd(&avail[tile], want - g);
+    if (g > 0) base = (unsigned)atomicAdd(&head[tile], g);
+    got = g;
+  }
+  got = __shfl_sync(0xffffffffu, got, 0);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  return got > 0 ? tile : -1;
+}
+
+// Take up to `want` fresh lineages of the batch without exceeding qcap
+// lineages in flight.  A lineage in flight holds one of qcap credits; a warp
+// draws credits from the global count in chunks, keeps those of lineages
+// that end on it for its next fresh lineages, and gives back any above one
+// per lane.  Warp-collective, warp-uniform result: the first lineage offset
+// and the count; *exhausted is set once the batch is used up.
+__device__ __forceinline__ int take_fresh(const TraceArgs &a, const TiledArgs &ta, int want, int &credits,
+                                          int64_t &base, bool &exhausted) {
+  int *used = ta.ctl + 3 * ta.n_tiles;
+  int got = 0;
+  unsigned long long b = 0;
+  int ex = 0, c = credits;
+  if (lane_id() == 0) {
+    if (c < want) {
+      int req = 32 - c;
+      int old = atomicAdd(used, req);
+      int g = (int)ta.qcap - old;
+      g = g < 0 ? 0 : (g < req ? g : req);
+      if (g < req) atomicSub(used, req - g);
+      c += g;
+    }
+    int k = c < want ? c : want;
+    if (k > 0) {
+      const unsigned long long n = (unsigned long long)(a.lineage_end - a.lineage_begin);
+      b = atomicAdd(a.lineage_next, (unsigned long long)k);
+      unsigned long long left = b < n ? n - b : 0;
+      if (left <= (unsigned long long)k) ex = 1;
+      got = left < (unsigned long long)k ? (int)left : k;
+      c -= got;
+    }
+  }
+  got = __shfl_sync(0xffffffffu, got, 0);
+  b = __shfl_sync(0xffffffffu, b, 0);
+  credits = __shfl_sync(0xffffffffu, c, 0);
+  if (__shfl_sync(0xffffffffu, ex, 0)) exhausted = true;
+  base = (int64_t)b;
+  return got;
+}
+
+// The sub-domain trace (Section 3: the geometry is split into tiles; a beam
+// whose ray leaves a tile is sent to the tile it enters; exchanged beams are
+// served before new ones; idle workers take work from busy tiles), as one
+// persistent launch per batch.  Every warp has a home tile.  Lanes without
+// work take, in this order, hand-offs from the home tile's queue, hand-offs
+// from the other tiles' queues (a steal), and fresh lineages of the batch.  A
+// lineage keeps going while it stays in its tile -- a reflection starts in
+// the tile of its hit point -- and is pushed to the queue of the next tile
+// when its ray leaves the tile without a hit there.  The launch ends when the
+// batch has no fresh lineages left and no lineage is in flight (traced or
+// queued).  A warp with nothing to do waits at most watchdog_ns for work;
+// waits on a queue slot are bounded the same way.
 template <bool kMixed, bool kCount>
-__global__ void __launch_bounds__(kTraceThreads) k_trace_tiled(TraceArgs a, TiledArgs ta) {
+__global__ void __launch_bounds__(kTraceThreads, 5) k_trace_tiled(TraceArgs a, const __grid_constant__ TiledArgs ta) {
   __shared__ LineageSmem<kMixed> sm;
   const int t = threadIdx.x;
   const unsigned lane = lane_id();
+  const unsigned below = (1u << lane) - 1u;
   const MicGrid g = *a.grid;
-  const TileGrid tg = ta.tg;
-  TraceCounts cn = {0, 0, 0, 0, 0, 0, 0, 0};
+  const TileGrid &tg = ta.tg;  // read from parameter space, not held in registers
+  const TraceCounts cn = init_counts(sm, t);
+  const size_t qc = ta.qcap;
+  const unsigned qmask = ta.qcap - 1u;
+  int *const used = ta.ctl + 3 * ta.n_tiles;
+  int *const finished = used + 1;
+  const int n_batch = (int)(a.lineage_end - a.lineage_begin);
+  int credits = 0;  // warp-uniform
   LaneState ls = {-1, 0, -1, 0.0f, 0.0};
-  int slot = -1, tile = -1;
-  bool done = false;
-  const int home = (int)(blockIdx.x % (unsigned)ta.n_tiles);
-  int cursor = home, tried = 0;  // warp-uniform
+  bool active = false;
+  int tile = -1;
+  bool exhausted = false;  // warp-uniform: the batch has no fresh lineages left
+  const int home = (int)((blockIdx.x * (kTraceThreads / 32) + (threadIdx.x >> 5)) % (unsigned)ta.n_tiles);
+  unsigned long long idle_since = 0, last_prog = 0;
   const RaySrc rs{&sm.hi[kRowO][t], kMixed ? &sm.lo[kRowO][t] : &sm.hi[kRowO][t], kTraceThreads};
   while (true) {
-    bool need = !done && slot < 0;
-    if (ta.round == 0) {
-      int64_t mine = take_lineage(a, need);
-      if (need) {
-        if (mine >= 0) {
+    // ---- refill: hand-offs first (home tile, then steals), then fresh lineages
+    unsigned nm = __ballot_sync(0xffffffffu, !active);
+    if (nm) {
+      unsigned base;
+      int got;
+      int qt = take_handoffs(ta, home, __popc(nm), base, got);
+      if (qt >= 0 && !active) {
+        int rank = __popc(nm & below);
+        if (rank < got) {
+          unsigned pos = base + (unsigned)rank, gen = pos & ~qmask, slot = pos & qmask;
+          unsigned *sq = ta.seq + (size_t)qt * qc + slot;
+          // the item is counted in avail only after it is written, but the
+          // position handed out may belong to a producer still writing
+          if (wait_slot(a, ta, sq, gen + 1u)) {
+            load_state(ta.ring + (size_t)qt * kStateRows * qc + slot, qc, sm, t, ls);
+            st_release_u32(sq, gen + ta.qcap);
+            tile = qt;
+            active = true;
+            if (qt != home) cn[kCSteal]++;
+          }
+        }
+      }
+      nm = __ballot_sync(0xffffffffu, !active);
+      if (nm && !exhausted) {
+        int64_t fb;
+        int got_f = take_fresh(a, ta, __popc(nm), credits, fb, exhausted);
+        int rank = __popc(nm & below);
+        if (!active && rank < got_f) {
+          int64_t mine = a.lineage_begin + fb + rank;
           ls = LaneState{mine, 0, -1, 0.0f, 0.0};
           init_lineage(a, sm, t, mine);
-          slot = (int)(mine - a.lineage_begin);
+          active = true;
           float3 o = ld_hi3(sm, kRowO, t);
           tile = clampi((int)floorf((o.y - tg.gy0) / tg.wy), 0, tg.ty - 1) * tg.tx +
                  clampi((int)floorf((o.x - tg.gx0) / tg.wx), 0, tg.tx - 1);
-        } else {
-          done = true;
-        }
-      }
-    } else {
-      unsigned nm = __ballot_sync(0xffffffffu, need);
-      if (nm) {
-        const int leader = __ffs(nm) - 1, cnt = __popc(nm);
-        int got = 0, base = 0;
-        while (tried < ta.n_tiles && got == 0) {
-          if ((int)lane == leader) {
-            int old = atomicAdd(&ta.q_in_head[cursor], cnt);
-            int avail = __ldg(&ta.q_in_count[cursor]) - old;
-            got = avail < 0 ? 0 : (avail < cnt ? avail : cnt);
-            base = old;
-          }
-          got = __shfl_sync(0xffffffffu, got, leader);
-          base = __shfl_sync(0xffffffffu, base, leader);
-          if (got == 0) {
-            cursor = cursor + 1 == ta.n_tiles ? 0 : cursor + 1;
-            tried++;
-          }
-        }
-        if (need) {
-          int rank = __popc(nm & ((1u << lane) - 1u));
-          if (rank < got) {
-            slot = __ldg(&ta.q_in[(size_t)cursor * ta.cap + base + rank]);
-            tile = cursor;
-            load_state(ta, sm, t, slot, ls);
-            if (cursor != home) cn.steal++;
-          } else if (tried >= ta.n_tiles) {
-            done = true;
-          }
         }
       }
     }
-    if (__all_sync(0xffffffffu, done)) break;
-    if (done || slot < 0) continue;
+    if (!__any_sync(0xffffffffu, active)) {
+      // nothing to trace: done once every lineage of the batch has finished
+      const int fin = *(volatile int *)finished;
+      if (fin == n_batch) break;
+      if (*(volatile int *)&a.ctr->error) break;
+      // the watchdog runs while the launch as a whole makes no progress: no
+      // fresh lineage taken and none finished (both counts only grow)
+      const unsigned long long now = global_ns();
+      const unsigned long long prog = *(volatile unsigned long long *)a.lineage_next + (unsigned)fin;
+      if (idle_since == 0 || prog != last_prog) {
+        idle_since = now;
+        last_prog = prog;
+      } else if (now - idle_since > ta.watchdog_ns) {
+        if (lane == 0) watchdog_fired(a);
+        break;
+      }
+      __nanosleep(128);
+      continue;
+    }
+    idle_since = 0;
     // ---- search the current tile for this lane's ray
-    const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), a.t_eps, ls.dns);
-    Best best;
-    int hit = closest_hit<kMixed, kCount>(a.sc, r, rs, ls.dns64, best, &a.ctr->error, cn.nodes, cn.tris,
-                                          __ldg(&ta.roots[tile]), &tg, tile);
-    if (hit >= 0) {
-      // the hit lies in this tile; a reflected beam starts here as well
-      if (!finish_segment(a, sm, t, r, best, hit, ls, g, cn)) slot = -1;
-      continue;
+    int next = -1;
+    bool ended = false;
+    if (active) {
+      const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), a.t_eps, ls.dns);
+      Best best;
+      int hit = closest_hit<kMixed, kCount>(a.sc, r, rs, ls.dns64, best, &a.ctr->error, cn[kCNodes], cn[kCTris],
+                                            __ldg(&ta.roots[tile]), &tg, tile);
+      if (hit >= 0) {
+        // the hit lies in this tile; a reflected beam starts here as well
+        if (!finish_segment(a, sm, t, r, best, hit, ls, g, cn)) ended = true;
+      } else {
+        // no hit in this tile: step to the next tile along the ray whose
+        // geometry the ray can reach -- tiles whose root boxes it misses
+        // could give no hit, so the lane walks past them itself
+        int ix = tile % tg.tx, iy = tile / tg.tx;
+        bool leaves = false;
+        while (true) {
+          float tex = kInf, tey = kInf;
+          if (r.d.x > 0.0f) tex = (tg.gx0 + (ix + 1) * tg.wx - r.o.x) / r.d.x;
+          else if (r.d.x < 0.0f) tex = (tg.gx0 + ix * tg.wx - r.o.x) / r.d.x;
+          if (r.d.y > 0.0f) tey = (tg.gy0 + (iy + 1) * tg.wy - r.o.y) / r.d.y;
+          else if (r.d.y < 0.0f) tey = (tg.gy0 + iy * tg.wy - r.o.y) / r.d.y;
+          leaves = tex == kInf && tey == kInf;
+          if (!leaves) {
+            if (tex <= tey) ix += r.d.x > 0.0f ? 1 : -1;
+            if (tey <= tex) iy += r.d.y > 0.0f ? 1 : -1;
+            leaves = ix < 0 || ix >= tg.tx || iy < 0 || iy >= tg.ty;
+          }
+          if (leaves || root_reachable(a.sc, __ldg(&ta.roots[iy * tg.tx + ix]), r)) break;
+        }
+        if (leaves) {
+          // the ray leaves the grid, and with it every triangle: it escapes
+          finish_segment(a, sm, t, r, best, -1, ls, g, cn);
+          ended = true;
+        } else {
+          next = iy * tg.tx + ix;
+        }
+      }
+      if (ended) active = false;
     }
-    // no hit in this tile: step to the tile the ray enters next
-    int ix = tile % tg.tx, iy = tile / tg.tx;
-    float tex = kInf, tey = kInf;
-    if (r.d.x > 0.0f) tex = (tg.gx0 + (ix + 1) * tg.wx - r.o.x) / r.d.x;
-    else if (r.d.x < 0.0f) tex = (tg.gx0 + ix * tg.wx - r.o.x) / r.d.x;
-    if (r.d.y > 0.0f) tey = (tg.gy0 + (iy + 1) * tg.wy - r.o.y) / r.d.y;
-    else if (r.d.y < 0.0f) tey = (tg.gy0 + iy * tg.wy - r.o.y) / r.d.y;
-    bool leaves = tex == kInf && tey == kInf;
-    if (!leaves) {
-      if (tex <= tey) ix += r.d.x > 0.0f ? 1 : -1;
-      if (tey <= tex) iy += r.d.y > 0.0f ? 1 : -1;
-      leaves = ix < 0 || ix >= tg.tx || iy < 0 || iy >= tg.ty;
+    unsigned em = __ballot_sync(0xffffffffu, ended);
+    if (em) {
+      credits += __popc(em);
+      int give = credits > 32 ? credits - 32 : 0;
+      credits -= give;
+      if ((int)lane == __ffs(em) - 1) {
+        if (give) atomicSub(used, give);
+        atomicAdd(finished, __popc(em));
+      }
     }
-    if (leaves) {
-      // the ray leaves the grid, and with it every triangle: it escapes
-      finish_segment(a, sm, t, r, best, -1, ls, g, cn);
-      slot = -1;
-      continue;
+    // ---- hand-offs: one reservation per target tile, consecutive slots
+    bool push = next >= 0;
+    unsigned pm = __ballot_sync(0xffffffffu, push);
+    if (pm && push) {
+      unsigned grp = __match_any_sync(pm, next);
+      int gl = __ffs(grp) - 1;
+      int n = __popc(grp);
+      unsigned base = 0;
+      if ((int)lane == gl) base = (unsigned)atomicAdd(&ta.ctl[ta.n_tiles + next], n);
+      base = __shfl_sync(grp, base, gl);
+      unsigned pos = base + (unsigned)__popc(grp & below), gen = pos & ~qmask, slot = pos & qmask;
+      unsigned *sq = ta.seq + (size_t)next * qc + slot;
+      // with at most qcap lineages in flight the slot's previous item has
+      // been taken; its consumer may still be reading it
+      if (wait_slot(a, ta, sq, gen)) {
+        save_state(ta.ring + (size_t)next * kStateRows * qc + slot, qc, sm, t, ls);
+        st_release_u32(sq, gen + 1u);
+      }
+      __syncwarp(grp);
+      if ((int)lane == gl) atomicAdd(&ta.ctl[2 * ta.n_tiles + next], n);
+      cn[kCHand]++;
+      active = false;
     }
-    // hand-off to the neighbouring tile, processed in the next round
-    int next = iy * tg.tx + ix;
-    save_state(ta, sm, t, slot, ls);
-    int pos = atomicAdd(&ta.q_out_count[next], 1);
-    if (pos < ta.cap) ta.q_out[(size_t)next * ta.cap + pos] = slot;
-    else atomicExch(&a.ctr->error, BT_E_QUEUE_FULL);
-    cn.hand++;
-    slot = -1;
   }
   flush_counts(a, cn, kCount);
 }
@@ -763,8 +951,6 @@ static cudaError_t launch_tiled_t(cudaStream_t st, const TraceArgs &a, const Til
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int64_t blocks = (int64_t)n_sm * per_sm;
-  // at least one block per tile so that every tile has a home warp
-  if (blocks < ta.n_tiles) blocks = ta.n_tiles;
   k_trace_tiled<kMixed, kCount><<<(int)blocks, kTraceThreads, 0, st>>>(a, ta);
   return cudaGetLastError();
 }
@@ -775,6 +961,15 @@ cudaError_t launch_trace_tiled(cudaStream_t st, const TraceArgs &a, const TiledA
   else e = a.count_work ? launch_tiled_t<false, true>(st, a, ta, n_sm) : launch_tiled_t<false, false>(st, a, ta, n_sm);
   note_launches(1);
   return e;
+}
+
+int tiled_resident_lanes(int n_sm) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tiled<true, false>, kTraceThreads, 0) !=
+      cudaSuccess)
+    per_sm = 8;
+  if (per_sm < 1) per_sm = 1;
+  return n_sm * per_sm * kTraceThreads;
 }
 
 // Closest hit of arbitrary float32 rays (the axis-ray query of the trace
@@ -798,7 +993,7 @@ __global__ void __launch_bounds__(128) k_cast(DevScene sc, const float *o, const
   rl[3][t] = D.x.lo; rl[4][t] = D.y.lo; rl[5][t] = D.z.lo;
   Ray r = make_ray(O, df3_hi(D), t_eps, (float)dns);
   Best best;
-  unsigned long long a = 0, b = 0;
+  unsigned a = 0, b = 0;
   int slot = closest_hit<true, false>(sc, r, RaySrc{&rh[0][t], &rl[0][t], 128}, dns, best, err, a, b, sc.root);
   t_out[i] = slot >= 0 ? (best.has64 ? (float)best.t64 : best.t) : kInf;
   tri_out[i] = slot >= 0 ? best.id : -1;
