@@ -13,6 +13,10 @@ microphone test and energy scatter, level readout.
   e2e     the same calls with pinned host buffers, host->device copies and the
           device->host read of the levels inside the timed region
 
+The district configuration splits the city plane into 4 x 4 sub-domains
+linked by hand-off queues (the default --tiles); the line also carries the
+same workload timed without the split (`untiled`).
+
 `--impl reference` times the FP64 CPU oracle instead, on a bounded sample of
 the same workload (a seeded subset of the sources per step).
 """
@@ -46,7 +50,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--tiles", default="1x1", help="sub-domain grid, e.g. 4x4")
+    ap.add_argument("--tiles", default="4x4",
+                    help="sub-domain grid; the district configuration splits the plane 4x4")
+    ap.add_argument("--no-untiled", action="store_true",
+                    help="skip the secondary timing of the same workload without sub-domains")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"],
                     help="mixed: float64 image-source chain (the parity-checked default)")
     return ap.parse_args()
@@ -142,10 +149,14 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic():
+def trace_kernel_name(tiles):
+    return "k_trace" if tuple(tiles) == (1, 1) else "k_trace_tiled"
+
+
+def ncu_traffic(kernel):
     """DRAM bytes per launch of the traversal kernel from the committed ncu
     summary, only if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "k_trace_traffic.json")
+    p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
@@ -210,6 +221,18 @@ def run_ours(args, rank, world):
         step(d_in, d_level)
     with Clocks(dev.index) as clk:
         ms, stats, launches = timed(d_in, d_level, args.steps)
+    untiled = None
+    if tiles != (1, 1) and not args.no_untiled:
+        # the same workload without the sub-domain split, for comparison
+        params.tiles_x, params.tiles_y = 1, 1
+        for _ in range(args.warmup):
+            step(d_in, d_level)
+        u_ms, u_stats, _ = timed(d_in, d_level, args.steps)
+        untiled = {"value": sum(s["segments"] for s in u_stats) / (sum(u_ms) * 1e-3),
+                   "ms_per_step": sum(u_ms) / len(u_ms),
+                   "kernel_ms_per_step": sum(s["trace_kernel_ms"] for s in u_stats) / len(u_stats),
+                   "launches_per_step": sum(s["trace_launches"] for s in u_stats) / len(u_stats)}
+        params.tiles_x, params.tiles_y = tiles
     segs = sum(s["segments"] for s in stats)
     contrib = sum(s["contributions"] for s in stats)
     total_ms = sum(ms)
@@ -225,12 +248,12 @@ def run_ours(args, rank, world):
     bytes_per_launch = alg_bytes / max(1, cst["trace_launches"])
     achieved = bytes_per_launch / (tk / max(1, tl) * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = ncu_traffic()
+    traffic = ncu_traffic(trace_kernel_name(tiles))
     res = dict(segs=segs, contrib=contrib, total_ms=total_ms, ms=ms, launches=launches,
                stats=stats[-1], tk=tk, sk=sk, tl=tl, alg_bytes=alg_bytes,
                bytes_per_launch=bytes_per_launch, achieved=achieved, peak=peak,
                peak_kind=peak_kind, traffic=traffic, clocks=clk.summary(), work=cst, w=w,
-               tiles=tiles)
+               tiles=tiles, untiled=untiled)
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         h_in = {k: pin(v.cpu().numpy()) for k, v in d_in.items()}
@@ -291,7 +314,7 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {**describe(w, (1, 1)),
+            "config": {**describe(w, tuple(int(v) for v in args.tiles.lower().split("x"))),
                        "sample": f"{n} of {len(w.src)} sources per step (seeded), all microphones"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{n} of {len(w.src)} sources per step, {threads} threads"},
@@ -340,9 +363,11 @@ def main():
     value = segs / (total_ms * 1e-3)
     cfg = describe(w, res["tiles"])
     cfg.update({"l2": "flushed before every step (256 MB write, outside the events)",
-                "precision": ("MIXED: FP64 image-source chain, FP32 traversal with FP64 re-test of "
-                              "ambiguous hits, FP32 microphone tests with FP64 re-test near planes, "
-                              "FP64 energy accumulation") if args.precision == "mixed" else
+                "precision": ("MIXED: image-source chain in float pairs (double-float, about 48 "
+                              "bits) on the FP32 pipe, FP32 watertight traversal with an FP64 "
+                              "re-test of ambiguous hits, FP32 microphone tests with a float-pair "
+                              "re-test near cone and end planes, FP64 energy accumulation")
+                             if args.precision == "mixed" else
                              "FP32 chain, traversal and microphone tests, FP64 energy accumulation",
                 "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -351,7 +376,8 @@ def main():
             "data": "synthetic", "config": cfg, "clocks": res["clocks"],
             "gpu_launches": res["launches"],
             "contributions_per_s": res["contrib"] * world / (total_ms * 1e-3),
-            "roofline": {"kernel": "k_trace", "bound": "hbm", "achieved": res["achieved"],
+            "roofline": {"kernel": trace_kernel_name(res["tiles"]), "bound": "hbm",
+                         "achieved": res["achieved"],
                          "peak": res["peak"], "unit": "GB/s",
                          "frac": res["achieved"] / res["peak"], "traffic": res["traffic"],
                          "peak_kind": res["peak_kind"],
@@ -366,6 +392,8 @@ def main():
                                                    "steals", "rounds")}}
     if "e2e" in res:
         line["e2e"] = res["e2e"]
+    if res["untiled"]:
+        line["untiled"] = res["untiled"]
     if not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         cb = oracle_sample(w, args.cpu_seconds, threads)

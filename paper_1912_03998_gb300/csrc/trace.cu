@@ -575,8 +575,11 @@ __device__ __forceinline__ int64_t take_lineage(const TraceArgs &a, bool need) {
 // Persistent warps: every lane works on one lineage at a time and takes the
 // next one from a global counter as soon as its lineage ends, so a warp stays
 // full until the batch runs out (warp-vote refill of finished lanes).
+// Six resident blocks per SM (at most 80 registers a thread): the traversal
+// is latency-bound, and on the district workload this beat both fewer blocks
+// without spills and more blocks with heavier spills.
 template <bool kMixed, bool kCount>
-__global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
+__global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
   __shared__ LineageSmem<kMixed> sm;
   const int t = threadIdx.x;
   const MicGrid g = *a.grid;
@@ -784,8 +787,9 @@ __device__ __forceinline__ int take_fresh(const TraceArgs &a, const TiledArgs &t
 // batch has no fresh lineages left and no lineage is in flight (traced or
 // queued).  A warp with nothing to do waits at most watchdog_ns for work;
 // waits on a queue slot are bounded the same way.
+// Six resident blocks per SM, as for k_trace.
 template <bool kMixed, bool kCount>
-__global__ void __launch_bounds__(kTraceThreads, 5) k_trace_tiled(TraceArgs a, const __grid_constant__ TiledArgs ta) {
+__global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, const __grid_constant__ TiledArgs ta) {
   __shared__ LineageSmem<kMixed> sm;
   const int t = threadIdx.x;
   const unsigned lane = lane_id();
