@@ -51,10 +51,13 @@ extern "C" {
 /* Precision of the trace (Section 2 does not fix one).
  * BT_PREC_FP32: the whole beam lineage (directions, image-source apex, ray
  *   origin, cone planes) in float32; float64 energy accumulation.
- * BT_PREC_MIXED (default): the image-source chain in float64; float32
- *   traversal whose ambiguous triangle tests (ray within 1e-4 relative of an
- *   edge) and near-equal hit distances are settled in float64; float32
- *   microphone tests relative to the float64 apex; float64 accumulation.
+ * BT_PREC_MIXED (default): the image-source chain (apex, cone normals, ray
+ *   origin and direction) in float pairs (double-float, about 48 bits) on the
+ *   float32 pipe; float32 watertight traversal whose ambiguous triangle tests
+ *   (ray within 1e-4 relative of an edge) are re-done in float64, near-equal
+ *   hit distances settled in float64; float32 microphone tests relative to
+ *   the apex, re-done in float pairs near the cone and end planes; float64
+ *   energy accumulation.
  * BT_PREC_FP64 is not implemented yet and is rejected with BT_E_INVALID. */
 #define BT_PREC_FP32 0
 #define BT_PREC_MIXED 1
