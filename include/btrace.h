@@ -210,6 +210,20 @@ int bt_cast_rays(bt_ctx *ctx, int32_t scene_id, const float *origins, const floa
 int bt_trace_noalloc(bt_ctx *ctx, int32_t scene_id, const bt_trace_params *p, double *level_db,
                      int32_t *path_count);
 
+/* Install a trace result computed elsewhere into a scene, replacing its last
+ * result: the sum of the partial results of traces of disjoint subsets of the
+ * scene's sources (Section 3: processes trace their own beams and their
+ * results are gathered; beams of different sources never interact, so the
+ * sum over source shards is the result for all sources).  A caller splits
+ * the sources over contexts or GPUs, reads each partial with bt_read_levels
+ * (intensity, path_count), sums them (e.g. an all-reduce), installs the sum
+ * here, and reads the levels with bt_read_levels.
+ *   intensity  [n_m][n_bands] float64, W/m^2, input microphone order
+ *   path_count [n_m] int32, or NULL for zero counts
+ * The scene's microphones must be set (BT_E_STATE otherwise).  Stats of the
+ * scene are zeroed. */
+int bt_set_result(bt_ctx *ctx, int32_t scene_id, const double *intensity, const int32_t *path_count);
+
 /* Message of the last error of the context ("" if none).  Valid until the
  * next call on the context. */
 const char *bt_last_error(const bt_ctx *ctx);

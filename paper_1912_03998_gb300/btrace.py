@@ -57,7 +57,7 @@ _lib = None
 EXPECTED_SYMBOLS = ("bt_params_default", "bt_create", "bt_destroy", "bt_load_scene",
                     "bt_unload_scene", "bt_set_sources", "bt_set_microphones", "bt_trace",
                     "bt_read_levels", "bt_last_error", "bt_kernel_launches", "bt_cast_rays",
-                    "bt_trace_noalloc")
+                    "bt_trace_noalloc", "bt_set_result")
 
 
 def lib_path() -> str:
@@ -87,6 +87,7 @@ def lib():
             L.bt_last_error.restype = C.c_char_p
             L.bt_cast_rays.argtypes = [p, i32, p, p, p, i64, C.c_float, p, p]
             L.bt_trace_noalloc.argtypes = [p, i32, C.POINTER(bt_trace_params), p, p]
+            L.bt_set_result.argtypes = [p, i32, p, p]
             L.bt_kernel_launches.argtypes = []
             L.bt_kernel_launches.restype = C.c_int64
             for name in EXPECTED_SYMBOLS:
@@ -203,6 +204,14 @@ def bt_read_levels(ctx, scene_id: int, level_db=None, intensity=None, path_count
                               out_ptr(path_count), C.byref(st))
     _check(rc, ctx)
     return st.as_dict()
+
+
+def bt_set_result(ctx, scene_id: int, intensity, path_count=None):
+    """Install a summed result ([n_m][n_bands] float64 intensity, [n_m] int32
+    counts or None) in input microphone order."""
+    pi, _, ki = _arr(intensity, np.float64)
+    pc, _, kc = _arr(path_count, np.int32)
+    _check(lib().bt_set_result(ctx, int(scene_id), pi, pc), ctx)
 
 
 def bt_cast_rays(ctx, scene_id: int, origins, dirs, start_normals=None, t_eps_m: float = 1e-3):

@@ -785,6 +785,30 @@ BT_API int bt_read_levels(bt_ctx *c, int32_t scene_id, double *level_db, double 
   return BT_OK;
 }
 
+BT_API int bt_set_result(bt_ctx *c, int32_t scene_id, const double *intensity, const int32_t *path_count) {
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  SceneState *s;
+  TRY(scene_ref(c, scene_id, &s));
+  if (!s->has_mics) return fail(c, BT_E_STATE, "scene %d has no microphones", scene_id);
+  if (s->n_mics > 0 && !intensity) return fail(c, BT_E_INVALID, "NULL intensity");
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  const size_t nv = (size_t)s->n_mics * s->n_bands;
+  TRY(ensure(c, s->out_int, sizeof(double) * (nv ? nv : 1)));
+  TRY(ensure(c, s->out_cnt, sizeof(int) * (size_t)(s->n_mics ? s->n_mics : 1)));
+  if (nv) CK(cudaMemcpyAsync(s->out_int.p, intensity, sizeof(double) * nv, cudaMemcpyDefault, st));
+  if (path_count && s->n_mics)
+    CK(cudaMemcpyAsync(s->out_cnt.p, path_count, sizeof(int) * (size_t)s->n_mics, cudaMemcpyDefault, st));
+  CK(bt::launch_set_result(st, (const double *)s->out_int.p, path_count ? (const int *)s->out_cnt.p : nullptr,
+                           (const float4 *)s->mics.p, s->n_mics, s->n_bands, (double *)s->energy.p,
+                           (int *)s->count.p));
+  CK(cudaStreamSynchronize(st));
+  memset(&s->stats, 0, sizeof(s->stats));
+  s->traced = true;
+  return BT_OK;
+}
+
 BT_API int bt_cast_rays(bt_ctx *c, int32_t scene_id, const float *origins, const float *dirs,
                         const float *start_normals, int64_t n, float t_eps_m, float *t_out,
                         int32_t *tri_out) {

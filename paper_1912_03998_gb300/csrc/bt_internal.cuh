@@ -512,6 +512,8 @@ constexpr int kStateRows = 56;
 cudaError_t launch_cast(cudaStream_t st, const DevScene &sc, const float *o, const float *d, const float *ns,
                         int64_t n, float t_eps, float *t_out, int *tri_out, int *err);
 cudaError_t launch_scatter(cudaStream_t st, const ScatterArgs &a, int n_sm);
+cudaError_t launch_set_result(cudaStream_t st, const double *intensity, const int *count_in, const float4 *mics,
+                              int64_t n_m, int n_bands, double *energy, int *count);
 cudaError_t launch_levels(cudaStream_t st, const double *energy, const int *count, const float4 *mics,
                           int64_t n_m, int n_bands, double *level_db, double *intensity, int *path_count);
 }  // namespace bt

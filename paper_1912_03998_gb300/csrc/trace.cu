@@ -1296,4 +1296,26 @@ cudaError_t launch_levels(cudaStream_t st, const double *energy, const int *coun
   return cudaGetLastError();
 }
 
+// Install a result given in input microphone order (partial results of
+// source shards, summed by the caller) into a scene's accumulators, which are
+// kept in binned order.
+__global__ void k_set_result(const double *intensity, const int *count_in, const float4 *mics, int64_t n_m,
+                             int n_bands, double *energy, int *count) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n_m) return;
+  int64_t orig = __float_as_int(mics[p].w);
+  for (int b = 0; b < kMaxBands; b++) energy[p * kMaxBands + b] = b < n_bands ? intensity[orig * n_bands + b] : 0.0;
+  count[p] = count_in ? count_in[orig] : 0;
+}
+
+cudaError_t launch_set_result(cudaStream_t st, const double *intensity, const int *count_in, const float4 *mics,
+                              int64_t n_m, int n_bands, double *energy, int *count) {
+  if (n_m == 0) return cudaSuccess;
+  int threads = 256;
+  k_set_result<<<(int)((n_m + threads - 1) / threads), threads, 0, st>>>(intensity, count_in, mics, n_m,
+                                                                         n_bands, energy, count);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace bt

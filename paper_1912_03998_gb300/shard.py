@@ -1,0 +1,59 @@
+"""Source sharding of one problem over several ranks (GPUs or contexts).
+
+Beams of different sources never interact (Section 2: every beam carries its
+own source's energy; Section 3: processes trace their own beams and their
+results are gathered), so the result for all sources is the sum of the
+results for disjoint subsets of them.  Each rank traces one contiguous block
+of the sources, the partial intensities and path counts are summed over the
+ranks by one all-reduce, and every rank installs the sum with bt_set_result
+and reads the levels through its own level kernel.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import btrace
+
+
+def source_block(n_sources: int, rank: int, world: int) -> tuple[int, int]:
+    """The block [lo, hi) of sources owned by `rank`: contiguous, sizes
+    differing by at most one, blocks in rank order covering 0..n_sources."""
+    if world < 1 or not 0 <= rank < world or n_sources < 0:
+        raise ValueError("bad shard request")
+    q, r = divmod(n_sources, world)
+    lo = rank * q + min(rank, r)
+    return lo, lo + q + (1 if rank < r else 0)
+
+
+def allreduce_result(intensity, path_count, group=None):
+    """Sum a float64 intensity tensor and an int32 path-count tensor over the
+    ranks of `group`, in place (CPU tensors under gloo, CUDA tensors under
+    NCCL)."""
+    import torch.distributed as dist
+    dist.all_reduce(intensity, op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(path_count, op=dist.ReduceOp.SUM, group=group)
+    return intensity, path_count
+
+
+def trace_sharded(tracer, w, rank: int, world: int, group=None, **params):
+    """Trace workload `w` with its sources split over `world` ranks; every
+    rank gets the levels for all sources.  Returns dict(level, I, cnt) as
+    numpy arrays and the scene id holding the summed result."""
+    import torch
+    import torch.distributed as dist
+    lo, hi = source_block(len(w.src), rank, world)
+    part = w.subset_sources(np.arange(lo, hi))
+    g = tracer.run(part, **params)
+    on_gpu = dist.get_backend(group) == "nccl"
+    dev = torch.device("cuda", torch.cuda.current_device()) if on_gpu else torch.device("cpu")
+    I = torch.from_numpy(g["I"]).to(dev)
+    cnt = torch.from_numpy(g["cnt"]).to(dev)
+    allreduce_result(I, cnt, group)
+    sid = g["scene_id"]
+    btrace.bt_set_result(tracer.ctx, sid, I, cnt)
+    n, nb = I.shape
+    level = np.empty((n, nb), np.float64)
+    I_out = np.empty((n, nb), np.float64)
+    cnt_out = np.empty(n, np.int32)
+    btrace.bt_read_levels(tracer.ctx, sid, level, I_out, cnt_out)
+    return dict(level=level, I=I_out, cnt=cnt_out, scene_id=sid)

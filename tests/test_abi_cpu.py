@@ -63,5 +63,6 @@ def test_null_arguments_are_rejected_without_a_gpu(libpath):
     assert L.bt_destroy(None) == btrace.BT_OK
     assert L.bt_create(None, 0, None) == btrace.BT_E_INVALID
     assert L.bt_trace(None, 0, None) == btrace.BT_E_INVALID
+    assert L.bt_set_result(None, 0, None, None) == btrace.BT_E_INVALID
     assert L.bt_last_error(None) == b"null context"
     assert btrace.bt_kernel_launches() == 0

@@ -1,0 +1,80 @@
+"""Source sharding across ranks (the multi-GPU path), on CPU: two gloo ranks
+each trace a block of the sources with the oracle, sum their partial
+intensities and path counts with the package's all-reduce, and must obtain
+the oracle's result for all sources (Section 3: processes trace their own
+beams and their results are gathered)."""
+import multiprocessing as mp
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_1912_03998_gb300 import shard, synth
+
+
+def test_source_blocks_partition_the_sources():
+    for n in (0, 1, 5, 16, 1000, 1001):
+        for world in (1, 2, 3, 4, 7):
+            blocks = [shard.source_block(n, r, world) for r in range(world)]
+            assert blocks[0][0] == 0 and blocks[-1][1] == n
+            for (a, b), (c, d) in zip(blocks, blocks[1:]):
+                assert b == c
+            sizes = [b - a for a, b in blocks]
+            assert max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        shard.source_block(5, 2, 2)
+
+
+def _workload():
+    return synth.tiny_city(seed=3, level=3, max_order=3, n_sources=5)
+
+
+def _rank_main(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch
+    import torch.distributed as dist
+    from oracle import oracle as O
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w = _workload()
+        lo, hi = shard.source_block(len(w.src), rank, world)
+        r = O.trace(O.Scene(w.scene), w.src[lo:hi], w.power[lo:hi], w.level, w.mics, w.max_order)
+        I = torch.from_numpy(np.ascontiguousarray(r["I"], np.float64))
+        cnt = torch.from_numpy(np.ascontiguousarray(r["cnt"], np.int32))
+        shard.allreduce_result(I, cnt)
+        np.save(os.path.join(out_dir, f"I{rank}.npy"), I.numpy())
+        np.save(os.path.join(out_dir, f"c{rank}.npy"), cnt.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks_sum_to_the_full_result(oracle_mod, tmp_path, world):
+    pytest.importorskip("torch")
+    w = _workload()
+    full = oracle_mod.trace(oracle_mod.Scene(w.scene), w.src, w.power, w.level, w.mics, w.max_order)
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, str(tmp_path))) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        if p.is_alive():
+            p.kill()
+            p.join()
+        assert p.exitcode == 0
+    for r in range(world):
+        I = np.load(tmp_path / f"I{r}.npy")
+        c = np.load(tmp_path / f"c{r}.npy")
+        assert (c == full["cnt"]).all()
+        assert np.allclose(I, full["I"], rtol=1e-12, atol=0)
