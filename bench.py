@@ -54,8 +54,8 @@ def parse():
                     help="sub-domain grid; the district configuration splits the plane 4x4")
     ap.add_argument("--no-untiled", action="store_true",
                     help="skip the secondary timing of the same workload without sub-domains")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"],
-                    help="mixed: float64 image-source chain (the parity-checked default)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"],
+                    help="mixed: float-pair image-source chain (the parity-checked default)")
     return ap.parse_args()
 
 
@@ -187,7 +187,8 @@ def run_ours(args, rank, world):
     params = btrace.bt_params_default()
     params.max_order = w.max_order
     params.tiles_x, params.tiles_y = tiles
-    params.precision = btrace.BT_PREC_MIXED if args.precision == "mixed" else btrace.BT_PREC_FP32
+    params.precision = {"mixed": btrace.BT_PREC_MIXED, "fp32": btrace.BT_PREC_FP32,
+                        "fp64": btrace.BT_PREC_FP64}[args.precision]
     l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(inp, level_out):
@@ -368,11 +369,15 @@ def main():
                               "re-test of ambiguous hits, FP32 microphone tests with a float-pair "
                               "re-test near cone and end planes, FP64 energy accumulation")
                              if args.precision == "mixed" else
+                             ("FP64 image-source chain, triangle tests, microphone tests and "
+                              "contributions; FP32 BVH boxes and band powers; FP64 accumulation")
+                             if args.precision == "fp64" else
                              "FP32 chain, traversal and microphone tests, FP64 energy accumulation",
                 "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32",
             "data": "synthetic", "config": cfg, "clocks": res["clocks"],
             "gpu_launches": res["launches"],
             "contributions_per_s": res["contrib"] * world / (total_ms * 1e-3),

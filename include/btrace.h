@@ -58,7 +58,12 @@ extern "C" {
  *   hit distances settled in float64; float32 microphone tests relative to
  *   the apex, re-done in float pairs near the cone and end planes; float64
  *   energy accumulation.
- * BT_PREC_FP64 is not implemented yet and is rejected with BT_E_INVALID. */
+ * BT_PREC_FP64: the image-source chain in float64; every triangle test in
+ *   float64 (Moller-Trumbore on the float64 ray; the BVH boxes stay float32,
+ *   grown to be conservative); every microphone test and contribution in
+ *   float64 (the apex exact, cone normals to about 48 bits); band powers
+ *   W_b prod(r_b) in float32; float64 accumulation.  Slower: GB300 issues
+ *   float64 at a small fraction of the float32 rate. */
 #define BT_PREC_FP32 0
 #define BT_PREC_MIXED 1
 #define BT_PREC_FP64 2

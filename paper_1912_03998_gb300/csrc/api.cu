@@ -553,8 +553,8 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   if (p->max_order < 0 || p->max_order > 32) return fail(c, BT_E_INVALID, "max_order %d not in 0..32", p->max_order);
   if (!(p->t_eps_m > 0.0f) || !isfinite(p->t_eps_m)) return fail(c, BT_E_INVALID, "t_eps_m must be > 0");
   if (!(p->energy_threshold_w >= 0.0f)) return fail(c, BT_E_INVALID, "energy_threshold_w must be >= 0");
-  if (p->precision != BT_PREC_MIXED && p->precision != BT_PREC_FP32)
-    return fail(c, BT_E_INVALID, "precision %d not implemented (BT_PREC_FP32 or BT_PREC_MIXED)", p->precision);
+  if (p->precision != BT_PREC_MIXED && p->precision != BT_PREC_FP32 && p->precision != BT_PREC_FP64)
+    return fail(c, BT_E_INVALID, "unknown precision %d", p->precision);
   if (p->tiles_x < 1 || p->tiles_y < 1 || p->tiles_x > BT_MAX_TILES || p->tiles_y > BT_MAX_TILES)
     return fail(c, BT_E_INVALID, "tiles %dx%d not in 1..%d per axis", p->tiles_x, p->tiles_y, BT_MAX_TILES);
   if (p->chunk_beams < 0) return fail(c, BT_E_INVALID, "chunk_beams must be >= 0");
@@ -635,8 +635,8 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   ta.lineage_next = c->d_lineage_next;
   ta.ctr = c->d_ctr;
   ta.count_work = p->count_work ? 1 : 0;
-  ta.mixed = p->precision == BT_PREC_MIXED ? 1 : 0;
-  if (ta.mixed && total > 0) {
+  ta.prec = p->precision;
+  if (ta.prec == BT_PREC_MIXED && total > 0) {
     if (c->beam_table_level != s->level) {
       TRY(ensure(c, c->beam_table, sizeof(float) * 24 * (size_t)n_beams));
       CK(bt::launch_beam_table(st, s->level, (float *)c->beam_table.p));
@@ -648,6 +648,8 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   memset(&sa, 0, sizeof(sa));
   sa.tris = ta.sc.tris;
   sa.planes_df = ta.sc.planes_df;
+  sa.planes64 = ta.sc.planes64;
+  sa.fp64 = p->precision == BT_PREC_FP64 ? 1 : 0;
   sa.segs = ta.segs;
   sa.seg_count = c->d_seg_count;
   sa.seg_capacity = cap;
@@ -890,8 +892,8 @@ BT_API int bt_trace_noalloc(bt_ctx *c, int32_t scene_id, const bt_trace_params *
   if (p->max_order < 0 || p->max_order > 32) return fail(c, BT_E_INVALID, "max_order %d not in 0..32", p->max_order);
   if (!(p->t_eps_m > 0.0f) || !isfinite(p->t_eps_m)) return fail(c, BT_E_INVALID, "t_eps_m must be > 0");
   if (!(p->energy_threshold_w >= 0.0f)) return fail(c, BT_E_INVALID, "energy_threshold_w must be >= 0");
-  if (p->precision != BT_PREC_MIXED && p->precision != BT_PREC_FP32)
-    return fail(c, BT_E_INVALID, "precision %d not implemented (BT_PREC_FP32 or BT_PREC_MIXED)", p->precision);
+  if (p->precision != BT_PREC_MIXED && p->precision != BT_PREC_FP32 && p->precision != BT_PREC_FP64)
+    return fail(c, BT_E_INVALID, "unknown precision %d", p->precision);
   if (p->tiles_x != 1 || p->tiles_y != 1)
     return fail(c, BT_E_INVALID, "tiles %dx%d: only 1x1 is implemented in this build", p->tiles_x, p->tiles_y);
   if (s->level > BT_NOALLOC_MAX_LEVEL)
@@ -966,12 +968,14 @@ BT_API int bt_trace_noalloc(bt_ctx *c, int32_t scene_id, const bt_trace_params *
   ta.lineage_next = lineage_next;
   ta.ctr = ctr;
   ta.count_work = 0;
-  ta.mixed = mixed;
+  ta.prec = p->precision;
   ta.beam_table = mixed ? beam_table : nullptr;
   bt::ScatterArgs sa;
   memset(&sa, 0, sizeof(sa));
   sa.tris = ta.sc.tris;
   sa.planes_df = ta.sc.planes_df;
+  sa.planes64 = ta.sc.planes64;
+  sa.fp64 = p->precision == BT_PREC_FP64 ? 1 : 0;
   sa.segs = segs;
   sa.seg_count = seg_count;
   sa.seg_capacity = cap;

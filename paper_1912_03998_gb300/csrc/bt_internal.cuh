@@ -146,13 +146,15 @@ struct TraceArgs {
   unsigned long long seg_capacity;
   Counters *ctr;
   int count_work;
-  int mixed;  // 1: float64 image-source chain (BT_PREC_MIXED), 0: float32 (BT_PREC_FP32)
+  int prec;   // BT_PREC_FP32, BT_PREC_MIXED or BT_PREC_FP64
   const float *beam_table;   // MIXED: per beam 3 cone normals + axis as float pairs: [n_beams][12] hi, then lo
 };
 
 struct ScatterArgs {
   const Tri *tris;          // leaf order (start/end plane vertices)
   const PlaneDF *planes_df; // leaf order
+  const Plane64 *planes64;  // leaf order
+  int fp64;                 // 1: every microphone test in float64 (BT_PREC_FP64)
   const Seg *segs;
   const unsigned long long *seg_count;
   unsigned long long seg_capacity;

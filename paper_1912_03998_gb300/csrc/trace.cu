@@ -31,6 +31,9 @@
 
 namespace bt {
 
+// precision variants of the trace kernels (BT_PREC_*)
+constexpr int kPF32 = 0, kPMixed = 1, kPF64 = 2;
+
 // Regular icosahedron: unit vertices (the cyclic permutations of
 // (0, +-1, +-phi), normalised) and its 20 faces, counter-clockwise seen
 // from outside.  Vertex coordinates are 0, +-A or +-B with
@@ -137,10 +140,17 @@ struct Best {
 
 // Ray as float pairs in shared memory: rows 0..5 of `hi` and `lo` hold origin
 // xyz and direction xyz, `stride` floats apart.
+// In FP64 mode `dv` points at the same rows held as float64.
 struct RaySrc {
   const float *hi, *lo;
   int stride;
+  const double *dv;
   __device__ __forceinline__ void get(double3 &o, double3 &d) const {
+    if (dv) {
+      o = make_double3(dv[0], dv[stride], dv[2 * stride]);
+      d = make_double3(dv[3 * stride], dv[4 * stride], dv[5 * stride]);
+      return;
+    }
     o = make_double3((double)hi[0] + lo[0], (double)hi[stride] + lo[stride], (double)hi[2 * stride] + lo[2 * stride]);
     d = make_double3((double)hi[3 * stride] + lo[3 * stride], (double)hi[4 * stride] + lo[4 * stride],
                      (double)hi[5 * stride] + lo[5 * stride]);
@@ -157,10 +167,11 @@ __device__ __forceinline__ int tile_ix(double x, double g0, double g1, int n) {
   return clampi((int)floor((x - g0) / (g1 - g0) * n), 0, n - 1);
 }
 
-template <bool kMixed, bool kCount>
+template <int kP, bool kCount>
 __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, RaySrc rs, double dns64, Best &best,
                                            int *err, unsigned &n_nodes, unsigned &n_tris,
                                            int root, const TileGrid *tf = nullptr, int tile = 0) {
+  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   best.t = kInf;
   best.slot = -1;
   best.id = 0x7fffffff;
@@ -173,11 +184,25 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, Ray
     if (kCount) n_tris++;
     const Tri *tp = sc.tris + slot;
     float4 v0 = __ldg(&tp->v0), v1 = __ldg(&tp->v1), v2 = __ldg(&tp->v2);
-    bool amb;
-    float t = hit_watertight(r, v0, v1, v2, amb);
+    float t;
     double t64 = 0.0;
     bool has64 = false;
-    if (kMixed && amb) {
+    bool amb = false;
+    if (kF64) {
+      // FP64: every candidate in float64 Moller-Trumbore on the float64 ray
+      double3 o, d;
+      rs.get(o, d);
+      double tt;
+      if (!hit_mt64(o, d, v0, v1, v2, tt)) return;
+      if (!(tt > (double)r.t_eps && (dns64 == 0.0 || tt * dns64 > (double)r.t_eps))) return;
+      t64 = tt;
+      has64 = true;
+      t = (float)tt;
+    } else {
+      t = hit_watertight(r, v0, v1, v2, amb);
+    }
+    if (kF64) {
+    } else if (kMixed && amb) {
       double3 o, d;
       rs.get(o, d);
       double tt;
@@ -196,7 +221,7 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, Ray
       float ux = (hx - tf->gx0) / tf->wx, uy = (hy - tf->gy0) / tf->wy;
       int ix = clampi((int)floorf(ux), 0, tf->tx - 1), iy = clampi((int)floorf(uy), 0, tf->ty - 1);
       bool near = fabsf(ux - rintf(ux)) < 1e-3f || fabsf(uy - rintf(uy)) < 1e-3f;
-      if (kMixed && near) {
+      if ((kMixed && near) || kF64) {
         double3 o, d;
         rs.get(o, d);
         double tt = has64 ? t64 : plane_t64(sc, slot, o, d);
@@ -206,7 +231,7 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, Ray
       if (ix != tile_x || iy != tile_y) return;
     }
     int id = __float_as_int(v1.w);
-    if (!kMixed) {
+    if (kP == kPF32) {
       if (t < best.t || (t == best.t && id < best.id)) { best.t = t; best.slot = slot; best.id = id; }
       return;
     }
@@ -253,8 +278,8 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, Ray
       if (kCount) n_nodes++;
       float4 lxy = __ldg(&nd->lxy), rxy = __ldg(&nd->rxy), lrz = __ldg(&nd->lrz);
       int2 ch = __ldg((const int2 *)&nd->child);
-      // in MIXED mode near ties must still be visited
-      float tmax = kMixed ? best.t + (1e-5f * fabsf(best.t) + 1e-4f) : best.t;
+      // in MIXED and FP64 mode near ties must still be visited
+      float tmax = kP != kPF32 ? best.t + (1e-5f * fabsf(best.t) + 1e-4f) : best.t;
       float tl, tr;
       bool hl = slab(r, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, tmax, tl);
       bool hr = slab(r, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, tmax, tr);
@@ -325,28 +350,32 @@ __device__ __forceinline__ void emit_segment(const TraceArgs &a, const Seg &s, b
 // normals 3..11, ray origin 12..14, ray direction 15..17; `lo` holds the low
 // parts of the float pairs (MIXED only).
 constexpr int kTraceThreads = 128;
+
 constexpr int kRowA = 0, kRowN = 3, kRowO = 12, kRowD = 15, kRows = 18;
 // per-lane event counters (rows of LineageSmem::cnt)
 enum { kCSeg, kCHit, kCEsc, kCEmit, kCHand, kCSteal, kCNodes, kCTris, kNumCounts };
-template <bool kMixed>
+template <int kP>
 struct LineageSmem {
+  double dv[kP == kPF64 ? kRows : 1][kTraceThreads];  // FP64: the chain itself; `hi` holds its float32 rounding
   float hi[kRows][kTraceThreads];
-  float lo[kMixed ? kRows : 1][kTraceThreads];
+  float lo[kP == kPMixed ? kRows : 1][kTraceThreads];
   float p[kMaxBands][kTraceThreads];  // band power W_b prod(r_b)
   float st[4][kTraceThreads];         // start plane (relative to the apex)
   unsigned cnt[kNumCounts][kTraceThreads];  // per-lane event counts of the launch
 };
 
-template <bool kMixed>
-__device__ __forceinline__ df3 ld_df3(const LineageSmem<kMixed> &sm, int row, int t) {
+template <int kP>
+__device__ __forceinline__ df3 ld_df3(const LineageSmem<kP> &sm, int row, int t) {
+  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   df3 v;
   v.x = df{sm.hi[row][t], kMixed ? sm.lo[row][t] : 0.0f};
   v.y = df{sm.hi[row + 1][t], kMixed ? sm.lo[row + 1][t] : 0.0f};
   v.z = df{sm.hi[row + 2][t], kMixed ? sm.lo[row + 2][t] : 0.0f};
   return v;
 }
-template <bool kMixed>
-__device__ __forceinline__ void st_df3(LineageSmem<kMixed> &sm, int row, int t, df3 v) {
+template <int kP>
+__device__ __forceinline__ void st_df3(LineageSmem<kP> &sm, int row, int t, df3 v) {
+  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   sm.hi[row][t] = v.x.hi;
   sm.hi[row + 1][t] = v.y.hi;
   sm.hi[row + 2][t] = v.z.hi;
@@ -356,25 +385,54 @@ __device__ __forceinline__ void st_df3(LineageSmem<kMixed> &sm, int row, int t, 
     sm.lo[row + 2][t] = v.z.lo;
   }
 }
-template <bool kMixed>
-__device__ __forceinline__ float3 ld_hi3(const LineageSmem<kMixed> &sm, int row, int t) {
+template <int kP>
+__device__ __forceinline__ float3 ld_hi3(const LineageSmem<kP> &sm, int row, int t) {
+  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   return make_float3(sm.hi[row][t], sm.hi[row + 1][t], sm.hi[row + 2][t]);
 }
-template <bool kMixed>
-__device__ __forceinline__ void st_f3(LineageSmem<kMixed> &sm, int row, int t, float3 v) {
+template <int kP>
+__device__ __forceinline__ void st_f3(LineageSmem<kP> &sm, int row, int t, float3 v) {
+  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   sm.hi[row][t] = v.x;
   sm.hi[row + 1][t] = v.y;
   sm.hi[row + 2][t] = v.z;
 }
 
+// FP64 rows: the float64 value and its float32 rounding in `hi` (read by the
+// float32 traversal and the segment records).
+template <int kP>
+__device__ __forceinline__ double3 ld_d3(const LineageSmem<kP> &sm, int row, int t) {
+  return make_double3(sm.dv[row][t], sm.dv[row + 1][t], sm.dv[row + 2][t]);
+}
+template <int kP>
+__device__ __forceinline__ void st_d3(LineageSmem<kP> &sm, int row, int t, double3 v) {
+  sm.dv[row][t] = v.x;
+  sm.dv[row + 1][t] = v.y;
+  sm.dv[row + 2][t] = v.z;
+  sm.hi[row][t] = (float)v.x;
+  sm.hi[row + 1][t] = (float)v.y;
+  sm.hi[row + 2][t] = (float)v.z;
+}
+
 // Start lineage `lin` (source si, beam bi) in this thread's column.
-template <bool kMixed>
-__device__ __forceinline__ void init_lineage(const TraceArgs &a, LineageSmem<kMixed> &sm, int t, int64_t lin) {
+template <int kP>
+__device__ __forceinline__ void init_lineage(const TraceArgs &a, LineageSmem<kP> &sm, int t, int64_t lin) {
+  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   const int nb = a.sc.n_bands;
   int64_t si = lin / a.n_beams, bi = lin - si * a.n_beams;
   float4 s4 = __ldg(&a.src[si]);
   float3 A = make_float3(s4.x, s4.y, s4.z);
-  if (kMixed) {
+  if (kF64) {
+    double3 d0, d1, d2;
+    beam_dirs<double>(a.level, bi, d0, d1, d2);
+    st_d3(sm, kRowN, t, cross_exact(d0, d1));
+    st_d3(sm, kRowN + 3, t, cross_exact(d1, d2));
+    st_d3(sm, kRowN + 6, t, cross_exact(d2, d0));
+    st_d3(sm, kRowD, t, normalize3((d0 + d1) + d2));
+    const double3 A64 = make_double3(s4.x, s4.y, s4.z);
+    st_d3(sm, kRowA, t, A64);
+    st_d3(sm, kRowO, t, A64);
+  } else if (kMixed) {
     // table: 9 normal components then the 3 axis components, hi parts
     // first, lo parts 12 floats later
     const float *bt = a.beam_table + 24 * bi;
@@ -422,8 +480,9 @@ struct TraceCounts {
   unsigned *p;  // &cnt[0][lane's column]
   __device__ unsigned &operator[](int i) const { return p[i * kTraceThreads]; }
 };
-template <bool kMixed>
-__device__ __forceinline__ TraceCounts init_counts(LineageSmem<kMixed> &sm, int t) {
+template <int kP>
+__device__ __forceinline__ TraceCounts init_counts(LineageSmem<kP> &sm, int t) {
+  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   for (int q = 0; q < kNumCounts; q++) sm.cnt[q][t] = 0u;
   return TraceCounts{&sm.cnt[0][t]};
 }
@@ -432,10 +491,11 @@ __device__ __forceinline__ TraceCounts init_counts(LineageSmem<kMixed> &sm, int 
 // < 0).  Write the segment record and, if the beam goes on, reflect it: the
 // image source (Section 2), mirrored cone and axis, energy lost at the
 // reflection.  Returns true if the lineage continues.
-template <bool kMixed>
-__device__ __forceinline__ bool finish_segment(const TraceArgs &a, LineageSmem<kMixed> &sm, int t, const Ray &r,
+template <int kP>
+__device__ __forceinline__ bool finish_segment(const TraceArgs &a, LineageSmem<kP> &sm, int t, const Ray &r,
                                                const Best &best, int slot, LaneState &ls, const MicGrid &g,
                                                const TraceCounts &cn) {
+  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   const int nb = a.sc.n_bands;
   cn[kCSeg]++;
   float4 end = make_float4(0.0f, 0.0f, 0.0f, -kInf);
@@ -449,8 +509,14 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, LineageSmem<k
     float3 pn = f3(plf);
     float3 en = dot3(pn, r.d) < 0.0f ? pn : pn * -1.0f;
     float ew;
-    if (kMixed) ew = df3_dot(mkdf3(en), df3_sub(mkdf3(f3(v0)), ld_df3(sm, kRowA, t))).hi;
-    else ew = dot3(en, f3(v0) - ld_hi3(sm, kRowA, t));
+    if (kF64) {
+      double3 end = make_double3(en.x, en.y, en.z);
+      ew = (float)dot3(end, make_double3(v0.x, v0.y, v0.z) - ld_d3(sm, kRowA, t));
+    } else if (kMixed) {
+      ew = df3_dot(mkdf3(en), df3_sub(mkdf3(f3(v0)), ld_df3(sm, kRowA, t))).hi;
+    } else {
+      ew = dot3(en, f3(v0) - ld_hi3(sm, kRowA, t));
+    }
     end = make_float4(en.x, en.y, en.z, ew);
   } else {
     cn[kCEsc]++;
@@ -467,6 +533,16 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, LineageSmem<k
     s.n2 = make_float4(n2.x, n2.y, n2.z, __int_as_float(ls.k));
     for (int q = 0; q < 9; q++) s.nlo[q] = kMixed ? sm.lo[kRowN + q][t] : 0.0f;
     s.pad[0] = s.pad[1] = s.pad[2] = 0.0f;
+    if (kF64) {
+      // float64 values as float pairs, the apex with a third word so that
+      // hi + lo + pad gives it back exactly
+      for (int q = 0; q < 3; q++) {
+        double x = sm.dv[kRowA + q][t];
+        s.alo[q] = (float)(x - (double)s.ahi[q]);
+        s.pad[q] = (float)((x - (double)s.ahi[q]) - (double)s.alo[q]);
+      }
+      for (int q = 0; q < 9; q++) s.nlo[q] = (float)(sm.dv[kRowN + q][t] - (double)sm.hi[kRowN + q][t]);
+    }
     s.start = make_float4(sm.st[0][t], sm.st[1][t], sm.st[2][t], sm.st[3][t]);
     s.end = end;
     s.p03 = make_float4(sm.p[0][t], sm.p[1][t], sm.p[2][t], sm.p[3][t]);
@@ -491,7 +567,30 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, LineageSmem<k
   // the reflected beam starts at the hit point on that plane.
   float3 pn = f3(plf), pv0 = f3(v0);
   float3 Dn;
-  if (kMixed) {
+  if (kF64) {
+    Plane64 pl = ldg_d4(&a.sc.planes64[slot]);
+    const double3 n = make_double3(pl.x, pl.y, pl.z), v0d = make_double3(v0.x, v0.y, v0.z);
+    double3 A = ld_d3(sm, kRowA, t), O = ld_d3(sm, kRowO, t), D = ld_d3(sm, kRowD, t);
+    const double th = best.has64 ? best.t64 : (pl.w - dot3(n, O)) / dot3(n, D);
+    const double3 H = O + D * th;
+    A = A - n * (2.0 * dot3(A - v0d, n));
+    st_d3(sm, kRowA, t, A);
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      double3 nj = ld_d3(sm, kRowN + 3 * j, t);
+      st_d3(sm, kRowN + 3 * j, t, nj - n * (2.0 * dot3(nj, n)));
+    }
+    D = D - n * (2.0 * dot3(D, n));
+    st_d3(sm, kRowO, t, H);
+    st_d3(sm, kRowD, t, D);
+    const double dn = dot3(n, D);
+    ls.dns64 = fabs(dn);
+    ls.dns = (float)ls.dns64;
+    Dn = make_float3((float)D.x, (float)D.y, (float)D.z);
+    const double3 sn = dn > 0.0 ? n : n * -1.0;
+    const double sw = dot3(sn, v0d - A);
+    sm.st[0][t] = (float)sn.x; sm.st[1][t] = (float)sn.y; sm.st[2][t] = (float)sn.z; sm.st[3][t] = (float)sw;
+  } else if (kMixed) {
     PlaneDF pd = a.sc.planes_df[slot];
     df3 n = df3{df{pd.hi.x, pd.lo.x}, df{pd.hi.y, pd.lo.y}, df{pd.hi.z, pd.lo.z}};
     df w = df{pd.hi.w, pd.lo.w};
@@ -578,15 +677,17 @@ __device__ __forceinline__ int64_t take_lineage(const TraceArgs &a, bool need) {
 // Six resident blocks per SM (at most 80 registers a thread): the traversal
 // is latency-bound, and on the district workload this beat both fewer blocks
 // without spills and more blocks with heavier spills.
-template <bool kMixed, bool kCount>
+template <int kP, bool kCount>
 __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
-  __shared__ LineageSmem<kMixed> sm;
+  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
+  __shared__ LineageSmem<kP> sm;
   const int t = threadIdx.x;
   const MicGrid g = *a.grid;
   const TraceCounts cn = init_counts(sm, t);
   LaneState ls = {-1, 0, -1, 0.0f, 0.0};
   bool done = false;
-  const RaySrc rs{&sm.hi[kRowO][t], kMixed ? &sm.lo[kRowO][t] : &sm.hi[kRowO][t], kTraceThreads};
+  const RaySrc rs{&sm.hi[kRowO][t], kMixed ? &sm.lo[kRowO][t] : &sm.hi[kRowO][t], kTraceThreads,
+                  kF64 ? &sm.dv[kRowO][t] : nullptr};
   while (true) {
     bool need = !done && ls.lin < 0;
     int64_t mine = take_lineage(a, need);
@@ -603,7 +704,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
     // ---- one segment of this lane's lineage
     const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), a.t_eps, ls.dns);
     Best best;
-    int slot = closest_hit<kMixed, kCount>(a.sc, r, rs, ls.dns64, best, &a.ctr->error, cn[kCNodes], cn[kCTris],
+    int slot = closest_hit<kP, kCount>(a.sc, r, rs, ls.dns64, best, &a.ctr->error, cn[kCNodes], cn[kCTris],
                                            a.sc.root);
     if (!finish_segment(a, sm, t, r, best, slot, ls, g, cn)) ls.lin = -1;
   }
@@ -652,12 +753,22 @@ __device__ __forceinline__ bool wait_slot(const TraceArgs &a, const TiledArgs &t
 // A lineage's state in a queue slot: S points at row 0, rows c words apart.
 // Queue slots are written once and read once by another SM, so both sides
 // go through L2 only.
-template <bool kMixed>
-__device__ __forceinline__ void save_state(uint32_t *S, size_t c, const LineageSmem<kMixed> &sm, int t,
+template <int kP>
+__device__ __forceinline__ void save_state(uint32_t *S, size_t c, const LineageSmem<kP> &sm, int t,
                                            const LaneState &ls) {
-  for (int q = 0; q < kRows; q++) __stcg(S + q * c, __float_as_uint(sm.hi[q][t]));
-  if (kMixed)
-    for (int q = 0; q < kRows; q++) __stcg(S + (kRows + q) * c, __float_as_uint(sm.lo[q][t]));
+  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
+  if (kF64) {
+    // rows 0..35: the float64 chain, low word then high word
+    for (int q = 0; q < kRows; q++) {
+      unsigned long long b = __double_as_longlong(sm.dv[q][t]);
+      __stcg(S + (2 * q) * c, (uint32_t)(b & 0xffffffffu));
+      __stcg(S + (2 * q + 1) * c, (uint32_t)(b >> 32));
+    }
+  } else {
+    for (int q = 0; q < kRows; q++) __stcg(S + q * c, __float_as_uint(sm.hi[q][t]));
+    if (kMixed)
+      for (int q = 0; q < kRows; q++) __stcg(S + (kRows + q) * c, __float_as_uint(sm.lo[q][t]));
+  }
   for (int b = 0; b < kMaxBands; b++) __stcg(S + (36 + b) * c, __float_as_uint(sm.p[b][t]));
   for (int q = 0; q < 4; q++) __stcg(S + (44 + q) * c, __float_as_uint(sm.st[q][t]));
   __stcg(S + 48 * c, (uint32_t)(ls.lin & 0xffffffffu));
@@ -670,12 +781,23 @@ __device__ __forceinline__ void save_state(uint32_t *S, size_t c, const LineageS
   __stcg(S + 54 * c, (uint32_t)(d >> 32));
 }
 
-template <bool kMixed>
-__device__ __forceinline__ void load_state(const uint32_t *S, size_t c, LineageSmem<kMixed> &sm, int t,
+template <int kP>
+__device__ __forceinline__ void load_state(const uint32_t *S, size_t c, LineageSmem<kP> &sm, int t,
                                            LaneState &ls) {
-  for (int q = 0; q < kRows; q++) sm.hi[q][t] = __uint_as_float(__ldcg(S + q * c));
-  if (kMixed)
-    for (int q = 0; q < kRows; q++) sm.lo[q][t] = __uint_as_float(__ldcg(S + (kRows + q) * c));
+  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
+  if (kF64) {
+    for (int q = 0; q < kRows; q++) {
+      unsigned long long b = (unsigned long long)__ldcg(S + (2 * q) * c) |
+                             ((unsigned long long)__ldcg(S + (2 * q + 1) * c) << 32);
+      double x = __longlong_as_double((long long)b);
+      sm.dv[q][t] = x;
+      sm.hi[q][t] = (float)x;
+    }
+  } else {
+    for (int q = 0; q < kRows; q++) sm.hi[q][t] = __uint_as_float(__ldcg(S + q * c));
+    if (kMixed)
+      for (int q = 0; q < kRows; q++) sm.lo[q][t] = __uint_as_float(__ldcg(S + (kRows + q) * c));
+  }
   for (int b = 0; b < kMaxBands; b++) sm.p[b][t] = __uint_as_float(__ldcg(S + (36 + b) * c));
   for (int q = 0; q < 4; q++) sm.st[q][t] = __uint_as_float(__ldcg(S + (44 + q) * c));
   ls.lin = (int64_t)__ldcg(S + 48 * c) | ((int64_t)__ldcg(S + 49 * c) << 32);
@@ -788,9 +910,10 @@ __device__ __forceinline__ int take_fresh(const TraceArgs &a, const TiledArgs &t
 // queued).  A warp with nothing to do waits at most watchdog_ns for work;
 // waits on a queue slot are bounded the same way.
 // Six resident blocks per SM, as for k_trace.
-template <bool kMixed, bool kCount>
+template <int kP, bool kCount>
 __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, const __grid_constant__ TiledArgs ta) {
-  __shared__ LineageSmem<kMixed> sm;
+  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
+  __shared__ LineageSmem<kP> sm;
   const int t = threadIdx.x;
   const unsigned lane = lane_id();
   const unsigned below = (1u << lane) - 1u;
@@ -809,7 +932,8 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, c
   bool exhausted = false;  // warp-uniform: the batch has no fresh lineages left
   const int home = (int)((blockIdx.x * (kTraceThreads / 32) + (threadIdx.x >> 5)) % (unsigned)ta.n_tiles);
   unsigned long long idle_since = 0, last_prog = 0;
-  const RaySrc rs{&sm.hi[kRowO][t], kMixed ? &sm.lo[kRowO][t] : &sm.hi[kRowO][t], kTraceThreads};
+  const RaySrc rs{&sm.hi[kRowO][t], kMixed ? &sm.lo[kRowO][t] : &sm.hi[kRowO][t], kTraceThreads,
+                  kF64 ? &sm.dv[kRowO][t] : nullptr};
   while (true) {
     // ---- refill: hand-offs first (home tile, then steals), then fresh lineages
     unsigned nm = __ballot_sync(0xffffffffu, !active);
@@ -875,7 +999,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, c
     if (active) {
       const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), a.t_eps, ls.dns);
       Best best;
-      int hit = closest_hit<kMixed, kCount>(a.sc, r, rs, ls.dns64, best, &a.ctr->error, cn[kCNodes], cn[kCTris],
+      int hit = closest_hit<kP, kCount>(a.sc, r, rs, ls.dns64, best, &a.ctr->error, cn[kCNodes], cn[kCTris],
                                             __ldg(&ta.roots[tile]), &tg, tile);
       if (hit >= 0) {
         // the hit lies in this tile; a reflected beam starts here as well
@@ -947,29 +1071,34 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, c
   flush_counts(a, cn, kCount);
 }
 
-template <bool kMixed, bool kCount>
+template <int kP, bool kCount>
 static cudaError_t launch_tiled_t(cudaStream_t st, const TraceArgs &a, const TiledArgs &ta, int n_sm) {
+  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   int per_sm = 0;
   cudaError_t e =
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tiled<kMixed, kCount>, kTraceThreads, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tiled<kP, kCount>, kTraceThreads, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int64_t blocks = (int64_t)n_sm * per_sm;
-  k_trace_tiled<kMixed, kCount><<<(int)blocks, kTraceThreads, 0, st>>>(a, ta);
+  k_trace_tiled<kP, kCount><<<(int)blocks, kTraceThreads, 0, st>>>(a, ta);
   return cudaGetLastError();
 }
 
 cudaError_t launch_trace_tiled(cudaStream_t st, const TraceArgs &a, const TiledArgs &ta, int n_sm) {
   cudaError_t e;
-  if (a.mixed) e = a.count_work ? launch_tiled_t<true, true>(st, a, ta, n_sm) : launch_tiled_t<true, false>(st, a, ta, n_sm);
-  else e = a.count_work ? launch_tiled_t<false, true>(st, a, ta, n_sm) : launch_tiled_t<false, false>(st, a, ta, n_sm);
+  if (a.prec == kPMixed)
+    e = a.count_work ? launch_tiled_t<kPMixed, true>(st, a, ta, n_sm) : launch_tiled_t<kPMixed, false>(st, a, ta, n_sm);
+  else if (a.prec == kPF64)
+    e = a.count_work ? launch_tiled_t<kPF64, true>(st, a, ta, n_sm) : launch_tiled_t<kPF64, false>(st, a, ta, n_sm);
+  else
+    e = a.count_work ? launch_tiled_t<kPF32, true>(st, a, ta, n_sm) : launch_tiled_t<kPF32, false>(st, a, ta, n_sm);
   note_launches(1);
   return e;
 }
 
 int tiled_resident_lanes(int n_sm) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tiled<true, false>, kTraceThreads, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tiled<kPMixed, false>, kTraceThreads, 0) !=
       cudaSuccess)
     per_sm = 8;
   if (per_sm < 1) per_sm = 1;
@@ -998,7 +1127,8 @@ __global__ void __launch_bounds__(128) k_cast(DevScene sc, const float *o, const
   Ray r = make_ray(O, df3_hi(D), t_eps, (float)dns);
   Best best;
   unsigned a = 0, b = 0;
-  int slot = closest_hit<true, false>(sc, r, RaySrc{&rh[0][t], &rl[0][t], 128}, dns, best, err, a, b, sc.root);
+  int slot = closest_hit<kPMixed, false>(sc, r, RaySrc{&rh[0][t], &rl[0][t], 128, nullptr}, dns, best, err, a, b,
+                                         sc.root);
   t_out[i] = slot >= 0 ? (best.has64 ? (float)best.t64 : best.t) : kInf;
   tri_out[i] = slot >= 0 ? best.id : -1;
 }
@@ -1013,17 +1143,18 @@ cudaError_t launch_cast(cudaStream_t st, const DevScene &sc, const float *o, con
 
 // One persistent grid: enough blocks to fill every SM at the kernel's
 // occupancy, each block looping until the batch's lineages are taken.
-template <bool kMixed, bool kCount>
+template <int kP, bool kCount>
 static cudaError_t launch_trace_t(cudaStream_t st, const TraceArgs &a, int n_sm) {
+  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<kMixed, kCount>, kTraceThreads, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<kP, kCount>, kTraceThreads, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int64_t n = a.lineage_end - a.lineage_begin;
   int64_t blocks = (int64_t)n_sm * per_sm;
   int64_t need = (n + kTraceThreads - 1) / kTraceThreads;
   if (blocks > need) blocks = need;
-  k_trace<kMixed, kCount><<<(int)blocks, kTraceThreads, 0, st>>>(a);
+  k_trace<kP, kCount><<<(int)blocks, kTraceThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1031,8 +1162,12 @@ cudaError_t launch_trace(cudaStream_t st, const TraceArgs &a, int n_sm) {
   int64_t n = a.lineage_end - a.lineage_begin;
   if (n <= 0) return cudaSuccess;
   cudaError_t e;
-  if (a.mixed) e = a.count_work ? launch_trace_t<true, true>(st, a, n_sm) : launch_trace_t<true, false>(st, a, n_sm);
-  else e = a.count_work ? launch_trace_t<false, true>(st, a, n_sm) : launch_trace_t<false, false>(st, a, n_sm);
+  if (a.prec == kPMixed)
+    e = a.count_work ? launch_trace_t<kPMixed, true>(st, a, n_sm) : launch_trace_t<kPMixed, false>(st, a, n_sm);
+  else if (a.prec == kPF64)
+    e = a.count_work ? launch_trace_t<kPF64, true>(st, a, n_sm) : launch_trace_t<kPF64, false>(st, a, n_sm);
+  else
+    e = a.count_work ? launch_trace_t<kPF32, true>(st, a, n_sm) : launch_trace_t<kPF32, false>(st, a, n_sm);
   note_launches(1);
   return e;
 }
@@ -1043,7 +1178,7 @@ cudaError_t launch_trace(cudaStream_t st, const TraceArgs &a, int n_sm) {
 constexpr int kScatterWarps = 4;
 enum : int {
   F_AX = 0, F_RX = 3, F_N0 = 6, F_NLO = 15, F_NS = 24, F_NE = 28, F_P = 32, F_SLOTS = 40,
-  F_CY0 = 42, F_PN = 43, F_PX = 44, F_PY = F_PX + kPolyMax, F_COUNT = F_PY + kPolyMax
+  F_CY0 = 42, F_PN = 43, F_PX = 44, F_PY = F_PX + kPolyMax, F_AP = F_PY + kPolyMax, F_COUNT = F_AP + 3
 };
 struct ScatterSmem {
   float f[kScatterWarps][F_COUNT][32];
@@ -1085,11 +1220,20 @@ __device__ __forceinline__ float plane_side_df(const ScatterArgs &a, int slot, f
   return sg * (e.hi + e.lo);
 }
 
+// Signed distance of m from the float64 plane of leaf slot `slot`, oriented
+// like the float32 normal `nf` of the segment record (FP64 mode).
+__device__ __forceinline__ double plane_side64(const ScatterArgs &a, int slot, float3 nf, float4 m) {
+  Plane64 pl = ldg_d4(&a.planes64[slot]);
+  double e = pl.x * (double)m.x + pl.y * (double)m.y + pl.z * (double)m.z - pl.w;
+  return pl.x * nf.x + pl.y * nf.y + pl.z * nf.z < 0.0 ? -e : e;
+}
+
 // One warp takes 32 segments at a time.  Each lane loads one segment and
 // builds its footprint; the warp then walks the (segment, cell row) pairs of
 // all 32 footprints 32 at a time, turns each into its run of microphones, and
 // walks the runs 32 candidates at a time, so every lane has work whatever
 // the footprint sizes.
+template <bool kF64>
 __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
   __shared__ ScatterSmem sm;
   const MicGrid g = *a.grid;
@@ -1125,6 +1269,7 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
       for (int q = 0; q < 3; q++) {
         F[F_AX + q][lane] = sl.ahi[q];
         F[F_RX + q][lane] = sl.alo[q];
+        F[F_AP + q][lane] = sl.pad[q];
       }
       F[F_N0][lane] = sl.n0.x; F[F_N0 + 1][lane] = sl.n0.y; F[F_N0 + 2][lane] = sl.n0.z;
       F[F_N0 + 3][lane] = sl.n1.x; F[F_N0 + 4][lane] = sl.n1.y; F[F_N0 + 5][lane] = sl.n1.z;
@@ -1197,6 +1342,49 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
         if (c < total_c) {
           int mi = ofirst + (c - oexcl);
           float4 m = __ldg(&a.mics[mi]);
+          if (kF64) {
+            // FP64: every test and the contribution in float64 (apex exact
+            // from its three words, cone normals from their float pairs,
+            // start/end planes from the triangles' float64 planes)
+            n_cand++;
+            const double3 A = make_double3(((double)F[F_AX][s] + F[F_RX][s]) + F[F_AP][s],
+                                           ((double)F[F_AX + 1][s] + F[F_RX + 1][s]) + F[F_AP + 1][s],
+                                           ((double)F[F_AX + 2][s] + F[F_RX + 2][s]) + F[F_AP + 2][s]);
+            const double3 vd = make_double3((double)m.x - A.x, (double)m.y - A.y, (double)m.z - A.z);
+            bool in = true;
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+              double3 nd = make_double3((double)F[F_N0 + 3 * j][s] + F[F_NLO + 3 * j][s],
+                                        (double)F[F_N0 + 3 * j + 1][s] + F[F_NLO + 3 * j + 1][s],
+                                        (double)F[F_N0 + 3 * j + 2][s] + F[F_NLO + 3 * j + 2][s]);
+              in = in && dot3(nd, vd) >= 0.0;
+            }
+            if (in) {
+              int s_slot = __float_as_int(F[F_SLOTS][s]), e_slot = __float_as_int(F[F_SLOTS + 1][s]);
+              float3 ns = make_float3(F[F_NS][s], F[F_NS + 1][s], F[F_NS + 2][s]);
+              float3 ne = make_float3(F[F_NE][s], F[F_NE + 1][s], F[F_NE + 2][s]);
+              double fs = s_slot >= 0 ? plane_side64(a, s_slot, ns, m) : 1.0;
+              double fe = e_slot >= 0 ? plane_side64(a, e_slot, ne, m) : 1.0;
+              in = fs > 0.0 && fe >= 0.0;
+            }
+            const double d2 = dot3(vd, vd);
+            if (in && d2 > 1e-18) {
+              const double gf = 1.0 / (4.0 * 3.141592653589793 * d2);
+              const double dist = a.has_alpha ? sqrt(d2) : 0.0;
+              double *e = a.energy + (size_t)mi * kMaxBands;
+#pragma unroll
+              for (int b = 0; b < kMaxBands; b++) {
+                if (b < nb) {
+                  double cval = (double)F[F_P + b][s] * gf;
+                  if (a.has_alpha) cval *= exp2((double)a.alpha_log2[b] * dist);
+                  atomicAdd(e + b, cval);
+                }
+              }
+              atomicAdd(a.count + mi, 1);
+              n_contrib++;
+            }
+            continue;
+          }
           // m - apex with the apex as hi + lo: one extra rounding at most
           float3 v = make_float3((m.x - F[F_AX][s]) - F[F_RX][s], (m.y - F[F_AX + 1][s]) - F[F_RX + 1][s],
                                  (m.z - F[F_AX + 2][s]) - F[F_RX + 2][s]);
@@ -1261,14 +1449,20 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
   }
 }
 
-cudaError_t launch_scatter(cudaStream_t st, const ScatterArgs &a, int n_sm) {
+template <bool kF64>
+static cudaError_t launch_scatter_t(cudaStream_t st, const ScatterArgs &a, int n_sm) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter, 32 * kScatterWarps, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<kF64>, 32 * kScatterWarps, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  k_scatter<<<n_sm * per_sm, 32 * kScatterWarps, 0, st>>>(a);
-  note_launches(1);
+  k_scatter<kF64><<<n_sm * per_sm, 32 * kScatterWarps, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(cudaStream_t st, const ScatterArgs &a, int n_sm) {
+  cudaError_t e = a.fp64 ? launch_scatter_t<true>(st, a, n_sm) : launch_scatter_t<false>(st, a, n_sm);
+  note_launches(1);
+  return e;
 }
 
 // ------------------------------------------------------------------ levels
