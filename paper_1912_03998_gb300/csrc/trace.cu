@@ -700,12 +700,17 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
       }
     }
     if (__all_sync(0xffffffffu, done)) break;
+    const unsigned act_mask = __ballot_sync(0xffffffffu, !done);
     if (done) continue;
     // ---- one segment of this lane's lineage
     const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), a.t_eps, ls.dns);
     Best best;
     int slot = closest_hit<kP, kCount>(a.sc, r, rs, ls.dns64, best, &a.ctr->error, cn[kCNodes], cn[kCTris],
                                            a.sc.root);
+    // the lanes leave the traversal loop at different times; reconverge them
+    // so that the segment's bookkeeping and reflection run once per warp
+    // rather than once per lane
+    __syncwarp(act_mask);
     if (!finish_segment(a, sm, t, r, best, slot, ls, g, cn)) ls.lin = -1;
   }
   flush_counts(a, cn, kCount);
@@ -996,11 +1001,13 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, c
     // ---- search the current tile for this lane's ray
     int next = -1;
     bool ended = false;
+    const unsigned act_mask = __ballot_sync(0xffffffffu, active);
     if (active) {
       const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), a.t_eps, ls.dns);
       Best best;
       int hit = closest_hit<kP, kCount>(a.sc, r, rs, ls.dns64, best, &a.ctr->error, cn[kCNodes], cn[kCTris],
                                             __ldg(&ta.roots[tile]), &tg, tile);
+      __syncwarp(act_mask);  // reconverge after the traversal loop (see k_trace)
       if (hit >= 0) {
         // the hit lies in this tile; a reflected beam starts here as well
         if (!finish_segment(a, sm, t, r, best, hit, ls, g, cn)) ended = true;
