@@ -45,7 +45,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="district", choices=["district", "tiny"])
+    ap.add_argument("--workload", default="district", choices=["district", "tiny", "batch"],
+                    help="batch: 64 cities of uneven size traced as one batch (CUDA graph)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="batch: tune blocks per SM and lineages per launch on 16 of the cities first")
     ap.add_argument("--sources", type=int, default=None, help="override the source count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -270,6 +273,79 @@ def run_ours(args, rank, world):
     return res
 
 
+# ------------------------------------------------------------------ batches
+def run_batch(args):
+    """64 cities of uneven size: one batch run (persistent launches replayed
+    from a CUDA graph) against the same cities traced one at a time."""
+    import torch
+    from paper_1912_03998_gb300 import autotune, btrace, synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ws = synth.batch_cities(seed=4, n=64)
+    stream = torch.cuda.Stream(dev)
+    tr = btrace.Tracer(0, stream.cuda_stream)
+    prec = {"mixed": btrace.BT_PREC_MIXED, "fp32": btrace.BT_PREC_FP32, "fp64": btrace.BT_PREC_FP64}[args.precision]
+    sids = [tr.load(w) for w in ws]
+    params = [tr.params(w.max_order, precision=prec) for w in ws]
+    tuned = None
+    if args.autotune:
+        knobs, table = autotune.tune_batch(tr, sids[:16], params[:16])
+        for p in params:
+            p.blocks_per_sm, p.chunk_beams = knobs["blocks_per_sm"], knobs["chunk_beams"]
+        tuned = {"chosen": knobs, "trials_ms": [[k["blocks_per_sm"], k["chunk_beams"], round(ms, 3)]
+                                                for k, ms in table]}
+    l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def span(fn):
+        with torch.cuda.stream(stream):
+            flush_l2(l2_flush)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b)
+
+    b = btrace.bt_batch_create(tr.ctx, sids, params)
+    for _ in range(args.warmup):
+        btrace.bt_batch_run(tr.ctx, b)
+    n0 = btrace.bt_kernel_launches()
+    with Clocks(0) as clk:
+        ms = [span(lambda: btrace.bt_batch_run(tr.ctx, b)) for _ in range(args.steps)]
+    launches = btrace.bt_kernel_launches() - n0
+    st = btrace.bt_batch_stats(b)
+    segs = st["segments"]
+
+    def one_at_a_time():
+        for sid, p in zip(sids, params):
+            btrace.bt_trace(tr.ctx, sid, p)
+
+    one_at_a_time()
+    ms1 = [span(one_at_a_time) for _ in range(max(1, min(args.steps, 2)))]
+    btrace.bt_batch_destroy(b)
+    tr.close()
+    value = segs / (np.mean(ms) * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": "batch: 64 cities of 100-5,000 buildings, 1-1,000 sources, L 3-6, "
+                                   "K 2-8, 1k-250k microphones (seeded), traced as one batch",
+                       "cities": len(ws), "triangles": int(sum(w.scene.n_tris for w in ws)),
+                       "sources": int(sum(len(w.src) for w in ws)),
+                       "lineages": int(sum(len(w.src) * 20 * 4 ** w.level for w in ws)),
+                       "microphones": int(sum(len(w.mics) for w in ws)), "precision": args.precision,
+                       "l2": "flushed before every step (256 MB write, outside the events)",
+                       "parallelism": "1 GPU"},
+            "clocks": clk.summary(), "gpu_launches": launches,
+            "segments_per_step": segs,
+            "one_at_a_time": {"value": segs / (np.mean(ms1) * 1e-3), "ms_per_step": float(np.mean(ms1))},
+            "speedup_vs_one_at_a_time": float(np.mean(ms1) / np.mean(ms))}
+    if tuned:
+        line["autotune"] = tuned
+    print(json.dumps(line))
+
+
 # ------------------------------------------------------------------ oracle
 def oracle_sample(w, seconds, threads, rng_seed=5):
     """Time the oracle on a seeded subset of sources sized to ~`seconds`."""
@@ -340,6 +416,10 @@ def main():
         return
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "batch":
+        if rank == 0:
+            run_batch(args)
+        return
     if world > 1:
         import torch
         import torch.distributed as dist

@@ -84,6 +84,8 @@ typedef struct {
   int32_t chunk_beams;                      /* beam lineages per launch batch; 0 = automatic */
   int32_t count_work;                       /* 1: also count BVH nodes visited and triangles
                                                tested (slower; for roofline accounting) */
+  int32_t blocks_per_sm;                    /* resident blocks per SM of the persistent trace
+                                               kernels; 0 = as many as fit (tuning knob) */
   int32_t queue_depth;                      /* hand-off queue slots per sub-domain, a power of
                                                two in 32..2^22, or 0 = automatic (at least
                                                twice the lanes of one launch); also the most
@@ -228,6 +230,31 @@ int bt_trace_noalloc(bt_ctx *ctx, int32_t scene_id, const bt_trace_params *p, do
  * The scene's microphones must be set (BT_E_STATE otherwise).  Stats of the
  * scene are zeroed. */
 int bt_set_result(bt_ctx *ctx, int32_t scene_id, const double *intensity, const int32_t *path_count);
+
+/* Batches (the paper has none: it traces one city at a time).  Several
+ * loaded scenes -- cities of uneven size, each with its own sources,
+ * microphones and parameters -- traced together: every run issues one
+ * persistent trace launch and one scatter launch per group of lineages drawn
+ * from all scenes, the whole sequence captured once as a CUDA graph and
+ * replayed by every later run.  Each scene's result is then read with
+ * bt_read_levels as after bt_trace.
+ *   scene_ids  [n_scenes] distinct loaded scenes with sources and microphones
+ *   params     [n_scenes] per-scene parameters; tiles must be 1x1, and
+ *              precision, count_work, blocks_per_sm and chunk_beams must agree
+ * The batch reads the scenes' device buffers in place: after bt_load_scene,
+ * bt_set_sources, bt_set_microphones or bt_unload_scene on any of its scenes,
+ * bt_batch_run fails with BT_E_STATE (create a new batch).  bt_batch_run
+ * synchronises the context's stream; the context's stream must not be in
+ * stream capture.  Batches are freed by bt_batch_destroy or with the
+ * context. */
+typedef struct bt_batch bt_batch;
+int bt_batch_create(bt_ctx *ctx, const int32_t *scene_ids, int32_t n_scenes, const bt_trace_params *params,
+                    bt_batch **batch_out);
+int bt_batch_run(bt_batch *batch);
+/* Totals of the last run (per-scene stats hold only `beams`); trace_ms is
+ * the device time of the whole run. */
+int bt_batch_stats(const bt_batch *batch, bt_stats *stats);
+int bt_batch_destroy(bt_batch *batch);
 
 /* Message of the last error of the context ("" if none).  Valid until the
  * next call on the context. */

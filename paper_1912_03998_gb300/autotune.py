@@ -1,0 +1,73 @@
+"""Autotuner for the trace's launch knobs, by measurement.
+
+Knobs searched:
+  blocks_per_sm  resident 128-thread blocks per SM of the persistent trace
+                 kernels (more warps hide more latency; fewer leave more
+                 registers and L1 to each), 0 = as many as fit
+  chunk_beams    lineages per persistent launch (fewer, larger launches have
+                 fewer tails; smaller ones keep the segment buffer small)
+  queue_depth    hand-off queue slots per sub-domain (split traces only)
+
+The tracer itself fixes one lineage per lane (32 beams per warp) and one
+triangle per BVH leaf (the LBVH's leaves), so those are not searched.  Every
+candidate runs the real workload (or a caller-chosen part of it) through the
+C ABI and is timed on the device (bt_stats.trace_ms); the fastest wins.
+"""
+from __future__ import annotations
+
+import itertools
+
+from . import btrace
+
+
+def _chunk_candidates(max_order: int):
+    per = max_order + 1
+    return [0, (1 << 21) // per, (1 << 22) // per, (1 << 24) // per]
+
+
+def tune_batch(tracer, scene_ids, params, blocks=(0, 4, 5), chunks=None, repeats=2):
+    """Tune blocks_per_sm and chunk_beams for a batch of loaded scenes with
+    per-scene `params` (bt_trace_params).  Returns (best knobs dict, list of
+    (knobs, ms) for every candidate)."""
+    kmax = max(p.max_order for p in params)
+    chunks = chunks if chunks is not None else _chunk_candidates(kmax)
+    results = []
+    for bps, chunk in itertools.product(blocks, chunks):
+        ps = []
+        for p in params:
+            q = btrace.bt_trace_params.from_buffer_copy(p)
+            q.blocks_per_sm = bps
+            q.chunk_beams = chunk
+            ps.append(q)
+        b = btrace.bt_batch_create(tracer.ctx, scene_ids, ps)
+        try:
+            btrace.bt_batch_run(tracer.ctx, b)  # captures the graph
+            best = None
+            for _ in range(repeats):
+                btrace.bt_batch_run(tracer.ctx, b)
+                ms = btrace.bt_batch_stats(b)["trace_ms"]
+                best = ms if best is None else min(best, ms)
+        finally:
+            btrace.bt_batch_destroy(b)
+        results.append((dict(blocks_per_sm=bps, chunk_beams=chunk), best))
+    results.sort(key=lambda r: r[1])
+    return results[0][0], results
+
+
+def tune_trace(tracer, scene_id, params, blocks=(0, 4, 5), depths=(0, 1 << 16, 1 << 18), repeats=2):
+    """Tune blocks_per_sm and, for a split trace, queue_depth for one scene.
+    Returns (best knobs dict, list of (knobs, ms))."""
+    split = params.tiles_x * params.tiles_y > 1
+    results = []
+    for bps, depth in itertools.product(blocks, depths if split else (0,)):
+        q = btrace.bt_trace_params.from_buffer_copy(params)
+        q.blocks_per_sm = bps
+        q.queue_depth = depth
+        best = None
+        for _ in range(repeats + 1):
+            btrace.bt_trace(tracer.ctx, scene_id, q)
+            ms = btrace.bt_read_levels(tracer.ctx, scene_id)["trace_ms"]
+            best = ms if best is None else min(best, ms)
+        results.append((dict(blocks_per_sm=bps, queue_depth=depth), best))
+    results.sort(key=lambda r: r[1])
+    return results[0][0], results

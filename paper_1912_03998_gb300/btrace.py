@@ -31,7 +31,7 @@ class bt_trace_params(C.Structure):
                 ("energy_threshold_w", C.c_float), ("t_eps_m", C.c_float),
                 ("tiles_x", C.c_int32), ("tiles_y", C.c_int32), ("precision", C.c_int32),
                 ("watchdog_ms", C.c_int32), ("chunk_beams", C.c_int32), ("count_work", C.c_int32),
-                ("queue_depth", C.c_int32)]
+                ("blocks_per_sm", C.c_int32), ("queue_depth", C.c_int32)]
 
 
 class bt_stats(C.Structure):
@@ -57,7 +57,8 @@ _lib = None
 EXPECTED_SYMBOLS = ("bt_params_default", "bt_create", "bt_destroy", "bt_load_scene",
                     "bt_unload_scene", "bt_set_sources", "bt_set_microphones", "bt_trace",
                     "bt_read_levels", "bt_last_error", "bt_kernel_launches", "bt_cast_rays",
-                    "bt_trace_noalloc", "bt_set_result")
+                    "bt_trace_noalloc", "bt_set_result", "bt_batch_create", "bt_batch_run",
+                    "bt_batch_stats", "bt_batch_destroy")
 
 
 def lib_path() -> str:
@@ -88,6 +89,10 @@ def lib():
             L.bt_cast_rays.argtypes = [p, i32, p, p, p, i64, C.c_float, p, p]
             L.bt_trace_noalloc.argtypes = [p, i32, C.POINTER(bt_trace_params), p, p]
             L.bt_set_result.argtypes = [p, i32, p, p]
+            L.bt_batch_create.argtypes = [p, p, i32, C.POINTER(bt_trace_params), C.POINTER(C.c_void_p)]
+            L.bt_batch_run.argtypes = [p]
+            L.bt_batch_stats.argtypes = [p, C.POINTER(bt_stats)]
+            L.bt_batch_destroy.argtypes = [p]
             L.bt_kernel_launches.argtypes = []
             L.bt_kernel_launches.restype = C.c_int64
             for name in EXPECTED_SYMBOLS:
@@ -212,6 +217,31 @@ def bt_set_result(ctx, scene_id: int, intensity, path_count=None):
     pi, _, ki = _arr(intensity, np.float64)
     pc, _, kc = _arr(path_count, np.int32)
     _check(lib().bt_set_result(ctx, int(scene_id), pi, pc), ctx)
+
+
+def bt_batch_create(ctx, scene_ids, params):
+    """Batch of loaded scenes with one bt_trace_params each."""
+    ids = np.ascontiguousarray(scene_ids, np.int32)
+    arr = (bt_trace_params * len(ids))(*params)
+    h = C.c_void_p()
+    _check(lib().bt_batch_create(ctx, ids.ctypes.data_as(C.c_void_p), len(ids), arr, C.byref(h)), ctx)
+    return h
+
+
+def bt_batch_run(ctx, batch):
+    _check(lib().bt_batch_run(batch), ctx)
+
+
+def bt_batch_stats(batch) -> dict:
+    st = bt_stats()
+    rc = lib().bt_batch_stats(batch, C.byref(st))
+    if rc != BT_OK:
+        raise BtError(rc, "bt_batch_stats failed")
+    return st.as_dict()
+
+
+def bt_batch_destroy(batch):
+    lib().bt_batch_destroy(batch)
 
 
 def bt_cast_rays(ctx, scene_id: int, origins, dirs, start_normals=None, t_eps_m: float = 1e-3):

@@ -54,10 +54,13 @@ struct SceneState {
   // result
   bool traced = false;
   bt_stats stats;
+  unsigned long long gen = 0;  // changes whenever the scene's buffers may change (batches check it)
   DevBuf out_level, out_int, out_cnt;
 };
 
 }  // namespace
+
+struct bt_batch;
 
 struct bt_ctx {
   int device = 0;
@@ -78,6 +81,8 @@ struct bt_ctx {
   std::vector<cudaEvent_t> kev;  // pairs of events around kernel launches of one trace
   std::vector<DevBuf> pool;      // released device buffers, reused before any new cudaMalloc
   DevBuf t_ring, t_seq, t_qctl;  // sub-domain trace: queue slots, slot sequence words, queue counters
+  unsigned long long gen_counter = 0;
+  std::vector<bt_batch *> batches;  // live batches, freed with the context
 };
 
 namespace {
@@ -338,10 +343,14 @@ BT_API int bt_create(bt_ctx **out, int device, void *cuda_stream) {
   return BT_OK;
 }
 
+static void free_batch(bt_batch *b);
+
 BT_API int bt_destroy(bt_ctx *c) {
   if (!c) return BT_OK;
   DeviceGuard g(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  for (bt_batch *b : c->batches) free_batch(b);
+  c->batches.clear();
   for (auto &s : c->sc) release_scene(c, s);
   for (DevBuf &q : c->pool) release(q);
   c->pool.clear();
@@ -415,6 +424,7 @@ BT_API int bt_load_scene(bt_ctx *c, const float *verts, int64_t n_verts, const i
   } while (0);
   if (rc != BT_OK) { release_scene(c, s); return rc; }
   s.used = true;
+  s.gen = ++c->gen_counter;
   cudaStream_t st = c->stream;
   float *box = c->d_box;
 #define CKS(call)                      \
@@ -466,6 +476,7 @@ BT_API int bt_unload_scene(bt_ctx *c, int32_t scene_id) {
   DeviceGuard g(c->device);
   cudaStreamSynchronize(c->stream);
   release_scene(c, *s);
+  s->gen = ++c->gen_counter;
   return BT_OK;
 }
 
@@ -504,6 +515,7 @@ BT_API int bt_set_sources(bt_ctx *c, int32_t scene_id, const float *pos, const f
   s->level = icosa_level;
   s->has_src = true;
   s->traced = false;
+  s->gen = ++c->gen_counter;
   return BT_OK;
 }
 
@@ -540,16 +552,39 @@ BT_API int bt_set_microphones(bt_ctx *c, int32_t scene_id, const float *pos, int
   s->side = side;
   s->has_mics = true;
   s->traced = false;
+  s->gen = ++c->gen_counter;
   return BT_OK;
 }
 
-BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
-  TRY(check_ctx(c));
-  c->err[0] = 0;
-  SceneState *s;
-  TRY(scene_ref(c, scene_id, &s));
+// The kernels' view of scene s traced with parameters p (alpha_log2 and
+// has_alpha already derived from p; the beam table is set by the caller).
+static void fill_view(bt::SceneView &v, SceneState &s, const bt_trace_params *p, const float *alpha_log2,
+                      int has_alpha) {
+  memset(&v, 0, sizeof(v));
+  v.sc = dev_scene(s);
+  v.src = (const float4 *)s.src.p;
+  v.power = (const float *)s.power.p;
+  v.n_src = s.n_src;
+  v.level = s.level;
+  v.max_order = p->max_order;
+  v.n_beams = (int64_t)20 << (2 * s.level);
+  v.lineage_base = 0;
+  v.t_eps = p->t_eps_m;
+  v.energy_threshold = p->energy_threshold_w;
+  for (int b = 0; b < BT_MAX_BANDS; b++) v.alpha_log2[b] = alpha_log2[b];
+  v.has_alpha = has_alpha;
+  v.grid = (const bt::MicGrid *)s.grid.p;
+  v.beam_table = nullptr;
+  v.mics = (const float4 *)s.mics.p;
+  v.cell_start = (const int *)s.cell_start.p;
+  v.energy = (double *)s.energy.p;
+  v.count = (int *)s.count.p;
+}
+
+// Check the trace parameters p for scene s; derive the air damping exponents.
+static int check_params(bt_ctx *c, SceneState *s, const bt_trace_params *p, float *alpha_log2, int *has_alpha) {
   if (!p) return fail(c, BT_E_INVALID, "NULL params");
-  if (!s->has_src || !s->has_mics) return fail(c, BT_E_STATE, "sources and microphones must be set before bt_trace");
+  if (!s->has_src || !s->has_mics) return fail(c, BT_E_STATE, "sources and microphones must be set before tracing");
   if (p->max_order < 0 || p->max_order > 32) return fail(c, BT_E_INVALID, "max_order %d not in 0..32", p->max_order);
   if (!(p->t_eps_m > 0.0f) || !isfinite(p->t_eps_m)) return fail(c, BT_E_INVALID, "t_eps_m must be > 0");
   if (!(p->energy_threshold_w >= 0.0f)) return fail(c, BT_E_INVALID, "energy_threshold_w must be >= 0");
@@ -558,17 +593,28 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   if (p->tiles_x < 1 || p->tiles_y < 1 || p->tiles_x > BT_MAX_TILES || p->tiles_y > BT_MAX_TILES)
     return fail(c, BT_E_INVALID, "tiles %dx%d not in 1..%d per axis", p->tiles_x, p->tiles_y, BT_MAX_TILES);
   if (p->chunk_beams < 0) return fail(c, BT_E_INVALID, "chunk_beams must be >= 0");
+  if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32) return fail(c, BT_E_INVALID, "blocks_per_sm must be in 0..32");
   if (p->queue_depth != 0 && (p->queue_depth < 32 || p->queue_depth > (1 << 22) ||
                               (p->queue_depth & (p->queue_depth - 1)) != 0))
     return fail(c, BT_E_INVALID, "queue_depth must be 0 or a power of two in 32..2^22");
-  int has_alpha = 0;
-  float alpha_log2[BT_MAX_BANDS];
+  *has_alpha = 0;
   for (int b = 0; b < BT_MAX_BANDS; b++) {
     float a = p->air_atten_db_per_m[b];
     if (!(a >= 0.0f) || !isfinite(a)) return fail(c, BT_E_INVALID, "air attenuation must be finite and >= 0");
     alpha_log2[b] = -a * 3.32192809488736f / 10.0f;  // 10^(-a d/10) = 2^(-a d log2(10)/10)
-    if (b < s->n_bands && a != 0.0f) has_alpha = 1;
+    if (b < s->n_bands && a != 0.0f) *has_alpha = 1;
   }
+  return BT_OK;
+}
+
+BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  SceneState *s;
+  TRY(scene_ref(c, scene_id, &s));
+  int has_alpha = 0;
+  float alpha_log2[BT_MAX_BANDS];
+  TRY(check_params(c, s, p, alpha_log2, &has_alpha));
   DeviceGuard g(c->device);
   cudaStream_t st = c->stream;
   const int64_t n_beams = (int64_t)20 << (2 * s->level);
@@ -608,27 +654,16 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   CK(cudaMemsetAsync(s->count.p, 0, sizeof(int) * (size_t)s->n_mics, st));
   bt::TraceArgs ta;
   memset(&ta, 0, sizeof(ta));
-  ta.sc = dev_scene(*s);
+  fill_view(ta.v, *s, p, alpha_log2, has_alpha);
   if (tiled) {
-    ta.sc.n_tris = s->n_pairs;
-    ta.sc.nodes = (const bt::Node *)s->t_nodes.p;
-    ta.sc.tris = (const bt::Tri *)s->t_tris.p;
-    ta.sc.planes = (const bt::Plane *)s->t_planes.p;
-    ta.sc.planes64 = (const bt::Plane64 *)s->t_planes64.p;
-    ta.sc.planes_df = (const bt::PlaneDF *)s->t_planes_df.p;
-    ta.sc.root = 0;
+    ta.v.sc.n_tris = s->n_pairs;
+    ta.v.sc.nodes = (const bt::Node *)s->t_nodes.p;
+    ta.v.sc.tris = (const bt::Tri *)s->t_tris.p;
+    ta.v.sc.planes = (const bt::Plane *)s->t_planes.p;
+    ta.v.sc.planes64 = (const bt::Plane64 *)s->t_planes64.p;
+    ta.v.sc.planes_df = (const bt::PlaneDF *)s->t_planes_df.p;
+    ta.v.sc.root = 0;
   }
-  ta.src = (const float4 *)s->src.p;
-  ta.power = (const float *)s->power.p;
-  ta.n_src = s->n_src;
-  ta.level = s->level;
-  ta.n_beams = n_beams;
-  ta.max_order = p->max_order;
-  ta.t_eps = p->t_eps_m;
-  ta.energy_threshold = p->energy_threshold_w;
-  for (int b = 0; b < BT_MAX_BANDS; b++) ta.alpha_log2[b] = alpha_log2[b];
-  ta.has_alpha = has_alpha;
-  ta.grid = (const bt::MicGrid *)s->grid.p;
   ta.segs = (bt::Seg *)c->segs.p;
   ta.seg_count = c->d_seg_count;
   ta.seg_capacity = cap;
@@ -636,31 +671,22 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   ta.ctr = c->d_ctr;
   ta.count_work = p->count_work ? 1 : 0;
   ta.prec = p->precision;
+  ta.blocks_per_sm = p->blocks_per_sm;
   if (ta.prec == BT_PREC_MIXED && total > 0) {
     if (c->beam_table_level != s->level) {
       TRY(ensure(c, c->beam_table, sizeof(float) * 24 * (size_t)n_beams));
       CK(bt::launch_beam_table(st, s->level, (float *)c->beam_table.p));
       c->beam_table_level = s->level;
     }
-    ta.beam_table = (const float *)c->beam_table.p;
+    ta.v.beam_table = (const float *)c->beam_table.p;
   }
   bt::ScatterArgs sa;
   memset(&sa, 0, sizeof(sa));
-  sa.tris = ta.sc.tris;
-  sa.planes_df = ta.sc.planes_df;
-  sa.planes64 = ta.sc.planes64;
+  sa.v = ta.v;
   sa.fp64 = p->precision == BT_PREC_FP64 ? 1 : 0;
   sa.segs = ta.segs;
   sa.seg_count = c->d_seg_count;
   sa.seg_capacity = cap;
-  sa.grid = ta.grid;
-  sa.mics = (const float4 *)s->mics.p;
-  sa.cell_start = (const int *)s->cell_start.p;
-  sa.energy = (double *)s->energy.p;
-  sa.count = (int *)s->count.p;
-  sa.n_bands = s->n_bands;
-  for (int b = 0; b < BT_MAX_BANDS; b++) sa.alpha_log2[b] = alpha_log2[b];
-  sa.has_alpha = has_alpha;
   sa.ctr = c->d_ctr;
   bt::TiledArgs tga;
   memset(&tga, 0, sizeof(tga));
@@ -811,6 +837,260 @@ BT_API int bt_set_result(bt_ctx *c, int32_t scene_id, const double *intensity, c
   return BT_OK;
 }
 
+// ===================================================================== batches
+// Many scenes traced together: one persistent trace launch and one scatter
+// launch per batch of lineages drawn from all scenes (every lane finds its
+// lineage's scene), the whole launch sequence captured once as a CUDA graph
+// and replayed by every run.
+struct bt_batch {
+  bt_ctx *c = nullptr;
+  std::vector<int> ids;
+  std::vector<unsigned long long> gens;
+  std::vector<int64_t> beams;  // lineages per scene
+  int prec = BT_PREC_MIXED;
+  int count_work = 0, blocks_per_sm = 0;
+  int max_order = 0;
+  int64_t total = 0, chunk = 1;
+  DevBuf views, segs, beam_tables[9];
+  bt::Counters *d_ctr = nullptr, *h_ctr = nullptr;
+  unsigned long long *d_cursors = nullptr;  // seg_count, lineage_next
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  long long kernels_per_run = 0;
+  bt_stats stats;
+};
+
+static void free_batch(bt_batch *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  release(b->views);
+  release(b->segs);
+  for (DevBuf &t : b->beam_tables) release(t);
+  if (b->d_ctr) cudaFree(b->d_ctr);
+  if (b->h_ctr) cudaFreeHost(b->h_ctr);
+  if (b->d_cursors) cudaFree(b->d_cursors);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  cudaGetLastError();
+  delete b;
+}
+
+BT_API int bt_batch_create(bt_ctx *c, const int32_t *scene_ids, int32_t n_scenes, const bt_trace_params *params,
+                           bt_batch **out) {
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  if (!out) return fail(c, BT_E_INVALID, "NULL output handle");
+  *out = nullptr;
+  if (n_scenes < 1 || n_scenes > BT_MAX_SCENES || !scene_ids || !params)
+    return fail(c, BT_E_INVALID, "a batch needs 1..%d scenes and their parameters", BT_MAX_SCENES);
+  std::vector<bt::SceneView> hv((size_t)n_scenes);
+  const int prec = params[0].precision;
+  for (int i = 0; i < n_scenes; i++) {
+    SceneState *s;
+    TRY(scene_ref(c, scene_ids[i], &s));
+    for (int j = 0; j < i; j++)
+      if (scene_ids[j] == scene_ids[i]) return fail(c, BT_E_INVALID, "scene %d listed twice", scene_ids[i]);
+    const bt_trace_params *p = &params[i];
+    float alpha_log2[BT_MAX_BANDS];
+    int has_alpha = 0;
+    TRY(check_params(c, s, p, alpha_log2, &has_alpha));
+    if (p->tiles_x != 1 || p->tiles_y != 1)
+      return fail(c, BT_E_INVALID, "a batch traces every scene unsplit (tiles 1x1)");
+    if (p->precision != prec || p->count_work != params[0].count_work ||
+        p->blocks_per_sm != params[0].blocks_per_sm || p->chunk_beams != params[0].chunk_beams)
+      return fail(c, BT_E_INVALID, "precision, count_work, blocks_per_sm and chunk_beams must agree across a batch");
+    fill_view(hv[i], *s, p, alpha_log2, has_alpha);
+  }
+  bt_batch *b = new bt_batch();
+  b->c = c;
+  b->prec = prec;
+  b->count_work = params[0].count_work ? 1 : 0;
+  b->blocks_per_sm = params[0].blocks_per_sm;
+  memset(&b->stats, 0, sizeof(b->stats));
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  int rc = BT_OK;
+  do {
+    for (int i = 0; i < n_scenes; i++) {
+      SceneState &s = c->sc[scene_ids[i]];
+      b->ids.push_back(scene_ids[i]);
+      b->gens.push_back(s.gen);
+      const int64_t nb = (int64_t)20 << (2 * s.level);
+      hv[i].lineage_base = b->total;
+      b->beams.push_back(s.n_src * nb);
+      b->total += s.n_src * nb;
+      if (params[i].max_order > b->max_order) b->max_order = params[i].max_order;
+      if (prec == BT_PREC_MIXED && s.n_src > 0) {
+        DevBuf &t = b->beam_tables[s.level];
+        if (!t.p) {
+          if ((rc = ensure(c, t, sizeof(float) * 24 * (size_t)nb))) break;
+          if (bt::launch_beam_table(st, s.level, (float *)t.p) != cudaSuccess) { rc = BT_E_CUDA; break; }
+        }
+        hv[i].beam_table = (const float *)t.p;
+      }
+    }
+    if (rc) break;
+    int64_t chunk = params[0].chunk_beams > 0 ? params[0].chunk_beams : ((int64_t)1 << 23) / (b->max_order + 1);
+    if (chunk > b->total) chunk = b->total;
+    if (chunk < 1) chunk = 1;
+    b->chunk = chunk;
+    if ((rc = ensure(c, b->views, sizeof(bt::SceneView) * (size_t)n_scenes))) break;
+    if ((rc = ensure(c, b->segs, sizeof(bt::Seg) * (size_t)chunk * (b->max_order + 1)))) break;
+    if (cudaMalloc(&b->d_ctr, sizeof(bt::Counters)) != cudaSuccess ||
+        cudaMallocHost(&b->h_ctr, sizeof(bt::Counters)) != cudaSuccess ||
+        cudaMalloc(&b->d_cursors, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+      rc = BT_E_NOMEM;
+      break;
+    }
+    if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess) { rc = BT_E_CUDA; break; }
+    if (cudaMemcpyAsync(b->views.p, hv.data(), sizeof(bt::SceneView) * (size_t)n_scenes, cudaMemcpyHostToDevice,
+                        st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      rc = BT_E_CUDA;
+      break;
+    }
+  } while (0);
+  if (rc) {
+    free_batch(b);
+    cudaGetLastError();
+    return fail(c, rc, "batch set-up failed (%d)", rc);
+  }
+  c->batches.push_back(b);
+  *out = b;
+  return BT_OK;
+}
+
+// Record the whole launch sequence of one batch run on the context's stream.
+static int record_batch(bt_batch *b) {
+  bt_ctx *c = b->c;
+  cudaStream_t st = c->stream;
+  const int n = (int)b->ids.size();
+  CK(cudaMemsetAsync(b->d_ctr, 0, sizeof(bt::Counters), st));
+  for (int i = 0; i < n; i++) {
+    SceneState &s = c->sc[b->ids[i]];
+    if (s.n_mics > 0) {
+      CK(cudaMemsetAsync(s.energy.p, 0, sizeof(double) * bt::kMaxBands * (size_t)s.n_mics, st));
+      CK(cudaMemsetAsync(s.count.p, 0, sizeof(int) * (size_t)s.n_mics, st));
+    }
+  }
+  bt::TraceArgs ta;
+  memset(&ta, 0, sizeof(ta));
+  ta.views = (const bt::SceneView *)b->views.p;
+  ta.n_views = n;
+  ta.segs = (bt::Seg *)b->segs.p;
+  ta.seg_count = b->d_cursors;
+  ta.lineage_next = b->d_cursors + 1;
+  ta.seg_capacity = (unsigned long long)b->chunk * (b->max_order + 1);
+  ta.ctr = b->d_ctr;
+  ta.count_work = b->count_work;
+  ta.prec = b->prec;
+  ta.blocks_per_sm = b->blocks_per_sm;
+  bt::ScatterArgs sa;
+  memset(&sa, 0, sizeof(sa));
+  sa.views = ta.views;
+  sa.n_views = n;
+  sa.fp64 = b->prec == BT_PREC_FP64 ? 1 : 0;
+  sa.segs = ta.segs;
+  sa.seg_count = ta.seg_count;
+  sa.seg_capacity = ta.seg_capacity;
+  sa.ctr = b->d_ctr;
+  const int64_t n_chunks = b->total > 0 ? (b->total + b->chunk - 1) / b->chunk : 0;
+  for (int64_t ci = 0; ci < n_chunks; ci++) {
+    ta.lineage_begin = ci * b->chunk;
+    ta.lineage_end = ta.lineage_begin + b->chunk < b->total ? ta.lineage_begin + b->chunk : b->total;
+    CK(cudaMemsetAsync(b->d_cursors, 0, 2 * sizeof(unsigned long long), st));
+    CK(bt::launch_trace(st, ta, c->n_sm));
+    CK(bt::launch_scatter(st, sa, c->n_sm));
+  }
+  return BT_OK;
+}
+
+BT_API int bt_batch_run(bt_batch *b) {
+  if (!b) return BT_E_INVALID;
+  bt_ctx *c = b->c;
+  c->err[0] = 0;
+  for (size_t i = 0; i < b->ids.size(); i++)
+    if (c->sc[b->ids[i]].gen != b->gens[i])
+      return fail(c, BT_E_STATE, "scene %d changed since the batch was created", b->ids[i]);
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  if (!b->exec) {
+    // capture the launch sequence once; every run replays it
+    const long long k0 = bt_kernel_launches();
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int rc = record_batch(b);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    b->kernels_per_run = bt_kernel_launches() - k0;
+    bt::note_launches((int)-b->kernels_per_run);  // counted when they run
+    if (rc != BT_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return fail(c, rc != BT_OK ? rc : BT_E_CUDA, "batch graph capture failed");
+    }
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      b->exec = nullptr;
+      return fail(c, BT_E_CUDA, "batch graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+  }
+  CK(cudaEventRecord(b->ev0, st));
+  CK(cudaGraphLaunch(b->exec, st));
+  CK(cudaEventRecord(b->ev1, st));
+  bt::note_launches((int)b->kernels_per_run);
+  CK(cudaMemcpyAsync(b->h_ctr, b->d_ctr, sizeof(bt::Counters), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+  const bt::Counters &h = *b->h_ctr;
+  bt_stats &o = b->stats;
+  memset(&o, 0, sizeof(o));
+  o.beams = b->total;
+  o.segments = (int64_t)h.segments;
+  o.hits = (int64_t)h.hits;
+  o.escapes = (int64_t)h.escapes;
+  o.emitted = (int64_t)h.emitted;
+  o.candidates = (int64_t)h.candidates;
+  o.contributions = (int64_t)h.contributions;
+  o.nodes_visited = (int64_t)h.nodes_visited;
+  o.tris_tested = (int64_t)h.tris_tested;
+  const int64_t n_chunks = b->total > 0 ? (b->total + b->chunk - 1) / b->chunk : 0;
+  o.trace_launches = n_chunks;
+  o.scatter_launches = n_chunks;
+  o.trace_ms = ms;
+  for (size_t i = 0; i < b->ids.size(); i++) {
+    SceneState &s = c->sc[b->ids[i]];
+    memset(&s.stats, 0, sizeof(s.stats));
+    s.stats.beams = b->beams[i];
+    s.traced = h.error == 0;
+  }
+  if (h.error)
+    return fail(c, h.error, h.error == BT_E_QUEUE_FULL ? "device queue or traversal stack overflow"
+                                                        : "device error %d", h.error);
+  return BT_OK;
+}
+
+BT_API int bt_batch_stats(const bt_batch *b, bt_stats *stats) {
+  if (!b || !stats) return BT_E_INVALID;
+  *stats = b->stats;
+  return BT_OK;
+}
+
+BT_API int bt_batch_destroy(bt_batch *b) {
+  if (!b) return BT_OK;
+  bt_ctx *c = b->c;
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (size_t i = 0; i < c->batches.size(); i++)
+    if (c->batches[i] == b) {
+      c->batches.erase(c->batches.begin() + (long)i);
+      break;
+    }
+  free_batch(b);
+  return BT_OK;
+}
+
 BT_API int bt_cast_rays(bt_ctx *c, int32_t scene_id, const float *origins, const float *dirs,
                         const float *start_normals, int64_t n, float t_eps_m, float *t_out,
                         int32_t *tri_out) {
@@ -950,18 +1230,8 @@ BT_API int bt_trace_noalloc(bt_ctx *c, int32_t scene_id, const bt_trace_params *
   if (mixed && total > 0) CK(bt::launch_beam_table(st, s->level, beam_table));
   bt::TraceArgs ta;
   memset(&ta, 0, sizeof(ta));
-  ta.sc = dev_scene(*s);
-  ta.src = (const float4 *)s->src.p;
-  ta.power = (const float *)s->power.p;
-  ta.n_src = s->n_src;
-  ta.level = s->level;
-  ta.n_beams = n_beams;
-  ta.max_order = p->max_order;
-  ta.t_eps = p->t_eps_m;
-  ta.energy_threshold = p->energy_threshold_w;
-  for (int b = 0; b < BT_MAX_BANDS; b++) ta.alpha_log2[b] = alpha_log2[b];
-  ta.has_alpha = has_alpha;
-  ta.grid = (const bt::MicGrid *)s->grid.p;
+  fill_view(ta.v, *s, p, alpha_log2, has_alpha);
+  ta.v.beam_table = mixed ? beam_table : nullptr;
   ta.segs = segs;
   ta.seg_count = seg_count;
   ta.seg_capacity = cap;
@@ -969,24 +1239,14 @@ BT_API int bt_trace_noalloc(bt_ctx *c, int32_t scene_id, const bt_trace_params *
   ta.ctr = ctr;
   ta.count_work = 0;
   ta.prec = p->precision;
-  ta.beam_table = mixed ? beam_table : nullptr;
+  ta.blocks_per_sm = p->blocks_per_sm;
   bt::ScatterArgs sa;
   memset(&sa, 0, sizeof(sa));
-  sa.tris = ta.sc.tris;
-  sa.planes_df = ta.sc.planes_df;
-  sa.planes64 = ta.sc.planes64;
+  sa.v = ta.v;
   sa.fp64 = p->precision == BT_PREC_FP64 ? 1 : 0;
   sa.segs = segs;
   sa.seg_count = seg_count;
   sa.seg_capacity = cap;
-  sa.grid = ta.grid;
-  sa.mics = (const float4 *)s->mics.p;
-  sa.cell_start = (const int *)s->cell_start.p;
-  sa.energy = (double *)s->energy.p;
-  sa.count = (int *)s->count.p;
-  sa.n_bands = s->n_bands;
-  for (int b = 0; b < BT_MAX_BANDS; b++) sa.alpha_log2[b] = alpha_log2[b];
-  sa.has_alpha = has_alpha;
   sa.ctr = ctr;
   const int64_t n_chunks = total > 0 ? (total + chunk - 1) / chunk : 0;
   for (int64_t ci = 0; ci < n_chunks; ci++) {

@@ -104,7 +104,7 @@ struct MicGrid {
 // missing plane is (0, 0, 0, -inf).
 struct __align__(16) Seg {
   float ahi[3], alo[3];  // apex (source or image source)
-  int cy0, cy1;          // footprint rows on the microphone grid (set by the scatter)
+  int view, pad_i;       // index of the scene view (0 in a single-scene trace)
   float4 n0;             // cone-face normal 0 (hi); w: leaf slot of the start plane's triangle (-1 none)
   float4 n1;             // w: leaf slot of the end plane's triangle (-1 none)
   float4 n2;             // w: reflection order (int bits)
@@ -126,20 +126,37 @@ struct Counters {
   int pad;
 };
 
-struct TraceArgs {
+// Everything the trace and scatter kernels need about one scene: geometry,
+// sources, microphones, result arrays and trace parameters.  A single-scene
+// trace passes one view by value; a batch passes an array of views in device
+// memory and every lineage and segment carries its view's index.
+struct SceneView {
   DevScene sc;
   const float4 *src;      // [n_s] xyz
   const float *power;     // [n_s][n_bands]
   int64_t n_src;
   int level;              // icosahedron level L
-  int64_t n_beams;        // 20 * 4^L
   int max_order;
+  int64_t n_beams;        // 20 * 4^L
+  int64_t lineage_base;   // batch: first lineage of this scene in the batch's lineage space
   float t_eps;
   float energy_threshold;
   float alpha_log2[kMaxBands];  // air damping as a base-2 exponent per metre: -alpha_b * log2(10) / 10
   int has_alpha;
+  int pad0;
   const MicGrid *grid;
-  int64_t lineage_begin, lineage_end;  // chunk of (source, beam) lineages
+  const float *beam_table;   // MIXED: per beam 3 cone normals + axis as float pairs: [n_beams][12] hi, then lo
+  const float4 *mics;        // sorted by cell: xyz, w = original index (int bits)
+  const int *cell_start;     // [nx * ny + 1]
+  double *energy;            // [n_mics][kMaxBands], sorted order
+  int *count;                // [n_mics], sorted order
+};
+
+struct TraceArgs {
+  SceneView v;                         // the scene (single-scene trace)
+  const SceneView *views;              // batch: [n_views] in device memory, else null
+  int n_views;
+  int64_t lineage_begin, lineage_end;  // chunk of (scene,) source, beam lineages
   unsigned long long *lineage_next;    // lineages of the chunk taken so far (zeroed per chunk)
   Seg *segs;
   unsigned long long *seg_count;
@@ -147,25 +164,17 @@ struct TraceArgs {
   Counters *ctr;
   int count_work;
   int prec;   // BT_PREC_FP32, BT_PREC_MIXED or BT_PREC_FP64
-  const float *beam_table;   // MIXED: per beam 3 cone normals + axis as float pairs: [n_beams][12] hi, then lo
+  int blocks_per_sm;  // persistent grid: resident blocks per SM, 0 = as many as fit
 };
 
 struct ScatterArgs {
-  const Tri *tris;          // leaf order (start/end plane vertices)
-  const PlaneDF *planes_df; // leaf order
-  const Plane64 *planes64;  // leaf order
+  SceneView v;              // the scene (single-scene trace)
+  const SceneView *views;   // batch: [n_views] in device memory, else null
+  int n_views;
   int fp64;                 // 1: every microphone test in float64 (BT_PREC_FP64)
   const Seg *segs;
   const unsigned long long *seg_count;
   unsigned long long seg_capacity;
-  const MicGrid *grid;
-  const float4 *mics;       // sorted by cell: xyz, w = original index (int bits)
-  const int *cell_start;    // [nx * ny + 1]
-  double *energy;           // [n_mics][kMaxBands], sorted order
-  int *count;               // [n_mics], sorted order
-  int n_bands;
-  float alpha_log2[kMaxBands];
-  int has_alpha;
   Counters *ctr;
 };
 

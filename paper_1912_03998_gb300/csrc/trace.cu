@@ -416,7 +416,7 @@ __device__ __forceinline__ void st_d3(LineageSmem<kP> &sm, int row, int t, doubl
 
 // Start lineage `lin` (source si, beam bi) in this thread's column.
 template <int kP>
-__device__ __forceinline__ void init_lineage(const TraceArgs &a, LineageSmem<kP> &sm, int t, int64_t lin) {
+__device__ __forceinline__ void init_lineage(const SceneView &a, LineageSmem<kP> &sm, int t, int64_t lin) {
   [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   const int nb = a.sc.n_bands;
   int64_t si = lin / a.n_beams, bi = lin - si * a.n_beams;
@@ -492,19 +492,19 @@ __device__ __forceinline__ TraceCounts init_counts(LineageSmem<kP> &sm, int t) {
 // image source (Section 2), mirrored cone and axis, energy lost at the
 // reflection.  Returns true if the lineage continues.
 template <int kP>
-__device__ __forceinline__ bool finish_segment(const TraceArgs &a, LineageSmem<kP> &sm, int t, const Ray &r,
-                                               const Best &best, int slot, LaneState &ls, const MicGrid &g,
+__device__ __forceinline__ bool finish_segment(const TraceArgs &a, const SceneView &v, int vi, LineageSmem<kP> &sm,
+                                               int t, const Ray &r, const Best &best, int slot, LaneState &ls,
                                                const TraceCounts &cn) {
   [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
-  const int nb = a.sc.n_bands;
+  const int nb = v.sc.n_bands;
   cn[kCSeg]++;
   float4 end = make_float4(0.0f, 0.0f, 0.0f, -kInf);
   float4 v0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   float4 plf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   if (slot >= 0) {
     cn[kCHit]++;
-    v0 = __ldg(&a.sc.tris[slot].v0);
-    plf = __ldg(&a.sc.planes[slot]);
+    v0 = __ldg(&v.sc.tris[slot].v0);
+    plf = __ldg(&v.sc.planes[slot]);
     // end plane on the incident side, offset relative to the apex
     float3 pn = f3(plf);
     float3 en = dot3(pn, r.d) < 0.0f ? pn : pn * -1.0f;
@@ -547,28 +547,29 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, LineageSmem<k
     s.end = end;
     s.p03 = make_float4(sm.p[0][t], sm.p[1][t], sm.p[2][t], sm.p[3][t]);
     s.p47 = make_float4(sm.p[4][t], sm.p[5][t], sm.p[6][t], sm.p[7][t]);
-    s.cy0 = 0;
-    s.cy1 = -1;
+    s.view = vi;
+    s.pad_i = 0;
+    const MicGrid &g = *v.grid;
     emit_segment(a, s, g.n_mics > 0 && may_reach_slab(n0, n1, n2, s.ahi[2], g), cn[kCEmit]);
   }
-  if (slot < 0 || ls.k == a.max_order) return false;
+  if (slot < 0 || ls.k == v.max_order) return false;
   // energy lost at the reflection
   int mat = __float_as_int(v0.w);
   float wmax = 0.0f;
 #pragma unroll
   for (int b = 0; b < kMaxBands; b++) {
     float p = sm.p[b][t];
-    if (b < nb) p *= __ldg(&a.sc.refl[mat * nb + b]);
+    if (b < nb) p *= __ldg(&v.sc.refl[mat * nb + b]);
     sm.p[b][t] = p;
     wmax = fmaxf(wmax, p);
   }
-  if (a.energy_threshold > 0.0f && wmax < a.energy_threshold) return false;
+  if (v.energy_threshold > 0.0f && wmax < v.energy_threshold) return false;
   // Image source: mirror the apex, the cone and the axis in the hit plane;
   // the reflected beam starts at the hit point on that plane.
   float3 pn = f3(plf), pv0 = f3(v0);
   float3 Dn;
   if (kF64) {
-    Plane64 pl = ldg_d4(&a.sc.planes64[slot]);
+    Plane64 pl = ldg_d4(&v.sc.planes64[slot]);
     const double3 n = make_double3(pl.x, pl.y, pl.z), v0d = make_double3(v0.x, v0.y, v0.z);
     double3 A = ld_d3(sm, kRowA, t), O = ld_d3(sm, kRowO, t), D = ld_d3(sm, kRowD, t);
     const double th = best.has64 ? best.t64 : (pl.w - dot3(n, O)) / dot3(n, D);
@@ -591,7 +592,7 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, LineageSmem<k
     const double sw = dot3(sn, v0d - A);
     sm.st[0][t] = (float)sn.x; sm.st[1][t] = (float)sn.y; sm.st[2][t] = (float)sn.z; sm.st[3][t] = (float)sw;
   } else if (kMixed) {
-    PlaneDF pd = a.sc.planes_df[slot];
+    PlaneDF pd = v.sc.planes_df[slot];
     df3 n = df3{df{pd.hi.x, pd.lo.x}, df{pd.hi.y, pd.lo.y}, df{pd.hi.z, pd.lo.z}};
     df w = df{pd.hi.w, pd.lo.w};
     df3 A = ld_df3(sm, kRowA, t), O = ld_df3(sm, kRowO, t), D = ld_df3(sm, kRowD, t);
@@ -674,17 +675,30 @@ __device__ __forceinline__ int64_t take_lineage(const TraceArgs &a, bool need) {
 // Persistent warps: every lane works on one lineage at a time and takes the
 // next one from a global counter as soon as its lineage ends, so a warp stays
 // full until the batch runs out (warp-vote refill of finished lanes).
+// Index of the view whose lineage range holds global lineage `g` (views in
+// lineage order).
+__device__ __forceinline__ int find_view(const TraceArgs &a, int64_t g) {
+  int lo = 0, hi = a.n_views - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (a.views[mid].lineage_base <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // Six resident blocks per SM (at most 80 registers a thread): the traversal
 // is latency-bound, and on the district workload this beat both fewer blocks
-// without spills and more blocks with heavier spills.
-template <int kP, bool kCount>
+// without spills and more blocks with heavier spills.  kBatch: the lineages
+// of many scenes (views) in one launch, each lane on its own lineage's scene.
+template <int kP, bool kCount, bool kBatch>
 __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
   [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   __shared__ LineageSmem<kP> sm;
   const int t = threadIdx.x;
-  const MicGrid g = *a.grid;
   const TraceCounts cn = init_counts(sm, t);
   LaneState ls = {-1, 0, -1, 0.0f, 0.0};
+  int vi = 0;  // this lane's scene view
   bool done = false;
   const RaySrc rs{&sm.hi[kRowO][t], kMixed ? &sm.lo[kRowO][t] : &sm.hi[kRowO][t], kTraceThreads,
                   kF64 ? &sm.dv[kRowO][t] : nullptr};
@@ -693,8 +707,12 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
     int64_t mine = take_lineage(a, need);
     if (need) {
       if (mine >= 0) {
+        if (kBatch) {
+          vi = find_view(a, mine);
+          mine -= a.views[vi].lineage_base;
+        }
         ls = LaneState{mine, 0, -1, 0.0f, 0.0};
-        init_lineage(a, sm, t, mine);
+        init_lineage(kBatch ? a.views[vi] : a.v, sm, t, mine);
       } else {
         done = true;
       }
@@ -703,15 +721,16 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
     const unsigned act_mask = __ballot_sync(0xffffffffu, !done);
     if (done) continue;
     // ---- one segment of this lane's lineage
-    const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), a.t_eps, ls.dns);
+    const SceneView &v = kBatch ? a.views[vi] : a.v;
+    const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), v.t_eps, ls.dns);
     Best best;
-    int slot = closest_hit<kP, kCount>(a.sc, r, rs, ls.dns64, best, &a.ctr->error, cn[kCNodes], cn[kCTris],
-                                           a.sc.root);
+    int slot = closest_hit<kP, kCount>(v.sc, r, rs, ls.dns64, best, &a.ctr->error, cn[kCNodes], cn[kCTris],
+                                       v.sc.root);
     // the lanes leave the traversal loop at different times; reconverge them
     // so that the segment's bookkeeping and reflection run once per warp
     // rather than once per lane
     __syncwarp(act_mask);
-    if (!finish_segment(a, sm, t, r, best, slot, ls, g, cn)) ls.lin = -1;
+    if (!finish_segment(a, v, vi, sm, t, r, best, slot, ls, cn)) ls.lin = -1;
   }
   flush_counts(a, cn, kCount);
 }
@@ -922,7 +941,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, c
   const int t = threadIdx.x;
   const unsigned lane = lane_id();
   const unsigned below = (1u << lane) - 1u;
-  const MicGrid g = *a.grid;
+  const SceneView &v = a.v;
   const TileGrid &tg = ta.tg;  // read from parameter space, not held in registers
   const TraceCounts cn = init_counts(sm, t);
   const size_t qc = ta.qcap;
@@ -970,7 +989,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, c
         if (!active && rank < got_f) {
           int64_t mine = a.lineage_begin + fb + rank;
           ls = LaneState{mine, 0, -1, 0.0f, 0.0};
-          init_lineage(a, sm, t, mine);
+          init_lineage(v, sm, t, mine);
           active = true;
           float3 o = ld_hi3(sm, kRowO, t);
           tile = clampi((int)floorf((o.y - tg.gy0) / tg.wy), 0, tg.ty - 1) * tg.tx +
@@ -1003,14 +1022,14 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, c
     bool ended = false;
     const unsigned act_mask = __ballot_sync(0xffffffffu, active);
     if (active) {
-      const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), a.t_eps, ls.dns);
+      const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), v.t_eps, ls.dns);
       Best best;
-      int hit = closest_hit<kP, kCount>(a.sc, r, rs, ls.dns64, best, &a.ctr->error, cn[kCNodes], cn[kCTris],
+      int hit = closest_hit<kP, kCount>(v.sc, r, rs, ls.dns64, best, &a.ctr->error, cn[kCNodes], cn[kCTris],
                                             __ldg(&ta.roots[tile]), &tg, tile);
       __syncwarp(act_mask);  // reconverge after the traversal loop (see k_trace)
       if (hit >= 0) {
         // the hit lies in this tile; a reflected beam starts here as well
-        if (!finish_segment(a, sm, t, r, best, hit, ls, g, cn)) ended = true;
+        if (!finish_segment(a, v, 0, sm, t, r, best, hit, ls, cn)) ended = true;
       } else {
         // no hit in this tile: step to the next tile along the ray whose
         // geometry the ray can reach -- tiles whose root boxes it misses
@@ -1029,11 +1048,11 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, c
             if (tey <= tex) iy += r.d.y > 0.0f ? 1 : -1;
             leaves = ix < 0 || ix >= tg.tx || iy < 0 || iy >= tg.ty;
           }
-          if (leaves || root_reachable(a.sc, __ldg(&ta.roots[iy * tg.tx + ix]), r)) break;
+          if (leaves || root_reachable(v.sc, __ldg(&ta.roots[iy * tg.tx + ix]), r)) break;
         }
         if (leaves) {
           // the ray leaves the grid, and with it every triangle: it escapes
-          finish_segment(a, sm, t, r, best, -1, ls, g, cn);
+          finish_segment(a, v, 0, sm, t, r, best, -1, ls, cn);
           ended = true;
         } else {
           next = iy * tg.tx + ix;
@@ -1085,6 +1104,7 @@ static cudaError_t launch_tiled_t(cudaStream_t st, const TraceArgs &a, const Til
   cudaError_t e =
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tiled<kP, kCount>, kTraceThreads, 0);
   if (e != cudaSuccess) return e;
+  if (a.blocks_per_sm > 0 && a.blocks_per_sm < per_sm) per_sm = a.blocks_per_sm;
   if (per_sm < 1) per_sm = 1;
   int64_t blocks = (int64_t)n_sm * per_sm;
   k_trace_tiled<kP, kCount><<<(int)blocks, kTraceThreads, 0, st>>>(a, ta);
@@ -1150,31 +1170,36 @@ cudaError_t launch_cast(cudaStream_t st, const DevScene &sc, const float *o, con
 
 // One persistent grid: enough blocks to fill every SM at the kernel's
 // occupancy, each block looping until the batch's lineages are taken.
-template <int kP, bool kCount>
+template <int kP, bool kCount, bool kBatch>
 static cudaError_t launch_trace_t(cudaStream_t st, const TraceArgs &a, int n_sm) {
-  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<kP, kCount>, kTraceThreads, 0);
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<kP, kCount, kBatch>, kTraceThreads, 0);
   if (e != cudaSuccess) return e;
+  if (a.blocks_per_sm > 0 && a.blocks_per_sm < per_sm) per_sm = a.blocks_per_sm;
   if (per_sm < 1) per_sm = 1;
   int64_t n = a.lineage_end - a.lineage_begin;
   int64_t blocks = (int64_t)n_sm * per_sm;
   int64_t need = (n + kTraceThreads - 1) / kTraceThreads;
   if (blocks > need) blocks = need;
-  k_trace<kP, kCount><<<(int)blocks, kTraceThreads, 0, st>>>(a);
+  k_trace<kP, kCount, kBatch><<<(int)blocks, kTraceThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_trace(cudaStream_t st, const TraceArgs &a, int n_sm) {
-  int64_t n = a.lineage_end - a.lineage_begin;
-  if (n <= 0) return cudaSuccess;
-  cudaError_t e;
+template <bool kBatch>
+static cudaError_t launch_trace_b(cudaStream_t st, const TraceArgs &a, int n_sm) {
   if (a.prec == kPMixed)
-    e = a.count_work ? launch_trace_t<kPMixed, true>(st, a, n_sm) : launch_trace_t<kPMixed, false>(st, a, n_sm);
-  else if (a.prec == kPF64)
-    e = a.count_work ? launch_trace_t<kPF64, true>(st, a, n_sm) : launch_trace_t<kPF64, false>(st, a, n_sm);
-  else
-    e = a.count_work ? launch_trace_t<kPF32, true>(st, a, n_sm) : launch_trace_t<kPF32, false>(st, a, n_sm);
+    return a.count_work ? launch_trace_t<kPMixed, true, kBatch>(st, a, n_sm)
+                        : launch_trace_t<kPMixed, false, kBatch>(st, a, n_sm);
+  if (a.prec == kPF64)
+    return a.count_work ? launch_trace_t<kPF64, true, kBatch>(st, a, n_sm)
+                        : launch_trace_t<kPF64, false, kBatch>(st, a, n_sm);
+  return a.count_work ? launch_trace_t<kPF32, true, kBatch>(st, a, n_sm)
+                      : launch_trace_t<kPF32, false, kBatch>(st, a, n_sm);
+}
+
+cudaError_t launch_trace(cudaStream_t st, const TraceArgs &a, int n_sm) {
+  cudaError_t e = a.views ? launch_trace_b<true>(st, a, n_sm) : launch_trace_b<false>(st, a, n_sm);
   note_launches(1);
   return e;
 }
@@ -1185,7 +1210,8 @@ cudaError_t launch_trace(cudaStream_t st, const TraceArgs &a, int n_sm) {
 constexpr int kScatterWarps = 4;
 enum : int {
   F_AX = 0, F_RX = 3, F_N0 = 6, F_NLO = 15, F_NS = 24, F_NE = 28, F_P = 32, F_SLOTS = 40,
-  F_CY0 = 42, F_PN = 43, F_PX = 44, F_PY = F_PX + kPolyMax, F_AP = F_PY + kPolyMax, F_COUNT = F_AP + 3
+  F_CY0 = 42, F_PN = 43, F_PX = 44, F_PY = F_PX + kPolyMax, F_AP = F_PY + kPolyMax, F_VI = F_AP + 3,
+  F_COUNT = F_VI + 1
 };
 struct ScatterSmem {
   float f[kScatterWarps][F_COUNT][32];
@@ -1217,9 +1243,9 @@ __device__ __forceinline__ df3 rel_df(const float (*F)[32], int s, float4 m) {
 
 // Signed distance of m from the plane of leaf slot `slot` as a float pair,
 // oriented like the float32 normal `nf` of the segment record.
-__device__ __forceinline__ float plane_side_df(const ScatterArgs &a, int slot, float3 nf, float4 m) {
-  PlaneDF pd = a.planes_df[slot];
-  float4 v0 = __ldg(&a.tris[slot].v0);
+__device__ __forceinline__ float plane_side_df(const SceneView &a, int slot, float3 nf, float4 m) {
+  PlaneDF pd = a.sc.planes_df[slot];
+  float4 v0 = __ldg(&a.sc.tris[slot].v0);
   df3 n = df3{df{pd.hi.x, pd.lo.x}, df{pd.hi.y, pd.lo.y}, df{pd.hi.z, pd.lo.z}};
   df3 rel = df3_sub(mkdf3(make_float3(m.x, m.y, m.z)), mkdf3(f3(v0)));
   df e = df3_dot(n, rel);
@@ -1229,8 +1255,8 @@ __device__ __forceinline__ float plane_side_df(const ScatterArgs &a, int slot, f
 
 // Signed distance of m from the float64 plane of leaf slot `slot`, oriented
 // like the float32 normal `nf` of the segment record (FP64 mode).
-__device__ __forceinline__ double plane_side64(const ScatterArgs &a, int slot, float3 nf, float4 m) {
-  Plane64 pl = ldg_d4(&a.planes64[slot]);
+__device__ __forceinline__ double plane_side64(const SceneView &a, int slot, float3 nf, float4 m) {
+  Plane64 pl = ldg_d4(&a.sc.planes64[slot]);
   double e = pl.x * (double)m.x + pl.y * (double)m.y + pl.z * (double)m.z - pl.w;
   return pl.x * nf.x + pl.y * nf.y + pl.z * nf.z < 0.0 ? -e : e;
 }
@@ -1240,15 +1266,13 @@ __device__ __forceinline__ double plane_side64(const ScatterArgs &a, int slot, f
 // all 32 footprints 32 at a time, turns each into its run of microphones, and
 // walks the runs 32 candidates at a time, so every lane has work whatever
 // the footprint sizes.
-template <bool kF64>
+template <bool kF64, bool kBatch>
 __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
   __shared__ ScatterSmem sm;
-  const MicGrid g = *a.grid;
   const unsigned lane = lane_id();
   const int w = threadIdx.x >> 5;
   float(*F)[32] = sm.f[w];
   const long long n_seg = (long long)min(*a.seg_count, a.seg_capacity);
-  const int nb = a.n_bands;
   unsigned long long n_cand = 0, n_contrib = 0;
   const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -1262,6 +1286,9 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
       float4 *dst4 = reinterpret_cast<float4 *>(&sl);
 #pragma unroll
       for (int q = 0; q < (int)(sizeof(Seg) / 16); q++) dst4[q] = __ldg(src4 + q);
+      const int vi = kBatch ? sl.view : 0;
+      const MicGrid &g = *(kBatch ? a.views[vi] : a.v).grid;
+      F[F_VI][lane] = __int_as_float(vi);
       Poly p;
       int cy0 = 0, cy1 = -1;
       if (seg_footprint(sl, g, p)) {
@@ -1309,6 +1336,8 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
       int so_excl = __shfl_sync(0xffffffffu, rexcl, so);
       int first = 0, cnt = 0;
       if (r < total_rows) {
+        const SceneView &V = kBatch ? a.views[__float_as_int(F[F_VI][so])] : a.v;
+        const MicGrid &g = *V.grid;
         int row = __float_as_int(F[F_CY0][so]) + (r - so_excl);
         float ya = g.y0 + row * g.ch, yb = ya + g.ch;
         float my = 1e-3f * g.ch;
@@ -1332,8 +1361,8 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
         if (xmin <= xmax) {
           int cx0 = clampi((int)floorf((xmin - g.x0) * g.inv_cw), 0, g.nx - 1);
           int cx1 = clampi((int)floorf((xmax - g.x0) * g.inv_cw), 0, g.nx - 1);
-          first = __ldg(&a.cell_start[row * g.nx + cx0]);
-          cnt = __ldg(&a.cell_start[row * g.nx + cx1 + 1]) - first;
+          first = __ldg(&V.cell_start[row * g.nx + cx0]);
+          cnt = __ldg(&V.cell_start[row * g.nx + cx1 + 1]) - first;
         }
       }
       // ---- 3. candidates of those runs, 32 at a time
@@ -1348,7 +1377,9 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
         int s = __shfl_sync(0xffffffffu, so, ro);
         if (c < total_c) {
           int mi = ofirst + (c - oexcl);
-          float4 m = __ldg(&a.mics[mi]);
+          const SceneView &V = kBatch ? a.views[__float_as_int(F[F_VI][s])] : a.v;
+          const int nb = V.sc.n_bands;
+          float4 m = __ldg(&V.mics[mi]);
           if (kF64) {
             // FP64: every test and the contribution in float64 (apex exact
             // from its three words, cone normals from their float pairs,
@@ -1370,24 +1401,24 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
               int s_slot = __float_as_int(F[F_SLOTS][s]), e_slot = __float_as_int(F[F_SLOTS + 1][s]);
               float3 ns = make_float3(F[F_NS][s], F[F_NS + 1][s], F[F_NS + 2][s]);
               float3 ne = make_float3(F[F_NE][s], F[F_NE + 1][s], F[F_NE + 2][s]);
-              double fs = s_slot >= 0 ? plane_side64(a, s_slot, ns, m) : 1.0;
-              double fe = e_slot >= 0 ? plane_side64(a, e_slot, ne, m) : 1.0;
+              double fs = s_slot >= 0 ? plane_side64(V, s_slot, ns, m) : 1.0;
+              double fe = e_slot >= 0 ? plane_side64(V, e_slot, ne, m) : 1.0;
               in = fs > 0.0 && fe >= 0.0;
             }
             const double d2 = dot3(vd, vd);
             if (in && d2 > 1e-18) {
               const double gf = 1.0 / (4.0 * 3.141592653589793 * d2);
-              const double dist = a.has_alpha ? sqrt(d2) : 0.0;
-              double *e = a.energy + (size_t)mi * kMaxBands;
+              const double dist = V.has_alpha ? sqrt(d2) : 0.0;
+              double *e = V.energy + (size_t)mi * kMaxBands;
 #pragma unroll
               for (int b = 0; b < kMaxBands; b++) {
                 if (b < nb) {
                   double cval = (double)F[F_P + b][s] * gf;
-                  if (a.has_alpha) cval *= exp2((double)a.alpha_log2[b] * dist);
+                  if (V.has_alpha) cval *= exp2((double)V.alpha_log2[b] * dist);
                   atomicAdd(e + b, cval);
                 }
               }
-              atomicAdd(a.count + mi, 1);
+              atomicAdd(V.count + mi, 1);
               n_contrib++;
             }
             continue;
@@ -1421,24 +1452,24 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
             float band = 1e-4f + 1e-6f * (fabsf(v.x) + fabsf(v.y) + fabsf(v.z));
             float fs = dot3(ns, v) - F[F_NS + 3][s], fe = dot3(ne, v) - F[F_NE + 3][s];
             int s_slot = __float_as_int(F[F_SLOTS][s]), e_slot = __float_as_int(F[F_SLOTS + 1][s]);
-            if (fabsf(fs) <= band && s_slot >= 0) fs = plane_side_df(a, s_slot, ns, m);
-            if (fabsf(fe) <= band && e_slot >= 0) fe = plane_side_df(a, e_slot, ne, m);
+            if (fabsf(fs) <= band && s_slot >= 0) fs = plane_side_df(V, s_slot, ns, m);
+            if (fabsf(fe) <= band && e_slot >= 0) fe = plane_side_df(V, e_slot, ne, m);
             in = fs > 0.0f && fe >= 0.0f;
           }
           float d2 = dot3(v, v);
           if (in && d2 > 1e-18f) {
             float gf = 1.0f / (4.0f * 3.14159265358979f * d2);
-            float dist = a.has_alpha ? sqrtf(d2) : 0.0f;
-            double *e = a.energy + (size_t)mi * kMaxBands;
+            float dist = V.has_alpha ? sqrtf(d2) : 0.0f;
+            double *e = V.energy + (size_t)mi * kMaxBands;
 #pragma unroll
             for (int b = 0; b < kMaxBands; b++) {
               if (b < nb) {
                 float cval = F[F_P + b][s] * gf;
-                if (a.has_alpha) cval *= exp2f(a.alpha_log2[b] * dist);
+                if (V.has_alpha) cval *= exp2f(V.alpha_log2[b] * dist);
                 atomicAdd(e + b, (double)cval);
               }
             }
-            atomicAdd(&a.count[mi], 1);
+            atomicAdd(&V.count[mi], 1);
             n_contrib++;
           }
         }
@@ -1456,18 +1487,21 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
   }
 }
 
-template <bool kF64>
+template <bool kF64, bool kBatch>
 static cudaError_t launch_scatter_t(cudaStream_t st, const ScatterArgs &a, int n_sm) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<kF64>, 32 * kScatterWarps, 0);
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<kF64, kBatch>, 32 * kScatterWarps, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  k_scatter<kF64><<<n_sm * per_sm, 32 * kScatterWarps, 0, st>>>(a);
+  k_scatter<kF64, kBatch><<<n_sm * per_sm, 32 * kScatterWarps, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scatter(cudaStream_t st, const ScatterArgs &a, int n_sm) {
-  cudaError_t e = a.fp64 ? launch_scatter_t<true>(st, a, n_sm) : launch_scatter_t<false>(st, a, n_sm);
+  cudaError_t e;
+  if (a.views) e = a.fp64 ? launch_scatter_t<true, true>(st, a, n_sm) : launch_scatter_t<false, true>(st, a, n_sm);
+  else e = a.fp64 ? launch_scatter_t<true, false>(st, a, n_sm) : launch_scatter_t<false, false>(st, a, n_sm);
   note_launches(1);
   return e;
 }

@@ -349,3 +349,26 @@ def district(seed: int = 2, n_buildings: int = 5000, n_sources: int = 1000, leve
     mics = mic_grid(0.0, 0.0, DIST_MIC_SIDE, DIST_MIC_SIDE, n_mic_side, n_mic_side, 1.5)
     return Workload("district", scene, src, power, mics, level, max_order, tuple(tiles),
                     {"seed": seed, **info})
+
+
+def batch_cities(seed: int = 4, n: int = 64):
+    """Cities of uneven size for batched tracing: each drawn like the district
+    (same footprint, height and source distributions on the same 2 km road
+    grid) with 100-5,000 buildings and 1-1,000 sources (both log-uniform),
+    icosahedron level 3-6 (1,280-81,920 beams per source) and reflection order
+    2-8 (both uniform), and 1k-250k microphones (log-uniform) on a square grid
+    at 1.5 m."""
+    rng = _rng(seed)
+    out = []
+    for i in range(n):
+        n_b = int(round(math.exp(rng.uniform(math.log(100), math.log(5000)))))
+        n_s = int(round(math.exp(rng.uniform(math.log(1), math.log(1000)))))
+        level = int(rng.integers(3, 7))
+        k = int(rng.integers(2, 9))
+        n_m = math.exp(rng.uniform(math.log(1000), math.log(250000)))
+        side = max(2, int(round(math.sqrt(n_m))))
+        w = district(seed=seed * 1000 + i, n_buildings=n_b, n_sources=n_s, level=level, max_order=k,
+                     n_mic_side=side, tiles=(1, 1))
+        w.name = f"city{i}"
+        out.append(w)
+    return out

@@ -52,7 +52,7 @@ def test_params_default_is_host_only(libpath):
 def test_struct_sizes_match_header(libpath):
     # the ctypes mirrors must have the C layout: 4-byte fields only in params
     from paper_1912_03998_gb300 import btrace
-    assert C.sizeof(btrace.bt_trace_params) == 4 * (1 + 8 + 1 + 1 + 2 + 1 + 1 + 1 + 1 + 1)
+    assert C.sizeof(btrace.bt_trace_params) == 4 * (1 + 8 + 1 + 1 + 2 + 1 + 1 + 1 + 1 + 1 + 1)
     assert C.sizeof(btrace.bt_stats) == 8 * (14 + 3)
 
 
@@ -64,5 +64,9 @@ def test_null_arguments_are_rejected_without_a_gpu(libpath):
     assert L.bt_create(None, 0, None) == btrace.BT_E_INVALID
     assert L.bt_trace(None, 0, None) == btrace.BT_E_INVALID
     assert L.bt_set_result(None, 0, None, None) == btrace.BT_E_INVALID
+    assert L.bt_batch_create(None, None, 0, None, None) == btrace.BT_E_INVALID
+    assert L.bt_batch_run(None) == btrace.BT_E_INVALID
+    assert L.bt_batch_stats(None, None) == btrace.BT_E_INVALID
+    assert L.bt_batch_destroy(None) == btrace.BT_OK
     assert L.bt_last_error(None) == b"null context"
     assert btrace.bt_kernel_launches() == 0
