@@ -45,8 +45,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="district", choices=["district", "tiny", "batch"],
-                    help="batch: 64 cities of uneven size traced as one batch (CUDA graph)")
+    ap.add_argument("--workload", default="district", choices=["district", "tiny", "batch", "serve"],
+                    help="batch: 64 cities of uneven size traced as one batch (CUDA graph); "
+                         "serve: Poisson query streams against 8 resident cities")
+    ap.add_argument("--rates", default="50,200,1000,2000", help="serve: arrival rates, queries/s")
+    ap.add_argument("--queries", type=int, default=200, help="serve: queries per rate")
     ap.add_argument("--autotune", action="store_true",
                     help="batch: tune blocks per SM and lineages per launch on 16 of the cities first")
     ap.add_argument("--sources", type=int, default=None, help="override the source count")
@@ -346,6 +349,54 @@ def run_batch(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------------ serving
+def run_serve(args):
+    """Poisson streams of traffic-noise queries against 8 resident cities,
+    served by the continuous-batching loop and, on the same stream, one query
+    at a time (plain whole-query traces)."""
+    import torch
+    from paper_1912_03998_gb300 import btrace, serve, synth
+    torch.cuda.set_device(0)
+    prec = {"mixed": btrace.BT_PREC_MIXED, "fp32": btrace.BT_PREC_FP32, "fp64": btrace.BT_PREC_FP64}[args.precision]
+    cities = synth.serving_cities(seed=5, n=8)
+    tr = btrace.Tracer(0)
+    rows = []
+    with Clocks(0) as clk:
+        for k, rate in enumerate(float(r) for r in args.rates.split(",")):
+            qs = synth.serving_queries(seed=100 + k, n_queries=args.queries, n_cities=len(cities), rate_qps=rate)
+            # warm-up: a few queries through both paths
+            srv = serve.Server(tr, cities, precision=prec)
+            srv.run(qs[:4], realtime=False)
+            serve.run_plain(tr, srv.city_ids, qs[:4], precision=prec, realtime=False)
+            n0 = btrace.bt_kernel_launches()
+            t0 = time.perf_counter()
+            done = srv.run(qs, realtime=True)
+            wall = time.perf_counter() - t0
+            launches = btrace.bt_kernel_launches() - n0
+            segs = srv.segments
+            t0 = time.perf_counter()
+            plain = serve.run_plain(tr, srv.city_ids, qs, precision=prec, realtime=True)
+            wall_p = time.perf_counter() - t0
+            srv.close()
+            rows.append({"rate_qps": rate, "served": serve.latency_summary(done, wall),
+                         "plain": serve.latency_summary(plain, wall_p), "steps": srv.steps,
+                         "segments_per_s": segs / wall, "gpu_launches": launches,
+                         "sources_mean": float(np.mean([len(q.src) for q in qs])),
+                         "microphones_mean": float(np.mean([len(q.mics) for q in qs]))})
+    tr.close()
+    head = rows[-1]
+    line = {"metric": "served p50/p99 latency and queries/s", "value": head["served"]["queries_per_s"],
+            "unit": "queries/s", "n_gpus": 1, "steps": len(rows), "warmup": 4,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": "serve: Poisson streams against 8 resident cities of 500-5,000 buildings; "
+                                   "queries of 1-2,000 sources (0.001-1 W per band), 1k-250k microphones, "
+                                   "L=4, K 3-6", "queries_per_rate": args.queries,
+                       "precision": args.precision, "parallelism": "1 GPU"},
+            "clocks": clk.summary(), "rates": rows}
+    print(json.dumps(line))
+
+
 # ------------------------------------------------------------------ oracle
 def oracle_sample(w, seconds, threads, rng_seed=5):
     """Time the oracle on a seeded subset of sources sized to ~`seconds`."""
@@ -419,6 +470,10 @@ def main():
     if args.workload == "batch":
         if rank == 0:
             run_batch(args)
+        return
+    if args.workload == "serve":
+        if rank == 0:
+            run_serve(args)
         return
     if world > 1:
         import torch

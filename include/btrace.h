@@ -81,7 +81,8 @@ typedef struct {
                                                (Section 3); 1 x 1 = no split; max 32 x 32 */
   int32_t precision;                        /* BT_PREC_* */
   int32_t watchdog_ms;                      /* bound on any device-side wait; default 2000 */
-  int32_t chunk_beams;                      /* beam lineages per launch batch; 0 = automatic */
+  int32_t chunk_beams;                      /* beam lineages per persistent launch; 0 = automatic
+                                               (segment records of at most 8 GiB) */
   int32_t count_work;                       /* 1: also count BVH nodes visited and triangles
                                                tested (slower; for roofline accounting) */
   int32_t blocks_per_sm;                    /* resident blocks per SM of the persistent trace
@@ -156,7 +157,8 @@ int bt_set_sources(bt_ctx *ctx, int32_t scene_id, const float *pos, const float 
 
 /* Microphones of a scene (Section 4: a regular grid of receivers).
  *   pos [n_m][3] float32.  They are binned on the device into an xy cell grid
- *   (Section 3: microphones are partitioned with the geometry). */
+ *   (Section 3: microphones are partitioned with the geometry).  The scene's
+ *   accumulated result starts at zero. */
 int bt_set_microphones(bt_ctx *ctx, int32_t scene_id, const float *pos, int64_t n_m);
 
 /* Trace every beam of every source of the scene (Section 2, hybrid method)
@@ -255,6 +257,27 @@ int bt_batch_run(bt_batch *batch);
  * the device time of the whole run. */
 int bt_batch_stats(const bt_batch *batch, bt_stats *stats);
 int bt_batch_destroy(bt_batch *batch);
+
+/* A new scene that shares the geometry (triangles, BVH, materials) of a
+ * loaded scene without copying it, for its own sources and microphones: one
+ * resident city serves many queries.  The base scene cannot be unloaded
+ * while shares remain (BT_E_STATE); unloading a share frees only its own
+ * buffers. */
+int bt_scene_share(bt_ctx *ctx, int32_t base_scene_id, int32_t *scene_id_out);
+
+/* Trace part of the lineages of several scenes together: for scene i the
+ * lineages lineage_begin[i] .. lineage_end[i]-1, numbered source-major
+ * (lineage = source * 20 * 4^L + beam), all in the same persistent launches
+ * (each lane on its own lineage's scene; Section 2's method for every
+ * scene).  With BT_ACCUMULATE the contributions are added to each scene's
+ * current result instead of replacing it, so a scene's lineages can be
+ * traced over several calls -- the step of a continuous-batching server.
+ * params[i] as for bt_trace (tiles 1x1; precision, blocks_per_sm and
+ * count_work must agree).  Synchronous; totals with bt_ranges_stats. */
+#define BT_ACCUMULATE 1
+int bt_trace_ranges(bt_ctx *ctx, int32_t n, const int32_t *scene_ids, const int64_t *lineage_begin,
+                    const int64_t *lineage_end, const bt_trace_params *params, int32_t flags);
+int bt_ranges_stats(const bt_ctx *ctx, bt_stats *stats);
 
 /* Message of the last error of the context ("" if none).  Valid until the
  * next call on the context. */

@@ -21,8 +21,9 @@ from . import btrace
 
 
 def _chunk_candidates(max_order: int):
+    # 0: the library's default, segment records of up to 8 GiB per launch
     per = max_order + 1
-    return [0, (1 << 21) // per, (1 << 22) // per, (1 << 24) // per]
+    return [0, (1 << 22) // per, (1 << 24) // per]
 
 
 def tune_batch(tracer, scene_ids, params, blocks=(0, 4, 5), chunks=None, repeats=2):

@@ -58,7 +58,8 @@ EXPECTED_SYMBOLS = ("bt_params_default", "bt_create", "bt_destroy", "bt_load_sce
                     "bt_unload_scene", "bt_set_sources", "bt_set_microphones", "bt_trace",
                     "bt_read_levels", "bt_last_error", "bt_kernel_launches", "bt_cast_rays",
                     "bt_trace_noalloc", "bt_set_result", "bt_batch_create", "bt_batch_run",
-                    "bt_batch_stats", "bt_batch_destroy")
+                    "bt_batch_stats", "bt_batch_destroy", "bt_scene_share", "bt_trace_ranges",
+                    "bt_ranges_stats")
 
 
 def lib_path() -> str:
@@ -93,6 +94,9 @@ def lib():
             L.bt_batch_run.argtypes = [p]
             L.bt_batch_stats.argtypes = [p, C.POINTER(bt_stats)]
             L.bt_batch_destroy.argtypes = [p]
+            L.bt_scene_share.argtypes = [p, i32, C.POINTER(C.c_int32)]
+            L.bt_trace_ranges.argtypes = [p, i32, p, p, p, C.POINTER(bt_trace_params), i32]
+            L.bt_ranges_stats.argtypes = [p, C.POINTER(bt_stats)]
             L.bt_kernel_launches.argtypes = []
             L.bt_kernel_launches.restype = C.c_int64
             for name in EXPECTED_SYMBOLS:
@@ -244,6 +248,35 @@ def bt_batch_destroy(batch):
     lib().bt_batch_destroy(batch)
 
 
+BT_ACCUMULATE = 1
+
+
+def bt_scene_share(ctx, base_scene_id: int) -> int:
+    """New scene on the geometry of a loaded one (no copy)."""
+    out = C.c_int32(-1)
+    _check(lib().bt_scene_share(ctx, int(base_scene_id), C.byref(out)), ctx)
+    return out.value
+
+
+def bt_trace_ranges(ctx, scene_ids, begins, ends, params, accumulate=False):
+    """Trace lineages [begins[i], ends[i]) of scene scene_ids[i], all scenes
+    in the same launches."""
+    n = len(scene_ids)
+    ids = np.ascontiguousarray(scene_ids, np.int32)
+    b = np.ascontiguousarray(begins, np.int64)
+    e = np.ascontiguousarray(ends, np.int64)
+    arr = (bt_trace_params * max(1, n))(*params)
+    rc = lib().bt_trace_ranges(ctx, n, ids.ctypes.data_as(C.c_void_p), b.ctypes.data_as(C.c_void_p),
+                               e.ctypes.data_as(C.c_void_p), arr, BT_ACCUMULATE if accumulate else 0)
+    _check(rc, ctx)
+
+
+def bt_ranges_stats(ctx) -> dict:
+    st = bt_stats()
+    _check(lib().bt_ranges_stats(ctx, C.byref(st)), ctx)
+    return st.as_dict()
+
+
 def bt_cast_rays(ctx, scene_id: int, origins, dirs, start_normals=None, t_eps_m: float = 1e-3):
     """Closest hit per ray: (t [n] float32, triangle index [n] int32)."""
     po, n, ko = _arr(origins, np.float32)
@@ -280,6 +313,10 @@ class Tracer:
             self.close()
         except Exception:
             pass
+
+    def load_geometry(self, w) -> int:
+        """Load only the city model of workload-like `w` (a resident scene)."""
+        return bt_load_scene(self.ctx, w.scene.verts, w.scene.tris, w.scene.mat, w.scene.refl)
 
     def load(self, w) -> int:
         sid = bt_load_scene(self.ctx, w.scene.verts, w.scene.tris, w.scene.mat, w.scene.refl)

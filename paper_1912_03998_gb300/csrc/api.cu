@@ -55,6 +55,8 @@ struct SceneState {
   bool traced = false;
   bt_stats stats;
   unsigned long long gen = 0;  // changes whenever the scene's buffers may change (batches check it)
+  int geom_of = -1;            // >= 0: the geometry buffers belong to that scene (bt_scene_share)
+  int n_shares = 0;            // scenes sharing this scene's geometry
   DevBuf out_level, out_int, out_cnt;
 };
 
@@ -83,6 +85,9 @@ struct bt_ctx {
   DevBuf t_ring, t_seq, t_qctl;  // sub-domain trace: queue slots, slot sequence words, queue counters
   unsigned long long gen_counter = 0;
   std::vector<bt_batch *> batches;  // live batches, freed with the context
+  DevBuf views;                     // scene views of the last bt_trace_ranges
+  DevBuf level_tables[9];           // float-pair beam tables per icosahedron level (bt_trace_ranges)
+  bt_stats range_stats;             // totals of the last bt_trace_ranges
 };
 
 namespace {
@@ -161,11 +166,18 @@ void release(DevBuf &b) {
 
 // Scene buffers go back to the context's pool (freed by bt_destroy).
 void release_scene(bt_ctx *c, SceneState &s) {
-  DevBuf *all[] = {&s.t_nodes, &s.t_tris, &s.t_planes, &s.t_planes64, &s.t_planes_df, &s.t_roots,
-                   &s.nodes, &s.tris, &s.planes, &s.planes64, &s.planes_df, &s.refl, &s.src, &s.power, &s.mics, &s.cell_start,
-                   &s.grid, &s.energy, &s.count, &s.out_level, &s.out_int, &s.out_cnt};
-  for (DevBuf *b : all)
+  DevBuf *own[] = {&s.t_nodes, &s.t_tris, &s.t_planes, &s.t_planes64, &s.t_planes_df, &s.t_roots, &s.src,
+                   &s.power, &s.mics, &s.cell_start, &s.grid, &s.energy, &s.count, &s.out_level, &s.out_int,
+                   &s.out_cnt};
+  DevBuf *geom[] = {&s.nodes, &s.tris, &s.planes, &s.planes64, &s.planes_df, &s.refl};
+  for (DevBuf *b : own)
     if (b->p) c->pool.push_back(*b);
+  if (s.geom_of >= 0) {
+    c->sc[s.geom_of].n_shares--;  // the geometry stays with its owner
+  } else {
+    for (DevBuf *b : geom)
+      if (b->p) c->pool.push_back(*b);
+  }
   s = SceneState();
 }
 
@@ -351,6 +363,8 @@ BT_API int bt_destroy(bt_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (bt_batch *b : c->batches) free_batch(b);
   c->batches.clear();
+  release(c->views);
+  for (DevBuf &t : c->level_tables) release(t);
   for (auto &s : c->sc) release_scene(c, s);
   for (DevBuf &q : c->pool) release(q);
   c->pool.clear();
@@ -473,10 +487,47 @@ BT_API int bt_unload_scene(bt_ctx *c, int32_t scene_id) {
   TRY(check_ctx(c));
   SceneState *s;
   TRY(scene_ref(c, scene_id, &s));
+  if (s->n_shares > 0)
+    return fail(c, BT_E_STATE, "scene %d: %d scenes still share its geometry", scene_id, s->n_shares);
   DeviceGuard g(c->device);
   cudaStreamSynchronize(c->stream);
   release_scene(c, *s);
   s->gen = ++c->gen_counter;
+  return BT_OK;
+}
+
+BT_API int bt_scene_share(bt_ctx *c, int32_t base_id, int32_t *scene_id_out) {
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  SceneState *b;
+  TRY(scene_ref(c, base_id, &b));
+  if (!scene_id_out) return fail(c, BT_E_INVALID, "NULL scene id output");
+  if (b->geom_of >= 0) return fail(c, BT_E_INVALID, "scene %d itself shares another scene's geometry", base_id);
+  int id = -1;
+  for (int i = 0; i < BT_MAX_SCENES; i++)
+    if (!c->sc[i].used) {
+      id = i;
+      break;
+    }
+  if (id < 0) return fail(c, BT_E_NOMEM, "all %d scene slots are in use", BT_MAX_SCENES);
+  SceneState &s = c->sc[id];
+  s = SceneState();
+  s.used = true;
+  s.n_tris = b->n_tris;
+  s.n_mat = b->n_mat;
+  s.n_bands = b->n_bands;
+  s.root = b->root;
+  for (int q = 0; q < 6; q++) s.box[q] = b->box[q];
+  s.nodes = b->nodes;
+  s.tris = b->tris;
+  s.planes = b->planes;
+  s.planes64 = b->planes64;
+  s.planes_df = b->planes_df;
+  s.refl = b->refl;
+  s.geom_of = base_id;
+  s.gen = ++c->gen_counter;
+  b->n_shares++;
+  *scene_id_out = id;
   return BT_OK;
 }
 
@@ -538,6 +589,9 @@ BT_API int bt_set_microphones(bt_ctx *c, int32_t scene_id, const float *pos, int
   TRY(ensure(c, s->grid, sizeof(bt::MicGrid)));
   TRY(ensure(c, s->energy, sizeof(double) * bt::kMaxBands * (size_t)n_m));
   TRY(ensure(c, s->count, sizeof(int) * (size_t)n_m));
+  // the result accumulators start at zero (bt_trace_ranges may add to them)
+  CK(cudaMemsetAsync(s->energy.p, 0, sizeof(double) * bt::kMaxBands * (size_t)n_m, c->stream));
+  CK(cudaMemsetAsync(s->count.p, 0, sizeof(int) * (size_t)n_m, c->stream));
   TRY(reset_counters(c));
   if (n_m > 0) CK(cudaMemcpyAsync(c->stage_a.p, pos, sizeof(float) * 3 * n_m, cudaMemcpyDefault, st));
   CK(bt::build_mics(st, (const float *)c->stage_a.p, n_m, side, (bt::MicGrid *)s->grid.p,
@@ -581,6 +635,12 @@ static void fill_view(bt::SceneView &v, SceneState &s, const bt_trace_params *p,
   v.count = (int *)s.count.p;
 }
 
+// Lineages per persistent launch when the caller leaves it to the library:
+// segment records of at most 8 GiB.
+static int64_t default_chunk(int max_order) {
+  return ((int64_t)8 << 30) / ((int64_t)sizeof(bt::Seg) * (max_order + 1));
+}
+
 // Check the trace parameters p for scene s; derive the air damping exponents.
 static int check_params(bt_ctx *c, SceneState *s, const bt_trace_params *p, float *alpha_log2, int *has_alpha) {
   if (!p) return fail(c, BT_E_INVALID, "NULL params");
@@ -621,13 +681,10 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   const int64_t total = s->n_src * n_beams;
   const bool tiled = p->tiles_x * p->tiles_y > 1;
   const int T = p->tiles_x * p->tiles_y;
-  int64_t chunk = p->chunk_beams > 0 ? p->chunk_beams : ((int64_t)1 << 23) / (p->max_order + 1);
-  if (tiled && p->chunk_beams <= 0) {
-    // One persistent launch per batch: fewer, larger batches mean fewer
-    // launch tails.  The segment records of a batch are kept near 8 GiB, a
-    // small part of the device.
-    chunk = ((int64_t)8 << 30) / ((int64_t)sizeof(bt::Seg) * (p->max_order + 1));
-  }
+  // One persistent launch per group of lineages: fewer, larger groups mean
+  // fewer launch tails.  The segment records of a group are kept near 8 GiB,
+  // a small part of the device.
+  int64_t chunk = p->chunk_beams > 0 ? p->chunk_beams : default_chunk(p->max_order);
   if (chunk > total) chunk = total;
   if (chunk < 1) chunk = 1;
   const unsigned long long cap = (unsigned long long)chunk * (p->max_order + 1);
@@ -930,7 +987,7 @@ BT_API int bt_batch_create(bt_ctx *c, const int32_t *scene_ids, int32_t n_scenes
       }
     }
     if (rc) break;
-    int64_t chunk = params[0].chunk_beams > 0 ? params[0].chunk_beams : ((int64_t)1 << 23) / (b->max_order + 1);
+    int64_t chunk = params[0].chunk_beams > 0 ? params[0].chunk_beams : default_chunk(b->max_order);
     if (chunk > b->total) chunk = b->total;
     if (chunk < 1) chunk = 1;
     b->chunk = chunk;
@@ -1088,6 +1145,133 @@ BT_API int bt_batch_destroy(bt_batch *b) {
       break;
     }
   free_batch(b);
+  return BT_OK;
+}
+
+BT_API int bt_trace_ranges(bt_ctx *c, int32_t n, const int32_t *scene_ids, const int64_t *lineage_begin,
+                           const int64_t *lineage_end, const bt_trace_params *params, int32_t flags) {
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  if (n < 0 || n > BT_MAX_SCENES) return fail(c, BT_E_INVALID, "n must be in 0..%d", BT_MAX_SCENES);
+  if (n > 0 && (!scene_ids || !lineage_begin || !lineage_end || !params))
+    return fail(c, BT_E_INVALID, "NULL argument");
+  if (flags & ~BT_ACCUMULATE) return fail(c, BT_E_INVALID, "unknown flags 0x%x", flags);
+  memset(&c->range_stats, 0, sizeof(c->range_stats));
+  if (n == 0) return BT_OK;
+  std::vector<bt::SceneView> hv((size_t)n);
+  const int prec = params[0].precision;
+  int kmax = 0;
+  int64_t total = 0;
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  for (int i = 0; i < n; i++) {
+    SceneState *s;
+    TRY(scene_ref(c, scene_ids[i], &s));
+    for (int j = 0; j < i; j++)
+      if (scene_ids[j] == scene_ids[i]) return fail(c, BT_E_INVALID, "scene %d listed twice", scene_ids[i]);
+    const bt_trace_params *p = &params[i];
+    float alpha_log2[BT_MAX_BANDS];
+    int has_alpha = 0;
+    TRY(check_params(c, s, p, alpha_log2, &has_alpha));
+    if (p->tiles_x != 1 || p->tiles_y != 1) return fail(c, BT_E_INVALID, "bt_trace_ranges traces unsplit (tiles 1x1)");
+    if (p->precision != prec || p->blocks_per_sm != params[0].blocks_per_sm || p->count_work != params[0].count_work)
+      return fail(c, BT_E_INVALID, "precision, blocks_per_sm and count_work must agree across the scenes");
+    const int64_t nl = s->n_src * ((int64_t)20 << (2 * s->level));
+    if (lineage_begin[i] < 0 || lineage_end[i] < lineage_begin[i] || lineage_end[i] > nl)
+      return fail(c, BT_E_INVALID, "scene %d: lineage range [%lld, %lld) outside [0, %lld)", scene_ids[i],
+                  (long long)lineage_begin[i], (long long)lineage_end[i], (long long)nl);
+    fill_view(hv[i], *s, p, alpha_log2, has_alpha);
+    hv[i].lineage_base = total;
+    hv[i].lineage_first = lineage_begin[i];
+    total += lineage_end[i] - lineage_begin[i];
+    if (p->max_order > kmax) kmax = p->max_order;
+    if (prec == BT_PREC_MIXED && nl > 0) {
+      DevBuf &t = c->level_tables[s->level];
+      if (!t.p) {
+        TRY(ensure(c, t, sizeof(float) * 24 * (size_t)((int64_t)20 << (2 * s->level))));
+        CK(bt::launch_beam_table(st, s->level, (float *)t.p));
+      }
+      hv[i].beam_table = (const float *)t.p;
+    }
+  }
+  int64_t chunk = params[0].chunk_beams > 0 ? params[0].chunk_beams : default_chunk(kmax);
+  if (chunk > total) chunk = total;
+  if (chunk < 1) chunk = 1;
+  const unsigned long long cap = (unsigned long long)chunk * (kmax + 1);
+  TRY(ensure(c, c->segs, sizeof(bt::Seg) * cap));
+  TRY(ensure(c, c->views, sizeof(bt::SceneView) * (size_t)n));
+  CK(cudaMemcpyAsync(c->views.p, hv.data(), sizeof(bt::SceneView) * (size_t)n, cudaMemcpyHostToDevice, st));
+  TRY(reset_counters(c));
+  for (int i = 0; i < n; i++) {
+    SceneState &s = c->sc[scene_ids[i]];
+    if (!(flags & BT_ACCUMULATE) && s.n_mics > 0) {
+      CK(cudaMemsetAsync(s.energy.p, 0, sizeof(double) * bt::kMaxBands * (size_t)s.n_mics, st));
+      CK(cudaMemsetAsync(s.count.p, 0, sizeof(int) * (size_t)s.n_mics, st));
+    }
+  }
+  bt::TraceArgs ta;
+  memset(&ta, 0, sizeof(ta));
+  ta.views = (const bt::SceneView *)c->views.p;
+  ta.n_views = n;
+  ta.segs = (bt::Seg *)c->segs.p;
+  ta.seg_count = c->d_seg_count;
+  ta.lineage_next = c->d_lineage_next;
+  ta.seg_capacity = cap;
+  ta.ctr = c->d_ctr;
+  ta.count_work = params[0].count_work ? 1 : 0;
+  ta.prec = prec;
+  ta.blocks_per_sm = params[0].blocks_per_sm;
+  bt::ScatterArgs sa;
+  memset(&sa, 0, sizeof(sa));
+  sa.views = ta.views;
+  sa.n_views = n;
+  sa.fp64 = prec == BT_PREC_FP64 ? 1 : 0;
+  sa.segs = ta.segs;
+  sa.seg_count = ta.seg_count;
+  sa.seg_capacity = cap;
+  sa.ctr = c->d_ctr;
+  CK(cudaEventRecord(c->ev0, st));
+  const int64_t n_chunks = total > 0 ? (total + chunk - 1) / chunk : 0;
+  for (int64_t ci = 0; ci < n_chunks; ci++) {
+    ta.lineage_begin = ci * chunk;
+    ta.lineage_end = ta.lineage_begin + chunk < total ? ta.lineage_begin + chunk : total;
+    CK(cudaMemsetAsync(c->d_seg_count, 0, sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(c->d_lineage_next, 0, sizeof(unsigned long long), st));
+    CK(bt::launch_trace(st, ta, c->n_sm));
+    CK(bt::launch_scatter(st, sa, c->n_sm));
+  }
+  CK(cudaEventRecord(c->ev1, st));
+  TRY(read_counters(c));
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  const bt::Counters &h = *c->h_ctr;
+  bt_stats &o = c->range_stats;
+  o.beams = total;
+  o.segments = (int64_t)h.segments;
+  o.hits = (int64_t)h.hits;
+  o.escapes = (int64_t)h.escapes;
+  o.emitted = (int64_t)h.emitted;
+  o.candidates = (int64_t)h.candidates;
+  o.contributions = (int64_t)h.contributions;
+  o.nodes_visited = (int64_t)h.nodes_visited;
+  o.tris_tested = (int64_t)h.tris_tested;
+  o.trace_launches = n_chunks;
+  o.scatter_launches = n_chunks;
+  o.trace_ms = ms;
+  for (int i = 0; i < n; i++) {
+    SceneState &s = c->sc[scene_ids[i]];
+    memset(&s.stats, 0, sizeof(s.stats));
+    s.traced = h.error == 0;
+  }
+  if (h.error)
+    return fail(c, h.error, h.error == BT_E_QUEUE_FULL ? "device queue or traversal stack overflow"
+                                                        : "device error %d", h.error);
+  return BT_OK;
+}
+
+BT_API int bt_ranges_stats(const bt_ctx *c, bt_stats *stats) {
+  if (!c || !stats) return BT_E_INVALID;
+  *stats = c->range_stats;
   return BT_OK;
 }
 

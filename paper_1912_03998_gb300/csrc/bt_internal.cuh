@@ -139,6 +139,7 @@ struct SceneView {
   int max_order;
   int64_t n_beams;        // 20 * 4^L
   int64_t lineage_base;   // batch: first lineage of this scene in the batch's lineage space
+  int64_t lineage_first;  // batch: the scene's own lineage index at lineage_base
   float t_eps;
   float energy_threshold;
   float alpha_log2[kMaxBands];  // air damping as a base-2 exponent per metre: -alpha_b * log2(10) / 10

@@ -177,12 +177,17 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, Ray
   best.id = 0x7fffffff;
   best.t64 = 0.0;
   best.has64 = false;
-  if (sc.n_tris == 0 || root == (int)0x80000000) return -1;
+  // the hot fields in registers: in a batch `sc` lives in device memory and
+  // would otherwise be re-read on every node
+  const int64_t n_tri = sc.n_tris;
+  const Node *const nodes = sc.nodes;
+  const Tri *const tris = sc.tris;
+  if (n_tri == 0 || root == (int)0x80000000) return -1;
   const int tile_x = tf ? tile % tf->tx : 0, tile_y = tf ? tile / tf->tx : 0;
   // candidate evaluation (one call site, so the code is emitted once)
   auto consider = [&](int slot) {
     if (kCount) n_tris++;
-    const Tri *tp = sc.tris + slot;
+    const Tri *tp = tris + slot;
     float4 v0 = __ldg(&tp->v0), v1 = __ldg(&tp->v1), v2 = __ldg(&tp->v2);
     float t;
     double t64 = 0.0;
@@ -270,11 +275,11 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, Ray
       nc = 1;
       more = false;
     } else {
-      if (++visits > sc.n_tris + 64) {
+      if (++visits > n_tri + 64) {
         atomicExch(err, BT_E_TIMEOUT);
         break;
       }
-      const Node *nd = sc.nodes + node;
+      const Node *nd = nodes + node;
       if (kCount) n_nodes++;
       float4 lxy = __ldg(&nd->lxy), rxy = __ldg(&nd->rxy), lrz = __ldg(&nd->lrz);
       int2 ch = __ldg((const int2 *)&nd->child);
@@ -675,13 +680,13 @@ __device__ __forceinline__ int64_t take_lineage(const TraceArgs &a, bool need) {
 // Persistent warps: every lane works on one lineage at a time and takes the
 // next one from a global counter as soon as its lineage ends, so a warp stays
 // full until the batch runs out (warp-vote refill of finished lanes).
-// Index of the view whose lineage range holds global lineage `g` (views in
-// lineage order).
-__device__ __forceinline__ int find_view(const TraceArgs &a, int64_t g) {
-  int lo = 0, hi = a.n_views - 1;
+// Index of the view whose lineage range holds global lineage `g`; `base`
+// holds the views' first lineages in order (a shared-memory copy).
+__device__ __forceinline__ int find_view(const int64_t *base, int n_views, int64_t g) {
+  int lo = 0, hi = n_views - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    if (a.views[mid].lineage_base <= g) lo = mid;
+    if (base[mid] <= g) lo = mid;
     else hi = mid - 1;
   }
   return lo;
@@ -695,7 +700,12 @@ template <int kP, bool kCount, bool kBatch>
 __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
   [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   __shared__ LineageSmem<kP> sm;
+  __shared__ int64_t view_base[kBatch ? BT_MAX_SCENES : 1];
   const int t = threadIdx.x;
+  if (kBatch) {
+    for (int i = t; i < a.n_views; i += kTraceThreads) view_base[i] = a.views[i].lineage_base;
+    __syncthreads();
+  }
   const TraceCounts cn = init_counts(sm, t);
   LaneState ls = {-1, 0, -1, 0.0f, 0.0};
   int vi = 0;  // this lane's scene view
@@ -708,8 +718,8 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
     if (need) {
       if (mine >= 0) {
         if (kBatch) {
-          vi = find_view(a, mine);
-          mine -= a.views[vi].lineage_base;
+          vi = find_view(view_base, a.n_views, mine);
+          mine += a.views[vi].lineage_first - view_base[vi];
         }
         ls = LaneState{mine, 0, -1, 0.0f, 0.0};
         init_lineage(kBatch ? a.views[vi] : a.v, sm, t, mine);
@@ -1211,7 +1221,7 @@ constexpr int kScatterWarps = 4;
 enum : int {
   F_AX = 0, F_RX = 3, F_N0 = 6, F_NLO = 15, F_NS = 24, F_NE = 28, F_P = 32, F_SLOTS = 40,
   F_CY0 = 42, F_PN = 43, F_PX = 44, F_PY = F_PX + kPolyMax, F_AP = F_PY + kPolyMax, F_VI = F_AP + 3,
-  F_COUNT = F_VI + 1
+  F_MP = F_VI + 1, F_COUNT = F_MP + 2
 };
 struct ScatterSmem {
   float f[kScatterWarps][F_COUNT][32];
@@ -1289,6 +1299,12 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
       const int vi = kBatch ? sl.view : 0;
       const MicGrid &g = *(kBatch ? a.views[vi] : a.v).grid;
       F[F_VI][lane] = __int_as_float(vi);
+      if (kBatch) {
+        // the view's microphone array, read for every candidate
+        const unsigned long long mp = (unsigned long long)a.views[vi].mics;
+        F[F_MP][lane] = __uint_as_float((unsigned)mp);
+        F[F_MP + 1][lane] = __uint_as_float((unsigned)(mp >> 32));
+      }
       Poly p;
       int cy0 = 0, cy1 = -1;
       if (seg_footprint(sl, g, p)) {
@@ -1378,8 +1394,10 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
         if (c < total_c) {
           int mi = ofirst + (c - oexcl);
           const SceneView &V = kBatch ? a.views[__float_as_int(F[F_VI][s])] : a.v;
-          const int nb = V.sc.n_bands;
-          float4 m = __ldg(&V.mics[mi]);
+          const float4 *mics = kBatch ? (const float4 *)((unsigned long long)__float_as_uint(F[F_MP][s]) |
+                                                         ((unsigned long long)__float_as_uint(F[F_MP + 1][s]) << 32))
+                                      : a.v.mics;
+          float4 m = __ldg(&mics[mi]);
           if (kF64) {
             // FP64: every test and the contribution in float64 (apex exact
             // from its three words, cone normals from their float pairs,
@@ -1412,7 +1430,7 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
               double *e = V.energy + (size_t)mi * kMaxBands;
 #pragma unroll
               for (int b = 0; b < kMaxBands; b++) {
-                if (b < nb) {
+                if (b < V.sc.n_bands) {
                   double cval = (double)F[F_P + b][s] * gf;
                   if (V.has_alpha) cval *= exp2((double)V.alpha_log2[b] * dist);
                   atomicAdd(e + b, cval);
@@ -1463,7 +1481,7 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
             double *e = V.energy + (size_t)mi * kMaxBands;
 #pragma unroll
             for (int b = 0; b < kMaxBands; b++) {
-              if (b < nb) {
+              if (b < V.sc.n_bands) {
                 float cval = F[F_P + b][s] * gf;
                 if (V.has_alpha) cval *= exp2f(V.alpha_log2[b] * dist);
                 atomicAdd(e + b, (double)cval);

@@ -1,0 +1,196 @@
+"""Continuous-batching server for traffic-noise queries against resident
+cities.
+
+The cities' geometry and BVHs stay on the device; every query (a set of car
+sources with band powers, a microphone set, a reflection order) gets a scene
+that shares its city's geometry (bt_scene_share) for its own sources,
+microphones and result.  The server runs in steps.  Before a step it admits
+waiting queries in arrival order while a scene slot is free and their device
+memory fits the budget; a step then traces the next lineages of every
+admitted query -- an equal share of the step's lineage budget each, at most
+what the query has left -- in the same persistent launches
+(bt_trace_ranges, accumulating), so queries that arrive while others are on
+the GPU join at the next step and their work overlaps on the device.  A query
+whose lineages are all traced is read back (levels to the host), its scene
+freed, and its latency (completion - arrival) recorded.
+
+`run_plain` serves the same stream one query at a time with whole-query
+traces (bt_trace), the baseline the server is compared with.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import btrace
+
+# device bytes of a query's own state: sources (xyz + 8 powers), microphones
+# (sorted positions, cell ids, grid), accumulators (8 float64 + count) and the
+# read-back buffers (levels, intensity, count)
+BYTES_PER_SOURCE = 16 + 4 * 8
+BYTES_PER_MIC = 16 + 8 + 8 * 8 + 4 + 8 * 8 * 2 + 4
+
+
+def query_bytes(q) -> int:
+    return len(q.src) * BYTES_PER_SOURCE + len(q.mics) * BYTES_PER_MIC + (1 << 16)
+
+
+@dataclass
+class Done:
+    index: int
+    arrival_s: float
+    admitted_s: float
+    done_s: float
+    level: np.ndarray = field(repr=False)
+    count: np.ndarray = field(repr=False)
+
+    @property
+    def latency_s(self) -> float:
+        return self.done_s - self.arrival_s
+
+
+class Server:
+    def __init__(self, tracer, cities, step_lineages: int = 1 << 22, mem_budget: int = 4 << 30,
+                 max_active: int = 48, precision: int = btrace.BT_PREC_MIXED):
+        self.tr = tracer
+        self.city_ids = [tracer.load_geometry(w) for w in cities]
+        self.step_lineages = int(step_lineages)
+        self.mem_budget = int(mem_budget)
+        self.max_active = int(max_active)
+        self.precision = precision
+        self.waiting = collections.deque()
+        self.active = []
+        self.mem_used = 0
+        self.done = []
+        self.steps = 0
+        self.segments = 0
+        self.t0 = time.perf_counter()
+
+    def now(self) -> float:
+        return time.perf_counter() - self.t0
+
+    def submit(self, index: int, q, arrival_s: float):
+        self.waiting.append((index, q, arrival_s))
+
+    def _admit(self):
+        while self.waiting and len(self.active) < self.max_active:
+            index, q, arrival = self.waiting[0]
+            need = query_bytes(q)
+            if self.active and self.mem_used + need > self.mem_budget:
+                break  # wait for memory; a lone query is always admitted
+            self.waiting.popleft()
+            ctx = self.tr.ctx
+            sid = btrace.bt_scene_share(ctx, self.city_ids[q.city])
+            btrace.bt_set_sources(ctx, sid, q.src, q.power, q.level)
+            btrace.bt_set_microphones(ctx, sid, q.mics)
+            p = self.tr.params(q.max_order, precision=self.precision)
+            total = len(q.src) * 20 * 4 ** q.level
+            self.active.append(dict(index=index, q=q, sid=sid, p=p, next=0, total=total, mem=need,
+                                    arrival=arrival, admitted=self.now()))
+            self.mem_used += need
+
+    def step(self) -> bool:
+        """Admit, trace one step, retire finished queries.  False when idle."""
+        self._admit()
+        if not self.active:
+            return False
+        # an equal share of the step's lineages for every active query,
+        # what a query does not need passed on to the others
+        left = [a["total"] - a["next"] for a in self.active]
+        share = [0] * len(left)
+        budget = self.step_lineages
+        open_ = [i for i, r in enumerate(left) if r > 0]
+        while budget > 0 and open_:
+            per = max(1, budget // len(open_))
+            nxt = []
+            for i in open_:
+                g = min(per, left[i] - share[i], budget)
+                share[i] += g
+                budget -= g
+                if share[i] < left[i]:
+                    nxt.append(i)
+                if budget == 0:
+                    break
+            open_ = nxt
+        ids, begins, ends, params = [], [], [], []
+        for a, s in zip(self.active, share):
+            if s > 0:
+                ids.append(a["sid"])
+                begins.append(a["next"])
+                ends.append(a["next"] + s)
+                params.append(a["p"])
+                a["next"] += s
+        if ids:
+            btrace.bt_trace_ranges(self.tr.ctx, ids, begins, ends, params, accumulate=True)
+            self.segments += btrace.bt_ranges_stats(self.tr.ctx)["segments"]
+        self.steps += 1
+        still = []
+        for a in self.active:
+            if a["next"] < a["total"]:
+                still.append(a)
+                continue
+            q = a["q"]
+            n, nb = len(q.mics), q.power.shape[1]
+            level = np.empty((n, nb), np.float64)
+            count = np.empty(n, np.int32)
+            btrace.bt_read_levels(self.tr.ctx, a["sid"], level, None, count)
+            btrace.bt_unload_scene(self.tr.ctx, a["sid"])
+            self.mem_used -= a["mem"]
+            self.done.append(Done(a["index"], a["arrival"], a["admitted"], self.now(), level, count))
+        self.active = still
+        return True
+
+    def run(self, queries, realtime: bool = True):
+        """Serve `queries` (arrival_s from the start of the run).  With
+        realtime, a query is submitted once its arrival time has passed;
+        otherwise all are submitted at once.  Returns the Done records in
+        query order."""
+        self.t0 = time.perf_counter()
+        i = 0
+        while i < len(queries) or self.waiting or self.active:
+            now = self.now()
+            while i < len(queries) and (not realtime or queries[i].arrival_s <= now):
+                self.submit(i, queries[i], queries[i].arrival_s if realtime else 0.0)
+                i += 1
+            if not self.step() and i < len(queries):
+                time.sleep(max(0.0, min(1e-3, queries[i].arrival_s - self.now())))
+        return sorted(self.done, key=lambda d: d.index)
+
+    def close(self):
+        for cid in self.city_ids:
+            btrace.bt_unload_scene(self.tr.ctx, cid)
+        self.city_ids = []
+
+
+def run_plain(tracer, city_ids, queries, precision: int = btrace.BT_PREC_MIXED, realtime: bool = True):
+    """The same stream served one query at a time, each traced whole."""
+    ctx = tracer.ctx
+    t0 = time.perf_counter()
+    done = []
+    for i, q in enumerate(queries):
+        if realtime:
+            wait = q.arrival_s - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+        start = time.perf_counter() - t0
+        sid = btrace.bt_scene_share(ctx, city_ids[q.city])
+        btrace.bt_set_sources(ctx, sid, q.src, q.power, q.level)
+        btrace.bt_set_microphones(ctx, sid, q.mics)
+        btrace.bt_trace(ctx, sid, tracer.params(q.max_order, precision=precision))
+        n, nb = len(q.mics), q.power.shape[1]
+        level = np.empty((n, nb), np.float64)
+        count = np.empty(n, np.int32)
+        btrace.bt_read_levels(ctx, sid, level, None, count)
+        btrace.bt_unload_scene(ctx, sid)
+        done.append(Done(i, q.arrival_s if realtime else 0.0, start, time.perf_counter() - t0, level, count))
+    return done
+
+
+def latency_summary(done, wall_s: float) -> dict:
+    lat = np.array([d.latency_s for d in done])
+    return {"queries": len(done), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+            "queries_per_s": len(done) / wall_s}

@@ -294,6 +294,22 @@ def _footprint(rng, lot):
     return pts, _polygon_area(pts)
 
 
+def _lane_sources(rng, n_sources, log10_p_lo, log10_p_hi):
+    """Car sources on lane centres of the district road grid (two 5 m lanes
+    per 10 m road, centres at +-2.5 m) at 0.5 m, with per-band power
+    log-uniform in [10^lo, 10^hi] W."""
+    horiz = rng.random(n_sources) < 0.5
+    road = rng.integers(0, DIST_NBLK + 1, size=n_sources)
+    lane = np.where(rng.random(n_sources) < 0.5, -2.5, 2.5)
+    along = rng.uniform(0.0, DIST_EXTENT, size=n_sources)
+    across = DIST_PITCH * road + 0.5 * DIST_ROAD + lane
+    sx = np.where(horiz, along, across)
+    sy = np.where(horiz, across, along)
+    src = np.stack([sx, sy, np.full(n_sources, 0.5)], axis=1).astype(np.float32)
+    power = (10.0 ** rng.uniform(log10_p_lo, log10_p_hi, size=(n_sources, N_BANDS))).astype(np.float32)
+    return src, power
+
+
 def district(seed: int = 2, n_buildings: int = 5000, n_sources: int = 1000, level: int = 5,
              max_order: int = 6, n_mic_side: int = 500, tiles=(4, 4), band_h=15.0) -> Workload:
     """2 km x 2 km district of extruded convex buildings on a Manhattan road grid."""
@@ -336,16 +352,7 @@ def district(seed: int = 2, n_buildings: int = 5000, n_sources: int = 1000, leve
             "height_quantiles": np.quantile(heights, [0.1, 0.5, 0.9, 0.999]).tolist(),
             "height_max": float(np.max(heights)), "ngon_mean": float(np.mean(ngons))}
     scene = mb.scene(refl_table(), info)
-    # sources on lane centres: two 5 m lanes per 10 m road, centres at +-2.5 m
-    horiz = rng.random(n_sources) < 0.5
-    road = rng.integers(0, DIST_NBLK + 1, size=n_sources)
-    lane = np.where(rng.random(n_sources) < 0.5, -2.5, 2.5)
-    along = rng.uniform(0.0, DIST_EXTENT, size=n_sources)
-    across = DIST_PITCH * road + 0.5 * DIST_ROAD + lane
-    sx = np.where(horiz, along, across)
-    sy = np.where(horiz, across, along)
-    src = np.stack([sx, sy, np.full(n_sources, 0.5)], axis=1).astype(np.float32)
-    power = (10.0 ** rng.uniform(-2.0, 0.0, size=(n_sources, N_BANDS))).astype(np.float32)
+    src, power = _lane_sources(rng, n_sources, -2.0, 0.0)
     mics = mic_grid(0.0, 0.0, DIST_MIC_SIDE, DIST_MIC_SIDE, n_mic_side, n_mic_side, 1.5)
     return Workload("district", scene, src, power, mics, level, max_order, tuple(tiles),
                     {"seed": seed, **info})
@@ -371,4 +378,56 @@ def batch_cities(seed: int = 4, n: int = 64):
                      n_mic_side=side, tiles=(1, 1))
         w.name = f"city{i}"
         out.append(w)
+    return out
+
+
+def serving_cities(seed: int = 5, n: int = 8):
+    """Resident cities for the serving loop: drawn like the district with
+    500-5,000 buildings (log-uniform); their sources and microphones come with
+    the queries."""
+    rng = _rng(seed)
+    out = []
+    for i in range(n):
+        n_b = int(round(math.exp(rng.uniform(math.log(500), math.log(5000)))))
+        w = district(seed=seed * 1000 + i, n_buildings=n_b, n_sources=1, level=4, max_order=3, n_mic_side=2,
+                     tiles=(1, 1))
+        w.name = f"resident{i}"
+        out.append(w)
+    return out
+
+
+@dataclass
+class Query:
+    """One traffic-noise query against a resident city."""
+    arrival_s: float
+    city: int
+    src: np.ndarray
+    power: np.ndarray
+    mics: np.ndarray
+    level: int
+    max_order: int
+
+
+def serving_queries(seed: int, n_queries: int, n_cities: int, rate_qps: float, level: int = 4,
+                    max_sources: int = 2000, max_mics: int = 250000):
+    """A Poisson stream of queries: arrival gaps exponential with mean
+    1/rate; a uniformly chosen city; 1-max_sources car sources (log-uniform)
+    with per-band power log-uniform 0.001-1 W; 1k-max_mics microphones
+    (log-uniform) on a 4 m grid at 1.5 m over a square window placed
+    uniformly in the city; reflection order 3-6 (uniform)."""
+    rng = _rng(seed)
+    t = 0.0
+    out = []
+    for _ in range(n_queries):
+        t += float(rng.exponential(1.0 / rate_qps))
+        city = int(rng.integers(0, n_cities))
+        n_s = int(round(math.exp(rng.uniform(0.0, math.log(max_sources)))))
+        src, power = _lane_sources(rng, n_s, -3.0, 0.0)
+        n_m = math.exp(rng.uniform(math.log(1000), math.log(max_mics)))
+        side = max(2, int(round(math.sqrt(n_m))))
+        span = min(DIST_MIC_SIDE, 4.0 * side)
+        x0 = float(rng.uniform(0.0, DIST_MIC_SIDE - span))
+        y0 = float(rng.uniform(0.0, DIST_MIC_SIDE - span))
+        mics = mic_grid(x0, y0, x0 + span, y0 + span, side, side, 1.5)
+        out.append(Query(t, city, src, power, mics, level, int(rng.integers(3, 7))))
     return out

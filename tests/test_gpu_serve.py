@@ -1,0 +1,73 @@
+"""The continuous-batching server: every query's result is the same alone
+(one whole-query trace) and in the mix (traced step by step together with the
+other admitted queries); admission respects the memory budget."""
+import numpy as np
+import pytest
+
+from paper_1912_03998_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tracer():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_03998_gb300 import btrace
+    t = btrace.Tracer(0)
+    yield t
+    t.close()
+
+
+@pytest.fixture(scope="module")
+def setting():
+    cities = synth.serving_cities(seed=5, n=2)
+    queries = synth.serving_queries(seed=9, n_queries=10, n_cities=2, rate_qps=1000.0,
+                                    max_sources=24, max_mics=6000)
+    return cities, queries
+
+
+def same(a, b):
+    assert (a.count == b.count).all()
+    assert (np.isneginf(a.level) == np.isneginf(b.level)).all()
+    fin = np.isfinite(b.level)
+    assert np.abs(a.level[fin] - b.level[fin]).max(initial=0.0) < 1e-6
+
+
+@pytest.mark.parametrize("step_lineages", [1 << 12, 1 << 20])
+def test_results_same_alone_and_in_the_mix(tracer, setting, step_lineages):
+    from paper_1912_03998_gb300 import serve
+    cities, queries = setting
+    srv = serve.Server(tracer, cities, step_lineages=step_lineages)
+    try:
+        mixed = srv.run(queries, realtime=False)
+        alone = serve.run_plain(tracer, srv.city_ids, queries, realtime=False)
+    finally:
+        srv.close()
+    assert len(mixed) == len(alone) == len(queries)
+    if step_lineages == 1 << 12:
+        assert srv.steps > len(queries)  # queries spanned several steps and overlapped
+    for a, b in zip(mixed, alone):
+        same(a, b)
+        assert a.count.max() > 0
+
+
+def test_admission_by_memory(tracer, setting):
+    from paper_1912_03998_gb300 import serve
+    cities, queries = setting
+    srv = serve.Server(tracer, cities, step_lineages=1 << 14, mem_budget=1)
+    seen = []
+    orig = srv.step
+
+    def step():
+        r = orig()
+        seen.append(len(srv.active))
+        return r
+
+    srv.step = step
+    try:
+        done = srv.run(queries[:4], realtime=False)
+    finally:
+        srv.close()
+    assert len(done) == 4 and max(seen) <= 1  # one query at a time fits a 1-byte budget
