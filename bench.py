@@ -381,6 +381,8 @@ def run_serve(args):
             rows.append({"rate_qps": rate, "served": serve.latency_summary(done, wall),
                          "plain": serve.latency_summary(plain, wall_p), "steps": srv.steps,
                          "segments_per_s": segs / wall, "gpu_launches": launches,
+                         "server_time_s": {k: round(v, 4) for k, v in srv.host_s.items()},
+                         "wall_s": round(wall, 4),
                          "sources_mean": float(np.mean([len(q.src) for q in qs])),
                          "microphones_mean": float(np.mean([len(q.mics) for q in qs]))})
     tr.close()

@@ -7,8 +7,9 @@ that shares its city's geometry (bt_scene_share) for its own sources,
 microphones and result.  The server runs in steps.  Before a step it admits
 waiting queries in arrival order while a scene slot is free and their device
 memory fits the budget; a step then traces the next lineages of every
-admitted query -- an equal share of the step's lineage budget each, at most
-what the query has left -- in the same persistent launches
+admitted query -- first up to a small quantum each, so that small queries
+finish at once, then the rest of the step's lineage budget in admission
+order -- in the same persistent launches
 (bt_trace_ranges, accumulating), so queries that arrive while others are on
 the GPU join at the next step and their work overlaps on the device.  A query
 whose lineages are all traced is read back (levels to the host), its scene
@@ -53,9 +54,10 @@ class Done:
 
 
 class Server:
-    def __init__(self, tracer, cities, step_lineages: int = 1 << 22, mem_budget: int = 4 << 30,
-                 max_active: int = 48, precision: int = btrace.BT_PREC_MIXED):
+    def __init__(self, tracer, cities, step_lineages: int = 1 << 22, quantum: int = 1 << 16,
+                 mem_budget: int = 4 << 30, max_active: int = 48, precision: int = btrace.BT_PREC_MIXED):
         self.tr = tracer
+        self.quantum = int(quantum)
         self.city_ids = [tracer.load_geometry(w) for w in cities]
         self.step_lineages = int(step_lineages)
         self.mem_budget = int(mem_budget)
@@ -67,6 +69,7 @@ class Server:
         self.done = []
         self.steps = 0
         self.segments = 0
+        self.host_s = dict(admit=0.0, step=0.0, gpu_trace=0.0, retire=0.0)
         self.t0 = time.perf_counter()
 
     def now(self) -> float:
@@ -94,27 +97,25 @@ class Server:
 
     def step(self) -> bool:
         """Admit, trace one step, retire finished queries.  False when idle."""
+        t0 = time.perf_counter()
         self._admit()
+        t1 = time.perf_counter()
+        self.host_s["admit"] += t1 - t0
         if not self.active:
             return False
-        # an equal share of the step's lineages for every active query,
-        # what a query does not need passed on to the others
+        # every active query first gets up to `quantum` lineages, so that a
+        # small query finishes in the step after its arrival; the rest of the
+        # step's budget goes to the queries in admission order
         left = [a["total"] - a["next"] for a in self.active]
-        share = [0] * len(left)
-        budget = self.step_lineages
-        open_ = [i for i, r in enumerate(left) if r > 0]
-        while budget > 0 and open_:
-            per = max(1, budget // len(open_))
-            nxt = []
-            for i in open_:
-                g = min(per, left[i] - share[i], budget)
-                share[i] += g
-                budget -= g
-                if share[i] < left[i]:
-                    nxt.append(i)
-                if budget == 0:
-                    break
-            open_ = nxt
+        quantum = max(1, min(self.quantum, self.step_lineages // len(left)))
+        share = [min(r, quantum) for r in left]
+        budget = self.step_lineages - sum(share)
+        for i, r in enumerate(left):
+            if budget <= 0:
+                break
+            g = min(r - share[i], budget)
+            share[i] += g
+            budget -= g
         ids, begins, ends, params = [], [], [], []
         for a, s in zip(self.active, share):
             if s > 0:
@@ -125,8 +126,12 @@ class Server:
                 a["next"] += s
         if ids:
             btrace.bt_trace_ranges(self.tr.ctx, ids, begins, ends, params, accumulate=True)
-            self.segments += btrace.bt_ranges_stats(self.tr.ctx)["segments"]
+            st = btrace.bt_ranges_stats(self.tr.ctx)
+            self.segments += st["segments"]
+            self.host_s["gpu_trace"] += st["trace_ms"] * 1e-3
         self.steps += 1
+        t2 = time.perf_counter()
+        self.host_s["step"] += t2 - t1
         still = []
         for a in self.active:
             if a["next"] < a["total"]:
@@ -141,6 +146,7 @@ class Server:
             self.mem_used -= a["mem"]
             self.done.append(Done(a["index"], a["arrival"], a["admitted"], self.now(), level, count))
         self.active = still
+        self.host_s["retire"] += time.perf_counter() - t2
         return True
 
     def run(self, queries, realtime: bool = True):
@@ -149,6 +155,8 @@ class Server:
         otherwise all are submitted at once.  Returns the Done records in
         query order."""
         self.t0 = time.perf_counter()
+        self.done, self.steps, self.segments = [], 0, 0
+        self.host_s = dict(admit=0.0, step=0.0, gpu_trace=0.0, retire=0.0)
         i = 0
         while i < len(queries) or self.waiting or self.active:
             now = self.now()

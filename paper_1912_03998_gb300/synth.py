@@ -413,8 +413,9 @@ def serving_queries(seed: int, n_queries: int, n_cities: int, rate_qps: float, l
     """A Poisson stream of queries: arrival gaps exponential with mean
     1/rate; a uniformly chosen city; 1-max_sources car sources (log-uniform)
     with per-band power log-uniform 0.001-1 W; 1k-max_mics microphones
-    (log-uniform) on a 4 m grid at 1.5 m over a square window placed
-    uniformly in the city; reflection order 3-6 (uniform)."""
+    (log-uniform) on a 4 m grid at 1.5 m over a square window centred on one
+    of the query's sources (kept inside the city); reflection order 3-6
+    (uniform)."""
     rng = _rng(seed)
     t = 0.0
     out = []
@@ -426,8 +427,9 @@ def serving_queries(seed: int, n_queries: int, n_cities: int, rate_qps: float, l
         n_m = math.exp(rng.uniform(math.log(1000), math.log(max_mics)))
         side = max(2, int(round(math.sqrt(n_m))))
         span = min(DIST_MIC_SIDE, 4.0 * side)
-        x0 = float(rng.uniform(0.0, DIST_MIC_SIDE - span))
-        y0 = float(rng.uniform(0.0, DIST_MIC_SIDE - span))
+        cx, cy = src[int(rng.integers(0, n_s)), :2]
+        x0 = float(np.clip(cx - 0.5 * span, 0.0, DIST_MIC_SIDE - span))
+        y0 = float(np.clip(cy - 0.5 * span, 0.0, DIST_MIC_SIDE - span))
         mics = mic_grid(x0, y0, x0 + span, y0 + span, side, side, 1.5)
         out.append(Query(t, city, src, power, mics, level, int(rng.integers(3, 7))))
     return out
