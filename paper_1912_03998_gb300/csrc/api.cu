@@ -636,9 +636,18 @@ static void fill_view(bt::SceneView &v, SceneState &s, const bt_trace_params *p,
 }
 
 // Lineages per persistent launch when the caller leaves it to the library:
-// segment records of at most 8 GiB.
+// segment records of at most a quarter of the free device memory and at most
+// 32 GiB (fewer, larger launches have fewer launch tails), at least 1 GiB.
 static int64_t default_chunk(int max_order) {
-  return ((int64_t)8 << 30) / ((int64_t)sizeof(bt::Seg) * (max_order + 1));
+  size_t free_b = 0, total_b = 0;
+  int64_t budget = (int64_t)8 << 30;
+  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+    budget = (int64_t)(free_b / 4);
+    if (budget > ((int64_t)32 << 30)) budget = (int64_t)32 << 30;
+  }
+  cudaGetLastError();
+  if (budget < ((int64_t)1 << 30)) budget = (int64_t)1 << 30;
+  return budget / ((int64_t)sizeof(bt::Seg) * (max_order + 1));
 }
 
 // Check the trace parameters p for scene s; derive the air damping exponents.

@@ -440,8 +440,11 @@ cudaError_t build_scene(cudaStream_t st, const float *d_verts, const int32_t *d_
 // sorted by (tile, large flag, Morton code), so the leaves of one tile are
 // contiguous and form one subtree of the LBVH, whose root k_tile_roots finds.
 // Input: the scene's packed triangles (leaf order of the 1x1 hierarchy).
+// A triangle is listed in every tile its xy box, grown by 5 cm, overlaps; the
+// trace accepts a hit in a tile up to 1 cm past the tile's exit along the ray,
+// so every triangle such a hit could lie on is in the tile's list.
 __device__ __forceinline__ void tile_span(float lo, float hi, float g0, float w, int n, int &a, int &b) {
-  const float mg = 1e-3f;
+  const float mg = 5e-2f;
   a = clampi((int)floorf((lo - mg - g0) / w), 0, n - 1);
   b = clampi((int)floorf((hi + mg - g0) / w), 0, n - 1);
 }

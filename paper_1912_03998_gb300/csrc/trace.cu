@@ -161,16 +161,11 @@ struct RaySrc {
 // lowest original triangle id.  With kMixed, `rs` gives the float-pair ray
 // that the float32 ray `r` rounds, read only on the rare float64 paths.
 // Returns the leaf slot or -1.
-// Tile of an xy point, as the definition forms it: floor((x - gx0) /
-// (gx1 - gx0) * tx), clamped to the grid.
-__device__ __forceinline__ int tile_ix(double x, double g0, double g1, int n) {
-  return clampi((int)floor((x - g0) / (g1 - g0) * n), 0, n - 1);
-}
 
 template <int kP, bool kCount>
 __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, RaySrc rs, double dns64, Best &best,
                                            int *err, unsigned &n_nodes, unsigned &n_tris,
-                                           int root, const TileGrid *tf = nullptr, int tile = 0) {
+                                           int root, float tlim = kInf) {
   [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   best.t = kInf;
   best.slot = -1;
@@ -183,7 +178,6 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, Ray
   const Node *const nodes = sc.nodes;
   const Tri *const tris = sc.tris;
   if (n_tri == 0 || root == (int)0x80000000) return -1;
-  const int tile_x = tf ? tile % tf->tx : 0, tile_y = tf ? tile / tf->tx : 0;
   // candidate evaluation (one call site, so the code is emitted once)
   auto consider = [&](int slot) {
     if (kCount) n_tris++;
@@ -219,22 +213,7 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, Ray
     } else {
       if (!(t < kInf && accept_hit(r, t))) return;
     }
-    if (tf) {
-      // sub-domain: the hit point must lie in this tile (half-open); near a
-      // tile border the point is formed in float64 in MIXED mode
-      float hx = r.o.x + t * r.d.x, hy = r.o.y + t * r.d.y;
-      float ux = (hx - tf->gx0) / tf->wx, uy = (hy - tf->gy0) / tf->wy;
-      int ix = clampi((int)floorf(ux), 0, tf->tx - 1), iy = clampi((int)floorf(uy), 0, tf->ty - 1);
-      bool near = fabsf(ux - rintf(ux)) < 1e-3f || fabsf(uy - rintf(uy)) < 1e-3f;
-      if ((kMixed && near) || kF64) {
-        double3 o, d;
-        rs.get(o, d);
-        double tt = has64 ? t64 : plane_t64(sc, slot, o, d);
-        ix = tile_ix(o.x + tt * d.x, tf->gx0, tf->gx1, tf->tx);
-        iy = tile_ix(o.y + tt * d.y, tf->gy0, tf->gy1, tf->ty);
-      }
-      if (ix != tile_x || iy != tile_y) return;
-    }
+    if (t > tlim) return;  // sub-domain: beyond the tile (see k_trace_tiled)
     int id = __float_as_int(v1.w);
     if (kP == kPF32) {
       if (t < best.t || (t == best.t && id < best.id)) { best.t = t; best.slot = slot; best.id = id; }
@@ -284,7 +263,7 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, Ray
       float4 lxy = __ldg(&nd->lxy), rxy = __ldg(&nd->rxy), lrz = __ldg(&nd->lrz);
       int2 ch = __ldg((const int2 *)&nd->child);
       // in MIXED and FP64 mode near ties must still be visited
-      float tmax = kP != kPF32 ? best.t + (1e-5f * fabsf(best.t) + 1e-4f) : best.t;
+      float tmax = fminf(kP != kPF32 ? best.t + (1e-5f * fabsf(best.t) + 1e-4f) : best.t, tlim);
       float tl, tr;
       bool hl = slab(r, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, tmax, tl);
       bool hr = slab(r, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, tmax, tr);
@@ -357,6 +336,8 @@ __device__ __forceinline__ void emit_segment(const TraceArgs &a, const Seg &s, b
 constexpr int kTraceThreads = 128;
 
 constexpr int kRowA = 0, kRowN = 3, kRowO = 12, kRowD = 15, kRows = 18;
+// a sub-domain accepts hits up to this far (m along the ray) past its exit
+constexpr float kTileEps = 1e-2f;
 // per-lane event counters (rows of LineageSmem::cnt)
 enum { kCSeg, kCHit, kCEsc, kCEmit, kCHand, kCSteal, kCNodes, kCTris, kNumCounts };
 template <int kP>
@@ -1034,8 +1015,21 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, c
     if (active) {
       const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), v.t_eps, ls.dns);
       Best best;
+      // Hits are searched up to 1 cm past the ray's exit from the tile (the
+      // tile lists hold every triangle within 5 cm of the tile): a hit there
+      // is the ray's first, and a ray with none goes on to the next tile.
+      float t_exit;
+      {
+        const int ix = tile % tg.tx, iy = tile / tg.tx;
+        float tex = kInf, tey = kInf;
+        if (r.d.x > 0.0f) tex = (tg.gx0 + (ix + 1) * tg.wx - r.o.x) / r.d.x;
+        else if (r.d.x < 0.0f) tex = (tg.gx0 + ix * tg.wx - r.o.x) / r.d.x;
+        if (r.d.y > 0.0f) tey = (tg.gy0 + (iy + 1) * tg.wy - r.o.y) / r.d.y;
+        else if (r.d.y < 0.0f) tey = (tg.gy0 + iy * tg.wy - r.o.y) / r.d.y;
+        t_exit = fminf(tex, tey) + kTileEps;
+      }
       int hit = closest_hit<kP, kCount>(v.sc, r, rs, ls.dns64, best, &a.ctr->error, cn[kCNodes], cn[kCTris],
-                                            __ldg(&ta.roots[tile]), &tg, tile);
+                                        __ldg(&ta.roots[tile]), t_exit);
       __syncwarp(act_mask);  // reconverge after the traversal loop (see k_trace)
       if (hit >= 0) {
         // the hit lies in this tile; a reflected beam starts here as well
