@@ -44,7 +44,7 @@ struct SceneState {
   // microphones
   bool has_mics = false;
   int64_t n_mics = 0;
-  int side = 1;
+  int side = 1, nz = 1;
   DevBuf mics, cell_start, grid, energy, count;
   // tiled hierarchy (sub-domains), built on the first trace that asks for it
   int tiled_tx = 0, tiled_ty = 0;
@@ -579,13 +579,9 @@ BT_API int bt_set_microphones(bt_ctx *c, int32_t scene_id, const float *pos, int
   if (n_m > 0 && !pos) return fail(c, BT_E_INVALID, "NULL microphone array");
   DeviceGuard g(c->device);
   cudaStream_t st = c->stream;
-  int side = (int)ceil(sqrt((double)n_m / 4.0));
-  if (side < 1) side = 1;
-  size_t n_cells = (size_t)side * side;
   TRY(ensure(c, c->stage_a, sizeof(float) * 3 * (size_t)n_m));
-  TRY(ensure(c, c->scratch, bt::build_mics_scratch_bytes(n_m, side)));
+  TRY(ensure(c, c->scratch, bt::build_mics_scratch_bytes(n_m)));
   TRY(ensure(c, s->mics, sizeof(float4) * (size_t)n_m));
-  TRY(ensure(c, s->cell_start, sizeof(int) * (n_cells + 1)));
   TRY(ensure(c, s->grid, sizeof(bt::MicGrid)));
   TRY(ensure(c, s->energy, sizeof(double) * bt::kMaxBands * (size_t)n_m));
   TRY(ensure(c, s->count, sizeof(int) * (size_t)n_m));
@@ -594,16 +590,38 @@ BT_API int bt_set_microphones(bt_ctx *c, int32_t scene_id, const float *pos, int
   CK(cudaMemsetAsync(s->count.p, 0, sizeof(int) * (size_t)n_m, c->stream));
   TRY(reset_counters(c));
   if (n_m > 0) CK(cudaMemcpyAsync(c->stage_a.p, pos, sizeof(float) * 3 * n_m, cudaMemcpyDefault, st));
-  CK(bt::build_mics(st, (const float *)c->stage_a.p, n_m, side, (bt::MicGrid *)s->grid.p,
-                    (float4 *)s->mics.p, (int *)s->cell_start.p, c->scratch.p, c->scratch.cap,
-                    &c->d_ctr->error));
+  CK(bt::mic_box(st, (const float *)c->stage_a.p, n_m, c->d_box, &c->d_ctr->error));
+  float box[6] = {0, 0, 0, 0, 0, 0};
+  CK(cudaMemcpyAsync(box, c->d_box, sizeof(box), cudaMemcpyDeviceToHost, st));
   TRY(read_counters(c));
   if (c->h_ctr->error) {
     s->has_mics = false;
     return fail(c, BT_E_INVALID, "microphone position not finite");
   }
+  // Grid: about four microphones per cell.  Microphones at (nearly) one
+  // height get square xy cells and one layer; a volumetric set gets cubic
+  // cells, at most 16 layers.
+  int nx = 1, ny = 1, nz = 1;
+  if (n_m > 0) {
+    const double ex = box[3] - box[0], ey = box[4] - box[1], ez = box[5] - box[2];
+    if (ez <= 1.0) {
+      nx = ny = (int)ceil(sqrt((double)n_m / 4.0));
+    } else {
+      const double h = cbrt(fmax(ex, 1.0) * fmax(ey, 1.0) * ez / fmax(1.0, (double)n_m / 4.0));
+      nx = (int)fmin(4096.0, fmax(1.0, ceil(ex / h)));
+      ny = (int)fmin(4096.0, fmax(1.0, ceil(ey / h)));
+      nz = (int)fmin(16.0, fmax(1.0, ceil(ez / h)));
+    }
+  }
+  const size_t n_cells = (size_t)nx * ny * nz;
+  TRY(ensure(c, s->cell_start, sizeof(int) * (n_cells + 1)));
+  CK(bt::build_mics(st, (const float *)c->stage_a.p, n_m, nx, ny, nz, c->d_box, (bt::MicGrid *)s->grid.p,
+                    (float4 *)s->mics.p, (int *)s->cell_start.p, c->scratch.p, c->scratch.cap));
+  CK(cudaStreamSynchronize(st));
+  const int side = nx;
   s->n_mics = n_m;
   s->side = side;
+  s->nz = nz;
   s->has_mics = true;
   s->traced = false;
   s->gen = ++c->gen_counter;
@@ -750,6 +768,7 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   memset(&sa, 0, sizeof(sa));
   sa.v = ta.v;
   sa.fp64 = p->precision == BT_PREC_FP64 ? 1 : 0;
+  sa.max_nz = s->nz;
   sa.segs = ta.segs;
   sa.seg_count = c->d_seg_count;
   sa.seg_capacity = cap;
@@ -915,7 +934,7 @@ struct bt_batch {
   std::vector<int64_t> beams;  // lineages per scene
   int prec = BT_PREC_MIXED;
   int count_work = 0, blocks_per_sm = 0;
-  int max_order = 0;
+  int max_order = 0, max_nz = 1;
   int64_t total = 0, chunk = 1;
   DevBuf views, segs, beam_tables[9];
   bt::Counters *d_ctr = nullptr, *h_ctr = nullptr;
@@ -986,6 +1005,7 @@ BT_API int bt_batch_create(bt_ctx *c, const int32_t *scene_ids, int32_t n_scenes
       b->beams.push_back(s.n_src * nb);
       b->total += s.n_src * nb;
       if (params[i].max_order > b->max_order) b->max_order = params[i].max_order;
+      if (s.nz > b->max_nz) b->max_nz = s.nz;
       if (prec == BT_PREC_MIXED && s.n_src > 0) {
         DevBuf &t = b->beam_tables[s.level];
         if (!t.p) {
@@ -1056,6 +1076,7 @@ static int record_batch(bt_batch *b) {
   sa.views = ta.views;
   sa.n_views = n;
   sa.fp64 = b->prec == BT_PREC_FP64 ? 1 : 0;
+  sa.max_nz = b->max_nz;
   sa.segs = ta.segs;
   sa.seg_count = ta.seg_count;
   sa.seg_capacity = ta.seg_capacity;
@@ -1169,7 +1190,7 @@ BT_API int bt_trace_ranges(bt_ctx *c, int32_t n, const int32_t *scene_ids, const
   if (n == 0) return BT_OK;
   std::vector<bt::SceneView> hv((size_t)n);
   const int prec = params[0].precision;
-  int kmax = 0;
+  int kmax = 0, max_nz = 1;
   int64_t total = 0;
   DeviceGuard g(c->device);
   cudaStream_t st = c->stream;
@@ -1194,6 +1215,7 @@ BT_API int bt_trace_ranges(bt_ctx *c, int32_t n, const int32_t *scene_ids, const
     hv[i].lineage_first = lineage_begin[i];
     total += lineage_end[i] - lineage_begin[i];
     if (p->max_order > kmax) kmax = p->max_order;
+    if (s->nz > max_nz) max_nz = s->nz;
     if (prec == BT_PREC_MIXED && nl > 0) {
       DevBuf &t = c->level_tables[s->level];
       if (!t.p) {
@@ -1235,6 +1257,7 @@ BT_API int bt_trace_ranges(bt_ctx *c, int32_t n, const int32_t *scene_ids, const
   sa.views = ta.views;
   sa.n_views = n;
   sa.fp64 = prec == BT_PREC_FP64 ? 1 : 0;
+  sa.max_nz = max_nz;
   sa.segs = ta.segs;
   sa.seg_count = ta.seg_count;
   sa.seg_capacity = cap;
@@ -1437,6 +1460,7 @@ BT_API int bt_trace_noalloc(bt_ctx *c, int32_t scene_id, const bt_trace_params *
   memset(&sa, 0, sizeof(sa));
   sa.v = ta.v;
   sa.fp64 = p->precision == BT_PREC_FP64 ? 1 : 0;
+  sa.max_nz = s->nz;
   sa.segs = segs;
   sa.seg_count = seg_count;
   sa.seg_capacity = cap;

@@ -87,13 +87,16 @@ struct DevScene {
   float lo[3], hi[3];    // scene box
 };
 
-// Microphone bin grid over the microphones' xy box; the box [zlo, zhi] is the
-// microphones' height slab.
+// Microphone bin grid over the microphones' box: nx x ny cells in xy and nz
+// layers in z (one layer for microphones at one height; several for a
+// volumetric set), cell (layer, row, column) = (iz * ny + iy) * nx + ix.
+// [zlo, zhi] is the microphones' height slab.
 struct MicGrid {
   float x0, y0, cw, ch, inv_cw, inv_ch, zlo, zhi;
   int nx, ny;
   int n_mics;
-  int pad;
+  int nz;
+  float z0, dz, inv_dz, pad;
 };
 
 // One beam segment handed from the trace kernel to the scatter kernel, 192 B.
@@ -173,6 +176,7 @@ struct ScatterArgs {
   const SceneView *views;   // batch: [n_views] in device memory, else null
   int n_views;
   int fp64;                 // 1: every microphone test in float64 (BT_PREC_FP64)
+  int max_nz;               // most microphone layers of any scene traced
   const Seg *segs;
   const unsigned long long *seg_count;
   unsigned long long seg_capacity;
@@ -438,9 +442,9 @@ __device__ __forceinline__ void poly_clip(Poly &p, float ax, float ay, float b) 
 }
 
 // Clip by the relaxation of a.m >= b; returns false when the footprint is empty.
-__device__ __forceinline__ bool poly_halfspace(Poly &p, float3 a, float b, const MicGrid &g) {
+__device__ __forceinline__ bool poly_halfspace(Poly &p, float3 a, float b, float zl, float zh) {
   if (!(b > -kInf)) return true;  // missing plane
-  float bz = fmaxf(a.z * g.zlo, a.z * g.zhi);
+  float bz = fmaxf(a.z * zl, a.z * zh);
   float axy = fabsf(a.x) + fabsf(a.y);
   float bb = b - bz - 0.01f * axy - 1e-6f * fabsf(b);
   if (axy == 0.0f) return bb <= 0.0f;
@@ -448,9 +452,15 @@ __device__ __forceinline__ bool poly_halfspace(Poly &p, float3 a, float b, const
   return p.n >= 3;
 }
 
-// Footprint of segment s over the grid; returns false if empty.  Planes are
+// Footprint of segment s over layer `layer` of the grid (the whole height
+// slab when the grid has one layer); returns false if empty.  Planes are
 // relative to the apex: n . (m - A) >= w  <=>  n . m >= w + n . A.
-__device__ __forceinline__ bool seg_footprint(const Seg &s, const MicGrid &g, Poly &p) {
+__device__ __forceinline__ bool seg_footprint(const Seg &s, const MicGrid &g, int layer, Poly &p) {
+  float zl = g.zlo, zh = g.zhi;
+  if (g.nz > 1) {
+    zl = fmaxf(g.zlo, g.z0 + layer * g.dz) - 1e-3f;
+    zh = fminf(g.zhi, g.z0 + (layer + 1) * g.dz) + 1e-3f;
+  }
   float m = 0.01f;
   float X0 = g.x0 - m, X1 = g.x0 + g.cw * g.nx + m, Y0 = g.y0 - m, Y1 = g.y0 + g.ch * g.ny + m;
   p.n = 4;
@@ -461,11 +471,11 @@ __device__ __forceinline__ bool seg_footprint(const Seg &s, const MicGrid &g, Po
   float3 A = make_float3(s.ahi[0], s.ahi[1], s.ahi[2]);
   float3 n0 = f3(s.n0), n1 = f3(s.n1), n2 = f3(s.n2);
   float3 ns = f3(s.start), ne = f3(s.end);
-  if (!poly_halfspace(p, n0, dot3(n0, A), g)) return false;
-  if (!poly_halfspace(p, n1, dot3(n1, A), g)) return false;
-  if (!poly_halfspace(p, n2, dot3(n2, A), g)) return false;
-  if (!poly_halfspace(p, ns, s.start.w + dot3(ns, A), g)) return false;
-  if (!poly_halfspace(p, ne, s.end.w + dot3(ne, A), g)) return false;
+  if (!poly_halfspace(p, n0, dot3(n0, A), zl, zh)) return false;
+  if (!poly_halfspace(p, n1, dot3(n1, A), zl, zh)) return false;
+  if (!poly_halfspace(p, n2, dot3(n2, A), zl, zh)) return false;
+  if (!poly_halfspace(p, ns, s.start.w + dot3(ns, A), zl, zh)) return false;
+  if (!poly_halfspace(p, ne, s.end.w + dot3(ne, A), zl, zh)) return false;
   return true;
 }
 
@@ -513,10 +523,11 @@ cudaError_t tiled_build(cudaStream_t st, const Tri *src, const Plane *sp, const 
                         void *scratch, size_t scratch_bytes, Node *nodes, Tri *tris, Plane *planes,
                         Plane64 *planes64, PlaneDF *planes_df, int *roots, int *d_error);
 size_t build_scene_scratch_bytes(int64_t n_tris);
-cudaError_t build_mics(cudaStream_t st, const float *d_pos, int64_t n_m, int side, MicGrid *d_grid,
-                       float4 *d_sorted, int *d_cell_start, void *d_scratch, size_t scratch_bytes,
-                       int *d_error);
-size_t build_mics_scratch_bytes(int64_t n_m, int side);
+cudaError_t mic_box(cudaStream_t st, const float *d_pos, int64_t n_m, float *d_box, int *d_error);
+cudaError_t build_mics(cudaStream_t st, const float *d_pos, int64_t n_m, int nx, int ny, int nz,
+                       const float *d_box, MicGrid *d_grid, float4 *d_sorted, int *d_cell_start, void *d_scratch,
+                       size_t scratch_bytes);
+size_t build_mics_scratch_bytes(int64_t n_m);
 cudaError_t launch_trace(cudaStream_t st, const TraceArgs &a, int n_sm);
 cudaError_t launch_trace_tiled(cudaStream_t st, const TraceArgs &a, const TiledArgs &t, int n_sm);
 int tiled_resident_lanes(int n_sm);  // lanes of one full persistent sub-domain launch

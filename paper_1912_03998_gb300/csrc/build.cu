@@ -616,21 +616,25 @@ __global__ void k_mic_validate(const float *pos, int64_t n, float *box, int *err
   warp_box_reduce(lo, hi, box);
 }
 
-__global__ void k_mic_grid(const float *box, int side, int64_t n, MicGrid *g) {
+__global__ void k_mic_grid(const float *box, int nx, int ny, int nz, int64_t n, MicGrid *g) {
   MicGrid r;
-  float ex = box[3] - box[0], ey = box[4] - box[1];
+  float ex = box[3] - box[0], ey = box[4] - box[1], ez = box[5] - box[2];
   r.x0 = box[0];
   r.y0 = box[1];
-  r.cw = fmaxf(ex / side * 1.000001f, 1e-3f);
-  r.ch = fmaxf(ey / side * 1.000001f, 1e-3f);
+  r.cw = fmaxf(ex / nx * 1.000001f, 1e-3f);
+  r.ch = fmaxf(ey / ny * 1.000001f, 1e-3f);
   r.inv_cw = 1.0f / r.cw;
   r.inv_ch = 1.0f / r.ch;
   r.zlo = box[2];
   r.zhi = box[5];
-  r.nx = side;
-  r.ny = side;
+  r.nx = nx;
+  r.ny = ny;
   r.n_mics = (int)n;
-  r.pad = 0;
+  r.nz = nz;
+  r.z0 = box[2];
+  r.dz = fmaxf(ez / nz * 1.000001f, 1e-3f);
+  r.inv_dz = 1.0f / r.dz;
+  r.pad = 0.0f;
   *g = r;
 }
 
@@ -640,7 +644,8 @@ __global__ void k_mic_keys(const float *pos, int64_t n, const MicGrid *g, uint32
   MicGrid gr = *g;
   int cx = clampi((int)floorf((pos[3 * i] - gr.x0) * gr.inv_cw), 0, gr.nx - 1);
   int cy = clampi((int)floorf((pos[3 * i + 1] - gr.y0) * gr.inv_ch), 0, gr.ny - 1);
-  keys[i] = (uint32_t)(cy * gr.nx + cx);
+  int cz = gr.nz > 1 ? clampi((int)floorf((pos[3 * i + 2] - gr.z0) * gr.inv_dz), 0, gr.nz - 1) : 0;
+  keys[i] = (uint32_t)((cz * gr.ny + cy) * gr.nx + cx);
   vals[i] = (uint32_t)i;
 }
 
@@ -658,15 +663,27 @@ __global__ void k_mic_gather(const float *pos, int64_t n, const uint32_t *keys, 
     for (int c = k + 1; c <= n_cells; c++) cell_start[c] = (int)n;
 }
 
-size_t build_mics_scratch_bytes(int64_t n_m, int side) {
+size_t build_mics_scratch_bytes(int64_t n_m) {
   size_t m = (size_t)(n_m > 0 ? n_m : 1);
-  return 4 * align256(4 * m) + align256(4 * rs_hist_entries((int)m)) + align256(64);
+  return 4 * align256(4 * m) + align256(4 * rs_hist_entries((int)m));
 }
 
-cudaError_t build_mics(cudaStream_t st, const float *d_pos, int64_t n_m, int side, MicGrid *d_grid,
-                       float4 *d_sorted, int *d_cell_start, void *d_scratch, size_t scratch_bytes,
-                       int *d_error) {
-  if (scratch_bytes < build_mics_scratch_bytes(n_m, side)) return cudaErrorInvalidValue;
+// The microphones' box (and a non-finite check); the host reads the box to
+// choose the grid before build_mics.
+cudaError_t mic_box(cudaStream_t st, const float *d_pos, int64_t n_m, float *d_box, int *d_error) {
+  k_box_init<<<1, 32, 0, st>>>(d_box);
+  int threads = 256;
+  int64_t blocks = (n_m + threads - 1) / threads;
+  if (blocks < 1) blocks = 1;
+  k_mic_validate<<<(int)(blocks < 4096 ? blocks : 4096), threads, 0, st>>>(d_pos, n_m, d_box, d_error);
+  note_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t build_mics(cudaStream_t st, const float *d_pos, int64_t n_m, int nx, int ny, int nz,
+                       const float *d_box, MicGrid *d_grid, float4 *d_sorted, int *d_cell_start, void *d_scratch,
+                       size_t scratch_bytes) {
+  if (scratch_bytes < build_mics_scratch_bytes(n_m)) return cudaErrorInvalidValue;
   int n = (int)n_m;
   size_t m = (size_t)(n > 0 ? n : 1);
   char *s = (char *)d_scratch;
@@ -674,20 +691,16 @@ cudaError_t build_mics(cudaStream_t st, const float *d_pos, int64_t n_m, int sid
   uint32_t *vals = (uint32_t *)s; s += align256(4 * m);
   uint32_t *kalt = (uint32_t *)s; s += align256(4 * m);
   uint32_t *valt = (uint32_t *)s; s += align256(4 * m);
-  uint32_t *hist = (uint32_t *)s; s += align256(4 * rs_hist_entries(n));
-  float *box = (float *)s;
-  k_box_init<<<1, 32, 0, st>>>(box);
-  int threads = 256;
-  int blocks = (n + threads - 1) / threads;
-  if (blocks < 1) blocks = 1;
-  k_mic_validate<<<blocks < 4096 ? blocks : 4096, threads, 0, st>>>(d_pos, n_m, box, d_error);
-  k_mic_grid<<<1, 1, 0, st>>>(box, side, n_m, d_grid);
-  note_launches(3);
-  int n_cells = side * side;
+  uint32_t *hist = (uint32_t *)s;
+  k_mic_grid<<<1, 1, 0, st>>>(d_box, nx, ny, nz, n_m, d_grid);
+  note_launches(1);
+  const int n_cells = nx * ny * nz;
   if (n == 0) {
     cudaMemsetAsync(d_cell_start, 0, sizeof(int) * (n_cells + 1), st);
     return cudaGetLastError();
   }
+  int threads = 256;
+  int blocks = (n + threads - 1) / threads;
   k_mic_keys<<<blocks, threads, 0, st>>>(d_pos, n_m, d_grid, keys, vals);
   note_launches(1);
   int bits = 1;

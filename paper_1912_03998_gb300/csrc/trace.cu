@@ -1282,7 +1282,7 @@ constexpr int kScatterWarps = 4;
 enum : int {
   F_AX = 0, F_RX = 3, F_N0 = 6, F_NLO = 15, F_NS = 24, F_NE = 28, F_P = 32, F_SLOTS = 40,
   F_CY0 = 42, F_PN = 43, F_PX = 44, F_PY = F_PX + kPolyMax, F_AP = F_PY + kPolyMax, F_VI = F_AP + 3,
-  F_MP = F_VI + 1, F_COUNT = F_MP + 2
+  F_MP = F_VI + 1, F_LAYER = F_MP + 2, F_COUNT = F_LAYER + 1
 };
 struct ScatterSmem {
   float f[kScatterWarps][F_COUNT][32];
@@ -1344,14 +1344,20 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
   const int w = threadIdx.x >> 5;
   float(*F)[32] = sm.f[w];
   const long long n_seg = (long long)min(*a.seg_count, a.seg_capacity);
+  // work items: (segment, microphone layer) pairs; one per segment when the
+  // microphones lie in one layer
+  const int n_layers = a.max_nz > 1 ? a.max_nz : 1;
+  const long long n_items = n_seg * n_layers;
   unsigned long long n_cand = 0, n_contrib = 0;
   const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long base = warp0 * 32; base < n_seg; base += n_warps * 32) {
-    // ---- 1. one segment per lane: parameters and footprint
-    long long si = base + lane;
+  for (long long base = warp0 * 32; base < n_items; base += n_warps * 32) {
+    // ---- 1. one item per lane: segment parameters and the layer's footprint
+    const long long it = base + lane;
+    const long long si = it / n_layers;
+    const int layer = (int)(it - si * n_layers);
     int nrows = 0;
-    if (si < n_seg) {
+    if (it < n_items) {
       Seg sl;
       const float4 *src4 = reinterpret_cast<const float4 *>(a.segs + si);
       float4 *dst4 = reinterpret_cast<float4 *>(&sl);
@@ -1368,7 +1374,8 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
       }
       Poly p;
       int cy0 = 0, cy1 = -1;
-      if (seg_footprint(sl, g, p)) {
+      F[F_LAYER][lane] = __int_as_float(layer);
+      if (layer < g.nz && seg_footprint(sl, g, layer, p)) {
         float ymin = kInf, ymax = -kInf;
         for (int i = 0; i < p.n; i++) { ymin = fminf(ymin, p.y[i]); ymax = fmaxf(ymax, p.y[i]); }
         if (ymin <= ymax) {
@@ -1438,8 +1445,9 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
         if (xmin <= xmax) {
           int cx0 = clampi((int)floorf((xmin - g.x0) * g.inv_cw), 0, g.nx - 1);
           int cx1 = clampi((int)floorf((xmax - g.x0) * g.inv_cw), 0, g.nx - 1);
-          first = __ldg(&V.cell_start[row * g.nx + cx0]);
-          cnt = __ldg(&V.cell_start[row * g.nx + cx1 + 1]) - first;
+          const int cell0 = (__float_as_int(F[F_LAYER][so]) * g.ny + row) * g.nx;
+          first = __ldg(&V.cell_start[cell0 + cx0]);
+          cnt = __ldg(&V.cell_start[cell0 + cx1 + 1]) - first;
         }
       }
       // ---- 3. candidates of those runs, 32 at a time

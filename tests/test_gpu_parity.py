@@ -237,6 +237,24 @@ def test_source_linearity(tracer):
     assert np.allclose(ab["I"], a["I"] + b["I"], rtol=1e-9, atol=0)
 
 
+# ------------------------------------------------------- volumetric microphones
+def test_volumetric_microphones(tracer, oracle_mod):
+    # microphones through the whole height of the city (Section 4's receivers
+    # fill a volume): binned in xy cells and height layers
+    base = synth.tiny_city(seed=7, level=4, max_order=4, n_sources=2)
+    layers = [synth.mic_grid(10.0, 10.0, 550.0, 550.0, 20, 20, z) for z in np.linspace(1.5, 71.5, 8)]
+    w = base.with_mics(np.concatenate(layers).astype(np.float32))
+    g = gpu_run(tracer, w)
+    r, L = oracle_levels(oracle_mod, w)
+    s = assert_parity(g["level"], L, "volumetric microphones")
+    assert (g["cnt"] == r["cnt"]).mean() >= 0.999, s
+    assert g["stats"]["segments"] == r["stats"]["segments"]
+    assert (r["cnt"] > 0).mean() > 0.3  # many microphones sit inside buildings
+    # split 4x4 as well
+    g4 = gpu_run(tracer, w, tiles_x=4, tiles_y=4)
+    assert (g4["cnt"] == g["cnt"]).all() and np.allclose(g4["I"], g["I"], rtol=1e-9, atol=0)
+
+
 # ------------------------------------------------------------- district scale
 @pytest.fixture(scope="module")
 def district():
