@@ -72,3 +72,30 @@ def test_admission_by_memory(tracer, setting):
     finally:
         srv.close()
     assert len(done) == 4 and max(seen) <= 1  # one query at a time fits a 1-byte budget
+
+
+def test_shared_geometry_scenes(tracer):
+    # a scene sharing a resident city's geometry traces like a scene of its
+    # own, split or not; the city cannot be unloaded while shared
+    from paper_1912_03998_gb300 import btrace
+    w = synth.tiny_city(seed=4, level=4, max_order=4, n_sources=2)
+    own = tracer.run(w)
+    btrace.bt_unload_scene(tracer.ctx, own["scene_id"])
+    city = tracer.load_geometry(w)
+    sid = btrace.bt_scene_share(tracer.ctx, city)
+    try:
+        btrace.bt_set_sources(tracer.ctx, sid, w.src, w.power, w.level)
+        btrace.bt_set_microphones(tracer.ctx, sid, w.mics)
+        for tiles in ((1, 1), (4, 4)):
+            btrace.bt_trace(tracer.ctx, sid, tracer.params(w.max_order, tiles_x=tiles[0], tiles_y=tiles[1]))
+            n = len(w.mics)
+            I = np.empty((n, 8))
+            c = np.empty(n, np.int32)
+            btrace.bt_read_levels(tracer.ctx, sid, None, I, c)
+            assert (c == own["cnt"]).all() and np.allclose(I, own["I"], rtol=1e-9, atol=0)
+        with pytest.raises(btrace.BtError) as e:
+            btrace.bt_unload_scene(tracer.ctx, city)
+        assert e.value.code == btrace.BT_E_STATE
+    finally:
+        btrace.bt_unload_scene(tracer.ctx, sid)
+        btrace.bt_unload_scene(tracer.ctx, city)
