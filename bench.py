@@ -50,6 +50,9 @@ def parse():
                          "serve: Poisson query streams against 8 resident cities")
     ap.add_argument("--rates", default="50,200,1000,2000", help="serve: arrival rates, queries/s")
     ap.add_argument("--queries", type=int, default=200, help="serve: queries per rate")
+    ap.add_argument("--step-lineages", type=int, default=1 << 21, help="serve: lineages per server step")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the short served-latency measurement in the default line")
     ap.add_argument("--autotune", action="store_true",
                     help="batch: tune blocks per SM and lineages per launch on 16 of the cities first")
     ap.add_argument("--sources", type=int, default=None, help="override the source count")
@@ -350,6 +353,33 @@ def run_batch(args):
 
 
 # ------------------------------------------------------------------ serving
+def serve_once(tr, cities, rate, n_queries, seed, prec, step_lineages):
+    """One Poisson stream served by the loop and, on the same stream, one
+    query at a time; latency summaries of both."""
+    from paper_1912_03998_gb300 import btrace, serve, synth
+    qs = synth.serving_queries(seed=seed, n_queries=n_queries, n_cities=len(cities), rate_qps=rate)
+    srv = serve.Server(tr, cities, step_lineages=step_lineages, precision=prec)
+    try:
+        srv.run(qs[:4], realtime=False)  # warm-up through both paths
+        serve.run_plain(tr, srv.city_ids, qs[:4], precision=prec, realtime=False)
+        n0 = btrace.bt_kernel_launches()
+        t0 = time.perf_counter()
+        done = srv.run(qs, realtime=True)
+        wall = time.perf_counter() - t0
+        launches = btrace.bt_kernel_launches() - n0
+        t0 = time.perf_counter()
+        plain = serve.run_plain(tr, srv.city_ids, qs, precision=prec, realtime=True)
+        wall_p = time.perf_counter() - t0
+    finally:
+        srv.close()
+    return {"rate_qps": rate, "served": serve.latency_summary(done, wall),
+            "plain": serve.latency_summary(plain, wall_p), "steps": srv.steps,
+            "segments_per_s": srv.segments / wall, "gpu_launches": launches,
+            "server_time_s": {k: round(v, 4) for k, v in srv.host_s.items()}, "wall_s": round(wall, 4),
+            "sources_mean": float(np.mean([len(q.src) for q in qs])),
+            "microphones_mean": float(np.mean([len(q.mics) for q in qs]))}
+
+
 def run_serve(args):
     """Poisson streams of traffic-noise queries against 8 resident cities,
     served by the continuous-batching loop and, on the same stream, one query
@@ -363,28 +393,7 @@ def run_serve(args):
     rows = []
     with Clocks(0) as clk:
         for k, rate in enumerate(float(r) for r in args.rates.split(",")):
-            qs = synth.serving_queries(seed=100 + k, n_queries=args.queries, n_cities=len(cities), rate_qps=rate)
-            # warm-up: a few queries through both paths
-            srv = serve.Server(tr, cities, precision=prec)
-            srv.run(qs[:4], realtime=False)
-            serve.run_plain(tr, srv.city_ids, qs[:4], precision=prec, realtime=False)
-            n0 = btrace.bt_kernel_launches()
-            t0 = time.perf_counter()
-            done = srv.run(qs, realtime=True)
-            wall = time.perf_counter() - t0
-            launches = btrace.bt_kernel_launches() - n0
-            segs = srv.segments
-            t0 = time.perf_counter()
-            plain = serve.run_plain(tr, srv.city_ids, qs, precision=prec, realtime=True)
-            wall_p = time.perf_counter() - t0
-            srv.close()
-            rows.append({"rate_qps": rate, "served": serve.latency_summary(done, wall),
-                         "plain": serve.latency_summary(plain, wall_p), "steps": srv.steps,
-                         "segments_per_s": segs / wall, "gpu_launches": launches,
-                         "server_time_s": {k: round(v, 4) for k, v in srv.host_s.items()},
-                         "wall_s": round(wall, 4),
-                         "sources_mean": float(np.mean([len(q.src) for q in qs])),
-                         "microphones_mean": float(np.mean([len(q.mics) for q in qs]))})
+            rows.append(serve_once(tr, cities, rate, args.queries, 100 + k, prec, args.step_lineages))
     tr.close()
     head = rows[-1]
     line = {"metric": "served p50/p99 latency and queries/s", "value": head["served"]["queries_per_s"],
@@ -536,6 +545,19 @@ def main():
         line["e2e"] = res["e2e"]
     if res["untiled"]:
         line["untiled"] = res["untiled"]
+    if not args.no_serve and world == 1 and args.workload == "district":
+        # the metric's second half: served p50/p99 latency on a short stream
+        import torch
+        from paper_1912_03998_gb300 import btrace, synth
+        torch.cuda.set_device(0)
+        prec = {"mixed": btrace.BT_PREC_MIXED, "fp32": btrace.BT_PREC_FP32,
+                "fp64": btrace.BT_PREC_FP64}[args.precision]
+        tr = btrace.Tracer(0)
+        try:
+            line["serving"] = serve_once(tr, synth.serving_cities(seed=5, n=8), 200.0, 100, 100, prec,
+                                         args.step_lineages)
+        finally:
+            tr.close()
     if not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         cb = oracle_sample(w, args.cpu_seconds, threads)

@@ -54,7 +54,7 @@ class Done:
 
 
 class Server:
-    def __init__(self, tracer, cities, step_lineages: int = 1 << 22, quantum: int = 1 << 16,
+    def __init__(self, tracer, cities, step_lineages: int = 1 << 21, quantum: int = 1 << 16,
                  mem_budget: int = 4 << 30, max_active: int = 48, precision: int = btrace.BT_PREC_MIXED):
         self.tr = tracer
         self.quantum = int(quantum)
