@@ -82,7 +82,9 @@ typedef struct {
   int32_t precision;                        /* BT_PREC_* */
   int32_t watchdog_ms;                      /* bound on any device-side wait; default 2000 */
   int32_t chunk_beams;                      /* beam lineages per persistent launch; 0 = automatic
-                                               (segment records of at most 8 GiB) */
+                                               (room for (max_order + 1) segment records of
+                                               192 B per lineage within a quarter of the free
+                                               device memory, clamped to 1..32 GiB) */
   int32_t count_work;                       /* 1: also count BVH nodes visited and triangles
                                                tested (slower; for roofline accounting) */
   int32_t blocks_per_sm;                    /* resident blocks per SM of the persistent trace

@@ -21,7 +21,8 @@ from . import btrace
 
 
 def _chunk_candidates(max_order: int):
-    # 0: the library's default, segment records of up to 8 GiB per launch
+    # 0: the library's default, segment records in a quarter of the free
+    # device memory (1..32 GiB) per launch
     per = max_order + 1
     return [0, (1 << 22) // per, (1 << 24) // per]
 
