@@ -412,92 +412,6 @@ __device__ __forceinline__ df d_to_df(double x) {
   return df{hi, (float)(x - (double)hi)};
 }
 
-// ------------------------------------------------------- footprint polygon
-// Conservative xy footprint of a segment on the microphone slab: each 3D
-// half-space a.m >= b becomes, over z in [zlo, zhi], the weaker half-plane
-// ax x + ay y >= b - max(az zlo, az zhi), grown by a 1 cm slack; the grid
-// rectangle is clipped by those half-planes (Sutherland-Hodgman).
-constexpr int kPolyMax = 12;
-struct Poly {
-  float x[kPolyMax], y[kPolyMax];
-  int n;
-};
-
-__device__ __forceinline__ void poly_clip(Poly &p, float ax, float ay, float b) {
-  Poly q;
-  q.n = 0;
-  for (int i = 0; i < p.n; i++) {
-    int j = i + 1 == p.n ? 0 : i + 1;
-    float fi = ax * p.x[i] + ay * p.y[i] - b;
-    float fj = ax * p.x[j] + ay * p.y[j] - b;
-    if (fi >= 0.0f && q.n < kPolyMax) { q.x[q.n] = p.x[i]; q.y[q.n] = p.y[i]; q.n++; }
-    if ((fi >= 0.0f) != (fj >= 0.0f) && q.n < kPolyMax) {
-      float s = fi / (fi - fj);
-      q.x[q.n] = p.x[i] + s * (p.x[j] - p.x[i]);
-      q.y[q.n] = p.y[i] + s * (p.y[j] - p.y[i]);
-      q.n++;
-    }
-  }
-  p = q;
-}
-
-// Clip by the relaxation of a.m >= b; returns false when the footprint is empty.
-__device__ __forceinline__ bool poly_halfspace(Poly &p, float3 a, float b, float zl, float zh) {
-  if (!(b > -kInf)) return true;  // missing plane
-  float bz = fmaxf(a.z * zl, a.z * zh);
-  float axy = fabsf(a.x) + fabsf(a.y);
-  float bb = b - bz - 0.01f * axy - 1e-6f * fabsf(b);
-  if (axy == 0.0f) return bb <= 0.0f;
-  poly_clip(p, a.x, a.y, bb);
-  return p.n >= 3;
-}
-
-// Footprint of segment s over layer `layer` of the grid (the whole height
-// slab when the grid has one layer); returns false if empty.  Planes are
-// relative to the apex: n . (m - A) >= w  <=>  n . m >= w + n . A.
-__device__ __forceinline__ bool seg_footprint(const Seg &s, const MicGrid &g, int layer, Poly &p) {
-  float zl = g.zlo, zh = g.zhi;
-  if (g.nz > 1) {
-    zl = fmaxf(g.zlo, g.z0 + layer * g.dz) - 1e-3f;
-    zh = fminf(g.zhi, g.z0 + (layer + 1) * g.dz) + 1e-3f;
-  }
-  float m = 0.01f;
-  float X0 = g.x0 - m, X1 = g.x0 + g.cw * g.nx + m, Y0 = g.y0 - m, Y1 = g.y0 + g.ch * g.ny + m;
-  p.n = 4;
-  p.x[0] = X0; p.y[0] = Y0;
-  p.x[1] = X1; p.y[1] = Y0;
-  p.x[2] = X1; p.y[2] = Y1;
-  p.x[3] = X0; p.y[3] = Y1;
-  float3 A = make_float3(s.ahi[0], s.ahi[1], s.ahi[2]);
-  float3 n0 = f3(s.n0), n1 = f3(s.n1), n2 = f3(s.n2);
-  float3 ns = f3(s.start), ne = f3(s.end);
-  if (!poly_halfspace(p, n0, dot3(n0, A), zl, zh)) return false;
-  if (!poly_halfspace(p, n1, dot3(n1, A), zl, zh)) return false;
-  if (!poly_halfspace(p, n2, dot3(n2, A), zl, zh)) return false;
-  if (!poly_halfspace(p, ns, s.start.w + dot3(ns, A), zl, zh)) return false;
-  if (!poly_halfspace(p, ne, s.end.w + dot3(ne, A), zl, zh)) return false;
-  return true;
-}
-
-// x extent of the polygon within the strip y in [ya, yb]
-__device__ __forceinline__ void poly_strip_x(const Poly &p, float ya, float yb, float &xmin, float &xmax) {
-  xmin = kInf;
-  xmax = -kInf;
-  for (int i = 0; i < p.n; i++) {
-    int j = i + 1 == p.n ? 0 : i + 1;
-    float xi = p.x[i], yi = p.y[i], xj = p.x[j], yj = p.y[j];
-    if (yi >= ya && yi <= yb) { xmin = fminf(xmin, xi); xmax = fmaxf(xmax, xi); }
-    if ((yi < ya) != (yj < ya) && yi != yj) {
-      float x = xi + (ya - yi) / (yj - yi) * (xj - xi);
-      xmin = fminf(xmin, x); xmax = fmaxf(xmax, x);
-    }
-    if ((yi < yb) != (yj < yb) && yi != yj) {
-      float x = xi + (yb - yi) / (yj - yi) * (xj - xi);
-      xmin = fminf(xmin, x); xmax = fmaxf(xmax, x);
-    }
-  }
-}
-
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 }  // namespace bt
