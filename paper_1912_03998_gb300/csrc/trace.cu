@@ -976,6 +976,16 @@ __device__ __forceinline__ int take_fresh(const TraceArgs &a, const TiledArgs &t
   return got;
 }
 
+// Distance along r to its exit from tile (ix, iy) of the grid, in the xy plane.
+__device__ __forceinline__ float tile_exit(const TileGrid &tg, int ix, int iy, const Ray &r) {
+  float tex = kInf, tey = kInf;
+  if (r.d.x > 0.0f) tex = (tg.gx0 + (ix + 1) * tg.wx - r.o.x) / r.d.x;
+  else if (r.d.x < 0.0f) tex = (tg.gx0 + ix * tg.wx - r.o.x) / r.d.x;
+  if (r.d.y > 0.0f) tey = (tg.gy0 + (iy + 1) * tg.wy - r.o.y) / r.d.y;
+  else if (r.d.y < 0.0f) tey = (tg.gy0 + iy * tg.wy - r.o.y) / r.d.y;
+  return fminf(tex, tey);
+}
+
 // The sub-domain trace (Section 3: the geometry is split into tiles; a beam
 // whose ray leaves a tile is sent to the tile it enters; exchanged beams are
 // served before new ones; idle workers take work from busy tiles), as one
@@ -988,6 +998,13 @@ __device__ __forceinline__ int take_fresh(const TraceArgs &a, const TiledArgs &t
 // batch has no fresh lineages left and no lineage is in flight (traced or
 // queued).  A warp with nothing to do waits at most watchdog_ns for work;
 // waits on a queue slot are bounded the same way.
+//
+// As in k_trace, each warp alternates a search phase (every lane with a ray
+// steps through its tile's hierarchy one node at a time, until kRefillLanes
+// lanes need service or none is searching) and a service phase (finished
+// searches write their segment and reflect, escape, or are handed to the
+// next tile; lanes without a lineage take hand-offs or fresh lineages; new
+// searches start), so a long search does not hold the whole warp.
 // Six resident blocks per SM, as for k_trace.
 template <int kP, bool kCount>
 __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, const __grid_constant__ TiledArgs ta) {
@@ -1006,98 +1023,31 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, c
   const int n_batch = (int)(a.lineage_end - a.lineage_begin);
   int credits = 0;  // warp-uniform
   LaneState ls = {-1, 0, -1, 0.0f, 0.0};
-  bool active = false;
+  bool active = false;      // the lane holds a lineage
+  bool searching = false;   // its search in the current tile is under way
+  bool pending = false;     // its search is over and awaits service
   int tile = -1;
-  bool exhausted = false;  // warp-uniform: the batch has no fresh lineages left
+  float tlim = kInf;        // hits are accepted up to this distance
+  bool exhausted = false;   // warp-uniform: the batch has no fresh lineages left
   const int home = (int)((blockIdx.x * (kTraceThreads / 32) + (threadIdx.x >> 5)) % (unsigned)ta.n_tiles);
   unsigned long long idle_since = 0, last_prog = 0;
+  HitSearch hs;
+  hs.start(-1);
+  int stack[kStackDepth];
   const RaySrc rs{&sm.hi[kRowO][t], kMixed ? &sm.lo[kRowO][t] : &sm.hi[kRowO][t], kTraceThreads,
                   kF64 ? &sm.dv[kRowO][t] : nullptr};
   while (true) {
-    // ---- refill: hand-offs first (home tile, then steals), then fresh lineages
-    unsigned nm = __ballot_sync(0xffffffffu, !active);
-    if (nm) {
-      unsigned base;
-      int got;
-      int qt = take_handoffs(ta, home, __popc(nm), base, got);
-      if (qt >= 0 && !active) {
-        int rank = __popc(nm & below);
-        if (rank < got) {
-          unsigned pos = base + (unsigned)rank, gen = pos & ~qmask, slot = pos & qmask;
-          unsigned *sq = ta.seq + (size_t)qt * qc + slot;
-          // the item is counted in avail only after it is written, but the
-          // position handed out may belong to a producer still writing
-          if (wait_slot(a, ta, sq, gen + 1u)) {
-            load_state(ta.ring + (size_t)qt * kStateRows * qc + slot, qc, sm, t, ls);
-            st_release_u32(sq, gen + ta.qcap);
-            tile = qt;
-            active = true;
-            if (qt != home) cn[kCSteal]++;
-          }
-        }
-      }
-      nm = __ballot_sync(0xffffffffu, !active);
-      if (nm && !exhausted) {
-        int64_t fb;
-        int got_f = take_fresh(a, ta, __popc(nm), credits, fb, exhausted);
-        int rank = __popc(nm & below);
-        if (!active && rank < got_f) {
-          int64_t mine = a.lineage_begin + fb + rank;
-          ls = LaneState{mine, 0, -1, 0.0f, 0.0};
-          init_lineage(v, sm, t, mine);
-          active = true;
-          float3 o = ld_hi3(sm, kRowO, t);
-          tile = clampi((int)floorf((o.y - tg.gy0) / tg.wy), 0, tg.ty - 1) * tg.tx +
-                 clampi((int)floorf((o.x - tg.gx0) / tg.wx), 0, tg.tx - 1);
-        }
-      }
-    }
-    if (!__any_sync(0xffffffffu, active)) {
-      // nothing to trace: done once every lineage of the batch has finished
-      const int fin = *(volatile int *)finished;
-      if (fin == n_batch) break;
-      if (*(volatile int *)&a.ctr->error) break;
-      // the watchdog runs while the launch as a whole makes no progress: no
-      // fresh lineage taken and none finished (both counts only grow)
-      const unsigned long long now = global_ns();
-      const unsigned long long prog = *(volatile unsigned long long *)a.lineage_next + (unsigned)fin;
-      if (idle_since == 0 || prog != last_prog) {
-        idle_since = now;
-        last_prog = prog;
-      } else if (now - idle_since > ta.watchdog_ns) {
-        if (lane == 0) watchdog_fired(a);
-        break;
-      }
-      __nanosleep(128);
-      continue;
-    }
-    idle_since = 0;
-    // ---- search the current tile for this lane's ray
+    // ---- service: finished searches write their segment and reflect, end,
+    // or go on to the next tile
+    bool start = false, ended = false;
     int next = -1;
-    bool ended = false;
-    const unsigned act_mask = __ballot_sync(0xffffffffu, active);
-    if (active) {
+    if (__ballot_sync(0xffffffffu, pending) && pending) {
+      pending = false;
       const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), v.t_eps, ls.dns);
-      Best best;
-      // Hits are searched up to 1 cm past the ray's exit from the tile (the
-      // tile lists hold every triangle within 5 cm of the tile): a hit there
-      // is the ray's first, and a ray with none goes on to the next tile.
-      float t_exit;
-      {
-        const int ix = tile % tg.tx, iy = tile / tg.tx;
-        float tex = kInf, tey = kInf;
-        if (r.d.x > 0.0f) tex = (tg.gx0 + (ix + 1) * tg.wx - r.o.x) / r.d.x;
-        else if (r.d.x < 0.0f) tex = (tg.gx0 + ix * tg.wx - r.o.x) / r.d.x;
-        if (r.d.y > 0.0f) tey = (tg.gy0 + (iy + 1) * tg.wy - r.o.y) / r.d.y;
-        else if (r.d.y < 0.0f) tey = (tg.gy0 + iy * tg.wy - r.o.y) / r.d.y;
-        t_exit = fminf(tex, tey) + kTileEps;
-      }
-      int hit = closest_hit<kP, kCount>(v.sc, r, rs, ls.dns64, best, &a.ctr->error, cn[kCNodes], cn[kCTris],
-                                        __ldg(&ta.roots[tile]), t_exit);
-      __syncwarp(act_mask);  // reconverge after the traversal loop (see k_trace)
-      if (hit >= 0) {
+      if (hs.best.slot >= 0) {
         // the hit lies in this tile; a reflected beam starts here as well
-        if (!finish_segment(a, v, 0, sm, t, r, best, hit, ls, cn)) ended = true;
+        if (finish_segment(a, v, 0, sm, t, r, hs.best, hs.best.slot, ls, cn)) start = true;
+        else ended = true;
       } else {
         // no hit in this tile: step to the next tile along the ray whose
         // geometry the ray can reach -- tiles whose root boxes it misses
@@ -1120,7 +1070,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, c
         }
         if (leaves) {
           // the ray leaves the grid, and with it every triangle: it escapes
-          finish_segment(a, v, 0, sm, t, r, best, -1, ls, cn);
+          finish_segment(a, v, 0, sm, t, r, hs.best, -1, ls, cn);
           ended = true;
         } else {
           next = iy * tg.tx + ix;
@@ -1160,6 +1110,93 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, c
       if ((int)lane == gl) atomicAdd(&ta.ctl[2 * ta.n_tiles + next], n);
       cn[kCHand]++;
       active = false;
+    }
+    // ---- refill: hand-offs first (home tile, then steals), then fresh lineages
+    unsigned nm = __ballot_sync(0xffffffffu, !active);
+    if (nm) {
+      unsigned base;
+      int got;
+      int qt = take_handoffs(ta, home, __popc(nm), base, got);
+      if (qt >= 0 && !active) {
+        int rank = __popc(nm & below);
+        if (rank < got) {
+          unsigned pos = base + (unsigned)rank, gen = pos & ~qmask, slot = pos & qmask;
+          unsigned *sq = ta.seq + (size_t)qt * qc + slot;
+          // the item is counted in avail only after it is written, but the
+          // position handed out may belong to a producer still writing
+          if (wait_slot(a, ta, sq, gen + 1u)) {
+            load_state(ta.ring + (size_t)qt * kStateRows * qc + slot, qc, sm, t, ls);
+            st_release_u32(sq, gen + ta.qcap);
+            tile = qt;
+            active = true;
+            start = true;
+            if (qt != home) cn[kCSteal]++;
+          }
+        }
+      }
+      nm = __ballot_sync(0xffffffffu, !active);
+      if (nm && !exhausted) {
+        int64_t fb;
+        int got_f = take_fresh(a, ta, __popc(nm), credits, fb, exhausted);
+        int rank = __popc(nm & below);
+        if (!active && rank < got_f) {
+          int64_t mine = a.lineage_begin + fb + rank;
+          ls = LaneState{mine, 0, -1, 0.0f, 0.0};
+          init_lineage(v, sm, t, mine);
+          active = true;
+          start = true;
+          float3 o = ld_hi3(sm, kRowO, t);
+          tile = clampi((int)floorf((o.y - tg.gy0) / tg.wy), 0, tg.ty - 1) * tg.tx +
+                 clampi((int)floorf((o.x - tg.gx0) / tg.wx), 0, tg.tx - 1);
+        }
+      }
+    }
+    if (start) {
+      // Hits are searched up to 1 cm past the ray's exit from the tile (the
+      // tile lists hold every triangle within 5 cm of the tile): a hit there
+      // is the ray's first, and a ray with none goes on to the next tile.
+      const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), v.t_eps, ls.dns);
+      tlim = tile_exit(tg, tile % tg.tx, tile / tg.tx, r) + kTileEps;
+      hs.start(__ldg(&ta.roots[tile]));
+      searching = true;
+    }
+    if (!__any_sync(0xffffffffu, active)) {
+      // nothing to trace: done once every lineage of the batch has finished
+      const int fin = *(volatile int *)finished;
+      if (fin == n_batch) break;
+      if (*(volatile int *)&a.ctr->error) break;
+      // the watchdog runs while the launch as a whole makes no progress: no
+      // fresh lineage taken and none finished (both counts only grow)
+      const unsigned long long now = global_ns();
+      const unsigned long long prog = *(volatile unsigned long long *)a.lineage_next + (unsigned)fin;
+      if (idle_since == 0 || prog != last_prog) {
+        idle_since = now;
+        last_prog = prog;
+      } else if (now - idle_since > ta.watchdog_ns) {
+        if (lane == 0) watchdog_fired(a);
+        break;
+      }
+      __nanosleep(128);
+      continue;
+    }
+    idle_since = 0;
+    // ---- search: until kRefillLanes lanes need service (a finished search,
+    // or no lineage while fresh ones remain) or no lane is searching
+    {
+      const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), v.t_eps, ls.dns);
+      const int64_t n_tri = v.sc.n_tris;
+      const Node *const nodes = v.sc.nodes;
+      const Tri *const tris = v.sc.tris;
+      while (true) {
+        if (searching && !hs.step<kP, kCount>(v.sc, nodes, tris, n_tri, r, rs, ls.dns64, stack, &a.ctr->error,
+                                              cn[kCNodes], cn[kCTris], tlim)) {
+          searching = false;
+          pending = true;
+        }
+        const unsigned srch = __ballot_sync(0xffffffffu, searching);
+        const unsigned idle = __ballot_sync(0xffffffffu, pending || (!active && !exhausted));
+        if (!srch || __popc(idle) >= kRefillLanes) break;
+      }
     }
   }
   flush_counts(a, cn, kCount);
