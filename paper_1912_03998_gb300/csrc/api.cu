@@ -5,6 +5,7 @@
 // ordered on the context's stream.
 #include <math.h>
 #include <stdarg.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -668,6 +669,18 @@ static int64_t default_chunk(int max_order) {
   return budget / ((int64_t)sizeof(bt::Seg) * (max_order + 1));
 }
 
+// Lineages per launch: the caller's chunk_beams, else default_chunk, at most
+// the whole batch, and small enough that a launch's segment records are
+// indexed by int32 (the scatter keeps record indices in 32 bits).
+static int64_t launch_chunk(int32_t chunk_beams, int64_t total, int max_order) {
+  int64_t chunk = chunk_beams > 0 ? chunk_beams : default_chunk(max_order);
+  const int64_t max_chunk = (int64_t)INT32_MAX / (max_order + 1);
+  if (chunk > max_chunk) chunk = max_chunk;
+  if (chunk > total) chunk = total;
+  if (chunk < 1) chunk = 1;
+  return chunk;
+}
+
 // Check the trace parameters p for scene s; derive the air damping exponents.
 static int check_params(bt_ctx *c, SceneState *s, const bt_trace_params *p, float *alpha_log2, int *has_alpha) {
   if (!p) return fail(c, BT_E_INVALID, "NULL params");
@@ -709,11 +722,8 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   const bool tiled = p->tiles_x * p->tiles_y > 1;
   const int T = p->tiles_x * p->tiles_y;
   // One persistent launch per group of lineages: fewer, larger groups mean
-  // fewer launch tails.  The segment records of a group are kept near 8 GiB,
-  // a small part of the device.
-  int64_t chunk = p->chunk_beams > 0 ? p->chunk_beams : default_chunk(p->max_order);
-  if (chunk > total) chunk = total;
-  if (chunk < 1) chunk = 1;
+  // fewer launch tails.
+  const int64_t chunk = launch_chunk(p->chunk_beams, total, p->max_order);
   const unsigned long long cap = (unsigned long long)chunk * (p->max_order + 1);
   TRY(ensure(c, c->segs, sizeof(bt::Seg) * cap));
   // Hand-off queues: at most qcap lineages are in flight (traced or queued),
@@ -1016,12 +1026,9 @@ BT_API int bt_batch_create(bt_ctx *c, const int32_t *scene_ids, int32_t n_scenes
       }
     }
     if (rc) break;
-    int64_t chunk = params[0].chunk_beams > 0 ? params[0].chunk_beams : default_chunk(b->max_order);
-    if (chunk > b->total) chunk = b->total;
-    if (chunk < 1) chunk = 1;
-    b->chunk = chunk;
+    b->chunk = launch_chunk(params[0].chunk_beams, b->total, b->max_order);
     if ((rc = ensure(c, b->views, sizeof(bt::SceneView) * (size_t)n_scenes))) break;
-    if ((rc = ensure(c, b->segs, sizeof(bt::Seg) * (size_t)chunk * (b->max_order + 1)))) break;
+    if ((rc = ensure(c, b->segs, sizeof(bt::Seg) * (size_t)b->chunk * (b->max_order + 1)))) break;
     if (cudaMalloc(&b->d_ctr, sizeof(bt::Counters)) != cudaSuccess ||
         cudaMallocHost(&b->h_ctr, sizeof(bt::Counters)) != cudaSuccess ||
         cudaMalloc(&b->d_cursors, 2 * sizeof(unsigned long long)) != cudaSuccess) {
@@ -1225,9 +1232,7 @@ BT_API int bt_trace_ranges(bt_ctx *c, int32_t n, const int32_t *scene_ids, const
       hv[i].beam_table = (const float *)t.p;
     }
   }
-  int64_t chunk = params[0].chunk_beams > 0 ? params[0].chunk_beams : default_chunk(kmax);
-  if (chunk > total) chunk = total;
-  if (chunk < 1) chunk = 1;
+  const int64_t chunk = launch_chunk(params[0].chunk_beams, total, kmax);
   const unsigned long long cap = (unsigned long long)chunk * (kmax + 1);
   TRY(ensure(c, c->segs, sizeof(bt::Seg) * cap));
   TRY(ensure(c, c->views, sizeof(bt::SceneView) * (size_t)n));
@@ -1240,10 +1245,20 @@ BT_API int bt_trace_ranges(bt_ctx *c, int32_t n, const int32_t *scene_ids, const
       CK(cudaMemsetAsync(s.count.p, 0, sizeof(int) * (size_t)s.n_mics, st));
     }
   }
+  // One scene: the single-scene kernels, with the view in kernel parameters
+  // and the scene's own lineage indices; several: the batch kernels over the
+  // ranges laid end to end.
+  const bool single = n == 1;
+  const int64_t first = single ? lineage_begin[0] : 0;
   bt::TraceArgs ta;
   memset(&ta, 0, sizeof(ta));
-  ta.views = (const bt::SceneView *)c->views.p;
-  ta.n_views = n;
+  if (single) {
+    ta.v = hv[0];
+    ta.v.lineage_first = 0;
+  } else {
+    ta.views = (const bt::SceneView *)c->views.p;
+    ta.n_views = n;
+  }
   ta.segs = (bt::Seg *)c->segs.p;
   ta.seg_count = c->d_seg_count;
   ta.lineage_next = c->d_lineage_next;
@@ -1254,8 +1269,9 @@ BT_API int bt_trace_ranges(bt_ctx *c, int32_t n, const int32_t *scene_ids, const
   ta.blocks_per_sm = params[0].blocks_per_sm;
   bt::ScatterArgs sa;
   memset(&sa, 0, sizeof(sa));
+  sa.v = ta.v;
   sa.views = ta.views;
-  sa.n_views = n;
+  sa.n_views = ta.n_views;
   sa.fp64 = prec == BT_PREC_FP64 ? 1 : 0;
   sa.max_nz = max_nz;
   sa.segs = ta.segs;
@@ -1265,8 +1281,8 @@ BT_API int bt_trace_ranges(bt_ctx *c, int32_t n, const int32_t *scene_ids, const
   CK(cudaEventRecord(c->ev0, st));
   const int64_t n_chunks = total > 0 ? (total + chunk - 1) / chunk : 0;
   for (int64_t ci = 0; ci < n_chunks; ci++) {
-    ta.lineage_begin = ci * chunk;
-    ta.lineage_end = ta.lineage_begin + chunk < total ? ta.lineage_begin + chunk : total;
+    ta.lineage_begin = first + ci * chunk;
+    ta.lineage_end = ci * chunk + chunk < total ? ta.lineage_begin + chunk : first + total;
     CK(cudaMemsetAsync(c->d_seg_count, 0, sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(c->d_lineage_next, 0, sizeof(unsigned long long), st));
     CK(bt::launch_trace(st, ta, c->n_sm));

@@ -109,28 +109,44 @@ __device__ __forceinline__ int seg_footprint(const Seg &s, const MicGrid &g, int
 // ------------------------------------------------------------------ scatter
 // Per-warp shared state of the scatter: 32 segments, one per lane, stored as
 // [field][lane] so that lanes reading different segments hit different banks.
+// The rows hold what every candidate reads; what only the rare float-pair
+// re-tests (and every FP64 test) need -- the cone normals' low parts, the
+// apex's third word, the start and end planes' triangle slots -- is read
+// from the segment record (F_SI) when needed.
 constexpr int kScatterWarps = 4;
 enum : int {
-  F_AX = 0, F_RX = 3, F_N0 = 6, F_NLO = 15, F_NS = 24, F_NE = 28, F_P = 32, F_SLOTS = 40,
-  F_CY0 = 42, F_PN = 43, F_VI = 44, F_LAYER = 45, F_PX = 46, F_PY = F_PX + kPolyMax,
-  // rows only some variants use: the apex's third word (FP64) and the
-  // view's microphone array (batches)
-  F_AP = F_PY + kPolyMax, F_MP = F_AP + 3, F_COUNT = F_MP + 2
+  F_AX = 0, F_RX = 3, F_N0 = 6, F_NS = 15, F_NE = 19, F_P = 23, F_SI = 31, F_CY0 = 32, F_PN = 33,
+  F_VI = 34, F_LAYER = 35, F_PX = 36, F_PY = F_PX + kPolyMax,
+  // batches only: the view's microphone array, accumulators and band count
+  // (plus an air-damping flag), read for every candidate
+  F_MP = F_PY + kPolyMax, F_EP = F_MP + 2, F_CP = F_EP + 2, F_FL = F_CP + 2, F_COUNT = F_FL + 1
 };
 // While a lane clips its footprint, its columns of the rows below F_PX
 // (written only afterwards) hold the clip's second vertex buffer.
 constexpr int F_QX = 0, F_QY = kPolyMax;
 static_assert(F_QY + kPolyMax <= F_PX, "clip scratch overlaps the polygon rows");
-// Rows a variant needs; the single-scene float32 / float-pair variant fits
-// six 128-thread blocks per SM.
-template <bool kF64, bool kBatch>
+// Rows a variant needs: 60 for one scene, 67 for a batch, either way six
+// 128-thread blocks per SM.
+template <bool kBatch>
 constexpr int scatter_rows() {
-  return kBatch ? F_COUNT : kF64 ? F_AP + 3 : F_AP;
+  return kBatch ? F_COUNT : F_MP;
 }
-template <bool kF64, bool kBatch>
+template <bool kBatch>
 struct ScatterSmem {
-  float f[kScatterWarps][scatter_rows<kF64, kBatch>()][32];
+  float f[kScatterWarps][scatter_rows<kBatch>()][32];
 };
+
+// A pointer kept as two float rows (bit patterns).
+__device__ __forceinline__ void put_ptr(float (*F)[32], int row, unsigned lane, const void *p) {
+  const unsigned long long u = (unsigned long long)p;
+  F[row][lane] = __uint_as_float((unsigned)u);
+  F[row + 1][lane] = __uint_as_float((unsigned)(u >> 32));
+}
+template <typename T>
+__device__ __forceinline__ T *get_ptr(const float (*F)[32], int row, int s) {
+  return (T *)((unsigned long long)__float_as_uint(F[row][s]) |
+               ((unsigned long long)__float_as_uint(F[row + 1][s]) << 32));
+}
 
 __device__ __forceinline__ int warp_incl_scan(int v, unsigned lane) {
   for (int o = 1; o < 32; o <<= 1) {
@@ -183,7 +199,7 @@ __device__ __forceinline__ double plane_side64(const SceneView &a, int slot, flo
 // the footprint sizes.
 template <bool kF64, bool kBatch>
 __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
-  __shared__ ScatterSmem<kF64, kBatch> sm;
+  __shared__ ScatterSmem<kBatch> sm;
   const unsigned lane = lane_id();
   const int w = threadIdx.x >> 5;
   float(*F)[32] = sm.f[w];
@@ -228,25 +244,26 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
       }
       nrows = cy1 >= cy0 ? cy1 - cy0 + 1 : 0;
       if (nrows > 0) {
-#pragma unroll
-        for (int q = 7; q < (int)(sizeof(Seg) / 16); q++) dst4[q] = __ldg(src4 + q);
+        // band powers (p03, p47); the normals' low parts stay in the record
+        dst4[7] = __ldg(src4 + 7);
+        dst4[8] = __ldg(src4 + 8);
         F[F_VI][lane] = __int_as_float(vi);
+        F[F_SI][lane] = __int_as_float((int)si);
         if (kBatch) {
-          // the view's microphone array, read for every candidate
-          const unsigned long long mp = (unsigned long long)a.views[vi].mics;
-          F[F_MP][lane] = __uint_as_float((unsigned)mp);
-          F[F_MP + 1][lane] = __uint_as_float((unsigned)(mp >> 32));
+          const SceneView &V = a.views[vi];
+          put_ptr(F, F_MP, lane, V.mics);
+          put_ptr(F, F_EP, lane, V.energy);
+          put_ptr(F, F_CP, lane, V.count);
+          F[F_FL][lane] = __int_as_float(V.sc.n_bands | (V.has_alpha ? 0x100 : 0));
         }
         F[F_LAYER][lane] = __int_as_float(layer);
         for (int q = 0; q < 3; q++) {
           F[F_AX + q][lane] = sl.ahi[q];
           F[F_RX + q][lane] = sl.alo[q];
-          if (kF64) F[F_AP + q][lane] = sl.pad[q];
         }
         F[F_N0][lane] = sl.n0.x; F[F_N0 + 1][lane] = sl.n0.y; F[F_N0 + 2][lane] = sl.n0.z;
         F[F_N0 + 3][lane] = sl.n1.x; F[F_N0 + 4][lane] = sl.n1.y; F[F_N0 + 5][lane] = sl.n1.z;
         F[F_N0 + 6][lane] = sl.n2.x; F[F_N0 + 7][lane] = sl.n2.y; F[F_N0 + 8][lane] = sl.n2.z;
-        for (int q = 0; q < 9; q++) F[F_NLO + q][lane] = sl.nlo[q];
         F[F_NS][lane] = sl.start.x; F[F_NS + 1][lane] = sl.start.y; F[F_NS + 2][lane] = sl.start.z;
         F[F_NS + 3][lane] = sl.start.w;
         F[F_NE][lane] = sl.end.x; F[F_NE + 1][lane] = sl.end.y; F[F_NE + 2][lane] = sl.end.z;
@@ -254,8 +271,6 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
         F[F_P][lane] = sl.p03.x; F[F_P + 1][lane] = sl.p03.y; F[F_P + 2][lane] = sl.p03.z;
         F[F_P + 3][lane] = sl.p03.w; F[F_P + 4][lane] = sl.p47.x; F[F_P + 5][lane] = sl.p47.y;
         F[F_P + 6][lane] = sl.p47.z; F[F_P + 7][lane] = sl.p47.w;
-        F[F_SLOTS][lane] = sl.n0.w;      // start-plane triangle slot (int bits)
-        F[F_SLOTS + 1][lane] = sl.n1.w;  // end-plane triangle slot (int bits)
         F[F_CY0][lane] = __int_as_float(cy0);
         F[F_PN][lane] = __int_as_float(pn);
       }
@@ -315,30 +330,50 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
         int s = __shfl_sync(0xffffffffu, so, ro);
         if (c < total_c) {
           int mi = ofirst + (c - oexcl);
-          const SceneView &V = kBatch ? a.views[__float_as_int(F[F_VI][s])] : a.v;
-          const float4 *mics = kBatch ? (const float4 *)((unsigned long long)__float_as_uint(F[F_MP][s]) |
-                                                         ((unsigned long long)__float_as_uint(F[F_MP + 1][s]) << 32))
-                                      : a.v.mics;
+          // where the contribution goes: the scene's accumulators, band
+          // count and air damping (kernel parameters for one scene, the
+          // segment's rows in a batch)
+          const float4 *mics;
+          double *energy;
+          int *count;
+          int nb;
+          bool has_alpha;
+          if (kBatch) {
+            mics = get_ptr<const float4>(F, F_MP, s);
+            energy = get_ptr<double>(F, F_EP, s);
+            count = get_ptr<int>(F, F_CP, s);
+            const int fl = __float_as_int(F[F_FL][s]);
+            nb = fl & 0xff;
+            has_alpha = (fl & 0x100) != 0;
+          } else {
+            mics = a.v.mics;
+            energy = a.v.energy;
+            count = a.v.count;
+            nb = a.v.sc.n_bands;
+            has_alpha = a.v.has_alpha != 0;
+          }
+          const Seg *rec = a.segs + __float_as_int(F[F_SI][s]);
           float4 m = __ldg(&mics[mi]);
           if (kF64) {
             // FP64: every test and the contribution in float64 (apex exact
             // from its three words, cone normals from their float pairs,
             // start/end planes from the triangles' float64 planes)
             n_cand++;
-            const double3 A = make_double3(((double)F[F_AX][s] + F[F_RX][s]) + F[F_AP][s],
-                                           ((double)F[F_AX + 1][s] + F[F_RX + 1][s]) + F[F_AP + 1][s],
-                                           ((double)F[F_AX + 2][s] + F[F_RX + 2][s]) + F[F_AP + 2][s]);
+            const double3 A = make_double3(((double)F[F_AX][s] + F[F_RX][s]) + __ldg(&rec->pad[0]),
+                                           ((double)F[F_AX + 1][s] + F[F_RX + 1][s]) + __ldg(&rec->pad[1]),
+                                           ((double)F[F_AX + 2][s] + F[F_RX + 2][s]) + __ldg(&rec->pad[2]));
             const double3 vd = make_double3((double)m.x - A.x, (double)m.y - A.y, (double)m.z - A.z);
             bool in = true;
 #pragma unroll
             for (int j = 0; j < 3; j++) {
-              double3 nd = make_double3((double)F[F_N0 + 3 * j][s] + F[F_NLO + 3 * j][s],
-                                        (double)F[F_N0 + 3 * j + 1][s] + F[F_NLO + 3 * j + 1][s],
-                                        (double)F[F_N0 + 3 * j + 2][s] + F[F_NLO + 3 * j + 2][s]);
+              double3 nd = make_double3((double)F[F_N0 + 3 * j][s] + __ldg(&rec->nlo[3 * j]),
+                                        (double)F[F_N0 + 3 * j + 1][s] + __ldg(&rec->nlo[3 * j + 1]),
+                                        (double)F[F_N0 + 3 * j + 2][s] + __ldg(&rec->nlo[3 * j + 2]));
               in = in && dot3(nd, vd) >= 0.0;
             }
             if (in) {
-              int s_slot = __float_as_int(F[F_SLOTS][s]), e_slot = __float_as_int(F[F_SLOTS + 1][s]);
+              const SceneView &V = kBatch ? a.views[__float_as_int(F[F_VI][s])] : a.v;
+              int s_slot = __float_as_int(__ldg(&rec->n0.w)), e_slot = __float_as_int(__ldg(&rec->n1.w));
               float3 ns = make_float3(F[F_NS][s], F[F_NS + 1][s], F[F_NS + 2][s]);
               float3 ne = make_float3(F[F_NE][s], F[F_NE + 1][s], F[F_NE + 2][s]);
               double fs = s_slot >= 0 ? plane_side64(V, s_slot, ns, m) : 1.0;
@@ -348,17 +383,18 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
             const double d2 = dot3(vd, vd);
             if (in && d2 > 1e-18) {
               const double gf = 1.0 / (4.0 * 3.141592653589793 * d2);
-              const double dist = V.has_alpha ? sqrt(d2) : 0.0;
-              double *e = V.energy + (size_t)mi * kMaxBands;
+              const double dist = has_alpha ? sqrt(d2) : 0.0;
+              const float *alpha = (kBatch ? a.views[__float_as_int(F[F_VI][s])] : a.v).alpha_log2;
+              double *e = energy + (size_t)mi * kMaxBands;
 #pragma unroll
               for (int b = 0; b < kMaxBands; b++) {
-                if (b < V.sc.n_bands) {
+                if (b < nb) {
                   double cval = (double)F[F_P + b][s] * gf;
-                  if (V.has_alpha) cval *= exp2((double)V.alpha_log2[b] * dist);
+                  if (has_alpha) cval *= exp2((double)alpha[b] * dist);
                   atomicAdd(e + b, cval);
                 }
               }
-              atomicAdd(V.count + mi, 1);
+              atomicAdd(count + mi, 1);
               n_contrib++;
             }
             continue;
@@ -376,8 +412,8 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
             float3 nj = make_float3(F[F_N0 + 3 * j][s], F[F_N0 + 3 * j + 1][s], F[F_N0 + 3 * j + 2][s]);
             float e = dot3(nj, v);
             if (fabsf(e) <= band_v * (fabsf(nj.x) + fabsf(nj.y) + fabsf(nj.z))) {
-              df3 nd = df3{df{nj.x, F[F_NLO + 3 * j][s]}, df{nj.y, F[F_NLO + 3 * j + 1][s]},
-                           df{nj.z, F[F_NLO + 3 * j + 2][s]}};
+              df3 nd = df3{df{nj.x, __ldg(&rec->nlo[3 * j])}, df{nj.y, __ldg(&rec->nlo[3 * j + 1])},
+                           df{nj.z, __ldg(&rec->nlo[3 * j + 2])}};
               df ed = df3_dot(nd, rel_df(F, s, m));
               e = ed.hi + ed.lo;
             }
@@ -391,25 +427,30 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
             float3 ne = make_float3(F[F_NE][s], F[F_NE + 1][s], F[F_NE + 2][s]);
             float band = 1e-4f + 1e-6f * (fabsf(v.x) + fabsf(v.y) + fabsf(v.z));
             float fs = dot3(ns, v) - F[F_NS + 3][s], fe = dot3(ne, v) - F[F_NE + 3][s];
-            int s_slot = __float_as_int(F[F_SLOTS][s]), e_slot = __float_as_int(F[F_SLOTS + 1][s]);
-            if (fabsf(fs) <= band && s_slot >= 0) fs = plane_side_df(V, s_slot, ns, m);
-            if (fabsf(fe) <= band && e_slot >= 0) fe = plane_side_df(V, e_slot, ne, m);
+            if (fabsf(fs) <= band || fabsf(fe) <= band) {
+              const SceneView &V = kBatch ? a.views[__float_as_int(F[F_VI][s])] : a.v;
+              int s_slot = __float_as_int(__ldg(&rec->n0.w)), e_slot = __float_as_int(__ldg(&rec->n1.w));
+              if (fabsf(fs) <= band && s_slot >= 0) fs = plane_side_df(V, s_slot, ns, m);
+              if (fabsf(fe) <= band && e_slot >= 0) fe = plane_side_df(V, e_slot, ne, m);
+            }
             in = fs > 0.0f && fe >= 0.0f;
           }
           float d2 = dot3(v, v);
           if (in && d2 > 1e-18f) {
             float gf = 1.0f / (4.0f * 3.14159265358979f * d2);
-            float dist = V.has_alpha ? sqrtf(d2) : 0.0f;
-            double *e = V.energy + (size_t)mi * kMaxBands;
+            float dist = has_alpha ? sqrtf(d2) : 0.0f;
+            double *e = energy + (size_t)mi * kMaxBands;
+            if (has_alpha) {
+              const float *alpha = (kBatch ? a.views[__float_as_int(F[F_VI][s])] : a.v).alpha_log2;
 #pragma unroll
-            for (int b = 0; b < kMaxBands; b++) {
-              if (b < V.sc.n_bands) {
-                float cval = F[F_P + b][s] * gf;
-                if (V.has_alpha) cval *= exp2f(V.alpha_log2[b] * dist);
-                atomicAdd(e + b, (double)cval);
-              }
+              for (int b = 0; b < kMaxBands; b++)
+                if (b < nb) atomicAdd(e + b, (double)(F[F_P + b][s] * gf * exp2f(alpha[b] * dist)));
+            } else {
+#pragma unroll
+              for (int b = 0; b < kMaxBands; b++)
+                if (b < nb) atomicAdd(e + b, (double)(F[F_P + b][s] * gf));
             }
-            atomicAdd(&V.count[mi], 1);
+            atomicAdd(&count[mi], 1);
             n_contrib++;
           }
         }

@@ -6,10 +6,10 @@ sources with band powers, a microphone set, a reflection order) gets a scene
 that shares its city's geometry (bt_scene_share) for its own sources,
 microphones and result.  The server runs in steps.  Before a step it admits
 waiting queries in arrival order while a scene slot is free and their device
-memory fits the budget; a step then traces the next lineages of every
-admitted query -- first up to a small quantum each, so that small queries
-finish at once, then the rest of the step's lineage budget in admission
-order -- in the same persistent launches
+memory fits the budget; a step then traces the next lineages of the admitted
+queries -- the step's lineage budget in order of remaining work (shortest
+remaining first, optionally with a small quantum for each query the budget
+did not reach) -- in the same persistent launches
 (bt_trace_ranges, accumulating), so queries that arrive while others are on
 the GPU join at the next step and their work overlaps on the device.  A query
 whose lineages are all traced is read back (levels to the host), its scene
@@ -54,10 +54,12 @@ class Done:
 
 
 class Server:
-    def __init__(self, tracer, cities, step_lineages: int = 1 << 21, quantum: int = 1 << 16,
-                 mem_budget: int = 4 << 30, max_active: int = 48, precision: int = btrace.BT_PREC_MIXED):
+    def __init__(self, tracer, cities, step_lineages: int = 1 << 21, quantum: int = 0,
+                 mem_budget: int = 4 << 30, max_active: int = 48, precision: int = btrace.BT_PREC_MIXED,
+                 oldest_share: float = 0.0):
         self.tr = tracer
         self.quantum = int(quantum)
+        self.oldest_share = float(oldest_share)
         self.city_ids = [tracer.load_geometry(w) for w in cities]
         self.step_lineages = int(step_lineages)
         self.mem_budget = int(mem_budget)
@@ -103,19 +105,31 @@ class Server:
         self.host_s["admit"] += t1 - t0
         if not self.active:
             return False
-        # every active query first gets up to `quantum` lineages, so that a
-        # small query finishes in the step after its arrival; the rest of the
-        # step's budget goes to the queries in admission order
+        # shortest remaining work first (SRPT): the step's lineage budget goes
+        # to the active queries in order of remaining work, lineages times
+        # segments per lineage (K + 1), so small queries finish in the step
+        # after their arrival and a big one takes what is left; with a
+        # nonzero `quantum` every query the budget did not reach still gets
+        # that many lineages
         left = [a["total"] - a["next"] for a in self.active]
-        quantum = max(1, min(self.quantum, self.step_lineages // len(left)))
-        share = [min(r, quantum) for r in left]
-        budget = self.step_lineages - sum(share)
-        for i, r in enumerate(left):
+        order = sorted(range(len(left)), key=lambda i: left[i] * (self.active[i]["q"].max_order + 1))
+        share = [0] * len(left)
+        budget = self.step_lineages
+        if self.oldest_share > 0.0:
+            # the oldest admitted query first takes its share of the budget
+            share[0] = min(left[0], int(self.step_lineages * self.oldest_share))
+            budget -= share[0]
+        for i in order:
             if budget <= 0:
                 break
-            g = min(r - share[i], budget)
+            g = min(left[i] - share[i], budget)
             share[i] += g
             budget -= g
+        if budget <= 0 and self.quantum > 0:
+            quantum = max(1, min(self.quantum, self.step_lineages // len(left)))
+            for i in order:
+                if share[i] == 0 and left[i] > 0:
+                    share[i] = min(left[i], quantum)
         ids, begins, ends, params = [], [], [], []
         for a, s in zip(self.active, share):
             if s > 0:
@@ -173,8 +187,11 @@ class Server:
         self.city_ids = []
 
 
-def run_plain(tracer, city_ids, queries, precision: int = btrace.BT_PREC_MIXED, realtime: bool = True):
-    """The same stream served one query at a time, each traced whole."""
+def run_plain(tracer, city_ids, queries, precision: int = btrace.BT_PREC_MIXED, realtime: bool = True,
+              gpu_s=None):
+    """The same stream served one query at a time, each traced whole.  With
+    `gpu_s` (a one-element list) the device time of the traces is added to
+    gpu_s[0] in seconds."""
     ctx = tracer.ctx
     t0 = time.perf_counter()
     done = []
@@ -191,7 +208,9 @@ def run_plain(tracer, city_ids, queries, precision: int = btrace.BT_PREC_MIXED, 
         n, nb = len(q.mics), q.power.shape[1]
         level = np.empty((n, nb), np.float64)
         count = np.empty(n, np.int32)
-        btrace.bt_read_levels(ctx, sid, level, None, count)
+        st = btrace.bt_read_levels(ctx, sid, level, None, count)
+        if gpu_s is not None:
+            gpu_s[0] += st["trace_ms"] * 1e-3
         btrace.bt_unload_scene(ctx, sid)
         done.append(Done(i, q.arrival_s if realtime else 0.0, start, time.perf_counter() - t0, level, count))
     return done
