@@ -7,9 +7,8 @@ that shares its city's geometry (bt_scene_share) for its own sources,
 microphones and result.  The server runs in steps.  Before a step it admits
 waiting queries in arrival order while a scene slot is free and their device
 memory fits the budget; a step then traces the next lineages of the admitted
-queries -- the step's lineage budget in order of remaining work (shortest
-remaining first, optionally with a small quantum for each query the budget
-did not reach) -- in the same persistent launches
+queries -- the step's lineage budget first to the oldest query, the rest to
+the others shortest remaining work first -- in the same persistent launches
 (bt_trace_ranges, accumulating), so queries that arrive while others are on
 the GPU join at the next step and their work overlaps on the device.  A query
 whose lineages are all traced is read back (levels to the host), its scene
@@ -54,9 +53,9 @@ class Done:
 
 
 class Server:
-    def __init__(self, tracer, cities, step_lineages: int = 1 << 21, quantum: int = 0,
+    def __init__(self, tracer, cities, step_lineages: int = 1 << 22, quantum: int = 0,
                  mem_budget: int = 4 << 30, max_active: int = 48, precision: int = btrace.BT_PREC_MIXED,
-                 oldest_share: float = 0.0):
+                 oldest_share: float = 1.0):
         self.tr = tracer
         self.quantum = int(quantum)
         self.oldest_share = float(oldest_share)
@@ -105,12 +104,13 @@ class Server:
         self.host_s["admit"] += t1 - t0
         if not self.active:
             return False
-        # shortest remaining work first (SRPT): the step's lineage budget goes
-        # to the active queries in order of remaining work, lineages times
-        # segments per lineage (K + 1), so small queries finish in the step
-        # after their arrival and a big one takes what is left; with a
-        # nonzero `quantum` every query the budget did not reach still gets
-        # that many lineages
+        # The oldest admitted query first takes `oldest_share` of the step's
+        # lineage budget (all of it by default: first come, first served, so
+        # a big query is not held back by the stream behind it); what is left
+        # goes to the other queries shortest remaining work first (lineages
+        # times segments per lineage, K + 1), so small queries finish in the
+        # step after their arrival.  With a nonzero `quantum` every query the
+        # budget did not reach still gets that many lineages.
         left = [a["total"] - a["next"] for a in self.active]
         order = sorted(range(len(left)), key=lambda i: left[i] * (self.active[i]["q"].max_order + 1))
         share = [0] * len(left)
