@@ -55,7 +55,8 @@ extern "C" {
  *   origin and direction) in float pairs (double-float, about 48 bits) on the
  *   float32 pipe; float32 watertight traversal whose ambiguous triangle tests
  *   (ray within 1e-4 relative of an edge) are re-done in float64, near-equal
- *   hit distances settled in float64; float32 microphone tests relative to
+ *   hit distances settled in float64 (up to 8 such candidates per ray, past
+ *   which float32 decides); float32 microphone tests relative to
  *   the apex, re-done in float pairs near the cone and end planes; float64
  *   energy accumulation.
  * BT_PREC_FP64: the image-source chain in float64; every triangle test in

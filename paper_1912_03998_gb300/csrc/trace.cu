@@ -17,9 +17,11 @@
 // float64 beam table through every reflection, on the triangles' float64
 // planes.  Traversal is float32; a triangle whose float32 test is ambiguous
 // (the ray within a relative 1e-4 of an edge) is re-tested in float64, near-
-// equal hit distances are compared in float64.  Microphone tests are float32
-// and re-tested with float pairs when a microphone lies within the rounding
-// band of a cone or start/end plane.
+// equal hit distances are compared in float64 -- both after the search, from
+// a short per-lane list, so that no float64 code sits in the traversal loop.
+// The reflection's float-pair arithmetic runs in stages, each reading its
+// rows from shared memory and writing them back.  The microphone tests are
+// in scatter.cu.
 #include <stdio.h>
 
 #include <type_traits>
@@ -135,13 +137,24 @@ struct Best {
   bool has64;
 };
 
+// Candidates a MIXED search leaves to float64 (kPend at most per search):
+// triangles whose float32 test was ambiguous (slot | kPendAmb) and near ties
+// of the best hit (slot).  Past kPend a candidate is decided in float32 like
+// any other (a search meets that many only on a ray running along a line of
+// triangle edges).
+constexpr int kPend = 8;
+constexpr int kPendAmb = 0x40000000;
+
 // Ray as float pairs in shared memory: rows 0..5 of `hi` and `lo` hold origin
 // xyz and direction xyz, `stride` floats apart.
-// In FP64 mode `dv` points at the same rows held as float64.
+// In FP64 mode `dv` points at the same rows held as float64.  MIXED: `pend`
+// is the lane's column of the pending list (entry 0 the count, entries 1..
+// kPend the candidates, `stride` ints apart).
 struct RaySrc {
   const float *hi, *lo;
   int stride;
   const double *dv;
+  int *pend;
   __device__ __forceinline__ void get(double3 &o, double3 &d) const {
     if (dv) {
       o = make_double3(dv[0], dv[stride], dv[2 * stride]);
@@ -153,6 +166,15 @@ struct RaySrc {
                      (double)hi[5 * stride] + lo[5 * stride]);
   }
 };
+
+// Record a candidate for float64 after the search; false if the list is full.
+__device__ __forceinline__ bool pend_add(const RaySrc &rs, int entry) {
+  const int n = rs.pend[0];
+  if (n >= kPend) return false;
+  rs.pend[(n + 1) * rs.stride] = entry;
+  rs.pend[0] = n + 1;
+  return true;
+}
 
 // Closest accepted hit of the ray in the BVH; ties in distance go to the
 // lowest original triangle id.  With kMixed, `rs` gives the float-pair ray
@@ -188,16 +210,9 @@ __device__ __forceinline__ void consider_tri(const DevScene &sc, const Tri *tris
     t = hit_watertight(r, v0, v1, v2, amb);
   }
   if (kF64) {
-  } else if (kMixed && amb) {
-    double3 o, d;
-    rs.get(o, d);
-    double tt;
-    if (!hit_mt64(o, d, v0, v1, v2, tt)) return;
-    if (!(tt > (double)r.t_eps && (dns64 == 0.0 || tt * dns64 > (double)r.t_eps))) return;
-    t64 = tt;
-    has64 = true;
-    t = (float)tt;
   } else {
+    // MIXED: an ambiguous candidate is decided in float64 after the search
+    if (kMixed && amb && pend_add(rs, slot | kPendAmb)) return;
     if (!(t < kInf && accept_hit(r, t))) return;
   }
   if (t > tlim) return;  // sub-domain: beyond the tile (see k_trace_tiled)
@@ -206,25 +221,68 @@ __device__ __forceinline__ void consider_tri(const DevScene &sc, const Tri *tris
     if (t < best.t || (t == best.t && id < best.id)) { best.t = t; best.slot = slot; best.id = id; }
     return;
   }
-  // MIXED: a clearly nearer or farther float32 distance decides; a near
-  // tie is settled in float64, where distances within 1e-9 relative tie
-  // and go to the lowest triangle index
+  // MIXED and FP64: a clearly nearer or farther float32 distance decides; a
+  // near tie is settled in float64, where distances within 1e-9 relative tie
+  // and go to the lowest triangle index (MIXED: after the search)
   float win = 1e-5f * fabsf(best.t) + 1e-4f;
   if (best.slot < 0 || t < best.t - win) {
     best.t = t; best.slot = slot; best.id = id; best.t64 = t64; best.has64 = has64;
     return;
   }
   if (t > best.t + win) return;
-  double3 o, d;
-  rs.get(o, d);
-  if (!has64) t64 = plane_t64(sc, slot, o, d);
-  if (!best.has64) {
-    best.t64 = plane_t64(sc, best.slot, o, d);
-    best.has64 = true;
+  if (kMixed) {
+    if (!pend_add(rs, slot) && (t < best.t || (t == best.t && id < best.id))) {
+      best.t = t; best.slot = slot; best.id = id; best.t64 = 0.0; best.has64 = false;
+    }
+    return;
   }
   double tol = 1e-9 * (1.0 + fabs(t64));
   if (t64 < best.t64 - tol || (fabs(t64 - best.t64) <= tol && id < best.id)) {
     best.t = (float)t64; best.slot = slot; best.id = id; best.t64 = t64; best.has64 = true;
+  }
+}
+
+// MIXED, after a search: the candidates it left to float64.  An ambiguous
+// triangle is tested with float64 Moller-Trumbore; a near tie compares the
+// float64 plane distances of both triangles.  Each is then weighed against
+// the best hit as during the search.
+__device__ __forceinline__ void settle_search(const DevScene &sc, const Ray &r, const RaySrc &rs, double dns64,
+                                              Best &best, float tlim) {
+  const int n = rs.pend[0];
+  if (n == 0) return;
+  const Tri *const tris = sc.tris;
+  double3 o, d;
+  rs.get(o, d);
+#pragma unroll 1
+  for (int q = 1; q <= n; q++) {
+    const int e = rs.pend[q * rs.stride];
+    const int slot = e & ~kPendAmb;
+    const Tri *tp = tris + slot;
+    const float4 v1 = __ldg(&tp->v1);
+    double tt;
+    if (e & kPendAmb) {
+      if (!hit_mt64(o, d, __ldg(&tp->v0), v1, __ldg(&tp->v2), tt)) continue;
+      if (!(tt > (double)r.t_eps && (dns64 == 0.0 || tt * dns64 > (double)r.t_eps))) continue;
+    } else {
+      tt = plane_t64(sc, slot, o, d);
+    }
+    const float t = (float)tt;
+    if (t > tlim) continue;
+    const int id = __float_as_int(v1.w);
+    const float win = 1e-5f * fabsf(best.t) + 1e-4f;
+    if (best.slot < 0 || t < best.t - win) {
+      best.t = t; best.slot = slot; best.id = id; best.t64 = tt; best.has64 = true;
+      continue;
+    }
+    if (t > best.t + win) continue;
+    if (!best.has64) {
+      best.t64 = plane_t64(sc, best.slot, o, d);
+      best.has64 = true;
+    }
+    const double tol = 1e-9 * (1.0 + fabs(tt));
+    if (tt < best.t64 - tol || (fabs(tt - best.t64) <= tol && id < best.id)) {
+      best.t = t; best.slot = slot; best.id = id; best.t64 = tt; best.has64 = true;
+    }
   }
 }
 
@@ -309,9 +367,11 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, Ray
   int stack[kStackDepth];
   HitSearch hs;
   hs.start(root);
+  if constexpr (kP == kPMixed) rs.pend[0] = 0;
   while (hs.step<kP, kCount>(sc, nodes, tris, n_tri, r, rs, dns64, stack, err, n_nodes, n_tris, tlim)) {
   }
   best = hs.best;
+  if constexpr (kP == kPMixed) settle_search(sc, r, rs, dns64, best, tlim);
   return best.slot;
 }
 
@@ -371,6 +431,7 @@ struct LineageSmem {
   float lo[kP == kPMixed ? kRows : 1][kTraceThreads];
   float p[kMaxBands][kTraceThreads];  // band power W_b prod(r_b)
   float st[4][kTraceThreads];         // start plane (relative to the apex)
+  int pend[kP == kPMixed ? kPend + 1 : 1][kTraceThreads];  // MIXED: candidates left to float64
   unsigned cnt[kNumCounts][kTraceThreads];  // per-lane event counts of the launch
 };
 
@@ -602,26 +663,40 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, const SceneVi
     const double sw = dot3(sn, v0d - A);
     sm.st[0][t] = (float)sn.x; sm.st[1][t] = (float)sn.y; sm.st[2][t] = (float)sn.z; sm.st[3][t] = (float)sw;
   } else if (kMixed) {
+    // in stages, each reading its rows from shared memory and writing them
+    // back before the next starts, so that few float pairs are live at once
+    // (the compiler fences keep the stages apart)
     PlaneDF pd = v.sc.planes_df[slot];
-    df3 n = df3{df{pd.hi.x, pd.lo.x}, df{pd.hi.y, pd.lo.y}, df{pd.hi.z, pd.lo.z}};
-    df w = df{pd.hi.w, pd.lo.w};
-    df3 A = ld_df3(sm, kRowA, t), O = ld_df3(sm, kRowO, t), D = ld_df3(sm, kRowD, t);
-    df th = best.has64 ? d_to_df(best.t64) : df_div(df_sub(w, df3_dot(n, O)), df3_dot(n, D));
-    df3 H = df3_add(O, df3_scale(D, th));
-    df da = df3_dot(df3_sub(A, mkdf3(pv0)), n);
-    A = df3_sub(A, df3_scale(n, df{2.0f * da.hi, 2.0f * da.lo}));
-    st_df3(sm, kRowA, t, A);
-#pragma unroll
-    for (int j = 0; j < 3; j++) st_df3(sm, kRowN + 3 * j, t, df3_mirror(ld_df3(sm, kRowN + 3 * j, t), n));
-    D = df3_mirror(D, n);
-    st_df3(sm, kRowO, t, H);
-    st_df3(sm, kRowD, t, D);
-    df dn = df3_dot(n, D);
+    const df3 n = df3{df{pd.hi.x, pd.lo.x}, df{pd.hi.y, pd.lo.y}, df{pd.hi.z, pd.lo.z}};
+    {
+      // the hit point on the plane (the reflected beam's origin), then the
+      // mirrored axis
+      const df3 O = ld_df3(sm, kRowO, t), D = ld_df3(sm, kRowD, t);
+      const df th = best.has64 ? d_to_df(best.t64)
+                               : df_div(df_sub(df{pd.hi.w, pd.lo.w}, df3_dot(n, O)), df3_dot(n, D));
+      st_df3(sm, kRowO, t, df3_add(O, df3_scale(D, th)));
+      st_df3(sm, kRowD, t, df3_mirror(D, n));
+    }
+    asm volatile("" ::: "memory");
+    {
+      // the image source
+      const df3 A = ld_df3(sm, kRowA, t);
+      const df da = df3_dot(df3_sub(A, mkdf3(pv0)), n);
+      st_df3(sm, kRowA, t, df3_sub(A, df3_scale(n, df{2.0f * da.hi, 2.0f * da.lo})));
+    }
+#pragma unroll 1
+    for (int j = 0; j < 3; j++) {
+      asm volatile("" ::: "memory");
+      st_df3(sm, kRowN + 3 * j, t, df3_mirror(ld_df3(sm, kRowN + 3 * j, t), n));
+    }
+    asm volatile("" ::: "memory");
+    const df3 D = ld_df3(sm, kRowD, t);
+    const df dn = df3_dot(n, D);
     ls.dns64 = fabs((double)dn.hi + (double)dn.lo);
     ls.dns = (float)ls.dns64;
     Dn = df3_hi(D);
     float3 sn = dot3(pn, Dn) > 0.0f ? pn : pn * -1.0f;
-    float sw = df3_dot(mkdf3(sn), df3_sub(mkdf3(pv0), A)).hi;
+    float sw = df3_dot(mkdf3(sn), df3_sub(mkdf3(pv0), ld_df3(sm, kRowA, t))).hi;
     sm.st[0][t] = sn.x; sm.st[1][t] = sn.y; sm.st[2][t] = sn.z; sm.st[3][t] = sw;
   } else {
     float3 A = ld_hi3(sm, kRowA, t), O = ld_hi3(sm, kRowO, t), D = ld_hi3(sm, kRowD, t);
@@ -735,13 +810,14 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
   hs.start(-1);
   int stack[kStackDepth];
   const RaySrc rs{&sm.hi[kRowO][t], kMixed ? &sm.lo[kRowO][t] : &sm.hi[kRowO][t], kTraceThreads,
-                  kF64 ? &sm.dv[kRowO][t] : nullptr};
+                  kF64 ? &sm.dv[kRowO][t] : nullptr, &sm.pend[0][t]};
   while (true) {
     // ---- service: finished searches write their segment and reflect
     bool fresh = false;
     if (__ballot_sync(0xffffffffu, pending) && pending) {
       const SceneView &v = kBatch ? a.views[vi] : a.v;
       const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), v.t_eps, ls.dns);
+      if constexpr (kMixed) settle_search(v.sc, r, rs, ls.dns64, hs.best, kInf);
       if (finish_segment(a, v, vi, sm, t, r, hs.best, hs.best.slot, ls, cn)) fresh = true;
       else ls.lin = -1;
       pending = false;
@@ -764,6 +840,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
     }
     if (fresh) {
       hs.start((kBatch ? a.views[vi] : a.v).sc.root);
+      if constexpr (kMixed) rs.pend[0] = 0;
       searching = true;
     }
     if (__all_sync(0xffffffffu, done)) break;
@@ -1041,7 +1118,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, c
   hs.start(-1);
   int stack[kStackDepth];
   const RaySrc rs{&sm.hi[kRowO][t], kMixed ? &sm.lo[kRowO][t] : &sm.hi[kRowO][t], kTraceThreads,
-                  kF64 ? &sm.dv[kRowO][t] : nullptr};
+                  kF64 ? &sm.dv[kRowO][t] : nullptr, &sm.pend[0][t]};
   while (true) {
     // ---- service: finished searches write their segment and reflect, end,
     // or go on to the next tile
@@ -1050,6 +1127,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, c
     if (__ballot_sync(0xffffffffu, pending) && pending) {
       pending = false;
       const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), v.t_eps, ls.dns);
+      if constexpr (kMixed) settle_search(v.sc, r, rs, ls.dns64, hs.best, tlim);
       if (hs.best.slot >= 0) {
         // the hit lies in this tile; a reflected beam starts here as well
         if (finish_segment(a, v, 0, sm, t, r, hs.best, hs.best.slot, ls, cn)) start = true;
@@ -1164,6 +1242,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, c
       const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), v.t_eps, ls.dns);
       tlim = tile_exit(tg, tile % tg.tx, tile / tg.tx, r) + kTileEps;
       hs.start(__ldg(&ta.roots[tile]));
+      if constexpr (kMixed) rs.pend[0] = 0;
       searching = true;
     }
     if (!__any_sync(0xffffffffu, active)) {
@@ -1250,6 +1329,7 @@ int tiled_resident_lanes(int n_sm) {
 __global__ void __launch_bounds__(128) k_cast(DevScene sc, const float *o, const float *d, const float *ns,
                                               int64_t n, float t_eps, float *t_out, int *tri_out, int *err) {
   __shared__ float rh[6][128], rl[6][128];
+  __shared__ int pend[kPend + 1][128];
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int t = threadIdx.x;
@@ -1265,7 +1345,7 @@ __global__ void __launch_bounds__(128) k_cast(DevScene sc, const float *o, const
   Ray r = make_ray(O, df3_hi(D), t_eps, (float)dns);
   Best best;
   unsigned a = 0, b = 0;
-  int slot = closest_hit<kPMixed, false>(sc, r, RaySrc{&rh[0][t], &rl[0][t], 128, nullptr}, dns, best, err, a, b,
+  int slot = closest_hit<kPMixed, false>(sc, r, RaySrc{&rh[0][t], &rl[0][t], 128, nullptr, &pend[0][t]}, dns, best, err, a, b,
                                          sc.root);
   t_out[i] = slot >= 0 ? (best.has64 ? (float)best.t64 : best.t) : kInf;
   tri_out[i] = slot >= 0 ? best.id : -1;
