@@ -404,3 +404,58 @@ def test_source_shards_sum_to_the_full_trace(tracer):
     btrace.bt_read_levels(tracer.ctx, sid, L, I2, c2)
     assert (I2 == I).all() and (c2 == 0).all()
     btrace.bt_unload_scene(tracer.ctx, sid)
+
+
+def test_cast_rays_through_shared_vertices_and_edges(tracer):
+    # Rays straight down onto the shared vertices and edges of coplanar
+    # triangle fans: every float32 test there is ambiguous, so the MIXED
+    # search leaves the triangles to float64 after the traversal (up to 8 per
+    # ray; a 12-triangle fan overflows that list and the rest are decided in
+    # float32).  Every ray must still hit the plane at the right distance,
+    # on a triangle of the fan that contains the point.
+    from paper_1912_03998_gb300 import btrace
+    verts, tris = [], []
+
+    def fan(cx, cy, k, r):
+        c = len(verts)
+        verts.append((cx, cy, 10.0))
+        for i in range(k):
+            a = 2.0 * np.pi * i / k
+            verts.append((cx + r * np.cos(a), cy + r * np.sin(a), 10.0))
+        for i in range(k):
+            tris.append((c, c + 1 + i, c + 1 + (i + 1) % k))
+        return c
+
+    centres = [fan(0.0, 0.0, 12, 5.0), fan(20.0, 0.0, 6, 5.0), fan(40.0, 0.0, 3, 5.0), fan(60.0, 0.0, 8, 5.0)]
+    verts = np.asarray(verts, np.float32)
+    tris = np.asarray(tris, np.int32)
+    mat = np.zeros(len(tris), np.uint8)
+    refl = np.full((1, 8), 0.9, np.float32)
+    # targets: the fan centres (every triangle of the fan contains them) and
+    # the midpoints of the spokes (the edges two triangles share); points on
+    # the rim, the union's boundary, may round outside it and are left out
+    pts = [verts[c, :2] for c in centres]
+    for a, b, c in tris:
+        pts.append(0.5 * (verts[a, :2] + verts[b, :2]))
+    pts = np.asarray(pts, np.float32)
+    o = np.column_stack([pts, np.full(len(pts), 50.0, np.float32)]).astype(np.float32)
+    d = np.tile(np.asarray([[0.0, 0.0, -1.0]], np.float32), (len(pts), 1))
+    sid = btrace.bt_load_scene(tracer.ctx, verts, tris, mat, refl)
+    try:
+        t, ids = btrace.bt_cast_rays(tracer.ctx, sid, o, d)
+    finally:
+        btrace.bt_unload_scene(tracer.ctx, sid)
+    assert (ids >= 0).all(), np.nonzero(ids < 0)[0][:10]
+    assert np.allclose(t, 40.0, atol=1e-4), t[np.abs(t - 40.0) > 1e-4][:10]
+    # a centre is a tie of the whole fan, which goes to the lowest triangle
+    # index wherever the fan fits the float64 list (3, 6 and 8 triangles)
+    first = [0, 12, 18, 21]
+    assert [int(i) for i in ids[1:4]] == first[1:4], ids[:4]
+    assert 0 <= ids[0] < 12
+    # the hit triangle contains the target point (edges inclusive, 1e-5 m)
+    for p, i in zip(pts.astype(np.float64), ids):
+        a, b, c = verts[tris[i]].astype(np.float64)[:, :2]
+        def side(u, v, w):
+            return (v[0] - u[0]) * (w[1] - u[1]) - (v[1] - u[1]) * (w[0] - u[0])
+        s = [side(a, b, p), side(b, c, p), side(c, a, p)]
+        assert min(s) >= -1e-5 * 5.0 or max(s) <= 1e-5 * 5.0, (p, i, s)
