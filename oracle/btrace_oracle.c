@@ -11,7 +11,9 @@
  * steps below follow that prose with these readings:
  *   - beams: the faces of a geodesic icosahedron subdivided L times, one
  *     triangular cone per face, power split by solid angle (Section 2: the
- *     source energy is split between beams by its power per direction);
+ *     source energy is split between beams by its power per direction); a
+ *     directional source scales each beam's power by its pattern's gain for
+ *     that beam (or_trace_dir);
  *   - only the guiding (axis) ray of a beam is intersected with the model and
  *     a beam is never split (Section 2, last paragraph);
  *   - a reflection creates an image source, the mirror of the apex in the hit
@@ -769,6 +771,8 @@ typedef struct {
   const omics *mc;
   const oparams *p;
   const float *src, *power;
+  const float *dir_gain;  /* [n_patterns][n_beams] or NULL */
+  const int32_t *dir_of;  /* [n_src]: pattern of each source, -1 = omnidirectional */
   int64_t n_src;
   int level;
   const double *dirs, *omega;
@@ -788,7 +792,11 @@ static void trace_beam(job *J, int64_t si, int64_t bi) {
   g.apex = mk(J->src[3 * si], J->src[3 * si + 1], J->src[3 * si + 2]);
   for (int j = 0; j < 3; j++)
     g.dir[j] = mk(J->dirs[9 * bi + 3 * j], J->dirs[9 * bi + 3 * j + 1], J->dirs[9 * bi + 3 * j + 2]);
-  for (int b = 0; b < s->n_bands; b++) g.w[b] = J->power[si * s->n_bands + b];
+  /* a directional source: its power in this beam's direction, the pattern's
+   * gain times the omnidirectional power */
+  double gain = 1.0;
+  if (J->dir_of && J->dir_of[si] >= 0) gain = J->dir_gain[(int64_t)J->dir_of[si] * J->n_beams + bi];
+  for (int b = 0; b < s->n_bands; b++) g.w[b] = gain * J->power[si * s->n_bands + b];
   ray_q r;
   r.o = g.apex;
   r.d = unit(add(add(g.dir[0], g.dir[1]), g.dir[2]));
@@ -861,14 +869,20 @@ static void *run_job(void *arg) {
  * (single thread only) records each contribution's microphone, source, order,
  * distance and apex.  Returns 0, or a negative value on bad input.
  */
-int or_trace(const void *scene, const float *src, const float *power, int64_t n_src, int level,
-             const float *mics, int64_t n_mics, int max_order, const double *alpha,
-             double energy_threshold, double t_eps, int hit_mode, int mic_mode, int n_threads,
-             double *I, int32_t *cnt, double *stats, int64_t log_cap, int32_t *log_mic,
-             int32_t *log_src, int32_t *log_order, double *log_d, double *log_apex,
-             int64_t *log_n) {
+int or_trace_dir(const void *scene, const float *src, const float *power, int64_t n_src, int level,
+                 const float *dir_gain, int32_t n_patterns, const int32_t *dir_of,
+                 const float *mics, int64_t n_mics, int max_order, const double *alpha,
+                 double energy_threshold, double t_eps, int hit_mode, int mic_mode, int n_threads,
+                 double *I, int32_t *cnt, double *stats, int64_t log_cap, int32_t *log_mic,
+                 int32_t *log_src, int32_t *log_order, double *log_d, double *log_apex,
+                 int64_t *log_n) {
   const oscene *s = (const oscene *)scene;
   if (!s || level < 0 || level > 8 || max_order < 0 || max_order > 32 || n_threads < 1) return -1;
+  if (dir_of) {
+    if (!dir_gain || n_patterns < 1) return -1;
+    for (int64_t i = 0; i < n_src; i++)
+      if (dir_of[i] < -1 || dir_of[i] >= n_patterns) return -1;
+  }
   if (log_cap > 0 && n_threads != 1) return -2;
   oparams p;
   p.max_order = max_order;
@@ -891,6 +905,7 @@ int or_trace(const void *scene, const float *src, const float *power, int64_t n_
   for (int i = 0; i < n_threads && !rc; i++) {
     job *J = &jobs[i];
     J->s = s; J->mc = &mc; J->p = &p; J->src = src; J->power = power; J->n_src = n_src;
+    J->dir_gain = dir_of ? dir_gain : NULL; J->dir_of = dir_of;
     J->level = level; J->dirs = dirs; J->omega = omega; J->n_beams = nb;
     J->tid = i; J->n_threads = n_threads;
     J->acc.n_bands = s->n_bands;
@@ -934,6 +949,18 @@ int or_trace(const void *scene, const float *src, const float *power, int64_t n_
   free(jobs); free(th); free(dirs); free(omega);
   mics_free(&mc);
   return rc;
+}
+
+/* or_trace_dir with every source omnidirectional. */
+int or_trace(const void *scene, const float *src, const float *power, int64_t n_src, int level,
+             const float *mics, int64_t n_mics, int max_order, const double *alpha,
+             double energy_threshold, double t_eps, int hit_mode, int mic_mode, int n_threads,
+             double *I, int32_t *cnt, double *stats, int64_t log_cap, int32_t *log_mic,
+             int32_t *log_src, int32_t *log_order, double *log_d, double *log_apex,
+             int64_t *log_n) {
+  return or_trace_dir(scene, src, power, n_src, level, NULL, 0, NULL, mics, n_mics, max_order, alpha,
+                      energy_threshold, t_eps, hit_mode, mic_mode, n_threads, I, cnt, stats, log_cap,
+                      log_mic, log_src, log_order, log_d, log_apex, log_n);
 }
 
 /* Level readout: L = 10 log10(I / 1e-12) dB re 1e-12 W/m^2, -inf where I = 0. */

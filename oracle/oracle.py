@@ -57,6 +57,9 @@ def lib():
             L.or_trace.restype = i32
             L.or_trace.argtypes = [p, p, p, i64, i32, p, i64, i32, p, d, d, i32, i32, i32,
                                    p, p, p, i64, p, p, p, p, p, p]
+            L.or_trace_dir.restype = i32
+            L.or_trace_dir.argtypes = [p, p, p, i64, i32, p, i32, p, p, i64, i32, p, d, d, i32, i32,
+                                       i32, p, p, p, i64, p, p, p, p, p, p]
             L.or_levels.argtypes = [p, i64, p]
             L.isrc_bruteforce.restype = i64
             L.isrc_bruteforce.argtypes = [p, i64, p, i64, p, p, i32, i32, p, p, p, i64, i32,
@@ -123,8 +126,15 @@ def cast_rays(scene: Scene, o, d, has_start=None, ns=None, t_eps=1e-3, mode=HIT_
 
 
 def trace(scene: Scene, src, power, level, mics, max_order, alpha=None, energy_threshold=0.0,
-          t_eps=1e-3, hit_mode=HIT_BVH, mic_mode=MIC_GRID, n_threads=1, log_cap=0):
+          t_eps=1e-3, hit_mode=HIT_BVH, mic_mode=MIC_GRID, n_threads=1, log_cap=0,
+          directivity=None, pattern_of=None):
     """Full hybrid trace (Section 2), optionally tiled (Section 3).
+
+    Directional sources (Section 2: a source's energy is split between the
+    beams by its power in each direction): `directivity` [n_patterns,
+    20*4**level] gains per beam, `pattern_of` [n_src] the pattern of each
+    source (-1 = omnidirectional); a beam's band powers are the source's
+    times its pattern's gain for that beam.
 
     Returns dict(I [n_m, B] W/m^2, cnt [n_m], stats dict, log dict or None).
     """
@@ -144,9 +154,15 @@ def trace(scene: Scene, src, power, level, mics, max_order, alpha=None, energy_t
         log = dict(mic=np.empty(log_cap, np.int32), src=np.empty(log_cap, np.int32),
                    order=np.empty(log_cap, np.int32), d=np.empty(log_cap, np.float64),
                    apex=np.empty((log_cap, 3), np.float64))
-    rc = lib().or_trace(scene.h, _ptr(src), _ptr(power), len(src), level, _ptr(mics), len(mics),
-                        max_order, _ptr(a), energy_threshold, t_eps, hit_mode, mic_mode,
-                        n_threads, _ptr(I), _ptr(cnt), _ptr(stats), log_cap,
+    if pattern_of is not None:
+        gain = _c(directivity, np.float32).reshape(-1, 20 * 4 ** level)
+        pat = _c(pattern_of, np.int32).reshape(len(src))
+    else:
+        gain, pat = None, None
+    rc = lib().or_trace_dir(scene.h, _ptr(src), _ptr(power), len(src), level, _ptr(gain),
+                            0 if gain is None else len(gain), _ptr(pat), _ptr(mics), len(mics),
+                            max_order, _ptr(a), energy_threshold, t_eps, hit_mode, mic_mode,
+                            n_threads, _ptr(I), _ptr(cnt), _ptr(stats), log_cap,
                         *(_ptr(log[k]) if log else None for k in ("mic", "src", "order", "d",
                                                                    "apex")),
                         C.byref(ln))

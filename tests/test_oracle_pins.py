@@ -75,6 +75,47 @@ def test_free_field_closed_form(oracle_mod, level, alpha_db):
     assert np.abs(L - 10 * np.log10(expect / 1e-12)).max() < 1e-9
 
 
+@pytest.mark.parametrize("level", [1, 3])
+def test_directional_free_field_closed_form(oracle_mod, level):
+    # Section 2: a source's energy is split between the beams by its power in
+    # each direction.  With no geometry a microphone receives only the beam
+    # whose cone holds its direction from the source, so its intensity is
+    # that beam's gain times W / (4 pi r^2); the beam is found here by the
+    # cone-membership test on the beam table itself, not by the trace
+    w = synth.free_field(seed=5, level=level, n_mics=400)
+    dirs, _ = oracle_mod.beam_table(level)
+    n_b = len(dirs)
+    rng = np.random.Generator(np.random.PCG64(11))
+    gains = rng.uniform(0.0, 3.0, size=(2, n_b)).astype(np.float32)
+    src = np.repeat(w.src, 3, axis=0)
+    power = np.repeat(w.power, 3, axis=0)
+    pattern_of = np.array([0, -1, 1], np.int32)  # two patterns and one omnidirectional copy
+    sc = oracle_mod.Scene(w.scene)
+    r = oracle_mod.trace(sc, src, power, level, w.mics, w.max_order, directivity=gains, pattern_of=pattern_of)
+    v = w.mics.astype(np.float64) - w.src[0].astype(np.float64)
+    rr = np.linalg.norm(v, axis=1)
+    u = v / rr[:, None]
+    n = np.cross(dirs, np.roll(dirs, -1, axis=1))
+    inside = (np.einsum("nji,mi->mnj", n, u) >= 0).all(axis=2)
+    assert (inside.sum(axis=1) == 1).all()
+    beam = inside.argmax(axis=1)
+    g = 1.0 + gains[0, beam].astype(np.float64) + gains[1, beam].astype(np.float64)
+    expect = g[:, None] * w.power[0].astype(np.float64)[None, :] / (4 * np.pi * rr[:, None] ** 2)
+    assert (r["cnt"] == 3).all()
+    assert np.abs(r["I"] / expect - 1).max() < 1e-12
+
+
+def test_directivity_of_ones_is_omnidirectional(oracle_mod):
+    # a pattern of unit gains leaves every result exactly as without one
+    w = synth.tiny_city(seed=3)
+    n_b = 20 * 4 ** w.level
+    sc = oracle_mod.Scene(w.scene)
+    a = oracle_mod.trace(sc, w.src, w.power, w.level, w.mics, w.max_order)
+    b = oracle_mod.trace(sc, w.src, w.power, w.level, w.mics, w.max_order,
+                         directivity=np.ones((1, n_b), np.float32), pattern_of=np.zeros(len(w.src), np.int32))
+    assert np.array_equal(a["I"], b["I"]) and np.array_equal(a["cnt"], b["cnt"])
+
+
 def _max_beam_diameter(oracle_mod, level):
     dirs, _ = oracle_mod.beam_table(level)
     c = np.einsum("nij,nkj->nik", dirs, dirs)
