@@ -158,6 +158,28 @@ int bt_unload_scene(bt_ctx *ctx, int32_t scene_id);
 int bt_set_sources(bt_ctx *ctx, int32_t scene_id, const float *pos, const float *power_w,
                    int64_t n_s, int32_t icosa_level);
 
+/* Directional sources (Section 2: a source's energy is split between the
+ * beams by its power in each direction).
+ *   patterns   [n_patterns][20 * 4^L] float32 gains >= 0, one per beam of the
+ *              scene's icosahedron level L, in the beam order of bt_beam_axes
+ *   pattern_of [n_src] int32: each source's pattern, -1 = omnidirectional
+ * A beam's band powers are the source's power_w times its pattern's gain for
+ * the beam (a pattern whose gains average 1 over the sphere, weighted by the
+ * beams' solid angles, keeps the source's total power).  Host or device
+ * pointers; copied before the call returns.  n_patterns = 0 (the arrays may
+ * then be NULL) makes every source omnidirectional again, and so does every
+ * bt_set_sources.  Errors: BT_E_STATE before bt_set_sources; BT_E_INVALID for
+ * NULL arrays, a negative or non-finite gain, or a pattern index outside
+ * -1..n_patterns-1 (the scene then stays omnidirectional). */
+int bt_set_directivity(bt_ctx *ctx, int32_t scene_id, const float *patterns, int32_t n_patterns,
+                       const int32_t *pattern_of);
+
+/* Unit axis (float32, [20 * 4^L][3], host or device) of every beam of
+ * icosahedron level L in 0..8, in the order bt_set_directivity's gains use:
+ * beam i lies in base face i >> 2L and is refined by the base-4 digits of
+ * the rest of i (corner-0, corner-1, corner-2, centre child). */
+int bt_beam_axes(bt_ctx *ctx, int32_t icosa_level, float *axes);
+
 /* Microphones of a scene (Section 4: a regular grid of receivers).
  *   pos [n_m][3] float32.  They are binned on the device into an xy cell grid
  *   (Section 3: microphones are partitioned with the geometry).  The scene's
@@ -247,7 +269,8 @@ int bt_set_result(bt_ctx *ctx, int32_t scene_id, const double *intensity, const 
  *   params     [n_scenes] per-scene parameters; tiles must be 1x1, and
  *              precision, count_work, blocks_per_sm and chunk_beams must agree
  * The batch reads the scenes' device buffers in place: after bt_load_scene,
- * bt_set_sources, bt_set_microphones or bt_unload_scene on any of its scenes,
+ * bt_set_sources, bt_set_directivity, bt_set_microphones or bt_unload_scene on
+ * any of its scenes,
  * bt_batch_run fails with BT_E_STATE (create a new batch).  bt_batch_run
  * synchronises the context's stream; the context's stream must not be in
  * stream capture.  Batches are freed by bt_batch_destroy or with the

@@ -59,7 +59,7 @@ EXPECTED_SYMBOLS = ("bt_params_default", "bt_create", "bt_destroy", "bt_load_sce
                     "bt_read_levels", "bt_last_error", "bt_kernel_launches", "bt_cast_rays",
                     "bt_trace_noalloc", "bt_set_result", "bt_batch_create", "bt_batch_run",
                     "bt_batch_stats", "bt_batch_destroy", "bt_scene_share", "bt_trace_ranges",
-                    "bt_ranges_stats")
+                    "bt_ranges_stats", "bt_set_directivity", "bt_beam_axes")
 
 
 def lib_path() -> str:
@@ -83,6 +83,8 @@ def lib():
             L.bt_unload_scene.argtypes = [p, i32]
             L.bt_set_sources.argtypes = [p, i32, p, p, i64, i32]
             L.bt_set_microphones.argtypes = [p, i32, p, i64]
+            L.bt_set_directivity.argtypes = [p, i32, p, i32, p]
+            L.bt_beam_axes.argtypes = [p, i32, p]
             L.bt_trace.argtypes = [p, i32, C.POINTER(bt_trace_params)]
             L.bt_read_levels.argtypes = [p, i32, p, p, p, C.POINTER(bt_stats)]
             L.bt_last_error.argtypes = [p]
@@ -175,6 +177,27 @@ def bt_set_sources(ctx, scene_id: int, pos, power_w, icosa_level: int):
     pp, npos, kp = _arr(pos, np.float32)
     pw, _, kw = _arr(power_w, np.float32)
     _check(lib().bt_set_sources(ctx, int(scene_id), pp, pw, npos // 3, int(icosa_level)), ctx)
+
+
+def bt_set_directivity(ctx, scene_id: int, patterns, pattern_of):
+    """Directional sources: patterns [n_patterns, 20*4**L] per-beam gains,
+    pattern_of [n_src] (-1 = omnidirectional); patterns None = all
+    omnidirectional."""
+    if patterns is None:
+        _check(lib().bt_set_directivity(ctx, int(scene_id), None, 0, None), ctx)
+        return
+    pg, ng, kg = _arr(patterns, np.float32)
+    po, _, ko = _arr(pattern_of, np.int32)
+    n_pat = len(patterns) if hasattr(patterns, "__len__") else 1
+    _check(lib().bt_set_directivity(ctx, int(scene_id), pg, int(n_pat), po), ctx)
+
+
+def bt_beam_axes(ctx, icosa_level: int):
+    """Unit axes [20*4**L, 3] float32 of the beams, in the order of the
+    directivity gains."""
+    axes = np.empty((20 * 4 ** int(icosa_level), 3), np.float32)
+    _check(lib().bt_beam_axes(ctx, int(icosa_level), axes.ctypes.data_as(C.c_void_p)), ctx)
+    return axes
 
 
 def bt_set_microphones(ctx, scene_id: int, pos):

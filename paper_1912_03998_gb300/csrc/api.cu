@@ -42,6 +42,8 @@ struct SceneState {
   int64_t n_src = 0;
   int level = 0;
   DevBuf src, power;
+  int n_pat = 0;           // directional sources: patterns in dir_gain (0 = all omnidirectional)
+  DevBuf dir_gain, dir_of;
   // microphones
   bool has_mics = false;
   int64_t n_mics = 0;
@@ -168,8 +170,8 @@ void release(DevBuf &b) {
 // Scene buffers go back to the context's pool (freed by bt_destroy).
 void release_scene(bt_ctx *c, SceneState &s) {
   DevBuf *own[] = {&s.t_nodes, &s.t_tris, &s.t_planes, &s.t_planes64, &s.t_planes_df, &s.t_roots, &s.src,
-                   &s.power, &s.mics, &s.cell_start, &s.grid, &s.energy, &s.count, &s.out_level, &s.out_int,
-                   &s.out_cnt};
+                   &s.power, &s.dir_gain, &s.dir_of, &s.mics, &s.cell_start, &s.grid, &s.energy, &s.count,
+                   &s.out_level, &s.out_int, &s.out_cnt};
   DevBuf *geom[] = {&s.nodes, &s.tris, &s.planes, &s.planes64, &s.planes_df, &s.refl};
   for (DevBuf *b : own)
     if (b->p) c->pool.push_back(*b);
@@ -239,6 +241,15 @@ __global__ void k_pack_sources(const float *pos, const float *power, int64_t n, 
     if (!isfinite(w) || w < 0.0f) atomicExch(error, BT_E_INVALID);
     pw[i * n_bands + b] = w;
   }
+}
+
+// Directional source patterns: every gain finite and >= 0, every source's
+// pattern index in -1..n_pat-1.
+__global__ void k_check_directivity(const float *gain, int64_t n_gain, const int *of, int64_t n_src, int n_pat,
+                                    int *error) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n_gain && !(isfinite(gain[i]) && gain[i] >= 0.0f)) atomicExch(error, BT_E_INVALID);
+  if (i < n_src && (of[i] < -1 || of[i] >= n_pat)) atomicExch(error, BT_E_INVALID);
 }
 
 
@@ -565,9 +576,69 @@ BT_API int bt_set_sources(bt_ctx *c, int32_t scene_id, const float *pos, const f
   }
   s->n_src = n_s;
   s->level = icosa_level;
+  s->n_pat = 0;  // new sources are omnidirectional until bt_set_directivity
   s->has_src = true;
   s->traced = false;
   s->gen = ++c->gen_counter;
+  return BT_OK;
+}
+
+BT_API int bt_set_directivity(bt_ctx *c, int32_t scene_id, const float *patterns, int32_t n_patterns,
+                              const int32_t *pattern_of) {
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  SceneState *s;
+  TRY(scene_ref(c, scene_id, &s));
+  if (!s->has_src) return fail(c, BT_E_STATE, "bt_set_directivity needs the scene's sources");
+  if (n_patterns < 0) return fail(c, BT_E_INVALID, "n_patterns must be >= 0");
+  const int64_t n_beams = (int64_t)20 << (2 * s->level);
+  if (n_patterns > 0 && (int64_t)n_patterns * n_beams > ((int64_t)1 << 31))
+    return fail(c, BT_E_INVALID, "%d patterns of %lld beams are too many", n_patterns, (long long)n_beams);
+  if (n_patterns > 0 && (!patterns || !pattern_of)) return fail(c, BT_E_INVALID, "NULL directivity array");
+  if (n_patterns == 0) {
+    s->n_pat = 0;
+    s->traced = false;
+    s->gen = ++c->gen_counter;
+    return BT_OK;
+  }
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  const int64_t n_gain = (int64_t)n_patterns * n_beams;
+  TRY(ensure(c, s->dir_gain, sizeof(float) * (size_t)n_gain));
+  TRY(ensure(c, s->dir_of, sizeof(int) * (size_t)(s->n_src > 0 ? s->n_src : 1)));
+  TRY(reset_counters(c));
+  CK(cudaMemcpyAsync(s->dir_gain.p, patterns, sizeof(float) * (size_t)n_gain, cudaMemcpyDefault, st));
+  if (s->n_src > 0)
+    CK(cudaMemcpyAsync(s->dir_of.p, pattern_of, sizeof(int) * (size_t)s->n_src, cudaMemcpyDefault, st));
+  const int64_t n_check = n_gain > s->n_src ? n_gain : s->n_src;
+  k_check_directivity<<<(int)((n_check + 255) / 256), 256, 0, st>>>((const float *)s->dir_gain.p, n_gain,
+                                                                    (const int *)s->dir_of.p, s->n_src,
+                                                                    n_patterns, &c->d_ctr->error);
+  bt::note_launches(1);
+  CK(cudaGetLastError());
+  TRY(read_counters(c));
+  if (c->h_ctr->error) {
+    s->n_pat = 0;
+    return fail(c, BT_E_INVALID, "directivity gain negative or not finite, or pattern index out of range");
+  }
+  s->n_pat = n_patterns;
+  s->traced = false;
+  s->gen = ++c->gen_counter;
+  return BT_OK;
+}
+
+BT_API int bt_beam_axes(bt_ctx *c, int32_t icosa_level, float *axes) {
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  if (icosa_level < 0 || icosa_level > 8) return fail(c, BT_E_INVALID, "icosa_level %d not in 0..8", icosa_level);
+  if (!axes) return fail(c, BT_E_INVALID, "NULL axes array");
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  const int64_t n = (int64_t)20 << (2 * icosa_level);
+  TRY(ensure(c, c->stage_a, sizeof(float) * 3 * (size_t)n));
+  CK(bt::launch_beam_axes(st, icosa_level, (float *)c->stage_a.p));
+  CK(cudaMemcpyAsync(axes, c->stage_a.p, sizeof(float) * 3 * (size_t)n, cudaMemcpyDefault, st));
+  CK(cudaStreamSynchronize(st));
   return BT_OK;
 }
 
@@ -652,6 +723,8 @@ static void fill_view(bt::SceneView &v, SceneState &s, const bt_trace_params *p,
   v.cell_start = (const int *)s.cell_start.p;
   v.energy = (double *)s.energy.p;
   v.count = (int *)s.count.p;
+  v.dir_gain = s.n_pat > 0 ? (const float *)s.dir_gain.p : nullptr;
+  v.dir_of = s.n_pat > 0 ? (const int *)s.dir_of.p : nullptr;
 }
 
 // Lineages per persistent launch when the caller leaves it to the library:

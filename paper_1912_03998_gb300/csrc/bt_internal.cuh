@@ -154,6 +154,8 @@ struct SceneView {
   const int *cell_start;     // [nx * ny + 1]
   double *energy;            // [n_mics][kMaxBands], sorted order
   int *count;                // [n_mics], sorted order
+  const float *dir_gain;     // directional sources: [n_patterns][n_beams] gains, or null
+  const int *dir_of;         // [n_src]: each source's pattern, -1 = omnidirectional; null = all
 };
 
 struct TraceArgs {
@@ -430,6 +432,7 @@ cudaError_t build_scene(cudaStream_t st, const float *d_verts, const int32_t *d_
                         Plane64 *d_planes64, PlaneDF *d_planes_df, void *d_scratch, size_t scratch_bytes,
                         const float *d_box, int *d_error);
 cudaError_t launch_beam_table(cudaStream_t st, int level, float *table);
+cudaError_t launch_beam_axes(cudaStream_t st, int level, float *axes);
 size_t build_tiled_scratch_bytes(int64_t n_src, int64_t n_pairs);
 cudaError_t tiled_count(cudaStream_t st, const Tri *src, int64_t n_src, const TileGrid &tg, uint32_t *offs);
 cudaError_t tiled_build(cudaStream_t st, const Tri *src, const Plane *sp, const Plane64 *sp64, const PlaneDF *spdf,

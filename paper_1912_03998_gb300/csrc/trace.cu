@@ -122,6 +122,26 @@ cudaError_t launch_beam_table(cudaStream_t st, int level, float *table) {
   return cudaGetLastError();
 }
 
+// Unit axis of every beam of a level, float32 [n_beams][3] (the order of the
+// lineages' beam index: a directional source's gains are given in it).
+__global__ void k_beam_axes(int level, int64_t n_beams, float *axes) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_beams) return;
+  double3 d0, d1, d2;
+  beam_dirs<double>(level, i, d0, d1, d2);
+  const double3 ax = normalize3((d0 + d1) + d2);
+  axes[3 * i] = (float)ax.x;
+  axes[3 * i + 1] = (float)ax.y;
+  axes[3 * i + 2] = (float)ax.z;
+}
+
+cudaError_t launch_beam_axes(cudaStream_t st, int level, float *axes) {
+  const int64_t n = (int64_t)20 << (2 * level);
+  k_beam_axes<<<(int)((n + 127) / 128), 128, 0, st>>>(level, n, axes);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 // float64 distance along the ray to the plane of leaf slot `slot`.
 __device__ __forceinline__ double plane_t64(const DevScene &sc, int slot, double3 od, double3 dd) {
   Plane64 pl = ldg_d4(&sc.planes64[slot]);
@@ -527,8 +547,15 @@ __device__ __forceinline__ void init_lineage(const SceneView &a, LineageSmem<kP>
   }
   st_f3(sm, kRowA, t, A);
   st_f3(sm, kRowO, t, A);
+  // a directional source: its power in this beam's direction (Section 2),
+  // the pattern's gain times the omnidirectional power
+  float gain = 1.0f;
+  if (a.dir_of) {
+    const int pat = __ldg(&a.dir_of[si]);
+    if (pat >= 0) gain = __ldg(&a.dir_gain[pat * a.n_beams + bi]);
+  }
 #pragma unroll
-  for (int b = 0; b < kMaxBands; b++) sm.p[b][t] = b < nb ? __ldg(&a.power[si * nb + b]) : 0.0f;
+  for (int b = 0; b < kMaxBands; b++) sm.p[b][t] = b < nb ? gain * __ldg(&a.power[si * nb + b]) : 0.0f;
   sm.st[0][t] = 0.0f;
   sm.st[1][t] = 0.0f;
   sm.st[2][t] = 0.0f;

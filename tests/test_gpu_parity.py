@@ -459,3 +459,48 @@ def test_cast_rays_through_shared_vertices_and_edges(tracer):
             return (v[0] - u[0]) * (w[1] - u[1]) - (v[1] - u[1]) * (w[0] - u[0])
         s = [side(a, b, p), side(b, c, p), side(c, a, p)]
         assert min(s) >= -1e-5 * 5.0 or max(s) <= 1e-5 * 5.0, (p, i, s)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_directional_sources_match_oracle(tracer, oracle_mod, precision):
+    # Section 2: a source's energy is split between the beams by its power in
+    # each direction.  Three sources of the tiny city: two with seeded
+    # patterns (one of them reused), one omnidirectional; levels against the
+    # oracle.  The library and the oracle number the beams each in their own
+    # order, so the oracle gets the gains of the beam with the same axis
+    from paper_1912_03998_gb300 import btrace
+    w = synth.tiny_city(seed=6)
+    n_b = 20 * 4 ** w.level
+    axes = btrace.bt_beam_axes(tracer.ctx, w.level)
+    assert axes.shape == (n_b, 3) and np.allclose(np.linalg.norm(axes, axis=1), 1.0, atol=1e-6)
+    dirs, _ = oracle_mod.beam_table(w.level)
+    ax = dirs.sum(axis=1)
+    ax /= np.linalg.norm(ax, axis=1, keepdims=True)
+    match = (axes.astype(np.float64) @ ax.T).argmax(axis=1)  # oracle beam of each library beam
+    assert np.array_equal(np.sort(match), np.arange(n_b))
+    assert np.abs(axes - ax[match]).max() < 1e-6
+    rng = np.random.Generator(np.random.PCG64(21))
+    # a smooth pattern (louder towards +x) and a rough one (random gains)
+    patterns = np.stack([1.0 + 0.8 * axes[:, 0], rng.uniform(0.0, 2.0, n_b)]).astype(np.float32)
+    src = np.concatenate([w.src, w.src[:1] + np.float32([15.0, -10.0, 0.0]), w.src[:1] + np.float32([-20.0, 5.0, 0.0])])
+    power = np.concatenate([w.power, w.power[:1], w.power[:1] * 0.5]).astype(np.float32)
+    pattern_of = np.array([0] * len(w.src) + [1, -1], np.int32)
+    sid = btrace.bt_load_scene(tracer.ctx, w.scene.verts, w.scene.tris, w.scene.mat, w.scene.refl)
+    try:
+        btrace.bt_set_sources(tracer.ctx, sid, src, power, w.level)
+        btrace.bt_set_microphones(tracer.ctx, sid, w.mics)
+        btrace.bt_set_directivity(tracer.ctx, sid, patterns, pattern_of)
+        prec = {"mixed": btrace.BT_PREC_MIXED, "fp64": btrace.BT_PREC_FP64}[precision]
+        btrace.bt_trace(tracer.ctx, sid, tracer.params(w.max_order, precision=prec))
+        L = np.empty((len(w.mics), power.shape[1]), np.float64)
+        btrace.bt_read_levels(tracer.ctx, sid, L)
+        # a bad pattern index is rejected and leaves the scene omnidirectional
+        with pytest.raises(btrace.BtError):
+            btrace.bt_set_directivity(tracer.ctx, sid, patterns, np.array([5] * len(src), np.int32))
+    finally:
+        btrace.bt_unload_scene(tracer.ctx, sid)
+    oracle_patterns = np.empty_like(patterns)
+    oracle_patterns[:, match] = patterns
+    r = oracle_mod.trace(oracle_mod.Scene(w.scene), src, power, w.level, w.mics, w.max_order,
+                         directivity=oracle_patterns, pattern_of=pattern_of)
+    assert_parity(L, level_db(r["I"]), f"tiny city, directional sources, {precision}")
