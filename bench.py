@@ -45,8 +45,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="district", choices=["district", "tiny", "batch", "serve"],
+    ap.add_argument("--workload", default="district", choices=["district", "tiny", "batch", "serve", "volume"],
                     help="batch: 64 cities of uneven size traced as one batch (CUDA graph); "
+                         "volume: the district with 13.75 M microphones on a 4 m 3D grid; "
                          "serve: Poisson query streams against 8 resident cities")
     ap.add_argument("--rates", default="50,200,1000,2000", help="serve: arrival rates, queries/s")
     ap.add_argument("--queries", type=int, default=200, help="serve: queries per rate")
@@ -74,6 +75,10 @@ def make_workload(name, rank=0, n_sources=None):
     from paper_1912_03998_gb300 import synth
     if name == "tiny":
         w = synth.tiny_city(seed=1 + rank)
+    elif name == "volume":
+        w = synth.district(seed=2, n_sources=1000)
+        w = synth.Workload("district-volume", w.scene, w.src, w.power, synth.volume_mics(), w.level,
+                           w.max_order, w.tiles, dict(w.info))
     else:
         w = synth.district(seed=2, n_sources=1000)
         if rank:  # independent traffic snapshot per rank, same city
@@ -164,9 +169,13 @@ def trace_kernel_name(tiles):
     return "k_trace" if tuple(tiles) == (1, 1) else "k_trace_tiled"
 
 
-def ncu_traffic(kernel):
+def ncu_traffic(kernel, args, tiles):
     """DRAM bytes per launch of the traversal kernel from the committed ncu
-    summary, only if it was taken on the current kernel source."""
+    summary, only if it was taken on the current kernel source and on this
+    workload (the full district, MIXED, split 4x4 or unsplit)."""
+    if (args.workload != "district" or args.sources is not None or args.precision != "mixed"
+            or tuple(tiles) not in ((4, 4), (1, 1))):
+        return None
     p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     if not os.path.exists(p):
         return None
@@ -248,21 +257,36 @@ def run_ours(args, rank, world):
     segs = sum(s["segments"] for s in stats)
     contrib = sum(s["contributions"] for s in stats)
     total_ms = sum(ms)
-    # roofline of the dominant kernel: algorithmic node + triangle bytes per
-    # launch (counted in one extra, untimed trace) over its mean launch time
+    # roofline of the dominant kernel: its algorithmic bytes per launch over
+    # its mean launch time; for the traversal, node + triangle bytes counted
+    # in one extra, untimed trace
     tk = sum(s["trace_kernel_ms"] for s in stats)
     sk = sum(s["scatter_kernel_ms"] for s in stats)
     tl = sum(s["trace_launches"] for s in stats)
     params.count_work = 1
     cst = step(d_in, d_level)
     params.count_work = 0
-    alg_bytes = 64.0 * cst["nodes_visited"] + 48.0 * cst["tris_tested"]
-    bytes_per_launch = alg_bytes / max(1, cst["trace_launches"])
-    achieved = bytes_per_launch / (tk / max(1, tl) * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = ncu_traffic(trace_kernel_name(tiles))
+    if sk > tk:
+        # the scatter dominates (a volume of microphones): per launch, the
+        # segment records read (192 B each), a 16 B microphone position per
+        # candidate, and per contribution the 8 float64 accumulators and the
+        # int32 count read and written (136 B)
+        kernel = "k_scatter"
+        sl = sum(s["scatter_launches"] for s in stats)
+        last = stats[-1]
+        alg_bytes = 192.0 * last["emitted"] + 16.0 * last["candidates"] + 136.0 * last["contributions"]
+        bytes_per_launch = alg_bytes / max(1, last["scatter_launches"])
+        achieved = bytes_per_launch / (sk / max(1, sl) * 1e-3) / 1e9
+        traffic = None
+    else:
+        kernel = trace_kernel_name(tiles)
+        alg_bytes = 64.0 * cst["nodes_visited"] + 48.0 * cst["tris_tested"]
+        bytes_per_launch = alg_bytes / max(1, cst["trace_launches"])
+        achieved = bytes_per_launch / (tk / max(1, tl) * 1e-3) / 1e9
+        traffic = ncu_traffic(kernel, args, tiles)
     res = dict(segs=segs, contrib=contrib, total_ms=total_ms, ms=ms, launches=launches,
-               stats=stats[-1], tk=tk, sk=sk, tl=tl, alg_bytes=alg_bytes,
+               stats=stats[-1], tk=tk, sk=sk, tl=tl, alg_bytes=alg_bytes, kernel=kernel,
                bytes_per_launch=bytes_per_launch, achieved=achieved, peak=peak,
                peak_kind=peak_kind, traffic=traffic, clocks=clk.summary(), work=cst, w=w,
                tiles=tiles, untiled=untiled)
@@ -531,7 +555,7 @@ def main():
             "data": "synthetic", "config": cfg, "clocks": res["clocks"],
             "gpu_launches": res["launches"],
             "contributions_per_s": res["contrib"] * world / (total_ms * 1e-3),
-            "roofline": {"kernel": trace_kernel_name(res["tiles"]), "bound": "hbm",
+            "roofline": {"kernel": res["kernel"], "bound": "hbm",
                          "achieved": res["achieved"],
                          "peak": res["peak"], "unit": "GB/s",
                          "frac": res["achieved"] / res["peak"], "traffic": res["traffic"],

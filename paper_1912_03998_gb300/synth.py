@@ -262,6 +262,15 @@ DIST_EXTENT = DIST_PITCH * DIST_NBLK + DIST_ROAD  # 1990 m of roads and blocks
 DIST_MIC_SIDE = 2000.0
 
 
+def volume_mics(n_side: int = 500, n_heights: int = 55, pitch: float = 4.0, z0: float = 1.5) -> np.ndarray:
+    """A regular 3D microphone grid over the district (the paper's receivers
+    fill the city's volume on a 4 m grid): n_side x n_side cell-centred
+    columns, n_heights levels from z0 up in steps of `pitch`; 500 x 500 x 55
+    = 13.75 M points up to 217.5 m, above the tallest building."""
+    return np.concatenate([mic_grid(0.0, 0.0, DIST_MIC_SIDE, DIST_MIC_SIDE, n_side, n_side, z0 + pitch * k)
+                           for k in range(n_heights)]).astype(np.float32)
+
+
 def _kd_lots(rng, x0, y0, x1, y1, depth):
     if depth == 0:
         return [(x0, y0, x1, y1)]
