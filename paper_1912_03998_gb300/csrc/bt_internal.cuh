@@ -301,7 +301,6 @@ __device__ __forceinline__ Plane64 ldg_d4(const Plane64 *p) {
   r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
   return r;
 }
-__device__ __forceinline__ float3 to_f3(double3 a) { return make_float3((float)a.x, (float)a.y, (float)a.z); }
 
 // Moller & Trumbore (1997) in float64, two-sided, edges inclusive: the
 // float64 re-test of an ambiguous float32 decision, and the float64 hit
@@ -408,7 +407,6 @@ __device__ __forceinline__ df3 df3_mirror(df3 v, df3 n) {
   return df3_sub(v, df3_scale(n, k));
 }
 __device__ __forceinline__ float3 df3_hi(df3 a) { return make_float3(a.x.hi, a.y.hi, a.z.hi); }
-__device__ __forceinline__ double df_to_d(df a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ df d_to_df(double x) {
   float hi = (float)x;
   return df{hi, (float)(x - (double)hi)};
