@@ -562,7 +562,8 @@ def main():
                          "peak_kind": res["peak_kind"],
                          "algorithmic_bytes_per_launch": res["bytes_per_launch"],
                          "launches_per_step": res["tl"] / args.steps,
-                         "kernel_ms_per_step": res["tk"] / args.steps,
+                         "kernel_ms_per_step": (res["sk"] if res["kernel"] == "k_scatter" else res["tk"]) / args.steps,
+                         "trace_kernel_ms_per_step": res["tk"] / args.steps,
                          "scatter_kernel_ms_per_step": res["sk"] / args.steps,
                          "nodes_per_segment": res["work"]["nodes_visited"] / max(1, res["work"]["segments"]),
                          "tris_per_segment": res["work"]["tris_tested"] / max(1, res["work"]["segments"])},
