@@ -151,9 +151,15 @@ class Clocks:
 
 # ------------------------------------------------------------------ helpers
 def kernel_hash():
+    """Hash of the traversal kernels' source with comments and blank space
+    removed, so that a comment edit does not orphan a committed capture."""
+    import re
     h = hashlib.sha256()
     for f in ("trace.cu", "bt_internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1912_03998_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_1912_03998_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

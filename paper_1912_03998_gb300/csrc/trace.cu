@@ -1287,7 +1287,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace_tiled(TraceArgs a, c
       continue;
     }
     idle_since = 0;
-    // ---- search: until kRefillLanes lanes need service (a finished search,
+    // ---- search: until kRefillTiled lanes need service (a finished search,
     // or no lineage while fresh ones remain) or no lane is searching
     {
       const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), v.t_eps, ls.dns);

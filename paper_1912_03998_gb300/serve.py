@@ -38,6 +38,41 @@ def query_bytes(q) -> int:
     return len(q.src) * BYTES_PER_SOURCE + len(q.mics) * BYTES_PER_MIC + (1 << 16)
 
 
+def step_shares(left, work, budget: int, oldest_share: float = 1.0, quantum: int = 0):
+    """Lineages each active query traces in the next step.
+
+    left[i]: the query's lineages still to trace; work[i]: its remaining
+    work (lineages times segments per lineage); queries in admission order
+    (index 0 the oldest).  The oldest query first takes up to `oldest_share`
+    of the step's lineage budget (all of it by default: first come, first
+    served, so a big query is not held back by the stream behind it); what
+    is left goes to the queries shortest remaining work first, so small
+    queries finish in the step after their arrival.  With a nonzero
+    `quantum` every query the budget did not reach still gets that many
+    lineages (the step then exceeds the budget by up to len(left) quanta).
+    """
+    n = len(left)
+    share = [0] * n
+    if n == 0:
+        return share
+    b = int(budget)
+    if oldest_share > 0.0:
+        share[0] = min(left[0], int(budget * oldest_share))
+        b -= share[0]
+    for i in sorted(range(n), key=lambda i: work[i]):
+        if b <= 0:
+            break
+        g = min(left[i] - share[i], b)
+        share[i] += g
+        b -= g
+    if b <= 0 and quantum > 0:
+        q = max(1, min(int(quantum), int(budget) // n))
+        for i in range(n):
+            if share[i] == 0 and left[i] > 0:
+                share[i] = min(left[i], q)
+    return share
+
+
 @dataclass
 class Done:
     index: int
@@ -104,32 +139,9 @@ class Server:
         self.host_s["admit"] += t1 - t0
         if not self.active:
             return False
-        # The oldest admitted query first takes `oldest_share` of the step's
-        # lineage budget (all of it by default: first come, first served, so
-        # a big query is not held back by the stream behind it); what is left
-        # goes to the other queries shortest remaining work first (lineages
-        # times segments per lineage, K + 1), so small queries finish in the
-        # step after their arrival.  With a nonzero `quantum` every query the
-        # budget did not reach still gets that many lineages.
         left = [a["total"] - a["next"] for a in self.active]
-        order = sorted(range(len(left)), key=lambda i: left[i] * (self.active[i]["q"].max_order + 1))
-        share = [0] * len(left)
-        budget = self.step_lineages
-        if self.oldest_share > 0.0:
-            # the oldest admitted query first takes its share of the budget
-            share[0] = min(left[0], int(self.step_lineages * self.oldest_share))
-            budget -= share[0]
-        for i in order:
-            if budget <= 0:
-                break
-            g = min(left[i] - share[i], budget)
-            share[i] += g
-            budget -= g
-        if budget <= 0 and self.quantum > 0:
-            quantum = max(1, min(self.quantum, self.step_lineages // len(left)))
-            for i in order:
-                if share[i] == 0 and left[i] > 0:
-                    share[i] = min(left[i], quantum)
+        work = [l * (a["q"].max_order + 1) for l, a in zip(left, self.active)]
+        share = step_shares(left, work, self.step_lineages, self.oldest_share, self.quantum)
         ids, begins, ends, params = [], [], [], []
         for a, s in zip(self.active, share):
             if s > 0:

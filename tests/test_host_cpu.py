@@ -1,0 +1,51 @@
+"""Host-side logic that needs no GPU: the server's step allocation and the
+volumetric microphone grid."""
+import numpy as np
+
+from paper_1912_03998_gb300 import serve, synth
+
+
+def test_step_shares_oldest_first_then_shortest_remaining():
+    left = [5000, 300, 40, 2000]
+    work = [5000 * 7, 300 * 4, 40 * 7, 2000 * 4]
+    # the oldest query takes the whole budget when it can use it
+    assert serve.step_shares(left, work, 4096) == [4096, 0, 0, 0]
+    # what it leaves goes shortest remaining work first
+    s = serve.step_shares([100] + left[1:], [700] + work[1:], 1000)
+    assert s == [100, 300, 40, 560]
+    # pure shortest remaining first
+    s = serve.step_shares(left, work, 1000, oldest_share=0.0)
+    assert s == [0, 300, 40, 660]
+    # a share of the budget for the oldest query
+    s = serve.step_shares(left, work, 1000, oldest_share=0.5)
+    assert s == [500, 300, 40, 160]
+
+
+def test_step_shares_invariants():
+    rng = np.random.Generator(np.random.PCG64(3))
+    for _ in range(500):
+        n = int(rng.integers(1, 20))
+        left = [int(x) for x in rng.integers(0, 10000, n)]
+        work = [l * int(k) for l, k in zip(left, rng.integers(4, 8, n))]
+        budget = int(rng.integers(1, 30000))
+        frac = float(rng.choice([0.0, 0.25, 0.5, 1.0]))
+        q = int(rng.choice([0, 64]))
+        s = serve.step_shares(left, work, budget, frac, q)
+        assert all(0 <= a <= l for a, l in zip(s, left))
+        if q == 0:
+            assert sum(s) <= budget
+            # the budget is used up unless every query got all it has left
+            assert sum(s) == min(budget, sum(left))
+        else:
+            assert sum(s) <= budget + n * q
+
+
+def test_volume_microphone_grid():
+    m = synth.volume_mics(n_side=20, n_heights=5)
+    assert m.shape == (20 * 20 * 5, 3) and m.dtype == np.float32
+    zs = np.unique(m[:, 2])
+    assert np.allclose(zs, 1.5 + 4.0 * np.arange(5))
+    xs = np.unique(m[:, 0])
+    assert len(xs) == 20 and np.allclose(np.diff(xs), synth.DIST_MIC_SIDE / 20)
+    full = synth.volume_mics()
+    assert full.shape == (13_750_000, 3) and float(full[:, 2].max()) == 217.5
