@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--step-lineages", type=int, default=1 << 22, help="serve: lineages per server step")
     ap.add_argument("--oldest-share", type=float, default=1.0,
                     help="serve: share of a step's lineages that goes to the oldest query first")
+    ap.add_argument("--small-lineages", type=int, default=0,
+                    help="serve: queries with at most this many lineages left go first")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the short served-latency measurement in the default line")
     ap.add_argument("--autotune", action="store_true",
@@ -385,12 +387,13 @@ def run_batch(args):
 
 
 # ------------------------------------------------------------------ serving
-def serve_once(tr, cities, rate, n_queries, seed, prec, step_lineages, oldest_share=1.0):
+def serve_once(tr, cities, rate, n_queries, seed, prec, step_lineages, oldest_share=1.0, small_lineages=0):
     """One Poisson stream served by the loop and, on the same stream, one
     query at a time; latency summaries of both."""
     from paper_1912_03998_gb300 import btrace, serve, synth
     qs = synth.serving_queries(seed=seed, n_queries=n_queries, n_cities=len(cities), rate_qps=rate)
-    srv = serve.Server(tr, cities, step_lineages=step_lineages, precision=prec, oldest_share=oldest_share)
+    srv = serve.Server(tr, cities, step_lineages=step_lineages, precision=prec, oldest_share=oldest_share,
+                       small_lineages=small_lineages)
     try:
         srv.run(qs[:4], realtime=False)  # warm-up through both paths
         serve.run_plain(tr, srv.city_ids, qs[:4], precision=prec, realtime=False)
@@ -426,7 +429,7 @@ def run_serve(args):
     with Clocks(0) as clk:
         for k, rate in enumerate(float(r) for r in args.rates.split(",")):
             rows.append(serve_once(tr, cities, rate, args.queries, 100 + k, prec, args.step_lineages,
-                                   args.oldest_share))
+                                   args.oldest_share, args.small_lineages))
     tr.close()
     head = rows[-1]
     line = {"metric": "served p50/p99 latency and queries/s", "value": head["served"]["queries_per_s"],
@@ -437,6 +440,7 @@ def run_serve(args):
                                    "queries of 1-2,000 sources (0.001-1 W per band), 1k-250k microphones, "
                                    "L=4, K 3-6", "queries_per_rate": args.queries,
                        "step_lineages": args.step_lineages, "oldest_share": args.oldest_share,
+                       "small_lineages": args.small_lineages,
                        "precision": args.precision, "parallelism": "1 GPU"},
             "clocks": clk.summary(), "rates": rows}
     print(json.dumps(line))
@@ -590,7 +594,7 @@ def main():
         tr = btrace.Tracer(0)
         try:
             line["serving"] = serve_once(tr, synth.serving_cities(seed=5, n=8), 200.0, 100, 100, prec,
-                                         args.step_lineages, args.oldest_share)
+                                         args.step_lineages, args.oldest_share, args.small_lineages)
         finally:
             tr.close()
     if not args.no_cpu_baseline:

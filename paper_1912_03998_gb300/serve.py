@@ -38,27 +38,35 @@ def query_bytes(q) -> int:
     return len(q.src) * BYTES_PER_SOURCE + len(q.mics) * BYTES_PER_MIC + (1 << 16)
 
 
-def step_shares(left, work, budget: int, oldest_share: float = 1.0, quantum: int = 0):
+def step_shares(left, work, budget: int, oldest_share: float = 1.0, quantum: int = 0, small: int = 0):
     """Lineages each active query traces in the next step.
 
     left[i]: the query's lineages still to trace; work[i]: its remaining
     work (lineages times segments per lineage); queries in admission order
-    (index 0 the oldest).  The oldest query first takes up to `oldest_share`
-    of the step's lineage budget (all of it by default: first come, first
-    served, so a big query is not held back by the stream behind it); what
-    is left goes to the queries shortest remaining work first, so small
-    queries finish in the step after their arrival.  With a nonzero
-    `quantum` every query the budget did not reach still gets that many
-    lineages (the step then exceeds the budget by up to len(left) quanta).
+    (index 0 the oldest).  Queries with at most `small` lineages left are
+    served first, shortest remaining work first, so that they finish in this
+    step.  Then the oldest query takes up to `oldest_share` of the step's
+    lineage budget (all of it by default: first come, first served, so a big
+    query is not held back by the stream behind it); what is left goes to
+    the queries shortest remaining work first.  With a nonzero `quantum`
+    every query the budget did not reach still gets that many lineages (the
+    step then exceeds the budget by up to len(left) quanta).
     """
     n = len(left)
     share = [0] * n
     if n == 0:
         return share
     b = int(budget)
-    if oldest_share > 0.0:
-        share[0] = min(left[0], int(budget * oldest_share))
-        b -= share[0]
+    if small > 0:
+        for i in sorted(range(n), key=lambda i: work[i]):
+            if left[i] > small or left[i] > b:
+                continue
+            share[i] = left[i]
+            b -= left[i]
+    if oldest_share > 0.0 and share[0] < left[0] and b > 0:
+        g = min(left[0] - share[0], int(budget * oldest_share), b)
+        share[0] += g
+        b -= g
     for i in sorted(range(n), key=lambda i: work[i]):
         if b <= 0:
             break
@@ -90,10 +98,11 @@ class Done:
 class Server:
     def __init__(self, tracer, cities, step_lineages: int = 1 << 22, quantum: int = 0,
                  mem_budget: int = 4 << 30, max_active: int = 48, precision: int = btrace.BT_PREC_MIXED,
-                 oldest_share: float = 1.0):
+                 oldest_share: float = 1.0, small_lineages: int = 0):
         self.tr = tracer
         self.quantum = int(quantum)
         self.oldest_share = float(oldest_share)
+        self.small_lineages = int(small_lineages)
         self.city_ids = [tracer.load_geometry(w) for w in cities]
         self.step_lineages = int(step_lineages)
         self.mem_budget = int(mem_budget)
@@ -141,7 +150,7 @@ class Server:
             return False
         left = [a["total"] - a["next"] for a in self.active]
         work = [l * (a["q"].max_order + 1) for l, a in zip(left, self.active)]
-        share = step_shares(left, work, self.step_lineages, self.oldest_share, self.quantum)
+        share = step_shares(left, work, self.step_lineages, self.oldest_share, self.quantum, self.small_lineages)
         ids, begins, ends, params = [], [], [], []
         for a, s in zip(self.active, share):
             if s > 0:

@@ -49,3 +49,14 @@ def test_volume_microphone_grid():
     assert len(xs) == 20 and np.allclose(np.diff(xs), synth.DIST_MIC_SIDE / 20)
     full = synth.volume_mics()
     assert full.shape == (13_750_000, 3) and float(full[:, 2].max()) == 217.5
+
+
+def test_step_shares_small_queries_first():
+    left = [5_000_000, 200_000, 40_000, 3_000_000]
+    work = [l * 5 for l in left]
+    # without the small-query rule the oldest takes the whole step
+    assert serve.step_shares(left, work, 1 << 22) == [1 << 22, 0, 0, 0]
+    # with it the two small queries finish in this step, the oldest takes the rest
+    s = serve.step_shares(left, work, 1 << 22, small=1 << 18)
+    assert s[1:3] == [200_000, 40_000] and s[0] == (1 << 22) - 240_000 and s[3] == 0
+    assert sum(s) == 1 << 22
