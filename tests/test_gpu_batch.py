@@ -104,3 +104,61 @@ def test_batch_rejects_bad_requests(tracer):
     finally:
         for sid in sids:
             btrace.bt_unload_scene(tracer.ctx, sid)
+
+
+def test_batch_and_ranges_carry_directional_sources(tracer):
+    # a scene with directional sources traced alone, in a batch with another
+    # scene, and through the serving step (ranges of lineages, accumulated)
+    # gives the same result every way; the directivity calls check their
+    # state and arguments
+    from paper_1912_03998_gb300 import btrace
+    ws = uneven_workloads()[:2]
+    w = ws[1]
+    n_b = 20 * 4 ** w.level
+    axes = btrace.bt_beam_axes(tracer.ctx, w.level)
+    patterns = np.stack([0.5 + axes[:, 2] ** 2, np.linspace(0.0, 2.0, n_b)]).astype(np.float32)
+    pattern_of = np.array([1, -1, 0][:len(w.src)], np.int32)
+    sids = [tracer.load(x) for x in ws]
+    try:
+        btrace.bt_set_directivity(tracer.ctx, sids[1], patterns, pattern_of)
+        p = [tracer.params(x.max_order) for x in ws]
+        btrace.bt_trace(tracer.ctx, sids[1], p[1])
+        alone = read(tracer, sids[1], w)
+        b = btrace.bt_batch_create(tracer.ctx, sids, p)
+        try:
+            btrace.bt_batch_run(tracer.ctx, b)
+            batched = read(tracer, sids[1], w)
+        finally:
+            btrace.bt_batch_destroy(b)
+        assert (batched["cnt"] == alone["cnt"]).all()
+        assert np.allclose(batched["I"], alone["I"], rtol=1e-9, atol=0)
+        # in two ranges, accumulated
+        n_lin = len(w.src) * n_b
+        btrace.bt_set_microphones(tracer.ctx, sids[1], w.mics)  # zero the accumulators
+        for lo, hi in ((0, n_lin // 3), (n_lin // 3, n_lin)):
+            btrace.bt_trace_ranges(tracer.ctx, [sids[1], sids[0]], [lo, 0], [hi, 1], [p[1], p[0]], accumulate=True)
+        ranged = read(tracer, sids[1], w)
+        assert (ranged["cnt"] == alone["cnt"]).all()
+        assert np.allclose(ranged["I"], alone["I"], rtol=1e-9, atol=0)
+        # the patterns change the result, and clearing them restores the
+        # omnidirectional trace
+        btrace.bt_set_directivity(tracer.ctx, sids[1], None, None)
+        btrace.bt_trace(tracer.ctx, sids[1], p[1])
+        omni = read(tracer, sids[1], w)
+        assert not np.allclose(omni["I"], alone["I"])
+        r = tracer.run(w)
+        assert np.allclose(omni["I"], r["I"], rtol=1e-9, atol=0)
+        btrace.bt_unload_scene(tracer.ctx, r["scene_id"])
+        # errors: a negative gain, a level out of range, an unloaded scene
+        bad = patterns.copy()
+        bad[0, 5] = -1.0
+        with pytest.raises(btrace.BtError) as e:
+            btrace.bt_set_directivity(tracer.ctx, sids[1], bad, pattern_of)
+        assert e.value.code == btrace.BT_E_INVALID
+        with pytest.raises(btrace.BtError):
+            btrace.bt_beam_axes(tracer.ctx, 9)
+    finally:
+        for sid in sids:
+            btrace.bt_unload_scene(tracer.ctx, sid)
+    with pytest.raises(btrace.BtError) as e:
+        btrace.bt_set_directivity(tracer.ctx, sids[1], patterns, pattern_of)
