@@ -151,6 +151,41 @@ def test_ground_plane_closed_form(oracle_mod):
     assert all(a < b for a, b in zip(full_fraction, full_fraction[1:]))
 
 
+def test_directional_ground_plane_closed_form(oracle_mod):
+    # the ground-plane closed form with a directional source: the direct term
+    # carries the gain of the beam holding the direction to the microphone,
+    # the image term the gain of the beam holding the direction to the
+    # reflection point (the image direction mirrored in the ground)
+    for level in (4, 5):
+        w = synth.ground_only(seed=4, level=level, half=20.0)
+        dirs, _ = oracle_mod.beam_table(level)
+        gains = np.random.Generator(np.random.PCG64(level)).uniform(0.2, 2.0, (1, len(dirs))).astype(np.float32)
+        r = oracle_mod.trace(oracle_mod.Scene(w.scene), w.src, w.power, level, w.mics, w.max_order,
+                             directivity=gains, pattern_of=np.zeros(1, np.int32))
+        s = w.src[0].astype(np.float64)
+        m = w.mics.astype(np.float64)
+        img = s * np.array([1, 1, -1])
+        n = np.cross(dirs, np.roll(dirs, -1, axis=1))
+
+        def beam_of(v):
+            u = v / np.linalg.norm(v, axis=1, keepdims=True)
+            inside = (np.einsum("nji,mi->mnj", n, u) >= 0).all(axis=2)
+            assert (inside.sum(axis=1) >= 1).all()
+            return inside.argmax(axis=1)
+
+        g1 = gains[0, beam_of(m - s)].astype(np.float64)
+        g2 = gains[0, beam_of((m - img) * np.array([1, 1, -1]))].astype(np.float64)
+        r1 = np.linalg.norm(m - s, axis=1)
+        r2 = np.linalg.norm(m - img, axis=1)
+        expect = g1 / (4 * np.pi * r1 ** 2) + F32_07 * g2 / (4 * np.pi * r2 ** 2)
+        rho = np.hypot(m[:, 0] - s[0], m[:, 1] - s[1])
+        margin = np.arctan2(m[:, 2] - img[2], rho) > _max_beam_diameter(oracle_mod, level)
+        assert margin.sum() > 10
+        # ties (a direction on a shared cone edge) are measure-zero here
+        got = r["I"][margin] / expect[margin][:, None]
+        assert np.abs(got - 1).max() < 1e-12
+
+
 def test_single_wall_closed_form(oracle_mod):
     # a vertical wall at x = 0 (energy coefficient 0.9): direct plus the image
     # mirrored to (-x, y, z); exact for microphones whose image direction lies
