@@ -299,7 +299,8 @@ int bt_scene_share(bt_ctx *ctx, int32_t base_scene_id, int32_t *scene_id_out);
  * current result instead of replacing it, so a scene's lineages can be
  * traced over several calls -- the step of a continuous-batching server.
  * params[i] as for bt_trace (tiles 1x1; precision, blocks_per_sm and
- * count_work must agree).  Synchronous; totals with bt_ranges_stats. */
+ * count_work must agree).  One scene (n = 1) runs the single-scene kernels,
+ * several the batch kernels.  Synchronous; totals with bt_ranges_stats. */
 #define BT_ACCUMULATE 1
 int bt_trace_ranges(bt_ctx *ctx, int32_t n, const int32_t *scene_ids, const int64_t *lineage_begin,
                     const int64_t *lineage_end, const bt_trace_params *params, int32_t flags);
