@@ -177,11 +177,23 @@ def trace(scene: Scene, src, power, level, mics, max_order, alpha=None, energy_t
     return dict(I=I, cnt=cnt, stats=st, log=log)
 
 
+def beam_axes(level: int):
+    """Unit axes [N, 3] of the oracle's beams (normalised edge-direction sums)."""
+    dirs, _ = beam_table(level)
+    ax = dirs.sum(axis=1)
+    return ax / np.linalg.norm(ax, axis=1, keepdims=True)
+
+
 def trace_workload(w, tiles=None, **kw):
-    """Convenience: trace a synth.Workload with the oracle."""
+    """Convenience: trace a synth.Workload with the oracle (directional
+    sources sampled at the oracle's own beam axes)."""
     sc = Scene(w.scene, tiles if tiles is not None else (1, 1))
     if tiles is not None and tuple(tiles) != (1, 1):
         kw.setdefault("hit_mode", HIT_TILED)
+    d = getattr(w, "directivity", None)
+    if d is not None:
+        kw.setdefault("directivity", d.gains(beam_axes(w.level)))
+        kw.setdefault("pattern_of", d.pattern_of)
     return trace(sc, w.src, w.power, w.level, w.mics, w.max_order, **kw)
 
 

@@ -344,6 +344,10 @@ class Tracer:
     def load(self, w) -> int:
         sid = bt_load_scene(self.ctx, w.scene.verts, w.scene.tris, w.scene.mat, w.scene.refl)
         bt_set_sources(self.ctx, sid, w.src, w.power, w.level)
+        d = getattr(w, "directivity", None)
+        if d is not None:
+            # the patterns sampled at this library's beam axes
+            bt_set_directivity(self.ctx, sid, d.gains(bt_beam_axes(self.ctx, w.level)), d.pattern_of)
         bt_set_microphones(self.ctx, sid, w.mics)
         return sid
 

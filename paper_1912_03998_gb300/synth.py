@@ -54,6 +54,30 @@ class Scene:
 
 
 @dataclass
+class Directivity:
+    """Directional sources as functions of direction, so that every tracer
+    samples them at its own beams: patterns[k] maps unit directions [n, 3]
+    to gains [n] (>= 0), pattern_of[s] is source s's pattern (-1 =
+    omnidirectional)."""
+    patterns: list
+    pattern_of: np.ndarray  # int32 [n_s]
+
+    def gains(self, axes) -> np.ndarray:
+        """Gains [n_patterns, n_beams] float32 at the beam axes [n_beams, 3]."""
+        axes = np.asarray(axes, np.float64)
+        return np.stack([np.asarray(f(axes), np.float64) for f in self.patterns]).astype(np.float32)
+
+
+def cardioid(axis, a: float = 1.0):
+    """A pattern 1 + a (u . axis): louder towards `axis`; its mean over the
+    sphere is 1 (the source keeps its total power), and it stays >= 0 for
+    0 <= a <= 1."""
+    ax = np.asarray(axis, np.float64)
+    ax = ax / np.linalg.norm(ax)
+    return lambda u: 1.0 + a * (np.asarray(u, np.float64) @ ax)
+
+
+@dataclass
 class Workload:
     name: str
     scene: Scene
@@ -64,17 +88,21 @@ class Workload:
     max_order: int  # K: reflections 0..K are traced
     tiles: tuple = (1, 1)
     info: dict = field(default_factory=dict)
+    directivity: Directivity = None  # None: every source omnidirectional
 
     def subset_sources(self, idx) -> "Workload":
         idx = np.asarray(idx)
+        d = self.directivity
+        if d is not None:
+            d = Directivity(d.patterns, np.asarray(d.pattern_of)[idx].copy())
         return Workload(self.name + f"[{len(idx)} src]", self.scene, self.src[idx].copy(),
                         self.power[idx].copy(), self.mics, self.level, self.max_order,
-                        self.tiles, dict(self.info))
+                        self.tiles, dict(self.info), d)
 
     def with_mics(self, mics) -> "Workload":
         return Workload(self.name, self.scene, self.src, self.power,
                         np.ascontiguousarray(mics, dtype=np.float32), self.level,
-                        self.max_order, self.tiles, dict(self.info))
+                        self.max_order, self.tiles, dict(self.info), self.directivity)
 
 
 def _rng(seed: int) -> np.random.Generator:

@@ -504,3 +504,14 @@ def test_directional_sources_match_oracle(tracer, oracle_mod, precision):
     r = oracle_mod.trace(oracle_mod.Scene(w.scene), src, power, w.level, w.mics, w.max_order,
                          directivity=oracle_patterns, pattern_of=pattern_of)
     assert_parity(L, level_db(r["I"]), f"tiny city, directional sources, {precision}")
+
+
+def test_directional_workload_through_the_tracer(tracer, oracle_mod):
+    # directional sources given as functions of direction: the library and
+    # the oracle each sample them at their own beams' axes
+    w = synth.tiny_city(seed=8, n_sources=3)
+    w.directivity = synth.Directivity([synth.cardioid((0.3, -1.0, 0.2), 0.9)], np.array([0, -1, 0], np.int32))
+    g = gpu_run(tracer, w)
+    r, L = oracle_levels(oracle_mod, w)
+    assert_parity(g["level"], L, "tiny city, cardioid sources")
+    assert (g["cnt"] == r["cnt"]).mean() >= 0.999

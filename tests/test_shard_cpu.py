@@ -26,20 +26,27 @@ def test_source_blocks_partition_the_sources():
         shard.source_block(5, 2, 2)
 
 
-def _workload():
-    return synth.tiny_city(seed=3, level=3, max_order=3, n_sources=5)
+def _workload(directional=False):
+    w = synth.tiny_city(seed=3, level=3, max_order=3, n_sources=5)
+    if directional:
+        # two patterns and an omnidirectional source: the shards must carry
+        # each source's pattern with it
+        w.directivity = synth.Directivity([synth.cardioid((1.0, 0.0, 0.0), 0.8),
+                                           synth.cardioid((0.0, 1.0, 0.5), 0.5)],
+                                          np.array([0, 1, -1, 0, 1], np.int32))
+    return w
 
 
-def _rank_main(rank, world, port, out_dir):
+def _rank_main(rank, world, port, out_dir, directional=False):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     import torch
     import torch.distributed as dist
     from oracle import oracle as O
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        w = _workload()
+        w = _workload(directional)
         lo, hi = shard.source_block(len(w.src), rank, world)
-        r = O.trace(O.Scene(w.scene), w.src[lo:hi], w.power[lo:hi], w.level, w.mics, w.max_order)
+        r = O.trace_workload(w.subset_sources(np.arange(lo, hi)))
         I = torch.from_numpy(np.ascontiguousarray(r["I"], np.float64))
         cnt = torch.from_numpy(np.ascontiguousarray(r["cnt"], np.int32))
         shard.allreduce_result(I, cnt)
@@ -57,14 +64,19 @@ def _free_port():
     return port
 
 
-@pytest.mark.parametrize("world", [2, 3])
-def test_gloo_ranks_sum_to_the_full_result(oracle_mod, tmp_path, world):
+@pytest.mark.parametrize("world,directional", [(2, False), (3, False), (2, True)])
+def test_gloo_ranks_sum_to_the_full_result(oracle_mod, tmp_path, world, directional):
     pytest.importorskip("torch")
-    w = _workload()
-    full = oracle_mod.trace(oracle_mod.Scene(w.scene), w.src, w.power, w.level, w.mics, w.max_order)
+    w = _workload(directional)
+    full = oracle_mod.trace_workload(w)
+    if directional:
+        # the patterns matter: the omnidirectional result differs
+        omni = oracle_mod.trace(oracle_mod.Scene(w.scene), w.src, w.power, w.level, w.mics, w.max_order)
+        assert not np.allclose(omni["I"], full["I"])
     ctx = mp.get_context("spawn")
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, world, port, str(tmp_path))) for r in range(world)]
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, str(tmp_path), directional))
+             for r in range(world)]
     for p in procs:
         p.start()
     for p in procs:
