@@ -103,7 +103,8 @@ typedef struct {
   int64_t segments;       /* beam segments traced (one per axis-ray query) */
   int64_t hits;           /* segments whose axis ray hit a triangle */
   int64_t escapes;        /* segments whose axis ray left the scene */
-  int64_t emitted;        /* segments whose footprint overlapped the microphone grid */
+  int64_t emitted;        /* segments handed to the microphone scatter (those whose cone can
+                             reach the microphones' height range) */
   int64_t candidates;     /* microphones tested against a segment */
   int64_t contributions;  /* (microphone, segment) pairs inside the beam */
   int64_t handoffs;       /* rays passed from one sub-domain to the next through its queue */
@@ -180,10 +181,12 @@ int bt_set_directivity(bt_ctx *ctx, int32_t scene_id, const float *patterns, int
  * the rest of i (corner-0, corner-1, corner-2, centre child). */
 int bt_beam_axes(bt_ctx *ctx, int32_t icosa_level, float *axes);
 
-/* Microphones of a scene (Section 4: a regular grid of receivers).
- *   pos [n_m][3] float32.  They are binned on the device into an xy cell grid
- *   (Section 3: microphones are partitioned with the geometry).  The scene's
- *   accumulated result starts at zero. */
+/* Microphones of a scene (Section 4: a regular grid of receivers, filling a
+ * volume or a plane).
+ *   pos [n_m][3] float32, n_m <= 2^28.  They are binned on the device into an
+ *   xy cell grid with up to 16 height layers (Section 3: microphones are
+ *   partitioned with the geometry).  The scene's accumulated result starts
+ *   at zero.  Errors: BT_E_INVALID for NaN/inf positions. */
 int bt_set_microphones(bt_ctx *ctx, int32_t scene_id, const float *pos, int64_t n_m);
 
 /* Trace every beam of every source of the scene (Section 2, hybrid method)
