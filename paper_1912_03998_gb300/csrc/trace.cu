@@ -10,6 +10,10 @@
 //             band power) unless it cannot reach the microphones' height, and
 //             reflects the beam about the hit triangle's plane (image source);
 //             a lane whose lineage ends takes the next one at once.
+//   k_trace_tiled  the same over sub-domains (Section 3): one hierarchy per
+//             tile, hand-off queues between tiles and work stealing, all in
+//             one persistent launch.
+//   k_cast    the axis-ray query on its own (closest hit of given rays).
 //
 // Precision.  BT_PREC_FP32 carries the lineage in float32.  BT_PREC_MIXED
 // carries the image-source chain -- apex, cone normals, ray origin and
