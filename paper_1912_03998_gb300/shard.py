@@ -1,12 +1,19 @@
-"""Source sharding of one problem over several ranks (GPUs or contexts).
+"""Sharding one problem over several ranks (GPUs or contexts).
 
-Beams of different sources never interact (Section 2: every beam carries its
-own source's energy; Section 3: processes trace their own beams and their
-results are gathered), so the result for all sources is the sum of the
-results for disjoint subsets of them.  Each rank traces one contiguous block
-of the sources, the partial intensities and path counts are summed over the
-ranks by one all-reduce, and every rank installs the sum with bt_set_result
-and reads the levels through its own level kernel.
+Sources: beams of different sources never interact (Section 2: every beam
+carries its own source's energy; Section 3: processes trace their own beams
+and their results are gathered), so the result for all sources is the sum of
+the results for disjoint subsets of them.  Each rank traces one contiguous
+block of the sources, the partial intensities and path counts are summed
+over the ranks by one all-reduce, and every rank installs the sum with
+bt_set_result and reads the levels through its own level kernel.
+
+Microphones (Section 3, microphone partitioning: every process traces all
+beams and measures them at its own microphones): a microphone's result does
+not depend on the other microphones, so each rank traces every source
+against one contiguous block of the microphones and the blocks' levels are
+gathered in rank order.  This splits the scatter, which dominates when the
+microphones fill a volume, at the price of tracing every beam on every rank.
 """
 from __future__ import annotations
 
@@ -57,3 +64,41 @@ def trace_sharded(tracer, w, rank: int, world: int, group=None, **params):
     cnt_out = np.empty(n, np.int32)
     btrace.bt_read_levels(tracer.ctx, sid, level, I_out, cnt_out)
     return dict(level=level, I=I_out, cnt=cnt_out, scene_id=sid)
+
+
+def mic_block(n_mics: int, rank: int, world: int) -> tuple[int, int]:
+    """The block [lo, hi) of microphones owned by `rank` (as source_block)."""
+    return source_block(n_mics, rank, world)
+
+
+def gather_blocks(part, n_total: int, group=None):
+    """Concatenate per-rank blocks [lo, hi) of a result (rows of `part`, a
+    CPU or CUDA tensor, shaped [hi - lo, ...]) into the full [n_total, ...]
+    tensor on every rank, in rank order."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    full = torch.zeros((n_total,) + tuple(part.shape[1:]), dtype=part.dtype, device=part.device)
+    rank = dist.get_rank(group)
+    lo, hi = mic_block(n_total, rank, world)
+    full[lo:hi] = part
+    dist.all_reduce(full, op=dist.ReduceOp.SUM, group=group)
+    return full
+
+
+def trace_mic_sharded(tracer, w, rank: int, world: int, group=None, **params):
+    """Trace workload `w` with its microphones split over `world` ranks (every
+    rank traces all sources); every rank gets the levels, intensities and path
+    counts of all microphones.  Returns dict(level, I, cnt) as numpy arrays."""
+    import torch
+    import torch.distributed as dist
+    lo, hi = mic_block(len(w.mics), rank, world)
+    g = tracer.run(w.with_mics(w.mics[lo:hi]), **params)
+    btrace.bt_unload_scene(tracer.ctx, g["scene_id"])
+    on_gpu = dist.get_backend(group) == "nccl"
+    dev = torch.device("cuda", torch.cuda.current_device()) if on_gpu else torch.device("cpu")
+    out = {}
+    for k in ("level", "I", "cnt"):
+        out[k] = gather_blocks(torch.from_numpy(np.ascontiguousarray(g[k])).to(dev), len(w.mics), group).cpu().numpy()
+    return out
+

@@ -406,6 +406,22 @@ def test_source_shards_sum_to_the_full_trace(tracer):
     btrace.bt_unload_scene(tracer.ctx, sid)
 
 
+def test_microphone_blocks_gather_to_the_full_trace(tracer):
+    # Section 3's microphone partitioning: three blocks of the microphones,
+    # each traced against every source, concatenate to the one-trace result
+    from paper_1912_03998_gb300 import shard
+    w = synth.tiny_city(seed=9, level=4, max_order=4, n_sources=3)
+    full = gpu_run(tracer, w)
+    parts = []
+    for r in range(3):
+        lo, hi = shard.mic_block(len(w.mics), r, 3)
+        parts.append(gpu_run(tracer, w.with_mics(w.mics[lo:hi])))
+    cnt = np.concatenate([g["cnt"] for g in parts])
+    I = np.concatenate([g["I"] for g in parts])
+    assert (cnt == full["cnt"]).all()
+    assert np.allclose(I, full["I"], rtol=1e-9, atol=0)
+
+
 def test_cast_rays_through_shared_vertices_and_edges(tracer):
     # Rays straight down onto the shared vertices and edges of coplanar
     # triangle fans: every float32 test there is ambiguous, so the MIXED

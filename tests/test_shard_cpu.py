@@ -90,3 +90,54 @@ def test_gloo_ranks_sum_to_the_full_result(oracle_mod, tmp_path, world, directio
         c = np.load(tmp_path / f"c{r}.npy")
         assert (c == full["cnt"]).all()
         assert np.allclose(I, full["I"], rtol=1e-12, atol=0)
+
+
+def test_microphone_blocks_partition_the_microphones():
+    for n in (0, 7, 1024):
+        for world in (1, 2, 3):
+            blocks = [shard.mic_block(n, r, world) for r in range(world)]
+            assert blocks[0][0] == 0 and blocks[-1][1] == n
+            assert all(b == c for (a, b), (c, d) in zip(blocks, blocks[1:]))
+
+
+def _mic_rank_main(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch
+    import torch.distributed as dist
+    from oracle import oracle as O
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w = _workload(True)
+        lo, hi = shard.mic_block(len(w.mics), rank, world)
+        r = O.trace_workload(w.with_mics(w.mics[lo:hi]))
+        I = shard.gather_blocks(torch.from_numpy(np.ascontiguousarray(r["I"], np.float64)), len(w.mics))
+        cnt = shard.gather_blocks(torch.from_numpy(np.ascontiguousarray(r["cnt"], np.int32)), len(w.mics))
+        np.save(os.path.join(out_dir, f"mI{rank}.npy"), I.numpy())
+        np.save(os.path.join(out_dir, f"mc{rank}.npy"), cnt.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_microphone_blocks_gather_to_the_full_result(oracle_mod, tmp_path, world):
+    # Section 3's microphone partitioning: every rank traces all sources
+    # against its own block of microphones; the gathered blocks equal the
+    # one-process result exactly (a microphone's result depends on no other)
+    pytest.importorskip("torch")
+    w = _workload(True)
+    full = oracle_mod.trace_workload(w)
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_mic_rank_main, args=(r, world, port, str(tmp_path))) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        if p.is_alive():
+            p.kill()
+            p.join()
+        assert p.exitcode == 0
+    for r in range(world):
+        assert np.array_equal(np.load(tmp_path / f"mc{r}.npy"), full["cnt"])
+        assert np.array_equal(np.load(tmp_path / f"mI{r}.npy"), full["I"])
+
