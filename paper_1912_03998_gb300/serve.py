@@ -38,6 +38,13 @@ def query_bytes(q) -> int:
     return len(q.src) * BYTES_PER_SOURCE + len(q.mics) * BYTES_PER_MIC + (1 << 16)
 
 
+def set_query_directivity(ctx, sid, q):
+    """A query's directional sources, if it has any, sampled at the beams."""
+    d = getattr(q, "directivity", None)
+    if d is not None:
+        btrace.bt_set_directivity(ctx, sid, d.gains(btrace.bt_beam_axes(ctx, q.level)), d.pattern_of)
+
+
 def step_shares(left, work, budget: int, oldest_share: float = 1.0, quantum: int = 0, small: int = 0):
     """Lineages each active query traces in the next step.
 
@@ -133,6 +140,7 @@ class Server:
             ctx = self.tr.ctx
             sid = btrace.bt_scene_share(ctx, self.city_ids[q.city])
             btrace.bt_set_sources(ctx, sid, q.src, q.power, q.level)
+            set_query_directivity(ctx, sid, q)
             btrace.bt_set_microphones(ctx, sid, q.mics)
             p = self.tr.params(q.max_order, precision=self.precision)
             total = len(q.src) * 20 * 4 ** q.level
@@ -224,6 +232,7 @@ def run_plain(tracer, city_ids, queries, precision: int = btrace.BT_PREC_MIXED, 
         start = time.perf_counter() - t0
         sid = btrace.bt_scene_share(ctx, city_ids[q.city])
         btrace.bt_set_sources(ctx, sid, q.src, q.power, q.level)
+        set_query_directivity(ctx, sid, q)
         btrace.bt_set_microphones(ctx, sid, q.mics)
         btrace.bt_trace(ctx, sid, tracer.params(q.max_order, precision=precision))
         n, nb = len(q.mics), q.power.shape[1]

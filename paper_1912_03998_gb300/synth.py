@@ -443,6 +443,7 @@ class Query:
     mics: np.ndarray
     level: int
     max_order: int
+    directivity: Directivity = None  # None: every source omnidirectional
 
 
 def serving_queries(seed: int, n_queries: int, n_cities: int, rate_qps: float, level: int = 4,

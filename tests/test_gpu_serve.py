@@ -99,3 +99,32 @@ def test_shared_geometry_scenes(tracer):
     finally:
         btrace.bt_unload_scene(tracer.ctx, sid)
         btrace.bt_unload_scene(tracer.ctx, city)
+
+
+def test_directional_queries_same_alone_and_in_the_mix(tracer, setting):
+    # queries whose sources are cardioids (every other source omnidirectional)
+    # trace the same in the server's steps as alone, and the patterns reach
+    # the levels (they differ from the all-omnidirectional queries)
+    import dataclasses
+    from paper_1912_03998_gb300 import serve
+    cities, queries = setting
+    qs = []
+    for k, q in enumerate(queries[:6]):
+        of = np.where(np.arange(len(q.src)) % 2 == 0, k % 2, -1).astype(np.int32)
+        d = synth.Directivity([synth.cardioid((1.0, 0.0, 0.0)), synth.cardioid((0.0, 1.0, 0.3), 0.8)], of)
+        qs.append(dataclasses.replace(q, directivity=d))
+    srv = serve.Server(tracer, cities, step_lineages=1 << 12)
+    try:
+        mixed = srv.run(qs, realtime=False)
+        alone = serve.run_plain(tracer, srv.city_ids, qs, realtime=False)
+        omni = serve.run_plain(tracer, srv.city_ids, queries[:6], realtime=False)
+    finally:
+        srv.close()
+    for a, b in zip(mixed, alone):
+        same(a, b)
+    differs = 0
+    for a, o in zip(alone, omni):
+        assert (a.count == o.count).all()  # gains scale energy, not which beams hit
+        fin = np.isfinite(o.level)
+        differs += int(np.abs(a.level[fin] - o.level[fin]).max(initial=0.0) > 1e-3)
+    assert differs >= 1
