@@ -11,8 +11,9 @@
  * receive its energy; the result is a sound level per microphone and band.
  *
  * Conventions shared by every call:
- *   - Return value: BT_OK (0) or a negative BT_E_* code.  No call aborts the
- *     process.  After an error, bt_last_error() describes it.
+ *   - Return value: BT_OK (0) or a negative BT_E_* code (bt_poll may also
+ *     return BT_PENDING).  No call aborts the process.  After an error,
+ *     bt_last_error() describes it.
  *   - Pointers: every array argument may be host memory (pageable or pinned)
  *     or device memory of the context's GPU; the library tells them apart by
  *     unified addressing and copies them before the call returns.  The caller
@@ -43,6 +44,7 @@ extern "C" {
 #define BT_E_STATE (-4)      /* call out of order (e.g. trace before sources are set) */
 #define BT_E_QUEUE_FULL (-5) /* a device work queue overflowed */
 #define BT_E_TIMEOUT (-6)    /* a bounded device wait gave up (watchdog) */
+#define BT_PENDING 1         /* bt_poll: the submitted trace is still running (not an error) */
 
 #define BT_MAX_BANDS 8       /* octave bands 63 Hz .. 8 kHz */
 #define BT_MAX_SCENES 64     /* resident scenes per context */
@@ -195,6 +197,25 @@ int bt_set_microphones(bt_ctx *ctx, int32_t scene_id, const float *pos, int64_t 
  * microphones are missing; BT_E_INVALID for bad parameters;
  * BT_E_QUEUE_FULL / BT_E_TIMEOUT from the sub-domain scheduler. */
 int bt_trace(bt_ctx *ctx, int32_t scene_id, const bt_trace_params *p);
+
+/* Asynchronous trace: bt_submit enqueues the same work as bt_trace on the
+ * context's stream and returns without waiting for the GPU, so the caller's
+ * thread is free while the scene is traced.  bt_poll returns BT_PENDING while
+ * the trace runs and BT_OK once it has finished (its result and stats are then
+ * read with bt_read_levels); bt_wait blocks until it has finished.  A failed
+ * trace makes both return its error code (BT_E_QUEUE_FULL, BT_E_TIMEOUT,
+ * BT_E_CUDA), as bt_trace would have; they keep returning the outcome of the
+ * scene's last trace until the next one is submitted, and BT_E_STATE when the
+ * scene was never traced.  Submissions on several scenes run one after the
+ * other on the stream.  Any other call that names a scene with a trace in
+ * flight first waits for that trace, so calls take effect in the order they
+ * were made.  bt_submit may itself wait for earlier work on the stream when
+ * it builds a scene's sub-domain hierarchy or allocates.  Errors of
+ * bt_submit: those of bt_trace that are found before any GPU work (bad
+ * parameters, missing sources or microphones, allocation). */
+int bt_submit(bt_ctx *ctx, int32_t scene_id, const bt_trace_params *p);
+int bt_poll(bt_ctx *ctx, int32_t scene_id);
+int bt_wait(bt_ctx *ctx, int32_t scene_id);
 
 /* Read the result of the last trace of the scene.
  *   level_db  [n_m][n_bands] float64: 10 log10(I / 1e-12 W/m^2), -inf where no

@@ -18,6 +18,7 @@ from . import build_lib
 
 BT_OK = 0
 BT_E_INVALID, BT_E_NOMEM, BT_E_CUDA, BT_E_STATE, BT_E_QUEUE_FULL, BT_E_TIMEOUT = -1, -2, -3, -4, -5, -6
+BT_PENDING = 1
 BT_MAX_BANDS = 8
 BT_PREC_FP32, BT_PREC_MIXED, BT_PREC_FP64 = 0, 1, 2
 
@@ -59,7 +60,8 @@ EXPECTED_SYMBOLS = ("bt_params_default", "bt_create", "bt_destroy", "bt_load_sce
                     "bt_read_levels", "bt_last_error", "bt_kernel_launches", "bt_cast_rays",
                     "bt_trace_noalloc", "bt_set_result", "bt_batch_create", "bt_batch_run",
                     "bt_batch_stats", "bt_batch_destroy", "bt_scene_share", "bt_trace_ranges",
-                    "bt_ranges_stats", "bt_set_directivity", "bt_beam_axes")
+                    "bt_ranges_stats", "bt_set_directivity", "bt_beam_axes", "bt_submit", "bt_poll",
+                    "bt_wait")
 
 
 def lib_path() -> str:
@@ -86,6 +88,9 @@ def lib():
             L.bt_set_directivity.argtypes = [p, i32, p, i32, p]
             L.bt_beam_axes.argtypes = [p, i32, p]
             L.bt_trace.argtypes = [p, i32, C.POINTER(bt_trace_params)]
+            L.bt_submit.argtypes = [p, i32, C.POINTER(bt_trace_params)]
+            L.bt_poll.argtypes = [p, i32]
+            L.bt_wait.argtypes = [p, i32]
             L.bt_read_levels.argtypes = [p, i32, p, p, p, C.POINTER(bt_stats)]
             L.bt_last_error.argtypes = [p]
             L.bt_last_error.restype = C.c_char_p
@@ -207,6 +212,27 @@ def bt_set_microphones(ctx, scene_id: int, pos):
 
 def bt_trace(ctx, scene_id: int, params: bt_trace_params):
     _check(lib().bt_trace(ctx, int(scene_id), C.byref(params)), ctx)
+
+
+def bt_submit(ctx, scene_id: int, params: bt_trace_params):
+    """Enqueue a trace of the scene and return without waiting for it."""
+    _check(lib().bt_submit(ctx, int(scene_id), C.byref(params)), ctx)
+
+
+def bt_poll(ctx, scene_id: int) -> bool:
+    """True once the scene's submitted trace has finished, False while it
+    runs; raises BtError if it failed."""
+    rc = lib().bt_poll(ctx, int(scene_id))
+    if rc == BT_PENDING:
+        return False
+    _check(rc, ctx)
+    return True
+
+
+def bt_wait(ctx, scene_id: int):
+    """Block until the scene's submitted trace has finished; raises BtError
+    if it failed."""
+    _check(lib().bt_wait(ctx, int(scene_id)), ctx)
 
 
 def bt_trace_noalloc(ctx, scene_id: int, params: bt_trace_params, level_db, path_count=None):

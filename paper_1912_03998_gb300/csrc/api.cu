@@ -56,11 +56,24 @@ struct SceneState {
   DevBuf t_nodes, t_tris, t_planes, t_planes64, t_planes_df, t_roots;
   // result
   bool traced = false;
+  bool pending = false;  // a bt_submit trace is in flight
+  int trace_error = 0;   // error code of the last trace (0 = none)
   bt_stats stats;
   unsigned long long gen = 0;  // changes whenever the scene's buffers may change (batches check it)
   int geom_of = -1;            // >= 0: the geometry buffers belong to that scene (bt_scene_share)
   int n_shares = 0;            // scenes sharing this scene's geometry
   DevBuf out_level, out_int, out_cnt;
+};
+
+// A scene slot's trace: events around the whole trace and around each kernel
+// launch (kind 0 traversal, 1 scatter), launch counts, and the event that
+// marks its counters copied to the host.  Kept per slot so that traces of
+// several scenes can be in flight on the context's stream (bt_submit).
+struct TraceRec {
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, done = nullptr;
+  std::vector<cudaEvent_t> kev;
+  std::vector<int> kind;  // kind of each pair of events in kev
+  int64_t beams = 0, trace_launches = 0, scatter_launches = 0, rounds = 0;
 };
 
 }  // namespace
@@ -79,11 +92,12 @@ struct bt_ctx {
   int beam_table_level = -1;
   bt::Counters *d_ctr = nullptr;
   bt::Counters *h_ctr = nullptr;  // pinned
+  bt::Counters *h_sctr = nullptr; // pinned, one per scene slot: counters of the slot's last trace
+  TraceRec rec[BT_MAX_SCENES];
   unsigned long long *d_seg_count = nullptr;
   unsigned long long *d_lineage_next = nullptr;
   float *d_box = nullptr;  // scene box of the scene being loaded (6 floats)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  std::vector<cudaEvent_t> kev;  // pairs of events around kernel launches of one trace
   std::vector<DevBuf> pool;      // released device buffers, reused before any new cudaMalloc
   DevBuf t_ring, t_seq, t_qctl;  // sub-domain trace: queue slots, slot sequence words, queue counters
   unsigned long long gen_counter = 0;
@@ -209,9 +223,74 @@ bt::DevScene dev_scene(const SceneState &s) {
   return d;
 }
 
+// Finish the bt_submit trace of scene slot `id`, if one is in flight: with
+// `wait`, block until it is done, else return BT_PENDING while it runs.  A
+// finished trace's stats are filled from its events and counters.  With
+// `report` a failure is also written to the context's message; without, it is
+// only kept in the scene (trace_error) for bt_poll and bt_read_levels.
+int collect(bt_ctx *c, int id, bool wait, bool report) {
+  SceneState &s = c->sc[id];
+  if (!s.pending) return BT_OK;
+  TraceRec &r = c->rec[id];
+  DeviceGuard g(c->device);
+  cudaError_t e = wait ? cudaEventSynchronize(r.done) : cudaEventQuery(r.done);
+  if (e == cudaErrorNotReady && !wait) {
+    cudaGetLastError();  // not an error: leave no trace in the runtime's last-error state
+    return BT_PENDING;
+  }
+  s.pending = false;
+  s.traced = false;
+  float ms = 0.0f;
+  double trace_kms = 0.0, scatter_kms = 0.0;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.ev0, r.ev1);
+  for (size_t q = 0; e == cudaSuccess && q + 1 < r.kev.size() && q / 2 < r.kind.size(); q += 2) {
+    float a = 0.0f;
+    e = cudaEventElapsedTime(&a, r.kev[q], r.kev[q + 1]);
+    if (r.kind[q / 2] == 0) trace_kms += a;
+    else scatter_kms += a;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    s.trace_error = BT_E_CUDA;
+    return report ? fail(c, BT_E_CUDA, "trace of scene %d: %s", id, cudaGetErrorString(e)) : BT_E_CUDA;
+  }
+  const bt::Counters &h = c->h_sctr[id];
+  bt_stats &o = s.stats;
+  memset(&o, 0, sizeof(o));
+  o.beams = r.beams;
+  o.segments = (int64_t)h.segments;
+  o.hits = (int64_t)h.hits;
+  o.escapes = (int64_t)h.escapes;
+  o.emitted = (int64_t)h.emitted;
+  o.candidates = (int64_t)h.candidates;
+  o.contributions = (int64_t)h.contributions;
+  o.handoffs = (int64_t)h.handoffs;
+  o.steals = (int64_t)h.steals;
+  o.rounds = r.rounds;
+  o.nodes_visited = (int64_t)h.nodes_visited;
+  o.tris_tested = (int64_t)h.tris_tested;
+  o.trace_launches = r.trace_launches;
+  o.scatter_launches = r.scatter_launches;
+  o.trace_ms = ms;
+  o.trace_kernel_ms = trace_kms;
+  o.scatter_kernel_ms = scatter_kms;
+  if (h.error) {
+    s.trace_error = h.error;
+    if (!report) return h.error;
+    return fail(c, h.error, h.error == BT_E_QUEUE_FULL ? "device queue or traversal stack overflow"
+                                                       : "device error %d", h.error);
+  }
+  s.trace_error = 0;
+  s.traced = true;
+  return BT_OK;
+}
+
+// The scene `id`; a bt_submit trace of it still in flight is waited for first,
+// so every call sees the scene as if the submitted trace had been synchronous.
 int scene_ref(bt_ctx *c, int32_t id, SceneState **out) {
   if (id < 0 || id >= BT_MAX_SCENES || !c->sc[id].used)
     return fail(c, BT_E_INVALID, "unknown scene id %d", id);
+  if (c->sc[id].pending) collect(c, id, true, false);
   *out = &c->sc[id];
   return BT_OK;
 }
@@ -356,6 +435,7 @@ BT_API int bt_create(bt_ctx **out, int device, void *cuda_stream) {
     if (cudaMalloc(&c->d_box, 8 * sizeof(float)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
     if (cudaMalloc(&c->d_lineage_next, sizeof(unsigned long long)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
     if (cudaMallocHost(&c->h_ctr, sizeof(bt::Counters)) != cudaSuccess) { rc = BT_E_NOMEM; break; }
+    if (cudaMallocHost(&c->h_sctr, sizeof(bt::Counters) * BT_MAX_SCENES) != cudaSuccess) { rc = BT_E_NOMEM; break; }
     if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) { rc = BT_E_CUDA; break; }
   } while (0);
   if (rc != BT_OK) {
@@ -391,12 +471,17 @@ BT_API int bt_destroy(bt_ctx *c) {
   if (c->d_box) cudaFree(c->d_box);
   if (c->d_lineage_next) cudaFree(c->d_lineage_next);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
+  if (c->h_sctr) cudaFreeHost(c->h_sctr);
+  for (TraceRec &r : c->rec) {
+    for (cudaEvent_t e : {r.ev0, r.ev1, r.done})
+      if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : r.kev) cudaEventDestroy(e);
+  }
   release(c->t_ring);
   release(c->t_seq);
   release(c->t_qctl);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
-  for (cudaEvent_t e : c->kev) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();
   delete c;
@@ -780,15 +865,22 @@ static int check_params(bt_ctx *c, SceneState *s, const bt_trace_params *p, floa
   return BT_OK;
 }
 
-BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
-  TRY(check_ctx(c));
-  c->err[0] = 0;
-  SceneState *s;
-  TRY(scene_ref(c, scene_id, &s));
+// Enqueue a whole trace of scene slot `id` on the context's stream: chunks of
+// lineages, each a persistent traversal launch and a scatter launch, events
+// around every launch, and the counters' copy to the slot's pinned record.
+// The scene is then pending until collect().
+static int enqueue_trace(bt_ctx *c, int32_t id, const bt_trace_params *p) {
+  SceneState *s = &c->sc[id];
   int has_alpha = 0;
   float alpha_log2[BT_MAX_BANDS];
   TRY(check_params(c, s, p, alpha_log2, &has_alpha));
   DeviceGuard g(c->device);
+  s->traced = false;
+  s->trace_error = 0;
+  TraceRec &r = c->rec[id];
+  for (cudaEvent_t *e : {&r.ev0, &r.ev1, &r.done})
+    if (!*e) CK(cudaEventCreate(e));
+  r.kind.clear();
   cudaStream_t st = c->stream;
   const int64_t n_beams = (int64_t)20 << (2 * s->level);
   const int64_t total = s->n_src * n_beams;
@@ -868,20 +960,16 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
     tga.ctl = (int *)c->t_qctl.p;
     tga.watchdog_ns = (unsigned long long)(p->watchdog_ms > 0 ? p->watchdog_ms : 2000) * 1000000ull;
   }
-  // Events bracket every launch; kind 0 traversal, 1 scatter.
-  struct Mark {
-    int ev, kind;
-  };
-  std::vector<Mark> marks;
+  // Events bracket every launch: a pair per launch, its kind in r.kind.
   int n_ev = 0;
   auto mark = [&](int kind) -> int {
-    while ((int)c->kev.size() < n_ev + 1) {
+    while ((int)r.kev.size() < n_ev + 1) {
       cudaEvent_t e;
-      if (cudaEventCreate(&e) != cudaSuccess) return BT_E_CUDA;
-      c->kev.push_back(e);
+      CK(cudaEventCreate(&e));
+      r.kev.push_back(e);
     }
-    if (cudaEventRecord(c->kev[n_ev], st) != cudaSuccess) return BT_E_CUDA;
-    marks.push_back(Mark{n_ev, kind});
+    CK(cudaEventRecord(r.kev[n_ev], st));
+    if (n_ev % 2 == 0) r.kind.push_back(kind);
     n_ev++;
     return BT_OK;
   };
@@ -893,7 +981,7 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
   };
   const int64_t n_chunks = total > 0 ? (total + chunk - 1) / chunk : 0;
   int64_t n_trace_launches = 0, n_scatter_launches = 0, n_rounds = 0;
-  CK(cudaEventRecord(c->ev0, st));
+  CK(cudaEventRecord(r.ev0, st));
   for (int64_t ci = 0; ci < n_chunks; ci++) {
     int64_t b0 = ci * chunk;
     ta.lineage_begin = b0;
@@ -916,45 +1004,50 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
     TRY(scatter_round());
     n_scatter_launches += s->n_mics > 0;
   }
-  CK(cudaEventRecord(c->ev1, st));
-  TRY(read_counters(c));
-  float ms = 0.0f;
-  CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-  double trace_kms = 0.0, scatter_kms = 0.0;
-  for (size_t q = 0; q + 1 < marks.size(); q += 2) {
-    float a = 0.0f;
-    CK(cudaEventElapsedTime(&a, c->kev[marks[q].ev], c->kev[marks[q + 1].ev]));
-    if (marks[q].kind == 0) trace_kms += a;
-    else scatter_kms += a;
-  }
-  const bt::Counters &h = *c->h_ctr;
-  bt_stats &o = s->stats;
-  memset(&o, 0, sizeof(o));
-  o.beams = total;
-  o.segments = (int64_t)h.segments;
-  o.hits = (int64_t)h.hits;
-  o.escapes = (int64_t)h.escapes;
-  o.emitted = (int64_t)h.emitted;
-  o.candidates = (int64_t)h.candidates;
-  o.contributions = (int64_t)h.contributions;
-  o.handoffs = (int64_t)h.handoffs;
-  o.steals = (int64_t)h.steals;
-  o.rounds = n_rounds;
-  o.nodes_visited = (int64_t)h.nodes_visited;
-  o.tris_tested = (int64_t)h.tris_tested;
-  o.trace_launches = n_trace_launches;
-  o.scatter_launches = n_scatter_launches;
-  o.trace_ms = ms;
-  o.trace_kernel_ms = trace_kms;
-  o.scatter_kernel_ms = scatter_kms;
-  if (h.error) {
-    s->traced = false;
-    return fail(c, h.error, h.error == BT_E_QUEUE_FULL ? "device queue or traversal stack overflow"
-                                                        : "device error %d", h.error);
-  }
-  s->traced = true;
+  CK(cudaEventRecord(r.ev1, st));
+  CK(cudaMemcpyAsync(&c->h_sctr[id], c->d_ctr, sizeof(bt::Counters), cudaMemcpyDeviceToHost, st));
+  CK(cudaEventRecord(r.done, st));
+  r.beams = total;
+  r.trace_launches = n_trace_launches;
+  r.scatter_launches = n_scatter_launches;
+  r.rounds = n_rounds;
+  s->pending = true;
   return BT_OK;
 }
+
+BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  SceneState *s;
+  TRY(scene_ref(c, scene_id, &s));
+  TRY(enqueue_trace(c, scene_id, p));
+  return collect(c, scene_id, true, true);
+}
+
+BT_API int bt_submit(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  SceneState *s;
+  TRY(scene_ref(c, scene_id, &s));
+  return enqueue_trace(c, scene_id, p);
+}
+
+// bt_poll (wait = false) and bt_wait (wait = true).
+static int finish(bt_ctx *c, int32_t scene_id, bool wait) {
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  if (scene_id < 0 || scene_id >= BT_MAX_SCENES || !c->sc[scene_id].used)
+    return fail(c, BT_E_INVALID, "unknown scene id %d", scene_id);
+  SceneState &s = c->sc[scene_id];
+  if (s.pending) return collect(c, scene_id, wait, true);
+  if (s.traced) return BT_OK;
+  if (s.trace_error) return fail(c, s.trace_error, "the last trace of scene %d failed (code %d)", scene_id, s.trace_error);
+  return fail(c, BT_E_STATE, "scene %d has no trace submitted", scene_id);
+}
+
+BT_API int bt_poll(bt_ctx *c, int32_t scene_id) { return finish(c, scene_id, false); }
+
+BT_API int bt_wait(bt_ctx *c, int32_t scene_id) { return finish(c, scene_id, true); }
 
 BT_API int bt_read_levels(bt_ctx *c, int32_t scene_id, double *level_db, double *intensity,
                           int32_t *path_count, bt_stats *stats) {
@@ -962,7 +1055,10 @@ BT_API int bt_read_levels(bt_ctx *c, int32_t scene_id, double *level_db, double 
   c->err[0] = 0;
   SceneState *s;
   TRY(scene_ref(c, scene_id, &s));
-  if (!s->traced) return fail(c, BT_E_STATE, "scene %d has no trace result", scene_id);
+  if (!s->traced) {
+    if (s->trace_error) return fail(c, s->trace_error, "the last trace of scene %d failed (code %d)", scene_id, s->trace_error);
+    return fail(c, BT_E_STATE, "scene %d has no trace result", scene_id);
+  }
   DeviceGuard g(c->device);
   cudaStream_t st = c->stream;
   const size_t nv = (size_t)s->n_mics * s->n_bands;
@@ -1176,9 +1272,11 @@ BT_API int bt_batch_run(bt_batch *b) {
   if (!b) return BT_E_INVALID;
   bt_ctx *c = b->c;
   c->err[0] = 0;
-  for (size_t i = 0; i < b->ids.size(); i++)
+  for (size_t i = 0; i < b->ids.size(); i++) {
     if (c->sc[b->ids[i]].gen != b->gens[i])
       return fail(c, BT_E_STATE, "scene %d changed since the batch was created", b->ids[i]);
+    if (c->sc[b->ids[i]].pending) collect(c, b->ids[i], true, false);  // a submitted trace finishes first
+  }
   DeviceGuard g(c->device);
   cudaStream_t st = c->stream;
   if (!b->exec) {

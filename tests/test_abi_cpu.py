@@ -73,5 +73,8 @@ def test_null_arguments_are_rejected_without_a_gpu(libpath):
     assert L.bt_ranges_stats(None, None) == btrace.BT_E_INVALID
     assert L.bt_set_directivity(None, 0, None, 0, None) == btrace.BT_E_INVALID
     assert L.bt_beam_axes(None, 0, None) == btrace.BT_E_INVALID
+    assert L.bt_submit(None, 0, None) == btrace.BT_E_INVALID
+    assert L.bt_poll(None, 0) == btrace.BT_E_INVALID
+    assert L.bt_wait(None, 0) == btrace.BT_E_INVALID
     assert L.bt_last_error(None) == b"null context"
     assert btrace.bt_kernel_launches() == 0
