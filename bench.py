@@ -60,6 +60,8 @@ def parse():
                     help="skip the short served-latency measurement in the default line")
     ap.add_argument("--autotune", action="store_true",
                     help="batch: tune blocks per SM and lineages per launch on 16 of the cities first")
+    ap.add_argument("--tune-cache", default=None,
+                    help="batch --autotune: JSON file of tuned knobs per (cities, GPU model), reused when present")
     ap.add_argument("--sources", type=int, default=None, help="override the source count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -329,11 +331,18 @@ def run_batch(args):
     params = [tr.params(w.max_order, precision=prec) for w in ws]
     tuned = None
     if args.autotune:
-        knobs, table = autotune.tune_batch(tr, sids[:16], params[:16])
+        cache = autotune.TuneCache(args.tune_cache) if args.tune_cache else None
+        key, gpu = autotune.batch_key(ws[:16], params[:16]), torch.cuda.get_device_name(dev)
+        knobs, table = (cache.get(key, gpu) if cache else None), None
+        if knobs is None:
+            knobs, table = autotune.tune_batch(tr, sids[:16], params[:16])
+            if cache:
+                cache.put(key, gpu, knobs, table)
         for p in params:
             p.blocks_per_sm, p.chunk_beams = knobs["blocks_per_sm"], knobs["chunk_beams"]
-        tuned = {"chosen": knobs, "trials_ms": [[k["blocks_per_sm"], k["chunk_beams"], round(ms, 3)]
-                                                for k, ms in table]}
+        tuned = {"chosen": knobs, "cached": table is None}
+        if table is not None:
+            tuned["trials_ms"] = [[k["blocks_per_sm"], k["chunk_beams"], round(ms, 3)] for k, ms in table]
     l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def span(fn):

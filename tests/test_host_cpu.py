@@ -1,5 +1,5 @@
-"""Host-side logic that needs no GPU: the server's step allocation and the
-volumetric microphone grid."""
+"""Host-side logic that needs no GPU: the server's step allocation, the
+volumetric microphone grid and the autotuner's cache."""
 import numpy as np
 
 from paper_1912_03998_gb300 import serve, synth
@@ -60,3 +60,38 @@ def test_step_shares_small_queries_first():
     s = serve.step_shares(left, work, 1 << 22, small=1 << 18)
     assert s[1:3] == [200_000, 40_000] and s[0] == (1 << 22) - 240_000 and s[3] == 0
     assert sum(s) == 1 << 22
+
+
+def test_tune_cache_per_workload_and_device(tmp_path):
+    # a workload is tuned once per device model; the cache survives a reload,
+    # a different scene or device misses, and an unreadable file is empty
+    from paper_1912_03998_gb300 import autotune, btrace, synth
+    w1 = synth.tiny_city(seed=1, level=3, max_order=3)
+    w2 = synth.tiny_city(seed=2, level=3, max_order=3)
+    p = btrace.bt_trace_params()
+    p.max_order, p.tiles_x, p.tiles_y, p.precision = 3, 1, 1, btrace.BT_PREC_MIXED
+    k1, k2 = autotune.workload_key(w1, p), autotune.workload_key(w2, p)
+    assert k1 != k2 and k1 == autotune.workload_key(synth.tiny_city(seed=1, level=3, max_order=3), p)
+    q = btrace.bt_trace_params.from_buffer_copy(p)
+    q.tiles_x = q.tiles_y = 4
+    assert autotune.workload_key(w1, q) != k1
+    assert autotune.batch_key([w1, w2], [p, p]) != autotune.batch_key([w2, w1], [p, p])
+    calls = []
+
+    def tune():
+        calls.append(1)
+        return {"blocks_per_sm": 4, "chunk_beams": 0}, [({"blocks_per_sm": 4, "chunk_beams": 0}, 1.5)]
+
+    path = str(tmp_path / "tune.json")
+    c = autotune.TuneCache(path)
+    assert autotune.tuned(c, k1, "GB300", tune) == {"blocks_per_sm": 4, "chunk_beams": 0}
+    assert autotune.tuned(c, k1, "GB300", tune) == {"blocks_per_sm": 4, "chunk_beams": 0}
+    assert len(calls) == 1
+    c2 = autotune.TuneCache(path)
+    assert c2.get(k1, "GB300") == {"blocks_per_sm": 4, "chunk_beams": 0}
+    assert c2.get(k2, "GB300") is None and c2.get(k1, "B200") is None
+    autotune.tuned(c2, k1, "B200", tune)
+    assert len(calls) == 2
+    with open(path, "w") as f:
+        f.write("{not json")
+    assert autotune.TuneCache(path).get(k1, "GB300") is None
