@@ -18,6 +18,21 @@
 
 #define BT_API extern "C" __attribute__((visibility("default")))
 
+#include <nvtx3/nvToolsExt.h>
+
+namespace {
+// An NVTX range named after the entry point, open while the call runs, so
+// that profilers can attribute kernels and copies to library calls (ncu
+// --nvtx, Nsight Systems); without an attached tool it costs one pointer test.
+struct ApiRange {
+  explicit ApiRange(const char *name) { nvtxRangePushA(name); }
+  ~ApiRange() { nvtxRangePop(); }
+  ApiRange(const ApiRange &) = delete;
+  ApiRange &operator=(const ApiRange &) = delete;
+};
+}  // namespace
+#define BT_RANGE() ApiRange bt_range_(__func__)
+
 namespace bt {
 static std::atomic<long long> g_launches{0};
 void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -407,6 +422,7 @@ BT_API int bt_params_default(bt_trace_params *p) {
 }
 
 BT_API int bt_create(bt_ctx **out, int device, void *cuda_stream) {
+  BT_RANGE();
   if (!out) return BT_E_INVALID;
   *out = nullptr;
   int n_dev = 0;
@@ -450,6 +466,7 @@ BT_API int bt_create(bt_ctx **out, int device, void *cuda_stream) {
 static void free_batch(bt_batch *b);
 
 BT_API int bt_destroy(bt_ctx *c) {
+  BT_RANGE();
   if (!c) return BT_OK;
   DeviceGuard g(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
@@ -495,6 +512,7 @@ BT_API int64_t bt_kernel_launches(void) { return (int64_t)bt::g_launches.load();
 BT_API int bt_load_scene(bt_ctx *c, const float *verts, int64_t n_verts, const int32_t *tris,
                          int64_t n_tris, const uint8_t *tri_material, const float *refl,
                          int32_t n_materials, int32_t n_bands, int32_t *scene_id_out) {
+  BT_RANGE();
   TRY(check_ctx(c));
   c->err[0] = 0;
   if (!scene_id_out) return fail(c, BT_E_INVALID, "scene_id_out is NULL");
@@ -581,6 +599,7 @@ BT_API int bt_load_scene(bt_ctx *c, const float *verts, int64_t n_verts, const i
 }
 
 BT_API int bt_unload_scene(bt_ctx *c, int32_t scene_id) {
+  BT_RANGE();
   TRY(check_ctx(c));
   SceneState *s;
   TRY(scene_ref(c, scene_id, &s));
@@ -594,6 +613,7 @@ BT_API int bt_unload_scene(bt_ctx *c, int32_t scene_id) {
 }
 
 BT_API int bt_scene_share(bt_ctx *c, int32_t base_id, int32_t *scene_id_out) {
+  BT_RANGE();
   TRY(check_ctx(c));
   c->err[0] = 0;
   SceneState *b;
@@ -630,6 +650,7 @@ BT_API int bt_scene_share(bt_ctx *c, int32_t base_id, int32_t *scene_id_out) {
 
 BT_API int bt_set_sources(bt_ctx *c, int32_t scene_id, const float *pos, const float *power_w,
                           int64_t n_s, int32_t icosa_level) {
+  BT_RANGE();
   TRY(check_ctx(c));
   c->err[0] = 0;
   SceneState *s;
@@ -670,6 +691,7 @@ BT_API int bt_set_sources(bt_ctx *c, int32_t scene_id, const float *pos, const f
 
 BT_API int bt_set_directivity(bt_ctx *c, int32_t scene_id, const float *patterns, int32_t n_patterns,
                               const int32_t *pattern_of) {
+  BT_RANGE();
   TRY(check_ctx(c));
   c->err[0] = 0;
   SceneState *s;
@@ -713,6 +735,7 @@ BT_API int bt_set_directivity(bt_ctx *c, int32_t scene_id, const float *patterns
 }
 
 BT_API int bt_beam_axes(bt_ctx *c, int32_t icosa_level, float *axes) {
+  BT_RANGE();
   TRY(check_ctx(c));
   c->err[0] = 0;
   if (icosa_level < 0 || icosa_level > 8) return fail(c, BT_E_INVALID, "icosa_level %d not in 0..8", icosa_level);
@@ -728,6 +751,7 @@ BT_API int bt_beam_axes(bt_ctx *c, int32_t icosa_level, float *axes) {
 }
 
 BT_API int bt_set_microphones(bt_ctx *c, int32_t scene_id, const float *pos, int64_t n_m) {
+  BT_RANGE();
   TRY(check_ctx(c));
   c->err[0] = 0;
   SceneState *s;
@@ -1016,6 +1040,7 @@ static int enqueue_trace(bt_ctx *c, int32_t id, const bt_trace_params *p) {
 }
 
 BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
+  BT_RANGE();
   TRY(check_ctx(c));
   c->err[0] = 0;
   SceneState *s;
@@ -1025,6 +1050,7 @@ BT_API int bt_trace(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
 }
 
 BT_API int bt_submit(bt_ctx *c, int32_t scene_id, const bt_trace_params *p) {
+  BT_RANGE();
   TRY(check_ctx(c));
   c->err[0] = 0;
   SceneState *s;
@@ -1045,12 +1071,13 @@ static int finish(bt_ctx *c, int32_t scene_id, bool wait) {
   return fail(c, BT_E_STATE, "scene %d has no trace submitted", scene_id);
 }
 
-BT_API int bt_poll(bt_ctx *c, int32_t scene_id) { return finish(c, scene_id, false); }
+BT_API int bt_poll(bt_ctx *c, int32_t scene_id) { BT_RANGE(); return finish(c, scene_id, false); }
 
-BT_API int bt_wait(bt_ctx *c, int32_t scene_id) { return finish(c, scene_id, true); }
+BT_API int bt_wait(bt_ctx *c, int32_t scene_id) { BT_RANGE(); return finish(c, scene_id, true); }
 
 BT_API int bt_read_levels(bt_ctx *c, int32_t scene_id, double *level_db, double *intensity,
                           int32_t *path_count, bt_stats *stats) {
+  BT_RANGE();
   TRY(check_ctx(c));
   c->err[0] = 0;
   SceneState *s;
@@ -1078,6 +1105,7 @@ BT_API int bt_read_levels(bt_ctx *c, int32_t scene_id, double *level_db, double 
 }
 
 BT_API int bt_set_result(bt_ctx *c, int32_t scene_id, const double *intensity, const int32_t *path_count) {
+  BT_RANGE();
   TRY(check_ctx(c));
   c->err[0] = 0;
   SceneState *s;
@@ -1141,6 +1169,7 @@ static void free_batch(bt_batch *b) {
 
 BT_API int bt_batch_create(bt_ctx *c, const int32_t *scene_ids, int32_t n_scenes, const bt_trace_params *params,
                            bt_batch **out) {
+  BT_RANGE();
   TRY(check_ctx(c));
   c->err[0] = 0;
   if (!out) return fail(c, BT_E_INVALID, "NULL output handle");
@@ -1269,6 +1298,7 @@ static int record_batch(bt_batch *b) {
 }
 
 BT_API int bt_batch_run(bt_batch *b) {
+  BT_RANGE();
   if (!b) return BT_E_INVALID;
   bt_ctx *c = b->c;
   c->err[0] = 0;
@@ -1337,12 +1367,14 @@ BT_API int bt_batch_run(bt_batch *b) {
 }
 
 BT_API int bt_batch_stats(const bt_batch *b, bt_stats *stats) {
+  BT_RANGE();
   if (!b || !stats) return BT_E_INVALID;
   *stats = b->stats;
   return BT_OK;
 }
 
 BT_API int bt_batch_destroy(bt_batch *b) {
+  BT_RANGE();
   if (!b) return BT_OK;
   bt_ctx *c = b->c;
   DeviceGuard g(c->device);
@@ -1358,6 +1390,7 @@ BT_API int bt_batch_destroy(bt_batch *b) {
 
 BT_API int bt_trace_ranges(bt_ctx *c, int32_t n, const int32_t *scene_ids, const int64_t *lineage_begin,
                            const int64_t *lineage_end, const bt_trace_params *params, int32_t flags) {
+  BT_RANGE();
   TRY(check_ctx(c));
   c->err[0] = 0;
   if (n < 0 || n > BT_MAX_SCENES) return fail(c, BT_E_INVALID, "n must be in 0..%d", BT_MAX_SCENES);
@@ -1489,6 +1522,7 @@ BT_API int bt_trace_ranges(bt_ctx *c, int32_t n, const int32_t *scene_ids, const
 }
 
 BT_API int bt_ranges_stats(const bt_ctx *c, bt_stats *stats) {
+  BT_RANGE();
   if (!c || !stats) return BT_E_INVALID;
   *stats = c->range_stats;
   return BT_OK;
@@ -1497,6 +1531,7 @@ BT_API int bt_ranges_stats(const bt_ctx *c, bt_stats *stats) {
 BT_API int bt_cast_rays(bt_ctx *c, int32_t scene_id, const float *origins, const float *dirs,
                         const float *start_normals, int64_t n, float t_eps_m, float *t_out,
                         int32_t *tri_out) {
+  BT_RANGE();
   TRY(check_ctx(c));
   c->err[0] = 0;
   SceneState *s;
@@ -1566,6 +1601,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 BT_API int bt_trace_noalloc(bt_ctx *c, int32_t scene_id, const bt_trace_params *p, double *level_db,
                             int32_t *path_count) {
+  BT_RANGE();
   TRY(check_ctx(c));
   c->err[0] = 0;
   SceneState *s;
