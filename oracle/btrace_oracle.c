@@ -648,6 +648,22 @@ static int mic_in_segment(const segment *g, v3 m, int *tie) {
   return 1;
 }
 
+/* The cone's edge-plane normals from its edge directions. */
+static void seg_edges(segment *g) {
+  for (int j = 0; j < 3; j++) g->en[j] = cross(g->dir[j], g->dir[(j + 1) % 3]);
+}
+
+/* Image source (Section 2): mirror the apex and the cone's edge directions in
+ * the reflecting plane (point p, normal n), and reverse the edge order so that
+ * the mirrored cone stays counter-clockwise seen from outside. */
+static void reflect_cone(segment *g, v3 p, v3 n) {
+  v3 d0 = mirror_dir(g->dir[0], n), d1 = mirror_dir(g->dir[1], n), d2 = mirror_dir(g->dir[2], n);
+  g->dir[0] = d0;
+  g->dir[1] = d2;
+  g->dir[2] = d1;
+  g->apex = mirror_pt(g->apex, p, n);
+}
+
 /* Half-space list of a segment, each as n.x >= c with |n| = 1, for culling. */
 static int seg_halfspaces(const segment *g, v3 hn[5], double hc[5]) {
   int k = 0;
@@ -808,7 +824,7 @@ static void trace_beam(job *J, int64_t si, int64_t bi) {
     double pw = 0.0;
     for (int b = 0; b < s->n_bands; b++) pw += g.w[b] * omega4pi;
     J->stats[OR_NSTAT_FIXED + k] += pw;
-    for (int j = 0; j < 3; j++) g.en[j] = cross(g.dir[j], g.dir[(j + 1) % 3]);
+    seg_edges(&g);
     double th;
     int hid, ho = 0;
     closest_hit(s, &r, p->hit_mode, &th, &hid, &ho);
@@ -826,14 +842,9 @@ static void trace_beam(job *J, int64_t si, int64_t bi) {
     acc->cur_order = k;
     scatter_segment(acc, &g, J->mc, p->mic_mode);
     if (hid < 0 || k == p->max_order) break;
-    /* image source: mirror apex and cone in the hit plane, reverse the edge
-     * order so the mirrored cone stays counter-clockwise; lose energy. */
+    /* image source: the mirrored apex and cone; the reflection loses energy */
     v3 n = s->n[hid];
-    v3 d0 = mirror_dir(g.dir[0], n), d1 = mirror_dir(g.dir[1], n), d2 = mirror_dir(g.dir[2], n);
-    g.dir[0] = d0;
-    g.dir[1] = d2;
-    g.dir[2] = d1;
-    g.apex = mirror_pt(g.apex, s->a[hid], n);
+    reflect_cone(&g, s->a[hid], n);
     double wmax = 0.0;
     for (int b = 0; b < s->n_bands; b++) {
       g.w[b] *= s->refl[s->mat[hid] * s->n_bands + b];
@@ -966,4 +977,51 @@ int or_trace(const void *scene, const float *src, const float *power, int64_t n_
 /* Level readout: L = 10 log10(I / 1e-12) dB re 1e-12 W/m^2, -inf where I = 0. */
 void or_levels(const double *I, int64_t n, double *L) {
   for (int64_t i = 0; i < n; i++) L[i] = I[i] > 0.0 ? 10.0 * log10(I[i] / 1e-12) : -INFINITY;
+}
+
+/* ------------------------------------------------------------ primitives --
+ * The building blocks above, one call each, for hand-worked unit cases. */
+static v3 ld3(const double *a) { return mk(a[0], a[1], a[2]); }
+static void st3(double *o, v3 a) { o[0] = a.x; o[1] = a.y; o[2] = a.z; }
+
+/* Ray (o, d) against triangle (a, b, c): 1 and *t on a hit (any sign of t),
+ * else 0. */
+int or_ray_tri(const double *o, const double *d, const double *a, const double *b, const double *c, double *t) {
+  return ray_tri(ld3(o), ld3(d), ld3(a), ld3(b), ld3(c), t);
+}
+
+/* Mirror image of point a in the plane through p with unit normal n. */
+void or_mirror_point(const double *a, const double *p, const double *n, double *out) {
+  st3(out, mirror_pt(ld3(a), ld3(p), ld3(n)));
+}
+
+/* Mirror image of direction d in a plane with unit normal n. */
+void or_mirror_dir(const double *d, const double *n, double *out) { st3(out, mirror_dir(ld3(d), ld3(n))); }
+
+/* A beam's cone (apex [3], edge directions dirs [3][3]) reflected in the plane
+ * through p with unit normal n, as the trace reflects it. */
+void or_reflect_cone(const double *apex, const double *dirs, const double *p, const double *n, double *apex_out,
+                     double *dirs_out) {
+  segment g;
+  memset(&g, 0, sizeof(g));
+  g.apex = ld3(apex);
+  for (int j = 0; j < 3; j++) g.dir[j] = ld3(dirs + 3 * j);
+  reflect_cone(&g, ld3(p), ld3(n));
+  st3(apex_out, g.apex);
+  for (int j = 0; j < 3; j++) st3(dirs_out + 3 * j, g.dir[j]);
+}
+
+/* Is point m in the segment with apex [3], edge directions dirs [3][3], an
+ * optional start plane start [6] = (normal, point) and end plane end [6]
+ * (NULL: none)?  *tie as in the trace. */
+int or_in_segment(const double *apex, const double *dirs, const double *start, const double *end, const double *m,
+                  int *tie) {
+  segment g;
+  memset(&g, 0, sizeof(g));
+  g.apex = ld3(apex);
+  for (int j = 0; j < 3; j++) g.dir[j] = ld3(dirs + 3 * j);
+  seg_edges(&g);
+  if (start) { g.has_start = 1; g.ns = ld3(start); g.ps = ld3(start + 3); }
+  if (end) { g.has_end = 1; g.ne = ld3(end); g.pe = ld3(end + 3); }
+  return mic_in_segment(&g, ld3(m), tie);
 }

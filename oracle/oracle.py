@@ -61,6 +61,13 @@ def lib():
             L.or_trace_dir.argtypes = [p, p, p, i64, i32, p, i32, p, p, i64, i32, p, d, d, i32, i32,
                                        i32, p, p, p, i64, p, p, p, p, p, p]
             L.or_levels.argtypes = [p, i64, p]
+            L.or_ray_tri.restype = i32
+            L.or_ray_tri.argtypes = [p, p, p, p, p, p]
+            L.or_mirror_point.argtypes = [p, p, p, p]
+            L.or_mirror_dir.argtypes = [p, p, p]
+            L.or_reflect_cone.argtypes = [p, p, p, p, p, p]
+            L.or_in_segment.restype = i32
+            L.or_in_segment.argtypes = [p, p, p, p, p, p]
             L.isrc_bruteforce.restype = i64
             L.isrc_bruteforce.argtypes = [p, i64, p, i64, p, p, i32, i32, p, p, p, i64, i32,
                                           p, d, i32, p, p, i64, p, p, p, p]
@@ -195,6 +202,54 @@ def trace_workload(w, tiles=None, **kw):
         kw.setdefault("directivity", d.gains(beam_axes(w.level)))
         kw.setdefault("pattern_of", d.pattern_of)
     return trace(sc, w.src, w.power, w.level, w.mics, w.max_order, **kw)
+
+
+# ------------------------------------------------------------ primitives
+# One oracle building block per call, for hand-worked unit cases.
+def _v(a, n=3):
+    return _c(np.asarray(a, np.float64).reshape(n), np.float64)
+
+
+def ray_tri(o, d, a, b, c):
+    """Moller-Trumbore, two-sided, edges inclusive: t of the hit (any sign)
+    or None."""
+    t = np.zeros(1)
+    args = [_v(x) for x in (o, d, a, b, c)]
+    hit = lib().or_ray_tri(*[_ptr(x) for x in args], _ptr(t))
+    return float(t[0]) if hit else None
+
+
+def mirror_point(a, p, n):
+    out = np.zeros(3)
+    args = [_v(x) for x in (a, p, n)]
+    lib().or_mirror_point(*[_ptr(x) for x in args], _ptr(out))
+    return out
+
+
+def mirror_dir(d, n):
+    out = np.zeros(3)
+    args = [_v(x) for x in (d, n)]
+    lib().or_mirror_dir(*[_ptr(x) for x in args], _ptr(out))
+    return out
+
+
+def reflect_cone(apex, dirs, p, n):
+    """The image-source step on a cone: (mirrored apex [3], edge dirs [3, 3])."""
+    ao, do = np.zeros(3), np.zeros(9)
+    args = [_v(apex), _v(dirs, 9), _v(p), _v(n)]
+    lib().or_reflect_cone(*[_ptr(x) for x in args], _ptr(ao), _ptr(do))
+    return ao, do.reshape(3, 3)
+
+
+def in_segment(apex, dirs, m, start=None, end=None):
+    """(inside, tie) of point m for the segment; start / end planes as
+    (normal, point) pairs or None."""
+    tie = np.zeros(1, np.int32)
+    st = _v(np.concatenate([np.ravel(start[0]), np.ravel(start[1])]), 6) if start is not None else None
+    en = _v(np.concatenate([np.ravel(end[0]), np.ravel(end[1])]), 6) if end is not None else None
+    args = [_v(apex), _v(dirs, 9)]
+    inside = lib().or_in_segment(_ptr(args[0]), _ptr(args[1]), _ptr(st), _ptr(en), _ptr(_v(m)), _ptr(tie))
+    return bool(inside), bool(tie[0])
 
 
 def levels(I):

@@ -95,3 +95,20 @@ def test_tune_cache_per_workload_and_device(tmp_path):
     with open(path, "w") as f:
         f.write("{not json")
     assert autotune.TuneCache(path).get(k1, "GB300") is None
+
+
+def test_generators_are_deterministic_per_seed():
+    # every synthetic input is a function of its seed alone
+    def arrays(w):
+        return [w.scene.verts, w.scene.tris, w.scene.mat, w.scene.refl, w.src, w.power, w.mics]
+
+    for make in (lambda s: synth.tiny_city(seed=s, n_sources=3),
+                 lambda s: synth.district(seed=s, n_buildings=200, n_sources=20, n_mic_side=40)):
+        a, b, c = make(7), make(7), make(8)
+        assert all(np.array_equal(x, y) for x, y in zip(arrays(a), arrays(b)))
+        assert not all(np.array_equal(x, y) if x.shape == y.shape else False
+                       for x, y in zip(arrays(a), arrays(c)))
+    q1 = synth.serving_queries(seed=3, n_queries=5, n_cities=2, rate_qps=100.0, max_sources=20, max_mics=2000)
+    q2 = synth.serving_queries(seed=3, n_queries=5, n_cities=2, rate_qps=100.0, max_sources=20, max_mics=2000)
+    assert all(x.arrival_s == y.arrival_s and np.array_equal(x.src, y.src) and np.array_equal(x.mics, y.mics)
+               for x, y in zip(q1, q2))
