@@ -78,3 +78,21 @@ def test_null_arguments_are_rejected_without_a_gpu(libpath):
     assert L.bt_wait(None, 0) == btrace.BT_E_INVALID
     assert L.bt_last_error(None) == b"null context"
     assert btrace.bt_kernel_launches() == 0
+
+
+def test_plain_c_program_uses_the_boundary(libpath, tmp_path):
+    # the header compiles as strict C11 and a C program links and calls the
+    # library (argument checks, defaults, layouts; no compute call)
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    exe = str(tmp_path / "c_abi_check")
+    libdir = os.path.dirname(libpath)
+    subprocess.run([gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c_abi_check.c"), "-L", libdir, "-lbtrace",
+                    f"-Wl,-rpath,{libdir}", "-o", exe], check=True, capture_output=True, text=True)
+    args = [exe] + ([] if os.path.exists("/dev/nvidia0") else ["--no-device"])
+    r = subprocess.run(args, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert "c_abi_check: ok" in r.stdout
