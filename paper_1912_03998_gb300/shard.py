@@ -32,11 +32,35 @@ def source_block(n_sources: int, rank: int, world: int) -> tuple[int, int]:
     return lo, lo + q + (1 if rank < r else 0)
 
 
-def allreduce_result(intensity, path_count, group=None):
+class ShardFailure(RuntimeError):
+    """A rank did not reach the exchange step in time: it raised, exited or
+    is stuck.  The message names the rank(s) where the backend can tell."""
+
+
+def check_ranks(group=None, timeout_s: float = 30.0):
+    """Failure detection before the exchange step: every rank of `group` (a
+    gloo group; beside an NCCL group, one made with
+    dist.new_group(backend="gloo")) must arrive within `timeout_s`.  A rank
+    that failed its partial trace and left, or hangs, is then reported on the
+    others as ShardFailure instead of a collective that never completes."""
+    import datetime
+
+    import torch.distributed as dist
+    try:
+        dist.monitored_barrier(group=group, timeout=datetime.timedelta(seconds=float(timeout_s)),
+                               wait_all_ranks=True)
+    except RuntimeError as e:
+        raise ShardFailure(str(e)) from e
+
+
+def allreduce_result(intensity, path_count, group=None, check_timeout_s=None, check_group=None):
     """Sum a float64 intensity tensor and an int32 path-count tensor over the
     ranks of `group`, in place (CPU tensors under gloo, CUDA tensors under
-    NCCL)."""
+    NCCL).  With `check_timeout_s`, check_ranks runs first (on `check_group`,
+    default `group`)."""
     import torch.distributed as dist
+    if check_timeout_s is not None:
+        check_ranks(check_group if check_group is not None else group, check_timeout_s)
     dist.all_reduce(intensity, op=dist.ReduceOp.SUM, group=group)
     dist.all_reduce(path_count, op=dist.ReduceOp.SUM, group=group)
     return intensity, path_count

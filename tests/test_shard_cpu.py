@@ -49,7 +49,7 @@ def _rank_main(rank, world, port, out_dir, directional=False):
         r = O.trace_workload(w.subset_sources(np.arange(lo, hi)))
         I = torch.from_numpy(np.ascontiguousarray(r["I"], np.float64))
         cnt = torch.from_numpy(np.ascontiguousarray(r["cnt"], np.int32))
-        shard.allreduce_result(I, cnt)
+        shard.allreduce_result(I, cnt, check_timeout_s=60.0)  # every rank arrives: the check passes
         np.save(os.path.join(out_dir, f"I{rank}.npy"), I.numpy())
         np.save(os.path.join(out_dir, f"c{rank}.npy"), cnt.numpy())
     finally:
@@ -141,3 +141,55 @@ def test_gloo_microphone_blocks_gather_to_the_full_result(oracle_mod, tmp_path, 
         assert np.array_equal(np.load(tmp_path / f"mc{r}.npy"), full["cnt"])
         assert np.array_equal(np.load(tmp_path / f"mI{r}.npy"), full["I"])
 
+
+
+def _failing_rank_main(rank, world, port, out_dir, bad_rank):
+    # every rank traces its block; `bad_rank` fails before the exchange step
+    # and leaves; the others must learn of it from the rank check, not hang
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import datetime
+
+    import torch
+    import torch.distributed as dist
+    from oracle import oracle as O
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=30))
+    w = _workload()
+    lo, hi = shard.source_block(len(w.src), rank, world)
+    r = O.trace_workload(w.subset_sources(np.arange(lo, hi)))
+    if rank == bad_rank:
+        os._exit(7)  # a failed partial trace: the process leaves without the exchange
+    I = torch.from_numpy(np.ascontiguousarray(r["I"], np.float64))
+    cnt = torch.from_numpy(np.ascontiguousarray(r["cnt"], np.int32))
+    try:
+        shard.allreduce_result(I, cnt, check_timeout_s=5.0)
+        outcome = "completed"
+    except shard.ShardFailure as e:
+        outcome = "detected: " + str(e).replace("\n", " ")[:300]
+    with open(os.path.join(out_dir, f"outcome{rank}.txt"), "w") as f:
+        f.write(outcome)
+    os._exit(0)
+
+
+def test_failed_rank_is_detected_before_the_exchange(tmp_path):
+    pytest.importorskip("torch")
+    world, bad = 3, 2
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_rank_main, args=(r, world, port, str(tmp_path), bad))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        if p.is_alive():
+            p.kill()
+            p.join()
+    assert procs[bad].exitcode == 7
+    for r in range(world):
+        if r == bad:
+            continue
+        assert procs[r].exitcode == 0
+        outcome = (tmp_path / f"outcome{r}.txt").read_text()
+        assert outcome.startswith("detected"), outcome
+    # rank 0 runs the check and names the rank that left
+    assert "2" in (tmp_path / "outcome0.txt").read_text()
