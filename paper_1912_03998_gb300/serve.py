@@ -35,7 +35,12 @@ BYTES_PER_MIC = 16 + 8 + 8 * 8 + 4 + 8 * 8 * 2 + 4
 
 
 def query_bytes(q) -> int:
-    return len(q.src) * BYTES_PER_SOURCE + len(q.mics) * BYTES_PER_MIC + (1 << 16)
+    n = len(q.src) * BYTES_PER_SOURCE + len(q.mics) * BYTES_PER_MIC + (1 << 16)
+    d = getattr(q, "directivity", None)
+    if d is not None:
+        # gains (float32 per pattern and beam) and each source's pattern index
+        n += 4 * len(d.patterns) * 20 * 4 ** q.level + 4 * len(q.src)
+    return n
 
 
 def set_query_directivity(ctx, sid, q):

@@ -112,3 +112,11 @@ def test_generators_are_deterministic_per_seed():
     q2 = synth.serving_queries(seed=3, n_queries=5, n_cities=2, rate_qps=100.0, max_sources=20, max_mics=2000)
     assert all(x.arrival_s == y.arrival_s and np.array_equal(x.src, y.src) and np.array_equal(x.mics, y.mics)
                for x, y in zip(q1, q2))
+
+
+def test_query_bytes_count_directivity():
+    q = synth.serving_queries(seed=1, n_queries=1, n_cities=1, rate_qps=10.0, max_sources=10, max_mics=2000)[0]
+    base = serve.query_bytes(q)
+    import dataclasses
+    d = synth.Directivity([synth.cardioid((1, 0, 0))], np.zeros(len(q.src), np.int32))
+    assert serve.query_bytes(dataclasses.replace(q, directivity=d)) == base + 4 * 20 * 4 ** q.level + 4 * len(q.src)
