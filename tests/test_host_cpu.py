@@ -120,3 +120,85 @@ def test_query_bytes_count_directivity():
     import dataclasses
     d = synth.Directivity([synth.cardioid((1, 0, 0))], np.zeros(len(q.src), np.int32))
     assert serve.query_bytes(dataclasses.replace(q, directivity=d)) == base + 4 * 20 * 4 ** q.level + 4 * len(q.src)
+
+
+class _FakeLib:
+    """Stands in for the library calls the server makes: records every
+    lineage range it is asked to trace (no GPU)."""
+
+    def __init__(self):
+        self.next_sid = 100
+        self.live = set()
+        self.ranges = {}      # sid -> list of (begin, end)
+        self.calls = []       # per bt_trace_ranges call: list of sids
+        self.totals = []      # per bt_trace_ranges call: lineages traced
+        self.directivity = {}
+
+    def bt_scene_share(self, ctx, base):
+        self.next_sid += 1
+        self.live.add(self.next_sid)
+        self.ranges[self.next_sid] = []
+        return self.next_sid
+
+    def bt_set_sources(self, ctx, sid, src, power, level):
+        assert sid in self.live
+
+    def bt_set_microphones(self, ctx, sid, mics):
+        assert sid in self.live
+
+    def bt_beam_axes(self, ctx, level):
+        return np.zeros((20 * 4 ** level, 3), np.float32)
+
+    def bt_set_directivity(self, ctx, sid, gains, of):
+        self.directivity[sid] = (gains.shape, len(of))
+
+    def bt_trace_ranges(self, ctx, ids, begins, ends, params, accumulate=False):
+        assert accumulate
+        self.calls.append(list(ids))
+        self.totals.append(sum(e - b for b, e in zip(begins, ends)))
+        for sid, b, e in zip(ids, begins, ends):
+            assert sid in self.live and 0 <= b < e
+            self.ranges[sid].append((b, e))
+
+    def bt_ranges_stats(self, ctx):
+        return {"segments": 0, "trace_ms": 0.0}
+
+    def bt_read_levels(self, ctx, sid, level, intensity, count):
+        level[:] = sid
+        count[:] = 1
+
+    def bt_unload_scene(self, ctx, sid):
+        self.live.discard(sid)
+
+
+class _FakeTracer:
+    ctx = None
+
+    def load_geometry(self, w):
+        return 0
+
+    def params(self, max_order, **kw):
+        return ("params", max_order)
+
+
+def test_server_traces_every_lineage_once_in_order(monkeypatch):
+    # each query's lineages are traced exactly once, as consecutive ranges,
+    # its scene is freed after its last range, results come back in query
+    # order, and no step holds more than max_active queries
+    lib = _FakeLib()
+    for name in ("bt_scene_share", "bt_set_sources", "bt_set_microphones", "bt_beam_axes", "bt_set_directivity",
+                 "bt_trace_ranges", "bt_ranges_stats", "bt_read_levels", "bt_unload_scene"):
+        monkeypatch.setattr(serve.btrace, name, getattr(lib, name))
+    qs = synth.serving_queries(seed=2, n_queries=12, n_cities=2, rate_qps=1e4, level=3, max_sources=40,
+                               max_mics=3000)
+    srv = serve.Server(_FakeTracer(), [None, None], step_lineages=1500, max_active=4)
+    done = srv.run(qs, realtime=False)
+    assert [d.index for d in done] == list(range(len(qs)))
+    assert not lib.live  # every query's scene was freed
+    assert max(len(c) for c in lib.calls) <= 4
+    assert max(lib.totals) <= 1500 and srv.steps == len(lib.calls)
+    for d, q in zip(done, qs):
+        sid = int(d.level[0, 0])
+        rs = lib.ranges[sid]
+        assert rs[0][0] == 0 and rs[-1][1] == len(q.src) * 20 * 4 ** q.level
+        assert all(a[1] == b[0] for a, b in zip(rs, rs[1:]))  # consecutive, no gap or overlap
