@@ -91,7 +91,7 @@ def test_plain_c_program_uses_the_boundary(libpath, tmp_path):
     libdir = os.path.dirname(libpath)
     subprocess.run([gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
                     os.path.join(ROOT, "tests", "c_abi_check.c"), "-L", libdir, "-lbtrace",
-                    f"-Wl,-rpath,{libdir}", "-o", exe], check=True, capture_output=True, text=True)
+                    "-lm", f"-Wl,-rpath,{libdir}", "-o", exe], check=True, capture_output=True, text=True)
     args = [exe] + ([] if os.path.exists("/dev/nvidia0") else ["--no-device"])
     r = subprocess.run(args, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
