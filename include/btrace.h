@@ -198,7 +198,8 @@ int bt_set_microphones(bt_ctx *ctx, int32_t scene_id, const float *pos, int64_t 
  * BT_E_QUEUE_FULL / BT_E_TIMEOUT from the sub-domain scheduler. */
 int bt_trace(bt_ctx *ctx, int32_t scene_id, const bt_trace_params *p);
 
-/* Asynchronous trace: bt_submit enqueues the same work as bt_trace on the
+/* Asynchronous trace: bt_submit enqueues the same work as bt_trace (Section
+ * 2's trace; the asynchrony has no counterpart in the paper) on the
  * context's stream and returns without waiting for the GPU, so the caller's
  * thread is free while the scene is traced.  bt_poll returns BT_PENDING while
  * the trace runs and BT_OK once it has finished (its result and stats are then
