@@ -685,6 +685,7 @@ BT_API int bt_set_sources(bt_ctx *c, int32_t scene_id, const float *pos, const f
   s->n_pat = 0;  // new sources are omnidirectional until bt_set_directivity
   s->has_src = true;
   s->traced = false;
+  s->trace_error = 0;
   s->gen = ++c->gen_counter;
   return BT_OK;
 }
@@ -705,6 +706,7 @@ BT_API int bt_set_directivity(bt_ctx *c, int32_t scene_id, const float *patterns
   if (n_patterns == 0) {
     s->n_pat = 0;
     s->traced = false;
+    s->trace_error = 0;
     s->gen = ++c->gen_counter;
     return BT_OK;
   }
@@ -730,6 +732,7 @@ BT_API int bt_set_directivity(bt_ctx *c, int32_t scene_id, const float *patterns
   }
   s->n_pat = n_patterns;
   s->traced = false;
+  s->trace_error = 0;
   s->gen = ++c->gen_counter;
   return BT_OK;
 }
@@ -805,6 +808,7 @@ BT_API int bt_set_microphones(bt_ctx *c, int32_t scene_id, const float *pos, int
   s->nz = nz;
   s->has_mics = true;
   s->traced = false;
+  s->trace_error = 0;
   s->gen = ++c->gen_counter;
   return BT_OK;
 }
@@ -1126,6 +1130,7 @@ BT_API int bt_set_result(bt_ctx *c, int32_t scene_id, const double *intensity, c
   CK(cudaStreamSynchronize(st));
   memset(&s->stats, 0, sizeof(s->stats));
   s->traced = true;
+  s->trace_error = 0;
   return BT_OK;
 }
 
@@ -1359,6 +1364,7 @@ BT_API int bt_batch_run(bt_batch *b) {
     memset(&s.stats, 0, sizeof(s.stats));
     s.stats.beams = b->beams[i];
     s.traced = h.error == 0;
+    s.trace_error = h.error;
   }
   if (h.error)
     return fail(c, h.error, h.error == BT_E_QUEUE_FULL ? "device queue or traversal stack overflow"
@@ -1514,6 +1520,7 @@ BT_API int bt_trace_ranges(bt_ctx *c, int32_t n, const int32_t *scene_ids, const
     SceneState &s = c->sc[scene_ids[i]];
     memset(&s.stats, 0, sizeof(s.stats));
     s.traced = h.error == 0;
+    s.trace_error = h.error;
   }
   if (h.error)
     return fail(c, h.error, h.error == BT_E_QUEUE_FULL ? "device queue or traversal stack overflow"
@@ -1719,8 +1726,10 @@ BT_API int bt_trace_noalloc(bt_ctx *c, int32_t scene_id, const bt_trace_params *
   o.scatter_launches = s->n_mics > 0 ? n_chunks : 0;
   if (h.error) {
     s->traced = false;
+    s->trace_error = h.error;
     return fail(c, h.error, "device error %d in the no-allocation trace", h.error);
   }
   s->traced = true;
+  s->trace_error = 0;
   return BT_OK;
 }
