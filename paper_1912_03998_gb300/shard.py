@@ -14,6 +14,11 @@ not depend on the other microphones, so each rank traces every source
 against one contiguous block of the microphones and the blocks' levels are
 gathered in rank order.  This splits the scatter, which dominates when the
 microphones fill a volume, at the price of tracing every beam on every rank.
+
+Failure detection: before the exchange step, check_ranks (a monitored
+barrier with a timeout on a gloo group) turns a rank that failed and left, or
+hangs, into ShardFailure on the others instead of a collective that never
+completes.
 """
 from __future__ import annotations
 
