@@ -39,6 +39,12 @@ METRIC = "beam segments/s"
 UNIT = "segments/s"
 
 
+# The arithmetic type each precision variant computes in: "mixed" is float32
+# traversal with a float-pair (double-float) image-source chain and float64
+# energy accumulation.
+DTYPE = {"fp32": "f32", "mixed": "mixed", "fp64": "f64"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -377,7 +383,7 @@ def run_batch(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+            "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": {"workload": "batch: 64 cities of 100-5,000 buildings, 1-1,000 sources, L 3-6, "
                                    "K 2-8, 1k-250k microphones (seeded), traced as one batch",
                        "cities": len(ws), "triangles": int(sum(w.scene.n_tris for w in ws)),
@@ -444,7 +450,7 @@ def run_serve(args):
     line = {"metric": "served p50/p99 latency and queries/s", "value": head["served"]["queries_per_s"],
             "unit": "queries/s", "n_gpus": 1, "steps": len(rows), "warmup": 4,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+            "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": {"workload": "serve: Poisson streams against 8 resident cities of 500-5,000 buildings; "
                                    "queries of 1-2,000 sources (0.001-1 W per band), 1k-250k microphones, "
                                    "L=4, K 3-6", "queries_per_rate": args.queries,
@@ -570,7 +576,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f32",
+            "dtype": DTYPE[args.precision],
             "data": "synthetic", "config": cfg, "clocks": res["clocks"],
             "gpu_launches": res["launches"],
             "contributions_per_s": res["contrib"] * world / (total_ms * 1e-3),

@@ -255,10 +255,17 @@ int bt_cast_rays(bt_ctx *ctx, int32_t scene_id, const float *origins, const floa
  * then refer to it).
  *   level_db   [n_m][n_bands] float64, DEVICE memory of the context's GPU
  *   path_count [n_m] int32, device memory, or NULL
+ * The parameters are checked as bt_trace checks them; in addition only
+ * tiles_x = tiles_y = 1 is accepted (this call traces without sub-domains,
+ * so queue_depth is not used), and chunk_beams, when > 0, can only lower the
+ * lineages per launch below what the scratch holds.  count_work fills the
+ * stats' work counters as in bt_trace.
  * Its scratch is one static device array of BT_NOALLOC_SCRATCH_MB MiB inside
  * the library, held on every GPU that loads the library until the process
  * exits.  The icosahedron level must be <= BT_NOALLOC_MAX_LEVEL (the beam table
- * lives in that scratch); larger requests fail with BT_E_INVALID and say so.
+ * lives in that scratch), and (max_order + 1) segment records must fit in
+ * it; larger requests, and tiles other than 1x1, fail with BT_E_INVALID and
+ * say so.
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Every call, from any context, shares the one

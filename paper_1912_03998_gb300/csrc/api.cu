@@ -1578,8 +1578,10 @@ constexpr size_t kNoAllocBytes = (size_t)BT_NOALLOC_SCRATCH_MB << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Device address of g_noalloc_scratch per device ordinal, looked up on the
-// first no-allocation call made with that device current.
-void *g_noalloc_ptr[256] = {nullptr};
+// first no-allocation call made with that device current.  Atomic, so that
+// first calls from several host threads at once are well defined (they all
+// store the same address).
+std::atomic<void *> g_noalloc_ptr[256];
 
 __global__ void k_levels_noalloc(const double *energy, const int *count, const float4 *mics, int64_t n_m,
                                  int n_bands, double *level_db, int *path_count) {
@@ -1613,15 +1615,12 @@ BT_API int bt_trace_noalloc(bt_ctx *c, int32_t scene_id, const bt_trace_params *
   c->err[0] = 0;
   SceneState *s;
   TRY(scene_ref(c, scene_id, &s));
-  if (!p) return fail(c, BT_E_INVALID, "NULL params");
-  if (!s->has_src || !s->has_mics) return fail(c, BT_E_STATE, "sources and microphones must be set first");
-  if (p->max_order < 0 || p->max_order > 32) return fail(c, BT_E_INVALID, "max_order %d not in 0..32", p->max_order);
-  if (!(p->t_eps_m > 0.0f) || !isfinite(p->t_eps_m)) return fail(c, BT_E_INVALID, "t_eps_m must be > 0");
-  if (!(p->energy_threshold_w >= 0.0f)) return fail(c, BT_E_INVALID, "energy_threshold_w must be >= 0");
-  if (p->precision != BT_PREC_MIXED && p->precision != BT_PREC_FP32 && p->precision != BT_PREC_FP64)
-    return fail(c, BT_E_INVALID, "unknown precision %d", p->precision);
+  int has_alpha = 0;
+  float alpha_log2[BT_MAX_BANDS];
+  TRY(check_params(c, s, p, alpha_log2, &has_alpha));
   if (p->tiles_x != 1 || p->tiles_y != 1)
-    return fail(c, BT_E_INVALID, "tiles %dx%d: only 1x1 is implemented in this build", p->tiles_x, p->tiles_y);
+    return fail(c, BT_E_INVALID, "tiles %dx%d: bt_trace_noalloc traces without sub-domains (1x1 only)", p->tiles_x,
+                p->tiles_y);
   if (s->level > BT_NOALLOC_MAX_LEVEL)
     return fail(c, BT_E_INVALID, "bt_trace_noalloc: icosahedron level %d exceeds the limit of %d of its %d MiB scratch",
                 s->level, BT_NOALLOC_MAX_LEVEL, BT_NOALLOC_SCRATCH_MB);
@@ -1630,17 +1629,10 @@ BT_API int bt_trace_noalloc(bt_ctx *c, int32_t scene_id, const bt_trace_params *
     return fail(c, BT_E_INVALID, "bt_trace_noalloc: level_db must be device memory of device %d", c->device);
   if (path_count && !is_device_ptr(path_count, c->device))
     return fail(c, BT_E_INVALID, "bt_trace_noalloc: path_count must be device memory of device %d or NULL", c->device);
-  int has_alpha = 0;
-  float alpha_log2[BT_MAX_BANDS];
-  for (int b = 0; b < BT_MAX_BANDS; b++) {
-    float a = p->air_atten_db_per_m[b];
-    if (!(a >= 0.0f) || !isfinite(a)) return fail(c, BT_E_INVALID, "air attenuation must be finite and >= 0");
-    alpha_log2[b] = -a * 3.32192809488736f / 10.0f;
-    if (b < s->n_bands && a != 0.0f) has_alpha = 1;
-  }
   DeviceGuard g(c->device);
   if (c->device < 0 || c->device >= 256) return fail(c, BT_E_INVALID, "device ordinal %d out of range", c->device);
-  if (!g_noalloc_ptr[c->device]) {
+  char *base = (char *)g_noalloc_ptr[c->device].load(std::memory_order_acquire);
+  if (!base) {
     // set-up, once per device, with that device current
     void *ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
@@ -1648,10 +1640,10 @@ BT_API int bt_trace_noalloc(bt_ctx *c, int32_t scene_id, const bt_trace_params *
       cudaGetLastError();
       return fail(c, BT_E_CUDA, "bt_trace_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
     }
-    g_noalloc_ptr[c->device] = ptr;
+    g_noalloc_ptr[c->device].store(ptr, std::memory_order_release);
+    base = (char *)ptr;
   }
   // carve the scratch: counters, two cursors, beam table, segment records
-  char *base = (char *)g_noalloc_ptr[c->device];
   const int64_t n_beams = (int64_t)20 << (2 * s->level);
   const int mixed = p->precision == BT_PREC_MIXED ? 1 : 0;
   size_t off = 0;
@@ -1667,6 +1659,7 @@ BT_API int bt_trace_noalloc(bt_ctx *c, int32_t scene_id, const bt_trace_params *
   const int64_t total = s->n_src * n_beams;
   int64_t chunk = (int64_t)(seg_room / (unsigned long long)(p->max_order + 1));
   if (chunk < 1) return fail(c, BT_E_INVALID, "bt_trace_noalloc: max_order %d too large for its scratch", p->max_order);
+  if (p->chunk_beams > 0 && p->chunk_beams < chunk) chunk = p->chunk_beams;
   if (chunk > total) chunk = total > 0 ? total : 1;
   const unsigned long long cap = (unsigned long long)chunk * (p->max_order + 1);
   cudaStream_t st = c->stream;
@@ -1683,7 +1676,7 @@ BT_API int bt_trace_noalloc(bt_ctx *c, int32_t scene_id, const bt_trace_params *
   ta.seg_capacity = cap;
   ta.lineage_next = lineage_next;
   ta.ctr = ctr;
-  ta.count_work = 0;
+  ta.count_work = p->count_work ? 1 : 0;
   ta.prec = p->precision;
   ta.blocks_per_sm = p->blocks_per_sm;
   bt::ScatterArgs sa;
@@ -1722,6 +1715,8 @@ BT_API int bt_trace_noalloc(bt_ctx *c, int32_t scene_id, const bt_trace_params *
   o.emitted = (int64_t)h.emitted;
   o.candidates = (int64_t)h.candidates;
   o.contributions = (int64_t)h.contributions;
+  o.nodes_visited = (int64_t)h.nodes_visited;
+  o.tris_tested = (int64_t)h.tris_tested;
   o.trace_launches = n_chunks;
   o.scatter_launches = s->n_mics > 0 ? n_chunks : 0;
   if (h.error) {
