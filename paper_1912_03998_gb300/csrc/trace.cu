@@ -1155,14 +1155,15 @@ __global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_ti
       pending = false;
       const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), v.t_eps, ls.dns);
       if constexpr (kMixed) settle_search(v.sc, r, rs, ls.dns64, hs.best, tlim);
-      if (hs.best.slot >= 0) {
-        // the hit lies in this tile; a reflected beam starts here as well
-        if (finish_segment(a, v, 0, sm, t, r, hs.best, hs.best.slot, ls, cn)) start = true;
-        else ended = true;
-      } else {
-        // no hit in this tile: step to the next tile along the ray whose
-        // geometry the ray can reach -- tiles whose root boxes it misses
-        // could give no hit, so the lane walks past them itself
+      // the hit lies in this tile (a reflected beam starts here as well); a
+      // ray without one either leaves the grid, and with it every triangle
+      // (it escapes), or goes on to the next tile
+      int fslot = hs.best.slot;
+      bool fin = fslot >= 0;
+      if (!fin) {
+        // step to the next tile along the ray whose geometry the ray can
+        // reach -- tiles whose root boxes it misses could give no hit, so the
+        // lane walks past them itself
         int ix = tile % tg.tx, iy = tile / tg.tx;
         bool leaves = false;
         while (true) {
@@ -1179,13 +1180,14 @@ __global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_ti
           }
           if (leaves || root_reachable(v.sc, __ldg(&ta.roots[iy * tg.tx + ix]), r)) break;
         }
-        if (leaves) {
-          // the ray leaves the grid, and with it every triangle: it escapes
-          finish_segment(a, v, 0, sm, t, r, hs.best, -1, ls, cn);
-          ended = true;
-        } else {
-          next = iy * tg.tx + ix;
-        }
+        if (leaves) fin = true;
+        else next = iy * tg.tx + ix;
+      }
+      // one call site, so that lanes with a hit and lanes that escape run the
+      // segment and reflection code together
+      if (fin) {
+        if (finish_segment(a, v, 0, sm, t, r, hs.best, fslot, ls, cn)) start = true;
+        else ended = true;
       }
       if (ended) active = false;
     }
