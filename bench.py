@@ -76,6 +76,10 @@ def parse():
                     help="sub-domain grid; the district configuration splits the plane 4x4")
     ap.add_argument("--no-untiled", action="store_true",
                     help="skip the secondary timing of the same workload without sub-domains")
+    ap.add_argument("--leaf-size", type=int, default=0, help="most triangles per BVH leaf (0 = library default)")
+    ap.add_argument("--beams-per-warp", type=int, default=0,
+                    help="lineages a warp reserves at a time (0 = library default)")
+    ap.add_argument("--queue-depth", type=int, default=0, help="hand-off queue slots per sub-domain (0 = automatic)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"],
                     help="mixed: float-pair image-source chain (the parity-checked default)")
     return ap.parse_args()
@@ -225,6 +229,7 @@ def run_ours(args, rank, world):
     params.tiles_x, params.tiles_y = tiles
     params.precision = {"mixed": btrace.BT_PREC_MIXED, "fp32": btrace.BT_PREC_FP32,
                         "fp64": btrace.BT_PREC_FP64}[args.precision]
+    params.leaf_size, params.beams_per_warp, params.queue_depth = args.leaf_size, args.beams_per_warp, args.queue_depth
     l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(inp, level_out):

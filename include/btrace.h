@@ -97,7 +97,24 @@ typedef struct {
                                                twice the lanes of one launch); also the most
                                                lineages in flight at once, so that no queue
                                                can overflow */
+  int32_t leaf_size;                        /* most triangles per BVH leaf, 1..4 (0 = 1): a
+                                               subtree of the LBVH holding at most this many
+                                               triangles is tested as one leaf (tuning knob;
+                                               the hits do not depend on it) */
+  int32_t beams_per_warp;                   /* beam lineages a warp of the persistent trace
+                                               reserves from the launch's lineage counter at a
+                                               time and hands to its lanes as they free up: 0
+                                               (as many as lanes need) or a multiple of 32 up
+                                               to 4096 (tuning knob) */
+  int32_t fault_test;                       /* test hook, 0 in normal use.  BT_FAULT_WITHHOLD:
+                                               the sub-domain trace withholds the publication
+                                               of its first hand-off, so the bounded wait of
+                                               its consumer runs out (BT_E_TIMEOUT);
+                                               BT_FAULT_SEGMENTS: the segment buffer gets room
+                                               for one record (BT_E_QUEUE_FULL) */
 } bt_trace_params;
+#define BT_FAULT_WITHHOLD 1
+#define BT_FAULT_SEGMENTS 2
 
 /* Counters of the last trace of a scene. */
 typedef struct {

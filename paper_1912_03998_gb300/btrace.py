@@ -21,6 +21,7 @@ BT_E_INVALID, BT_E_NOMEM, BT_E_CUDA, BT_E_STATE, BT_E_QUEUE_FULL, BT_E_TIMEOUT =
 BT_PENDING = 1
 BT_MAX_BANDS = 8
 BT_PREC_FP32, BT_PREC_MIXED, BT_PREC_FP64 = 0, 1, 2
+BT_FAULT_WITHHOLD, BT_FAULT_SEGMENTS = 1, 2  # bt_trace_params.fault_test (test hooks)
 
 _ERR_NAMES = {BT_E_INVALID: "BT_E_INVALID", BT_E_NOMEM: "BT_E_NOMEM", BT_E_CUDA: "BT_E_CUDA",
               BT_E_STATE: "BT_E_STATE", BT_E_QUEUE_FULL: "BT_E_QUEUE_FULL",
@@ -32,7 +33,8 @@ class bt_trace_params(C.Structure):
                 ("energy_threshold_w", C.c_float), ("t_eps_m", C.c_float),
                 ("tiles_x", C.c_int32), ("tiles_y", C.c_int32), ("precision", C.c_int32),
                 ("watchdog_ms", C.c_int32), ("chunk_beams", C.c_int32), ("count_work", C.c_int32),
-                ("blocks_per_sm", C.c_int32), ("queue_depth", C.c_int32)]
+                ("blocks_per_sm", C.c_int32), ("queue_depth", C.c_int32), ("leaf_size", C.c_int32),
+                ("beams_per_warp", C.c_int32), ("fault_test", C.c_int32)]
 
 
 class bt_stats(C.Structure):

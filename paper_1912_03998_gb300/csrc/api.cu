@@ -76,6 +76,7 @@ struct SceneState {
   bt_stats stats;
   unsigned long long gen = 0;  // changes whenever the scene's buffers may change (batches check it)
   int geom_of = -1;            // >= 0: the geometry buffers belong to that scene (bt_scene_share)
+  int leaf = 1, t_leaf = 1;    // leaf size the flat and the tiled hierarchy are collapsed to
   int n_shares = 0;            // scenes sharing this scene's geometry
   DevBuf out_level, out_int, out_cnt;
 };
@@ -883,6 +884,11 @@ static int check_params(bt_ctx *c, SceneState *s, const bt_trace_params *p, floa
   if (p->queue_depth != 0 && (p->queue_depth < 32 || p->queue_depth > (1 << 22) ||
                               (p->queue_depth & (p->queue_depth - 1)) != 0))
     return fail(c, BT_E_INVALID, "queue_depth must be 0 or a power of two in 32..2^22");
+  if (p->leaf_size < 0 || p->leaf_size > bt::kMaxLeafSize)
+    return fail(c, BT_E_INVALID, "leaf_size %d not in 0..%d", p->leaf_size, bt::kMaxLeafSize);
+  if (p->beams_per_warp < 0 || p->beams_per_warp > 4096 || p->beams_per_warp % 32 != 0)
+    return fail(c, BT_E_INVALID, "beams_per_warp must be 0 or a multiple of 32 up to 4096");
+  if (p->fault_test < 0 || p->fault_test > BT_FAULT_SEGMENTS) return fail(c, BT_E_INVALID, "unknown fault_test %d", p->fault_test);
   *has_alpha = 0;
   for (int b = 0; b < BT_MAX_BANDS; b++) {
     float a = p->air_atten_db_per_m[b];
@@ -890,6 +896,24 @@ static int check_params(bt_ctx *c, SceneState *s, const bt_trace_params *p, floa
     alpha_log2[b] = -a * 3.32192809488736f / 10.0f;  // 10^(-a d/10) = 2^(-a d log2(10)/10)
     if (b < s->n_bands && a != 0.0f) *has_alpha = 1;
   }
+  return BT_OK;
+}
+
+// Collapse the flat (or, with `tiled`, the sub-domain) hierarchy of scene s
+// to the leaf size p asks for, unless it already has it.  The hits do not
+// depend on the leaf size, so every scene sharing the geometry may see the
+// change.
+static int apply_leaf_size(bt_ctx *c, SceneState &s, const bt_trace_params *p, bool tiled) {
+  const int want = p->leaf_size > 0 ? p->leaf_size : 1;
+  SceneState &g = s.geom_of >= 0 ? c->sc[s.geom_of] : s;
+  int &have = tiled ? s.t_leaf : g.leaf;
+  if (have == want) return BT_OK;
+  const int64_t n = tiled ? s.n_pairs : g.n_tris;
+  if (want > 1 && n >= ((int64_t)1 << bt::kLeafShift))
+    return fail(c, BT_E_INVALID, "leaf_size > 1 needs fewer than 2^%d leaves (the hierarchy has %lld)", bt::kLeafShift,
+                (long long)n);
+  CK(bt::collapse_leaves(c->stream, (bt::Node *)(tiled ? s.t_nodes.p : g.nodes.p), n, want));
+  have = want;
   return BT_OK;
 }
 
@@ -925,6 +949,7 @@ static int enqueue_trace(bt_ctx *c, int32_t id, const bt_trace_params *p) {
   unsigned qcap = 1024;
   if (tiled) {
     TRY(ensure_tiled(c, *s, p->tiles_x, p->tiles_y));
+    TRY(apply_leaf_size(c, *s, p, true));
     if (p->queue_depth > 0) {
       qcap = (unsigned)p->queue_depth;
     } else {
@@ -934,7 +959,9 @@ static int enqueue_trace(bt_ctx *c, int32_t id, const bt_trace_params *p) {
     }
     TRY(ensure(c, c->t_ring, sizeof(uint32_t) * bt::kStateRows * (size_t)T * qcap));
     TRY(ensure(c, c->t_seq, sizeof(unsigned) * (size_t)T * qcap));
-    TRY(ensure(c, c->t_qctl, sizeof(int) * (3 * (size_t)T + 2)));
+    TRY(ensure(c, c->t_qctl, sizeof(int) * (3 * (size_t)T + 3)));
+  } else {
+    TRY(apply_leaf_size(c, *s, p, false));
   }
   TRY(reset_counters(c));
   CK(cudaMemsetAsync(s->energy.p, 0, sizeof(double) * bt::kMaxBands * (size_t)s->n_mics, st));
@@ -953,12 +980,15 @@ static int enqueue_trace(bt_ctx *c, int32_t id, const bt_trace_params *p) {
   }
   ta.segs = (bt::Seg *)c->segs.p;
   ta.seg_count = c->d_seg_count;
-  ta.seg_capacity = cap;
+  // (test hook: room for one segment record, so that the trace overflows)
+  ta.seg_capacity = p->fault_test == BT_FAULT_SEGMENTS ? 1 : cap;
   ta.lineage_next = c->d_lineage_next;
   ta.ctr = c->d_ctr;
   ta.count_work = p->count_work ? 1 : 0;
   ta.prec = p->precision;
   ta.blocks_per_sm = p->blocks_per_sm;
+  ta.beams_per_warp = p->beams_per_warp;
+  ta.leaf_size = p->leaf_size > 1 ? p->leaf_size : 1;
   if (ta.prec == BT_PREC_MIXED && total > 0) {
     if (c->beam_table_level != s->level) {
       TRY(ensure(c, c->beam_table, sizeof(float) * 24 * (size_t)n_beams));
@@ -974,7 +1004,7 @@ static int enqueue_trace(bt_ctx *c, int32_t id, const bt_trace_params *p) {
   sa.max_nz = s->nz;
   sa.segs = ta.segs;
   sa.seg_count = c->d_seg_count;
-  sa.seg_capacity = cap;
+  sa.seg_capacity = ta.seg_capacity;
   sa.ctr = c->d_ctr;
   bt::TiledArgs tga;
   memset(&tga, 0, sizeof(tga));
@@ -987,6 +1017,7 @@ static int enqueue_trace(bt_ctx *c, int32_t id, const bt_trace_params *p) {
     tga.seq = (unsigned *)c->t_seq.p;
     tga.ctl = (int *)c->t_qctl.p;
     tga.watchdog_ns = (unsigned long long)(p->watchdog_ms > 0 ? p->watchdog_ms : 2000) * 1000000ull;
+    tga.withhold = p->fault_test == BT_FAULT_WITHHOLD ? 1 : 0;
   }
   // Events bracket every launch: a pair per launch, its kind in r.kind.
   int n_ev = 0;
@@ -1018,7 +1049,7 @@ static int enqueue_trace(bt_ctx *c, int32_t id, const bt_trace_params *p) {
     CK(cudaMemsetAsync(c->d_lineage_next, 0, sizeof(unsigned long long), st));
     if (tiled) {
       CK(cudaMemsetAsync(c->t_seq.p, 0, sizeof(unsigned) * (size_t)T * qcap, st));
-      CK(cudaMemsetAsync(c->t_qctl.p, 0, sizeof(int) * (3 * (size_t)T + 2), st));
+      CK(cudaMemsetAsync(c->t_qctl.p, 0, sizeof(int) * (3 * (size_t)T + 3), st));
     }
     TRY(mark(0));
     if (tiled) {
@@ -1145,7 +1176,7 @@ struct bt_batch {
   std::vector<unsigned long long> gens;
   std::vector<int64_t> beams;  // lineages per scene
   int prec = BT_PREC_MIXED;
-  int count_work = 0, blocks_per_sm = 0;
+  int count_work = 0, blocks_per_sm = 0, beams_per_warp = 0, leaf_size = 1;
   int max_order = 0, max_nz = 1;
   int64_t total = 0, chunk = 1;
   DevBuf views, segs, beam_tables[9];
@@ -1195,8 +1226,11 @@ BT_API int bt_batch_create(bt_ctx *c, const int32_t *scene_ids, int32_t n_scenes
     if (p->tiles_x != 1 || p->tiles_y != 1)
       return fail(c, BT_E_INVALID, "a batch traces every scene unsplit (tiles 1x1)");
     if (p->precision != prec || p->count_work != params[0].count_work ||
-        p->blocks_per_sm != params[0].blocks_per_sm || p->chunk_beams != params[0].chunk_beams)
-      return fail(c, BT_E_INVALID, "precision, count_work, blocks_per_sm and chunk_beams must agree across a batch");
+        p->blocks_per_sm != params[0].blocks_per_sm || p->chunk_beams != params[0].chunk_beams ||
+        p->beams_per_warp != params[0].beams_per_warp)
+      return fail(c, BT_E_INVALID,
+                  "precision, count_work, blocks_per_sm, beams_per_warp and chunk_beams must agree across a batch");
+    TRY(apply_leaf_size(c, *s, p, false));
     fill_view(hv[i], *s, p, alpha_log2, has_alpha);
   }
   bt_batch *b = new bt_batch();
@@ -1204,6 +1238,9 @@ BT_API int bt_batch_create(bt_ctx *c, const int32_t *scene_ids, int32_t n_scenes
   b->prec = prec;
   b->count_work = params[0].count_work ? 1 : 0;
   b->blocks_per_sm = params[0].blocks_per_sm;
+  b->beams_per_warp = params[0].beams_per_warp;
+  for (int i = 0; i < n_scenes; i++)
+    if (params[i].leaf_size > b->leaf_size) b->leaf_size = params[i].leaf_size;
   memset(&b->stats, 0, sizeof(b->stats));
   DeviceGuard g(c->device);
   cudaStream_t st = c->stream;
@@ -1281,6 +1318,8 @@ static int record_batch(bt_batch *b) {
   ta.count_work = b->count_work;
   ta.prec = b->prec;
   ta.blocks_per_sm = b->blocks_per_sm;
+  ta.beams_per_warp = b->beams_per_warp;
+  ta.leaf_size = b->leaf_size;
   bt::ScatterArgs sa;
   memset(&sa, 0, sizeof(sa));
   sa.views = ta.views;
@@ -1421,8 +1460,10 @@ BT_API int bt_trace_ranges(bt_ctx *c, int32_t n, const int32_t *scene_ids, const
     int has_alpha = 0;
     TRY(check_params(c, s, p, alpha_log2, &has_alpha));
     if (p->tiles_x != 1 || p->tiles_y != 1) return fail(c, BT_E_INVALID, "bt_trace_ranges traces unsplit (tiles 1x1)");
-    if (p->precision != prec || p->blocks_per_sm != params[0].blocks_per_sm || p->count_work != params[0].count_work)
-      return fail(c, BT_E_INVALID, "precision, blocks_per_sm and count_work must agree across the scenes");
+    if (p->precision != prec || p->blocks_per_sm != params[0].blocks_per_sm || p->count_work != params[0].count_work ||
+        p->beams_per_warp != params[0].beams_per_warp)
+      return fail(c, BT_E_INVALID, "precision, blocks_per_sm, beams_per_warp and count_work must agree across the scenes");
+    TRY(apply_leaf_size(c, *s, p, false));
     const int64_t nl = s->n_src * ((int64_t)20 << (2 * s->level));
     if (lineage_begin[i] < 0 || lineage_end[i] < lineage_begin[i] || lineage_end[i] > nl)
       return fail(c, BT_E_INVALID, "scene %d: lineage range [%lld, %lld) outside [0, %lld)", scene_ids[i],
@@ -1477,6 +1518,10 @@ BT_API int bt_trace_ranges(bt_ctx *c, int32_t n, const int32_t *scene_ids, const
   ta.count_work = params[0].count_work ? 1 : 0;
   ta.prec = prec;
   ta.blocks_per_sm = params[0].blocks_per_sm;
+  ta.beams_per_warp = params[0].beams_per_warp;
+  ta.leaf_size = 1;
+  for (int i = 0; i < n; i++)
+    if (params[i].leaf_size > ta.leaf_size) ta.leaf_size = params[i].leaf_size;
   bt::ScatterArgs sa;
   memset(&sa, 0, sizeof(sa));
   sa.v = ta.v;
@@ -1667,6 +1712,7 @@ BT_API int bt_trace_noalloc(bt_ctx *c, int32_t scene_id, const bt_trace_params *
   CK(cudaMemsetAsync(s->energy.p, 0, sizeof(double) * bt::kMaxBands * (size_t)s->n_mics, st));
   CK(cudaMemsetAsync(s->count.p, 0, sizeof(int) * (size_t)s->n_mics, st));
   if (mixed && total > 0) CK(bt::launch_beam_table(st, s->level, beam_table));
+  TRY(apply_leaf_size(c, *s, p, false));
   bt::TraceArgs ta;
   memset(&ta, 0, sizeof(ta));
   fill_view(ta.v, *s, p, alpha_log2, has_alpha);
@@ -1679,6 +1725,8 @@ BT_API int bt_trace_noalloc(bt_ctx *c, int32_t scene_id, const bt_trace_params *
   ta.count_work = p->count_work ? 1 : 0;
   ta.prec = p->precision;
   ta.blocks_per_sm = p->blocks_per_sm;
+  ta.beams_per_warp = p->beams_per_warp;
+  ta.leaf_size = p->leaf_size > 1 ? p->leaf_size : 1;
   bt::ScatterArgs sa;
   memset(&sa, 0, sizeof(sa));
   sa.v = ta.v;

@@ -15,13 +15,20 @@ constexpr float kInf = __builtin_huge_valf();
 
 // ------------------------------------------------------------------ layouts
 // BVH2 node, 64 bytes: both children's boxes, so one node fetch decides both.
-// Child index c >= 0: internal node; c < 0: leaf holding triangle slot ~c.
+// Child index c >= 0: internal node; c < 0: a leaf, v = ~c: the leaf holds
+// leaf_count(v) triangles from slot leaf_slot(v) on (a leaf of one triangle
+// is ~slot; larger leaves come from collapsing small subtrees).
 struct __align__(16) Node {
   float4 lxy;  // left  lo.x, hi.x, lo.y, hi.y
   float4 rxy;  // right lo.x, hi.x, lo.y, hi.y
   float4 lrz;  // left lo.z, hi.z, right lo.z, hi.z
   int4 child;  // left, right, parent, unused
 };
+
+constexpr int kLeafShift = 29;  // leaf code: slot in bits 0..28, count - 1 above
+constexpr int kMaxLeafSize = 4;
+__host__ __device__ __forceinline__ int leaf_slot(int v) { return v & ((1 << kLeafShift) - 1); }
+__host__ __device__ __forceinline__ int leaf_count(int v) { return (v >> kLeafShift) + 1; }
 
 // Triangle in leaf order, 48 bytes for the hit test: v0.w = material (int
 // bits), v1.w = original triangle id (int bits), v2.w unused.
@@ -72,6 +79,7 @@ struct TiledArgs {
   int *ctl;                 // zero at launch: head[n_tiles], tail[n_tiles], avail[n_tiles],
                             // credits in use, lineages finished
   unsigned long long watchdog_ns;  // bound on any wait of a warp that has no work
+  int withhold;             // test hook: the launch's first hand-off is never published
 };
 
 struct DevScene {
@@ -171,6 +179,8 @@ struct TraceArgs {
   int count_work;
   int prec;   // BT_PREC_FP32, BT_PREC_MIXED or BT_PREC_FP64
   int blocks_per_sm;  // persistent grid: resident blocks per SM, 0 = as many as fit
+  int beams_per_warp; // lineages a warp reserves at a time (0 = what its lanes need)
+  int leaf_size;      // most triangles per BVH leaf (1: the traversal without leaf runs)
 };
 
 struct ScatterArgs {
@@ -438,6 +448,10 @@ cudaError_t tiled_build(cudaStream_t st, const Tri *src, const Plane *sp, const 
                         void *scratch, size_t scratch_bytes, Node *nodes, Tri *tris, Plane *planes,
                         Plane64 *planes64, PlaneDF *planes_df, int *roots, int *d_error);
 size_t build_scene_scratch_bytes(int64_t n_tris);
+// Rewrite the child links of a built LBVH (n_leaves leaves) so that every
+// subtree of at most leaf_size triangles is one leaf; any earlier collapse is
+// undone first, so the call can change the leaf size back and forth.
+cudaError_t collapse_leaves(cudaStream_t st, Node *nodes, int64_t n_leaves, int leaf_size);
 cudaError_t mic_box(cudaStream_t st, const float *d_pos, int64_t n_m, float *d_box, int *d_error);
 cudaError_t build_mics(cudaStream_t st, const float *d_pos, int64_t n_m, int nx, int ny, int nz,
                        const float *d_box, MicGrid *d_grid, float4 *d_sorted, int *d_cell_start, void *d_scratch,

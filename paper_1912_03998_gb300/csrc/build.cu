@@ -374,6 +374,43 @@ __global__ void k_lbvh_boxes(const Tri *tris, int n, Node *nodes, const int *lea
   }
 }
 
+// Leaf size of the traversal: one thread per internal node rewrites its two
+// child links.  A link first goes back to the node the LBVH built (a left
+// child covers the key range ending at its own index, a right child the range
+// starting at it, so a collapsed leaf (first, count) names its node); then a
+// child node whose range holds at most leaf_size leaves becomes one leaf of
+// those leaves, which are consecutive slots.  Ranges (child.w) are never
+// written, so the threads do not race.
+__global__ void k_collapse_leaves(Node *nodes, int n_internal, int leaf_size) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_internal) return;
+  int2 ch = make_int2(nodes[p].child.x, nodes[p].child.y);
+  int out[2];
+  for (int side = 0; side < 2; side++) {
+    int c = side == 0 ? ch.x : ch.y;
+    if (c < 0 && leaf_count(~c) > 1) {
+      const int v = ~c;
+      c = side == 0 ? leaf_slot(v) + leaf_count(v) - 1 : leaf_slot(v);
+    }
+    if (c >= 0) {
+      const int j = nodes[c].child.w;
+      const int lo = c < j ? c : j, cnt = (c < j ? j - c : c - j) + 1;
+      if (cnt <= leaf_size) c = ~(lo | ((cnt - 1) << kLeafShift));
+    }
+    out[side] = c;
+  }
+  nodes[p].child.x = out[0];
+  nodes[p].child.y = out[1];
+}
+
+cudaError_t collapse_leaves(cudaStream_t st, Node *nodes, int64_t n_leaves, int leaf_size) {
+  if (n_leaves < 2) return cudaSuccess;
+  const int n = (int)(n_leaves - 1);
+  k_collapse_leaves<<<(n + 255) / 256, 256, 0, st>>>(nodes, n, leaf_size);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t build_scene_scratch_bytes(int64_t n) {

@@ -328,17 +328,21 @@ struct HitSearch {
   }
   // One node of the traversal (nearer child first, both children's boxes in
   // one fetch) and the leaves it exposes.  False once the search is over.
-  template <int kP, bool kCount>
+  template <int kP, bool kCount, bool kLeaves>
   __device__ __forceinline__ bool step(const DevScene &sc, const Node *nodes, const Tri *tris, int64_t n_tri,
                                        const Ray &r, const RaySrc &rs, double dns64, int *stack, int *err,
                                        unsigned &n_nodes, unsigned &n_tris, float tlim) {
     if (n_tri == 0 || node == (int)0x80000000) return false;
+    // up to two leaves per step (leaf codes v: see Node)
     int c0 = -1, c1 = -1, nc = 0;
     bool more = true;
-    if (node < 0) {  // a single-triangle scene: the root is a leaf
+    if (node < 0) {
+      // a leaf: the root of a one-leaf hierarchy, or (kLeaves) the rest of a
+      // larger leaf put back on the stack (below)
       c0 = ~node;
       nc = 1;
-      more = false;
+      if (kLeaves && sp > 0) node = stack[--sp];
+      else more = false;
     } else {
       // a well-formed BVH is visited at most once per node; the bound only
       // guarantees termination should the structure ever be malformed
@@ -373,7 +377,24 @@ struct HitSearch {
       }
     }
 #pragma unroll 1
-    for (int c = 0; c < nc; c++) consider_tri<kP, kCount>(sc, tris, r, rs, dns64, best, c == 0 ? c0 : c1, n_tris, tlim);
+    for (int c = 0; c < nc; c++) {
+      const int v = c == 0 ? c0 : c1;
+      if (kLeaves && (v >> kLeafShift)) {
+        // a leaf of several triangles: its first now, the rest as a leaf of
+        // one triangle fewer at a later step, so that a step still tests at
+        // most two triangles
+        const int rest = ~((leaf_slot(v) + 1) | (((v >> kLeafShift) - 1) << kLeafShift));
+        if (!more) {
+          node = rest;
+          more = true;
+        } else if (sp < kStackDepth) {
+          stack[sp++] = rest;
+        } else {
+          atomicExch(err, BT_E_QUEUE_FULL);
+        }
+      }
+      consider_tri<kP, kCount>(sc, tris, r, rs, dns64, best, kLeaves ? leaf_slot(v) : v, n_tris, tlim);
+    }
     return more;
   }
 };
@@ -392,7 +413,7 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, Ray
   HitSearch hs;
   hs.start(root);
   if constexpr (kP == kPMixed) rs.pend[0] = 0;
-  while (hs.step<kP, kCount>(sc, nodes, tris, n_tri, r, rs, dns64, stack, err, n_nodes, n_tris, tlim)) {
+  while (hs.step<kP, kCount, true>(sc, nodes, tris, n_tri, r, rs, dns64, stack, err, n_nodes, n_tris, tlim)) {
   }
   best = hs.best;
   if constexpr (kP == kPMixed) settle_search(sc, r, rs, dns64, best, tlim);
@@ -773,19 +794,67 @@ __device__ __forceinline__ void flush_counts(const TraceArgs &a, const TraceCoun
   }
 }
 
+// A warp's reservation of lineages, [next, end) relative to the launch's
+// first lineage, in shared memory; `last` once the launch's counter has run
+// past the end (nothing more to reserve).
+struct WarpLineages {
+  unsigned long long next, end;
+  int last;
+};
+
+// Lineages a warp reserves at a time: what its lanes need now, or at least
+// beams_per_warp, so that it draws from the launch's counter less often (at
+// the price of a coarser end of the launch).
+__device__ __forceinline__ unsigned long long reserve_size(const TraceArgs &a, unsigned long long need) {
+  const unsigned long long b = (unsigned long long)a.beams_per_warp;
+  return need > b ? need : b;
+}
+
 // Take the next lineage of the batch for every lane in `need` (warp-vote
-// refill).  Returns the lineage index or -1 when the batch is used up.
-__device__ __forceinline__ int64_t take_lineage(const TraceArgs &a, bool need) {
+// refill): first from the warp's reservation, then from a new one.  Returns
+// the lineage index or -1 when the batch is used up.
+__device__ __forceinline__ int64_t take_lineage(const TraceArgs &a, bool need, WarpLineages &wl) {
   unsigned nm = __ballot_sync(0xffffffffu, need);
   if (!nm) return -1;
   const unsigned lane = lane_id();
-  int leader = __ffs(nm) - 1;
-  unsigned long long base = 0;
-  if ((int)lane == leader) base = atomicAdd(a.lineage_next, (unsigned long long)__popc(nm));
-  base = __shfl_sync(0xffffffffu, base, leader);
+  if (a.beams_per_warp == 0) {
+    // as many as the lanes need, straight from the launch's counter
+    const int leader = __ffs(nm) - 1;
+    unsigned long long base = 0;
+    if ((int)lane == leader) base = atomicAdd(a.lineage_next, (unsigned long long)__popc(nm));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (!need) return -1;
+    const int64_t mine = a.lineage_begin + (int64_t)(base + __popc(nm & ((1u << lane) - 1u)));
+    return mine < a.lineage_end ? mine : -1;
+  }
+  const unsigned long long total = (unsigned long long)(a.lineage_end - a.lineage_begin);
+  const unsigned long long n = (unsigned long long)__popc(nm);
+  const unsigned long long next = wl.next, end = wl.end, have = end - next;
+  const int last = wl.last;
+  unsigned long long b = total, got = 0;
+  if (have < n && !last && (int)lane == __ffs(nm) - 1) {
+    const unsigned long long R = reserve_size(a, n - have);
+    b = atomicAdd(a.lineage_next, R);
+    got = b < total ? (b + R < total ? R : total - b) : 0;
+    if (b + R >= total) wl.last = 1;
+  }
+  b = __shfl_sync(0xffffffffu, b, __ffs(nm) - 1);
+  got = __shfl_sync(0xffffffffu, got, __ffs(nm) - 1);
+  __syncwarp();
+  if (lane == 0) {
+    if (have < n && !last) {
+      const unsigned long long used = n - have < got ? n - have : got;
+      wl.next = b + used;
+      wl.end = b + got;
+    } else {
+      wl.next = next + (n < have ? n : have);
+    }
+  }
+  __syncwarp();
   if (!need) return -1;
-  int64_t mine = a.lineage_begin + (int64_t)(base + __popc(nm & ((1u << lane) - 1u)));
-  return mine < a.lineage_end ? mine : -1;
+  const unsigned long long r = (unsigned long long)__popc(nm & ((1u << lane) - 1u));
+  if (r < have) return a.lineage_begin + (int64_t)(next + r);
+  return r - have < got ? a.lineage_begin + (int64_t)(b + (r - have)) : -1;
 }
 
 // Persistent warps: every lane works on one lineage at a time and takes the
@@ -823,12 +892,15 @@ constexpr int kRefillLanes = 28;
 // lineage), lanes without a lineage take new ones, and new searches start --
 // while the lanes still searching keep their state, so a long search no longer
 // holds the whole warp (dynamic ray fetch, after Aila & Laine 2009).
-template <int kP, bool kCount, bool kBatch>
+template <int kP, bool kCount, bool kBatch, bool kLeaves>
 __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
   [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   __shared__ LineageSmem<kP> sm;
   __shared__ int64_t view_base[kBatch ? BT_MAX_SCENES : 1];
+  __shared__ WarpLineages wlin[kTraceThreads / 32];
   const int t = threadIdx.x;
+  if ((t & 31) == 0) wlin[t >> 5] = WarpLineages{0ull, 0ull, 0};
+  __syncwarp();
   if (kBatch) {
     for (int i = t; i < a.n_views; i += kTraceThreads) view_base[i] = a.views[i].lineage_base;
     __syncthreads();
@@ -855,7 +927,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
     }
     // ---- service: lanes without a lineage take the next ones
     bool need = !done && ls.lin < 0;
-    int64_t mine = take_lineage(a, need);
+    int64_t mine = take_lineage(a, need, wlin[t >> 5]);
     if (need) {
       if (mine >= 0) {
         if (kBatch) {
@@ -884,8 +956,8 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
       const Tri *const tris = v.sc.tris;
       while (true) {
         if (searching &&
-            !hs.step<kP, kCount>(v.sc, nodes, tris, n_tri, r, rs, ls.dns64, stack, &a.ctr->error, cn[kCNodes],
-                                 cn[kCTris], kInf)) {
+            !hs.step<kP, kCount, kLeaves>(v.sc, nodes, tris, n_tri, r, rs, ls.dns64, stack, &a.ctr->error,
+                                          cn[kCNodes], cn[kCTris], kInf)) {
           searching = false;
           pending = true;
         }
@@ -1047,28 +1119,54 @@ __device__ __forceinline__ int take_handoffs(const TiledArgs &ta, int home, int 
 // per lane.  Warp-collective, warp-uniform result: the first lineage offset
 // and the count; *exhausted is set once the batch is used up.
 __device__ __forceinline__ int take_fresh(const TraceArgs &a, const TiledArgs &ta, int want, int &credits,
-                                          int64_t &base, bool &exhausted) {
+                                          int64_t &base, bool &exhausted, WarpLineages &wl) {
   int *used = ta.ctl + 3 * ta.n_tiles;
   int got = 0;
   unsigned long long b = 0;
   int ex = 0, c = credits;
   if (lane_id() == 0) {
-    if (c < want) {
-      int req = 32 - c;
+    const unsigned long long n = (unsigned long long)(a.lineage_end - a.lineage_begin);
+    // with beams_per_warp the warp reserves lineages ahead, and a reserved
+    // lineage holds its credit from the moment it is reserved, so that
+    // reservations never exceed the cap on lineages in flight
+    const int bpw = a.beams_per_warp;
+    const bool refill = bpw > 0 && wl.next == wl.end && !wl.last;
+    const int target = bpw > 32 ? bpw : 32;
+    if (c < want || (refill && c < target)) {
+      int req = target - c;
       int old = atomicAdd(used, req);
       int g = (int)ta.qcap - old;
       g = g < 0 ? 0 : (g < req ? g : req);
       if (g < req) atomicSub(used, req - g);
       c += g;
     }
-    int k = c < want ? c : want;
-    if (k > 0) {
-      const unsigned long long n = (unsigned long long)(a.lineage_end - a.lineage_begin);
-      b = atomicAdd(a.lineage_next, (unsigned long long)k);
-      unsigned long long left = b < n ? n - b : 0;
-      if (left <= (unsigned long long)k) ex = 1;
-      got = left < (unsigned long long)k ? (int)left : k;
-      c -= got;
+    if (bpw == 0) {
+      int k = c < want ? c : want;
+      if (k > 0) {
+        b = atomicAdd(a.lineage_next, (unsigned long long)k);
+        unsigned long long left = b < n ? n - b : 0;
+        if (left <= (unsigned long long)k) ex = 1;
+        got = left < (unsigned long long)k ? (int)left : k;
+        c -= got;
+      }
+    } else {
+      if (refill && c > 0) {
+        const unsigned long long R = (unsigned long long)(c < bpw ? c : bpw);
+        const unsigned long long r0 = atomicAdd(a.lineage_next, R);
+        wl.next = r0 < n ? r0 : n;
+        wl.end = r0 + R < n ? r0 + R : n;
+        if (r0 + R >= n) wl.last = 1;
+        c -= (int)(wl.end - wl.next);
+      }
+      const unsigned long long have = wl.end - wl.next;
+      got = have < (unsigned long long)want ? (int)have : want;
+      b = wl.next;
+      wl.next += got;
+      if (wl.last && wl.next == wl.end) ex = 1;
+    }
+    if (ex && c > 0) {  // no fresh lineages left for this warp: its spare credits go back
+      atomicSub(used, c);
+      c = 0;
     }
   }
   got = __shfl_sync(0xffffffffu, got, 0);
@@ -1116,7 +1214,7 @@ __device__ __forceinline__ float tile_exit(const TileGrid &tg, int ix, int iy, c
 // searches start), so a long search does not hold the whole warp.
 // Six resident blocks per SM, as for k_trace; seven for the float32 variant,
 // whose smaller state fits them (40.7 -> 38.3 ms on the district split 4x4).
-template <int kP, bool kCount>
+template <int kP, bool kCount, bool kLeaves>
 __global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_tiled(TraceArgs a, const __grid_constant__ TiledArgs ta) {
   [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   __shared__ LineageSmem<kP> sm;
@@ -1132,6 +1230,9 @@ __global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_ti
   int *const finished = used + 1;
   const int n_batch = (int)(a.lineage_end - a.lineage_begin);
   int credits = 0;  // warp-uniform
+  __shared__ WarpLineages wlin[kTraceThreads / 32];
+  if (lane == 0) wlin[threadIdx.x >> 5] = WarpLineages{0ull, 0ull, 0};
+  __syncwarp();
   LaneState ls = {-1, 0, -1, 0.0f, 0.0};
   bool active = false;      // the lane holds a lineage
   bool searching = false;   // its search in the current tile is under way
@@ -1217,7 +1318,9 @@ __global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_ti
       // been taken; its consumer may still be reading it
       if (wait_slot(a, ta, sq, gen)) {
         save_state(ta.ring + (size_t)next * kStateRows * qc + slot, qc, sm, t, ls);
-        st_release_u32(sq, gen + 1u);
+        // (test hook: the launch's first hand-off is never published, so its
+        // consumer's bounded wait runs out)
+        if (!ta.withhold || atomicAdd(ta.ctl + 3 * ta.n_tiles + 2, 1) != 0) st_release_u32(sq, gen + 1u);
       }
       __syncwarp(grp);
       if ((int)lane == gl) atomicAdd(&ta.ctl[2 * ta.n_tiles + next], n);
@@ -1250,7 +1353,7 @@ __global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_ti
       nm = __ballot_sync(0xffffffffu, !active);
       if (nm && !exhausted) {
         int64_t fb;
-        int got_f = take_fresh(a, ta, __popc(nm), credits, fb, exhausted);
+        int got_f = take_fresh(a, ta, __popc(nm), credits, fb, exhausted, wlin[threadIdx.x >> 5]);
         int rank = __popc(nm & below);
         if (!active && rank < got_f) {
           int64_t mine = a.lineage_begin + fb + rank;
@@ -1302,8 +1405,8 @@ __global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_ti
       const Node *const nodes = v.sc.nodes;
       const Tri *const tris = v.sc.tris;
       while (true) {
-        if (searching && !hs.step<kP, kCount>(v.sc, nodes, tris, n_tri, r, rs, ls.dns64, stack, &a.ctr->error,
-                                              cn[kCNodes], cn[kCTris], tlim)) {
+        if (searching && !hs.step<kP, kCount, kLeaves>(v.sc, nodes, tris, n_tri, r, rs, ls.dns64, stack,
+                                                       &a.ctr->error, cn[kCNodes], cn[kCTris], tlim)) {
           searching = false;
           pending = true;
         }
@@ -1316,35 +1419,38 @@ __global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_ti
   flush_counts(a, cn, kCount);
 }
 
-template <int kP, bool kCount>
+template <int kP, bool kCount, bool kLeaves>
 static cudaError_t launch_tiled_t(cudaStream_t st, const TraceArgs &a, const TiledArgs &ta, int n_sm) {
-  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
   int per_sm = 0;
-  cudaError_t e =
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tiled<kP, kCount>, kTraceThreads, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tiled<kP, kCount, kLeaves>,
+                                                                kTraceThreads, 0);
   if (e != cudaSuccess) return e;
   if (a.blocks_per_sm > 0 && a.blocks_per_sm < per_sm) per_sm = a.blocks_per_sm;
   if (per_sm < 1) per_sm = 1;
   int64_t blocks = (int64_t)n_sm * per_sm;
-  k_trace_tiled<kP, kCount><<<(int)blocks, kTraceThreads, 0, st>>>(a, ta);
+  k_trace_tiled<kP, kCount, kLeaves><<<(int)blocks, kTraceThreads, 0, st>>>(a, ta);
   return cudaGetLastError();
+}
+
+template <int kP>
+static cudaError_t launch_tiled_p(cudaStream_t st, const TraceArgs &a, const TiledArgs &ta, int n_sm) {
+  if (a.leaf_size > 1)
+    return a.count_work ? launch_tiled_t<kP, true, true>(st, a, ta, n_sm) : launch_tiled_t<kP, false, true>(st, a, ta, n_sm);
+  return a.count_work ? launch_tiled_t<kP, true, false>(st, a, ta, n_sm) : launch_tiled_t<kP, false, false>(st, a, ta, n_sm);
 }
 
 cudaError_t launch_trace_tiled(cudaStream_t st, const TraceArgs &a, const TiledArgs &ta, int n_sm) {
   cudaError_t e;
-  if (a.prec == kPMixed)
-    e = a.count_work ? launch_tiled_t<kPMixed, true>(st, a, ta, n_sm) : launch_tiled_t<kPMixed, false>(st, a, ta, n_sm);
-  else if (a.prec == kPF64)
-    e = a.count_work ? launch_tiled_t<kPF64, true>(st, a, ta, n_sm) : launch_tiled_t<kPF64, false>(st, a, ta, n_sm);
-  else
-    e = a.count_work ? launch_tiled_t<kPF32, true>(st, a, ta, n_sm) : launch_tiled_t<kPF32, false>(st, a, ta, n_sm);
+  if (a.prec == kPMixed) e = launch_tiled_p<kPMixed>(st, a, ta, n_sm);
+  else if (a.prec == kPF64) e = launch_tiled_p<kPF64>(st, a, ta, n_sm);
+  else e = launch_tiled_p<kPF32>(st, a, ta, n_sm);
   note_launches(1);
   return e;
 }
 
 int tiled_resident_lanes(int n_sm) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tiled<kPMixed, false>, kTraceThreads, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tiled<kPMixed, false, false>, kTraceThreads, 0) !=
       cudaSuccess)
     per_sm = 8;
   if (per_sm < 1) per_sm = 1;
@@ -1390,11 +1496,11 @@ cudaError_t launch_cast(cudaStream_t st, const DevScene &sc, const float *o, con
 
 // One persistent grid: enough blocks to fill every SM at the kernel's
 // occupancy, each block looping until the batch's lineages are taken.
-template <int kP, bool kCount, bool kBatch>
+template <int kP, bool kCount, bool kBatch, bool kLeaves>
 static cudaError_t launch_trace_t(cudaStream_t st, const TraceArgs &a, int n_sm) {
   int per_sm = 0;
-  cudaError_t e =
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<kP, kCount, kBatch>, kTraceThreads, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<kP, kCount, kBatch, kLeaves>,
+                                                                kTraceThreads, 0);
   if (e != cudaSuccess) return e;
   if (a.blocks_per_sm > 0 && a.blocks_per_sm < per_sm) per_sm = a.blocks_per_sm;
   if (per_sm < 1) per_sm = 1;
@@ -1402,20 +1508,24 @@ static cudaError_t launch_trace_t(cudaStream_t st, const TraceArgs &a, int n_sm)
   int64_t blocks = (int64_t)n_sm * per_sm;
   int64_t need = (n + kTraceThreads - 1) / kTraceThreads;
   if (blocks > need) blocks = need;
-  k_trace<kP, kCount, kBatch><<<(int)blocks, kTraceThreads, 0, st>>>(a);
+  k_trace<kP, kCount, kBatch, kLeaves><<<(int)blocks, kTraceThreads, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int kP, bool kBatch>
+static cudaError_t launch_trace_p(cudaStream_t st, const TraceArgs &a, int n_sm) {
+  if (a.leaf_size > 1)
+    return a.count_work ? launch_trace_t<kP, true, kBatch, true>(st, a, n_sm)
+                        : launch_trace_t<kP, false, kBatch, true>(st, a, n_sm);
+  return a.count_work ? launch_trace_t<kP, true, kBatch, false>(st, a, n_sm)
+                      : launch_trace_t<kP, false, kBatch, false>(st, a, n_sm);
 }
 
 template <bool kBatch>
 static cudaError_t launch_trace_b(cudaStream_t st, const TraceArgs &a, int n_sm) {
-  if (a.prec == kPMixed)
-    return a.count_work ? launch_trace_t<kPMixed, true, kBatch>(st, a, n_sm)
-                        : launch_trace_t<kPMixed, false, kBatch>(st, a, n_sm);
-  if (a.prec == kPF64)
-    return a.count_work ? launch_trace_t<kPF64, true, kBatch>(st, a, n_sm)
-                        : launch_trace_t<kPF64, false, kBatch>(st, a, n_sm);
-  return a.count_work ? launch_trace_t<kPF32, true, kBatch>(st, a, n_sm)
-                      : launch_trace_t<kPF32, false, kBatch>(st, a, n_sm);
+  if (a.prec == kPMixed) return launch_trace_p<kPMixed, kBatch>(st, a, n_sm);
+  if (a.prec == kPF64) return launch_trace_p<kPF64, kBatch>(st, a, n_sm);
+  return launch_trace_p<kPF32, kBatch>(st, a, n_sm);
 }
 
 cudaError_t launch_trace(cudaStream_t st, const TraceArgs &a, int n_sm) {

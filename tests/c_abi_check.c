@@ -87,9 +87,9 @@ int main(int argc, char **argv) {
   int trace = argc > 1 && strcmp(argv[1], "--trace") == 0;
   /* layouts: every field of the parameters is 4 bytes wide, the stats are
    * 14 int64 counters then 3 doubles */
-  CHECK(sizeof(bt_trace_params) == 4 * (1 + BT_MAX_BANDS + 1 + 1 + 2 + 1 + 1 + 1 + 1 + 1 + 1));
+  CHECK(sizeof(bt_trace_params) == 4 * (1 + BT_MAX_BANDS + 1 + 1 + 2 + 1 + 1 + 1 + 1 + 1 + 1 + 3));
   CHECK(offsetof(bt_trace_params, air_atten_db_per_m) == 4);
-  CHECK(offsetof(bt_trace_params, queue_depth) == sizeof(bt_trace_params) - 4);
+  CHECK(offsetof(bt_trace_params, fault_test) == sizeof(bt_trace_params) - 4);
   CHECK(sizeof(bt_stats) == 8 * 17);
   CHECK(offsetof(bt_stats, trace_ms) == 8 * 14);
 
@@ -98,6 +98,7 @@ int main(int argc, char **argv) {
   CHECK(bt_params_default(&p) == BT_OK);
   CHECK(p.max_order == 4 && p.tiles_x == 1 && p.tiles_y == 1 && p.precision == BT_PREC_MIXED);
   CHECK(p.t_eps_m == 1e-3f && p.watchdog_ms == 2000 && p.chunk_beams == 0 && p.queue_depth == 0);
+  CHECK(p.leaf_size == 0 && p.beams_per_warp == 0 && p.fault_test == 0);
   for (int b = 0; b < BT_MAX_BANDS; b++) CHECK(p.air_atten_db_per_m[b] == 0.0f);
   CHECK(bt_params_default(NULL) == BT_E_INVALID);
 

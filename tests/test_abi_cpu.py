@@ -52,7 +52,7 @@ def test_params_default_is_host_only(libpath):
 def test_struct_sizes_match_header(libpath):
     # the ctypes mirrors must have the C layout: 4-byte fields only in params
     from paper_1912_03998_gb300 import btrace
-    assert C.sizeof(btrace.bt_trace_params) == 4 * (1 + 8 + 1 + 1 + 2 + 1 + 1 + 1 + 1 + 1 + 1)
+    assert C.sizeof(btrace.bt_trace_params) == 4 * (1 + 8 + 1 + 1 + 2 + 1 + 1 + 1 + 1 + 1 + 1 + 3)
     assert C.sizeof(btrace.bt_stats) == 8 * (14 + 3)
 
 
