@@ -210,6 +210,12 @@ def flush_l2(buf):
 
 
 # ------------------------------------------------------------------ our arm
+def trial_table(table):
+    """An autotuner's trials as rows of knob values and ms, fastest first."""
+    names = sorted({k for knobs, _ in table for k in knobs})
+    return {"knobs": names, "rows": [[knobs.get(n) for n in names] + [round(ms, 3)] for knobs, ms in table]}
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_1912_03998_gb300 import btrace
@@ -230,6 +236,24 @@ def run_ours(args, rank, world):
     params.precision = {"mixed": btrace.BT_PREC_MIXED, "fp32": btrace.BT_PREC_FP32,
                         "fp64": btrace.BT_PREC_FP64}[args.precision]
     params.leaf_size, params.beams_per_warp, params.queue_depth = args.leaf_size, args.beams_per_warp, args.queue_depth
+    tuned = None
+    if args.autotune:
+        # knobs picked by measurement on this workload (cached per GPU model)
+        from paper_1912_03998_gb300 import autotune
+        tr = btrace.Tracer(ctx=ctx)
+        sid = tr.load(w)
+        key, gpu = autotune.workload_key(w, params), torch.cuda.get_device_name(dev)
+        cache = autotune.TuneCache(args.tune_cache) if args.tune_cache else None
+        knobs, table = (cache.get(key, gpu) if cache else None), None
+        if knobs is None:
+            knobs, table = autotune.tune_trace(tr, sid, params)
+            if cache:
+                cache.put(key, gpu, knobs, table)
+        btrace.bt_unload_scene(ctx, sid)
+        autotune.apply(params, knobs)
+        tuned = {"chosen": knobs, "cached": table is None, "tuned_on": "the whole workload"}
+        if table is not None:
+            tuned["trials_ms"] = trial_table(table)
     l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(inp, level_out):
@@ -310,7 +334,7 @@ def run_ours(args, rank, world):
                stats=stats[-1], tk=tk, sk=sk, tl=tl, alg_bytes=alg_bytes, kernel=kernel,
                bytes_per_launch=bytes_per_launch, achieved=achieved, peak=peak,
                peak_kind=peak_kind, traffic=traffic, clocks=clk.summary(), work=cst, w=w,
-               tiles=tiles, untiled=untiled)
+               tiles=tiles, untiled=untiled, autotune=tuned)
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         h_in = {k: pin(v.cpu().numpy()) for k, v in d_in.items()}
@@ -350,10 +374,10 @@ def run_batch(args):
             if cache:
                 cache.put(key, gpu, knobs, table)
         for p in params:
-            p.blocks_per_sm, p.chunk_beams = knobs["blocks_per_sm"], knobs["chunk_beams"]
-        tuned = {"chosen": knobs, "cached": table is None}
+            autotune.apply(p, knobs)
+        tuned = {"chosen": knobs, "cached": table is None, "tuned_on": "the first 16 cities"}
         if table is not None:
-            tuned["trials_ms"] = [[k["blocks_per_sm"], k["chunk_beams"], round(ms, 3)] for k, ms in table]
+            tuned["trials_ms"] = trial_table(table)
     l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def span(fn):
@@ -604,6 +628,8 @@ def main():
         line["e2e"] = res["e2e"]
     if res["untiled"]:
         line["untiled"] = res["untiled"]
+    if res.get("autotune"):
+        line["autotune"] = res["autotune"]
     if not args.no_serve and world == 1 and args.workload == "district":
         # the metric's second half: served p50/p99 latency on a short stream
         import torch

@@ -1,49 +1,116 @@
-"""Autotuner for the trace's launch knobs, by measurement.
+"""Autotuner for the trace's knobs, by measurement.
 
-Knobs searched:
-  blocks_per_sm  resident 128-thread blocks per SM of the persistent trace
-                 kernels (more warps hide more latency; fewer leave more
-                 registers and L1 to each), 0 = as many as fit
-  chunk_beams    lineages per persistent launch (fewer, larger launches have
-                 fewer tails; smaller ones keep the segment buffer small)
-  queue_depth    hand-off queue slots per sub-domain (split traces only)
+Knobs searched (each changes only the speed of a trace, never its result):
+  queue_depth     hand-off queue slots per sub-domain, also the most lineages
+                  in flight at once (split traces only); 0 = automatic
+  leaf_size       most triangles per BVH leaf (1..4): fewer node visits
+                  against more triangle tests per leaf
+  beams_per_warp  beam lineages a warp of the persistent trace reserves at a
+                  time (0 = as many as its lanes need): fewer draws on the
+                  launch's lineage counter against a coarser launch tail
+  blocks_per_sm   resident 128-thread blocks per SM of the persistent trace
+                  kernels, 0 = as many as fit
+  chunk_beams     lineages per persistent launch (batches)
 
-The tracer itself fixes one lineage per lane (32 beams per warp) and one
-triangle per BVH leaf (the LBVH's leaves), so those are not searched.  Every
-candidate runs the real workload (or a caller-chosen part of it) through the
-C ABI and is timed on the device (bt_stats.trace_ms); the fastest wins.
-`TuneCache` keeps the winners on disk per (workload, GPU model), so that a
-workload is measured once per GPU model (`tuned`).
+The search is coordinate descent from the library's defaults: one knob at a
+time over its candidates, the others held at the best so far, repeated until
+a pass changes nothing (at most `passes` passes).  Every candidate runs the
+real workload (or a caller-chosen part of it) through the C ABI and is timed
+on the device (bt_stats.trace_ms, the best of `repeats` runs after one
+warm-up); the fastest wins.  `TuneCache` keeps the winners on disk per
+(workload, GPU model), so that a workload is measured once per GPU model
+(`tuned`).
 """
 from __future__ import annotations
 
-import itertools
-
 from . import btrace
+
+TRACE_SPACE = {
+    "queue_depth": (0, 1 << 16, 1 << 17),
+    "leaf_size": (1, 2, 4),
+    "beams_per_warp": (0, 64, 256),
+    "blocks_per_sm": (0, 5),
+}
+DEFAULTS = {"queue_depth": 0, "leaf_size": 1, "beams_per_warp": 0, "blocks_per_sm": 0, "chunk_beams": 0}
 
 
 def _chunk_candidates(max_order: int):
     # 0: the library's default, segment records in a quarter of the free
     # device memory (1..32 GiB) per launch
     per = max_order + 1
-    return [0, (1 << 22) // per, (1 << 24) // per]
+    return (0, (1 << 22) // per, (1 << 24) // per)
 
 
-def tune_batch(tracer, scene_ids, params, blocks=(0, 4, 5), chunks=None, repeats=2):
-    """Tune blocks_per_sm and chunk_beams for a batch of loaded scenes with
-    per-scene `params` (bt_trace_params).  Returns (best knobs dict, list of
-    (knobs, ms) for every candidate)."""
+def coordinate_search(measure, space: dict, start: dict | None = None, passes: int = 2):
+    """Minimise measure(knobs) -> ms over the product of `space`'s candidate
+    lists by coordinate descent from `start` (default: each knob's first
+    candidate).  Returns (best knobs, [(knobs, ms), ...] for every distinct
+    setting measured, fastest first)."""
+    best = {k: (start or {}).get(k, v[0]) for k, v in space.items()}
+    seen = {}
+
+    def run(knobs):
+        key = tuple(sorted(knobs.items()))
+        if key not in seen:
+            seen[key] = float(measure(dict(knobs)))
+        return seen[key]
+
+    best_ms = run(best)
+    for _ in range(passes):
+        changed = False
+        for name, cands in space.items():
+            for v in cands:
+                if v == best[name]:
+                    continue
+                trial = dict(best, **{name: v})
+                ms = run(trial)
+                if ms < best_ms:
+                    best, best_ms, changed = trial, ms, True
+        if not changed:
+            break
+    table = sorted(((dict(k), ms) for k, ms in seen.items()), key=lambda r: r[1])
+    return best, table
+
+
+def _with(params, knobs):
+    q = btrace.bt_trace_params.from_buffer_copy(params)
+    for k, v in knobs.items():
+        setattr(q, k, int(v))
+    return q
+
+
+def tune_trace(tracer, scene_id, params, space=None, repeats=2, passes=2):
+    """Tune one scene's trace: queue depth (split traces), leaf size, beams
+    per warp and blocks per SM.  Returns (best knobs dict, trial table)."""
+    space = dict(space or TRACE_SPACE)
+    if params.tiles_x * params.tiles_y <= 1:
+        space.pop("queue_depth", None)
+
+    def measure(knobs):
+        q = _with(params, knobs)
+        btrace.bt_trace(tracer.ctx, scene_id, q)  # warm-up (and any leaf re-collapse)
+        best = None
+        for _ in range(repeats):
+            btrace.bt_trace(tracer.ctx, scene_id, q)
+            ms = btrace.bt_read_levels(tracer.ctx, scene_id)["trace_ms"]
+            best = ms if best is None else min(best, ms)
+        return best
+
+    return coordinate_search(measure, space, DEFAULTS, passes)
+
+
+def tune_batch(tracer, scene_ids, params, space=None, repeats=2, passes=2):
+    """Tune a batch of loaded scenes with per-scene `params`: leaf size, beams
+    per warp, blocks per SM and lineages per launch (a batch traces its scenes
+    unsplit, so there is no queue).  Returns (best knobs dict, trial table)."""
     kmax = max(p.max_order for p in params)
-    chunks = chunks if chunks is not None else _chunk_candidates(kmax)
-    results = []
-    for bps, chunk in itertools.product(blocks, chunks):
-        ps = []
-        for p in params:
-            q = btrace.bt_trace_params.from_buffer_copy(p)
-            q.blocks_per_sm = bps
-            q.chunk_beams = chunk
-            ps.append(q)
-        b = btrace.bt_batch_create(tracer.ctx, scene_ids, ps)
+    space = dict(space or {"leaf_size": TRACE_SPACE["leaf_size"],
+                           "beams_per_warp": TRACE_SPACE["beams_per_warp"],
+                           "blocks_per_sm": (0, 4, 5),
+                           "chunk_beams": _chunk_candidates(kmax)})
+
+    def measure(knobs):
+        b = btrace.bt_batch_create(tracer.ctx, scene_ids, [_with(p, knobs) for p in params])
         try:
             btrace.bt_batch_run(tracer.ctx, b)  # captures the graph
             best = None
@@ -53,28 +120,16 @@ def tune_batch(tracer, scene_ids, params, blocks=(0, 4, 5), chunks=None, repeats
                 best = ms if best is None else min(best, ms)
         finally:
             btrace.bt_batch_destroy(b)
-        results.append((dict(blocks_per_sm=bps, chunk_beams=chunk), best))
-    results.sort(key=lambda r: r[1])
-    return results[0][0], results
+        return best
+
+    return coordinate_search(measure, space, DEFAULTS, passes)
 
 
-def tune_trace(tracer, scene_id, params, blocks=(0, 4, 5), depths=(0, 1 << 16, 1 << 18), repeats=2):
-    """Tune blocks_per_sm and, for a split trace, queue_depth for one scene.
-    Returns (best knobs dict, list of (knobs, ms))."""
-    split = params.tiles_x * params.tiles_y > 1
-    results = []
-    for bps, depth in itertools.product(blocks, depths if split else (0,)):
-        q = btrace.bt_trace_params.from_buffer_copy(params)
-        q.blocks_per_sm = bps
-        q.queue_depth = depth
-        best = None
-        for _ in range(repeats + 1):
-            btrace.bt_trace(tracer.ctx, scene_id, q)
-            ms = btrace.bt_read_levels(tracer.ctx, scene_id)["trace_ms"]
-            best = ms if best is None else min(best, ms)
-        results.append((dict(blocks_per_sm=bps, queue_depth=depth), best))
-    results.sort(key=lambda r: r[1])
-    return results[0][0], results
+def apply(params, knobs):
+    """Set the tuned knobs on bt_trace_params `params` in place."""
+    for k, v in knobs.items():
+        setattr(params, k, int(v))
+    return params
 
 
 # ------------------------------------------------------------------ cache

@@ -345,13 +345,16 @@ class Tracer:
     """Convenience wrapper: one context, scenes loaded from synth.Workload-like
     objects, results returned as numpy arrays."""
 
-    def __init__(self, device: int = 0, stream=None):
-        self.ctx = bt_create(device, stream)
+    def __init__(self, device: int = 0, stream=None, ctx=None):
+        """A new context on `device`, or a view of the caller's context `ctx`
+        (which close() then leaves alone)."""
+        self._own = ctx is None
+        self.ctx = bt_create(device, stream) if ctx is None else ctx
 
     def close(self):
-        if self.ctx:
+        if self.ctx and self._own:
             bt_destroy(self.ctx)
-            self.ctx = None
+        self.ctx = None
 
     def __enter__(self):
         return self

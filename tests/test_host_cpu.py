@@ -202,3 +202,34 @@ def test_server_traces_every_lineage_once_in_order(monkeypatch):
         rs = lib.ranges[sid]
         assert rs[0][0] == 0 and rs[-1][1] == len(q.src) * 20 * 4 ** q.level
         assert all(a[1] == b[0] for a, b in zip(rs, rs[1:]))  # consecutive, no gap or overlap
+
+
+def test_coordinate_search_finds_the_separable_minimum_with_few_trials():
+    """The autotuner's search on a made-up cost with a known best setting: it
+    must reach it, report every measured setting once, fastest first, and
+    measure far fewer settings than the whole product."""
+    from paper_1912_03998_gb300 import autotune
+    space = {"queue_depth": (0, 1 << 16, 1 << 17), "leaf_size": (1, 2, 4), "beams_per_warp": (0, 64, 256),
+             "blocks_per_sm": (0, 5)}
+    best = {"queue_depth": 1 << 16, "leaf_size": 2, "beams_per_warp": 0, "blocks_per_sm": 5}
+    calls = []
+
+    def cost(k):
+        calls.append(dict(k))
+        return 10.0 + sum((space[n].index(k[n]) - space[n].index(best[n])) ** 2 for n in space)
+
+    knobs, table = autotune.coordinate_search(cost, space, autotune.DEFAULTS)
+    assert knobs == best
+    assert table[0][0] == best and table[0][1] == 10.0
+    assert [ms for _, ms in table] == sorted(ms for _, ms in table)
+    assert len(table) == len(calls) == len({tuple(sorted(c.items())) for c in calls})
+    assert len(calls) < 3 * 3 * 3 * 2
+
+
+def test_coordinate_search_keeps_defaults_when_nothing_is_faster():
+    from paper_1912_03998_gb300 import autotune
+    space = {"leaf_size": (1, 2, 4), "beams_per_warp": (0, 64, 256)}
+    knobs, table = autotune.coordinate_search(lambda k: 5.0 + k["leaf_size"] + k["beams_per_warp"] / 64,
+                                              space, autotune.DEFAULTS)
+    assert knobs == {"leaf_size": 1, "beams_per_warp": 0}
+    assert len(table) == 5  # the defaults and the four single-knob changes, one pass
