@@ -171,6 +171,8 @@ def kernel_hash():
     h = hashlib.sha256()
     for f in ("trace.cu", "bt_internal.cuh"):
         src = open(os.path.join(ROOT, "paper_1912_03998_gb300", "csrc", f)).read()
+        # the header's host launcher declarations do not change device code
+        src = src.split("// ------------------------------------------------------------ host launchers")[0]
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
         h.update(" ".join(src.split()).encode())
@@ -189,20 +191,35 @@ def trace_kernel_name(tiles):
     return "k_trace" if tuple(tiles) == (1, 1) else "k_trace_tiled"
 
 
-def ncu_traffic(kernel, args, tiles):
-    """DRAM bytes per launch of the traversal kernel from the committed ncu
-    summary, only if it was taken on the current kernel source and on this
-    workload (the full district, MIXED, split 4x4 or unsplit)."""
-    if (args.workload != "district" or args.sources is not None or args.precision != "mixed"
+def ncu_counters(kernel, args, tiles):
+    """DRAM and L2 bytes of one launch of `kernel` as a function of its units
+    of work, from the committed ncu summary of two small cases of the same
+    workload (the district's geometry with 16 and 64 of its sources, MIXED,
+    split 4x4 or unsplit), only if it was taken on the current kernel source:
+    {"dram": (a, b), "l2": (a, b), "unit": "segment" or "emitted segment"},
+    bytes = a + b * units, or None.  The committed summaries set a = 0 and b =
+    the bytes per unit of the larger case: traffic grows in proportion to the
+    segments a launch traces (for the scatter, emits)."""
+    if (args.workload != "district" or args.precision != "mixed"
             or tuple(tiles) not in ((4, 4), (1, 1))):
         return None
-    p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
+    split = "4x4" if tuple(tiles) == (4, 4) else "1x1"
+    p = os.path.join(ROOT, "profiles", f"{kernel}_district_{split}_counters.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("kernel_hash") != kernel_hash():
+    if kernel != "k_scatter" and d.get("kernel_hash") != kernel_hash():
         return None
-    return d.get("dram_bytes_per_launch_scaled")
+    return {"dram": tuple(d["fit"]["dram"]), "l2": tuple(d["fit"]["lts"]), "unit": d["unit"],
+            "file": os.path.relpath(p, ROOT)}
+
+
+def l2_peak(ctx):
+    """Measured L2 read bandwidth of this GPU, GB/s: the library's probe reads
+    a 48 MB buffer (resident in the 126 MB L2) 200 times over in one kernel
+    with L2-only loads; the best of a few grid sizes and 3 runs each."""
+    from paper_1912_03998_gb300 import btrace
+    return max(btrace.bt_l2_bandwidth(ctx, 48 << 20, 200, b) for b in (2, 4, 8) for _ in range(3))
 
 
 def flush_l2(buf):
@@ -323,18 +340,29 @@ def run_ours(args, rank, world):
         alg_bytes = 192.0 * last["emitted"] + 16.0 * last["candidates"] + 136.0 * last["contributions"]
         bytes_per_launch = alg_bytes / max(1, last["scatter_launches"])
         achieved = bytes_per_launch / (sk / max(1, sl) * 1e-3) / 1e9
-        traffic = None
+        counters = ncu_counters(kernel, args, tiles)
+        units, kms = float(stats[-1]["emitted"]) / max(1, sl // args.steps), sk / max(1, sl)
     else:
         kernel = trace_kernel_name(tiles)
         alg_bytes = 64.0 * cst["nodes_visited"] + 48.0 * cst["tris_tested"]
         bytes_per_launch = alg_bytes / max(1, cst["trace_launches"])
         achieved = bytes_per_launch / (tk / max(1, tl) * 1e-3) / 1e9
-        traffic = ncu_traffic(kernel, args, tiles)
+        counters = ncu_counters(kernel, args, tiles)
+        units, kms = float(stats[-1]["segments"]) / max(1, tl // args.steps), tk / max(1, tl)
+    traffic, l2 = None, None
+    if counters:
+        traffic = counters["dram"][0] + counters["dram"][1] * units
+        l2_bytes = counters["l2"][0] + counters["l2"][1] * units
+        l2_pk = l2_peak(ctx)
+        l2 = {"achieved": l2_bytes / (kms * 1e-3) / 1e9, "peak": l2_pk, "unit": "GB/s",
+              "frac": l2_bytes / (kms * 1e-3) / 1e9 / l2_pk, "bytes_per_launch": l2_bytes,
+              "peak_kind": "measured in this run: L2-only reads of a 48 MB resident buffer (bt_l2_bandwidth)",
+              "counters": counters["file"] + f" (ncu lts__t_bytes of two small cases, linear in the {counters['unit']}s of a launch)"}
     res = dict(segs=segs, contrib=contrib, total_ms=total_ms, ms=ms, launches=launches,
                stats=stats[-1], tk=tk, sk=sk, tl=tl, alg_bytes=alg_bytes, kernel=kernel,
                bytes_per_launch=bytes_per_launch, achieved=achieved, peak=peak,
                peak_kind=peak_kind, traffic=traffic, clocks=clk.summary(), work=cst, w=w,
-               tiles=tiles, untiled=untiled, autotune=tuned)
+               tiles=tiles, untiled=untiled, autotune=tuned, l2=l2)
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         h_in = {k: pin(v.cpu().numpy()) for k, v in d_in.items()}
@@ -619,6 +647,7 @@ def main():
                          "kernel_ms_per_step": (res["sk"] if res["kernel"] == "k_scatter" else res["tk"]) / args.steps,
                          "trace_kernel_ms_per_step": res["tk"] / args.steps,
                          "scatter_kernel_ms_per_step": res["sk"] / args.steps,
+                         "l2": res["l2"],
                          "nodes_per_segment": res["work"]["nodes_visited"] / max(1, res["work"]["segments"]),
                          "tris_per_segment": res["work"]["tris_tested"] / max(1, res["work"]["segments"])},
             "stats": {k: res["stats"][k] for k in ("segments", "hits", "escapes", "emitted",

@@ -363,6 +363,16 @@ const char *bt_last_error(const bt_ctx *ctx);
  * (all contexts).  Lets a caller count the kernels inside a timed region. */
 int64_t bt_kernel_launches(void);
 
+/* Measured L2 read bandwidth of the context's GPU, GB/s (the paper has no
+ * counterpart: a measurement aid).  Reads a `bytes`-byte device buffer
+ * (16 MiB..96 MiB, small enough to stay resident in L2) `repeats` times
+ * (1..10000) in one kernel, with loads cached in L2 only, on a grid of
+ * `blocks_per_sm` blocks of 256 threads per SM (1..8), and returns the bytes
+ * read over the kernel's CUDA-event time.  The traversal's node, triangle and
+ * plane arrays stay in L2, so this is the roof its L2 traffic is reported
+ * against.  Allocates the buffer from the context's pool; synchronous. */
+int bt_l2_bandwidth(bt_ctx *ctx, int64_t bytes, int32_t repeats, int32_t blocks_per_sm, double *gbs_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,7 +63,7 @@ EXPECTED_SYMBOLS = ("bt_params_default", "bt_create", "bt_destroy", "bt_load_sce
                     "bt_trace_noalloc", "bt_set_result", "bt_batch_create", "bt_batch_run",
                     "bt_batch_stats", "bt_batch_destroy", "bt_scene_share", "bt_trace_ranges",
                     "bt_ranges_stats", "bt_set_directivity", "bt_beam_axes", "bt_submit", "bt_poll",
-                    "bt_wait")
+                    "bt_wait", "bt_l2_bandwidth")
 
 
 def lib_path() -> str:
@@ -106,6 +106,7 @@ def lib():
             L.bt_scene_share.argtypes = [p, i32, C.POINTER(C.c_int32)]
             L.bt_trace_ranges.argtypes = [p, i32, p, p, p, C.POINTER(bt_trace_params), i32]
             L.bt_ranges_stats.argtypes = [p, C.POINTER(bt_stats)]
+            L.bt_l2_bandwidth.argtypes = [p, i64, i32, i32, C.POINTER(C.c_double)]
             L.bt_kernel_launches.argtypes = []
             L.bt_kernel_launches.restype = C.c_int64
             for name in EXPECTED_SYMBOLS:
@@ -156,6 +157,13 @@ def bt_destroy(ctx):
 
 def bt_kernel_launches() -> int:
     return int(lib().bt_kernel_launches())
+
+
+def bt_l2_bandwidth(ctx, n_bytes: int = 48 << 20, repeats: int = 200, blocks_per_sm: int = 4) -> float:
+    """Measured L2 read bandwidth of the context's GPU, GB/s."""
+    g = C.c_double(0.0)
+    _check(lib().bt_l2_bandwidth(ctx, int(n_bytes), int(repeats), int(blocks_per_sm), C.byref(g)), ctx)
+    return g.value
 
 
 def bt_last_error(ctx) -> str:

@@ -510,6 +510,43 @@ BT_API const char *bt_last_error(const bt_ctx *c) { return c ? c->err : "null co
 
 BT_API int64_t bt_kernel_launches(void) { return (int64_t)bt::g_launches.load(); }
 
+BT_API int bt_l2_bandwidth(bt_ctx *c, int64_t bytes, int32_t repeats, int32_t blocks_per_sm, double *gbs_out) {
+  BT_RANGE();
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  if (!gbs_out) return fail(c, BT_E_INVALID, "gbs_out is NULL");
+  if (bytes < ((int64_t)16 << 20) || bytes > ((int64_t)96 << 20) || bytes % 16 != 0)
+    return fail(c, BT_E_INVALID, "bytes must be a multiple of 16 in 16..96 MiB");
+  if (repeats < 1 || repeats > 10000) return fail(c, BT_E_INVALID, "repeats must be in 1..10000");
+  if (blocks_per_sm < 1 || blocks_per_sm > 8) return fail(c, BT_E_INVALID, "blocks_per_sm must be in 1..8");
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  const int blocks = c->n_sm * blocks_per_sm;
+  TRY(ensure(c, c->stage_a, (size_t)bytes));
+  TRY(ensure(c, c->stage_b, sizeof(float) * 256 * (size_t)blocks));
+  CK(cudaMemsetAsync(c->stage_a.p, 0, (size_t)bytes, st));
+  const float4 *buf = (const float4 *)c->stage_a.p;
+  float *sink = (float *)c->stage_b.p;
+  CK(bt::launch_l2_read(st, buf, bytes / 16, 2, sink, blocks));  // warm: the buffer into L2
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  cudaError_t e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) e = bt::launch_l2_read(st, buf, bytes / 16, repeats, sink, blocks);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, BT_E_CUDA, "L2 probe: %s", cudaGetErrorString(e));
+  }
+  *gbs_out = (double)bytes * repeats / (ms * 1e-3) / 1e9;
+  return BT_OK;
+}
+
 BT_API int bt_load_scene(bt_ctx *c, const float *verts, int64_t n_verts, const int32_t *tris,
                          int64_t n_tris, const uint8_t *tri_material, const float *refl,
                          int32_t n_materials, int32_t n_bands, int32_t *scene_id_out) {
