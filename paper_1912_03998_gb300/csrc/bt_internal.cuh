@@ -337,16 +337,39 @@ __device__ __forceinline__ bool accept_hit(const Ray &r, float t) {
   return t > r.t_eps && (r.dns == 0.0f || t * r.dns > r.t_eps);
 }
 
-// Robust slab test (Ize 2013: the far distance is grown by 1 + 2*gamma(3)).
-__device__ __forceinline__ bool slab(const Ray &r, float lox, float hix, float loy, float hiy,
+// Three-input minimum and maximum (one instruction each on sm_100 and later).
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// Slab test with the ray origin pre-scaled: (lo - o) * inv is formed as
+// fma(lo, inv, -o * inv), one instruction per bound; oi = o * inv.  The far
+// distance is grown by 1 + 2*gamma(3) as in the robust test of Ize (2013), and
+// the boxes themselves are grown at build time (1e-6 relative + 0.1 mm), which
+// covers the rounding of o * inv (at most |o| * 2^-24 along the ray).
+__device__ __forceinline__ bool slab(const Ray &r, float3 oi, float lox, float hix, float loy, float hiy,
                                      float loz, float hiz, float tmax, float &tnear) {
-  float tx0 = (lox - r.o.x) * r.inv.x, tx1 = (hix - r.o.x) * r.inv.x;
-  float ty0 = (loy - r.o.y) * r.inv.y, ty1 = (hiy - r.o.y) * r.inv.y;
-  float tz0 = (loz - r.o.z) * r.inv.z, tz1 = (hiz - r.o.z) * r.inv.z;
-  float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
-  float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1)) * 1.0000004f;
+  float tx0 = fmaf(lox, r.inv.x, -oi.x), tx1 = fmaf(hix, r.inv.x, -oi.x);
+  float ty0 = fmaf(loy, r.inv.y, -oi.y), ty1 = fmaf(hiy, r.inv.y, -oi.y);
+  float tz0 = fmaf(loz, r.inv.z, -oi.z), tz1 = fmaf(hiz, r.inv.z, -oi.z);
+  float tn = fmax3(fminf(tx0, tx1), fminf(ty0, ty1), fmaxf(fminf(tz0, tz1), 0.0f));
+  float tf = fmin3(fmaxf(tx0, tx1), fmaxf(ty0, ty1), fmaxf(tz0, tz1)) * 1.0000004f;
   tnear = tn;
   return tn <= fminf(tf, tmax);
+}
+__device__ __forceinline__ float3 origin_scaled(const Ray &r) {
+  return make_float3(r.o.x * r.inv.x, r.o.y * r.inv.y, r.o.z * r.inv.z);
+}
+__device__ __forceinline__ bool slab(const Ray &r, float lox, float hix, float loy, float hiy, float loz, float hiz,
+                                     float tmax, float &tnear) {
+  return slab(r, origin_scaled(r), lox, hix, loy, hiy, loz, hiz, tmax, tnear);
 }
 
 // ------------------------------------------------------------ double-float

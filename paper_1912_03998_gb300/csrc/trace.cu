@@ -346,7 +346,7 @@ struct HitSearch {
     } else {
       // a well-formed BVH is visited at most once per node; the bound only
       // guarantees termination should the structure ever be malformed
-      if (++visits > n_tri + 64) {
+      if (++visits > (int)n_tri + 64) {
         atomicExch(err, BT_E_TIMEOUT);
         return false;
       }
@@ -357,8 +357,9 @@ struct HitSearch {
       // in MIXED and FP64 mode near ties must still be visited
       float tmax = fminf(kP != kPF32 ? best.t + (1e-5f * fabsf(best.t) + 1e-4f) : best.t, tlim);
       float tl, tr;
-      bool hl = slab(r, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, tmax, tl);
-      bool hr = slab(r, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, tmax, tr);
+      const float3 oi = origin_scaled(r);
+      bool hl = slab(r, oi, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, tmax, tl);
+      bool hr = slab(r, oi, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, tmax, tr);
       if (hl && ch.x < 0) { c0 = ~ch.x; nc = 1; hl = false; }
       if (hr && ch.y < 0) { if (nc) c1 = ~ch.y; else c0 = ~ch.y; nc++; hr = false; }
       if (hl && hr) {
