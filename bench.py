@@ -42,7 +42,7 @@ UNIT = "segments/s"
 # The arithmetic type each precision variant computes in: "mixed" is float32
 # traversal with a float-pair (double-float) image-source chain and float64
 # energy accumulation.
-DTYPE = {"fp32": "f32", "mixed": "mixed", "fp64": "f64"}
+DTYPE = {"fp32": "f32", "mixed": "mixed", "fp64": "f64", "mixed64": "mixed64"}
 
 
 def parse():
@@ -80,7 +80,7 @@ def parse():
     ap.add_argument("--beams-per-warp", type=int, default=0,
                     help="lineages a warp reserves at a time (0 = library default)")
     ap.add_argument("--queue-depth", type=int, default=0, help="hand-off queue slots per sub-domain (0 = automatic)")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"],
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64", "mixed64"],
                     help="mixed: float-pair image-source chain (the parity-checked default)")
     return ap.parse_args()
 
@@ -251,7 +251,7 @@ def run_ours(args, rank, world):
     params.max_order = w.max_order
     params.tiles_x, params.tiles_y = tiles
     params.precision = {"mixed": btrace.BT_PREC_MIXED, "fp32": btrace.BT_PREC_FP32,
-                        "fp64": btrace.BT_PREC_FP64}[args.precision]
+                        "fp64": btrace.BT_PREC_FP64, "mixed64": btrace.BT_PREC_MIXED64}[args.precision]
     params.leaf_size, params.beams_per_warp, params.queue_depth = args.leaf_size, args.beams_per_warp, args.queue_depth
     tuned = None
     if args.autotune:
@@ -389,7 +389,7 @@ def run_batch(args):
     ws = synth.batch_cities(seed=4, n=64)
     stream = torch.cuda.Stream(dev)
     tr = btrace.Tracer(0, stream.cuda_stream)
-    prec = {"mixed": btrace.BT_PREC_MIXED, "fp32": btrace.BT_PREC_FP32, "fp64": btrace.BT_PREC_FP64}[args.precision]
+    prec = {"mixed": btrace.BT_PREC_MIXED, "fp32": btrace.BT_PREC_FP32, "fp64": btrace.BT_PREC_FP64, "mixed64": btrace.BT_PREC_MIXED64}[args.precision]
     sids = [tr.load(w) for w in ws]
     params = [tr.params(w.max_order, precision=prec) for w in ws]
     tuned = None
@@ -494,7 +494,7 @@ def run_serve(args):
     import torch
     from paper_1912_03998_gb300 import btrace, serve, synth
     torch.cuda.set_device(0)
-    prec = {"mixed": btrace.BT_PREC_MIXED, "fp32": btrace.BT_PREC_FP32, "fp64": btrace.BT_PREC_FP64}[args.precision]
+    prec = {"mixed": btrace.BT_PREC_MIXED, "fp32": btrace.BT_PREC_FP32, "fp64": btrace.BT_PREC_FP64, "mixed64": btrace.BT_PREC_MIXED64}[args.precision]
     cities = synth.serving_cities(seed=5, n=8)
     tr = btrace.Tracer(0)
     rows = []
@@ -628,6 +628,10 @@ def main():
                              ("FP64 image-source chain, triangle tests, microphone tests and "
                               "contributions; FP32 BVH boxes and band powers; FP64 accumulation")
                              if args.precision == "fp64" else
+                             ("MIXED64: FP32 watertight traversal with FP64 settling of ambiguous hits "
+                              "and near ties, FP64 image-source chain, FP32 microphone tests with a "
+                              "float-pair re-test, FP64 energy accumulation")
+                             if args.precision == "mixed64" else
                              "FP32 chain, traversal and microphone tests, FP64 energy accumulation",
                 "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -665,7 +669,7 @@ def main():
         from paper_1912_03998_gb300 import btrace, synth
         torch.cuda.set_device(0)
         prec = {"mixed": btrace.BT_PREC_MIXED, "fp32": btrace.BT_PREC_FP32,
-                "fp64": btrace.BT_PREC_FP64}[args.precision]
+                "fp64": btrace.BT_PREC_FP64, "mixed64": btrace.BT_PREC_MIXED64}[args.precision]
         tr = btrace.Tracer(0)
         try:
             line["serving"] = serve_once(tr, synth.serving_cities(seed=5, n=8), 200.0, 100, 100, prec,

@@ -66,10 +66,15 @@ extern "C" {
  *   grown to be conservative); every microphone test and contribution in
  *   float64 (the apex exact, cone normals to about 48 bits); band powers
  *   W_b prod(r_b) in float32; float64 accumulation.  Slower: GB300 issues
- *   float64 at a small fraction of the float32 rate. */
+ *   float64 at a small fraction of the float32 rate.
+ * BT_PREC_MIXED64: float32 traversal and hit tests as in MIXED (ambiguous
+ *   tests and near ties settled in float64), the image-source chain in
+ *   float64 as in FP64, microphone tests as in MIXED, float64 accumulation:
+ *   float64 only where the chain's stability needs it. */
 #define BT_PREC_FP32 0
 #define BT_PREC_MIXED 1
 #define BT_PREC_FP64 2
+#define BT_PREC_MIXED64 3
 
 typedef struct bt_ctx bt_ctx;
 
@@ -292,6 +297,19 @@ int bt_cast_rays(bt_ctx *ctx, int32_t scene_id, const float *origins, const floa
 #define BT_NOALLOC_MAX_LEVEL 6
 int bt_trace_noalloc(bt_ctx *ctx, int32_t scene_id, const bt_trace_params *p, double *level_db,
                      int32_t *path_count);
+
+/* Hit log of a scene's traces (the paper has no counterpart: a measurement
+ * aid for precision studies, which hit decisions differ between variants).
+ * Registers the caller's DEVICE array hits[n] (int32, device memory of the
+ * context's GPU); every later bt_trace / bt_submit of the scene writes, per
+ * segment, hits[lineage * (max_order + 1) + order] = the input index of the
+ * triangle the segment's axis ray hit, or -1 if it escaped; entries of orders
+ * a lineage does not reach are left as they were.  Lineage = source *
+ * 20 * 4^L + beam, beams in the order of bt_beam_axes.  A trace whose
+ * lineages x (max_order + 1) exceed n fails with BT_E_INVALID.  Batches,
+ * range traces and bt_trace_noalloc do not write it.  hits = NULL clears the
+ * log.  The array must outlive the traces that write it. */
+int bt_set_hit_log(bt_ctx *ctx, int32_t scene_id, int32_t *hits, int64_t n);
 
 /* Install a trace result computed elsewhere into a scene, replacing its last
  * result: the sum of the partial results of traces of disjoint subsets of the

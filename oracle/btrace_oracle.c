@@ -796,6 +796,7 @@ typedef struct {
   int tid, n_threads;
   accum acc;
   double *stats;
+  int32_t *hit_log;  /* [n_src][n_beams][K+1] or NULL: hit triangle per segment, -1 escape */
 } job;
 
 /* Section 2 hybrid method, one beam from apex s along face i, orders 0..K. */
@@ -830,6 +831,7 @@ static void trace_beam(job *J, int64_t si, int64_t bi) {
     closest_hit(s, &r, p->hit_mode, &th, &hid, &ho);
     J->stats[4] += ho;
     J->stats[0] += 1;
+    if (J->hit_log) J->hit_log[(si * J->n_beams + bi) * (p->max_order + 1) + k] = hid;
     if (hid >= 0) {
       J->stats[2] += 1;
       g.has_end = 1;
@@ -878,7 +880,10 @@ static void *run_job(void *arg) {
  * Threads split the sources statically (source s goes to thread s mod T) and
  * their partial sums are added in thread order.  An optional path log
  * (single thread only) records each contribution's microphone, source, order,
- * distance and apex.  Returns 0, or a negative value on bad input.
+ * distance and apex.  An optional hit log [n_src][n_beams][max_order + 1]
+ * receives the triangle each segment's axis ray hit (-1: it escaped); entries
+ * of orders a beam did not reach are left as they were.  Returns 0, or a
+ * negative value on bad input.
  */
 int or_trace_dir(const void *scene, const float *src, const float *power, int64_t n_src, int level,
                  const float *dir_gain, int32_t n_patterns, const int32_t *dir_of,
@@ -886,7 +891,7 @@ int or_trace_dir(const void *scene, const float *src, const float *power, int64_
                  double energy_threshold, double t_eps, int hit_mode, int mic_mode, int n_threads,
                  double *I, int32_t *cnt, double *stats, int64_t log_cap, int32_t *log_mic,
                  int32_t *log_src, int32_t *log_order, double *log_d, double *log_apex,
-                 int64_t *log_n) {
+                 int64_t *log_n, int32_t *hit_log) {
   const oscene *s = (const oscene *)scene;
   if (!s || level < 0 || level > 8 || max_order < 0 || max_order > 32 || n_threads < 1) return -1;
   if (dir_of) {
@@ -919,6 +924,7 @@ int or_trace_dir(const void *scene, const float *src, const float *power, int64_
     J->dir_gain = dir_of ? dir_gain : NULL; J->dir_of = dir_of;
     J->level = level; J->dirs = dirs; J->omega = omega; J->n_beams = nb;
     J->tid = i; J->n_threads = n_threads;
+    J->hit_log = hit_log;
     J->acc.n_bands = s->n_bands;
     J->acc.alpha = p.alpha;
     J->acc.I = i == 0 ? I : (double *)calloc((size_t)(n_mics > 0 ? n_mics : 1) * s->n_bands, sizeof(double));
@@ -971,7 +977,7 @@ int or_trace(const void *scene, const float *src, const float *power, int64_t n_
              int64_t *log_n) {
   return or_trace_dir(scene, src, power, n_src, level, NULL, 0, NULL, mics, n_mics, max_order, alpha,
                       energy_threshold, t_eps, hit_mode, mic_mode, n_threads, I, cnt, stats, log_cap,
-                      log_mic, log_src, log_order, log_d, log_apex, log_n);
+                      log_mic, log_src, log_order, log_d, log_apex, log_n, NULL);
 }
 
 /* Level readout: L = 10 log10(I / 1e-12) dB re 1e-12 W/m^2, -inf where I = 0. */

@@ -59,7 +59,7 @@ def lib():
                                    p, p, p, i64, p, p, p, p, p, p]
             L.or_trace_dir.restype = i32
             L.or_trace_dir.argtypes = [p, p, p, i64, i32, p, i32, p, p, i64, i32, p, d, d, i32, i32,
-                                       i32, p, p, p, i64, p, p, p, p, p, p]
+                                       i32, p, p, p, i64, p, p, p, p, p, p, p]
             L.or_levels.argtypes = [p, i64, p]
             L.or_ray_tri.restype = i32
             L.or_ray_tri.argtypes = [p, p, p, p, p, p]
@@ -134,7 +134,7 @@ def cast_rays(scene: Scene, o, d, has_start=None, ns=None, t_eps=1e-3, mode=HIT_
 
 def trace(scene: Scene, src, power, level, mics, max_order, alpha=None, energy_threshold=0.0,
           t_eps=1e-3, hit_mode=HIT_BVH, mic_mode=MIC_GRID, n_threads=1, log_cap=0,
-          directivity=None, pattern_of=None):
+          directivity=None, pattern_of=None, hit_log=False):
     """Full hybrid trace (Section 2), optionally tiled (Section 3).
 
     Directional sources (Section 2: a source's energy is split between the
@@ -142,6 +142,11 @@ def trace(scene: Scene, src, power, level, mics, max_order, alpha=None, energy_t
     20*4**level] gains per beam, `pattern_of` [n_src] the pattern of each
     source (-1 = omnidirectional); a beam's band powers are the source's
     times its pattern's gain for that beam.
+
+    With `hit_log`, also returns "hits" [n_src * 20*4**level, max_order + 1]
+    int32: the triangle each segment's axis ray hit (-1: it escaped; -2: the
+    beam did not reach that order), lineage = source * beams + the oracle's
+    own beam index.
 
     Returns dict(I [n_m, B] W/m^2, cnt [n_m], stats dict, log dict or None).
     """
@@ -161,6 +166,7 @@ def trace(scene: Scene, src, power, level, mics, max_order, alpha=None, energy_t
         log = dict(mic=np.empty(log_cap, np.int32), src=np.empty(log_cap, np.int32),
                    order=np.empty(log_cap, np.int32), d=np.empty(log_cap, np.float64),
                    apex=np.empty((log_cap, 3), np.float64))
+    hits = np.full((len(src) * 20 * 4 ** level, max_order + 1), -2, np.int32) if hit_log else None
     if pattern_of is not None:
         gain = _c(directivity, np.float32).reshape(-1, 20 * 4 ** level)
         pat = _c(pattern_of, np.int32).reshape(len(src))
@@ -172,7 +178,7 @@ def trace(scene: Scene, src, power, level, mics, max_order, alpha=None, energy_t
                             n_threads, _ptr(I), _ptr(cnt), _ptr(stats), log_cap,
                         *(_ptr(log[k]) if log else None for k in ("mic", "src", "order", "d",
                                                                    "apex")),
-                        C.byref(ln))
+                        C.byref(ln), _ptr(hits))
     if rc != 0:
         raise ValueError(f"or_trace failed: {rc}")
     if log is not None:
@@ -181,7 +187,10 @@ def trace(scene: Scene, src, power, level, mics, max_order, alpha=None, energy_t
         log["full"] = k < log_cap
     st = dict(segments=stats[0], contributions=stats[1], hits=stats[2], escapes=stats[3],
               handoffs=stats[4], ties=stats[5], order_power=stats[N_STAT_FIXED:].copy())
-    return dict(I=I, cnt=cnt, stats=st, log=log)
+    out = dict(I=I, cnt=cnt, stats=st, log=log)
+    if hits is not None:
+        out["hits"] = hits
+    return out
 
 
 def beam_axes(level: int):

@@ -20,7 +20,7 @@ BT_OK = 0
 BT_E_INVALID, BT_E_NOMEM, BT_E_CUDA, BT_E_STATE, BT_E_QUEUE_FULL, BT_E_TIMEOUT = -1, -2, -3, -4, -5, -6
 BT_PENDING = 1
 BT_MAX_BANDS = 8
-BT_PREC_FP32, BT_PREC_MIXED, BT_PREC_FP64 = 0, 1, 2
+BT_PREC_FP32, BT_PREC_MIXED, BT_PREC_FP64, BT_PREC_MIXED64 = 0, 1, 2, 3
 BT_FAULT_WITHHOLD, BT_FAULT_SEGMENTS = 1, 2  # bt_trace_params.fault_test (test hooks)
 
 _ERR_NAMES = {BT_E_INVALID: "BT_E_INVALID", BT_E_NOMEM: "BT_E_NOMEM", BT_E_CUDA: "BT_E_CUDA",
@@ -63,7 +63,7 @@ EXPECTED_SYMBOLS = ("bt_params_default", "bt_create", "bt_destroy", "bt_load_sce
                     "bt_trace_noalloc", "bt_set_result", "bt_batch_create", "bt_batch_run",
                     "bt_batch_stats", "bt_batch_destroy", "bt_scene_share", "bt_trace_ranges",
                     "bt_ranges_stats", "bt_set_directivity", "bt_beam_axes", "bt_submit", "bt_poll",
-                    "bt_wait", "bt_l2_bandwidth")
+                    "bt_wait", "bt_l2_bandwidth", "bt_set_hit_log")
 
 
 def lib_path() -> str:
@@ -107,6 +107,7 @@ def lib():
             L.bt_trace_ranges.argtypes = [p, i32, p, p, p, C.POINTER(bt_trace_params), i32]
             L.bt_ranges_stats.argtypes = [p, C.POINTER(bt_stats)]
             L.bt_l2_bandwidth.argtypes = [p, i64, i32, i32, C.POINTER(C.c_double)]
+            L.bt_set_hit_log.argtypes = [p, i32, p, i64]
             L.bt_kernel_launches.argtypes = []
             L.bt_kernel_launches.restype = C.c_int64
             for name in EXPECTED_SYMBOLS:
@@ -157,6 +158,16 @@ def bt_destroy(ctx):
 
 def bt_kernel_launches() -> int:
     return int(lib().bt_kernel_launches())
+
+
+def bt_set_hit_log(ctx, scene_id: int, hits=None):
+    """Register a device int32 tensor (lineages x (max_order + 1)) as the
+    scene's hit log, or clear it with None."""
+    if hits is None:
+        _check(lib().bt_set_hit_log(ctx, int(scene_id), None, 0), ctx)
+        return
+    ph, n, keep = _arr(hits, np.int32)
+    _check(lib().bt_set_hit_log(ctx, int(scene_id), ph, n), ctx)
 
 
 def bt_l2_bandwidth(ctx, n_bytes: int = 48 << 20, repeats: int = 200, blocks_per_sm: int = 4) -> float:

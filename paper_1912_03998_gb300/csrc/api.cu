@@ -77,6 +77,8 @@ struct SceneState {
   unsigned long long gen = 0;  // changes whenever the scene's buffers may change (batches check it)
   int geom_of = -1;            // >= 0: the geometry buffers belong to that scene (bt_scene_share)
   int leaf = 1, t_leaf = 1;    // leaf size the flat and the tiled hierarchy are collapsed to
+  int32_t *hit_log = nullptr;  // bt_set_hit_log: caller's device array, or null
+  int64_t hit_log_n = 0;
   int n_shares = 0;            // scenes sharing this scene's geometry
   DevBuf out_level, out_int, out_cnt;
 };
@@ -221,6 +223,17 @@ void release_scene(bt_ctx *c, SceneState &s) {
   } while (0)
 
 int check_ctx(bt_ctx *c) { return c ? BT_OK : BT_E_INVALID; }
+
+// True if p is device (or managed) memory of device `device`.
+bool is_device_ptr(const void *p, int device) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == device;
+}
+
 
 bt::DevScene dev_scene(const SceneState &s) {
   bt::DevScene d;
@@ -912,7 +925,8 @@ static int check_params(bt_ctx *c, SceneState *s, const bt_trace_params *p, floa
   if (p->max_order < 0 || p->max_order > 32) return fail(c, BT_E_INVALID, "max_order %d not in 0..32", p->max_order);
   if (!(p->t_eps_m > 0.0f) || !isfinite(p->t_eps_m)) return fail(c, BT_E_INVALID, "t_eps_m must be > 0");
   if (!(p->energy_threshold_w >= 0.0f)) return fail(c, BT_E_INVALID, "energy_threshold_w must be >= 0");
-  if (p->precision != BT_PREC_MIXED && p->precision != BT_PREC_FP32 && p->precision != BT_PREC_FP64)
+  if (p->precision != BT_PREC_MIXED && p->precision != BT_PREC_FP32 && p->precision != BT_PREC_FP64 &&
+      p->precision != BT_PREC_MIXED64)
     return fail(c, BT_E_INVALID, "unknown precision %d", p->precision);
   if (p->tiles_x < 1 || p->tiles_y < 1 || p->tiles_x > BT_MAX_TILES || p->tiles_y > BT_MAX_TILES)
     return fail(c, BT_E_INVALID, "tiles %dx%d not in 1..%d per axis", p->tiles_x, p->tiles_y, BT_MAX_TILES);
@@ -1026,6 +1040,13 @@ static int enqueue_trace(bt_ctx *c, int32_t id, const bt_trace_params *p) {
   ta.blocks_per_sm = p->blocks_per_sm;
   ta.beams_per_warp = p->beams_per_warp;
   ta.leaf_size = p->leaf_size > 1 ? p->leaf_size : 1;
+  if (s->hit_log) {
+    if (s->hit_log_n < total * (p->max_order + 1))
+      return fail(c, BT_E_INVALID, "hit log of %lld entries is smaller than %lld lineages x %d orders",
+                  (long long)s->hit_log_n, (long long)total, p->max_order + 1);
+    ta.hit_log = s->hit_log;
+    ta.hit_log_stride = p->max_order + 1;
+  }
   if (ta.prec == BT_PREC_MIXED && total > 0) {
     if (c->beam_table_level != s->level) {
       TRY(ensure(c, c->beam_table, sizeof(float) * 24 * (size_t)n_beams));
@@ -1108,6 +1129,24 @@ static int enqueue_trace(bt_ctx *c, int32_t id, const bt_trace_params *p) {
   r.scatter_launches = n_scatter_launches;
   r.rounds = n_rounds;
   s->pending = true;
+  return BT_OK;
+}
+
+BT_API int bt_set_hit_log(bt_ctx *c, int32_t scene_id, int32_t *hits, int64_t n) {
+  BT_RANGE();
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  SceneState *s;
+  TRY(scene_ref(c, scene_id, &s));
+  if (!hits) {
+    s->hit_log = nullptr;
+    s->hit_log_n = 0;
+    return BT_OK;
+  }
+  if (n < 0) return fail(c, BT_E_INVALID, "negative hit log size");
+  if (!is_device_ptr(hits, c->device)) return fail(c, BT_E_INVALID, "the hit log must be device memory of device %d", c->device);
+  s->hit_log = hits;
+  s->hit_log_n = n;
   return BT_OK;
 }
 
@@ -1675,15 +1714,6 @@ __global__ void k_levels_noalloc(const double *energy, const int *count, const f
     level_db[orig * n_bands + b] = I > 0.0 ? 10.0 * log10(I) + 120.0 : -__builtin_huge_val();
   }
   if (path_count) path_count[orig] = count[p];
-}
-
-bool is_device_ptr(const void *p, int device) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == device;
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

@@ -181,6 +181,8 @@ struct TraceArgs {
   int blocks_per_sm;  // persistent grid: resident blocks per SM, 0 = as many as fit
   int beams_per_warp; // lineages a warp reserves at a time (0 = what its lanes need)
   int leaf_size;      // most triangles per BVH leaf (1: the traversal without leaf runs)
+  int *hit_log;       // single-scene traces: [lineages][hit_log_stride] hit triangle per segment, or null
+  int hit_log_stride; // max_order + 1
 };
 
 struct ScatterArgs {

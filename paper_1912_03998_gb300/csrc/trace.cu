@@ -35,7 +35,20 @@
 namespace bt {
 
 // precision variants of the trace kernels (BT_PREC_*)
-constexpr int kPF32 = 0, kPMixed = 1, kPF64 = 2;
+constexpr int kPF32 = 0, kPMixed = 1, kPF64 = 2, kPMixed64 = 3;
+// What each variant does: the image-source chain (apex, cone normals, ray
+// origin and direction) as float pairs (`pairs`, MIXED) or in float64
+// (`chain64`, FP64 and MIXED64), else float32; float32 triangle tests whose
+// ambiguous cases and near ties are settled in float64 after the search
+// (`defer`, MIXED and MIXED64), or every triangle test in float64 (`all64`,
+// FP64).
+template <int kP>
+struct Prec {
+  static constexpr bool pairs = kP == kPMixed;
+  static constexpr bool chain64 = kP == kPF64 || kP == kPMixed64;
+  static constexpr bool defer = kP == kPMixed || kP == kPMixed64;
+  static constexpr bool all64 = kP == kPF64;
+};
 
 // Regular icosahedron: unit vertices (the cyclic permutations of
 // (0, +-1, +-phi), normalised) and its 20 faces, counter-clockwise seen
@@ -201,8 +214,9 @@ __device__ __forceinline__ bool pend_add(const RaySrc &rs, int entry) {
 }
 
 // Closest accepted hit of the ray in the BVH; ties in distance go to the
-// lowest original triangle id.  With kMixed, `rs` gives the float-pair ray
-// that the float32 ray `r` rounds, read only on the rare float64 paths.
+// lowest original triangle id.  In the deferring variants `rs` gives the
+// float-pair or float64 ray that the float32 ray `r` rounds, read only on the
+// rare float64 paths.
 // Returns the leaf slot or -1.
 
 // Candidate triangle `slot` against the best hit so far (ties in distance go
@@ -212,7 +226,7 @@ __device__ __forceinline__ bool pend_add(const RaySrc &rs, int entry) {
 template <int kP, bool kCount>
 __device__ __forceinline__ void consider_tri(const DevScene &sc, const Tri *tris, const Ray &r, const RaySrc &rs,
                                              double dns64, Best &best, int slot, unsigned &n_tris, float tlim) {
-  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
+  constexpr bool kDefer = Prec<kP>::defer, kAll64 = Prec<kP>::all64;
   if (kCount) n_tris++;
   const Tri *tp = tris + slot;
   float4 v0 = __ldg(&tp->v0), v1 = __ldg(&tp->v1), v2 = __ldg(&tp->v2);
@@ -220,7 +234,7 @@ __device__ __forceinline__ void consider_tri(const DevScene &sc, const Tri *tris
   double t64 = 0.0;
   bool has64 = false;
   bool amb = false;
-  if (kF64) {
+  if (kAll64) {
     // FP64: every candidate in float64 Moller-Trumbore on the float64 ray
     double3 o, d;
     rs.get(o, d);
@@ -233,10 +247,10 @@ __device__ __forceinline__ void consider_tri(const DevScene &sc, const Tri *tris
   } else {
     t = hit_watertight(r, v0, v1, v2, amb);
   }
-  if (kF64) {
+  if (kAll64) {
   } else {
     // MIXED: an ambiguous candidate is decided in float64 after the search
-    if (kMixed && amb && pend_add(rs, slot | kPendAmb)) return;
+    if (kDefer && amb && pend_add(rs, slot | kPendAmb)) return;
     if (!(t < kInf && accept_hit(r, t))) return;
   }
   if (t > tlim) return;  // sub-domain: beyond the tile (see k_trace_tiled)
@@ -254,7 +268,7 @@ __device__ __forceinline__ void consider_tri(const DevScene &sc, const Tri *tris
     return;
   }
   if (t > best.t + win) return;
-  if (kMixed) {
+  if (kDefer) {
     if (!pend_add(rs, slot) && (t < best.t || (t == best.t && id < best.id))) {
       best.t = t; best.slot = slot; best.id = id; best.t64 = 0.0; best.has64 = false;
     }
@@ -413,11 +427,11 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, Ray
   int stack[kStackDepth];
   HitSearch hs;
   hs.start(root);
-  if constexpr (kP == kPMixed) rs.pend[0] = 0;
+  if constexpr (Prec<kP>::defer) rs.pend[0] = 0;
   while (hs.step<kP, kCount, true>(sc, nodes, tris, n_tri, r, rs, dns64, stack, err, n_nodes, n_tris, tlim)) {
   }
   best = hs.best;
-  if constexpr (kP == kPMixed) settle_search(sc, r, rs, dns64, best, tlim);
+  if constexpr (Prec<kP>::defer) settle_search(sc, r, rs, dns64, best, tlim);
   return best.slot;
 }
 
@@ -472,31 +486,31 @@ constexpr float kTileEps = 1e-2f;
 enum { kCSeg, kCHit, kCEsc, kCEmit, kCHand, kCSteal, kCNodes, kCTris, kNumCounts };
 template <int kP>
 struct LineageSmem {
-  double dv[kP == kPF64 ? kRows : 1][kTraceThreads];  // FP64: the chain itself; `hi` holds its float32 rounding
+  double dv[Prec<kP>::chain64 ? kRows : 1][kTraceThreads];  // float64 chain; `hi` holds its float32 rounding
   float hi[kRows][kTraceThreads];
-  float lo[kP == kPMixed ? kRows : 1][kTraceThreads];
+  float lo[Prec<kP>::pairs ? kRows : 1][kTraceThreads];
   float p[kMaxBands][kTraceThreads];  // band power W_b prod(r_b)
   float st[4][kTraceThreads];         // start plane (relative to the apex)
-  int pend[kP == kPMixed ? kPend + 1 : 1][kTraceThreads];  // MIXED: candidates left to float64
+  int pend[Prec<kP>::defer ? kPend + 1 : 1][kTraceThreads];  // candidates left to float64
   unsigned cnt[kNumCounts][kTraceThreads];  // per-lane event counts of the launch
 };
 
 template <int kP>
 __device__ __forceinline__ df3 ld_df3(const LineageSmem<kP> &sm, int row, int t) {
-  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
+  [[maybe_unused]] constexpr bool kPairs = Prec<kP>::pairs, kChain64 = Prec<kP>::chain64, kDefer = Prec<kP>::defer;
   df3 v;
-  v.x = df{sm.hi[row][t], kMixed ? sm.lo[row][t] : 0.0f};
-  v.y = df{sm.hi[row + 1][t], kMixed ? sm.lo[row + 1][t] : 0.0f};
-  v.z = df{sm.hi[row + 2][t], kMixed ? sm.lo[row + 2][t] : 0.0f};
+  v.x = df{sm.hi[row][t], kPairs ? sm.lo[row][t] : 0.0f};
+  v.y = df{sm.hi[row + 1][t], kPairs ? sm.lo[row + 1][t] : 0.0f};
+  v.z = df{sm.hi[row + 2][t], kPairs ? sm.lo[row + 2][t] : 0.0f};
   return v;
 }
 template <int kP>
 __device__ __forceinline__ void st_df3(LineageSmem<kP> &sm, int row, int t, df3 v) {
-  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
+  [[maybe_unused]] constexpr bool kPairs = Prec<kP>::pairs, kChain64 = Prec<kP>::chain64, kDefer = Prec<kP>::defer;
   sm.hi[row][t] = v.x.hi;
   sm.hi[row + 1][t] = v.y.hi;
   sm.hi[row + 2][t] = v.z.hi;
-  if (kMixed) {
+  if (kPairs) {
     sm.lo[row][t] = v.x.lo;
     sm.lo[row + 1][t] = v.y.lo;
     sm.lo[row + 2][t] = v.z.lo;
@@ -504,12 +518,12 @@ __device__ __forceinline__ void st_df3(LineageSmem<kP> &sm, int row, int t, df3 
 }
 template <int kP>
 __device__ __forceinline__ float3 ld_hi3(const LineageSmem<kP> &sm, int row, int t) {
-  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
+  [[maybe_unused]] constexpr bool kPairs = Prec<kP>::pairs, kChain64 = Prec<kP>::chain64, kDefer = Prec<kP>::defer;
   return make_float3(sm.hi[row][t], sm.hi[row + 1][t], sm.hi[row + 2][t]);
 }
 template <int kP>
 __device__ __forceinline__ void st_f3(LineageSmem<kP> &sm, int row, int t, float3 v) {
-  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
+  [[maybe_unused]] constexpr bool kPairs = Prec<kP>::pairs, kChain64 = Prec<kP>::chain64, kDefer = Prec<kP>::defer;
   sm.hi[row][t] = v.x;
   sm.hi[row + 1][t] = v.y;
   sm.hi[row + 2][t] = v.z;
@@ -534,12 +548,12 @@ __device__ __forceinline__ void st_d3(LineageSmem<kP> &sm, int row, int t, doubl
 // Start lineage `lin` (source si, beam bi) in this thread's column.
 template <int kP>
 __device__ __forceinline__ void init_lineage(const SceneView &a, LineageSmem<kP> &sm, int t, int64_t lin) {
-  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
+  [[maybe_unused]] constexpr bool kPairs = Prec<kP>::pairs, kChain64 = Prec<kP>::chain64, kDefer = Prec<kP>::defer;
   const int nb = a.sc.n_bands;
   int64_t si = lin / a.n_beams, bi = lin - si * a.n_beams;
   float4 s4 = __ldg(&a.src[si]);
   float3 A = make_float3(s4.x, s4.y, s4.z);
-  if (kF64) {
+  if (kChain64) {
     double3 d0, d1, d2;
     beam_dirs<double>(a.level, bi, d0, d1, d2);
     st_d3(sm, kRowN, t, cross_exact(d0, d1));
@@ -549,7 +563,7 @@ __device__ __forceinline__ void init_lineage(const SceneView &a, LineageSmem<kP>
     const double3 A64 = make_double3(s4.x, s4.y, s4.z);
     st_d3(sm, kRowA, t, A64);
     st_d3(sm, kRowO, t, A64);
-  } else if (kMixed) {
+  } else if (kPairs) {
     // table: 9 normal components then the 3 axis components, hi parts
     // first, lo parts 12 floats later
     const float *bt = a.beam_table + 24 * bi;
@@ -606,7 +620,7 @@ struct TraceCounts {
 };
 template <int kP>
 __device__ __forceinline__ TraceCounts init_counts(LineageSmem<kP> &sm, int t) {
-  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
+  [[maybe_unused]] constexpr bool kPairs = Prec<kP>::pairs, kChain64 = Prec<kP>::chain64, kDefer = Prec<kP>::defer;
   for (int q = 0; q < kNumCounts; q++) sm.cnt[q][t] = 0u;
   return TraceCounts{&sm.cnt[0][t]};
 }
@@ -619,12 +633,16 @@ template <int kP>
 __device__ __forceinline__ bool finish_segment(const TraceArgs &a, const SceneView &v, int vi, LineageSmem<kP> &sm,
                                                int t, const Ray &r, const Best &best, int slot, LaneState &ls,
                                                const TraceCounts &cn) {
-  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
+  [[maybe_unused]] constexpr bool kPairs = Prec<kP>::pairs, kChain64 = Prec<kP>::chain64, kDefer = Prec<kP>::defer;
   const int nb = v.sc.n_bands;
   cn[kCSeg]++;
   float4 end = make_float4(0.0f, 0.0f, 0.0f, -kInf);
   float4 v0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   float4 plf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  if (a.hit_log) {
+    // (measurement aid: which triangle each segment's axis ray hit)
+    a.hit_log[ls.lin * a.hit_log_stride + ls.k] = slot >= 0 ? __float_as_int(__ldg(&v.sc.tris[slot].v1.w)) : -1;
+  }
   if (slot >= 0) {
     cn[kCHit]++;
     v0 = __ldg(&v.sc.tris[slot].v0);
@@ -633,10 +651,10 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, const SceneVi
     float3 pn = f3(plf);
     float3 en = dot3(pn, r.d) < 0.0f ? pn : pn * -1.0f;
     float ew;
-    if (kF64) {
+    if (kChain64) {
       double3 end = make_double3(en.x, en.y, en.z);
       ew = (float)dot3(end, make_double3(v0.x, v0.y, v0.z) - ld_d3(sm, kRowA, t));
-    } else if (kMixed) {
+    } else if (kPairs) {
       ew = df3_dot(mkdf3(en), df3_sub(mkdf3(f3(v0)), ld_df3(sm, kRowA, t))).hi;
     } else {
       ew = dot3(en, f3(v0) - ld_hi3(sm, kRowA, t));
@@ -649,15 +667,15 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, const SceneVi
     Seg s;
     for (int q = 0; q < 3; q++) {
       s.ahi[q] = sm.hi[kRowA + q][t];
-      s.alo[q] = kMixed ? sm.lo[kRowA + q][t] : 0.0f;
+      s.alo[q] = kPairs ? sm.lo[kRowA + q][t] : 0.0f;
     }
     float3 n0 = ld_hi3(sm, kRowN, t), n1 = ld_hi3(sm, kRowN + 3, t), n2 = ld_hi3(sm, kRowN + 6, t);
     s.n0 = make_float4(n0.x, n0.y, n0.z, __int_as_float(ls.start_slot));
     s.n1 = make_float4(n1.x, n1.y, n1.z, __int_as_float(slot));
     s.n2 = make_float4(n2.x, n2.y, n2.z, __int_as_float(ls.k));
-    for (int q = 0; q < 9; q++) s.nlo[q] = kMixed ? sm.lo[kRowN + q][t] : 0.0f;
+    for (int q = 0; q < 9; q++) s.nlo[q] = kPairs ? sm.lo[kRowN + q][t] : 0.0f;
     s.pad[0] = s.pad[1] = s.pad[2] = 0.0f;
-    if (kF64) {
+    if (kChain64) {
       // float64 values as float pairs, the apex with a third word so that
       // hi + lo + pad gives it back exactly
       for (int q = 0; q < 3; q++) {
@@ -692,7 +710,7 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, const SceneVi
   // the reflected beam starts at the hit point on that plane.
   float3 pn = f3(plf), pv0 = f3(v0);
   float3 Dn;
-  if (kF64) {
+  if (kChain64) {
     Plane64 pl = ldg_d4(&v.sc.planes64[slot]);
     const double3 n = make_double3(pl.x, pl.y, pl.z), v0d = make_double3(v0.x, v0.y, v0.z);
     double3 A = ld_d3(sm, kRowA, t), O = ld_d3(sm, kRowO, t), D = ld_d3(sm, kRowD, t);
@@ -715,7 +733,7 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, const SceneVi
     const double3 sn = dn > 0.0 ? n : n * -1.0;
     const double sw = dot3(sn, v0d - A);
     sm.st[0][t] = (float)sn.x; sm.st[1][t] = (float)sn.y; sm.st[2][t] = (float)sn.z; sm.st[3][t] = (float)sw;
-  } else if (kMixed) {
+  } else if (kPairs) {
     // in stages, each reading its rows from shared memory and writing them
     // back before the next starts, so that few float pairs are live at once
     // (the compiler fences keep the stages apart)
@@ -895,7 +913,7 @@ constexpr int kRefillLanes = 28;
 // holds the whole warp (dynamic ray fetch, after Aila & Laine 2009).
 template <int kP, bool kCount, bool kBatch, bool kLeaves>
 __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
-  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
+  [[maybe_unused]] constexpr bool kPairs = Prec<kP>::pairs, kChain64 = Prec<kP>::chain64, kDefer = Prec<kP>::defer;
   __shared__ LineageSmem<kP> sm;
   __shared__ int64_t view_base[kBatch ? BT_MAX_SCENES : 1];
   __shared__ WarpLineages wlin[kTraceThreads / 32];
@@ -913,15 +931,15 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
   HitSearch hs;
   hs.start(-1);
   int stack[kStackDepth];
-  const RaySrc rs{&sm.hi[kRowO][t], kMixed ? &sm.lo[kRowO][t] : &sm.hi[kRowO][t], kTraceThreads,
-                  kF64 ? &sm.dv[kRowO][t] : nullptr, &sm.pend[0][t]};
+  const RaySrc rs{&sm.hi[kRowO][t], kPairs ? &sm.lo[kRowO][t] : &sm.hi[kRowO][t], kTraceThreads,
+                  kChain64 ? &sm.dv[kRowO][t] : nullptr, &sm.pend[0][t]};
   while (true) {
     // ---- service: finished searches write their segment and reflect
     bool fresh = false;
     if (__ballot_sync(0xffffffffu, pending) && pending) {
       const SceneView &v = kBatch ? a.views[vi] : a.v;
       const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), v.t_eps, ls.dns);
-      if constexpr (kMixed) settle_search(v.sc, r, rs, ls.dns64, hs.best, kInf);
+      if constexpr (kDefer) settle_search(v.sc, r, rs, ls.dns64, hs.best, kInf);
       if (finish_segment(a, v, vi, sm, t, r, hs.best, hs.best.slot, ls, cn)) fresh = true;
       else ls.lin = -1;
       pending = false;
@@ -944,7 +962,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
     }
     if (fresh) {
       hs.start((kBatch ? a.views[vi] : a.v).sc.root);
-      if constexpr (kMixed) rs.pend[0] = 0;
+      if constexpr (kDefer) rs.pend[0] = 0;
       searching = true;
     }
     if (__all_sync(0xffffffffu, done)) break;
@@ -1011,8 +1029,8 @@ __device__ __forceinline__ bool wait_slot(const TraceArgs &a, const TiledArgs &t
 template <int kP>
 __device__ __forceinline__ void save_state(uint32_t *S, size_t c, const LineageSmem<kP> &sm, int t,
                                            const LaneState &ls) {
-  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
-  if (kF64) {
+  [[maybe_unused]] constexpr bool kPairs = Prec<kP>::pairs, kChain64 = Prec<kP>::chain64, kDefer = Prec<kP>::defer;
+  if (kChain64) {
     // rows 0..35: the float64 chain, low word then high word
     for (int q = 0; q < kRows; q++) {
       unsigned long long b = __double_as_longlong(sm.dv[q][t]);
@@ -1021,7 +1039,7 @@ __device__ __forceinline__ void save_state(uint32_t *S, size_t c, const LineageS
     }
   } else {
     for (int q = 0; q < kRows; q++) __stcg(S + q * c, __float_as_uint(sm.hi[q][t]));
-    if (kMixed)
+    if (kPairs)
       for (int q = 0; q < kRows; q++) __stcg(S + (kRows + q) * c, __float_as_uint(sm.lo[q][t]));
   }
   for (int b = 0; b < kMaxBands; b++) __stcg(S + (36 + b) * c, __float_as_uint(sm.p[b][t]));
@@ -1039,8 +1057,8 @@ __device__ __forceinline__ void save_state(uint32_t *S, size_t c, const LineageS
 template <int kP>
 __device__ __forceinline__ void load_state(const uint32_t *S, size_t c, LineageSmem<kP> &sm, int t,
                                            LaneState &ls) {
-  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
-  if (kF64) {
+  [[maybe_unused]] constexpr bool kPairs = Prec<kP>::pairs, kChain64 = Prec<kP>::chain64, kDefer = Prec<kP>::defer;
+  if (kChain64) {
     for (int q = 0; q < kRows; q++) {
       unsigned long long b = (unsigned long long)__ldcg(S + (2 * q) * c) |
                              ((unsigned long long)__ldcg(S + (2 * q + 1) * c) << 32);
@@ -1050,7 +1068,7 @@ __device__ __forceinline__ void load_state(const uint32_t *S, size_t c, LineageS
     }
   } else {
     for (int q = 0; q < kRows; q++) sm.hi[q][t] = __uint_as_float(__ldcg(S + q * c));
-    if (kMixed)
+    if (kPairs)
       for (int q = 0; q < kRows; q++) sm.lo[q][t] = __uint_as_float(__ldcg(S + (kRows + q) * c));
   }
   for (int b = 0; b < kMaxBands; b++) sm.p[b][t] = __uint_as_float(__ldcg(S + (36 + b) * c));
@@ -1217,7 +1235,7 @@ __device__ __forceinline__ float tile_exit(const TileGrid &tg, int ix, int iy, c
 // whose smaller state fits them (40.7 -> 38.3 ms on the district split 4x4).
 template <int kP, bool kCount, bool kLeaves>
 __global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_tiled(TraceArgs a, const __grid_constant__ TiledArgs ta) {
-  [[maybe_unused]] constexpr bool kMixed = kP == kPMixed, kF64 = kP == kPF64;
+  [[maybe_unused]] constexpr bool kPairs = Prec<kP>::pairs, kChain64 = Prec<kP>::chain64, kDefer = Prec<kP>::defer;
   __shared__ LineageSmem<kP> sm;
   const int t = threadIdx.x;
   const unsigned lane = lane_id();
@@ -1246,8 +1264,8 @@ __global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_ti
   HitSearch hs;
   hs.start(-1);
   int stack[kStackDepth];
-  const RaySrc rs{&sm.hi[kRowO][t], kMixed ? &sm.lo[kRowO][t] : &sm.hi[kRowO][t], kTraceThreads,
-                  kF64 ? &sm.dv[kRowO][t] : nullptr, &sm.pend[0][t]};
+  const RaySrc rs{&sm.hi[kRowO][t], kPairs ? &sm.lo[kRowO][t] : &sm.hi[kRowO][t], kTraceThreads,
+                  kChain64 ? &sm.dv[kRowO][t] : nullptr, &sm.pend[0][t]};
   while (true) {
     // ---- service: finished searches write their segment and reflect, end,
     // or go on to the next tile
@@ -1256,7 +1274,7 @@ __global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_ti
     if (__ballot_sync(0xffffffffu, pending) && pending) {
       pending = false;
       const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), v.t_eps, ls.dns);
-      if constexpr (kMixed) settle_search(v.sc, r, rs, ls.dns64, hs.best, tlim);
+      if constexpr (kDefer) settle_search(v.sc, r, rs, ls.dns64, hs.best, tlim);
       // the hit lies in this tile (a reflected beam starts here as well); a
       // ray without one either leaves the grid, and with it every triangle
       // (it escapes), or goes on to the next tile
@@ -1375,7 +1393,7 @@ __global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_ti
       const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), v.t_eps, ls.dns);
       tlim = tile_exit(tg, tile % tg.tx, tile / tg.tx, r) + kTileEps;
       hs.start(__ldg(&ta.roots[tile]));
-      if constexpr (kMixed) rs.pend[0] = 0;
+      if constexpr (kDefer) rs.pend[0] = 0;
       searching = true;
     }
     if (!__any_sync(0xffffffffu, active)) {
@@ -1444,6 +1462,7 @@ cudaError_t launch_trace_tiled(cudaStream_t st, const TraceArgs &a, const TiledA
   cudaError_t e;
   if (a.prec == kPMixed) e = launch_tiled_p<kPMixed>(st, a, ta, n_sm);
   else if (a.prec == kPF64) e = launch_tiled_p<kPF64>(st, a, ta, n_sm);
+  else if (a.prec == kPMixed64) e = launch_tiled_p<kPMixed64>(st, a, ta, n_sm);
   else e = launch_tiled_p<kPF32>(st, a, ta, n_sm);
   note_launches(1);
   return e;
@@ -1526,6 +1545,7 @@ template <bool kBatch>
 static cudaError_t launch_trace_b(cudaStream_t st, const TraceArgs &a, int n_sm) {
   if (a.prec == kPMixed) return launch_trace_p<kPMixed, kBatch>(st, a, n_sm);
   if (a.prec == kPF64) return launch_trace_p<kPF64, kBatch>(st, a, n_sm);
+  if (a.prec == kPMixed64) return launch_trace_p<kPMixed64, kBatch>(st, a, n_sm);
   return launch_trace_p<kPF32, kBatch>(st, a, n_sm);
 }
 
