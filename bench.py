@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--tune-cache", default=None,
                     help="batch --autotune: JSON file of tuned knobs per (cities, GPU model), reused when present")
     ap.add_argument("--sources", type=int, default=None, help="override the source count")
+    ap.add_argument("--split-sources", action="store_true",
+                    help="trace one district with its sources split over the ranks (one sum all-reduce of "
+                         "the partial results per step); the default under torchrun with more than one GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -233,12 +236,30 @@ def trial_table(table):
     return {"knobs": names, "rows": [[knobs.get(n) for n in names] + [round(ms, 3)] for knobs, ms in table]}
 
 
+def source_shard_result(trace_block, n_sources, rank, world, reduce):
+    """One step of the sources split over the ranks (beams of different
+    sources never interact, so the result for all sources is the sum of the
+    ranks' partial results): this rank traces its contiguous block of the
+    sources with trace_block(lo, hi) -> (intensity, path counts) as tensors on
+    its device, and the partial results are summed over the ranks in place by
+    reduce(intensity, counts) (one all-reduce; nothing to sum on one rank)."""
+    from paper_1912_03998_gb300 import shard
+    lo, hi = shard.source_block(n_sources, rank, world)
+    I, cnt = trace_block(lo, hi)
+    if world > 1:
+        reduce(I, cnt)
+    return I, cnt
+
+
 def run_ours(args, rank, world):
     import torch
-    from paper_1912_03998_gb300 import btrace
+    from paper_1912_03998_gb300 import btrace, shard
     dev = torch.device("cuda", rank % max(1, torch.cuda.device_count()))
     torch.cuda.set_device(dev)
-    w = make_workload(args.workload, rank, args.sources)
+    split = args.split_sources
+    # split: every rank holds the same district and traces a block of its
+    # sources; replicas: every rank traces its own traffic snapshot
+    w = make_workload(args.workload, 0 if split else rank, args.sources)
     tiles = tuple(int(v) for v in args.tiles.lower().split("x"))
     stream = torch.cuda.current_stream(dev)
     ctx = btrace.bt_create(dev.index, stream.cuda_stream)
@@ -273,12 +294,26 @@ def run_ours(args, rank, world):
             tuned["trials_ms"] = trial_table(table)
     l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    d_I = torch.empty((n_m, nb), dtype=torch.float64, device=dev)
+    d_cnt = torch.empty(n_m, dtype=torch.int32, device=dev)
+
     def step(inp, level_out):
         sid = btrace.bt_load_scene(ctx, inp["verts"], inp["tris"], inp["mat"], inp["refl"])
-        btrace.bt_set_sources(ctx, sid, inp["src"], inp["power"], w.level)
         btrace.bt_set_microphones(ctx, sid, inp["mics"])
-        btrace.bt_trace(ctx, sid, params)
-        st = btrace.bt_read_levels(ctx, sid, level_out, None, None)
+        if split:
+            def trace_block(lo, hi):
+                btrace.bt_set_sources(ctx, sid, inp["src"][lo:hi], inp["power"][lo:hi], w.level)
+                btrace.bt_trace(ctx, sid, params)
+                btrace.bt_read_levels(ctx, sid, None, d_I, d_cnt)
+                return d_I, d_cnt
+            I, cnt = source_shard_result(trace_block, len(w.src), rank, world, shard.allreduce_result)
+            st = btrace.bt_read_levels(ctx, sid)  # this rank's trace
+            btrace.bt_set_result(ctx, sid, I, cnt)
+            btrace.bt_read_levels(ctx, sid, level_out, None, None)
+        else:
+            btrace.bt_set_sources(ctx, sid, inp["src"], inp["power"], w.level)
+            btrace.bt_trace(ctx, sid, params)
+            st = btrace.bt_read_levels(ctx, sid, level_out, None, None)
         btrace.bt_unload_scene(ctx, sid)
         return st
 
@@ -305,7 +340,7 @@ def run_ours(args, rank, world):
     with Clocks(dev.index) as clk:
         ms, stats, launches = timed(d_in, d_level, args.steps)
     untiled = None
-    if tiles != (1, 1) and not args.no_untiled:
+    if tiles != (1, 1) and not args.no_untiled and world == 1:
         # the same workload without the sub-domain split, for comparison
         params.tiles_x, params.tiles_y = 1, 1
         for _ in range(args.warmup):
@@ -600,6 +635,8 @@ def main():
         import torch
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", int(os.environ.get("LOCAL_RANK", rank))))
+        # several GPUs trace one district with its sources split between them
+        args.split_sources = args.workload == "district"
     res = run_ours(args, int(os.environ.get("LOCAL_RANK", rank)), world)
     # whole-job value: segments of all ranks over the slowest rank's time
     segs, total_ms = float(res["segs"]), float(res["total_ms"])
@@ -633,10 +670,12 @@ def main():
                               "float-pair re-test, FP64 energy accumulation")
                              if args.precision == "mixed64" else
                              "FP32 chain, traversal and microphone tests, FP64 energy accumulation",
-                "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"})
+                "parallelism": (f"sources split over {world} GPU(s), one float64 sum all-reduce of the "
+                                f"partial intensities and path counts per step" if args.split_sources else
+                                f"replicas x{world}" if world > 1 else "1 GPU")})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong" if args.split_sources else "weak", "vs_baseline": None,
             "dtype": DTYPE[args.precision],
             "data": "synthetic", "config": cfg, "clocks": res["clocks"],
             "gpu_launches": res["launches"],
