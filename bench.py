@@ -494,13 +494,14 @@ def run_batch(args):
 
 
 # ------------------------------------------------------------------ serving
-def serve_once(tr, cities, rate, n_queries, seed, prec, step_lineages, oldest_share=1.0, small_lineages=0):
+def serve_once(tr, cities, rate, n_queries, seed, prec, step_lineages, oldest_share=1.0, small_lineages=0,
+               **server_kw):
     """One Poisson stream served by the loop and, on the same stream, one
     query at a time; latency summaries of both."""
     from paper_1912_03998_gb300 import btrace, serve, synth
     qs = synth.serving_queries(seed=seed, n_queries=n_queries, n_cities=len(cities), rate_qps=rate)
     srv = serve.Server(tr, cities, step_lineages=step_lineages, precision=prec, oldest_share=oldest_share,
-                       small_lineages=small_lineages)
+                       small_lineages=small_lineages, **server_kw)
     try:
         srv.run(qs[:4], realtime=False)  # warm-up through both paths
         serve.run_plain(tr, srv.city_ids, qs[:4], precision=prec, realtime=False)

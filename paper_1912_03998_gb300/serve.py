@@ -14,6 +14,13 @@ the GPU join at the next step and their work overlaps on the device.  A query
 whose lineages are all traced is read back (levels to the host), its scene
 freed, and its latency (completion - arrival) recorded.
 
+A query that arrives to an idle server and fits one step is traced whole
+with the asynchronous call (bt_submit): while the GPU traces it the loop
+goes on admitting arrivals (their scenes, sources and microphones are set
+up on the host side meanwhile), and polls it (bt_poll) before each step, so
+that read-back and admission overlap the trace.  Admission also checks the
+device's free memory, not only the budget.
+
 `run_plain` serves the same stream one query at a time with whole-query
 traces (bt_trace), the baseline the server is compared with.
 """
@@ -107,10 +114,22 @@ class Done:
         return self.done_s - self.arrival_s
 
 
+def device_free_bytes():
+    """Free memory of the current CUDA device, or None without one."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.mem_get_info()[0])
+    except Exception:
+        pass
+    return None
+
+
 class Server:
     def __init__(self, tracer, cities, step_lineages: int = 1 << 22, quantum: int = 0,
                  mem_budget: int = 4 << 30, max_active: int = 48, precision: int = btrace.BT_PREC_MIXED,
-                 oldest_share: float = 1.0, small_lineages: int = 0):
+                 oldest_share: float = 1.0, small_lineages: int = 0, mem_reserve: int = 1 << 30,
+                 submit_alone: bool = True, check_free: bool = True):
         self.tr = tracer
         self.quantum = int(quantum)
         self.oldest_share = float(oldest_share)
@@ -120,6 +139,9 @@ class Server:
         self.mem_budget = int(mem_budget)
         self.max_active = int(max_active)
         self.precision = precision
+        self.mem_reserve = int(mem_reserve)
+        self.submit_alone = bool(submit_alone)
+        self.check_free = bool(check_free)
         self.waiting = collections.deque()
         self.active = []
         self.mem_used = 0
@@ -136,11 +158,15 @@ class Server:
         self.waiting.append((index, q, arrival_s))
 
     def _admit(self):
+        free = device_free_bytes() if self.waiting and self.check_free else None
         while self.waiting and len(self.active) < self.max_active:
             index, q, arrival = self.waiting[0]
             need = query_bytes(q)
-            if self.active and self.mem_used + need > self.mem_budget:
+            if self.active and (self.mem_used + need > self.mem_budget or
+                                (free is not None and need + self.mem_reserve > free)):
                 break  # wait for memory; a lone query is always admitted
+            if free is not None:
+                free -= need
             self.waiting.popleft()
             ctx = self.tr.ctx
             sid = btrace.bt_scene_share(ctx, self.city_ids[q.city])
@@ -150,23 +176,48 @@ class Server:
             p = self.tr.params(q.max_order, precision=self.precision)
             total = len(q.src) * 20 * 4 ** q.level
             self.active.append(dict(index=index, q=q, sid=sid, p=p, next=0, total=total, mem=need,
-                                    arrival=arrival, admitted=self.now()))
+                                    arrival=arrival, admitted=self.now(), inflight=False))
             self.mem_used += need
+
+    def _poll(self) -> bool:
+        """Poll the submitted whole-query trace, if any; True while it runs."""
+        busy = False
+        for a in self.active:
+            if a["inflight"]:
+                if btrace.bt_poll(self.tr.ctx, a["sid"]):
+                    a["inflight"] = False
+                else:
+                    busy = True
+        return busy
 
     def step(self) -> bool:
         """Admit, trace one step, retire finished queries.  False when idle."""
         t0 = time.perf_counter()
         self._admit()
+        busy = self._poll()
         t1 = time.perf_counter()
         self.host_s["admit"] += t1 - t0
         if not self.active:
             return False
+        pending = [a for a in self.active if a["next"] < a["total"]]
+        if (self.submit_alone and not busy and len(self.active) == 1 and not self.waiting
+                and pending and pending[0]["next"] == 0 and pending[0]["total"] <= self.step_lineages):
+            # alone and small: the whole query in one asynchronous trace
+            a = pending[0]
+            btrace.bt_submit(self.tr.ctx, a["sid"], a["p"])
+            a["inflight"] = a["submitted"] = True
+            a["next"] = a["total"]
+            self.steps += 1
+            self.host_s["step"] += time.perf_counter() - t1
+            return True
+        if busy and not pending:
+            return True  # only the submitted trace is running: nothing to step
         left = [a["total"] - a["next"] for a in self.active]
         work = [l * (a["q"].max_order + 1) for l, a in zip(left, self.active)]
         share = step_shares(left, work, self.step_lineages, self.oldest_share, self.quantum, self.small_lineages)
         ids, begins, ends, params = [], [], [], []
         for a, s in zip(self.active, share):
-            if s > 0:
+            if s > 0 and not a["inflight"]:
                 ids.append(a["sid"])
                 begins.append(a["next"])
                 ends.append(a["next"] + s)
@@ -182,14 +233,17 @@ class Server:
         self.host_s["step"] += t2 - t1
         still = []
         for a in self.active:
-            if a["next"] < a["total"]:
+            if a["next"] < a["total"] or a["inflight"]:
                 still.append(a)
                 continue
             q = a["q"]
             n, nb = len(q.mics), q.power.shape[1]
             level = np.empty((n, nb), np.float64)
             count = np.empty(n, np.int32)
-            btrace.bt_read_levels(self.tr.ctx, a["sid"], level, None, count)
+            st = btrace.bt_read_levels(self.tr.ctx, a["sid"], level, None, count)
+            if a.get("submitted"):
+                self.segments += st["segments"]
+                self.host_s["gpu_trace"] += st["trace_ms"] * 1e-3
             btrace.bt_unload_scene(self.tr.ctx, a["sid"])
             self.mem_used -= a["mem"]
             self.done.append(Done(a["index"], a["arrival"], a["admitted"], self.now(), level, count))
@@ -213,6 +267,9 @@ class Server:
                 i += 1
             if not self.step() and i < len(queries):
                 time.sleep(max(0.0, min(1e-3, queries[i].arrival_s - self.now())))
+            elif any(a["inflight"] for a in self.active) and not self.waiting and (
+                    i >= len(queries) or queries[i].arrival_s > self.now()):
+                time.sleep(50e-6)  # the GPU is tracing a submitted query; nothing else to do yet
         return sorted(self.done, key=lambda d: d.index)
 
     def close(self):

@@ -133,6 +133,7 @@ class _FakeLib:
         self.calls = []       # per bt_trace_ranges call: list of sids
         self.totals = []      # per bt_trace_ranges call: lineages traced
         self.directivity = {}
+        self.submitted, self.polls, self.total = [], {}, {}
 
     def bt_scene_share(self, ctx, base):
         self.next_sid += 1
@@ -142,6 +143,7 @@ class _FakeLib:
 
     def bt_set_sources(self, ctx, sid, src, power, level):
         assert sid in self.live
+        self.total[sid] = len(src) * 20 * 4 ** level
 
     def bt_set_microphones(self, ctx, sid, mics):
         assert sid in self.live
@@ -163,9 +165,23 @@ class _FakeLib:
     def bt_ranges_stats(self, ctx):
         return {"segments": 0, "trace_ms": 0.0}
 
-    def bt_read_levels(self, ctx, sid, level, intensity, count):
-        level[:] = sid
-        count[:] = 1
+    def bt_submit(self, ctx, sid, params):
+        # a whole-query trace: every lineage of the scene in one range
+        assert sid in self.live and not self.ranges[sid]
+        self.submitted.append(sid)
+        self.ranges[sid].append((0, self.total[sid]))
+        self.polls[sid] = 2  # finishes on the second poll
+
+    def bt_poll(self, ctx, sid):
+        self.polls[sid] -= 1
+        return self.polls[sid] <= 0
+
+    def bt_read_levels(self, ctx, sid, level=None, intensity=None, count=None):
+        if level is not None:
+            level[:] = sid
+        if count is not None:
+            count[:] = 1
+        return {"segments": 0, "trace_ms": 0.0}
 
     def bt_unload_scene(self, ctx, sid):
         self.live.discard(sid)
@@ -187,7 +203,7 @@ def test_server_traces_every_lineage_once_in_order(monkeypatch):
     # order, and no step holds more than max_active queries
     lib = _FakeLib()
     for name in ("bt_scene_share", "bt_set_sources", "bt_set_microphones", "bt_beam_axes", "bt_set_directivity",
-                 "bt_trace_ranges", "bt_ranges_stats", "bt_read_levels", "bt_unload_scene"):
+                 "bt_trace_ranges", "bt_ranges_stats", "bt_read_levels", "bt_unload_scene", "bt_submit", "bt_poll"):
         monkeypatch.setattr(serve.btrace, name, getattr(lib, name))
     qs = synth.serving_queries(seed=2, n_queries=12, n_cities=2, rate_qps=1e4, level=3, max_sources=40,
                                max_mics=3000)
@@ -196,7 +212,7 @@ def test_server_traces_every_lineage_once_in_order(monkeypatch):
     assert [d.index for d in done] == list(range(len(qs)))
     assert not lib.live  # every query's scene was freed
     assert max(len(c) for c in lib.calls) <= 4
-    assert max(lib.totals) <= 1500 and srv.steps == len(lib.calls)
+    assert max(lib.totals) <= 1500 and srv.steps == len(lib.calls) + len(lib.submitted)
     for d, q in zip(done, qs):
         sid = int(d.level[0, 0])
         rs = lib.ranges[sid]
@@ -233,3 +249,23 @@ def test_coordinate_search_keeps_defaults_when_nothing_is_faster():
                                               space, autotune.DEFAULTS)
     assert knobs == {"leaf_size": 1, "beams_per_warp": 0}
     assert len(table) == 5  # the defaults and the four single-knob changes, one pass
+
+
+def test_server_submits_a_lone_small_query_whole_and_polls_it(monkeypatch):
+    # a query arriving to an idle server that fits one step is traced whole
+    # by one asynchronous submission, polled until it finishes, then read back
+    lib = _FakeLib()
+    for name in ("bt_scene_share", "bt_set_sources", "bt_set_microphones", "bt_beam_axes", "bt_set_directivity",
+                 "bt_trace_ranges", "bt_ranges_stats", "bt_read_levels", "bt_unload_scene", "bt_submit", "bt_poll"):
+        monkeypatch.setattr(serve.btrace, name, getattr(lib, name))
+    qs = synth.serving_queries(seed=3, n_queries=3, n_cities=1, rate_qps=1.0, level=2, max_sources=3,
+                               max_mics=1000)
+    srv = serve.Server(_FakeTracer(), [None], step_lineages=1 << 20)
+    for i, q in enumerate(qs):  # one at a time: the server is idle at every arrival
+        srv.submit(i, q, 0.0)
+        while srv.waiting or srv.active:
+            srv.step()
+    assert len(lib.submitted) == 3 and not lib.calls and not lib.live
+    assert [d.index for d in srv.done] == [0, 1, 2]
+    for d, q in zip(srv.done, qs):
+        assert lib.ranges[int(d.level[0, 0])] == [(0, len(q.src) * 20 * 4 ** q.level)]
