@@ -260,7 +260,7 @@ def test_server_submits_a_lone_small_query_whole_and_polls_it(monkeypatch):
         monkeypatch.setattr(serve.btrace, name, getattr(lib, name))
     qs = synth.serving_queries(seed=3, n_queries=3, n_cities=1, rate_qps=1.0, level=2, max_sources=3,
                                max_mics=1000)
-    srv = serve.Server(_FakeTracer(), [None], step_lineages=1 << 20)
+    srv = serve.Server(_FakeTracer(), [None], step_lineages=1 << 20, submit_alone=True)
     for i, q in enumerate(qs):  # one at a time: the server is idle at every arrival
         srv.submit(i, q, 0.0)
         while srv.waiting or srv.active:
