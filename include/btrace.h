@@ -208,7 +208,7 @@ int bt_beam_axes(bt_ctx *ctx, int32_t icosa_level, float *axes);
 /* Microphones of a scene (Section 4: a regular grid of receivers, filling a
  * volume or a plane).
  *   pos [n_m][3] float32, n_m <= 2^28.  They are binned on the device into an
- *   xy cell grid with up to 16 height layers (Section 3: microphones are
+ *   xy cell grid with up to 64 height layers (Section 3: microphones are
  *   partitioned with the geometry).  The scene's accumulated result starts
  *   at zero.  Errors: BT_E_INVALID for NaN/inf positions. */
 int bt_set_microphones(bt_ctx *ctx, int32_t scene_id, const float *pos, int64_t n_m);

