@@ -257,7 +257,8 @@ int bt_read_levels(bt_ctx *ctx, int32_t scene_id, double *level_db, double *inte
  *   start_normals  [n][3] float32 or NULL: for a ray leaving a reflector, the
  *                  reflector's normal; hits closer than t_eps_m to that plane
  *                  are then ignored, as in bt_trace
- *   t_out          [n] float32 hit distance, +inf on a miss
+ *   t_out          [n] float32 hit distance (formed in float64 along the
+ *                  normalised ray to the hit triangle's plane), +inf on a miss
  *   tri_out        [n] int32 index of the hit triangle in the scene's input
  *                  order, -1 on a miss; equal distances go to the lowest index
  * Hits with distance <= t_eps_m are ignored. */

@@ -1500,9 +1500,17 @@ __global__ void __launch_bounds__(128) k_cast(DevScene sc, const float *o, const
   Ray r = make_ray(O, df3_hi(D), t_eps, (float)dns);
   Best best;
   unsigned a = 0, b = 0;
-  int slot = closest_hit<kPMixed, false>(sc, r, RaySrc{&rh[0][t], &rl[0][t], 128, nullptr, &pend[0][t]}, dns, best, err, a, b,
-                                         sc.root);
-  t_out[i] = slot >= 0 ? (best.has64 ? (float)best.t64 : best.t) : kInf;
+  const RaySrc rs{&rh[0][t], &rl[0][t], 128, nullptr, &pend[0][t]};
+  int slot = closest_hit<kPMixed, false>(sc, r, rs, dns, best, err, a, b, sc.root);
+  // the reported distance is the float64 one to the hit triangle's plane
+  // along the float-pair ray (the search itself decides in float32)
+  double t64 = best.t64;
+  if (slot >= 0 && !best.has64) {
+    double3 o64, d64;
+    rs.get(o64, d64);
+    t64 = plane_t64(sc, slot, o64, d64);
+  }
+  t_out[i] = slot >= 0 ? (float)t64 : kInf;
   tri_out[i] = slot >= 0 ? best.id : -1;
 }
 

@@ -301,8 +301,10 @@ def test_cast_rays_match_oracle(tracer, oracle_mod, scene_name, district):
     mism = np.nonzero(ig != io)[0]
     assert len(mism) <= n * 1e-5, [(int(i), int(ig[i]), float(tg[i]), int(io[i]), float(to[i])) for i in mism[:10]]
     hit = (io >= 0) & (ig == io)
-    # float32 origins at 2 km carry 1.2e-4 m of rounding
-    assert np.allclose(tg[hit], to[hit], rtol=1e-5, atol=1e-3)
+    # both sides take the same float32 origins and directions; the library
+    # reports the float64 distance to the hit triangle's plane rounded to
+    # float32 (half an ulp: 6e-8 relative), the oracle its float64 one
+    assert np.allclose(tg[hit], to[hit], rtol=2e-7, atol=1e-6)
 
 
 def test_fp32_precision_mode(tracer, oracle_mod):
@@ -315,19 +317,19 @@ def test_fp32_precision_mode(tracer, oracle_mod):
 
 def test_district_full_size_sampled_microphones(tracer, oracle_mod, district):
     # the bench configuration itself: all 1,000 sources and all 250,000
-    # microphones on the GPU; the oracle computes a seeded sample of 2,000
-    # microphones from all sources (a microphone's result does not depend on
+    # microphones on the GPU; the oracle computes a seeded sample of 10,000
+    # microphones from all sources (the 99.9 % bar then allows 10 outliers) (a microphone's result does not depend on
     # the other microphones)
     import os
     g = gpu_run(tracer, district)
-    pick = np.sort(np.random.Generator(np.random.PCG64(33)).choice(len(district.mics), 2000, replace=False))
+    pick = np.sort(np.random.Generator(np.random.PCG64(33)).choice(len(district.mics), 10000, replace=False))
     r, L = oracle_levels(oracle_mod, district.with_mics(district.mics[pick]),
                          n_threads=max(1, os.cpu_count() or 1))
     s = assert_parity(g["level"][pick], L, "district, 1000 sources, sampled microphones")
     assert (g["cnt"][pick] == r["cnt"]).mean() >= 0.999
     assert (r["cnt"] > 0).mean() > 0.5
     assert abs(g["stats"]["segments"] / r["stats"]["segments"] - 1) < 1e-4
-    print("district full size, 2000 sampled microphones:", s)
+    print("district full size, 10000 sampled microphones:", s)
 
 
 # ------------------------------------------------------------- sub-domains

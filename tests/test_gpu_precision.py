@@ -145,13 +145,13 @@ def test_mixed64_parity(tracer, oracle_mod):
 def test_precision_matrix_district(tracer, oracle_mod):
     # The district configuration (all 1,000 sources, 250,000 microphones,
     # 4x4 sub-domains) in each precision; the oracle computes a seeded sample
-    # of 2,000 microphones from all sources.  Per variant: max and 99.9th
+    # of 10,000 microphones from all sources.  Per variant: max and 99.9th
     # percentile dB error over microphones and bands, the fraction within
     # 0.1 dB, microphones whose path count differs from the oracle's (the
     # visible trace of flipped hit or in-beam decisions), segment and hit
     # counts against the oracle's, and the trace's device time.
     w = synth.district(seed=2)
-    pick = np.sort(np.random.Generator(np.random.PCG64(33)).choice(len(w.mics), 2000, replace=False))
+    pick = np.sort(np.random.Generator(np.random.PCG64(33)).choice(len(w.mics), 10000, replace=False))
     r = oracle_mod.trace_workload(w.with_mics(w.mics[pick]), n_threads=max(1, os.cpu_count() or 1))
     L_ref = level_db(r["I"])
     rows = {}
