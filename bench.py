@@ -379,7 +379,9 @@ def run_ours(args, rank, world):
         units, kms = float(stats[-1]["emitted"]) / max(1, sl // args.steps), sk / max(1, sl)
     else:
         kernel = trace_kernel_name(tiles)
-        alg_bytes = 64.0 * cst["nodes_visited"] + 48.0 * cst["tris_tested"]
+        # a wide node visit reads four child boxes and four child codes (112 B),
+        # a triangle test the triangle's three vertices (48 B)
+        alg_bytes = 112.0 * cst["nodes_visited"] + 48.0 * cst["tris_tested"]
         bytes_per_launch = alg_bytes / max(1, cst["trace_launches"])
         achieved = bytes_per_launch / (tk / max(1, tl) * 1e-3) / 1e9
         counters = ncu_counters(kernel, args, tiles)

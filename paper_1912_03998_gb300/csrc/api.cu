@@ -240,7 +240,7 @@ bt::DevScene dev_scene(const SceneState &s) {
   memset(&d, 0, sizeof(d));
   d.n_tris = s.n_tris;
   d.root = s.root;
-  d.nodes = (const bt::Node *)s.nodes.p;
+  d.nodes = bt::hier_wide(s.nodes.p, s.n_tris);
   d.tris = (const bt::Tri *)s.tris.p;
   d.planes = (const bt::Plane *)s.planes.p;
   d.planes64 = (const bt::Plane64 *)s.planes64.p;
@@ -396,7 +396,7 @@ int ensure_tiled(bt_ctx *c, SceneState &s, int tx, int ty) {
       c->pool.push_back(c->scratch);
       c->scratch = fresh;
     }
-    TRY(ensure(c, s.t_nodes, sizeof(bt::Node) * (size_t)(P > 1 ? P - 1 : 1)));
+    TRY(ensure(c, s.t_nodes, bt::hier_bytes(P)));
     TRY(ensure(c, s.t_tris, sizeof(bt::Tri) * (size_t)P));
     TRY(ensure(c, s.t_planes, sizeof(bt::Plane) * (size_t)P));
     TRY(ensure(c, s.t_planes64, sizeof(bt::Plane64) * (size_t)P));
@@ -404,7 +404,7 @@ int ensure_tiled(bt_ctx *c, SceneState &s, int tx, int ty) {
     CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(bt::Counters), st));
     CK(bt::tiled_build(st, (const bt::Tri *)s.tris.p, (const bt::Plane *)s.planes.p, (const bt::Plane64 *)s.planes64.p,
                        (const bt::PlaneDF *)s.planes_df.p, s.n_tris, tg, c->d_box, (const uint32_t *)c->scratch.p, P,
-                       c->scratch.p, c->scratch.cap, (bt::Node *)s.t_nodes.p, (bt::Tri *)s.t_tris.p,
+                       c->scratch.p, c->scratch.cap, s.t_nodes.p, (bt::Tri *)s.t_tris.p,
                        (bt::Plane *)s.t_planes.p, (bt::Plane64 *)s.t_planes64.p, (bt::PlaneDF *)s.t_planes_df.p,
                        (int *)s.t_roots.p, &c->d_ctr->error));
   } else {
@@ -595,7 +595,7 @@ BT_API int bt_load_scene(bt_ctx *c, const float *verts, int64_t n_verts, const i
     if ((rc = ensure(c, c->stage_b, sizeof(int32_t) * 3 * (size_t)n_tris))) break;
     if ((rc = ensure(c, c->stage_c, (size_t)n_tris))) break;
     if ((rc = ensure(c, c->scratch, bt::build_scene_scratch_bytes(n_tris)))) break;
-    if ((rc = ensure(c, s.nodes, sizeof(bt::Node) * (size_t)(n_tris > 1 ? n_tris - 1 : 1)))) break;
+    if ((rc = ensure(c, s.nodes, bt::hier_bytes(n_tris)))) break;
     if ((rc = ensure(c, s.tris, sizeof(bt::Tri) * (size_t)n_tris))) break;
     if ((rc = ensure(c, s.planes, sizeof(bt::Plane) * (size_t)n_tris))) break;
     if ((rc = ensure(c, s.planes64, sizeof(bt::Plane64) * (size_t)n_tris))) break;
@@ -633,7 +633,7 @@ BT_API int bt_load_scene(bt_ctx *c, const float *verts, int64_t n_verts, const i
     return fail(c, BT_E_INVALID, "scene rejected: vertex index, material or coordinate out of range");
   }
   CKS(bt::build_scene(st, (const float *)c->stage_a.p, (const int32_t *)c->stage_b.p, n_tris,
-                      (const uint8_t *)c->stage_c.p, (bt::Node *)s.nodes.p, (bt::Tri *)s.tris.p,
+                      (const uint8_t *)c->stage_c.p, s.nodes.p, (bt::Tri *)s.tris.p,
                       (bt::Plane *)s.planes.p, (bt::Plane64 *)s.planes64.p, (bt::PlaneDF *)s.planes_df.p,
                       c->scratch.p, c->scratch.cap, box, &c->d_ctr->error));
   CKS(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(bt::Counters), cudaMemcpyDeviceToHost, st));
@@ -966,7 +966,7 @@ static int apply_leaf_size(bt_ctx *c, SceneState &s, const bt_trace_params *p, b
   if (want > 1 && n >= ((int64_t)1 << bt::kLeafShift))
     return fail(c, BT_E_INVALID, "leaf_size > 1 needs fewer than 2^%d leaves (the hierarchy has %lld)", bt::kLeafShift,
                 (long long)n);
-  CK(bt::collapse_leaves(c->stream, (bt::Node *)(tiled ? s.t_nodes.p : g.nodes.p), n, want));
+  CK(bt::collapse_leaves(c->stream, tiled ? s.t_nodes.p : g.nodes.p, n, want));
   have = want;
   return BT_OK;
 }
@@ -1025,7 +1025,7 @@ static int enqueue_trace(bt_ctx *c, int32_t id, const bt_trace_params *p) {
   fill_view(ta.v, *s, p, alpha_log2, has_alpha);
   if (tiled) {
     ta.v.sc.n_tris = s->n_pairs;
-    ta.v.sc.nodes = (const bt::Node *)s->t_nodes.p;
+    ta.v.sc.nodes = bt::hier_wide(s->t_nodes.p, s->n_pairs);
     ta.v.sc.tris = (const bt::Tri *)s->t_tris.p;
     ta.v.sc.planes = (const bt::Plane *)s->t_planes.p;
     ta.v.sc.planes64 = (const bt::Plane64 *)s->t_planes64.p;
@@ -1073,6 +1073,7 @@ static int enqueue_trace(bt_ctx *c, int32_t id, const bt_trace_params *p) {
     tga.tg = s->tg;
     tga.n_tiles = T;
     tga.roots = (const int *)s->t_roots.p;
+    tga.bin = (const bt::Node *)s->t_nodes.p;
     tga.qcap = qcap;
     tga.ring = (uint32_t *)c->t_ring.p;
     tga.seq = (unsigned *)c->t_seq.p;

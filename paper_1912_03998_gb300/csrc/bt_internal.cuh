@@ -10,20 +10,53 @@
 namespace bt {
 
 constexpr int kMaxBands = BT_MAX_BANDS;
-constexpr int kStackDepth = 64;        // BVH2 traversal stack (LBVH depth <= 64 for 30-bit keys + index)
+// traversal stack: a 4-wide step pushes at most three siblings, and the
+// 4-wide hierarchy is at most 32 levels deep (an LBVH over 64-bit keys at most
+// 64), plus the rests of multi-triangle leaves
+constexpr int kStackDepth = 112;
 constexpr float kInf = __builtin_huge_valf();
 
 // ------------------------------------------------------------------ layouts
-// BVH2 node, 64 bytes: both children's boxes, so one node fetch decides both.
-// Child index c >= 0: internal node; c < 0: a leaf, v = ~c: the leaf holds
-// leaf_count(v) triangles from slot leaf_slot(v) on (a leaf of one triangle
-// is ~slot; larger leaves come from collapsing small subtrees).
+// Binary LBVH node as built, 64 bytes: both children's boxes.  Child index
+// c >= 0: internal node; c < 0: a leaf, v = ~c: the leaf holds leaf_count(v)
+// triangles from slot leaf_slot(v) on (a leaf of one triangle is ~slot;
+// larger leaves come from collapsing small subtrees).  The traversal reads
+// the 4-wide form below; the sub-domain trace's tile walk tests the binary
+// root nodes.
 struct __align__(16) Node {
   float4 lxy;  // left  lo.x, hi.x, lo.y, hi.y
   float4 rxy;  // right lo.x, hi.x, lo.y, hi.y
   float4 lrz;  // left lo.z, hi.z, right lo.z, hi.z
-  int4 child;  // left, right, parent, unused
+  int4 child;  // left, right, parent, far end of the node's key range
 };
+
+// 4-wide node, 128 bytes (one cache line), what the traversal reads: the
+// boxes of up to four children, lane c of each float4 for child c, and their
+// codes (as in Node; kNoChild for an unused lane).  Wide node i stands for
+// binary node i and lists its grandchildren -- a child that is a leaf stands
+// for itself -- so a traversal from any binary node visits the wide nodes of
+// every other level below it.
+constexpr int kNoChild = (int)0x80000000;
+struct __align__(128) Node4 {
+  float4 lox, hix, loy, hiy, loz, hiz;
+  int4 child;
+  int4 unused;
+};
+static_assert(sizeof(Node4) == 128, "wide node layout");
+
+// A hierarchy's buffer: the binary LBVH (n_leaves - 1 nodes), then its wide
+// form at a 256-byte boundary (one Node4 per binary node).
+__host__ __device__ inline size_t hier_binary_bytes(int64_t n_leaves) {
+  const size_t m = (size_t)(n_leaves > 1 ? n_leaves - 1 : 1);
+  return (sizeof(Node) * m + 255) & ~(size_t)255;
+}
+__host__ __device__ inline size_t hier_bytes(int64_t n_leaves) {
+  const size_t m = (size_t)(n_leaves > 1 ? n_leaves - 1 : 1);
+  return hier_binary_bytes(n_leaves) + sizeof(Node4) * m;
+}
+__host__ __device__ inline Node4 *hier_wide(void *base, int64_t n_leaves) {
+  return (Node4 *)((char *)base + hier_binary_bytes(n_leaves));
+}
 
 constexpr int kLeafShift = 29;  // leaf code: slot in bits 0..28, count - 1 above
 constexpr int kMaxLeafSize = 4;
@@ -73,6 +106,7 @@ struct TiledArgs {
   TileGrid tg;
   int n_tiles;
   const int *roots;         // [n_tiles] subtree root per tile (INT_MIN: empty tile)
+  const Node *bin;          // the binary LBVH the wide nodes come from (the tile walk's root tests)
   unsigned qcap;            // ring slots per tile, a power of two; also the cap on lineages in flight
   uint32_t *ring;           // [n_tiles][kStateRows][qcap]
   unsigned *seq;            // [n_tiles][qcap], zero at launch
@@ -85,7 +119,7 @@ struct TiledArgs {
 struct DevScene {
   int64_t n_tris;
   int root;              // root child code: internal index >= 0, or ~leaf for one triangle (unused when n_tris == 0)
-  const Node *nodes;     // n_tris - 1 internal nodes
+  const Node4 *nodes;    // n_tris - 1 wide nodes (hier_wide)
   const Tri *tris;       // n_tris, leaf order
   const Plane *planes;   // n_tris, leaf order
   const Plane64 *planes64;  // n_tris, leaf order: float64 unit normal and n . v0
@@ -461,7 +495,7 @@ cudaError_t validate_scene(cudaStream_t st, const float *d_verts, int64_t n_vert
                            const int32_t *d_tris, int64_t n_tris, const uint8_t *d_mat, int n_mat,
                            float *d_box /*lo xyz, hi xyz*/, int *d_error);
 cudaError_t build_scene(cudaStream_t st, const float *d_verts, const int32_t *d_tris, int64_t n_tris,
-                        const uint8_t *d_mat, Node *d_nodes, Tri *d_tris_out, Plane *d_planes,
+                        const uint8_t *d_mat, void *d_hier, Tri *d_tris_out, Plane *d_planes,
                         Plane64 *d_planes64, PlaneDF *d_planes_df, void *d_scratch, size_t scratch_bytes,
                         const float *d_box, int *d_error);
 cudaError_t launch_beam_table(cudaStream_t st, int level, float *table);
@@ -470,13 +504,16 @@ size_t build_tiled_scratch_bytes(int64_t n_src, int64_t n_pairs);
 cudaError_t tiled_count(cudaStream_t st, const Tri *src, int64_t n_src, const TileGrid &tg, uint32_t *offs);
 cudaError_t tiled_build(cudaStream_t st, const Tri *src, const Plane *sp, const Plane64 *sp64, const PlaneDF *spdf,
                         int64_t n_src, const TileGrid &tg, const float *d_box, const uint32_t *offs, int64_t n_pairs,
-                        void *scratch, size_t scratch_bytes, Node *nodes, Tri *tris, Plane *planes,
+                        void *scratch, size_t scratch_bytes, void *hier, Tri *tris, Plane *planes,
                         Plane64 *planes64, PlaneDF *planes_df, int *roots, int *d_error);
 size_t build_scene_scratch_bytes(int64_t n_tris);
 // Rewrite the child links of a built LBVH (n_leaves leaves) so that every
 // subtree of at most leaf_size triangles is one leaf; any earlier collapse is
-// undone first, so the call can change the leaf size back and forth.
-cudaError_t collapse_leaves(cudaStream_t st, Node *nodes, int64_t n_leaves, int leaf_size);
+// undone first, so the call can change the leaf size back and forth.  The
+// wide form is rebuilt after.  `hier`: the hierarchy's buffer (hier_bytes).
+cudaError_t collapse_leaves(cudaStream_t st, void *hier, int64_t n_leaves, int leaf_size);
+// (Re)build the wide form of the binary LBVH in `hier`.
+cudaError_t widen(cudaStream_t st, void *hier, int64_t n_leaves);
 cudaError_t mic_box(cudaStream_t st, const float *d_pos, int64_t n_m, float *d_box, int *d_error);
 cudaError_t build_mics(cudaStream_t st, const float *d_pos, int64_t n_m, int nx, int ny, int nz,
                        const float *d_box, MicGrid *d_grid, float4 *d_sorted, int *d_cell_start, void *d_scratch,

@@ -403,12 +403,67 @@ __global__ void k_collapse_leaves(Node *nodes, int n_internal, int leaf_size) {
   nodes[p].child.y = out[1];
 }
 
-cudaError_t collapse_leaves(cudaStream_t st, Node *nodes, int64_t n_leaves, int leaf_size) {
+// The 4-wide form the traversal reads, one thread per binary node: wide node
+// p lists binary node p's grandchildren -- a child that is a leaf stands for
+// itself -- with the boxes the binary nodes hold for them (already grown, see
+// k_lbvh_boxes), so a search from any binary node tests the same boxes as a
+// binary search would, two levels per node fetch.  Child order: left
+// subtree first.
+__global__ void k_widen(const Node *nodes, int n_internal, Node4 *wide) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_internal) return;
+  const Node b = nodes[p];
+  float bx[4][6];  // lo.x, hi.x, lo.y, hi.y, lo.z, hi.z per child
+  int code[4];
+  int m = 0;
+  auto put = [&](float4 xy, float z0, float z1, int c) {
+    bx[m][0] = xy.x; bx[m][1] = xy.y; bx[m][2] = xy.z; bx[m][3] = xy.w; bx[m][4] = z0; bx[m][5] = z1;
+    code[m++] = c;
+  };
+#pragma unroll
+  for (int side = 0; side < 2; side++) {
+    const int c = side == 0 ? b.child.x : b.child.y;
+    if (c < 0) {
+      if (side == 0) put(b.lxy, b.lrz.x, b.lrz.y, c);
+      else put(b.rxy, b.lrz.z, b.lrz.w, c);
+    } else {
+      const Node g = nodes[c];
+      put(g.lxy, g.lrz.x, g.lrz.y, g.child.x);
+      put(g.rxy, g.lrz.z, g.lrz.w, g.child.y);
+    }
+  }
+  for (int q = m; q < 4; q++) {
+    for (int k = 0; k < 6; k++) bx[q][k] = 0.0f;
+    code[q] = kNoChild;
+  }
+  Node4 w;
+  w.lox = make_float4(bx[0][0], bx[1][0], bx[2][0], bx[3][0]);
+  w.hix = make_float4(bx[0][1], bx[1][1], bx[2][1], bx[3][1]);
+  w.loy = make_float4(bx[0][2], bx[1][2], bx[2][2], bx[3][2]);
+  w.hiy = make_float4(bx[0][3], bx[1][3], bx[2][3], bx[3][3]);
+  w.loz = make_float4(bx[0][4], bx[1][4], bx[2][4], bx[3][4]);
+  w.hiz = make_float4(bx[0][5], bx[1][5], bx[2][5], bx[3][5]);
+  w.child = make_int4(code[0], code[1], code[2], code[3]);
+  w.unused = make_int4(0, 0, 0, 0);
+  wide[p] = w;
+}
+
+cudaError_t widen(cudaStream_t st, void *hier, int64_t n_leaves) {
   if (n_leaves < 2) return cudaSuccess;
   const int n = (int)(n_leaves - 1);
-  k_collapse_leaves<<<(n + 255) / 256, 256, 0, st>>>(nodes, n, leaf_size);
+  k_widen<<<(n + 255) / 256, 256, 0, st>>>((const Node *)hier, n, hier_wide(hier, n_leaves));
   note_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t collapse_leaves(cudaStream_t st, void *hier, int64_t n_leaves, int leaf_size) {
+  if (n_leaves < 2) return cudaSuccess;
+  const int n = (int)(n_leaves - 1);
+  k_collapse_leaves<<<(n + 255) / 256, 256, 0, st>>>((Node *)hier, n, leaf_size);
+  note_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return widen(st, hier, n_leaves);
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -437,10 +492,11 @@ cudaError_t validate_scene(cudaStream_t st, const float *d_verts, int64_t n_vert
 // Scene build, run only after validate_scene() reported no error: every
 // index and material is then in range and every coordinate finite.
 cudaError_t build_scene(cudaStream_t st, const float *d_verts, const int32_t *d_tris, int64_t n_tris,
-                        const uint8_t *d_mat, Node *d_nodes, Tri *d_tris_out, Plane *d_planes,
+                        const uint8_t *d_mat, void *d_hier, Tri *d_tris_out, Plane *d_planes,
                         Plane64 *d_planes64, PlaneDF *d_planes_df, void *d_scratch, size_t scratch_bytes,
                         const float *d_box, int *d_error) {
   if (n_tris == 0) return cudaSuccess;
+  Node *const d_nodes = (Node *)d_hier;
   if (scratch_bytes < build_scene_scratch_bytes(n_tris)) return cudaErrorInvalidValue;
   int n = (int)n_tris;
   char *s = (char *)d_scratch;
@@ -467,6 +523,8 @@ cudaError_t build_scene(cudaStream_t st, const float *d_verts, const int32_t *d_
     cudaMemsetAsync(flags, 0, sizeof(unsigned) * m, st);
     k_lbvh_boxes<<<blocks, threads, 0, st>>>(d_tris_out, n, d_nodes, leaf_parent, aux, flags, d_error);
     note_launches(2);
+    cudaError_t e2 = widen(st, d_hier, n_tris);
+    if (e2 != cudaSuccess) return e2;
   }
   return cudaGetLastError();
 }
@@ -590,9 +648,10 @@ cudaError_t tiled_count(cudaStream_t st, const Tri *src, int64_t n_src, const Ti
 // them, pack the leaves and find the tile roots.
 cudaError_t tiled_build(cudaStream_t st, const Tri *src, const Plane *sp, const Plane64 *sp64, const PlaneDF *spdf,
                         int64_t n_src, const TileGrid &tg, const float *d_box, const uint32_t *offs, int64_t n_pairs,
-                        void *scratch, size_t scratch_bytes, Node *nodes, Tri *tris, Plane *planes,
+                        void *scratch, size_t scratch_bytes, void *hier, Tri *tris, Plane *planes,
                         Plane64 *planes64, PlaneDF *planes_df, int *roots, int *d_error) {
   if (scratch_bytes < build_tiled_scratch_bytes(n_src, n_pairs)) return cudaErrorInvalidValue;
+  Node *const nodes = (Node *)hier;
   int n = (int)n_src, P = (int)n_pairs, T = tg.tx * tg.ty;
   char *s = (char *)scratch + align256(4 * (size_t)(n_src + 1));
   size_t p4 = align256(4 * (size_t)P);
@@ -635,7 +694,9 @@ cudaError_t tiled_build(cudaStream_t st, const Tri *src, const Plane *sp, const 
   k_tile_roots<<<bp, th, 0, st>>>(key64, nodes, P, roots);
   note_launches(1);
   (void)n;
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return widen(st, hier, P);
 }
 
 // ------------------------------------------------------------ microphones

@@ -324,6 +324,17 @@ __device__ __forceinline__ void settle_search(const DevScene &sc, const Ray &r, 
   }
 }
 
+// Order two (distance, child) pairs by distance.
+__device__ __forceinline__ void sort_pair(float &ka, int &ca, float &kb, int &cb) {
+  const bool sw = kb < ka;
+  const float k = sw ? kb : ka;
+  const int c = sw ? cb : ca;
+  kb = sw ? ka : kb;
+  cb = sw ? ca : cb;
+  ka = k;
+  ca = c;
+}
+
 // A closest-hit search that can stop after any node and resume later: its
 // state is the current node, the stack (an array the caller keeps) and the
 // best hit so far.
@@ -340,21 +351,23 @@ struct HitSearch {
     best.t64 = 0.0;
     best.has64 = false;
   }
-  // One node of the traversal (nearer child first, both children's boxes in
-  // one fetch) and the leaves it exposes.  False once the search is over.
+  // One wide node of the traversal (the boxes of its up to four children in
+  // one 128-byte fetch; the nearest child hit next, the others pushed
+  // farthest first) and the leaves it exposes.  False once the search is
+  // over.
   template <int kP, bool kCount, bool kLeaves>
-  __device__ __forceinline__ bool step(const DevScene &sc, const Node *nodes, const Tri *tris, int64_t n_tri,
+  __device__ __forceinline__ bool step(const DevScene &sc, const Node4 *nodes, const Tri *tris, int64_t n_tri,
                                        const Ray &r, const RaySrc &rs, double dns64, int *stack, int *err,
                                        unsigned &n_nodes, unsigned &n_tris, float tlim) {
-    if (n_tri == 0 || node == (int)0x80000000) return false;
-    // up to two leaves per step (leaf codes v: see Node)
-    int c0 = -1, c1 = -1, nc = 0;
+    if (n_tri == 0 || node == kNoChild) return false;
+    // the leaves this step tests: child codes in `lc`, the lanes in `lm`
+    int4 lc = make_int4(node, 0, 0, 0);
+    unsigned lm = 0;
     bool more = true;
     if (node < 0) {
       // a leaf: the root of a one-leaf hierarchy, or (kLeaves) the rest of a
       // larger leaf put back on the stack (below)
-      c0 = ~node;
-      nc = 1;
+      lm = 1;
       if (kLeaves && sp > 0) node = stack[--sp];
       else more = false;
     } else {
@@ -364,27 +377,44 @@ struct HitSearch {
         atomicExch(err, BT_E_TIMEOUT);
         return false;
       }
-      const Node *nd = nodes + node;
+      const Node4 *nd = nodes + node;
       if (kCount) n_nodes++;
-      float4 lxy = __ldg(&nd->lxy), rxy = __ldg(&nd->rxy), lrz = __ldg(&nd->lrz);
-      int2 ch = __ldg((const int2 *)&nd->child);
+      const float4 lox = __ldg(&nd->lox), hix = __ldg(&nd->hix), loy = __ldg(&nd->loy), hiy = __ldg(&nd->hiy);
+      const float4 loz = __ldg(&nd->loz), hiz = __ldg(&nd->hiz);
+      const int4 ch = __ldg(&nd->child);
       // in MIXED and FP64 mode near ties must still be visited
-      float tmax = fminf(kP != kPF32 ? best.t + (1e-5f * fabsf(best.t) + 1e-4f) : best.t, tlim);
-      float tl, tr;
+      const float tmax = fminf(kP != kPF32 ? best.t + (1e-5f * fabsf(best.t) + 1e-4f) : best.t, tlim);
       const float3 oi = origin_scaled(r);
-      bool hl = slab(r, oi, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, tmax, tl);
-      bool hr = slab(r, oi, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, tmax, tr);
-      if (hl && ch.x < 0) { c0 = ~ch.x; nc = 1; hl = false; }
-      if (hr && ch.y < 0) { if (nc) c1 = ~ch.y; else c0 = ~ch.y; nc++; hr = false; }
-      if (hl && hr) {
-        bool lf = tl <= tr;
-        if (sp < kStackDepth) stack[sp++] = lf ? ch.y : ch.x;
-        else atomicExch(err, BT_E_QUEUE_FULL);
-        node = lf ? ch.x : ch.y;
-      } else if (hl) {
-        node = ch.x;
-      } else if (hr) {
-        node = ch.y;
+      float k0, k1, k2, k3;
+      const bool h0 = slab(r, oi, lox.x, hix.x, loy.x, hiy.x, loz.x, hiz.x, tmax, k0) && ch.x != kNoChild;
+      const bool h1 = slab(r, oi, lox.y, hix.y, loy.y, hiy.y, loz.y, hiz.y, tmax, k1) && ch.y != kNoChild;
+      const bool h2 = slab(r, oi, lox.z, hix.z, loy.z, hiy.z, loz.z, hiz.z, tmax, k2) && ch.z != kNoChild;
+      const bool h3 = slab(r, oi, lox.w, hix.w, loy.w, hiy.w, loz.w, hiz.w, tmax, k3) && ch.w != kNoChild;
+      lc = ch;
+      lm = (unsigned)(h0 && ch.x < 0) | (unsigned)(h1 && ch.y < 0) << 1 | (unsigned)(h2 && ch.z < 0) << 2 |
+           (unsigned)(h3 && ch.w < 0) << 3;
+      // inner children hit, nearest first (a sorting network on the entry
+      // distances; misses sort last)
+      int c0 = ch.x, c1 = ch.y, c2 = ch.z, c3 = ch.w;
+      k0 = h0 && c0 >= 0 ? k0 : kInf;
+      k1 = h1 && c1 >= 0 ? k1 : kInf;
+      k2 = h2 && c2 >= 0 ? k2 : kInf;
+      k3 = h3 && c3 >= 0 ? k3 : kInf;
+      const int ni = (k0 < kInf) + (k1 < kInf) + (k2 < kInf) + (k3 < kInf);
+      sort_pair(k0, c0, k1, c1);
+      sort_pair(k2, c2, k3, c3);
+      sort_pair(k0, c0, k2, c2);
+      sort_pair(k1, c1, k3, c3);
+      sort_pair(k1, c1, k2, c2);
+      if (ni > 0) {
+        if (sp + ni - 1 <= kStackDepth) {
+          if (ni > 3) stack[sp++] = c3;
+          if (ni > 2) stack[sp++] = c2;
+          if (ni > 1) stack[sp++] = c1;
+        } else {
+          atomicExch(err, BT_E_QUEUE_FULL);
+        }
+        node = c0;
       } else if (sp > 0) {
         node = stack[--sp];
       } else {
@@ -392,12 +422,14 @@ struct HitSearch {
       }
     }
 #pragma unroll 1
-    for (int c = 0; c < nc; c++) {
-      const int v = c == 0 ? c0 : c1;
+    while (lm) {
+      const int c = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const int v = ~(c == 0 ? lc.x : c == 1 ? lc.y : c == 2 ? lc.z : lc.w);
       if (kLeaves && (v >> kLeafShift)) {
         // a leaf of several triangles: its first now, the rest as a leaf of
         // one triangle fewer at a later step, so that a step still tests at
-        // most two triangles
+        // most one triangle per leaf
         const int rest = ~((leaf_slot(v) + 1) | (((v >> kLeafShift) - 1) << kLeafShift));
         if (!more) {
           node = rest;
@@ -422,7 +454,7 @@ __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, Ray
   // the hot fields in registers: in a batch `sc` lives in device memory and
   // would otherwise be re-read on every node
   const int64_t n_tri = sc.n_tris;
-  const Node *const nodes = sc.nodes;
+  const Node4 *const nodes = sc.nodes;
   const Tri *const tris = sc.tris;
   int stack[kStackDepth];
   HitSearch hs;
@@ -971,7 +1003,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
       const SceneView &v = kBatch ? a.views[vi] : a.v;
       const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), v.t_eps, ls.dns);
       const int64_t n_tri = v.sc.n_tris;
-      const Node *const nodes = v.sc.nodes;
+      const Node4 *const nodes = v.sc.nodes;
       const Tri *const tris = v.sc.tris;
       while (true) {
         if (searching &&
@@ -1082,12 +1114,13 @@ __device__ __forceinline__ void load_state(const uint32_t *S, size_t c, LineageS
 }
 
 // False if the ray cannot reach any triangle under a subtree root: an empty
-// tile, or both child boxes of the root missed (the test the traversal itself
-// would make first).  A single-triangle root is always reachable.
-__device__ __forceinline__ bool root_reachable(const DevScene &sc, int root, const Ray &r) {
-  if (root == (int)0x80000000) return false;
+// tile, or both child boxes of the root missed (the test a binary traversal
+// would make first; the root's binary node, half the bytes of its wide one).
+// A single-triangle root is always reachable.
+__device__ __forceinline__ bool root_reachable(const Node *bin, int root, const Ray &r) {
+  if (root == kNoChild) return false;
   if (root < 0) return true;
-  const Node *nd = sc.nodes + root;
+  const Node *nd = bin + root;
   float4 lxy = __ldg(&nd->lxy), rxy = __ldg(&nd->rxy), lrz = __ldg(&nd->lrz);
   float tl, tr;
   return slab(r, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, kInf, tl) ||
@@ -1298,7 +1331,7 @@ __global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_ti
             if (tey <= tex) iy += r.d.y > 0.0f ? 1 : -1;
             leaves = ix < 0 || ix >= tg.tx || iy < 0 || iy >= tg.ty;
           }
-          if (leaves || root_reachable(v.sc, __ldg(&ta.roots[iy * tg.tx + ix]), r)) break;
+          if (leaves || root_reachable(ta.bin, __ldg(&ta.roots[iy * tg.tx + ix]), r)) break;
         }
         if (leaves) fin = true;
         else next = iy * tg.tx + ix;
@@ -1421,7 +1454,7 @@ __global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_ti
     {
       const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), v.t_eps, ls.dns);
       const int64_t n_tri = v.sc.n_tris;
-      const Node *const nodes = v.sc.nodes;
+      const Node4 *const nodes = v.sc.nodes;
       const Tri *const tris = v.sc.tris;
       while (true) {
         if (searching && !hs.step<kP, kCount, kLeaves>(v.sc, nodes, tris, n_tri, r, rs, ls.dns64, stack,
