@@ -223,9 +223,19 @@ __device__ __forceinline__ bool pend_add(const RaySrc &rs, int entry) {
 // to the lowest original triangle id).  With MIXED/FP64, `rs` gives the
 // float-pair or float64 ray that the float32 ray `r` rounds, read only on the
 // float64 paths.  Hits beyond `tlim` are ignored.
+// An event count of a warp, in shared memory: every lane that passes an
+// increment adds one, the lanes that execute it together with one atomic.
+struct WarpCount {
+  unsigned *p;
+  __device__ __forceinline__ void operator++(int) const {
+    const unsigned m = __activemask();
+    if ((int)(threadIdx.x & 31u) == __ffs(m) - 1) atomicAdd(p, (unsigned)__popc(m));
+  }
+};
+
 template <int kP, bool kCount>
 __device__ __forceinline__ void consider_tri(const DevScene &sc, const Tri *tris, const Ray &r, const RaySrc &rs,
-                                             double dns64, Best &best, int slot, unsigned &n_tris, float tlim) {
+                                             double dns64, Best &best, int slot, const WarpCount &n_tris, float tlim) {
   constexpr bool kDefer = Prec<kP>::defer, kAll64 = Prec<kP>::all64;
   if (kCount) n_tris++;
   const Tri *tp = tris + slot;
@@ -358,7 +368,7 @@ struct HitSearch {
   template <int kP, bool kCount, bool kLeaves>
   __device__ __forceinline__ bool step(const DevScene &sc, const Node4 *nodes, const Tri *tris, int64_t n_tri,
                                        const Ray &r, const RaySrc &rs, double dns64, int *stack, int *err,
-                                       unsigned &n_nodes, unsigned &n_tris, float tlim) {
+                                       const WarpCount &n_nodes, const WarpCount &n_tris, float tlim) {
     if (n_tri == 0 || node == kNoChild) return false;
     // the leaves this step tests: child codes in `lc`, the lanes in `lm`
     int4 lc = make_int4(node, 0, 0, 0);
@@ -449,7 +459,7 @@ struct HitSearch {
 // Closest accepted hit of the ray in the BVH under `root`; the leaf slot or -1.
 template <int kP, bool kCount>
 __device__ __forceinline__ int closest_hit(const DevScene &sc, const Ray &r, RaySrc rs, double dns64, Best &best,
-                                           int *err, unsigned &n_nodes, unsigned &n_tris,
+                                           int *err, const WarpCount &n_nodes, const WarpCount &n_tris,
                                            int root, float tlim = kInf) {
   // the hot fields in registers: in a batch `sc` lives in device memory and
   // would otherwise be re-read on every node
@@ -489,19 +499,21 @@ __device__ __forceinline__ bool may_reach_slab(float3 n0, float3 n1, float3 n2, 
 
 // Warp-aggregated append of a segment record.
 __device__ __forceinline__ void emit_segment(const TraceArgs &a, const Seg &s, bool emit,
-                                             unsigned &n_emit) {
+                                             const WarpCount &n_emit) {
   unsigned mask = __activemask();
   unsigned bal = __ballot_sync(mask, emit);
   if (!bal) return;
   int leader = __ffs(bal) - 1;
   unsigned long long base = 0;
-  if ((int)lane_id() == leader) base = atomicAdd(a.seg_count, (unsigned long long)__popc(bal));
+  if ((int)lane_id() == leader) {
+    base = atomicAdd(a.seg_count, (unsigned long long)__popc(bal));
+    atomicAdd(n_emit.p, (unsigned)__popc(bal));
+  }
   base = __shfl_sync(mask, base, leader);
   if (emit) {
     unsigned long long idx = base + __popc(bal & ((1u << lane_id()) - 1u));
     if (idx < a.seg_capacity) a.segs[idx] = s;
     else atomicExch(&a.ctr->error, BT_E_QUEUE_FULL);
-    n_emit++;
   }
 }
 
@@ -524,7 +536,6 @@ struct LineageSmem {
   float p[kMaxBands][kTraceThreads];  // band power W_b prod(r_b)
   float st[4][kTraceThreads];         // start plane (relative to the apex)
   int pend[Prec<kP>::defer ? kPend + 1 : 1][kTraceThreads];  // candidates left to float64
-  unsigned cnt[kNumCounts][kTraceThreads];  // per-lane event counts of the launch
 };
 
 template <int kP>
@@ -642,19 +653,18 @@ struct LaneState {
   double dns64;
 };
 
-// Per-lane event counts of one launch, kept in the lane's shared-memory
-// column rather than in registers.  A lane handles at most a few thousand
-// segments per launch, so even the node count stays far below 2^32; the warp
-// sums are formed in 64-bit.
+// Event counts of one launch per warp, in shared memory rather than in
+// registers or per lane (4 KB less shared memory a block).  A warp handles at
+// most some ten thousand segments per launch, so even its node count stays
+// far below 2^32; the launch totals are formed in 64-bit.
 struct TraceCounts {
-  unsigned *p;  // &cnt[0][lane's column]
-  __device__ unsigned &operator[](int i) const { return p[i * kTraceThreads]; }
+  unsigned *p;  // the warp's counts
+  __device__ WarpCount operator[](int i) const { return WarpCount{p + i}; }
 };
-template <int kP>
-__device__ __forceinline__ TraceCounts init_counts(LineageSmem<kP> &sm, int t) {
-  [[maybe_unused]] constexpr bool kPairs = Prec<kP>::pairs, kChain64 = Prec<kP>::chain64, kDefer = Prec<kP>::defer;
-  for (int q = 0; q < kNumCounts; q++) sm.cnt[q][t] = 0u;
-  return TraceCounts{&sm.cnt[0][t]};
+__device__ __forceinline__ TraceCounts init_counts(unsigned (*wc)[kNumCounts], int t) {
+  if ((t & 31) < kNumCounts) wc[t >> 5][t & 31] = 0u;
+  __syncwarp();
+  return TraceCounts{wc[t >> 5]};
 }
 
 // A segment is resolved: its axis ray hit triangle `slot` (or escaped, slot
@@ -827,10 +837,9 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, const SceneVi
 
 __device__ __forceinline__ void flush_counts(const TraceArgs &a, const TraceCounts &cn, bool count_work) {
   // warp sums in 64-bit
+  __syncwarp();
   unsigned long long v[kNumCounts];
-  for (int q = 0; q < kNumCounts; q++) v[q] = cn[q];
-  for (int o = 16; o > 0; o >>= 1)
-    for (int q = 0; q < kNumCounts; q++) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  for (int q = 0; q < kNumCounts; q++) v[q] = cn.p[q];
   if (lane_id() == 0) {
     if (count_work) {
       atomicAdd(&a.ctr->nodes_visited, v[kCNodes]);
@@ -956,7 +965,8 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
     for (int i = t; i < a.n_views; i += kTraceThreads) view_base[i] = a.views[i].lineage_base;
     __syncthreads();
   }
-  const TraceCounts cn = init_counts(sm, t);
+  __shared__ unsigned wcount[kTraceThreads / 32][kNumCounts];
+  const TraceCounts cn = init_counts(wcount, t);
   LaneState ls = {-1, 0, -1, 0.0f, 0.0};
   int vi = 0;  // this lane's scene view
   bool done = false, searching = false, pending = false;
@@ -1275,7 +1285,8 @@ __global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_ti
   const unsigned below = (1u << lane) - 1u;
   const SceneView &v = a.v;
   const TileGrid &tg = ta.tg;  // read from parameter space, not held in registers
-  const TraceCounts cn = init_counts(sm, t);
+  __shared__ unsigned wcount[kTraceThreads / 32][kNumCounts];
+  const TraceCounts cn = init_counts(wcount, t);
   const size_t qc = ta.qcap;
   const unsigned qmask = ta.qcap - 1u;
   int *const used = ta.ctl + 3 * ta.n_tiles;
@@ -1532,7 +1543,7 @@ __global__ void __launch_bounds__(128) k_cast(DevScene sc, const float *o, const
   rl[3][t] = D.x.lo; rl[4][t] = D.y.lo; rl[5][t] = D.z.lo;
   Ray r = make_ray(O, df3_hi(D), t_eps, (float)dns);
   Best best;
-  unsigned a = 0, b = 0;
+  const WarpCount a{nullptr}, b{nullptr};
   const RaySrc rs{&rh[0][t], &rl[0][t], 128, nullptr, &pend[0][t]};
   int slot = closest_hit<kPMixed, false>(sc, r, rs, dns, best, err, a, b, sc.root);
   // the reported distance is the float64 one to the hit triangle's plane
