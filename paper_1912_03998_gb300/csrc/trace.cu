@@ -782,25 +782,23 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, const SceneVi
     PlaneDF pd = v.sc.planes_df[slot];
     const df3 n = df3{df{pd.hi.x, pd.lo.x}, df{pd.hi.y, pd.lo.y}, df{pd.hi.z, pd.lo.z}};
     {
-      // the hit point on the plane (the reflected beam's origin), then the
-      // mirrored axis
+      // the hit point on the plane (the reflected beam's origin)
       const df3 O = ld_df3(sm, kRowO, t), D = ld_df3(sm, kRowD, t);
       const df th = best.has64 ? d_to_df(best.t64)
                                : df_div(df_sub(df{pd.hi.w, pd.lo.w}, df3_dot(n, O)), df3_dot(n, D));
       st_df3(sm, kRowO, t, df3_add(O, df3_scale(D, th)));
-      st_df3(sm, kRowD, t, df3_mirror(D, n));
     }
-    asm volatile("" ::: "memory");
-    {
-      // the image source
-      const df3 A = ld_df3(sm, kRowA, t);
-      const df da = df3_dot(df3_sub(A, mkdf3(pv0)), n);
-      st_df3(sm, kRowA, t, df3_sub(A, df3_scale(n, df{2.0f * da.hi, 2.0f * da.lo})));
-    }
+    // the cone normals, the axis and the apex (the image source) mirrored
+    // by one copy of the code: v - 2 ((v - p) . n) n with p = 0 for the
+    // directions and p = v0, a point of the plane, for the apex
+    const df3 p0 = mkdf3(pv0);
 #pragma unroll 1
-    for (int j = 0; j < 3; j++) {
+    for (int j = 0; j < 5; j++) {
       asm volatile("" ::: "memory");
-      st_df3(sm, kRowN + 3 * j, t, df3_mirror(ld_df3(sm, kRowN + 3 * j, t), n));
+      const int row = j < 3 ? kRowN + 3 * j : (j == 3 ? kRowD : kRowA);
+      const df3 v = ld_df3(sm, row, t);
+      const df k = df3_dot(j == 4 ? df3_sub(v, p0) : v, n);
+      st_df3(sm, row, t, df3_sub(v, df3_scale(n, df{2.0f * k.hi, 2.0f * k.lo})));
     }
     asm volatile("" ::: "memory");
     const df3 D = ld_df3(sm, kRowD, t);
