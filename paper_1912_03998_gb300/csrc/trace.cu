@@ -792,22 +792,26 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, const SceneVi
     // by one copy of the code: v - 2 ((v - p) . n) n with p = 0 for the
     // directions and p = v0, a point of the plane, for the apex
     const df3 p0 = mkdf3(pv0);
+    df kd = df{0.0f, 0.0f}, ka = df{0.0f, 0.0f};
 #pragma unroll 1
     for (int j = 0; j < 5; j++) {
       asm volatile("" ::: "memory");
       const int row = j < 3 ? kRowN + 3 * j : (j == 3 ? kRowD : kRowA);
       const df3 v = ld_df3(sm, row, t);
       const df k = df3_dot(j == 4 ? df3_sub(v, p0) : v, n);
+      if (j == 3) kd = k;
+      if (j == 4) ka = k;
       st_df3(sm, row, t, df3_sub(v, df3_scale(n, df{2.0f * k.hi, 2.0f * k.lo})));
     }
     asm volatile("" ::: "memory");
-    const df3 D = ld_df3(sm, kRowD, t);
-    const df dn = df3_dot(n, D);
-    ls.dns64 = fabs((double)dn.hi + (double)dn.lo);
+    // |n . D| is the same for the axis and its mirror image, and the image
+    // source lies as far behind the plane as the apex in front of it
+    ls.dns64 = fabs((double)kd.hi + (double)kd.lo);
     ls.dns = (float)ls.dns64;
-    Dn = df3_hi(D);
-    float3 sn = dot3(pn, Dn) > 0.0f ? pn : pn * -1.0f;
-    float sw = df3_dot(mkdf3(sn), df3_sub(mkdf3(pv0), ld_df3(sm, kRowA, t))).hi;
+    Dn = ld_hi3(sm, kRowD, t);
+    const bool fwd = dot3(pn, Dn) > 0.0f;
+    float3 sn = fwd ? pn : pn * -1.0f;
+    float sw = fwd ? ka.hi : -ka.hi;
     sm.st[0][t] = sn.x; sm.st[1][t] = sn.y; sm.st[2][t] = sn.z; sm.st[3][t] = sw;
   } else {
     float3 A = ld_hi3(sm, kRowA, t), O = ld_hi3(sm, kRowO, t), D = ld_hi3(sm, kRowD, t);
