@@ -294,10 +294,25 @@ __device__ __forceinline__ void consider_tri(const DevScene &sc, const Tri *tris
 // triangle is tested with float64 Moller-Trumbore; a near tie compares the
 // float64 plane distances of both triangles.  Each is then weighed against
 // the best hit as during the search.
+__device__ __forceinline__ void settle_pending(const DevScene &sc, const Ray &r, const RaySrc &rs, double dns64,
+                                               Best &best, float tlim);
+__device__ __noinline__ void settle_pending_call(const DevScene &sc, const Ray &r, const RaySrc &rs, double dns64,
+                                                 Best &best, float tlim) {
+  settle_pending(sc, r, rs, dns64, best, tlim);
+}
+// kOutOfLine: the rarely needed float64 code as a call, out of the caller's
+// instruction stream (the sub-domain trace, whose service code measured
+// faster the smaller it was: 46.1 -> 45.2 ms on the district)
+template <bool kOutOfLine = false>
 __device__ __forceinline__ void settle_search(const DevScene &sc, const Ray &r, const RaySrc &rs, double dns64,
                                               Best &best, float tlim) {
+  if (rs.pend[0] == 0) return;
+  if (kOutOfLine) settle_pending_call(sc, r, rs, dns64, best, tlim);
+  else settle_pending(sc, r, rs, dns64, best, tlim);
+}
+__device__ __forceinline__ void settle_pending(const DevScene &sc, const Ray &r, const RaySrc &rs, double dns64,
+                                               Best &best, float tlim) {
   const int n = rs.pend[0];
-  if (n == 0) return;
   const Tri *const tris = sc.tris;
   double3 o, d;
   rs.get(o, d);
@@ -1320,7 +1335,7 @@ __global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_ti
     if (__ballot_sync(0xffffffffu, pending) && pending) {
       pending = false;
       const Ray r = make_ray(ld_hi3(sm, kRowO, t), ld_hi3(sm, kRowD, t), v.t_eps, ls.dns);
-      if constexpr (kDefer) settle_search(v.sc, r, rs, ls.dns64, hs.best, tlim);
+      if constexpr (kDefer) settle_search<true>(v.sc, r, rs, ls.dns64, hs.best, tlim);
       // the hit lies in this tile (a reflected beam starts here as well); a
       // ray without one either leaves the grid, and with it every triangle
       // (it escapes), or goes on to the next tile
