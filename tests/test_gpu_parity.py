@@ -479,6 +479,39 @@ def test_cast_rays_through_shared_vertices_and_edges(tracer):
         assert min(s) >= -1e-5 * 5.0 or max(s) <= 1e-5 * 5.0, (p, i, s)
 
 
+def test_cast_rays_through_coincident_stacks(tracer):
+    # Two stacks of 2,048 identical triangles, one 5 m above the other: every
+    # triangle of a stack has the same Morton code, so the LBVH splits them by
+    # index alone, every box of the stack overlaps every ray, and the search
+    # must visit the whole stack (the deepest hierarchies and longest stacks
+    # a scene can give).  Rays from above hit the upper stack at exactly 40 m:
+    # a tie of the whole stack, which MIXED decides in float64 up to the
+    # length of its list and then in float32, so the hit is some triangle of
+    # the upper stack.  Rays from below hit the lower stack.
+    from paper_1912_03998_gb300 import btrace
+    k = 2048
+    tri = np.asarray([(-5.0, -5.0, 0.0), (5.0, -5.0, 0.0), (0.0, 6.0, 0.0)], np.float32)
+    verts = np.concatenate([tri + np.float32([0.0, 0.0, 10.0])] * k + [tri + np.float32([0.0, 0.0, 5.0])] * k)
+    tris = np.arange(len(verts), dtype=np.int32).reshape(-1, 3)
+    mat = np.zeros(len(tris), np.uint8)
+    refl = np.full((1, 8), 0.9, np.float32)
+    rng = np.random.Generator(np.random.PCG64(31))
+    n = 4096
+    xy = np.column_stack([rng.uniform(-2.0, 2.0, n), rng.uniform(-3.0, 1.0, n)]).astype(np.float32)
+    up = np.arange(n) % 2 == 0
+    o = np.column_stack([xy, np.where(up, 50.0, -35.0)]).astype(np.float32)
+    d = np.zeros((n, 3), np.float32)
+    d[:, 2] = np.where(up, -1.0, 1.0)
+    sid = btrace.bt_load_scene(tracer.ctx, verts, tris, mat, refl)
+    try:
+        t, ids = btrace.bt_cast_rays(tracer.ctx, sid, o, d)
+    finally:
+        btrace.bt_unload_scene(tracer.ctx, sid)
+    assert (ids >= 0).all()
+    assert np.allclose(t, 40.0, atol=1e-4), t[np.abs(t - 40.0) > 1e-4][:10]
+    assert (ids[up] < k).all() and (ids[~up] >= k).all()
+
+
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_directional_sources_match_oracle(tracer, oracle_mod, precision):
     # Section 2: a source's energy is split between the beams by its power in
