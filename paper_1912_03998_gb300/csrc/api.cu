@@ -106,6 +106,7 @@ struct bt_ctx {
   SceneState sc[BT_MAX_SCENES];
   char err[512] = {0};
   DevBuf scratch, stage_a, stage_b, stage_c, segs;
+  DevBuf seg_order, order_hist;  // scatter in order of place (scenes with many microphones)
   DevBuf beam_table;       // cone normals + axis per beam of one icosahedron level, float pairs
   int beam_table_level = -1;
   bt::Counters *d_ctr = nullptr;
@@ -496,6 +497,8 @@ BT_API int bt_destroy(bt_ctx *c) {
   release(c->stage_b);
   release(c->stage_c);
   release(c->segs);
+  release(c->seg_order);
+  release(c->order_hist);
   release(c->beam_table);
   if (c->d_ctr) cudaFree(c->d_ctr);
   if (c->d_seg_count) cudaFree(c->d_seg_count);
@@ -894,6 +897,11 @@ static void fill_view(bt::SceneView &v, SceneState &s, const bt_trace_params *p,
   v.dir_of = s.n_pat > 0 ? (const int *)s.dir_of.p : nullptr;
 }
 
+// Above this many microphones (80 bytes of accumulators and position each:
+// 80 MB, against a 129 MB L2 shared with the geometry) a trace orders its
+// scatter by place.
+constexpr int64_t kOrderMics = (int64_t)1 << 20;
+
 // Lineages per persistent launch when the caller leaves it to the library:
 // segment records of at most a quarter of the free device memory and at most
 // 32 GiB (fewer, larger launches have fewer launch tails), at least 1 GiB.
@@ -997,6 +1005,13 @@ static int enqueue_trace(bt_ctx *c, int32_t id, const bt_trace_params *p) {
   const int64_t chunk = launch_chunk(p->chunk_beams, total, p->max_order);
   const unsigned long long cap = (unsigned long long)chunk * (p->max_order + 1);
   TRY(ensure(c, c->segs, sizeof(bt::Seg) * cap));
+  // Microphones whose accumulators and positions are several times the L2
+  // (a receiver volume) are scattered to in order of place.
+  const bool by_place = s->n_mics > kOrderMics;
+  if (by_place) {
+    TRY(ensure(c, c->seg_order, sizeof(uint32_t) * cap));
+    TRY(ensure(c, c->order_hist, sizeof(uint32_t) * bt::kOrderBins));
+  }
   // Hand-off queues: at most qcap lineages are in flight (traced or queued),
   // so no tile's ring of qcap slots can overflow.  Automatic: at least twice
   // the lanes of one launch, so that the cap rarely holds a lane back.
@@ -1023,6 +1038,7 @@ static int enqueue_trace(bt_ctx *c, int32_t id, const bt_trace_params *p) {
   bt::TraceArgs ta;
   memset(&ta, 0, sizeof(ta));
   fill_view(ta.v, *s, p, alpha_log2, has_alpha);
+  ta.v.seg_key = by_place ? 1 : 0;
   if (tiled) {
     ta.v.sc.n_tris = s->n_pairs;
     ta.v.sc.nodes = bt::hier_wide(s->t_nodes.p, s->n_pairs);
@@ -1067,6 +1083,7 @@ static int enqueue_trace(bt_ctx *c, int32_t id, const bt_trace_params *p) {
   sa.seg_count = c->d_seg_count;
   sa.seg_capacity = ta.seg_capacity;
   sa.ctr = c->d_ctr;
+  sa.order = by_place ? (const uint32_t *)c->seg_order.p : nullptr;
   bt::TiledArgs tga;
   memset(&tga, 0, sizeof(tga));
   if (tiled) {
@@ -1097,6 +1114,9 @@ static int enqueue_trace(bt_ctx *c, int32_t id, const bt_trace_params *p) {
   auto scatter_round = [&]() -> int {
     if (s->n_mics <= 0) return BT_OK;
     TRY(mark(1));
+    if (by_place)
+      CK(bt::launch_seg_order(st, ta.segs, c->d_seg_count, ta.seg_capacity, ta.v.grid,
+                              (uint32_t *)c->order_hist.p, (uint32_t *)c->seg_order.p, c->n_sm));
     CK(bt::launch_scatter(st, sa, c->n_sm));
     return mark(1);
   };

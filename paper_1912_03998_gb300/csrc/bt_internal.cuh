@@ -149,7 +149,9 @@ struct MicGrid {
 // missing plane is (0, 0, 0, -inf).
 struct __align__(16) Seg {
   float ahi[3], alo[3];  // apex (source or image source)
-  int view, pad_i;       // index of the scene view (0 in a single-scene trace)
+  int view;              // index of the scene view (0 in a single-scene trace)
+  int key;               // the microphone-grid cell under the segment, x | y << 16, when the scene orders
+                         // its scatter by place (SceneView::seg_key), else 0
   float4 n0;             // cone-face normal 0 (hi); w: leaf slot of the start plane's triangle (-1 none)
   float4 n1;             // w: leaf slot of the end plane's triangle (-1 none)
   float4 n2;             // w: reflection order (int bits)
@@ -189,7 +191,7 @@ struct SceneView {
   float energy_threshold;
   float alpha_log2[kMaxBands];  // air damping as a base-2 exponent per metre: -alpha_b * log2(10) / 10
   int has_alpha;
-  int pad0;
+  int seg_key;            // 1: each segment record carries its grid cell (Seg::key)
   const MicGrid *grid;
   const float *beam_table;   // MIXED: per beam 3 cone normals + axis as float pairs: [n_beams][12] hi, then lo
   const float4 *mics;        // sorted by cell: xyz, w = original index (int bits)
@@ -229,6 +231,7 @@ struct ScatterArgs {
   const unsigned long long *seg_count;
   unsigned long long seg_capacity;
   Counters *ctr;
+  const uint32_t *order;    // the emitted segments in order of place (launch_seg_order), or null
 };
 
 // ------------------------------------------------------------------ helpers
@@ -482,6 +485,53 @@ __device__ __forceinline__ df3 df3_mirror(df3 v, df3 n) {
   k = df{2.0f * k.hi, 2.0f * k.lo};
   return df3_sub(v, df3_scale(n, k));
 }
+// Fused forms for the reflection, each about half the operations of the
+// same expression built from the pair operations above, with an error of
+// the same order relative to the operands' magnitudes.
+// a . b: the products of the high parts exact (TwoProd) and summed by
+// TwoSum, every low-order term gathered in one float32 (the compensated dot
+// product Dot2 of Ogita, Rump and Oishi, with pair operands).
+__device__ __forceinline__ df df3_dot2(df3 a, df3 b) {
+  df px = two_prod(a.x.hi, b.x.hi), py = two_prod(a.y.hi, b.y.hi), pz = two_prod(a.z.hi, b.z.hi);
+  df s = two_sum(px.hi, py.hi);
+  df u = two_sum(s.hi, pz.hi);
+  float c = __fadd_rn(__fadd_rn(s.lo, u.lo), __fadd_rn(__fadd_rn(px.lo, py.lo), pz.lo));
+  c = __fmaf_rn(a.x.hi, b.x.lo, c);
+  c = __fmaf_rn(a.x.lo, b.x.hi, c);
+  c = __fmaf_rn(a.y.hi, b.y.lo, c);
+  c = __fmaf_rn(a.y.lo, b.y.hi, c);
+  c = __fmaf_rn(a.z.hi, b.z.lo, c);
+  c = __fmaf_rn(a.z.lo, b.z.hi, c);
+  return fast_two_sum(u.hi, c);
+}
+// v - 2 k n (a mirror image once k = v . n): the high product exact, the
+// high difference by TwoSum (2 k n is exact scaling), the rest in float32.
+__device__ __forceinline__ df df_sub2kn(df v, df k, df n) {
+  df q = two_prod(k.hi, n.hi);
+  df s = two_sum(v.hi, -2.0f * q.hi);
+  float t = __fmaf_rn(k.hi, n.lo, q.lo);
+  t = __fmaf_rn(k.lo, n.hi, t);
+  return fast_two_sum(s.hi, __fmaf_rn(-2.0f, t, __fadd_rn(s.lo, v.lo)));
+}
+__device__ __forceinline__ df3 df3_sub2kn(df3 v, df k, df3 n) {
+  return df3{df_sub2kn(v.x, k, n.x), df_sub2kn(v.y, k, n.y), df_sub2kn(v.z, k, n.z)};
+}
+// o + s d, the same way.
+__device__ __forceinline__ df df_axpy(df o, df s, df d) {
+  df q = two_prod(s.hi, d.hi);
+  df u = two_sum(o.hi, q.hi);
+  float t = __fmaf_rn(s.hi, d.lo, q.lo);
+  t = __fmaf_rn(s.lo, d.hi, t);
+  return fast_two_sum(u.hi, __fadd_rn(__fadd_rn(u.lo, o.lo), t));
+}
+// a / b to two terms: q1 = a.hi / b.hi, the remainder a - q1 b with q1 b.hi
+// exact, and its quotient as the low part.
+__device__ __forceinline__ df df_div2(df a, df b) {
+  float q1 = __fdiv_rn(a.hi, b.hi);
+  df p = two_prod(q1, b.hi);
+  float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p.hi), p.lo), __fsub_rn(a.lo, __fmul_rn(q1, b.lo)));
+  return fast_two_sum(q1, __fdiv_rn(r, b.hi));
+}
 __device__ __forceinline__ float3 df3_hi(df3 a) { return make_float3(a.x.hi, a.y.hi, a.z.hi); }
 __device__ __forceinline__ df d_to_df(double x) {
   float hi = (float)x;
@@ -533,6 +583,13 @@ constexpr int kStateRows = 56;
 cudaError_t launch_cast(cudaStream_t st, const DevScene &sc, const float *o, const float *d, const float *ns,
                         int64_t n, float t_eps, float *t_out, int *tri_out, int *err);
 cudaError_t launch_scatter(cudaStream_t st, const ScatterArgs &a, int n_sm);
+// Order of the emitted segments by place (the grid cell in each record's
+// key, bins along a Morton curve); hist holds kOrderBins counters and is
+// zeroed here, order receives min(*seg_count, cap) record indices.
+constexpr int kOrderBits = 6, kOrderBins = 1 << (2 * kOrderBits);
+cudaError_t launch_seg_order(cudaStream_t st, const Seg *segs, const unsigned long long *seg_count,
+                             unsigned long long cap, const MicGrid *grid, uint32_t *hist, uint32_t *order,
+                             int n_sm);
 cudaError_t launch_set_result(cudaStream_t st, const double *intensity, const int *count_in, const float4 *mics,
                               int64_t n_m, int n_bands, double *energy, int *count);
 // L2 read-bandwidth probe: `blocks` blocks of 256 threads read the n4 float4s

@@ -214,8 +214,10 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
   for (long long base = warp0 * 32; base < n_items; base += n_warps * 32) {
     // ---- 1. one item per lane: segment parameters and the layer's footprint
     const long long it = base + lane;
-    const long long si = it / n_layers;
-    const int layer = (int)(it - si * n_layers);
+    const long long ii = it / n_layers;
+    const int layer = (int)(it - ii * n_layers);
+    // the segment record: in order of place when the scene orders its scatter
+    const long long si = a.order && it < n_items ? (long long)__ldg(&a.order[ii]) : ii;
     int nrows = 0;
     if (it < n_items) {
       // the footprint needs the apex, the cone normals and the start and end
@@ -466,6 +468,100 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(ScatterArgs a) {
     atomicAdd(&a.ctr->candidates, n_cand);
     atomicAdd(&a.ctr->contributions, n_contrib);
   }
+}
+
+// ------------------------------------------------------ order of place
+// With microphones through a whole volume, the accumulators and positions
+// are many times the L2; segments taken in the order they were traced reach
+// microphones all over the city, so nearly every atomic update and position
+// load goes to HBM.  Taken in order of the cell under each segment (bins of
+// 2^kOrderBits x 2^kOrderBits cells along a Morton curve), the warps
+// resident at any time work in one neighbourhood and its accumulators stay
+// in L2.  A counting sort: bin histogram, exclusive scan, placement; the
+// order within a bin is immaterial (every contribution is added, whatever
+// the order).
+__device__ __forceinline__ int order_bin(const MicGrid &g, int key) {
+  const unsigned x = ((unsigned)(key & 0xffff) << kOrderBits) / (unsigned)max(g.nx, 1);
+  const unsigned y = ((unsigned)key >> 16 << kOrderBits) / (unsigned)max(g.ny, 1);
+  unsigned m = 0;
+#pragma unroll
+  for (int b = 0; b < kOrderBits; b++) m |= ((x >> b) & 1u) << (2 * b) | ((y >> b) & 1u) << (2 * b + 1);
+  return (int)(m & (kOrderBins - 1));
+}
+
+__global__ void __launch_bounds__(256) k_order_hist(const Seg *segs, const unsigned long long *seg_count,
+                                                    unsigned long long cap, const MicGrid *grid, uint32_t *hist) {
+  __shared__ uint32_t h[kOrderBins];
+  for (int i = threadIdx.x; i < kOrderBins; i += blockDim.x) h[i] = 0u;
+  __syncthreads();
+  const MicGrid g = *grid;
+  const long long n = (long long)min(*seg_count, cap);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    atomicAdd(&h[order_bin(g, __ldg(&segs[i].key))], 1u);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kOrderBins; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// Exclusive scan of the kOrderBins counts in place, one block.
+__global__ void __launch_bounds__(1024) k_order_scan(uint32_t *hist) {
+  constexpr int kPer = kOrderBins / 1024;
+  __shared__ uint32_t part[1024];
+  uint32_t v[kPer], sum = 0;
+#pragma unroll
+  for (int q = 0; q < kPer; q++) {
+    v[q] = hist[threadIdx.x * kPer + q];
+    sum += v[q];
+  }
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const uint32_t y = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += y;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - sum;
+#pragma unroll
+  for (int q = 0; q < kPer; q++) {
+    hist[threadIdx.x * kPer + q] = run;
+    run += v[q];
+  }
+}
+
+// Each record index to its bin's next place; lanes of a warp with the same
+// bin take their places with one atomic.
+__global__ void __launch_bounds__(256) k_order_place(const Seg *segs, const unsigned long long *seg_count,
+                                                     unsigned long long cap, const MicGrid *grid, uint32_t *offs,
+                                                     uint32_t *order) {
+  const MicGrid g = *grid;
+  const long long n = (long long)min(*seg_count, cap);
+  const unsigned lane = lane_id();
+  for (long long b0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) & ~31ll; b0 < n;
+       b0 += (long long)gridDim.x * blockDim.x) {
+    const long long i = b0 + lane;
+    const bool ok = i < n;
+    const int bin = ok ? order_bin(g, __ldg(&segs[i].key)) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, bin);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (ok && (int)lane == leader) base = atomicAdd(&offs[bin], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (ok) order[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
+  }
+}
+
+cudaError_t launch_seg_order(cudaStream_t st, const Seg *segs, const unsigned long long *seg_count,
+                             unsigned long long cap, const MicGrid *grid, uint32_t *hist, uint32_t *order, int n_sm) {
+  static_assert(kOrderBins % 1024 == 0, "scan layout");
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kOrderBins, st);
+  if (e != cudaSuccess) return e;
+  const int blocks = n_sm * 4;
+  k_order_hist<<<blocks, 256, 0, st>>>(segs, seg_count, cap, grid, hist);
+  k_order_scan<<<1, 1024, 0, st>>>(hist);
+  k_order_place<<<blocks, 256, 0, st>>>(segs, seg_count, cap, grid, hist, order);
+  note_launches(3);
+  return cudaGetLastError();
 }
 
 template <bool kF64, bool kBatch>

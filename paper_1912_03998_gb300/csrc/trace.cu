@@ -512,6 +512,17 @@ __device__ __forceinline__ bool may_reach_slab(float3 n0, float3 n1, float3 n2, 
   return true;
 }
 
+// The microphone-grid cell under the middle of a segment (of its first 200 m
+// when it is longer or escapes), x | y << 16: the place the scatter orders
+// segments by, so that segments processed together reach the same
+// microphones and accumulators.
+__device__ __forceinline__ int seg_cell_key(const MicGrid &g, const Ray &r, float t) {
+  const float h = 0.5f * fminf(t, 200.0f);
+  const int cx = clampi((int)((r.o.x + r.d.x * h - g.x0) * g.inv_cw), 0, g.nx - 1);
+  const int cy = clampi((int)((r.o.y + r.d.y * h - g.y0) * g.inv_ch), 0, g.ny - 1);
+  return (cx & 0xffff) | cy << 16;
+}
+
 // Warp-aggregated append of a segment record.
 __device__ __forceinline__ void emit_segment(const TraceArgs &a, const Seg &s, bool emit,
                                              const WarpCount &n_emit) {
@@ -712,7 +723,7 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, const SceneVi
       double3 end = make_double3(en.x, en.y, en.z);
       ew = (float)dot3(end, make_double3(v0.x, v0.y, v0.z) - ld_d3(sm, kRowA, t));
     } else if (kPairs) {
-      ew = df3_dot(mkdf3(en), df3_sub(mkdf3(f3(v0)), ld_df3(sm, kRowA, t))).hi;
+      ew = df3_dot2(mkdf3(en), df3_sub(mkdf3(f3(v0)), ld_df3(sm, kRowA, t))).hi;
     } else {
       ew = dot3(en, f3(v0) - ld_hi3(sm, kRowA, t));
     }
@@ -747,8 +758,8 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, const SceneVi
     s.p03 = make_float4(sm.p[0][t], sm.p[1][t], sm.p[2][t], sm.p[3][t]);
     s.p47 = make_float4(sm.p[4][t], sm.p[5][t], sm.p[6][t], sm.p[7][t]);
     s.view = vi;
-    s.pad_i = 0;
     const MicGrid &g = *v.grid;
+    s.key = v.seg_key ? seg_cell_key(g, r, best.t) : 0;
     emit_segment(a, s, g.n_mics > 0 && may_reach_slab(n0, n1, n2, s.ahi[2], g), cn[kCEmit]);
   }
   if (slot < 0 || ls.k == v.max_order) return false;
@@ -796,27 +807,28 @@ __device__ __forceinline__ bool finish_segment(const TraceArgs &a, const SceneVi
     // (the compiler fences keep the stages apart)
     PlaneDF pd = v.sc.planes_df[slot];
     const df3 n = df3{df{pd.hi.x, pd.lo.x}, df{pd.hi.y, pd.lo.y}, df{pd.hi.z, pd.lo.z}};
+    df kd = df{0.0f, 0.0f}, ka = df{0.0f, 0.0f};
     {
-      // the hit point on the plane (the reflected beam's origin)
+      // the hit point on the plane (the reflected beam's origin); n . D is
+      // also the axis' own coefficient in the mirror loop below
       const df3 O = ld_df3(sm, kRowO, t), D = ld_df3(sm, kRowD, t);
-      const df th = best.has64 ? d_to_df(best.t64)
-                               : df_div(df_sub(df{pd.hi.w, pd.lo.w}, df3_dot(n, O)), df3_dot(n, D));
-      st_df3(sm, kRowO, t, df3_add(O, df3_scale(D, th)));
+      kd = df3_dot2(D, n);
+      const df th = best.has64 ? d_to_df(best.t64) : df_div2(df_sub(df{pd.hi.w, pd.lo.w}, df3_dot2(n, O)), kd);
+      st_df3(sm, kRowO, t, df3{df_axpy(O.x, th, D.x), df_axpy(O.y, th, D.y), df_axpy(O.z, th, D.z)});
     }
     // the cone normals, the axis and the apex (the image source) mirrored
     // by one copy of the code: v - 2 ((v - p) . n) n with p = 0 for the
     // directions and p = v0, a point of the plane, for the apex
     const df3 p0 = mkdf3(pv0);
-    df kd = df{0.0f, 0.0f}, ka = df{0.0f, 0.0f};
 #pragma unroll 1
     for (int j = 0; j < 5; j++) {
       asm volatile("" ::: "memory");
       const int row = j < 3 ? kRowN + 3 * j : (j == 3 ? kRowD : kRowA);
       const df3 v = ld_df3(sm, row, t);
-      const df k = df3_dot(j == 4 ? df3_sub(v, p0) : v, n);
-      if (j == 3) kd = k;
+      df k = kd;
+      if (j != 3) k = df3_dot2(j == 4 ? df3_sub(v, p0) : v, n);
       if (j == 4) ka = k;
-      st_df3(sm, row, t, df3_sub(v, df3_scale(n, df{2.0f * k.hi, 2.0f * k.lo})));
+      st_df3(sm, row, t, df3_sub2kn(v, k, n));
     }
     asm volatile("" ::: "memory");
     // |n . D| is the same for the axis and its mirror image, and the image

@@ -255,6 +255,38 @@ def test_volumetric_microphones(tracer, oracle_mod):
     assert (g4["cnt"] == g["cnt"]).all() and np.allclose(g4["I"], g["I"], rtol=1e-9, atol=0)
 
 
+
+def test_scatter_in_order_of_place(tracer, oracle_mod):
+    # More than 2^20 microphones: the trace scatters its segments in order of
+    # the grid cell under each one.  The result must be the one the
+    # trace-order scatter gives: here the same microphones traced in two
+    # blocks below that size, whose scatters keep the trace order.
+    from paper_1912_03998_gb300 import shard
+    base = synth.tiny_city(seed=11, level=4, max_order=4, n_sources=3)
+    layers = [synth.mic_grid(5.0, 5.0, 555.0, 555.0, 380, 380, z) for z in np.linspace(1.5, 50.0, 8)]
+    mics = np.concatenate(layers).astype(np.float32)
+    assert len(mics) > (1 << 20)
+    w = base.with_mics(mics)
+    full = gpu_run(tracer, w)
+    parts = []
+    for r in range(2):
+        lo, hi = shard.mic_block(len(mics), r, 2)
+        assert hi - lo <= (1 << 20)
+        parts.append(gpu_run(tracer, w.with_mics(mics[lo:hi])))
+    cnt = np.concatenate([g["cnt"] for g in parts])
+    I = np.concatenate([g["I"] for g in parts])
+    assert (cnt == full["cnt"]).all()
+    assert np.allclose(I, full["I"], rtol=1e-9, atol=0)
+    assert full["stats"]["contributions"] == sum(g["stats"]["contributions"] for g in parts)
+    # sub-domains and order of place together
+    g4 = gpu_run(tracer, w, tiles_x=2, tiles_y=2)
+    assert (g4["cnt"] == full["cnt"]).all() and np.allclose(g4["I"], full["I"], rtol=1e-9, atol=0)
+    # and the oracle on a sample of the microphones
+    idx = np.random.default_rng(3).choice(len(mics), 3000, replace=False)
+    r, L = oracle_levels(oracle_mod, w.with_mics(mics[idx]))
+    assert_parity(full["level"][idx], L, "order of place, sampled microphones")
+    assert (full["cnt"][idx] == r["cnt"]).mean() >= 0.999
+
 # ------------------------------------------------------------- district scale
 @pytest.fixture(scope="module")
 def district():
