@@ -62,6 +62,9 @@ def parse():
                     help="serve: share of a step's lineages that goes to the oldest query first")
     ap.add_argument("--small-lineages", type=int, default=0,
                     help="serve: queries with at most this many lineages left go first")
+    ap.add_argument("--fill", default="work", choices=["work", "arrival"],
+                    help="serve: what is left of a step after the oldest query goes to the others "
+                         "shortest remaining work first (work) or in arrival order (arrival)")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the short served-latency measurement in the default line")
     ap.add_argument("--autotune", action="store_true",
@@ -539,7 +542,7 @@ def run_serve(args):
     with Clocks(0) as clk:
         for k, rate in enumerate(float(r) for r in args.rates.split(",")):
             rows.append(serve_once(tr, cities, rate, args.queries, 100 + k, prec, args.step_lineages,
-                                   args.oldest_share, args.small_lineages))
+                                   args.oldest_share, args.small_lineages, fill=args.fill))
     tr.close()
     head = rows[-1]
     line = {"metric": "served p50/p99 latency and queries/s", "value": head["served"]["queries_per_s"],
@@ -550,7 +553,7 @@ def run_serve(args):
                                    "queries of 1-2,000 sources (0.001-1 W per band), 1k-250k microphones, "
                                    "L=4, K 3-6", "queries_per_rate": args.queries,
                        "step_lineages": args.step_lineages, "oldest_share": args.oldest_share,
-                       "small_lineages": args.small_lineages,
+                       "small_lineages": args.small_lineages, "fill": args.fill,
                        "precision": args.precision, "parallelism": "1 GPU"},
             "clocks": clk.summary(), "rates": rows}
     print(json.dumps(line))

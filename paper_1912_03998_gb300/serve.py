@@ -14,6 +14,13 @@ the GPU join at the next step and their work overlaps on the device.  A query
 whose lineages are all traced is read back (levels to the host), its scene
 freed, and its latency (completion - arrival) recorded.
 
+A query is traced whole by one synchronous bt_trace, as plain serving
+would, when it is the only query to trace and none is waiting, or when it
+is the oldest and bigger than a step: there is nothing to overlap it with,
+and one launch over all its lineages pays one launch tail and no per-step
+host round trips (`whole`, on by default).  Steps over several queries
+keep the continuous batching.
+
 With `submit_alone`, a query that is the only one to trace and fits one
 step is traced whole with the asynchronous call (bt_submit), behind a
 submitted trace still running if there is one: while the GPU traces, the
@@ -61,7 +68,8 @@ def set_query_directivity(ctx, sid, q):
         btrace.bt_set_directivity(ctx, sid, d.gains(btrace.bt_beam_axes(ctx, q.level)), d.pattern_of)
 
 
-def step_shares(left, work, budget: int, oldest_share: float = 1.0, quantum: int = 0, small: int = 0):
+def step_shares(left, work, budget: int, oldest_share: float = 1.0, quantum: int = 0, small: int = 0,
+                fill: str = "work"):
     """Lineages each active query traces in the next step.
 
     left[i]: the query's lineages still to trace; work[i]: its remaining
@@ -71,7 +79,8 @@ def step_shares(left, work, budget: int, oldest_share: float = 1.0, quantum: int
     step.  Then the oldest query takes up to `oldest_share` of the step's
     lineage budget (all of it by default: first come, first served, so a big
     query is not held back by the stream behind it); what is left goes to
-    the queries shortest remaining work first.  With a nonzero `quantum`
+    the queries shortest remaining work first (`fill="work"`) or in
+    admission order (`fill="arrival"`).  With a nonzero `quantum`
     every query the budget did not reach still gets that many lineages (the
     step then exceeds the budget by up to len(left) quanta).
     """
@@ -90,7 +99,7 @@ def step_shares(left, work, budget: int, oldest_share: float = 1.0, quantum: int
         g = min(left[0] - share[0], int(budget * oldest_share), b)
         share[0] += g
         b -= g
-    for i in sorted(range(n), key=lambda i: work[i]):
+    for i in (sorted(range(n), key=lambda i: work[i]) if fill == "work" else range(n)):
         if b <= 0:
             break
         g = min(left[i] - share[i], b)
@@ -133,7 +142,8 @@ class Server:
     def __init__(self, tracer, cities, step_lineages: int = 1 << 22, quantum: int = 0,
                  mem_budget: int = 4 << 30, max_active: int = 48, precision: int = btrace.BT_PREC_MIXED,
                  oldest_share: float = 1.0, small_lineages: int = 0, mem_reserve: int = 1 << 30,
-                 submit_alone: bool = False, check_free: bool = True):
+                 submit_alone: bool = False, check_free: bool = True, whole: bool = True,
+                 fill: str = "work"):
         self.tr = tracer
         self.quantum = int(quantum)
         self.oldest_share = float(oldest_share)
@@ -145,6 +155,10 @@ class Server:
         self.precision = precision
         self.mem_reserve = int(mem_reserve)
         self.submit_alone = bool(submit_alone)
+        self.whole = bool(whole)
+        if fill not in ("work", "arrival"):
+            raise ValueError(f"fill must be 'work' or 'arrival', not {fill!r}")
+        self.fill = fill
         self.check_free = bool(check_free)
         self.waiting = collections.deque()
         self.active = []
@@ -221,9 +235,16 @@ class Server:
             # a submitted trace is running: retire it before a (synchronous)
             # step of the others, so that its latency does not include theirs
             return True
+        if self.whole and pending and self._trace_whole(pending):
+            self.steps += 1
+            t2 = time.perf_counter()
+            self.host_s["step"] += t2 - t1
+            self._retire(t2)
+            return True
         left = [a["total"] - a["next"] for a in self.active]
         work = [l * (a["q"].max_order + 1) for l, a in zip(left, self.active)]
-        share = step_shares(left, work, self.step_lineages, self.oldest_share, self.quantum, self.small_lineages)
+        share = step_shares(left, work, self.step_lineages, self.oldest_share, self.quantum, self.small_lineages,
+                            self.fill)
         ids, begins, ends, params = [], [], [], []
         for a, s in zip(self.active, share):
             if s > 0 and not a["inflight"]:
@@ -240,6 +261,25 @@ class Server:
         self.steps += 1
         t2 = time.perf_counter()
         self.host_s["step"] += t2 - t1
+        self._retire(t2)
+        return True
+
+    def _trace_whole(self, pending) -> bool:
+        """Trace the oldest pending query whole (one bt_trace) if it is the
+        only one to trace with nothing waiting, or bigger than a step; True
+        if it did."""
+        a = pending[0]
+        if a["next"] != 0 or a["inflight"]:
+            return False
+        if not ((len(pending) == 1 and not self.waiting) or a["total"] > self.step_lineages):
+            return False
+        btrace.bt_trace(self.tr.ctx, a["sid"], a["p"])
+        a["next"] = a["total"]
+        a["whole"] = True
+        return True
+
+    def _retire(self, t2):
+        """Read back every query whose lineages are all traced."""
         still = []
         for a in self.active:
             if a["next"] < a["total"] or a["inflight"]:
@@ -250,7 +290,7 @@ class Server:
             level = np.empty((n, nb), np.float64)
             count = np.empty(n, np.int32)
             st = btrace.bt_read_levels(self.tr.ctx, a["sid"], level, None, count)
-            if a.get("submitted"):
+            if a.get("submitted") or a.get("whole"):
                 self.segments += st["segments"]
                 self.host_s["gpu_trace"] += st["trace_ms"] * 1e-3
             btrace.bt_unload_scene(self.tr.ctx, a["sid"])
@@ -258,7 +298,6 @@ class Server:
             self.done.append(Done(a["index"], a["arrival"], a["admitted"], self.now(), level, count))
         self.active = still
         self.host_s["retire"] += time.perf_counter() - t2
-        return True
 
     def run(self, queries, realtime: bool = True):
         """Serve `queries` (arrival_s from the start of the run).  With

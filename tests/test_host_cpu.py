@@ -21,6 +21,16 @@ def test_step_shares_oldest_first_then_shortest_remaining():
     assert s == [500, 300, 40, 160]
 
 
+def test_step_shares_fill_in_arrival_order():
+    # after the oldest query, what is left of the budget goes to the others
+    # in admission order instead of shortest remaining work first
+    left = [300, 5000, 200, 100]
+    work = [l * 5 for l in left]
+    assert serve.step_shares(left, work, 1000) == [300, 400, 200, 100]
+    assert serve.step_shares(left, work, 1000, fill="arrival") == [300, 700, 0, 0]
+    assert serve.step_shares(left, work, 10000, fill="arrival") == left
+
+
 def test_step_shares_invariants():
     rng = np.random.Generator(np.random.PCG64(3))
     for _ in range(500):
@@ -134,6 +144,7 @@ class _FakeLib:
         self.totals = []      # per bt_trace_ranges call: lineages traced
         self.directivity = {}
         self.submitted, self.polls, self.total = [], {}, {}
+        self.whole = []       # per bt_trace call (a whole query): its sid
 
     def bt_scene_share(self, ctx, base):
         self.next_sid += 1
@@ -164,6 +175,12 @@ class _FakeLib:
 
     def bt_ranges_stats(self, ctx):
         return {"segments": 0, "trace_ms": 0.0}
+
+    def bt_trace(self, ctx, sid, params):
+        # a whole-query trace, synchronous
+        assert sid in self.live and not self.ranges[sid]
+        self.whole.append(sid)
+        self.ranges[sid].append((0, self.total[sid]))
 
     def bt_submit(self, ctx, sid, params):
         # a whole-query trace: every lineage of the scene in one range
@@ -203,16 +220,18 @@ def test_server_traces_every_lineage_once_in_order(monkeypatch):
     # order, and no step holds more than max_active queries
     lib = _FakeLib()
     for name in ("bt_scene_share", "bt_set_sources", "bt_set_microphones", "bt_beam_axes", "bt_set_directivity",
-                 "bt_trace_ranges", "bt_ranges_stats", "bt_read_levels", "bt_unload_scene", "bt_submit", "bt_poll"):
+                 "bt_trace_ranges", "bt_ranges_stats", "bt_read_levels", "bt_unload_scene", "bt_submit", "bt_poll",
+                 "bt_trace"):
         monkeypatch.setattr(serve.btrace, name, getattr(lib, name))
     qs = synth.serving_queries(seed=2, n_queries=12, n_cities=2, rate_qps=1e4, level=3, max_sources=40,
                                max_mics=3000)
-    srv = serve.Server(_FakeTracer(), [None, None], step_lineages=1500, max_active=4)
+    srv = serve.Server(_FakeTracer(), [None, None], step_lineages=1500, max_active=4, whole=False)
     done = srv.run(qs, realtime=False)
     assert [d.index for d in done] == list(range(len(qs)))
     assert not lib.live  # every query's scene was freed
     assert max(len(c) for c in lib.calls) <= 4
     assert max(lib.totals) <= 1500 and srv.steps == len(lib.calls) + len(lib.submitted)
+    assert not lib.whole
     for d, q in zip(done, qs):
         sid = int(d.level[0, 0])
         rs = lib.ranges[sid]
@@ -256,7 +275,8 @@ def test_server_submits_a_lone_small_query_whole_and_polls_it(monkeypatch):
     # by one asynchronous submission, polled until it finishes, then read back
     lib = _FakeLib()
     for name in ("bt_scene_share", "bt_set_sources", "bt_set_microphones", "bt_beam_axes", "bt_set_directivity",
-                 "bt_trace_ranges", "bt_ranges_stats", "bt_read_levels", "bt_unload_scene", "bt_submit", "bt_poll"):
+                 "bt_trace_ranges", "bt_ranges_stats", "bt_read_levels", "bt_unload_scene", "bt_submit", "bt_poll",
+                 "bt_trace"):
         monkeypatch.setattr(serve.btrace, name, getattr(lib, name))
     qs = synth.serving_queries(seed=3, n_queries=3, n_cities=1, rate_qps=1.0, level=2, max_sources=3,
                                max_mics=1000)
@@ -269,3 +289,46 @@ def test_server_submits_a_lone_small_query_whole_and_polls_it(monkeypatch):
     assert [d.index for d in srv.done] == [0, 1, 2]
     for d, q in zip(srv.done, qs):
         assert lib.ranges[int(d.level[0, 0])] == [(0, len(q.src) * 20 * 4 ** q.level)]
+
+
+def test_server_traces_lone_and_oversized_queries_whole(monkeypatch):
+    # With the whole-query policy (the default) a query that is the only one
+    # to trace with none waiting, or the oldest and bigger than a step, is
+    # traced by one bt_trace over all its lineages; queries that overlap
+    # otherwise share steps; every lineage is still traced exactly once.
+    lib = _FakeLib()
+    for name in ("bt_scene_share", "bt_set_sources", "bt_set_microphones", "bt_beam_axes", "bt_set_directivity",
+                 "bt_trace_ranges", "bt_ranges_stats", "bt_read_levels", "bt_unload_scene", "bt_submit", "bt_poll",
+                 "bt_trace"):
+        monkeypatch.setattr(serve.btrace, name, getattr(lib, name))
+    qs = synth.serving_queries(seed=2, n_queries=12, n_cities=2, rate_qps=1e4, level=3, max_sources=40,
+                               max_mics=3000)
+    step = 1500
+    srv = serve.Server(_FakeTracer(), [None, None], step_lineages=step, max_active=4)
+    done = srv.run(qs, realtime=False)
+    assert [d.index for d in done] == list(range(len(qs)))
+    assert not lib.live
+    assert srv.steps == len(lib.calls) + len(lib.whole)
+    totals = {d.index: len(q.src) * 20 * 4 ** q.level for d, q in zip(done, qs)}
+    for d, q in zip(done, qs):
+        sid = int(d.level[0, 0])
+        rs = lib.ranges[sid]
+        assert rs[0][0] == 0 and rs[-1][1] == totals[d.index]
+        assert all(a[1] == b[0] for a, b in zip(rs, rs[1:]))
+        if sid in lib.whole:
+            assert rs == [(0, totals[d.index])]
+    # the first query (the oldest, bigger than a step) is traced whole; a big
+    # query that already took part in a shared step goes on in steps; the
+    # shared steps keep to the budget
+    assert totals[0] > step and int(done[0].level[0, 0]) in lib.whole
+    assert lib.calls and max(lib.totals) <= step
+    # a lone query to an idle server: one whole trace
+    lib2 = _FakeLib()
+    for name in ("bt_scene_share", "bt_set_sources", "bt_set_microphones", "bt_trace", "bt_read_levels",
+                 "bt_unload_scene", "bt_trace_ranges"):
+        monkeypatch.setattr(serve.btrace, name, getattr(lib2, name))
+    srv2 = serve.Server(_FakeTracer(), [None], step_lineages=1 << 20)
+    srv2.submit(0, qs[0], 0.0)
+    while srv2.waiting or srv2.active:
+        srv2.step()
+    assert len(lib2.whole) == 1 and not lib2.calls
