@@ -1,7 +1,7 @@
 """Benchmark: beam segments/s of the hybrid beam/ray tracer on one GB300.
 
 Workload (default): the district configuration -- a synthetic 2 km x 2 km
-city of 5,000 extruded buildings (198,903 triangles), 1,000 point sources at
+city of 5,000 extruded buildings (201,381 triangles), 1,000 point sources at
 0.5 m on lane centres, 20,480 beams per source (icosahedron level 5),
 reflection orders 0..6, 250,000 microphones on a 4 m grid at 1.5 m.
 
@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--fill", default="work", choices=["work", "arrival"],
                     help="serve: what is left of a step after the oldest query goes to the others "
                          "shortest remaining work first (work) or in arrival order (arrival)")
+    ap.add_argument("--mix-ratio", type=float, default=0.0,
+                    help="serve: a step over several queries holds at most this many times the oldest "
+                         "query's lineages (0 = the whole step budget)")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the short served-latency measurement in the default line")
     ap.add_argument("--autotune", action="store_true",
@@ -542,7 +545,8 @@ def run_serve(args):
     with Clocks(0) as clk:
         for k, rate in enumerate(float(r) for r in args.rates.split(",")):
             rows.append(serve_once(tr, cities, rate, args.queries, 100 + k, prec, args.step_lineages,
-                                   args.oldest_share, args.small_lineages, fill=args.fill))
+                                   args.oldest_share, args.small_lineages, fill=args.fill,
+                                   mix_ratio=args.mix_ratio))
     tr.close()
     head = rows[-1]
     line = {"metric": "served p50/p99 latency and queries/s", "value": head["served"]["queries_per_s"],
@@ -553,7 +557,7 @@ def run_serve(args):
                                    "queries of 1-2,000 sources (0.001-1 W per band), 1k-250k microphones, "
                                    "L=4, K 3-6", "queries_per_rate": args.queries,
                        "step_lineages": args.step_lineages, "oldest_share": args.oldest_share,
-                       "small_lineages": args.small_lineages, "fill": args.fill,
+                       "small_lineages": args.small_lineages, "fill": args.fill, "mix_ratio": args.mix_ratio,
                        "precision": args.precision, "parallelism": "1 GPU"},
             "clocks": clk.summary(), "rates": rows}
     print(json.dumps(line))

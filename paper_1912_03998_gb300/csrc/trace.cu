@@ -1361,10 +1361,13 @@ __global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_ti
         bool leaves = false;
         while (true) {
           float tex = kInf, tey = kInf;
-          if (r.d.x > 0.0f) tex = (tg.gx0 + (ix + 1) * tg.wx - r.o.x) / r.d.x;
-          else if (r.d.x < 0.0f) tex = (tg.gx0 + ix * tg.wx - r.o.x) / r.d.x;
-          if (r.d.y > 0.0f) tey = (tg.gy0 + (iy + 1) * tg.wy - r.o.y) / r.d.y;
-          else if (r.d.y < 0.0f) tey = (tg.gy0 + iy * tg.wy - r.o.y) / r.d.y;
+          // (by the ray's inverse direction: which tile comes next needs no
+          // correctly rounded quotient, the tiles' triangle lists overlap by
+          // 5 cm)
+          if (r.d.x > 0.0f) tex = (tg.gx0 + (ix + 1) * tg.wx - r.o.x) * r.inv.x;
+          else if (r.d.x < 0.0f) tex = (tg.gx0 + ix * tg.wx - r.o.x) * r.inv.x;
+          if (r.d.y > 0.0f) tey = (tg.gy0 + (iy + 1) * tg.wy - r.o.y) * r.inv.y;
+          else if (r.d.y < 0.0f) tey = (tg.gy0 + iy * tg.wy - r.o.y) * r.inv.y;
           leaves = tex == kInf && tey == kInf;
           if (!leaves) {
             if (tex <= tey) ix += r.d.x > 0.0f ? 1 : -1;

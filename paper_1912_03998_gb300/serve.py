@@ -143,7 +143,7 @@ class Server:
                  mem_budget: int = 4 << 30, max_active: int = 48, precision: int = btrace.BT_PREC_MIXED,
                  oldest_share: float = 1.0, small_lineages: int = 0, mem_reserve: int = 1 << 30,
                  submit_alone: bool = False, check_free: bool = True, whole: bool = True,
-                 fill: str = "work"):
+                 fill: str = "work", mix_ratio: float = 0.0, mix_floor: int = 1 << 18):
         self.tr = tracer
         self.quantum = int(quantum)
         self.oldest_share = float(oldest_share)
@@ -159,6 +159,8 @@ class Server:
         if fill not in ("work", "arrival"):
             raise ValueError(f"fill must be 'work' or 'arrival', not {fill!r}")
         self.fill = fill
+        self.mix_ratio = float(mix_ratio)
+        self.mix_floor = int(mix_floor)
         self.check_free = bool(check_free)
         self.waiting = collections.deque()
         self.active = []
@@ -243,7 +245,12 @@ class Server:
             return True
         left = [a["total"] - a["next"] for a in self.active]
         work = [l * (a["q"].max_order + 1) for l, a in zip(left, self.active)]
-        share = step_shares(left, work, self.step_lineages, self.oldest_share, self.quantum, self.small_lineages,
+        budget = self.step_lineages
+        if self.mix_ratio > 0.0:
+            # the others may delay the oldest query's step by at most
+            # mix_ratio - 1 times its own lineages (at least mix_floor in all)
+            budget = min(budget, max(int(self.mix_ratio * left[0]), self.mix_floor))
+        share = step_shares(left, work, budget, self.oldest_share, self.quantum, self.small_lineages,
                             self.fill)
         ids, begins, ends, params = [], [], [], []
         for a, s in zip(self.active, share):

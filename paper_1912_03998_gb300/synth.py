@@ -315,19 +315,29 @@ def _polygon_area(p):
     return 0.5 * float(np.sum(x * np.roll(y, -1) - np.roll(x, -1) * y))
 
 
-def _footprint(rng, lot):
-    """Convex n-gon (n ~ U{4..12}) inscribed in a scaled ellipse of the lot, CCW."""
+def _footprint_shape(rng, lot):
+    """Convex n-gon (n ~ U{4..12}) with its vertices on the lot's inscribed
+    superellipse |x/a|^4 + |y/b|^4 = 1 (which fills 93 % of the lot), CCW and
+    centred on the origin, and the lot's centre."""
     x0, y0, x1, y1 = lot
-    cx, cy, a, b = 0.5 * (x0 + x1), 0.5 * (y0 + y1), 0.5 * (x1 - x0), 0.5 * (y1 - y0)
+    a, b = 0.5 * (x1 - x0), 0.5 * (y1 - y0)
     n = int(rng.integers(4, 13))
     th0 = rng.uniform(0.0, 2.0 * math.pi)
     th = th0 + 2.0 * math.pi * (np.arange(n) + rng.uniform(-0.3, 0.3, size=n)) / n
-    unit = np.stack([a * np.cos(th), b * np.sin(th)], axis=1)
-    a1 = _polygon_area(unit)
-    target = float(rng.lognormal(math.log(400.0), 0.6))
-    s = math.sqrt(target / a1)
-    s = min(s, math.sqrt(0.8 * math.pi * a * b / a1), 0.95)
-    pts = unit * s + np.array([cx, cy])
+    c, sn = np.cos(th), np.sin(th)
+    unit = np.stack([a * np.sign(c) * np.sqrt(np.abs(c)), b * np.sign(sn) * np.sqrt(np.abs(sn))], axis=1)
+    return unit, np.array([0.5 * (x0 + x1), 0.5 * (y0 + y1)])
+
+
+# largest scale of a footprint's shape within its lot (a gap of at least 2.5 %
+# of the lot's side to every neighbour)
+FOOTPRINT_MAX_SCALE = 0.95
+
+
+def _footprint(unit, centre, target):
+    """The shape scaled to area `target`, at most FOOTPRINT_MAX_SCALE."""
+    s = min(math.sqrt(target / _polygon_area(unit)), FOOTPRINT_MAX_SCALE)
+    pts = unit * s + centre
     return pts, _polygon_area(pts)
 
 
@@ -359,10 +369,18 @@ def district(seed: int = 2, n_buildings: int = 5000, n_sources: int = 1000, leve
             lots += _kd_lots(rng, x0, y0, x0 + DIST_PITCH - DIST_ROAD, y0 + DIST_PITCH - DIST_ROAD, 4)
     pick = rng.choice(len(lots), size=min(n_buildings, len(lots)), replace=False)
     pick.sort()
+    # footprint areas lognormal(ln 400 m^2, 0.6), the larger areas on the
+    # footprint shapes with room for more (matched by rank), so that the lots
+    # do not cut the distribution's upper half
+    shapes = [_footprint_shape(rng, lots[li]) for li in pick]
+    room = np.array([_polygon_area(u) for u, _ in shapes]) * FOOTPRINT_MAX_SCALE ** 2
+    targets = np.sort(rng.lognormal(math.log(400.0), 0.6, size=len(pick)))
+    target_of = np.empty(len(pick))
+    target_of[np.argsort(room, kind="stable")] = targets
     mb = _MeshBuilder()
     areas, heights, ngons = [], [], []
-    for li in pick:
-        pts, area = _footprint(rng, lots[li])
+    for (unit, centre), target in zip(shapes, target_of):
+        pts, area = _footprint(unit, centre, float(target))
         h = float(np.clip(rng.lognormal(math.log(20.0), 0.66), 5.0, 200.0))
         n = pts.shape[0]
         nb = max(1, int(math.ceil(h / band_h)))

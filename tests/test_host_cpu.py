@@ -332,3 +332,22 @@ def test_server_traces_lone_and_oversized_queries_whole(monkeypatch):
     while srv2.waiting or srv2.active:
         srv2.step()
     assert len(lib2.whole) == 1 and not lib2.calls
+
+
+def test_district_matches_its_configuration():
+    # the district configuration: 5,000 buildings of 4-12-gon footprints with
+    # areas lognormal around a 400 m^2 median and heights lognormal around
+    # 20 m with a tail to 200 m, about 200k triangles, 1,000 sources with
+    # 0.01-1 W per band, 250k microphones on a 4 m grid at 1.5 m
+    w = synth.district(seed=2)
+    info = w.info
+    assert info["n_buildings"] == 5000
+    q10, q50, q90 = info["area_quantiles"]
+    assert 360.0 <= q50 <= 440.0 and q10 < 0.6 * q50 and q90 > 1.5 * q50
+    assert 18.0 <= info["height_quantiles"][1] <= 22.0 and info["height_max"] <= 200.0
+    assert 4.0 < info["ngon_mean"] < 12.0
+    assert 190_000 <= w.scene.n_tris <= 210_000
+    assert len(w.src) == 1000 and np.all((w.power >= 0.01 - 1e-6) & (w.power <= 1.0 + 1e-6))
+    assert len(w.mics) == 250_000 and np.all(w.mics[:, 2] == np.float32(1.5))
+    d = np.diff(np.unique(w.mics[:, 0]))
+    assert np.allclose(d, 4.0, atol=1e-3)
