@@ -35,18 +35,22 @@ def same(a, b):
     assert np.abs(a.level[fin] - b.level[fin]).max(initial=0.0) < 1e-6
 
 
-@pytest.mark.parametrize("step_lineages", [1 << 12, 1 << 20])
-def test_results_same_alone_and_in_the_mix(tracer, setting, step_lineages):
+@pytest.mark.parametrize("step_lineages,whole,mix_ratio",
+                         [(1 << 12, False, 0.0), (1 << 12, False, 2.0), (1 << 12, True, 0.0), (1 << 20, True, 0.0)])
+def test_results_same_alone_and_in_the_mix(tracer, setting, step_lineages, whole, mix_ratio):
+    # whole=False: every query goes through steps shared with the others;
+    # whole=True (the default): lone or oversized queries are traced whole
     from paper_1912_03998_gb300 import serve
     cities, queries = setting
-    srv = serve.Server(tracer, cities, step_lineages=step_lineages)
+    srv = serve.Server(tracer, cities, step_lineages=step_lineages, whole=whole, mix_ratio=mix_ratio,
+                       mix_floor=1 << 10)
     try:
         mixed = srv.run(queries, realtime=False)
         alone = serve.run_plain(tracer, srv.city_ids, queries, realtime=False)
     finally:
         srv.close()
     assert len(mixed) == len(alone) == len(queries)
-    if step_lineages == 1 << 12:
+    if step_lineages == 1 << 12 and not whole:
         assert srv.steps > len(queries)  # queries spanned several steps and overlapped
     for a, b in zip(mixed, alone):
         same(a, b)
