@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--mix-ratio", type=float, default=0.0,
                     help="serve: a step over several queries holds at most this many times the oldest "
                          "query's lineages (0 = the whole step budget)")
+    ap.add_argument("--mix-floor", type=int, default=1 << 18,
+                    help="serve: with --mix-ratio, a shared step may always hold this many lineages")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the short served-latency measurement in the default line")
     ap.add_argument("--autotune", action="store_true",
@@ -546,7 +548,7 @@ def run_serve(args):
         for k, rate in enumerate(float(r) for r in args.rates.split(",")):
             rows.append(serve_once(tr, cities, rate, args.queries, 100 + k, prec, args.step_lineages,
                                    args.oldest_share, args.small_lineages, fill=args.fill,
-                                   mix_ratio=args.mix_ratio))
+                                   mix_ratio=args.mix_ratio, mix_floor=args.mix_floor))
     tr.close()
     head = rows[-1]
     line = {"metric": "served p50/p99 latency and queries/s", "value": head["served"]["queries_per_s"],
@@ -557,7 +559,7 @@ def run_serve(args):
                                    "queries of 1-2,000 sources (0.001-1 W per band), 1k-250k microphones, "
                                    "L=4, K 3-6", "queries_per_rate": args.queries,
                        "step_lineages": args.step_lineages, "oldest_share": args.oldest_share,
-                       "small_lineages": args.small_lineages, "fill": args.fill, "mix_ratio": args.mix_ratio,
+                       "small_lineages": args.small_lineages, "fill": args.fill, "mix_ratio": args.mix_ratio, "mix_floor": args.mix_floor,
                        "precision": args.precision, "parallelism": "1 GPU"},
             "clocks": clk.summary(), "rates": rows}
     print(json.dumps(line))
