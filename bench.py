@@ -65,9 +65,9 @@ def parse():
     ap.add_argument("--fill", default="work", choices=["work", "arrival"],
                     help="serve: what is left of a step after the oldest query goes to the others "
                          "shortest remaining work first (work) or in arrival order (arrival)")
-    ap.add_argument("--mix-ratio", type=float, default=0.0,
+    ap.add_argument("--mix-ratio", type=float, default=1.0,
                     help="serve: a step over several queries holds at most this many times the oldest "
-                         "query's lineages (0 = the whole step budget)")
+                         "query's lineages, at least --mix-floor (0 = the whole step budget)")
     ap.add_argument("--mix-floor", type=int, default=1 << 18,
                     help="serve: with --mix-ratio, a shared step may always hold this many lineages")
     ap.add_argument("--no-serve", action="store_true",
@@ -724,7 +724,8 @@ def main():
         tr = btrace.Tracer(0)
         try:
             line["serving"] = serve_once(tr, synth.serving_cities(seed=5, n=8), 200.0, 100, 100, prec,
-                                         args.step_lineages, args.oldest_share, args.small_lineages)
+                                         args.step_lineages, args.oldest_share, args.small_lineages,
+                                         fill=args.fill, mix_ratio=args.mix_ratio, mix_floor=args.mix_floor)
         finally:
             tr.close()
     if not args.no_cpu_baseline:

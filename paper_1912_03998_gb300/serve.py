@@ -19,7 +19,14 @@ would, when it is the only query to trace and none is waiting, or when it
 is the oldest and bigger than a step: there is nothing to overlap it with,
 and one launch over all its lineages pays one launch tail and no per-step
 host round trips (`whole`, on by default).  Steps over several queries
-keep the continuous batching.
+keep the continuous batching, each capped at `mix_ratio` times the
+oldest query's own lineages (at least `mix_floor`): by default a step
+holds the oldest query's lineages and, while those are fewer than
+mix_floor (2^18), the others' up to that many, so that small queries share
+launches (less per-query launch overhead) without a big one holding the
+oldest back (measured on Poisson streams: at 200 q/s the 99th percentile
+of uncapped steps was 1.4x plain serving's, capped it is within 4 %; under
+overload the cap also raised throughput).
 
 With `submit_alone`, a query that is the only one to trace and fits one
 step is traced whole with the asynchronous call (bt_submit), behind a
@@ -143,7 +150,7 @@ class Server:
                  mem_budget: int = 4 << 30, max_active: int = 48, precision: int = btrace.BT_PREC_MIXED,
                  oldest_share: float = 1.0, small_lineages: int = 0, mem_reserve: int = 1 << 30,
                  submit_alone: bool = False, check_free: bool = True, whole: bool = True,
-                 fill: str = "work", mix_ratio: float = 0.0, mix_floor: int = 1 << 18):
+                 fill: str = "work", mix_ratio: float = 1.0, mix_floor: int = 1 << 18):
         self.tr = tracer
         self.quantum = int(quantum)
         self.oldest_share = float(oldest_share)
