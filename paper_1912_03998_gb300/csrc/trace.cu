@@ -968,10 +968,13 @@ __device__ __forceinline__ int find_view(const int64_t *base, int n_views, int64
 // running too often for too few lanes.
 constexpr int kRefillLanes = 28;
 
-// Six resident blocks per SM (at most 80 registers a thread): the traversal
-// is latency-bound, and on the district workload this beat both fewer blocks
-// without spills and more blocks with heavier spills.  kBatch: the lineages
-// of many scenes (views) in one launch, each lane on its own lineage's scene.
+// Resident blocks per SM: the traversal is latency-bound, so more warps
+// help as long as the spills they force stay light.  Seven (at most 72
+// registers a thread) for the single-scene MIXED kernel, whose reflection
+// code is small enough (district unsplit 34.2 -> 32.8 ms against six);
+// six (80 registers) for the other variants and for batches, whose lanes
+// hold their scene's arrays in registers.  kBatch: the lineages of many
+// scenes (views) in one launch, each lane on its own lineage's scene.
 //
 // Each warp alternates two phases.  In the search phase every lane with a ray
 // steps through the BVH one node at a time; the phase ends once kRefillLanes
@@ -982,7 +985,7 @@ constexpr int kRefillLanes = 28;
 // while the lanes still searching keep their state, so a long search no longer
 // holds the whole warp (dynamic ray fetch, after Aila & Laine 2009).
 template <int kP, bool kCount, bool kBatch, bool kLeaves>
-__global__ void __launch_bounds__(kTraceThreads, 6) k_trace(TraceArgs a) {
+__global__ void __launch_bounds__(kTraceThreads, kP == kPMixed && !kBatch ? 7 : 6) k_trace(TraceArgs a) {
   [[maybe_unused]] constexpr bool kPairs = Prec<kP>::pairs, kChain64 = Prec<kP>::chain64, kDefer = Prec<kP>::defer;
   __shared__ LineageSmem<kP> sm;
   __shared__ int64_t view_base[kBatch ? BT_MAX_SCENES : 1];
@@ -1303,10 +1306,12 @@ __device__ __forceinline__ float tile_exit(const TileGrid &tg, int ix, int iy, c
 // searches write their segment and reflect, escape, or are handed to the
 // next tile; lanes without a lineage take hand-offs or fresh lineages; new
 // searches start), so a long search does not hold the whole warp.
-// Six resident blocks per SM, as for k_trace; seven for the float32 variant,
-// whose smaller state fits them (40.7 -> 38.3 ms on the district split 4x4).
+// Resident blocks per SM as for k_trace: seven for the float32 variant,
+// whose smaller state fits them (40.7 -> 38.3 ms on the district split 4x4),
+// and for MIXED (39.8 against 40.7 ms at six); six for the float64-chain
+// variants.
 template <int kP, bool kCount, bool kLeaves>
-__global__ void __launch_bounds__(kTraceThreads, kP == kPF32 ? 7 : 6) k_trace_tiled(TraceArgs a, const __grid_constant__ TiledArgs ta) {
+__global__ void __launch_bounds__(kTraceThreads, kP == kPF32 || kP == kPMixed ? 7 : 6) k_trace_tiled(TraceArgs a, const __grid_constant__ TiledArgs ta) {
   [[maybe_unused]] constexpr bool kPairs = Prec<kP>::pairs, kChain64 = Prec<kP>::chain64, kDefer = Prec<kP>::defer;
   __shared__ LineageSmem<kP> sm;
   const int t = threadIdx.x;
