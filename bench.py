@@ -385,6 +385,14 @@ def run_ours(args, rank, world):
         achieved = bytes_per_launch / (sk / max(1, sl) * 1e-3) / 1e9
         counters = ncu_counters(kernel, args, tiles)
         units, kms = float(stats[-1]["emitted"]) / max(1, sl // args.steps), sk / max(1, sl)
+        # its other roof: the L2's float64 atomic additions (8 per
+        # contribution), against the library's probe of the same pattern
+        adds = 8.0 * last["contributions"] / max(1, last["scatter_launches"])
+        a_pk = max(btrace.bt_l2_atomics(ctx, 32 << 20, 64, b) for b in (2, 4, 8))
+        atomics = {"achieved": adds / (kms * 1e-3), "peak": a_pk, "unit": "float64 atomic additions/s",
+                   "frac": adds / (kms * 1e-3) / a_pk, "additions_per_launch": adds,
+                   "peak_kind": "measured in this run: 8 float64 atomic additions to scattered 64-byte slots "
+                                "of a 32 MB L2-resident buffer (bt_l2_atomics)"}
     else:
         kernel = trace_kernel_name(tiles)
         # a wide node visit reads four child boxes and four child codes (112 B),
@@ -395,6 +403,8 @@ def run_ours(args, rank, world):
         counters = ncu_counters(kernel, args, tiles)
         units, kms = float(stats[-1]["segments"]) / max(1, tl // args.steps), tk / max(1, tl)
     traffic, l2 = None, None
+    if kernel != "k_scatter":
+        atomics = None
     if counters:
         traffic = counters["dram"][0] + counters["dram"][1] * units
         l2_bytes = counters["l2"][0] + counters["l2"][1] * units
@@ -407,7 +417,7 @@ def run_ours(args, rank, world):
                stats=stats[-1], tk=tk, sk=sk, tl=tl, alg_bytes=alg_bytes, kernel=kernel,
                bytes_per_launch=bytes_per_launch, achieved=achieved, peak=peak,
                peak_kind=peak_kind, traffic=traffic, clocks=clk.summary(), work=cst, w=w,
-               tiles=tiles, untiled=untiled, autotune=tuned, l2=l2)
+               tiles=tiles, untiled=untiled, autotune=tuned, l2=l2, atomics=atomics)
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         h_in = {k: pin(v.cpu().numpy()) for k, v in d_in.items()}
@@ -703,6 +713,7 @@ def main():
                          "trace_kernel_ms_per_step": res["tk"] / args.steps,
                          "scatter_kernel_ms_per_step": res["sk"] / args.steps,
                          "l2": res["l2"],
+                         "atomics": res["atomics"],
                          "nodes_per_segment": res["work"]["nodes_visited"] / max(1, res["work"]["segments"]),
                          "tris_per_segment": res["work"]["tris_tested"] / max(1, res["work"]["segments"])},
             "stats": {k: res["stats"][k] for k in ("segments", "hits", "escapes", "emitted",

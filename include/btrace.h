@@ -392,6 +392,18 @@ int64_t bt_kernel_launches(void);
  * against.  Allocates the buffer from the context's pool; synchronous. */
 int bt_l2_bandwidth(bt_ctx *ctx, int64_t bytes, int32_t repeats, int32_t blocks_per_sm, double *gbs_out);
 
+/* Measured rate of float64 atomic additions in the L2 of the context's GPU,
+ * additions per second (the paper has no counterpart: a measurement aid).
+ * Every thread of a grid of `blocks_per_sm` blocks of 256 threads per SM
+ * (1..8) adds to the eight consecutive doubles of a 64-byte slot `repeats`
+ * times (1..10000), at slots spread over a `bytes`-byte device buffer
+ * (16 MiB..96 MiB, a multiple of 64, small enough to stay resident in L2):
+ * the pattern of the scatter's band accumulators, which take every
+ * contribution as eight float64 atomic additions.  Returns the additions
+ * over the kernel's CUDA-event time in *ops_out.  Allocates the buffer from
+ * the context's pool; synchronous. */
+int bt_l2_atomics(bt_ctx *ctx, int64_t bytes, int32_t repeats, int32_t blocks_per_sm, double *ops_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,7 +63,7 @@ EXPECTED_SYMBOLS = ("bt_params_default", "bt_create", "bt_destroy", "bt_load_sce
                     "bt_trace_noalloc", "bt_set_result", "bt_batch_create", "bt_batch_run",
                     "bt_batch_stats", "bt_batch_destroy", "bt_scene_share", "bt_trace_ranges",
                     "bt_ranges_stats", "bt_set_directivity", "bt_beam_axes", "bt_submit", "bt_poll",
-                    "bt_wait", "bt_l2_bandwidth", "bt_set_hit_log")
+                    "bt_wait", "bt_l2_bandwidth", "bt_set_hit_log", "bt_l2_atomics")
 
 
 def lib_path() -> str:
@@ -107,6 +107,7 @@ def lib():
             L.bt_trace_ranges.argtypes = [p, i32, p, p, p, C.POINTER(bt_trace_params), i32]
             L.bt_ranges_stats.argtypes = [p, C.POINTER(bt_stats)]
             L.bt_l2_bandwidth.argtypes = [p, i64, i32, i32, C.POINTER(C.c_double)]
+            L.bt_l2_atomics.argtypes = [p, i64, i32, i32, C.POINTER(C.c_double)]
             L.bt_set_hit_log.argtypes = [p, i32, p, i64]
             L.bt_kernel_launches.argtypes = []
             L.bt_kernel_launches.restype = C.c_int64
@@ -174,6 +175,14 @@ def bt_l2_bandwidth(ctx, n_bytes: int = 48 << 20, repeats: int = 200, blocks_per
     """Measured L2 read bandwidth of the context's GPU, GB/s."""
     g = C.c_double(0.0)
     _check(lib().bt_l2_bandwidth(ctx, int(n_bytes), int(repeats), int(blocks_per_sm), C.byref(g)), ctx)
+    return g.value
+
+
+def bt_l2_atomics(ctx, n_bytes: int = 32 << 20, repeats: int = 64, blocks_per_sm: int = 4) -> float:
+    """Measured rate of float64 atomic additions in the context's GPU's L2,
+    additions per second."""
+    g = C.c_double(0.0)
+    _check(lib().bt_l2_atomics(ctx, int(n_bytes), int(repeats), int(blocks_per_sm), C.byref(g)), ctx)
     return g.value
 
 

@@ -563,6 +563,50 @@ BT_API int bt_l2_bandwidth(bt_ctx *c, int64_t bytes, int32_t repeats, int32_t bl
   return BT_OK;
 }
 
+BT_API int bt_l2_atomics(bt_ctx *c, int64_t bytes, int32_t repeats, int32_t blocks_per_sm, double *ops_out) {
+  BT_RANGE();
+  TRY(check_ctx(c));
+  c->err[0] = 0;
+  if (!ops_out) return fail(c, BT_E_INVALID, "ops_out is NULL");
+  if (bytes < ((int64_t)16 << 20) || bytes > ((int64_t)96 << 20) || bytes % 64 != 0)
+    return fail(c, BT_E_INVALID, "bytes must be a multiple of 64 in 16..96 MiB");
+  if (repeats < 1 || repeats > 10000) return fail(c, BT_E_INVALID, "repeats must be in 1..10000");
+  if (blocks_per_sm < 1 || blocks_per_sm > 8) return fail(c, BT_E_INVALID, "blocks_per_sm must be in 1..8");
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  const int blocks = c->n_sm * blocks_per_sm;
+  TRY(ensure(c, c->stage_a, (size_t)bytes));
+  CK(cudaMemsetAsync(c->stage_a.p, 0, (size_t)bytes, st));
+  double *buf = (double *)c->stage_a.p;
+  const uint32_t n_slots = (uint32_t)(bytes / 64);
+  CK(bt::launch_l2_atomics(st, buf, n_slots, 2, blocks));  // warm: the buffer into L2
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  cudaError_t e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) e = bt::launch_l2_atomics(st, buf, n_slots, repeats, blocks);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, BT_E_CUDA, "L2 atomics probe: %s", cudaGetErrorString(e));
+  }
+  // every addition must have landed: the buffer sums to their count
+  std::vector<double> h((size_t)bytes / 8);
+  CK(cudaMemcpy(h.data(), buf, (size_t)bytes, cudaMemcpyDeviceToHost));
+  double sum = 0.0;
+  for (double x : h) sum += x;
+  const double adds = (double)blocks * 256.0 * 8.0;
+  if (sum != adds * (2.0 + repeats))
+    return fail(c, BT_E_CUDA, "L2 atomics probe: the buffer sums to %.0f, not %.0f", sum, adds * (2.0 + repeats));
+  *ops_out = adds * repeats / (ms * 1e-3);
+  return BT_OK;
+}
+
 BT_API int bt_load_scene(bt_ctx *c, const float *verts, int64_t n_verts, const int32_t *tris,
                          int64_t n_tris, const uint8_t *tri_material, const float *refl,
                          int32_t n_materials, int32_t n_bands, int32_t *scene_id_out) {

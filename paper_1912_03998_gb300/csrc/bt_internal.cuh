@@ -595,6 +595,7 @@ cudaError_t launch_set_result(cudaStream_t st, const double *intensity, const in
 // L2 read-bandwidth probe: `blocks` blocks of 256 threads read the n4 float4s
 // of buf `repeats` times; sink holds blocks * 256 floats.
 cudaError_t launch_l2_read(cudaStream_t st, const float4 *buf, int64_t n4, int repeats, float *sink, int blocks);
+cudaError_t launch_l2_atomics(cudaStream_t st, double *buf, uint32_t n_slots, int repeats, int blocks);
 cudaError_t launch_levels(cudaStream_t st, const double *energy, const int *count, const float4 *mics,
                           int64_t n_m, int n_bands, double *level_db, double *intensity, int *path_count);
 }  // namespace bt
