@@ -734,7 +734,8 @@ def main():
                 "fp64": btrace.BT_PREC_FP64, "mixed64": btrace.BT_PREC_MIXED64}[args.precision]
         tr = btrace.Tracer(0)
         try:
-            line["serving"] = serve_once(tr, synth.serving_cities(seed=5, n=8), 200.0, 100, 100, prec,
+            # 300 queries, so that the 99th percentile rests on three of them
+            line["serving"] = serve_once(tr, synth.serving_cities(seed=5, n=8), 200.0, 300, 100, prec,
                                          args.step_lineages, args.oldest_share, args.small_lineages,
                                          fill=args.fill, mix_ratio=args.mix_ratio, mix_floor=args.mix_floor)
         finally:

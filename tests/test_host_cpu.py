@@ -351,3 +351,34 @@ def test_district_matches_its_configuration():
     assert len(w.mics) == 250_000 and np.all(w.mics[:, 2] == np.float32(1.5))
     d = np.diff(np.unique(w.mics[:, 0]))
     assert np.allclose(d, 4.0, atol=1e-3)
+
+
+def test_server_admits_just_in_time(monkeypatch):
+    # with admit_ahead, a waiting query is set up only while the admitted
+    # queries hold fewer untraced lineages than that: with 1, one query at a
+    # time; every query is still traced exactly once and answered in order
+    lib = _FakeLib()
+    for name in ("bt_scene_share", "bt_set_sources", "bt_set_microphones", "bt_beam_axes", "bt_set_directivity",
+                 "bt_trace_ranges", "bt_ranges_stats", "bt_read_levels", "bt_unload_scene", "bt_submit", "bt_poll",
+                 "bt_trace"):
+        monkeypatch.setattr(serve.btrace, name, getattr(lib, name))
+    qs = synth.serving_queries(seed=2, n_queries=8, n_cities=2, rate_qps=1e4, level=3, max_sources=40,
+                               max_mics=3000)
+    srv = serve.Server(_FakeTracer(), [None, None], step_lineages=1500, admit_ahead=1)
+    seen = []
+    orig = srv._admit
+
+    def admit():
+        orig()
+        seen.append(len(srv.active))
+
+    srv._admit = admit
+    done = srv.run(qs, realtime=False)
+    assert [d.index for d in done] == list(range(len(qs)))
+    assert not lib.live and max(seen) == 1
+    # -1 holds back once a shared step's worth of lineages is admitted; the
+    # default (0) admits every waiting query that fits
+    assert serve.Server(_FakeTracer(), [None], step_lineages=1 << 22, admit_ahead=-1).admit_ahead == 1 << 18
+    assert serve.Server(_FakeTracer(), [None], step_lineages=1 << 22, mix_ratio=0.0,
+                        admit_ahead=-1).admit_ahead == 1 << 22
+    assert serve.Server(_FakeTracer(), [None]).admit_ahead == 0
