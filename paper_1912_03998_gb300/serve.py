@@ -33,7 +33,10 @@ mix_floor (2^18), the others' up to that many, so that small queries share
 launches (less per-query launch overhead) without a big one holding the
 oldest back (measured on Poisson streams: at 200 q/s the 99th percentile
 of uncapped steps was 1.4x plain serving's, capped it is within 4 %; under
-overload the cap also raised throughput).
+overload the cap also raised throughput).  The others join a step only
+whole (`partial_fill` off): a big query given part of a step would lose
+its whole trace and go on in step-sized launches with their tails, and the
+queries behind it would wait through all of them.
 
 With `submit_alone`, a query that is the only one to trace and fits one
 step is traced whole with the asynchronous call (bt_submit), behind a
@@ -83,7 +86,7 @@ def set_query_directivity(ctx, sid, q):
 
 
 def step_shares(left, work, budget: int, oldest_share: float = 1.0, quantum: int = 0, small: int = 0,
-                fill: str = "work"):
+                fill: str = "work", partial: bool = True):
     """Lineages each active query traces in the next step.
 
     left[i]: the query's lineages still to trace; work[i]: its remaining
@@ -94,7 +97,10 @@ def step_shares(left, work, budget: int, oldest_share: float = 1.0, quantum: int
     lineage budget (all of it by default: first come, first served, so a big
     query is not held back by the stream behind it); what is left goes to
     the queries shortest remaining work first (`fill="work"`) or in
-    admission order (`fill="arrival"`).  With a nonzero `quantum`
+    admission order (`fill="arrival"`); with `partial` False a query other
+    than the oldest joins only if all its remaining lineages fit, so that
+    none is left part-traced (a part-traced query can no longer be traced
+    whole).  With a nonzero `quantum`
     every query the budget did not reach still gets that many lineages (the
     step then exceeds the budget by up to len(left) quanta).
     """
@@ -116,6 +122,8 @@ def step_shares(left, work, budget: int, oldest_share: float = 1.0, quantum: int
     for i in (sorted(range(n), key=lambda i: work[i]) if fill == "work" else range(n)):
         if b <= 0:
             break
+        if not partial and i > 0 and left[i] - share[i] > b:
+            continue
         g = min(left[i] - share[i], b)
         share[i] += g
         b -= g
@@ -158,7 +166,7 @@ class Server:
                  oldest_share: float = 1.0, small_lineages: int = 0, mem_reserve: int = 1 << 30,
                  submit_alone: bool = False, check_free: bool = True, whole: bool = True,
                  fill: str = "work", mix_ratio: float = 1.0, mix_floor: int = 1 << 18,
-                 admit_ahead: int = 0):
+                 admit_ahead: int = 0, partial_fill: bool = False):
         self.tr = tracer
         self.quantum = int(quantum)
         self.oldest_share = float(oldest_share)
@@ -175,6 +183,7 @@ class Server:
             raise ValueError(f"fill must be 'work' or 'arrival', not {fill!r}")
         self.fill = fill
         self.mix_ratio = float(mix_ratio)
+        self.partial_fill = bool(partial_fill)
         self.mix_floor = int(mix_floor)
         # optional admission just in time: set up (scene share, sources,
         # microphone binning) only while the admitted queries hold fewer
@@ -275,7 +284,7 @@ class Server:
             # mix_ratio - 1 times its own lineages (at least mix_floor in all)
             budget = min(budget, max(int(self.mix_ratio * left[0]), self.mix_floor))
         share = step_shares(left, work, budget, self.oldest_share, self.quantum, self.small_lineages,
-                            self.fill)
+                            self.fill, self.partial_fill)
         ids, begins, ends, params = [], [], [], []
         for a, s in zip(self.active, share):
             if s > 0 and not a["inflight"]:

@@ -31,6 +31,16 @@ def test_step_shares_fill_in_arrival_order():
     assert serve.step_shares(left, work, 10000, fill="arrival") == left
 
 
+def test_step_shares_without_partial_fill():
+    # other queries join only whole: one that does not fit what is left of
+    # the budget is skipped, a smaller one after it still joins
+    left = [300, 5000, 600, 200]
+    work = [l * 5 for l in left]
+    assert serve.step_shares(left, work, 1000) == [300, 0, 500, 200]
+    assert serve.step_shares(left, work, 1000, partial=False) == [300, 0, 0, 200]
+    assert serve.step_shares(left, work, 1100, partial=False) == [300, 0, 600, 200]
+
+
 def test_step_shares_invariants():
     rng = np.random.Generator(np.random.PCG64(3))
     for _ in range(500):
