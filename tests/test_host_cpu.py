@@ -58,6 +58,12 @@ def test_step_shares_invariants():
             assert sum(s) == min(budget, sum(left))
         else:
             assert sum(s) <= budget + n * q
+        # without partial fill every query but the oldest gets all it has
+        # left or nothing, within the budget
+        fill = str(rng.choice(["work", "arrival"]))
+        s = serve.step_shares(left, work, budget, frac, 0, 0, fill, partial=False)
+        assert sum(s) <= budget and 0 <= s[0] <= left[0]
+        assert all(a == 0 or a == l for a, l in zip(s[1:], left[1:]))
 
 
 def test_volume_microphone_grid():
